@@ -1,0 +1,184 @@
+/*
+ * respca.h -- C ABI of the GB300 RES-PCA solver (librespca.so).
+ *
+ * RES-PCA (Peng, Chen, Kang, Li, Cheng, "RES-PCA: A Scalable Approach to
+ * Recovering Low-rank Matrices", arXiv 1904.07497) splits a data matrix
+ * X (d x n, columns are samples) into X = L + S, L made of c groups of
+ * nearly equal columns and S sparse, by solving Eq. (8):
+ *
+ *   min  lambda * sum_i Tr(L d(p_i) (I - 11^T/n_i) d(p_i) L^T) + ||S||_1
+ *   s.t. X = L + S, p_i in {0,1}^n, sum_i p_i = 1
+ *
+ * with the augmented Lagrangian of Eq. (9) and, per iteration, the closed-form
+ * L update of Eq. (18), K-means on the columns of L (Sec. 4.2, Eq. (21)-(22)),
+ * soft-thresholding for S (Eq. (24)) and the multiplier update of Eq. (25),
+ * stopped by the rule of Sec. 5.  Parameters default to Sec. 5.1:
+ * lambda = sqrt(max(n, d)), rho0 = 1e-4, kappa = 1.5.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major: element (r, j) of X is X[j*ldx + r].
+ *   - Pointers are CUDA device pointers unless the entry point's name ends in
+ *     _host; the caller owns all of them.  X is never written.
+ *   - Work is queued on the handle's stream (respca_config.stream); the
+ *     calls return after the solve has finished (they read the convergence
+ *     test back every iteration) and the outputs are ready to use.
+ *   - Errors are returned as respca_status; nothing is thrown across the ABI.
+ *     After an error the outputs are unspecified; respca_last_error() gives
+ *     a one-line description.  RESPCA_ERR_CUDA leaves the handle usable only
+ *     if the CUDA context itself survived.
+ *   - A handle is thread-compatible, not thread-safe: one call at a time.
+ */
+#ifndef RESPCA_H
+#define RESPCA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RESPCA_ABI_VERSION 1
+
+typedef struct respca_ctx *respca_handle;
+
+typedef enum {
+    RESPCA_OK = 0,
+    RESPCA_ERR_INVALID_ARG = 1,     /* a size, pointer, label or parameter is out of range */
+    RESPCA_ERR_NONFINITE_INPUT = 2, /* X holds NaN or Inf */
+    RESPCA_ERR_OOM = 3,             /* device or pinned-host allocation failed */
+    RESPCA_ERR_CUDA = 4,            /* a CUDA call failed */
+    RESPCA_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
+    RESPCA_ERR_UNSUPPORTED = 6      /* a valid request this build does not handle */
+} respca_status;
+
+/* Element type of X. */
+typedef enum { RESPCA_F32 = 0, RESPCA_BF16 = 1, RESPCA_F16 = 2 } respca_dtype;
+
+typedef struct {
+    double rho0;             /* initial penalty rho (Sec. 5.1: 1e-4) */
+    double kappa;            /* penalty growth factor, rho <- kappa rho (Eq. (25); Sec. 5.1: 1.5) */
+    int32_t kmeans_max_iter; /* cap on Lloyd assignment passes per p step (default 100) */
+    int32_t reserved0;
+    uint64_t seed;           /* seed of the k-means++ draws for the initial labels */
+    void *stream;            /* cudaStream_t for all work; NULL = the legacy default stream */
+    int32_t device;          /* CUDA device ordinal; -1 = the device current at respca_create */
+    int32_t reserved1;
+} respca_config;
+
+typedef struct {
+    int32_t iters;           /* ALM iterations run */
+    int32_t converged;       /* 1 if the Sec. 5 criterion fell to tol */
+    double err;              /* max(err_resid, err_dL, err_dS) at exit */
+    double err_resid;        /* ||X - L - S||_F / ||X||_F */
+    double err_dL;           /* ||L_{t+1} - L_t||_F / ||X||_F */
+    double err_dS;           /* ||S_{t+1} - S_t||_F / ||X||_F */
+    double rho_final;        /* rho after the last update */
+    double lambda;           /* the lambda used */
+    int64_t label_changes;   /* labels changed by the p steps, summed over iterations */
+    int64_t lloyd_passes;    /* assignment passes run by the p steps */
+    int64_t assigned_columns;/* columns whose nearest centroid had to be searched */
+    int64_t rechecked_columns;/* near-tie columns re-decided in FP64 */
+    int32_t init_lloyd_passes;/* assignment passes of the initial K-means */
+    int32_t reserved;
+    float ms_total;          /* wall time of the call on the stream (CUDA events) */
+    float ms_init;           /* part of ms_total spent before the first iteration */
+} respca_stats;
+
+/* Optional warm start / checkpoint-resume state (the paper starts from zero;
+ * this hook lets a caller continue an earlier solve or supply a proposal). */
+typedef struct {
+    float *Theta;            /* d x n device multiplier Theta, leading dimension lds; in/out.
+                                NULL: the handle keeps Theta and starts it at zero */
+    double rho;              /* in: rho of the next iteration when warm != 0; out: rho_final */
+    int32_t warm;            /* 1: L, S, Theta and p hold a state to continue from;
+                                0: start from L = S = Theta = 0, rho = rho0 */
+    int32_t reserved;
+} respca_warm;
+
+/* One problem of a batch (respca_solve_batched). Same meaning as the
+ * arguments of respca_solve. */
+typedef struct {
+    int32_t x_dtype;
+    int32_t c;
+    const void *X;
+    int64_t d, n, ldx;
+    double lambda;
+    double tol;
+    int32_t max_iter;
+    int32_t reserved;
+    const int32_t *p0;
+    float *L;
+    float *S;
+    int64_t lds;
+    int32_t *p;
+} respca_problem;
+
+/* Fill *cfg with the defaults above. */
+void respca_config_default(respca_config *cfg);
+
+/* Create a solver handle bound to cfg->device and cfg->stream (cfg NULL =
+ * defaults).  The handle owns its device workspace, grown on demand and freed
+ * by respca_destroy.  Returns RESPCA_ERR_CUDA if no usable device exists. */
+respca_status respca_create(respca_handle *h, const respca_config *cfg);
+
+/* Free the handle and all of its device and pinned-host memory. NULL is a no-op. */
+respca_status respca_destroy(respca_handle h);
+
+/*
+ * Solve Eq. (8) for one matrix (Sec. 4, all four updates per iteration, in the
+ * order L (Sec. 4.1), p (Sec. 4.2), S (Sec. 4.3), Theta and rho (Sec. 4.4)).
+ *
+ *   x_dtype   element type of X (respca_dtype).
+ *   X         d x n device matrix, leading dimension ldx >= d. Read only.
+ *   lambda    weight of the variance term; <= 0 selects sqrt(max(d, n)) (Sec. 5.1).
+ *   c         number of column groups (the rank or a bound on it), 1 <= c <= n.
+ *   tol       stop when max(||X-L-S||, ||dL||, ||dS||)/||X|| <= tol (Sec. 5); >= 0.
+ *   max_iter  iteration cap (>= 0; the paper uses 500).
+ *   p0        optional initial labels (n int32 in [0, c), device); NULL = k-means++
+ *             seeding (cfg.seed) followed by Lloyd on the columns of X.
+ *   L, S      d x n device outputs (FP32), leading dimension lds >= d.
+ *   p         n device int32 output labels (the groups of Eq. (8)).
+ *   warm      optional warm start (see respca_warm); NULL = cold start.
+ *   stats     optional host struct filled on return.
+ * ||X||_F = 0 returns L = S = 0 at once.  Hitting max_iter is not an error
+ * (stats->converged = 0).
+ */
+respca_status respca_solve(respca_handle h, int32_t x_dtype, const void *X, int64_t d,
+                           int64_t n, int64_t ldx, double lambda, int32_t c, double tol,
+                           int32_t max_iter, const int32_t *p0, float *L, float *S,
+                           int64_t lds, int32_t *p, respca_warm *warm, respca_stats *stats);
+
+/* As respca_solve, but X, p0, L, S and p are HOST pointers (pageable or
+ * pinned).  The handle stages them through its device workspace; the
+ * host-to-device and device-to-host copies are part of the call. warm is not
+ * accepted here (pass NULL). */
+respca_status respca_solve_host(respca_handle h, int32_t x_dtype, const void *X, int64_t d,
+                                int64_t n, int64_t ldx, double lambda, int32_t c, double tol,
+                                int32_t max_iter, const int32_t *p0, float *L, float *S,
+                                int64_t lds, int32_t *p, respca_stats *stats);
+
+/* Initial labels alone: k-means++ seeding with cfg.seed (Arthur and
+ * Vassilvitskii's D^2 sampling; splitmix64 uniforms) and Lloyd's method on the
+ * columns of X until no label changes (cap cfg.kmeans_max_iter).  The paper
+ * leaves the initial p open; this is the reading the solver uses when p0 is
+ * NULL.  p: n device int32 output; *passes (nullable host) = assignment passes. */
+respca_status respca_init_labels(respca_handle h, int32_t x_dtype, const void *X, int64_t d,
+                                 int64_t n, int64_t ldx, int32_t c, int32_t *p,
+                                 int32_t *passes);
+
+/* Solve `batch` independent problems (device pointers as in respca_solve).
+ * stats: optional host array of `batch` entries.  The first failing problem's
+ * status is returned; later problems are still attempted. */
+respca_status respca_solve_batched(respca_handle h, int32_t batch, const respca_problem *probs,
+                                   respca_stats *stats);
+
+/* Static description of a status code. */
+const char *respca_status_string(respca_status s);
+
+/* Description of the last error on this handle ("" if none). */
+const char *respca_last_error(respca_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RESPCA_H */

@@ -1,0 +1,453 @@
+// K-means kernels of the RES-PCA p step (Sec. 4.2, Eq. (21)-(22)) and of the
+// initial labels (k-means++ seeding, then Lloyd).
+#include <cfloat>
+#include <climits>
+
+#include "respca_internal.cuh"
+
+namespace respca {
+
+namespace {
+
+inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
+
+// ---------------------------------------------------------------- label sort
+// Stable counting sort of the columns by label (single CTA).  Produces the
+// sorted column order perm, the cluster sizes n_i, and the label-pure tiles
+// of at most kTileCols sorted columns; flags labels outside [0, c).
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_labels(const int32_t* __restrict__ labels, int64_t n, int c, int32_t* __restrict__ perm,
+                  int32_t* __restrict__ counts, int32_t* __restrict__ tile_off,
+                  TileDesc* __restrict__ tiles, DevStatus* __restrict__ status) {
+    extern __shared__ int32_t sh[];
+    int32_t* cnt = sh;            // [c]
+    int32_t* run = sh + c;        // [c] running sorted position
+    int32_t* toff = sh + 2 * c;   // [c + 1]
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int i = threadIdx.x; i < c; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const int32_t l = labels[j];
+        if (l < 0 || l >= c) bad = 1;
+        else atomicAdd(&cnt[l], 1);
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) {
+            status->bad_labels = 1;
+            status->ntiles = 0;
+        }
+        return;
+    }
+    // exclusive scans of the sizes and of the tile counts (warp 0)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int32_t off = 0, toffs = 0;
+        for (int base = 0; base < c; base += 32) {
+            const int i = base + lane;
+            const int32_t v = (i < c) ? cnt[i] : 0;
+            const int32_t tv = (v + kTileCols - 1) / kTileCols;
+            int32_t iv = v, it = tv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t a = __shfl_up_sync(0xffffffffu, iv, o);
+                const int32_t b = __shfl_up_sync(0xffffffffu, it, o);
+                if (lane >= o) {
+                    iv += a;
+                    it += b;
+                }
+            }
+            if (i < c) {
+                run[i] = off + iv - v;
+                toff[i] = toffs + it - tv;
+            }
+            off += __shfl_sync(0xffffffffu, iv, 31);
+            toffs += __shfl_sync(0xffffffffu, it, 31);
+        }
+        if (lane == 0) {
+            toff[c] = toffs;
+            status->ntiles = toffs;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+        counts[i] = cnt[i];
+        tile_off[i] = toff[i];
+        const int nt = toff[i + 1] - toff[i];
+        for (int t = 0; t < nt; ++t) {
+            TileDesc td;
+            td.start = run[i] + t * kTileCols;
+            td.len = min(kTileCols, cnt[i] - t * kTileCols);
+            td.label = i;
+            td.pad = 0;
+            tiles[toff[i] + t] = td;
+        }
+    }
+    if (threadIdx.x == 0) tile_off[c] = toff[c];
+    __syncthreads();
+    // stable scatter, one warp, 32 columns at a time in column order
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned lt = (1u << lane) - 1u;
+        for (int64_t base = 0; base < n; base += 32) {
+            const int64_t j = base + lane;
+            const int32_t l = (j < n) ? labels[j] : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, l);
+            const int rank = __popc(peers & lt);
+            int32_t pos = 0;
+            if (l >= 0) pos = run[l] + rank;
+            __syncwarp();
+            if (l >= 0) {
+                perm[pos] = (int32_t)j;
+                if (rank == 0) run[l] += __popc(peers);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- assignment
+// Nearest centroid for a set of columns of Y (all columns, or the queued list):
+// scores s_i = ||mu_i||^2 - 2 mu_i . y_j over active clusters (n_i > 0), FP32
+// products with Kahan-summed 64-row partials.  When the best two scores are
+// closer than a bound on their rounding error, the candidates within the
+// bound are re-decided with the exact squared distance in FP64, so every
+// decision equals the argmin of the stored values (ties to the lowest index).
+constexpr float kTieRel = 1e-5f;
+
+template <typename TY>
+__global__ void __launch_bounds__(kThreads)
+    k_assign(const TY* __restrict__ Y, int64_t ldy, int64_t d, int64_t n,
+             const int32_t* __restrict__ list, const float* __restrict__ mu,
+             const float* __restrict__ mu_normf, const int32_t* __restrict__ counts, int c,
+             int32_t* __restrict__ labels, DevStatus* __restrict__ status) {
+    extern __shared__ __align__(16) float smem[];
+    constexpr int LS = kAsgCols + 1;          // Ls row stride
+    constexpr int MS = kAsgClusters + 4;      // Ms row stride (float4 aligned)
+    float* Ls = smem;                          // [kAsgRows][LS]
+    float* Ms = Ls + kAsgRows * LS;            // [kAsgRows][MS]
+    float* scores = Ms + kAsgRows * MS;        // [c][LS]
+    __shared__ int64_t colidx[kAsgCols];
+    __shared__ float nrmL[kAsgCols];
+
+    const int64_t total = list ? (int64_t)status->flagged : n;
+    const int64_t base = (int64_t)blockIdx.x * kAsgCols;
+    if (base >= total) return;
+    const int tx = threadIdx.x & 31;
+    const int ty = threadIdx.x >> 5;
+    if (threadIdx.x < kAsgCols) {
+        const int64_t q = base + threadIdx.x;
+        colidx[threadIdx.x] = q < total ? (list ? (int64_t)list[q] : q) : -1;
+    }
+    __syncthreads();
+
+    float nrm = 0.f;
+    for (int cb = 0; cb < c; cb += kAsgClusters) {
+        float acc[8], comp[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = comp[q] = 0.f;
+        for (int64_t k0 = 0; k0 < d; k0 += kAsgRows) {
+            for (int q = ty; q < kAsgCols; q += kThreads / 32) {
+                const int64_t col = colidx[q];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t r = k0 + h * 32 + tx;
+                    float v = 0.f;
+                    if (col >= 0 && r < d) v = XLoad<TY>::one(Y + col * ldy + r);
+                    Ls[(h * 32 + tx) * LS + q] = v;
+                }
+            }
+            for (int i = ty; i < kAsgClusters; i += kThreads / 32) {
+                const int ci = cb + i;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t r = k0 + h * 32 + tx;
+                    Ms[(h * 32 + tx) * MS + i] = (ci < c && r < d) ? mu[(int64_t)ci * d + r] : 0.f;
+                }
+            }
+            __syncthreads();
+            float part[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) part[q] = 0.f;
+#pragma unroll 8
+            for (int k = 0; k < kAsgRows; ++k) {
+                const float lv = Ls[k * LS + tx];
+                const float4 m0 = *reinterpret_cast<const float4*>(&Ms[k * MS + ty * 8]);
+                const float4 m1 = *reinterpret_cast<const float4*>(&Ms[k * MS + ty * 8 + 4]);
+                part[0] = fmaf(m0.x, lv, part[0]);
+                part[1] = fmaf(m0.y, lv, part[1]);
+                part[2] = fmaf(m0.z, lv, part[2]);
+                part[3] = fmaf(m0.w, lv, part[3]);
+                part[4] = fmaf(m1.x, lv, part[4]);
+                part[5] = fmaf(m1.y, lv, part[5]);
+                part[6] = fmaf(m1.z, lv, part[6]);
+                part[7] = fmaf(m1.w, lv, part[7]);
+                if (cb == 0 && ty == 0) nrm = fmaf(lv, lv, nrm);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {   // Kahan accumulation of the slab partials
+                const float y = part[q] - comp[q];
+                const float t = acc[q] + y;
+                comp[q] = (t - acc[q]) - y;
+                acc[q] = t;
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int ci = cb + ty * 8 + q;
+            if (ci < c)
+                scores[ci * LS + tx] = (counts[ci] > 0) ? fmaf(-2.f, acc[q], mu_normf[ci]) : INFINITY;
+        }
+    }
+    if (ty == 0) nrmL[tx] = nrm;
+    __syncthreads();
+
+    const int lane = tx;
+    for (int q = ty * (kAsgCols / 8); q < (ty + 1) * (kAsgCols / 8); ++q) {
+        const int64_t col = colidx[q];
+        if (col < 0) continue;
+        float bs = INFINITY;
+        int bi = INT_MAX;
+        for (int i = lane; i < c; i += 32) {
+            const float s = scores[i * LS + q];
+            if (s < bs) {
+                bs = s;
+                bi = i;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (os < bs || (os == bs && oi < bi)) {
+                bs = os;
+                bi = oi;
+            }
+        }
+        float ss = INFINITY;
+        for (int i = lane; i < c; i += 32) {
+            const float s = scores[i * LS + q];
+            if (i != bi && s < ss) ss = s;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss = fminf(ss, __shfl_xor_sync(0xffffffffu, ss, o));
+        if (bi >= c) continue;   // no finite score: keep the label
+        int newlab = bi;
+        const float margin = kTieRel * (nrmL[q] + fabsf(mu_normf[bi]));
+        if (ss - bs <= margin) {
+            double best = INFINITY;
+            int besti = bi;
+            for (int i = 0; i < c; ++i) {
+                if (!(scores[i * LS + q] <= bs + margin)) continue;
+                double a = 0.0;
+                const float* m = mu + (int64_t)i * d;
+                for (int64_t r = lane; r < d; r += 32) {
+                    const double diff = (double)XLoad<TY>::one(Y + col * ldy + r) - (double)m[r];
+                    a = fma(diff, diff, a);
+                }
+                a = warp_sum(a);
+                if (a < best) {
+                    best = a;
+                    besti = i;
+                }
+            }
+            newlab = besti;
+            if (lane == 0) atomicAdd(&status->rechecked, 1);
+        }
+        if (lane == 0) {
+            const int32_t old = labels[col];
+            if (old != newlab) {
+                labels[col] = newlab;
+                atomicAdd(&status->changed, 1);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- k-means++
+// D2[j] (= or min=) squared distance of column j to the centre centers[k].
+template <typename TX>
+__global__ void __launch_bounds__(kThreads)
+    k_seed_dist(const TX* __restrict__ X, int64_t ldx, int64_t d, int64_t n,
+                const int32_t* __restrict__ centers, int k, double* __restrict__ D2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t ctr = centers[k];
+    const TX* xc = X + ctr * ldx;
+    for (int64_t j = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); j < n; j += warps) {
+        const TX* xj = X + j * ldx;
+        float s = 0.f, comp = 0.f;
+        for (int64_t r0 = 0; r0 < d; r0 += 32 * 8) {
+            float part = 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t r = r0 + u * 32 + lane;
+                if (r < d) {
+                    const float t = XLoad<TX>::one(xj + r) - XLoad<TX>::one(xc + r);
+                    part = fmaf(t, t, part);
+                }
+            }
+            const float y = part - comp;
+            const float t = s + y;
+            comp = (t - s) - y;
+            s = t;
+        }
+        const double v = warp_sum((double)s);
+        if (lane == 0) D2[j] = (k == 0) ? v : fmin(D2[j], v);
+    }
+}
+
+// Pick centre k: the first column whose running sum of D2 exceeds u_k times
+// the total (single CTA; FP64 block scans in column order).
+__global__ void __launch_bounds__(1024)
+    k_seed_pick(const double* __restrict__ D2, int64_t n, const double* __restrict__ u, int k,
+                int32_t* __restrict__ centers) {
+    __shared__ double wsum[32];
+    __shared__ double s_total;
+    __shared__ long long s_first;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double t = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) t += D2[j];
+    t = warp_sum(t);
+    if (lane == 0) wsum[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 32; ++w) s += wsum[w];
+        s_total = s;
+        s_first = LLONG_MAX;
+    }
+    __syncthreads();
+    const double total = s_total;
+    const double uk = u[k];
+    if (!(total > 0.0)) {
+        if (threadIdx.x == 0) {
+            int64_t pick = (int64_t)(uk * (double)n);
+            if (pick >= n) pick = n - 1;
+            centers[k] = (int32_t)pick;
+        }
+        return;
+    }
+    const double target = uk * total;
+    double offset = 0.0;
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t j = base + threadIdx.x;
+        const double v = j < n ? D2[j] : 0.0;
+        double incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double a = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += a;
+        }
+        __syncthreads();
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            double w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double a = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += a;
+            }
+            wsum[lane] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        const double prefix = offset + (warp > 0 ? wsum[warp - 1] : 0.0) + incl;
+        if (j < n && prefix > target) atomicMin(&s_first, (long long)j);
+        __syncthreads();
+        if (s_first != LLONG_MAX) break;
+        offset += wsum[31];
+    }
+    if (s_first == LLONG_MAX) {
+        // rounding left no crossing: the last column with positive mass
+        if (threadIdx.x == 0) {
+            int64_t pick = n - 1;
+            for (int64_t j = n - 1; j >= 0; --j)
+                if (D2[j] > 0.0) {
+                    pick = j;
+                    break;
+                }
+            centers[k] = (int32_t)pick;
+        }
+        return;
+    }
+    if (threadIdx.x == 0) centers[k] = (int32_t)s_first;
+}
+
+template <typename TX>
+__global__ void __launch_bounds__(kThreads)
+    k_gather_centers(const TX* __restrict__ X, int64_t ldx, int64_t d,
+                     const int32_t* __restrict__ centers, float* __restrict__ mu,
+                     int32_t* __restrict__ counts) {
+    const int k = blockIdx.y;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[k] = 1;
+    if (r < d) mu[(int64_t)k * d + r] = XLoad<TX>::one(X + (int64_t)centers[k] * ldx + r);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_sort_labels(const int32_t* labels, int64_t n, int c, int32_t* perm,
+                               int32_t* counts, int32_t* tile_off, TileDesc* tiles,
+                               DevStatus* status, cudaStream_t st) {
+    const size_t smem = sizeof(int32_t) * (size_t)(3 * c + 1);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_sort_labels,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_sort_labels<<<1, kSortThreads, smem, st>>>(labels, n, c, perm, counts, tile_off, tiles, status);
+    return cudaGetLastError();
+}
+
+size_t assign_smem_bytes(int c) {
+    const int LS = kAsgCols + 1, MS = kAsgClusters + 4;
+    return sizeof(float) * ((size_t)kAsgRows * LS + (size_t)kAsgRows * MS + (size_t)c * LS);
+}
+
+cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
+                          const int32_t* list, const float* mu, const float* mu_normf,
+                          const int32_t* counts, int c, int32_t* labels, DevStatus* status,
+                          cudaStream_t st) {
+    const size_t smem = assign_smem_bytes(c);
+    const int grid = grid_for(n, kAsgCols);
+    cudaError_t e = cudaSuccess;
+    RESPCA_DISPATCH_X(dtype, TY, {
+        e = cudaFuncSetAttribute(k_assign<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            k_assign<TY><<<grid, kThreads, smem, st>>>((const TY*)Y, ldy, d, n, list, mu, mu_normf,
+                                                       counts, c, labels, status);
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_dist(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
+                             const int32_t* centers, int k, double* D2, cudaStream_t st) {
+    const int grid = grid_for(n, kThreads / 32);
+    RESPCA_DISPATCH_X(dtype, TX, {
+        k_seed_dist<TX><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, centers, k, D2);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_pick(const double* D2, int64_t n, const double* u, int k, int32_t* centers,
+                             cudaStream_t st) {
+    k_seed_pick<<<1, 1024, 0, st>>>(D2, n, u, k, centers);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_centers(int dtype, const void* X, int64_t ldx, int64_t d,
+                                  const int32_t* centers, int c, float* mu, int32_t* counts,
+                                  cudaStream_t st) {
+    const dim3 grid(grid_for(d, kThreads), c);
+    RESPCA_DISPATCH_X(dtype, TX, {
+        k_gather_centers<TX><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, centers, mu, counts);
+    });
+    return cudaGetLastError();
+}
+
+}  // namespace respca

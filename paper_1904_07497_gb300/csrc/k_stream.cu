@@ -1,0 +1,575 @@
+// Streaming kernels of the RES-PCA iteration (HBM-bound work).
+//
+// k_iteration is the hot path: one pass over X, S, Theta and L_prev per ALM
+// iteration computes D, the L step (Eq. (18)), the S step (Eq. (24)), the
+// multiplier step (Eq. (25)), the three Frobenius quantities of the Sec. 5
+// stopping rule, each column's squared distance to its own centroid (for the
+// exact pruning of the K-means search) and the cluster sums of the NEXT
+// iteration's D under the current labels, which become the next centroids
+// whenever the p step keeps every label.
+#include <cfloat>
+
+#include "respca_internal.cuh"
+
+namespace respca {
+
+namespace {
+
+// ---------------------------------------------------------------- ||X||_F
+template <typename TX, bool VEC>
+__global__ void __launch_bounds__(kThreads) k_fro2(const TX* __restrict__ X, int64_t d, int64_t n,
+                                                   int64_t ldx, double* __restrict__ part,
+                                                   DevStatus* __restrict__ status) {
+    __shared__ double red[kThreads / 32];
+    const int64_t rows_per_unit = kThreads * 4;
+    const int64_t seg = (d + rows_per_unit - 1) / rows_per_unit;
+    const int64_t units = seg * n;
+    double acc = 0.0;
+    bool bad = false;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int64_t j = u / seg;
+        const int64_t r = (u % seg) * rows_per_unit + threadIdx.x * 4;
+        const TX* col = X + j * ldx;
+        float s = 0.f;
+        if (VEC) {
+            if (r < d) {
+                const float4 v = XLoad<TX>::four(col + r);
+                bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+                s = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (r + q < d) {
+                    const float v = XLoad<TX>::one(col + r + q);
+                    bad |= !isfinite(v);
+                    s = fmaf(v, v, s);
+                }
+        }
+        acc += (double)s;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&status->nonfinite, 1);
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+    __shared__ double red[kThreads / 32];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) t += part[i];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+        *out = s;
+    }
+}
+
+// ---------------------------------------------------------------- fused iteration
+// One element of one ALM iteration.  l, sn, tn are the new L, S, Theta.
+__device__ __forceinline__ void alm_element(float x, float s, float t, float l0, float m,
+                                            const IterScalars& sc, float& l, float& sn, float& tn,
+                                            float& own, float& nr, float& ndl, float& nds,
+                                            float& dnext) {
+    const float tr = t * sc.inv_rho;
+    const float dv = (x - s) + tr;                    // D = X - S + Theta/rho (after Eq. (14))
+    l = fmaf(sc.a, dv, sc.b * m);                     // Eq. (18): a D_j + (1-a) mean of cluster
+    const float bb = (x - l) + tr;                    // B = X - L + Theta/rho
+    const float mag = fabsf(bb) - sc.inv_rho;
+    sn = mag > 0.f ? copysignf(mag, bb) : 0.f;        // Eq. (24), sign(0) = 0
+    tn = fminf(fmaxf(sc.rho * bb, -1.f), 1.f);        // Eq. (25): Theta + rho(X-L-S) = clip(rho B)
+    const float res = (x - l) - sn;
+    const float dl = l - l0;
+    const float ds = sn - s;
+    const float e = l - m;
+    own = fmaf(e, e, own);
+    nr = fmaf(res, res, nr);
+    ndl = fmaf(dl, dl, ndl);
+    nds = fmaf(ds, ds, nds);
+    dnext = (x - sn) + tn * sc.inv_rho_next;          // D of the next iteration
+}
+
+template <typename TX, bool VEC>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_iteration(const TX* __restrict__ X, int64_t ldx, float* __restrict__ L, float* __restrict__ S,
+                float* __restrict__ Th, int64_t lds, const float* __restrict__ mu,
+                const int32_t* __restrict__ perm, const TileDesc* __restrict__ tiles,
+                const DevStatus* __restrict__ status, int64_t d, int64_t n, IterScalars sc,
+                float* __restrict__ Dpart, float* __restrict__ own_part,
+                double* __restrict__ norm_part) {
+    __shared__ float red[kThreads / 32][kChunkRows];
+    __shared__ double nred[kThreads / 32][3];
+    const int tile_idx = blockIdx.x;
+    if (tile_idx >= status->ntiles) return;
+    const TileDesc td = tiles[tile_idx];
+    const int64_t r0 = (int64_t)blockIdx.y * kChunkRows;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const float* mup = mu + (int64_t)td.label * d;
+
+    float4 m[4], acc[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int64_t rr = r0 + s * 128 + lane * 4;
+        acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        m[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (VEC) {
+            if (rr < d) m[s] = *reinterpret_cast<const float4*>(mup + rr);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (rr + q < d) f4set(m[s], q, mup[rr + q]);
+        }
+    }
+    float nr = 0.f, ndl = 0.f, nds = 0.f;
+
+    for (int k = warp; k < td.len; k += kThreads / 32) {
+        const int64_t col = perm[td.start + k];
+        const TX* xc = X + col * ldx;
+        float* lc = L + col * lds;
+        float* scol = S + col * lds;
+        float* tc = Th + col * lds;
+        float own = 0.f;
+        if (VEC) {
+            float4 xv[4], sv[4], tv[4], lv[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int64_t rr = r0 + s * 128 + lane * 4;
+                if (rr < d) {
+                    xv[s] = XLoad<TX>::four(xc + rr);
+                    sv[s] = __ldcs(reinterpret_cast<const float4*>(scol + rr));
+                    tv[s] = __ldcs(reinterpret_cast<const float4*>(tc + rr));
+                    lv[s] = __ldcs(reinterpret_cast<const float4*>(lc + rr));
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int64_t rr = r0 + s * 128 + lane * 4;
+                if (rr < d) {
+                    float4 lo, so, to;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float l, sn, tn, dn;
+                        alm_element(f4get(xv[s], q), f4get(sv[s], q), f4get(tv[s], q),
+                                    f4get(lv[s], q), f4get(m[s], q), sc, l, sn, tn, own, nr, ndl,
+                                    nds, dn);
+                        f4set(lo, q, l);
+                        f4set(so, q, sn);
+                        f4set(to, q, tn);
+                        f4set(acc[s], q, f4get(acc[s], q) + dn);
+                    }
+                    __stcs(reinterpret_cast<float4*>(lc + rr), lo);
+                    __stcs(reinterpret_cast<float4*>(scol + rr), so);
+                    __stcs(reinterpret_cast<float4*>(tc + rr), to);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int64_t rr = r0 + s * 128 + lane * 4;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (rr + q < d) {
+                        float l, sn, tn, dn;
+                        alm_element(XLoad<TX>::one(xc + rr + q), scol[rr + q], tc[rr + q],
+                                    lc[rr + q], f4get(m[s], q), sc, l, sn, tn, own, nr, ndl, nds,
+                                    dn);
+                        lc[rr + q] = l;
+                        scol[rr + q] = sn;
+                        tc[rr + q] = tn;
+                        f4set(acc[s], q, f4get(acc[s], q) + dn);
+                    }
+                }
+            }
+        }
+        own = warp_sum(own);
+        if (lane == 0) own_part[(int64_t)blockIdx.y * n + col] = own;
+    }
+
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[warp][s * 128 + lane * 4 + q] = f4get(acc[s], q);
+    const double w0 = warp_sum((double)nr), w1 = warp_sum((double)ndl), w2 = warp_sum((double)nds);
+    if (lane == 0) {
+        nred[warp][0] = w0;
+        nred[warp][1] = w1;
+        nred[warp][2] = w2;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kChunkRows; i += kThreads) {
+        const int64_t r = r0 + i;
+        if (r < d) {
+            float v = 0.f;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) v += red[w][i];
+            Dpart[(int64_t)tile_idx * d + r] = v;
+        }
+    }
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += nred[w][threadIdx.x];
+        norm_part[((int64_t)blockIdx.y * gridDim.x + tile_idx) * 3 + threadIdx.x] = t;
+    }
+}
+
+// ---------------------------------------------------------------- cluster sums
+// Sum, per tile and row, the columns of X (kSumX), L (kSumL) or
+// D = X - S + Theta * inv_rho (kSumD).
+template <int MODE, typename TX, bool VEC>
+__global__ void __launch_bounds__(kThreads)
+    k_colsum(const TX* __restrict__ X, int64_t ldx, const float* __restrict__ L,
+             const float* __restrict__ S, const float* __restrict__ Th, int64_t lds,
+             float inv_rho, const int32_t* __restrict__ perm, const TileDesc* __restrict__ tiles,
+             const DevStatus* __restrict__ status, int64_t d, float* __restrict__ Dpart) {
+    __shared__ float red[kThreads / 32][kChunkRows];
+    const int tile_idx = blockIdx.x;
+    if (tile_idx >= status->ntiles) return;
+    const TileDesc td = tiles[tile_idx];
+    const int64_t r0 = (int64_t)blockIdx.y * kChunkRows;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    float4 acc[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    for (int k = warp; k < td.len; k += kThreads / 32) {
+        const int64_t col = perm[td.start + k];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int64_t rr = r0 + s * 128 + lane * 4;
+            if (VEC) {
+                if (rr < d) {
+                    float4 v;
+                    if (MODE == kSumX) {
+                        v = XLoad<TX>::four(X + col * ldx + rr);
+                    } else if (MODE == kSumL) {
+                        v = *reinterpret_cast<const float4*>(L + col * lds + rr);
+                    } else {
+                        const float4 x = XLoad<TX>::four(X + col * ldx + rr);
+                        const float4 sv = *reinterpret_cast<const float4*>(S + col * lds + rr);
+                        const float4 tv = *reinterpret_cast<const float4*>(Th + col * lds + rr);
+                        v = make_float4((x.x - sv.x) + tv.x * inv_rho, (x.y - sv.y) + tv.y * inv_rho,
+                                        (x.z - sv.z) + tv.z * inv_rho, (x.w - sv.w) + tv.w * inv_rho);
+                    }
+                    acc[s].x += v.x;
+                    acc[s].y += v.y;
+                    acc[s].z += v.z;
+                    acc[s].w += v.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t r = rr + q;
+                    if (r < d) {
+                        float v;
+                        if (MODE == kSumX) v = XLoad<TX>::one(X + col * ldx + r);
+                        else if (MODE == kSumL) v = L[col * lds + r];
+                        else v = (XLoad<TX>::one(X + col * ldx + r) - S[col * lds + r]) +
+                                 Th[col * lds + r] * inv_rho;
+                        f4set(acc[s], q, f4get(acc[s], q) + v);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[warp][s * 128 + lane * 4 + q] = f4get(acc[s], q);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kChunkRows; i += kThreads) {
+        const int64_t r = r0 + i;
+        if (r < d) {
+            float v = 0.f;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) v += red[w][i];
+            Dpart[(int64_t)tile_idx * d + r] = v;
+        }
+    }
+}
+
+// mu[i][r] = (sum over the tiles of cluster i of Dpart[t][r]) / n_i, summed in
+// FP64 in tile order.  Empty clusters keep their old centroid (they take part
+// in no assignment).
+__global__ void __launch_bounds__(kThreads)
+    k_centroids(const float* __restrict__ Dpart, const int32_t* __restrict__ tile_off,
+                const int32_t* __restrict__ counts, int64_t d, float* __restrict__ mu) {
+    const int i = blockIdx.y;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int cnt = counts[i];
+    if (cnt == 0 || r >= d) return;
+    const int t0 = tile_off[i], t1 = tile_off[i + 1];
+    double s = 0.0;
+    for (int t = t0; t < t1; ++t) s += (double)Dpart[(int64_t)t * d + r];
+    mu[(int64_t)i * d + r] = (float)(s / (double)cnt);
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_mu_norms(const float* __restrict__ mu, int64_t d, double* __restrict__ mu_norm2,
+               float* __restrict__ mu_normf) {
+    __shared__ double red[kThreads / 32];
+    const int i = blockIdx.x;
+    const float* m = mu + (int64_t)i * d;
+    double acc = 0.0;
+    for (int64_t r = threadIdx.x; r < d; r += kThreads) acc += (double)m[r] * (double)m[r];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        mu_norm2[i] = t;
+        mu_normf[i] = (float)t;
+    }
+}
+
+// Pairwise squared centroid distances, one CTA per 64-row slab, staged in
+// shared memory; partial sums are added into pair_ss (c x c, upper triangle).
+constexpr int kSepRows = 64;
+constexpr int kSepMaxC = 256;
+
+__global__ void __launch_bounds__(kThreads)
+    k_pair_dist(const float* __restrict__ mu, const int32_t* __restrict__ counts, int c, int64_t d,
+                float* __restrict__ pair_ss) {
+    extern __shared__ __align__(16) float ms[];  // [c][kSepRows]
+    const int64_t r0 = (int64_t)blockIdx.x * kSepRows;
+    for (int idx = threadIdx.x; idx < c * kSepRows; idx += kThreads) {
+        const int i = idx / kSepRows, rr = idx % kSepRows;
+        ms[idx] = (r0 + rr < d) ? mu[(int64_t)i * d + r0 + rr] : 0.f;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < c * c; p += kThreads) {
+        const int i = p / c, j = p % c;
+        if (j <= i || counts[i] == 0 || counts[j] == 0) continue;
+        const float* a = ms + i * kSepRows;
+        const float* b = ms + j * kSepRows;
+        float s = 0.f;
+#pragma unroll 16
+        for (int k = 0; k < kSepRows; ++k) {
+            const float t = a[k] - b[k];
+            s = fmaf(t, t, s);
+        }
+        atomicAdd(&pair_ss[p], s);
+    }
+}
+
+__global__ void k_sep_min(const float* __restrict__ pair_ss, const int32_t* __restrict__ counts,
+                          int c, double* __restrict__ sep2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c) return;
+    double best = INFINITY;
+    if (counts[i] > 0)
+        for (int j = 0; j < c; ++j) {
+            if (j == i || counts[j] == 0) continue;
+            const int a = min(i, j), b = max(i, j);
+            const double v = (double)pair_ss[(int64_t)a * c + b];
+            if (v < best) best = v;
+        }
+    sep2[i] = best;
+}
+
+__global__ void k_fill_double(double* __restrict__ p, int count, double v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) p[i] = v;
+}
+
+// ---------------------------------------------------------------- finalisers
+__global__ void __launch_bounds__(kThreads)
+    k_reduce_norms(const double* __restrict__ norm_part, int max_tiles, int nchunks,
+                   DevStatus* __restrict__ status) {
+    __shared__ double red[kThreads / 32][3];
+    const int ntiles = status->ntiles;
+    const int64_t units = (int64_t)ntiles * nchunks;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int64_t u = threadIdx.x; u < units; u += kThreads) {
+        const int64_t y = u / ntiles, t = u % ntiles;
+        const double* p = norm_part + (y * max_tiles + t) * 3;
+        a0 += p[0];
+        a1 += p[1];
+        a2 += p[2];
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = a0;
+        red[threadIdx.x >> 5][1] = a1;
+        red[threadIdx.x >> 5][2] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
+        status->norm2[threadIdx.x] = t;
+    }
+}
+
+// A column keeps its label for sure when its distance to its own centroid is
+// less than half the distance from that centroid to every other active one
+// (triangle inequality): ||L_j - mu_p|| < sep_p / 2.  All others are queued
+// for the nearest-centroid search.
+__global__ void __launch_bounds__(kThreads)
+    k_flag_columns(const float* __restrict__ own_part, int nchunks, int64_t n,
+                   const int32_t* __restrict__ labels, const double* __restrict__ sep2,
+                   double safety, int32_t* __restrict__ flag_list, DevStatus* __restrict__ status) {
+    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    bool flag = false;
+    if (j < n) {
+        double own = 0.0;
+        for (int ch = 0; ch < nchunks; ++ch) own += (double)own_part[(int64_t)ch * n + j];
+        const double sep = sep2[labels[j]];
+        flag = !(4.0 * own * (1.0 + 1e-5) < sep * safety);
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && mask) base = atomicAdd(&status->flagged, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (flag) flag_list[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)j;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_count_changed(const int32_t* __restrict__ labels, const int32_t* __restrict__ prev, int64_t n,
+                    DevStatus* __restrict__ status) {
+    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const bool ch = j < n && labels[j] != prev[j];
+    const unsigned mask = __ballot_sync(0xffffffffu, ch);
+    if ((threadIdx.x & 31) == 0 && mask) atomicAdd(&status->label_changes, __popc(mask));
+}
+
+inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_fro2(int dtype, const void* X, int64_t d, int64_t n, int64_t ldx, double* part,
+                        int nparts, DevStatus* status, cudaStream_t st) {
+    const int64_t seg = (d + kThreads * 4 - 1) / (kThreads * 4);
+    const int64_t units = seg * n;
+    const int grid = (int)(units < nparts ? units : nparts);
+    RESPCA_DISPATCH_X(dtype, TX, {
+        const bool vec = (ldx % 4 == 0) && (d % 4 == 0) &&
+                         (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(TX)) == 0);
+        if (vec)
+            k_fro2<TX, true><<<grid, kThreads, 0, st>>>((const TX*)X, d, n, ldx, part, status);
+        else
+            k_fro2<TX, false><<<grid, kThreads, 0, st>>>((const TX*)X, d, n, ldx, part, status);
+    });
+    k_sum_parts<<<1, kThreads, 0, st>>>(part, grid, &status->x_norm2);
+    return cudaGetLastError();
+}
+
+template <int M, typename TX>
+void colsum_mode(dim3 grid, const TX* x, int64_t ldx, const float* L, const float* S, const float* Th,
+                 int64_t lds, float inv_rho, const int32_t* perm, const TileDesc* tiles,
+                 const DevStatus* status, int64_t d, float* Dpart, bool vec, cudaStream_t st) {
+    if (vec)
+        k_colsum<M, TX, true><<<grid, kThreads, 0, st>>>(x, ldx, L, S, Th, lds, inv_rho, perm, tiles,
+                                                         status, d, Dpart);
+    else
+        k_colsum<M, TX, false><<<grid, kThreads, 0, st>>>(x, ldx, L, S, Th, lds, inv_rho, perm, tiles,
+                                                          status, d, Dpart);
+}
+
+cudaError_t launch_colsum(int mode, int dtype, const void* X, int64_t ldx, const float* L,
+                          const float* S, const float* Th, int64_t lds, float inv_rho,
+                          const int32_t* perm, const TileDesc* tiles, int max_tiles,
+                          const DevStatus* status, int64_t d, float* Dpart, bool vec,
+                          cudaStream_t st) {
+    const dim3 grid(max_tiles, grid_for(d, kChunkRows));
+    if (mode == kSumL) {
+        colsum_mode<kSumL, float>(grid, nullptr, 0, L, S, Th, lds, inv_rho, perm, tiles, status, d,
+                                  Dpart, vec, st);
+        return cudaGetLastError();
+    }
+    RESPCA_DISPATCH_X(dtype, TX, {
+        if (mode == kSumX)
+            colsum_mode<kSumX, TX>(grid, (const TX*)X, ldx, L, S, Th, lds, inv_rho, perm, tiles,
+                                   status, d, Dpart, vec, st);
+        else
+            colsum_mode<kSumD, TX>(grid, (const TX*)X, ldx, L, S, Th, lds, inv_rho, perm, tiles,
+                                   status, d, Dpart, vec, st);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centroids(const float* Dpart, const int32_t* tile_off, const int32_t* counts,
+                             int c, int64_t d, float* mu, cudaStream_t st) {
+    const dim3 grid(grid_for(d, kThreads), c);
+    k_centroids<<<grid, kThreads, 0, st>>>(Dpart, tile_off, counts, d, mu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu_norms(const float* mu, int c, int64_t d, double* mu_norm2, float* mu_normf,
+                            cudaStream_t st) {
+    k_mu_norms<<<c, kThreads, 0, st>>>(mu, d, mu_norm2, mu_normf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_separation(const float* mu, const int32_t* counts, int c, int64_t d,
+                              float* pair_ss, double* sep2, cudaStream_t st) {
+    if (c > kSepMaxC) {
+        // No pruning for very many clusters: every column is searched.
+        k_fill_double<<<grid_for(c, kThreads), kThreads, 0, st>>>(sep2, c, 0.0);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(pair_ss, 0, sizeof(float) * (size_t)c * c, st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(float) * (size_t)c * kSepRows;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_pair_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_pair_dist<<<grid_for(d, kSepRows), kThreads, smem, st>>>(mu, counts, c, d, pair_ss);
+    k_sep_min<<<grid_for(c, kThreads), kThreads, 0, st>>>(pair_ss, counts, c, sep2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iteration(int dtype, const void* X, int64_t ldx, float* L, float* S, float* Th,
+                             int64_t lds, const float* mu, const int32_t* perm,
+                             const TileDesc* tiles, int max_tiles, const DevStatus* status,
+                             int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
+                             double* norm_part, bool vec, cudaStream_t st) {
+    const dim3 grid(max_tiles, grid_for(d, kChunkRows));
+    RESPCA_DISPATCH_X(dtype, TX, {
+        if (vec)
+            k_iteration<TX, true><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, L, S, Th, lds, mu,
+                                                             perm, tiles, status, d, n, sc, Dpart,
+                                                             own_part, norm_part);
+        else
+            k_iteration<TX, false><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, L, S, Th, lds, mu,
+                                                              perm, tiles, status, d, n, sc, Dpart,
+                                                              own_part, norm_part);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchunks,
+                                DevStatus* status, cudaStream_t st) {
+    k_reduce_norms<<<1, kThreads, 0, st>>>(norm_part, max_tiles, nchunks, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_columns(const float* own_part, int nchunks, int64_t n,
+                                const int32_t* labels, const double* sep2, double safety,
+                                int32_t* flag_list, DevStatus* status, cudaStream_t st) {
+    k_flag_columns<<<grid_for(n, kThreads), kThreads, 0, st>>>(own_part, nchunks, n, labels, sep2,
+                                                               safety, flag_list, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_changed(const int32_t* labels, const int32_t* prev, int64_t n,
+                                 DevStatus* status, cudaStream_t st) {
+    k_count_changed<<<grid_for(n, kThreads), kThreads, 0, st>>>(labels, prev, n, status);
+    return cudaGetLastError();
+}
+
+}  // namespace respca

@@ -1,0 +1,586 @@
+// Host driver and C ABI of the RES-PCA solver (see include/respca.h).
+//
+// One solve = the initial labels (given, or k-means++ + Lloyd on X), then ALM
+// iterations in the order of Sec. 4: L (Sec. 4.1), p (Sec. 4.2), S (Sec. 4.3),
+// Theta and rho (Sec. 4.4), stopped by the rule of Sec. 5.  Every iteration is
+// one fused HBM pass (k_iteration) plus small kernels; the host reads back a
+// 64-byte status block once per iteration to run the stopping test and, when
+// some labels moved, the remaining Lloyd passes of the p step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/respca.h"
+#include "respca_internal.cuh"
+
+using namespace respca;
+
+namespace {
+
+// splitmix64 (Steele, Lea, Flood 2014): the draws of the k-means++ seeding.
+uint64_t splitmix64_next(uint64_t& s) {
+    s += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+double unit_draw(uint64_t& s) { return (double)(splitmix64_next(s) >> 11) * (1.0 / 9007199254740992.0); }
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct respca_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    respca_config cfg{};
+    std::string last_error;
+
+    // device workspace, grown on demand
+    DevBuf theta, mu, mu_norm2, mu_normf, pair_ss, sep2, perm, counts, tile_off, tiles, labels_prev,
+        Dpart, own_part, norm_part, flag_list, seedD2, centers, seed_u, fro_part, status,
+        hX, hL, hS, hp, hp0;
+    DevStatus* hstat = nullptr;     // pinned mirror of the status block
+    double* hseed_u = nullptr;      // pinned staging of the seeding draws
+    size_t hseed_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+};
+
+namespace {
+
+constexpr int kFroParts = 1216;  // 152 SMs x 8
+
+respca_status fail(respca_ctx* h, respca_status s, const char* what) {
+    if (h) h->last_error = what;
+    return s;
+}
+
+respca_status cuda_fail(respca_ctx* h, cudaError_t e, const char* where) {
+    if (h) h->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return (e == cudaErrorMemoryAllocation) ? RESPCA_ERR_OOM : RESPCA_ERR_CUDA;
+}
+
+#define CK(expr)                                                   \
+    do {                                                           \
+        cudaError_t _e = (expr);                                   \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, #expr);     \
+    } while (0)
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess) b.bytes = bytes;
+    return e;
+}
+
+template <typename T>
+T* P(DevBuf& b) { return reinterpret_cast<T*>(b.p); }
+
+int max_tiles_for(int64_t n, int c) { return (int)((n + kTileCols - 1) / kTileCols) + c; }
+int nchunks_for(int64_t d) { return (int)((d + kChunkRows - 1) / kChunkRows); }
+
+size_t elem_size(int dtype) { return dtype == RESPCA_F32 ? 4 : 2; }
+
+respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64_t lds,
+                               bool need_theta) {
+    const int mt = max_tiles_for(n, c);
+    const int nch = nchunks_for(d);
+    if (need_theta) CK(ensure(h->theta, sizeof(float) * (size_t)lds * n));
+    CK(ensure(h->mu, sizeof(float) * (size_t)c * d));
+    CK(ensure(h->mu_norm2, sizeof(double) * c));
+    CK(ensure(h->mu_normf, sizeof(float) * c));
+    CK(ensure(h->pair_ss, sizeof(float) * (size_t)std::min(c, 256) * std::min(c, 256)));
+    CK(ensure(h->sep2, sizeof(double) * c));
+    CK(ensure(h->perm, sizeof(int32_t) * n));
+    CK(ensure(h->counts, sizeof(int32_t) * c));
+    CK(ensure(h->tile_off, sizeof(int32_t) * (c + 1)));
+    CK(ensure(h->tiles, sizeof(TileDesc) * mt));
+    CK(ensure(h->labels_prev, sizeof(int32_t) * n));
+    CK(ensure(h->Dpart, sizeof(float) * (size_t)mt * d));
+    CK(ensure(h->own_part, sizeof(float) * (size_t)nch * n));
+    CK(ensure(h->norm_part, sizeof(double) * 3 * (size_t)mt * nch));
+    CK(ensure(h->flag_list, sizeof(int32_t) * n));
+    CK(ensure(h->seedD2, sizeof(double) * n));
+    CK(ensure(h->centers, sizeof(int32_t) * c));
+    CK(ensure(h->seed_u, sizeof(double) * c));
+    CK(ensure(h->fro_part, sizeof(double) * kFroParts));
+    CK(ensure(h->status, sizeof(DevStatus)));
+    if (h->hseed_cap < (size_t)c) {
+        if (h->hseed_u) cudaFreeHost(h->hseed_u);
+        h->hseed_u = nullptr;
+        h->hseed_cap = 0;
+        CK(cudaMallocHost(&h->hseed_u, sizeof(double) * c));
+        h->hseed_cap = c;
+    }
+    return RESPCA_OK;
+}
+
+respca_status read_status(respca_ctx* h) {
+    CK(cudaMemcpyAsync(h->hstat, h->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return RESPCA_OK;
+}
+
+// Zero the per-pass counters of the status block (not the running totals).
+cudaError_t zero_counters(respca_ctx* h) {
+    DevStatus* s = P<DevStatus>(h->status);
+    return cudaMemsetAsync(&s->flagged, 0, 3 * sizeof(int32_t), h->stream);
+}
+
+// Centroids mu (and their norms and separations) from the tile sums in Dpart.
+respca_status finish_centroids(respca_ctx* h, int c, int64_t d) {
+    CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c, d,
+                        P<float>(h->mu), h->stream));
+    CK(launch_mu_norms(P<float>(h->mu), c, d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
+                       h->stream));
+    CK(launch_separation(P<float>(h->mu), P<int32_t>(h->counts), c, d, P<float>(h->pair_ss),
+                         P<double>(h->sep2), h->stream));
+    return RESPCA_OK;
+}
+
+struct Problem {
+    int dtype;
+    const void* X;
+    int64_t d, n, ldx;
+    int c;
+    float* L;
+    float* S;
+    float* Th;
+    int64_t lds;
+    int32_t* p;
+    bool vec;     // 16-byte vector path usable for X, L, S, Theta, mu
+};
+
+// Initial labels: k-means++ seeding (D^2 sampling with splitmix64 draws),
+// then Lloyd on the columns of X until no label changes.
+respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out) {
+    const int c = pb.c;
+    uint64_t st = h->cfg.seed;
+    for (int k = 0; k < c; ++k) h->hseed_u[k] = unit_draw(st);
+    int first = (int)(h->hseed_u[0] * (double)pb.n);
+    if (first >= pb.n) first = (int)pb.n - 1;
+    CK(cudaMemcpyAsync(h->seed_u.p, h->hseed_u, sizeof(double) * c, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->centers.p, &first, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(launch_seed_dist(pb.dtype, pb.X, pb.ldx, pb.d, pb.n, P<int32_t>(h->centers), 0,
+                        P<double>(h->seedD2), h->stream));
+    for (int k = 1; k < c; ++k) {
+        CK(launch_seed_pick(P<double>(h->seedD2), pb.n, P<double>(h->seed_u), k, P<int32_t>(h->centers),
+                            h->stream));
+        if (k + 1 < c)
+            CK(launch_seed_dist(pb.dtype, pb.X, pb.ldx, pb.d, pb.n, P<int32_t>(h->centers), k,
+                                P<double>(h->seedD2), h->stream));
+    }
+    // the stack value `first` must outlive its async copy
+    CK(cudaStreamSynchronize(h->stream));
+    CK(launch_gather_centers(pb.dtype, pb.X, pb.ldx, pb.d, P<int32_t>(h->centers), c, P<float>(h->mu),
+                             P<int32_t>(h->counts), h->stream));
+    CK(launch_mu_norms(P<float>(h->mu), c, pb.d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
+                       h->stream));
+    CK(cudaMemsetAsync(pb.p, 0xFF, sizeof(int32_t) * pb.n, h->stream));
+    DevStatus* ds = P<DevStatus>(h->status);
+    int passes = 0;
+    const int km = std::max(1, h->cfg.kmeans_max_iter);
+    while (passes < km) {
+        CK(zero_counters(h));
+        CK(launch_assign(pb.dtype, pb.X, pb.ldx, pb.d, pb.n, nullptr, P<float>(h->mu),
+                         P<float>(h->mu_normf), P<int32_t>(h->counts), c, pb.p, ds, h->stream));
+        ++passes;
+        respca_status rs = read_status(h);
+        if (rs != RESPCA_OK) return rs;
+        if (h->hstat->changed == 0) break;
+        CK(launch_sort_labels(pb.p, pb.n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
+                              P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
+        CK(launch_colsum(kSumX, pb.dtype, pb.X, pb.ldx, nullptr, nullptr, nullptr, 0, 0.f,
+                         P<int32_t>(h->perm), P<TileDesc>(h->tiles), max_tiles_for(pb.n, c), ds, pb.d,
+                         P<float>(h->Dpart), pb.vec, h->stream));
+        CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c,
+                            pb.d, P<float>(h->mu), h->stream));
+        CK(launch_mu_norms(P<float>(h->mu), c, pb.d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
+                           h->stream));
+    }
+    if (passes_out) *passes_out = passes;
+    return RESPCA_OK;
+}
+
+bool vec_ok(const void* p, int64_t ld, size_t esz) {
+    return (reinterpret_cast<uintptr_t>(p) % (4 * esz) == 0) && (ld % 4 == 0);
+}
+
+respca_status check_args(respca_ctx* h, int dtype, const void* X, int64_t d, int64_t n, int64_t ldx,
+                         double lambda, int c, double tol, int max_iter, float* L, float* S,
+                         int64_t lds, int32_t* p) {
+    if (!h) return RESPCA_ERR_INVALID_ARG;
+    if (dtype < 0 || dtype > 2) return fail(h, RESPCA_ERR_INVALID_ARG, "x_dtype must be 0, 1 or 2");
+    if (!X || !L || !S || !p) return fail(h, RESPCA_ERR_INVALID_ARG, "null X, L, S or p");
+    if (d <= 0 || n <= 0) return fail(h, RESPCA_ERR_INVALID_ARG, "d and n must be positive");
+    if (n > INT32_MAX - 64) return fail(h, RESPCA_ERR_INVALID_ARG, "n too large");
+    if (ldx < d || lds < d) return fail(h, RESPCA_ERR_INVALID_ARG, "leading dimension < d");
+    if (c < 1 || c > n) return fail(h, RESPCA_ERR_INVALID_ARG, "c must satisfy 1 <= c <= n");
+    if (c > kMaxClusters) return fail(h, RESPCA_ERR_UNSUPPORTED, "c above 1024 is not supported");
+    if (!std::isfinite(lambda)) return fail(h, RESPCA_ERR_INVALID_ARG, "lambda not finite");
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(h, RESPCA_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (max_iter < 0) return fail(h, RESPCA_ERR_INVALID_ARG, "max_iter < 0");
+    if ((int64_t)(d / kChunkRows) >= 65535) return fail(h, RESPCA_ERR_UNSUPPORTED, "d too large");
+    return RESPCA_OK;
+}
+
+double safety_factor(int64_t d) {
+    // relative rounding slack on the FP32 squared separations (sums of d
+    // positive terms) used by the pruning test
+    double s = 1.0 - 2.0 * (double)d * 6.0e-8 - 1e-6;
+    return s < 0.5 ? 0.5 : s;
+}
+
+respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int64_t n, int64_t ldx,
+                         double lambda, int c, double tol, int max_iter, const int32_t* p0, float* L,
+                         float* S, int64_t lds, int32_t* p, respca_warm* warm, respca_stats* stats) {
+    respca_status rs = check_args(h, dtype, X, d, n, ldx, lambda, c, tol, max_iter, L, S, lds, p);
+    if (rs != RESPCA_OK) return rs;
+    const bool is_warm = warm && warm->warm;
+    if (is_warm && !(warm->rho > 0.0)) return fail(h, RESPCA_ERR_INVALID_ARG, "warm start needs rho > 0");
+    if (is_warm && !warm->Theta) return fail(h, RESPCA_ERR_INVALID_ARG, "warm start needs Theta");
+    CK(cudaSetDevice(h->device));
+    const bool user_theta = warm && warm->Theta;
+    rs = ensure_workspace(h, d, n, c, lds, !user_theta);
+    if (rs != RESPCA_OK) return rs;
+    h->last_error.clear();
+
+    respca_stats out{};
+    CK(cudaEventRecord(h->ev0, h->stream));
+    DevStatus* ds = P<DevStatus>(h->status);
+    CK(cudaMemsetAsync(ds, 0, sizeof(DevStatus), h->stream));
+    CK(launch_fro2(dtype, X, d, n, ldx, P<double>(h->fro_part), kFroParts, ds, h->stream));
+    rs = read_status(h);
+    if (rs != RESPCA_OK) return rs;
+    if (h->hstat->nonfinite) return fail(h, RESPCA_ERR_NONFINITE_INPUT, "X holds NaN or Inf");
+    const double nx = std::sqrt(h->hstat->x_norm2);
+    const double lam = lambda > 0.0 ? lambda : std::sqrt((double)std::max(d, n));
+    out.lambda = lam;
+
+    Problem pb;
+    pb.dtype = dtype;
+    pb.X = X;
+    pb.d = d;
+    pb.n = n;
+    pb.ldx = ldx;
+    pb.c = c;
+    pb.L = L;
+    pb.S = S;
+    pb.Th = user_theta ? warm->Theta : P<float>(h->theta);
+    pb.lds = lds;
+    pb.p = p;
+    pb.vec = vec_ok(X, ldx, elem_size(dtype)) && vec_ok(L, lds, 4) && vec_ok(S, lds, 4) &&
+             vec_ok(pb.Th, lds, 4) && (d % 4 == 0);
+
+    double rho = is_warm ? warm->rho : h->cfg.rho0;
+    if (!is_warm) {
+        if (p0) {
+            CK(cudaMemcpyAsync(p, p0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
+        } else if (nx > 0.0) {
+            int passes = 0;
+            rs = init_labels_impl(h, pb, &passes);
+            if (rs != RESPCA_OK) return rs;
+            out.init_lloyd_passes = passes;
+        } else {
+            CK(cudaMemsetAsync(p, 0, sizeof(int32_t) * n, h->stream));
+        }
+        CK(cudaMemset2DAsync(L, sizeof(float) * lds, 0, sizeof(float) * d, n, h->stream));
+        CK(cudaMemset2DAsync(S, sizeof(float) * lds, 0, sizeof(float) * d, n, h->stream));
+        CK(cudaMemset2DAsync(pb.Th, sizeof(float) * lds, 0, sizeof(float) * d, n, h->stream));
+    }
+    // sort the labels into tiles (and validate caller labels)
+    const int mt = max_tiles_for(n, c);
+    const int nch = nchunks_for(d);
+    CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts), P<int32_t>(h->tile_off),
+                          P<TileDesc>(h->tiles), ds, h->stream));
+    rs = read_status(h);
+    if (rs != RESPCA_OK) return rs;
+    if (h->hstat->bad_labels) return fail(h, RESPCA_ERR_INVALID_ARG, "labels outside [0, c)");
+
+    if (nx == 0.0) {
+        CK(cudaMemset2DAsync(L, sizeof(float) * lds, 0, sizeof(float) * d, n, h->stream));
+        CK(cudaMemset2DAsync(S, sizeof(float) * lds, 0, sizeof(float) * d, n, h->stream));
+        CK(cudaEventRecord(h->ev1, h->stream));
+        CK(cudaEventSynchronize(h->ev1));
+        out.converged = 1;
+        out.rho_final = rho;
+        cudaEventElapsedTime(&out.ms_total, h->ev0, h->ev1);
+        if (warm) warm->rho = rho;
+        if (stats) *stats = out;
+        return RESPCA_OK;
+    }
+
+    // centroids of D = X - S + Theta/rho under the current labels
+    CK(launch_colsum(kSumD, dtype, X, ldx, nullptr, S, pb.Th, lds, (float)(1.0 / rho),
+                     P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart), pb.vec,
+                     h->stream));
+    rs = finish_centroids(h, c, d);
+    if (rs != RESPCA_OK) return rs;
+    CK(cudaEventRecord(h->ev2, h->stream));
+
+    const int km = std::max(1, h->cfg.kmeans_max_iter);
+    const double kappa = h->cfg.kappa;
+    const double safety = safety_factor(d);
+    for (int t = 0; t < max_iter; ++t) {
+        const double rho_next = rho * kappa;
+        IterScalars sc;
+        sc.a = (float)(rho / (2.0 * lam + rho));
+        sc.b = (float)(2.0 * lam / (2.0 * lam + rho));
+        sc.inv_rho = (float)(1.0 / rho);
+        sc.rho = (float)std::min(rho, (double)FLT_MAX);
+        sc.inv_rho_next = (float)(1.0 / rho_next);
+
+        CK(zero_counters(h));
+        CK(cudaMemcpyAsync(h->labels_prev.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
+        // L, S, Theta, norms, own distances and next-D sums in one pass
+        CK(launch_iteration(dtype, X, ldx, L, S, pb.Th, lds, P<float>(h->mu), P<int32_t>(h->perm),
+                            P<TileDesc>(h->tiles), mt, ds, d, n, sc, P<float>(h->Dpart),
+                            P<float>(h->own_part), P<double>(h->norm_part), pb.vec, h->stream));
+        CK(launch_reduce_norms(P<double>(h->norm_part), mt, nch, ds, h->stream));
+        // p step: first Lloyd assignment, searching only the columns the bound cannot settle
+        CK(launch_flag_columns(P<float>(h->own_part), nch, n, p, P<double>(h->sep2), safety,
+                               P<int32_t>(h->flag_list), ds, h->stream));
+        CK(launch_assign(RESPCA_F32, L, lds, d, n, P<int32_t>(h->flag_list), P<float>(h->mu),
+                         P<float>(h->mu_normf), P<int32_t>(h->counts), c, p, ds, h->stream));
+        rs = read_status(h);
+        if (rs != RESPCA_OK) return rs;
+        out.lloyd_passes += 1;
+        out.assigned_columns += h->hstat->flagged;
+        out.rechecked_columns += h->hstat->rechecked;
+        const double r2 = h->hstat->norm2[0], dl2 = h->hstat->norm2[1], ds2 = h->hstat->norm2[2];
+
+        if (h->hstat->changed == 0) {
+            // labels kept: the next centroids are the D sums of this pass
+            rs = finish_centroids(h, c, d);
+            if (rs != RESPCA_OK) return rs;
+        } else {
+            // Lloyd on the columns of L until no label changes
+            int passes = 1;
+            while (passes < km) {
+                CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
+                                      P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
+                CK(launch_colsum(kSumL, RESPCA_F32, nullptr, 0, L, nullptr, nullptr, lds, 0.f,
+                                 P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d,
+                                 P<float>(h->Dpart), pb.vec, h->stream));
+                CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts),
+                                    c, d, P<float>(h->mu), h->stream));
+                CK(launch_mu_norms(P<float>(h->mu), c, d, P<double>(h->mu_norm2),
+                                   P<float>(h->mu_normf), h->stream));
+                CK(zero_counters(h));
+                CK(launch_assign(RESPCA_F32, L, lds, d, n, nullptr, P<float>(h->mu),
+                                 P<float>(h->mu_normf), P<int32_t>(h->counts), c, p, ds, h->stream));
+                rs = read_status(h);
+                if (rs != RESPCA_OK) return rs;
+                ++passes;
+                out.lloyd_passes += 1;
+                out.assigned_columns += n;
+                out.rechecked_columns += h->hstat->rechecked;
+                if (h->hstat->changed == 0) break;
+            }
+            // next centroids: D = X - S + Theta/rho_{t+1} under the final labels
+            CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
+                                  P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
+            CK(launch_colsum(kSumD, dtype, X, ldx, nullptr, S, pb.Th, lds, sc.inv_rho_next,
+                             P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart),
+                             pb.vec, h->stream));
+            rs = finish_centroids(h, c, d);
+            if (rs != RESPCA_OK) return rs;
+            CK(launch_count_changed(p, P<int32_t>(h->labels_prev), n, ds, h->stream));
+        }
+        rho = rho_next;
+        out.iters = t + 1;
+        out.err_resid = std::sqrt(r2) / nx;
+        out.err_dL = std::sqrt(dl2) / nx;
+        out.err_dS = std::sqrt(ds2) / nx;
+        out.err = std::max(out.err_resid, std::max(out.err_dL, out.err_dS));
+        if (out.err <= tol) {
+            out.converged = 1;
+            break;
+        }
+    }
+    CK(cudaEventRecord(h->ev1, h->stream));
+    rs = read_status(h);
+    if (rs != RESPCA_OK) return rs;
+    out.label_changes = h->hstat->label_changes;
+    out.rho_final = rho;
+    cudaEventElapsedTime(&out.ms_total, h->ev0, h->ev1);
+    cudaEventElapsedTime(&out.ms_init, h->ev0, h->ev2);
+    if (warm) warm->rho = rho;
+    if (stats) *stats = out;
+    return RESPCA_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+extern "C" {
+
+void respca_config_default(respca_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->rho0 = 1e-4;
+    cfg->kappa = 1.5;
+    cfg->kmeans_max_iter = 100;
+    cfg->seed = 0;
+    cfg->stream = nullptr;
+    cfg->device = -1;
+}
+
+respca_status respca_create(respca_handle* out, const respca_config* cfg) {
+    if (!out) return RESPCA_ERR_INVALID_ARG;
+    *out = nullptr;
+    respca_config c;
+    if (cfg) c = *cfg;
+    else respca_config_default(&c);
+    if (!(c.rho0 > 0.0) || !(c.kappa > 0.0) || !std::isfinite(c.rho0) || !std::isfinite(c.kappa))
+        return RESPCA_ERR_INVALID_ARG;
+    int dev = c.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return RESPCA_ERR_CUDA;
+    if (cudaSetDevice(dev) != cudaSuccess) return RESPCA_ERR_CUDA;
+    respca_ctx* h = new (std::nothrow) respca_ctx();
+    if (!h) return RESPCA_ERR_OOM;
+    h->cfg = c;
+    h->device = dev;
+    h->stream = reinterpret_cast<cudaStream_t>(c.stream);
+    if (cudaMallocHost(&h->hstat, sizeof(DevStatus)) != cudaSuccess ||
+        cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+        cudaEventCreate(&h->ev2) != cudaSuccess) {
+        respca_destroy(h);
+        return RESPCA_ERR_OOM;
+    }
+    *out = h;
+    return RESPCA_OK;
+}
+
+respca_status respca_destroy(respca_handle h) {
+    if (!h) return RESPCA_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    DevBuf* bufs[] = {&h->theta, &h->mu, &h->mu_norm2, &h->mu_normf, &h->pair_ss, &h->sep2, &h->perm,
+                      &h->counts, &h->tile_off, &h->tiles, &h->labels_prev, &h->Dpart, &h->own_part,
+                      &h->norm_part, &h->flag_list, &h->seedD2, &h->centers, &h->seed_u, &h->fro_part,
+                      &h->status, &h->hX, &h->hL, &h->hS, &h->hp, &h->hp0};
+    for (DevBuf* b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (h->hstat) cudaFreeHost(h->hstat);
+    if (h->hseed_u) cudaFreeHost(h->hseed_u);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->ev2) cudaEventDestroy(h->ev2);
+    delete h;
+    return RESPCA_OK;
+}
+
+respca_status respca_solve(respca_handle h, int32_t x_dtype, const void* X, int64_t d, int64_t n,
+                           int64_t ldx, double lambda, int32_t c, double tol, int32_t max_iter,
+                           const int32_t* p0, float* L, float* S, int64_t lds, int32_t* p,
+                           respca_warm* warm, respca_stats* stats) {
+    return solve_impl(h, x_dtype, X, d, n, ldx, lambda, c, tol, max_iter, p0, L, S, lds, p, warm, stats);
+}
+
+respca_status respca_solve_host(respca_handle h, int32_t x_dtype, const void* X, int64_t d, int64_t n,
+                                int64_t ldx, double lambda, int32_t c, double tol, int32_t max_iter,
+                                const int32_t* p0, float* L, float* S, int64_t lds, int32_t* p,
+                                respca_stats* stats) {
+    respca_status rs = check_args(h, x_dtype, X, d, n, ldx, lambda, c, tol, max_iter, L, S, lds, p);
+    if (rs != RESPCA_OK) return rs;
+    CK(cudaSetDevice(h->device));
+    const size_t esz = elem_size(x_dtype);
+    // device copies with leading dimension rounded up to 4 elements (16-byte columns)
+    const int64_t dpad = (d + 3) / 4 * 4;
+    CK(ensure(h->hX, esz * (size_t)dpad * n));
+    CK(ensure(h->hL, sizeof(float) * (size_t)dpad * n));
+    CK(ensure(h->hS, sizeof(float) * (size_t)dpad * n));
+    CK(ensure(h->hp, sizeof(int32_t) * n));
+    if (p0) CK(ensure(h->hp0, sizeof(int32_t) * n));
+    CK(cudaMemcpy2DAsync(h->hX.p, esz * dpad, X, esz * ldx, esz * d, n, cudaMemcpyHostToDevice, h->stream));
+    if (dpad != d) {
+        // zero the padding rows so no uninitialised value is ever read
+        CK(cudaMemset2DAsync((char*)h->hX.p + esz * d, esz * dpad, 0, esz * (dpad - d), n, h->stream));
+    }
+    if (p0) CK(cudaMemcpyAsync(h->hp0.p, p0, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+    rs = solve_impl(h, x_dtype, h->hX.p, d, n, dpad, lambda, c, tol, max_iter,
+                    p0 ? P<int32_t>(h->hp0) : nullptr, P<float>(h->hL), P<float>(h->hS), dpad,
+                    P<int32_t>(h->hp), nullptr, stats);
+    if (rs != RESPCA_OK) return rs;
+    CK(cudaMemcpy2DAsync(L, sizeof(float) * lds, h->hL.p, sizeof(float) * dpad, sizeof(float) * d, n,
+                         cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpy2DAsync(S, sizeof(float) * lds, h->hS.p, sizeof(float) * dpad, sizeof(float) * d, n,
+                         cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(p, h->hp.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return RESPCA_OK;
+}
+
+respca_status respca_init_labels(respca_handle h, int32_t x_dtype, const void* X, int64_t d, int64_t n,
+                                 int64_t ldx, int32_t c, int32_t* p, int32_t* passes) {
+    if (!h) return RESPCA_ERR_INVALID_ARG;
+    if (x_dtype < 0 || x_dtype > 2 || !X || !p || d <= 0 || n <= 0 || ldx < d || c < 1 || c > n)
+        return fail(h, RESPCA_ERR_INVALID_ARG, "invalid arguments");
+    if (c > kMaxClusters) return fail(h, RESPCA_ERR_UNSUPPORTED, "c above 1024 is not supported");
+    CK(cudaSetDevice(h->device));
+    respca_status rs = ensure_workspace(h, d, n, c, d, false);
+    if (rs != RESPCA_OK) return rs;
+    Problem pb{};
+    pb.dtype = x_dtype;
+    pb.X = X;
+    pb.d = d;
+    pb.n = n;
+    pb.ldx = ldx;
+    pb.c = c;
+    pb.p = p;
+    pb.vec = vec_ok(X, ldx, elem_size(x_dtype)) && (d % 4 == 0);
+    CK(cudaMemsetAsync(h->status.p, 0, sizeof(DevStatus), h->stream));
+    int np = 0;
+    rs = init_labels_impl(h, pb, &np);
+    if (rs != RESPCA_OK) return rs;
+    if (passes) *passes = np;
+    return RESPCA_OK;
+}
+
+respca_status respca_solve_batched(respca_handle h, int32_t batch, const respca_problem* probs,
+                                   respca_stats* stats) {
+    if (!h || batch < 0 || (batch > 0 && !probs)) return RESPCA_ERR_INVALID_ARG;
+    respca_status first = RESPCA_OK;
+    for (int32_t b = 0; b < batch; ++b) {
+        const respca_problem& q = probs[b];
+        respca_status rs = respca_solve(h, q.x_dtype, q.X, q.d, q.n, q.ldx, q.lambda, q.c, q.tol,
+                                        q.max_iter, q.p0, q.L, q.S, q.lds, q.p, nullptr,
+                                        stats ? &stats[b] : nullptr);
+        if (rs != RESPCA_OK && first == RESPCA_OK) first = rs;
+    }
+    return first;
+}
+
+const char* respca_status_string(respca_status s) {
+    switch (s) {
+        case RESPCA_OK: return "ok";
+        case RESPCA_ERR_INVALID_ARG: return "invalid argument";
+        case RESPCA_ERR_NONFINITE_INPUT: return "non-finite input";
+        case RESPCA_ERR_OOM: return "out of memory";
+        case RESPCA_ERR_CUDA: return "CUDA error";
+        case RESPCA_ERR_TIMEOUT: return "device wait timed out";
+        case RESPCA_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+const char* respca_last_error(respca_handle h) { return h ? h->last_error.c_str() : ""; }
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// Internal declarations shared by the RES-PCA CUDA translation units.
+//
+// Data layout in HBM (all column-major, a column = one sample):
+//   X      d x n, leading dim ldx, FP32 / BF16 / FP16 (read only)
+//   L, S   d x n FP32, leading dim lds (caller's outputs, updated in place)
+//   Theta  d x n FP32, leading dim lds (handle workspace or caller's)
+//   mu     c x d FP32, cluster i's centroid contiguous: mu[i*d + r]
+//   labels n int32
+// Columns are visited in label-sorted order (perm) through "tiles": runs of
+// at most kTileCols consecutive sorted columns that share one label, so a
+// thread can sum a row of one cluster in a register.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace respca {
+
+constexpr int kThreads = 256;       // threads per CTA of the streaming kernels
+constexpr int kTileCols = 32;       // columns per label-pure tile
+constexpr int kChunkRows = 512;     // rows per CTA in the streaming kernels
+constexpr int kAsgCols = 32;        // columns per CTA in the assignment kernel
+constexpr int kAsgRows = 64;        // rows staged per step in the assignment kernel
+constexpr int kAsgClusters = 64;    // centroids per register block in the assignment kernel
+constexpr int kMaxClusters = 1024;  // largest c this build accepts
+constexpr int kSortThreads = 1024;
+
+// Per-iteration scalars, derived in FP64 on the host and rounded once.
+struct IterScalars {
+    float a;             // rho / (2 lambda + rho)          (Eq. (18), first term)
+    float b;             // 2 lambda / (2 lambda + rho)      (Eq. (18), mean term)
+    float inv_rho;       // 1 / rho_t
+    float rho;           // rho_t, capped at FLT_MAX
+    float inv_rho_next;  // 1 / rho_{t+1}
+};
+
+struct TileDesc {
+    int32_t start;  // first sorted position
+    int32_t len;    // columns in the tile (1..kTileCols)
+    int32_t label;  // cluster of every column in the tile
+    int32_t pad;
+};
+
+// Device-side status block, read back once per iteration.
+struct DevStatus {
+    double norm2[3];        // sums of squares of X-L-S, L-L_prev, S-S_prev
+    double x_norm2;         // ||X||_F^2
+    int32_t flagged;        // columns queued for a nearest-centroid search
+    int32_t changed;        // labels changed by the last assignment pass
+    int32_t rechecked;      // near-tie columns re-decided in FP64
+    int32_t nonfinite;      // X holds NaN/Inf
+    int32_t ntiles;         // tiles of the current sort
+    int32_t bad_labels;     // labels outside [0, c)
+    int32_t label_changes;  // running total of changed labels (vs. start of iteration)
+    int32_t pad;
+};
+
+// Mode of the column-group sum kernel.
+enum SumMode : int { kSumX = 0, kSumL = 1, kSumD = 2 };
+
+// ---------------------------------------------------------------- launchers
+// (each returns the launch status; all run on `st`)
+cudaError_t launch_fro2(int dtype, const void* X, int64_t d, int64_t n, int64_t ldx,
+                        double* part, int nparts, DevStatus* status, cudaStream_t st);
+
+cudaError_t launch_sort_labels(const int32_t* labels, int64_t n, int c, int32_t* perm,
+                               int32_t* counts, int32_t* tile_off, TileDesc* tiles,
+                               DevStatus* status, cudaStream_t st);
+
+cudaError_t launch_colsum(int mode, int dtype, const void* X, int64_t ldx, const float* L,
+                          const float* S, const float* Th, int64_t lds, float inv_rho,
+                          const int32_t* perm, const TileDesc* tiles, int max_tiles,
+                          const DevStatus* status, int64_t d, float* Dpart, bool vec,
+                          cudaStream_t st);
+
+cudaError_t launch_centroids(const float* Dpart, const int32_t* tile_off, const int32_t* counts,
+                             int c, int64_t d, float* mu, cudaStream_t st);
+
+cudaError_t launch_mu_norms(const float* mu, int c, int64_t d, double* mu_norm2, float* mu_normf,
+                            cudaStream_t st);
+
+cudaError_t launch_separation(const float* mu, const int32_t* counts, int c, int64_t d,
+                              float* pair_ss, double* sep2, cudaStream_t st);
+
+cudaError_t launch_iteration(int dtype, const void* X, int64_t ldx, float* L, float* S, float* Th,
+                             int64_t lds, const float* mu, const int32_t* perm,
+                             const TileDesc* tiles, int max_tiles, const DevStatus* status,
+                             int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
+                             double* norm_part, bool vec, cudaStream_t st);
+
+cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchunks,
+                                DevStatus* status, cudaStream_t st);
+
+cudaError_t launch_flag_columns(const float* own_part, int nchunks, int64_t n,
+                                const int32_t* labels, const double* sep2, double safety,
+                                int32_t* flag_list, DevStatus* status, cudaStream_t st);
+
+cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
+                          const int32_t* list, const float* mu, const float* mu_normf,
+                          const int32_t* counts, int c, int32_t* labels, DevStatus* status,
+                          cudaStream_t st);
+
+cudaError_t launch_count_changed(const int32_t* labels, const int32_t* prev, int64_t n,
+                                 DevStatus* status, cudaStream_t st);
+
+cudaError_t launch_seed_dist(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
+                             const int32_t* centers, int k, double* D2, cudaStream_t st);
+
+cudaError_t launch_seed_pick(const double* D2, int64_t n, const double* u, int k,
+                             int32_t* centers, cudaStream_t st);
+
+cudaError_t launch_gather_centers(int dtype, const void* X, int64_t ldx, int64_t d,
+                                  const int32_t* centers, int c, float* mu, int32_t* counts,
+                                  cudaStream_t st);
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Element loads of X for the three supported element types.
+template <typename T>
+struct XLoad;
+
+template <>
+struct XLoad<float> {
+    static __device__ __forceinline__ float one(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float4 four(const float* p) {
+        return __ldg(reinterpret_cast<const float4*>(p));
+    }
+};
+
+template <>
+struct XLoad<__nv_bfloat16> {
+    static __device__ __forceinline__ float one(const __nv_bfloat16* p) {
+        return __bfloat162float(p[0]);
+    }
+    static __device__ __forceinline__ float4 four(const __nv_bfloat16* p) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+        const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+        const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+};
+
+template <>
+struct XLoad<__half> {
+    static __device__ __forceinline__ float one(const __half* p) { return __half2float(p[0]); }
+    static __device__ __forceinline__ float4 four(const __half* p) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+        const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+};
+
+__device__ __forceinline__ float f4get(const float4& v, int q) {
+    return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ void f4set(float4& v, int q, float x) {
+    if (q == 0) v.x = x;
+    else if (q == 1) v.y = x;
+    else if (q == 2) v.z = x;
+    else v.w = x;
+}
+
+// Dispatch a runtime dtype (0 f32, 1 bf16, 2 f16) to a template lambda.
+#define RESPCA_DISPATCH_X(dtype, TX, ...)                       \
+    do {                                                        \
+        if ((dtype) == 1) {                                     \
+            using TX = __nv_bfloat16;                           \
+            __VA_ARGS__;                                        \
+        } else if ((dtype) == 2) {                              \
+            using TX = __half;                                  \
+            __VA_ARGS__;                                        \
+        } else {                                                \
+            using TX = float;                                   \
+            __VA_ARGS__;                                        \
+        }                                                       \
+    } while (0)
+
+}  // namespace respca

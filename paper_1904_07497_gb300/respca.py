@@ -1,0 +1,270 @@
+"""Python binding of librespca.so (the C ABI in include/respca.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+The functions carry the C names.  Matrices are torch tensors on the handle's
+device, column-major d x n: ``X.stride(0) == 1`` and the leading dimension is
+``X.stride(1)`` (a contiguous (n, d) tensor transposed is such a view).
+If the compiled library is missing this module raises; there is no other
+code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "librespca.so")
+
+RESPCA_OK = 0
+RESPCA_ERR_INVALID_ARG = 1
+RESPCA_ERR_NONFINITE_INPUT = 2
+RESPCA_ERR_OOM = 3
+RESPCA_ERR_CUDA = 4
+RESPCA_ERR_TIMEOUT = 5
+RESPCA_ERR_UNSUPPORTED = 6
+
+RESPCA_F32, RESPCA_BF16, RESPCA_F16 = 0, 1, 2
+
+
+class respca_config(ctypes.Structure):
+    _fields_ = [("rho0", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("kmeans_max_iter", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+                ("device", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+
+
+class respca_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("err", ctypes.c_double), ("err_resid", ctypes.c_double),
+                ("err_dL", ctypes.c_double), ("err_dS", ctypes.c_double),
+                ("rho_final", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("label_changes", ctypes.c_int64), ("lloyd_passes", ctypes.c_int64),
+                ("assigned_columns", ctypes.c_int64), ("rechecked_columns", ctypes.c_int64),
+                ("init_lloyd_passes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms_total", ctypes.c_float), ("ms_init", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {(k[:-1] if k.endswith("_") else k): getattr(self, k) for k, _ in self._fields_
+                if not k.startswith("reserved")}
+
+
+class respca_warm(ctypes.Structure):
+    _fields_ = [("Theta", ctypes.c_void_p), ("rho", ctypes.c_double),
+                ("warm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class respca_problem(ctypes.Structure):
+    _fields_ = [("x_dtype", ctypes.c_int32), ("c", ctypes.c_int32), ("X", ctypes.c_void_p),
+                ("d", ctypes.c_int64), ("n", ctypes.c_int64), ("ldx", ctypes.c_int64),
+                ("lambda_", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("p0", ctypes.c_void_p), ("L", ctypes.c_void_p), ("S", ctypes.c_void_p),
+                ("lds", ctypes.c_int64), ("p", ctypes.c_void_p)]
+
+
+_lib = None
+_I64 = ctypes.c_int64
+_VP = ctypes.c_void_p
+
+
+def load():
+    """Load librespca.so (build it first with __graft_entry__.build() or
+    paper_1904_07497_gb300._build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"RES-PCA CUDA library not built: {LIB_PATH} is missing")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.respca_config_default.argtypes = [ctypes.POINTER(respca_config)]
+    lib.respca_config_default.restype = None
+    lib.respca_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(respca_config)]
+    lib.respca_create.restype = ctypes.c_int
+    lib.respca_destroy.argtypes = [_VP]
+    lib.respca_destroy.restype = ctypes.c_int
+    solve_args = [_VP, ctypes.c_int32, _VP, _I64, _I64, _I64, ctypes.c_double, ctypes.c_int32,
+                  ctypes.c_double, ctypes.c_int32, _VP, _VP, _VP, _I64, _VP]
+    lib.respca_solve.argtypes = solve_args + [ctypes.POINTER(respca_warm), ctypes.POINTER(respca_stats)]
+    lib.respca_solve.restype = ctypes.c_int
+    lib.respca_solve_host.argtypes = solve_args + [ctypes.POINTER(respca_stats)]
+    lib.respca_solve_host.restype = ctypes.c_int
+    lib.respca_init_labels.argtypes = [_VP, ctypes.c_int32, _VP, _I64, _I64, _I64, ctypes.c_int32,
+                                       _VP, ctypes.POINTER(ctypes.c_int32)]
+    lib.respca_init_labels.restype = ctypes.c_int
+    lib.respca_solve_batched.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(respca_problem),
+                                         ctypes.POINTER(respca_stats)]
+    lib.respca_solve_batched.restype = ctypes.c_int
+    lib.respca_status_string.argtypes = [ctypes.c_int]
+    lib.respca_status_string.restype = ctypes.c_char_p
+    lib.respca_last_error.argtypes = [_VP]
+    lib.respca_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class RespcaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _check(h, rc: int, where: str):
+    if rc != RESPCA_OK:
+        lib = load()
+        detail = lib.respca_last_error(h).decode() if h else ""
+        raise RespcaError(rc, f"{where}: {lib.respca_status_string(rc).decode()}"
+                              + (f" -- {detail}" if detail else ""))
+
+
+def _dtype_code(t) -> int:
+    import torch
+    return {torch.float32: RESPCA_F32, torch.bfloat16: RESPCA_BF16,
+            torch.float16: RESPCA_F16}[t.dtype]
+
+
+def _colmajor(t, name):
+    if t.dim() != 2 or t.stride(0) != 1:
+        raise ValueError(f"{name} must be a column-major (d, n) view (stride(0) == 1)")
+    return max(t.stride(1), t.shape[0])
+
+
+# ------------------------------------------------------------------ C names
+def respca_config_default() -> respca_config:
+    cfg = respca_config()
+    load().respca_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def respca_create(cfg: respca_config | None = None):
+    h = _VP()
+    _check(None, load().respca_create(ctypes.byref(h), ctypes.byref(cfg) if cfg else None),
+           "respca_create")
+    return h
+
+
+def respca_destroy(h) -> None:
+    _check(None, load().respca_destroy(h), "respca_destroy")
+
+
+def respca_solve(h, X, c: int, L, S, p, *, lam: float = 0.0, tol: float = 1e-6,
+                 max_iter: int = 500, p0=None, warm: respca_warm | None = None) -> dict:
+    """X, L, S: (d, n) column-major CUDA tensors; p, p0: int32 (n,) CUDA tensors."""
+    d, n = X.shape
+    ldx = _colmajor(X, "X")
+    lds = _colmajor(L, "L")
+    if _colmajor(S, "S") != lds:
+        raise ValueError("L and S must share a leading dimension")
+    st = respca_stats()
+    rc = load().respca_solve(h, _dtype_code(X), X.data_ptr(), d, n, ldx, float(lam), int(c),
+                             float(tol), int(max_iter), p0.data_ptr() if p0 is not None else None,
+                             L.data_ptr(), S.data_ptr(), lds, p.data_ptr(),
+                             ctypes.byref(warm) if warm is not None else None, ctypes.byref(st))
+    _check(h, rc, "respca_solve")
+    return st.as_dict()
+
+
+def respca_solve_host(h, X, c: int, L, S, p, *, lam: float = 0.0, tol: float = 1e-6,
+                      max_iter: int = 500, p0=None) -> dict:
+    """X, L, S: (d, n) column-major CPU tensors (pinned or not); p: int32 CPU."""
+    d, n = X.shape
+    ldx = _colmajor(X, "X")
+    lds = _colmajor(L, "L")
+    st = respca_stats()
+    rc = load().respca_solve_host(h, _dtype_code(X), X.data_ptr(), d, n, ldx, float(lam), int(c),
+                                  float(tol), int(max_iter),
+                                  p0.data_ptr() if p0 is not None else None, L.data_ptr(),
+                                  S.data_ptr(), lds, p.data_ptr(), ctypes.byref(st))
+    _check(h, rc, "respca_solve_host")
+    return st.as_dict()
+
+
+def respca_init_labels(h, X, c: int, p) -> int:
+    d, n = X.shape
+    ldx = _colmajor(X, "X")
+    passes = ctypes.c_int32(0)
+    rc = load().respca_init_labels(h, _dtype_code(X), X.data_ptr(), d, n, ldx, int(c),
+                                   p.data_ptr(), ctypes.byref(passes))
+    _check(h, rc, "respca_init_labels")
+    return passes.value
+
+
+def respca_solve_batched(h, problems: list[dict]) -> list[dict]:
+    """problems: dicts with X, c, L, S, p (and optional lam, tol, max_iter, p0)."""
+    arr = (respca_problem * len(problems))()
+    for i, q in enumerate(problems):
+        X = q["X"]
+        d, n = X.shape
+        arr[i].x_dtype = _dtype_code(X)
+        arr[i].c = int(q["c"])
+        arr[i].X = X.data_ptr()
+        arr[i].d, arr[i].n, arr[i].ldx = d, n, _colmajor(X, "X")
+        arr[i].lambda_ = float(q.get("lam", 0.0))
+        arr[i].tol = float(q.get("tol", 1e-6))
+        arr[i].max_iter = int(q.get("max_iter", 500))
+        arr[i].p0 = q["p0"].data_ptr() if q.get("p0") is not None else None
+        arr[i].L = q["L"].data_ptr()
+        arr[i].S = q["S"].data_ptr()
+        arr[i].lds = _colmajor(q["L"], "L")
+        arr[i].p = q["p"].data_ptr()
+    stats = (respca_stats * len(problems))()
+    rc = load().respca_solve_batched(h, len(problems), arr, stats)
+    _check(h, rc, "respca_solve_batched")
+    return [s.as_dict() for s in stats]
+
+
+# ------------------------------------------------------------------ convenience
+@dataclass
+class Result:
+    L: object
+    S: object
+    p: object
+    stats: dict
+
+
+class Solver:
+    """Owns a handle bound to the current torch CUDA stream."""
+
+    def __init__(self, rho0: float = 1e-4, kappa: float = 1.5, kmeans_max_iter: int = 100,
+                 seed: int = 0, stream=None, device: int | None = None):
+        import torch
+        cfg = respca_config_default()
+        cfg.rho0, cfg.kappa, cfg.kmeans_max_iter, cfg.seed = rho0, kappa, kmeans_max_iter, seed
+        dev = torch.cuda.current_device() if device is None else device
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        cfg.stream = s.cuda_stream
+        cfg.device = dev
+        self.stream = s
+        self.device = dev
+        self.h = respca_create(cfg)
+
+    def close(self):
+        if self.h:
+            respca_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, X, c: int, *, lam: float = 0.0, tol: float = 1e-6, max_iter: int = 500,
+              p0=None, warm=None, out=None) -> Result:
+        import torch
+        d, n = X.shape
+        if out is None:
+            L = torch.empty((n, d), device=X.device, dtype=torch.float32).T
+            S = torch.empty((n, d), device=X.device, dtype=torch.float32).T
+            p = torch.empty(n, device=X.device, dtype=torch.int32)
+        else:
+            L, S, p = out
+        st = respca_solve(self.h, X, c, L, S, p, lam=lam, tol=tol, max_iter=max_iter, p0=p0,
+                          warm=warm)
+        return Result(L, S, p, st)
+
+    def init_labels(self, X, c: int):
+        import torch
+        p = torch.empty(X.shape[1], device=X.device, dtype=torch.int32)
+        passes = respca_init_labels(self.h, X, c, p)
+        return p, passes

@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerance: the FP32 path must match the FP64 oracle within 1e-5 relative
+Frobenius error after a fixed iteration count, labels identical.  Element by
+element, |L_gpu - L_oracle| <= 1e-5 * max|L_oracle| (and likewise for S);
+Theta is compared through Theta/rho, the quantity the iteration uses.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_07497_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev(A, dtype=None):
+    """numpy (d, n) -> column-major CUDA tensor (d, n)."""
+    t = torch.from_numpy(np.ascontiguousarray(np.asarray(A).T))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda().T
+
+
+def _host(t):
+    return t.T.contiguous().cpu().numpy().T.astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def solver():
+    from paper_1904_07497_gb300 import respca
+    respca.load()
+    s = respca.Solver(seed=3)
+    yield s
+    s.close()
+
+
+def _rel(a, b, scale=None):
+    den = np.linalg.norm(b) if scale is None else scale
+    return np.linalg.norm(a - b) / max(den, 1e-300)
+
+
+def _check_state(L, S, ref, X64, tol=1e-5):
+    eL = _rel(L, ref.L)
+    sS = max(np.linalg.norm(ref.S), 1e-2 * np.linalg.norm(X64))
+    eS = _rel(S, ref.S, sS)
+    assert eL <= tol, f"L rel err {eL:.3e}"
+    assert eS <= tol, f"S rel err {eS:.3e}"
+    assert np.abs(L - ref.L).max() <= tol * np.abs(ref.L).max() + 1e-7
+    assert np.abs(S - ref.S).max() <= tol * max(np.abs(ref.S).max(), 1.0) + 1e-7
+    return eL, eS
+
+
+def _run(solver, X32, c, T, p0, warm=None, tol=0.0):
+    from paper_1904_07497_gb300 import respca
+    d, n = X32.shape
+    X = _dev(X32)
+    L = torch.zeros((n, d), device="cuda").T
+    S = torch.zeros((n, d), device="cuda").T
+    p = torch.zeros(n, device="cuda", dtype=torch.int32)
+    wst = None
+    Th = None
+    if warm is not None:
+        L.copy_(_dev(warm.L.astype(np.float32)))
+        S.copy_(_dev(warm.S.astype(np.float32)))
+        p.copy_(torch.from_numpy(warm.labels).cuda())
+        Th = torch.zeros((n, d), device="cuda").T
+        Th.copy_(_dev(warm.Theta.astype(np.float32)))
+        wst = respca.respca_warm(Theta=Th.data_ptr(), rho=warm.rho, warm=1)
+    st = respca.respca_solve(solver.h, X, c, L, S, p, tol=tol, max_iter=T,
+                             p0=None if p0 is None else torch.from_numpy(p0).cuda(), warm=wst)
+    torch.cuda.synchronize()
+    out = dict(L=_host(L), S=_host(S), p=p.cpu().numpy(), stats=st)
+    if Th is not None:
+        out["Theta"] = _host(Th)
+        out["rho"] = wst.rho
+    return out
+
+
+def _rounded(state):
+    s = state.copy()
+    s.L = s.L.astype(np.float32).astype(np.float64)
+    s.S = s.S.astype(np.float32).astype(np.float64)
+    s.Theta = s.Theta.astype(np.float32).astype(np.float64)
+    return s
+
+
+# ------------------------------------------------------------------ one iteration
+@pytest.mark.parametrize("T", [0, 12, 22, 26, 31, 40])
+def test_single_iteration_from_oracle_state(solver, T):
+    """From the same (FP32-representable) state, one GPU iteration equals one
+    oracle iteration: ramp (T <= 20), S activation (22), label churn (26-31),
+    convergence (40)."""
+    pr = synth.lowrank_sparse(500, 500, 25, 0.05, seed=0)
+    X64 = pr.X.astype(np.float64)
+    c, lam = 25, np.sqrt(500)
+    p0, _ = oracle.init_labels(X64, c, seed=0)
+    st = oracle.State(np.zeros((500, 500), order="F"), np.zeros((500, 500), order="F"),
+                      np.zeros((500, 500), order="F"), p0, 1e-4)
+    for _ in range(T):
+        st, *_ = oracle.iteration(X64, st, c, lam)
+    st = _rounded(st)
+    ref, norms, _, _ = oracle.iteration(X64, st, c, lam)
+    got = _run(solver, pr.X, c, 1, None, warm=st)
+    np.testing.assert_array_equal(got["p"], ref.labels)
+    _check_state(got["L"], got["S"], ref, X64)
+    tr_ref = ref.Theta / st.rho
+    tr_got = got["Theta"] / st.rho
+    assert np.abs(tr_got - tr_ref).max() <= 1e-5 * max(np.abs(X64).max(), 1.0)
+    assert got["rho"] == pytest.approx(st.rho * 1.5, rel=1e-15)
+    e_ref = max(norms) / np.linalg.norm(X64)
+    assert got["stats"]["err"] == pytest.approx(e_ref, rel=1e-4, abs=1e-7)
+
+
+# ------------------------------------------------------------------ fixed count
+@pytest.mark.parametrize("T", [30, 60])
+def test_c1_fixed_iterations(solver, T):
+    """d = n = 500, rank 25, 5 % +-1 corruption, c = 25: 30 iterations (S
+    active, labels moving) and 60 (past convergence to 1e-6)."""
+    pr = synth.lowrank_sparse(500, 500, 25, 0.05, seed=0)
+    X64 = pr.X.astype(np.float64)
+    p0, _ = oracle.init_labels(X64, 25, seed=0)
+    ref, rs = oracle.solve(X64, 25, tol=0.0, max_iter=T, p0=p0)
+    got = _run(solver, pr.X, 25, T, p0)
+    assert got["stats"]["iters"] == T
+    np.testing.assert_array_equal(got["p"], ref.labels)
+    _check_state(got["L"], got["S"], ref, X64)
+
+
+def test_c1_to_tolerance(solver):
+    """Solve to the Sec. 5 criterion at 1e-6: the GPU stops within one
+    iteration of the oracle and its result matches the oracle's at the same
+    iteration count."""
+    pr = synth.lowrank_sparse(500, 500, 25, 0.05, seed=1)
+    X64 = pr.X.astype(np.float64)
+    p0, _ = oracle.init_labels(X64, 25, seed=1)
+    ref, rs = oracle.solve(X64, 25, tol=1e-6, max_iter=500, p0=p0)
+    got = _run(solver, pr.X, 25, 500, p0, tol=1e-6)
+    assert got["stats"]["converged"] == 1
+    assert abs(got["stats"]["iters"] - rs["iters"]) <= 1
+    ref2, _ = oracle.solve(X64, 25, tol=0.0, max_iter=got["stats"]["iters"], p0=p0)
+    np.testing.assert_array_equal(got["p"], ref2.labels)
+    _check_state(got["L"], got["S"], ref2, X64)
+    assert np.linalg.norm(X64 - got["L"] - got["S"]) / np.linalg.norm(X64) <= 2e-6
+
+
+# ------------------------------------------------------------------ shapes
+@pytest.mark.parametrize("d,n,c,rank,sp", [
+    (37, 41, 3, 3, 0.1),        # scalar path (d % 4 != 0), single partial tile per cluster
+    (1203, 70, 4, 4, 0.05),     # three row chunks with a ragged tail, scalar path
+    (1028, 97, 5, 5, 0.1),      # vector path, ragged chunk tail, partial tiles
+    (64, 300, 1, 4, 0.05),      # one cluster
+    (48, 40, 40, 3, 0.05),      # c = n: every column its own cluster
+    (256, 200, 130, 8, 0.05),   # more clusters than one 64-wide register block
+])
+def test_shapes_and_edges(solver, d, n, c, rank, sp):
+    pr = synth.lowrank_sparse(d, n, rank, sp, seed=d + n + c)
+    X64 = pr.X.astype(np.float64)
+    p0 = np.arange(n, dtype=np.int32) if c == n else oracle.init_labels(X64, c, seed=2)[0]
+    ref, _ = oracle.solve(X64, c, tol=0.0, max_iter=35, p0=p0)
+    got = _run(solver, pr.X, c, 35, p0)
+    np.testing.assert_array_equal(got["p"], ref.labels)
+    _check_state(got["L"], got["S"], ref, X64)
+
+
+def test_video_shaped(solver):
+    """Tall-skinny frames-as-columns with 3 backgrounds (reduced size)."""
+    pr = synth.video(n=240, height=48, width=64, n_backgrounds=3, seed=4)
+    X64 = pr.X.astype(np.float64)
+    p0, _ = oracle.init_labels(X64, 3, seed=1)
+    ref, rs = oracle.solve(X64, 3, tol=0.0, max_iter=40, p0=p0)
+    got = _run(solver, pr.X, 3, 40, p0)
+    np.testing.assert_array_equal(got["p"], ref.labels)
+    _check_state(got["L"], got["S"], ref, X64)
+
+
+@pytest.mark.parametrize("dt", ["bf16", "f16"])
+def test_half_precision_x(solver, dt):
+    """X stored in BF16 / FP16: the oracle runs on the same rounded values."""
+    from paper_1904_07497_gb300 import respca
+    tdt = torch.bfloat16 if dt == "bf16" else torch.float16
+    pr = synth.lowrank_sparse(256, 180, 6, 0.05, seed=9)
+    Xh = torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(tdt)
+    X64 = Xh.float().numpy().T.astype(np.float64)
+    p0, _ = oracle.init_labels(X64, 6, seed=1)
+    ref, _ = oracle.solve(X64, 6, tol=0.0, max_iter=30, p0=p0)
+    X = Xh.cuda().T
+    d, n = X.shape
+    L = torch.zeros((n, d), device="cuda").T
+    S = torch.zeros((n, d), device="cuda").T
+    p = torch.zeros(n, device="cuda", dtype=torch.int32)
+    respca.respca_solve(solver.h, X, 6, L, S, p, tol=0.0, max_iter=30, p0=torch.from_numpy(p0).cuda())
+    np.testing.assert_array_equal(p.cpu().numpy(), ref.labels)
+    _check_state(_host(L), _host(S), ref, X64)
+
+
+# ------------------------------------------------------------------ initial labels
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_init_labels_match_oracle(seed):
+    from paper_1904_07497_gb300 import respca
+    s = respca.Solver(seed=seed)
+    pr = synth.lowrank_sparse(300, 260, 12, 0.05, seed=30 + seed)
+    X64 = pr.X.astype(np.float64)
+    want, steps = oracle.init_labels(X64, 12, seed=seed)
+    p, passes = s.init_labels(_dev(pr.X), 12)
+    s.close()
+    np.testing.assert_array_equal(p.cpu().numpy(), want)
+    assert passes == steps
+
+
+def test_full_solve_without_p0(solver):
+    """Cold start with the library's own k-means++ + Lloyd initial labels."""
+    from paper_1904_07497_gb300 import respca
+    s = respca.Solver(seed=5)
+    pr = synth.lowrank_sparse(200, 150, 5, 0.05, seed=44)
+    X64 = pr.X.astype(np.float64)
+    ref, _ = oracle.solve(X64, 5, tol=0.0, max_iter=40, seed=5)
+    res = s.solve(_dev(pr.X), 5, tol=0.0, max_iter=40)
+    s.close()
+    np.testing.assert_array_equal(res.p.cpu().numpy(), ref.labels)
+    _check_state(_host(res.L), _host(res.S), ref, X64)
+
+
+# ------------------------------------------------------------------ host API, errors
+def test_solve_host_matches_device(solver):
+    from paper_1904_07497_gb300 import respca
+    pr = synth.lowrank_sparse(130, 90, 4, 0.1, seed=50)
+    p0, _ = oracle.init_labels(pr.X.astype(np.float64), 4, seed=0)
+    dev = _run(solver, pr.X, 4, 25, p0)
+    Xh = torch.from_numpy(np.ascontiguousarray(pr.X.T)).T
+    L = torch.zeros((90, 130)).T
+    S = torch.zeros((90, 130)).T
+    p = torch.zeros(90, dtype=torch.int32)
+    respca.respca_solve_host(solver.h, Xh, 4, L, S, p, tol=0.0, max_iter=25, p0=torch.from_numpy(p0))
+    np.testing.assert_array_equal(p.numpy(), dev["p"])
+    np.testing.assert_array_equal(L.numpy().astype(np.float64), dev["L"])
+    np.testing.assert_array_equal(S.numpy().astype(np.float64), dev["S"])
+
+
+def test_zero_input(solver):
+    got = _run(solver, np.zeros((40, 30), dtype=np.float32), 3, 10, None)
+    assert np.all(got["L"] == 0) and np.all(got["S"] == 0)
+    assert got["stats"]["iters"] == 0 and got["stats"]["converged"] == 1
+
+
+def test_errors(solver):
+    from paper_1904_07497_gb300 import respca
+    X = np.ones((20, 10), dtype=np.float32)
+    X[3, 4] = np.nan
+    with pytest.raises(respca.RespcaError) as e:
+        _run(solver, X, 2, 5, None)
+    assert e.value.status == respca.RESPCA_ERR_NONFINITE_INPUT
+    X[3, 4] = 1.0
+    with pytest.raises(respca.RespcaError) as e:
+        _run(solver, X, 11, 5, None)
+    assert e.value.status == respca.RESPCA_ERR_INVALID_ARG
+    with pytest.raises(respca.RespcaError) as e:
+        _run(solver, X, 2, 5, np.array([0, 1, 2] + [0] * 7, dtype=np.int32))
+    assert e.value.status == respca.RESPCA_ERR_INVALID_ARG
+    # the handle still works after errors
+    got = _run(solver, X, 2, 3, None)
+    assert got["stats"]["iters"] >= 1
+
+
+def test_batched_matches_single(solver):
+    from paper_1904_07497_gb300 import respca
+    probs, singles = [], []
+    for k, e in enumerate(synth.batch_table(4, seed=3, d_range=(60, 300), n_range=(40, 200))):
+        pr = synth.batch_problem(e)
+        d, n = pr.X.shape
+        X = _dev(pr.X)
+        q = dict(X=X, c=e.r, L=torch.zeros((n, d), device="cuda").T,
+                 S=torch.zeros((n, d), device="cuda").T,
+                 p=torch.zeros(n, device="cuda", dtype=torch.int32), tol=0.0, max_iter=20)
+        probs.append(q)
+        singles.append(_run(solver, pr.X, e.r, 20, None))
+    respca.respca_solve_batched(solver.h, probs)
+    for q, s in zip(probs, singles):
+        np.testing.assert_array_equal(q["p"].cpu().numpy(), s["p"])
+        np.testing.assert_array_equal(_host(q["L"]), s["L"])
