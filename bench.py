@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""RES-PCA benchmark: time to 1e-6 relative error on one GB300.
+
+Workload (default): d = n = 10000, L0 = U V^T with U, V of rank 50 and i.i.d.
+N(0, 1e-4) entries, S0 with Bernoulli(0.10) support of +-1 values, X = L0 + S0
+in FP32; c = 50 groups, lambda = sqrt(max(d, n)), rho0 = 1e-4, kappa = 1.5,
+stopping rule of Sec. 5 at tol = 1e-6 (cap 500).  One step = one whole solve
+(initial labels by k-means++ and Lloyd, then the ALM iterations) with X already
+in HBM.  Every array is 400 MB, larger than the 129 MB L2, so no flush is
+needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead
+(a bounded sample of the same workload, extrapolated; see cpu_sample()).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-6 rel. err & per-iter HBM GB/s vs peak; BF16+learned vs plain FP32"
+FALLBACK_HBM_GBS = 6800.0
+BYTES_PER_ELEM_FP32 = 28   # read X, S, Theta, L_prev; write L, S, Theta (4 B each)
+
+WORKLOADS = {
+    # name: (d, n, rank, sparsity, c)
+    "c2": (10000, 10000, 50, 0.10, 50),
+    "c2r100": (10000, 10000, 50, 0.10, 100),
+    "small": (6000, 6000, 50, 0.10, 50),
+    "c1": (500, 500, 25, 0.05, 25),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload_config(name, tol):
+    d, n, r, sp, c = WORKLOADS[name]
+    return {
+        "workload": f"lowrank+sparse d={d} n={n} rank={r} sparsity={sp} +-1, c={c}, "
+                    f"lambda=sqrt(max(d,n)), rho0=1e-4, kappa=1.5, tol={tol:g}",
+        "d": d, "n": n, "rank": r, "sparsity": sp, "c": c, "tol": tol, "x_dtype": "f32",
+        "l2": "inputs larger than L2 (each d x n FP32 array exceeds 129 MB)"
+        if d * n * 4 > 129e6 else "inputs L2-resident (latency-bound size)",
+    }
+
+
+def make_problem(name, seed):
+    from paper_1904_07497_gb300 import synth
+    d, n, r, sp, c = WORKLOADS[name]
+    return synth.lowrank_sparse(d, n, r, sp, seed, keep_parts=False), c
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def cpu_sample(name, seed, steps=1, warmup=0):
+    """Time the FP64 oracle on a bounded sample of the workload.
+
+    Sample: one ALM iteration (L step, one K-means assignment pass, S and
+    Theta steps) on the first n_s columns of the same X, from the zero state
+    with labels j mod c; its time is scaled by n / n_s (every step is linear
+    in n) and by the oracle's own iteration count to 1e-6 measured on a
+    1000 x 1000 instance of the same family (rank 50, same sparsity, c).
+    Extra Lloyd passes and the initial k-means++/Lloyd labels are left out,
+    so the figure is a lower bound on the oracle's time to solution."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    d, n, r, sp, c = WORKLOADS[name]
+    pr, _ = make_problem(name, seed)
+    n_s = min(n, 1000)
+    Xs = np.asfortranarray(pr.X[:, :n_s].astype(np.float64))
+    from paper_1904_07497_gb300 import synth
+    small = synth.lowrank_sparse(min(d, 1000), min(n, 1000), r, sp, seed + 1)
+    _, st_small = oracle.solve(small.X.astype(np.float64), c, tol=1e-6, max_iter=500, seed=seed)
+    iters = st_small["iters"]
+    lam = np.sqrt(max(d, n))
+    labels = (np.arange(n_s) % c).astype(np.int32)
+    zero = np.zeros((d, n_s), order="F")
+    times = []
+    for k in range(warmup + steps):
+        state = oracle.State(zero.copy(order="F"), zero.copy(order="F"), zero.copy(order="F"),
+                             labels.copy(), 1e-4)
+        t0 = time.perf_counter()
+        oracle.iteration(Xs, state, c, lam, km_max=1)
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            times.append(dt)
+    per_iter_full = statistics.median(times) * (n / n_s)
+    value_ms = per_iter_full * iters * 1e3
+    sample = (f"1 ALM iteration (1 assignment pass) on {n_s} of {n} columns, FP64, x{n / n_s:g} "
+              f"in n, x{iters} iterations (oracle's count to 1e-6 on a 1000x1000 instance); "
+              f"excludes initial labels and extra Lloyd passes (lower bound)")
+    return value_ms, times, sample
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), max=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        loaded = [r["sm"] for r in rows if r["power"] > 200] or [r["sm"] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        pk = json.load(open(path))
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic(kernel_file, profile_name):
+    """Per-launch DRAM bytes of the fused kernel from a committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    prof = os.path.join(ROOT, "profiles", profile_name)
+    src = os.path.join(ROOT, "paper_1904_07497_gb300", "csrc", kernel_file)
+    try:
+        text = open(prof).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_scaled"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1904_07497_gb300 import respca
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pr, c = make_problem(args.workload, args.seed + rank)
+    d, n = pr.X.shape
+    X = torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(dev).T          # (d, n) col-major
+    L = torch.empty((n, d), device=dev).T
+    S = torch.empty((n, d), device=dev).T
+    p = torch.empty(n, device=dev, dtype=torch.int32)
+    stream = torch.cuda.current_stream(dev)
+    solver = respca.Solver(seed=args.seed, timing=True, stream=stream, device=local_rank)
+
+    def one():
+        return respca.respca_solve(solver.h, X, c, L, S, p, tol=args.tol, max_iter=500)
+
+    for _ in range(args.warmup):
+        one()
+    gpu_index = local_rank
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis and vis.split(",")[local_rank].strip().isdigit():
+        gpu_index = int(vis.split(",")[local_rank])
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = [one() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_per_step = t.item() / args.steps
+
+    fused_ms = sum(s["ms_fused"] for s in stats)
+    fused_n = sum(s["fused_launches"] for s in stats)
+    iters = [s["iters"] for s in stats]
+    launches = sum(s["kernel_launches"] for s in stats)
+    bytes_per_launch = BYTES_PER_ELEM_FP32 * d * n
+    achieved = bytes_per_launch / (fused_ms / fused_n / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = kernel_traffic("k_stream.cu", f"k_iteration_{args.workload}.txt")
+
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(np.ascontiguousarray(pr.X.T)).pin_memory().T
+        Lh = torch.empty((n, d), pin_memory=True).T
+        Sh = torch.empty((n, d), pin_memory=True).T
+        ph = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        respca.respca_solve_host(solver.h, Xh, c, Lh, Sh, ph, tol=args.tol, max_iter=500)
+        ke = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            respca.respca_solve_host(solver.h, Xh, c, Lh, Sh, ph, tol=args.tol, max_iter=500)
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / ke
+        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": round(te.item(), 3), "unit": "ms", "h2d_bytes_per_step": 4 * d * n,
+               "d2h_bytes_per_step": 8 * d * n + 4 * n,
+               "note": "respca_solve_host on pinned host buffers; copies inside the timed region"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, times, sample = cpu_sample(args.workload, args.seed)
+        cpu = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
+
+    solver.close()
+    if rank != 0:
+        return None
+    last = stats[-1]
+    return {
+        "metric": METRIC, "value": round(ms_per_step, 3), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded numpy PCG64)",
+        "config": workload_config(args.workload, args.tol),
+        "iters": iters, "converged": last["converged"], "err": last["err"],
+        "ms_init": round(last["ms_init"], 3),
+        "per_iter_hbm_gbs": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": "k_iteration (fused ALM iteration)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": round(fused_ms / fused_n, 4)},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "label_changes": last["label_changes"], "lloyd_passes": last["lloyd_passes"],
+        "assigned_columns": last["assigned_columns"],
+    }
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    v_steps = []
+    v, times, sample = cpu_sample(args.workload, args.seed, steps=args.steps, warmup=args.warmup)
+    d, n, r, sp, c = WORKLOADS[args.workload]
+    per = [t * (n / min(n, 1000)) for t in times]
+    ms_per_step = statistics.mean(times) * 1e3
+    return {
+        "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded numpy PCG64)",
+        "config": workload_config(args.workload, args.tol), "impl": "reference",
+        "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "gpu":
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_gpu(args, rank, world, local_rank)
+    if world > 1 and args.impl == "gpu":
+        import torch
+        torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

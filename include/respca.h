@@ -58,7 +58,8 @@ typedef struct {
     double rho0;             /* initial penalty rho (Sec. 5.1: 1e-4) */
     double kappa;            /* penalty growth factor, rho <- kappa rho (Eq. (25); Sec. 5.1: 1.5) */
     int32_t kmeans_max_iter; /* cap on Lloyd assignment passes per p step (default 100) */
-    int32_t reserved0;
+    int32_t timing;          /* 1: time the fused iteration kernel with CUDA events
+                                (respca_stats.ms_fused); default 0 */
     uint64_t seed;           /* seed of the k-means++ draws for the initial labels */
     void *stream;            /* cudaStream_t for all work; NULL = the legacy default stream */
     int32_t device;          /* CUDA device ordinal; -1 = the device current at respca_create */
@@ -78,10 +79,13 @@ typedef struct {
     int64_t lloyd_passes;    /* assignment passes run by the p steps */
     int64_t assigned_columns;/* columns whose nearest centroid had to be searched */
     int64_t rechecked_columns;/* near-tie columns re-decided in FP64 */
+    int64_t kernel_launches; /* CUDA kernels this call launched */
     int32_t init_lloyd_passes;/* assignment passes of the initial K-means */
-    int32_t reserved;
+    int32_t fused_launches;  /* launches of the fused iteration kernel */
     float ms_total;          /* wall time of the call on the stream (CUDA events) */
     float ms_init;           /* part of ms_total spent before the first iteration */
+    float ms_fused;          /* summed duration of the fused iteration kernel (cfg.timing = 1) */
+    float reserved;
 } respca_stats;
 
 /* Optional warm start / checkpoint-resume state (the paper starts from zero;

@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(kThreads)
 cudaError_t launch_sort_labels(const int32_t* labels, int64_t n, int c, int32_t* perm,
                                int32_t* counts, int32_t* tile_off, TileDesc* tiles,
                                DevStatus* status, cudaStream_t st) {
+    count_launches(1);
     const size_t smem = sizeof(int32_t) * (size_t)(3 * c + 1);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_sort_labels,
@@ -412,6 +413,7 @@ cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int6
                           const int32_t* list, const float* mu, const float* mu_normf,
                           const int32_t* counts, int c, int32_t* labels, DevStatus* status,
                           cudaStream_t st) {
+    count_launches(1);
     const size_t smem = assign_smem_bytes(c);
     const int grid = grid_for(n, kAsgCols);
     cudaError_t e = cudaSuccess;
@@ -427,6 +429,7 @@ cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int6
 
 cudaError_t launch_seed_dist(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
                              const int32_t* centers, int k, double* D2, cudaStream_t st) {
+    count_launches(1);
     const int grid = grid_for(n, kThreads / 32);
     RESPCA_DISPATCH_X(dtype, TX, {
         k_seed_dist<TX><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, centers, k, D2);
@@ -436,6 +439,7 @@ cudaError_t launch_seed_dist(int dtype, const void* X, int64_t ldx, int64_t d, i
 
 cudaError_t launch_seed_pick(const double* D2, int64_t n, const double* u, int k, int32_t* centers,
                              cudaStream_t st) {
+    count_launches(1);
     k_seed_pick<<<1, 1024, 0, st>>>(D2, n, u, k, centers);
     return cudaGetLastError();
 }
@@ -443,6 +447,7 @@ cudaError_t launch_seed_pick(const double* D2, int64_t n, const double* u, int k
 cudaError_t launch_gather_centers(int dtype, const void* X, int64_t ldx, int64_t d,
                                   const int32_t* centers, int c, float* mu, int32_t* counts,
                                   cudaStream_t st) {
+    count_launches(1);
     const dim3 grid(grid_for(d, kThreads), c);
     RESPCA_DISPATCH_X(dtype, TX, {
         k_gather_centers<TX><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, centers, mu, counts);

@@ -452,6 +452,7 @@ inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_fro2(int dtype, const void* X, int64_t d, int64_t n, int64_t ldx, double* part,
                         int nparts, DevStatus* status, cudaStream_t st) {
+    count_launches(2);
     const int64_t seg = (d + kThreads * 4 - 1) / (kThreads * 4);
     const int64_t units = seg * n;
     const int grid = (int)(units < nparts ? units : nparts);
@@ -484,6 +485,7 @@ cudaError_t launch_colsum(int mode, int dtype, const void* X, int64_t ldx, const
                           const int32_t* perm, const TileDesc* tiles, int max_tiles,
                           const DevStatus* status, int64_t d, float* Dpart, bool vec,
                           cudaStream_t st) {
+    count_launches(1);
     const dim3 grid(max_tiles, grid_for(d, kChunkRows));
     if (mode == kSumL) {
         colsum_mode<kSumL, float>(grid, nullptr, 0, L, S, Th, lds, inv_rho, perm, tiles, status, d,
@@ -503,6 +505,7 @@ cudaError_t launch_colsum(int mode, int dtype, const void* X, int64_t ldx, const
 
 cudaError_t launch_centroids(const float* Dpart, const int32_t* tile_off, const int32_t* counts,
                              int c, int64_t d, float* mu, cudaStream_t st) {
+    count_launches(1);
     const dim3 grid(grid_for(d, kThreads), c);
     k_centroids<<<grid, kThreads, 0, st>>>(Dpart, tile_off, counts, d, mu);
     return cudaGetLastError();
@@ -510,12 +513,14 @@ cudaError_t launch_centroids(const float* Dpart, const int32_t* tile_off, const 
 
 cudaError_t launch_mu_norms(const float* mu, int c, int64_t d, double* mu_norm2, float* mu_normf,
                             cudaStream_t st) {
+    count_launches(1);
     k_mu_norms<<<c, kThreads, 0, st>>>(mu, d, mu_norm2, mu_normf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_separation(const float* mu, const int32_t* counts, int c, int64_t d,
                               float* pair_ss, double* sep2, cudaStream_t st) {
+    count_launches(c > kSepMaxC ? 1 : 2);
     if (c > kSepMaxC) {
         // No pruning for very many clusters: every column is searched.
         k_fill_double<<<grid_for(c, kThreads), kThreads, 0, st>>>(sep2, c, 0.0);
@@ -538,6 +543,7 @@ cudaError_t launch_iteration(int dtype, const void* X, int64_t ldx, float* L, fl
                              const TileDesc* tiles, int max_tiles, const DevStatus* status,
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
                              double* norm_part, bool vec, cudaStream_t st) {
+    count_launches(1);
     const dim3 grid(max_tiles, grid_for(d, kChunkRows));
     RESPCA_DISPATCH_X(dtype, TX, {
         if (vec)
@@ -554,6 +560,7 @@ cudaError_t launch_iteration(int dtype, const void* X, int64_t ldx, float* L, fl
 
 cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchunks,
                                 DevStatus* status, cudaStream_t st) {
+    count_launches(1);
     k_reduce_norms<<<1, kThreads, 0, st>>>(norm_part, max_tiles, nchunks, status);
     return cudaGetLastError();
 }
@@ -561,6 +568,7 @@ cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchu
 cudaError_t launch_flag_columns(const float* own_part, int nchunks, int64_t n,
                                 const int32_t* labels, const double* sep2, double safety,
                                 int32_t* flag_list, DevStatus* status, cudaStream_t st) {
+    count_launches(1);
     k_flag_columns<<<grid_for(n, kThreads), kThreads, 0, st>>>(own_part, nchunks, n, labels, sep2,
                                                                safety, flag_list, status);
     return cudaGetLastError();
@@ -568,6 +576,7 @@ cudaError_t launch_flag_columns(const float* own_part, int nchunks, int64_t n,
 
 cudaError_t launch_count_changed(const int32_t* labels, const int32_t* prev, int64_t n,
                                  DevStatus* status, cudaStream_t st) {
+    count_launches(1);
     k_count_changed<<<grid_for(n, kThreads), kThreads, 0, st>>>(labels, prev, n, status);
     return cudaGetLastError();
 }

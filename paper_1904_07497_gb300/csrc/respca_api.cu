@@ -55,7 +55,7 @@ struct respca_ctx {
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evk0 = nullptr, evk1 = nullptr;
 };
 
 namespace {
@@ -261,6 +261,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     h->last_error.clear();
 
     respca_stats out{};
+    const int64_t launches0 = t_kernel_launches;
+    const bool timing = h->cfg.timing != 0;
     CK(cudaEventRecord(h->ev0, h->stream));
     DevStatus* ds = P<DevStatus>(h->status);
     CK(cudaMemsetAsync(ds, 0, sizeof(DevStatus), h->stream));
@@ -319,6 +321,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         CK(cudaEventSynchronize(h->ev1));
         out.converged = 1;
         out.rho_final = rho;
+        out.kernel_launches = t_kernel_launches - launches0;
         cudaEventElapsedTime(&out.ms_total, h->ev0, h->ev1);
         if (warm) warm->rho = rho;
         if (stats) *stats = out;
@@ -348,9 +351,12 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         CK(zero_counters(h));
         CK(cudaMemcpyAsync(h->labels_prev.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
         // L, S, Theta, norms, own distances and next-D sums in one pass
+        if (timing) CK(cudaEventRecord(h->evk0, h->stream));
         CK(launch_iteration(dtype, X, ldx, L, S, pb.Th, lds, P<float>(h->mu), P<int32_t>(h->perm),
                             P<TileDesc>(h->tiles), mt, ds, d, n, sc, P<float>(h->Dpart),
                             P<float>(h->own_part), P<double>(h->norm_part), pb.vec, h->stream));
+        if (timing) CK(cudaEventRecord(h->evk1, h->stream));
+        out.fused_launches += 1;
         CK(launch_reduce_norms(P<double>(h->norm_part), mt, nch, ds, h->stream));
         // p step: first Lloyd assignment, searching only the columns the bound cannot settle
         CK(launch_flag_columns(P<float>(h->own_part), nch, n, p, P<double>(h->sep2), safety,
@@ -359,6 +365,11 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
                          P<float>(h->mu_normf), P<int32_t>(h->counts), c, p, ds, h->stream));
         rs = read_status(h);
         if (rs != RESPCA_OK) return rs;
+        if (timing) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, h->evk0, h->evk1));
+            out.ms_fused += ms;
+        }
         out.lloyd_passes += 1;
         out.assigned_columns += h->hstat->flagged;
         out.rechecked_columns += h->hstat->rechecked;
@@ -418,6 +429,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     if (rs != RESPCA_OK) return rs;
     out.label_changes = h->hstat->label_changes;
     out.rho_final = rho;
+    out.kernel_launches = t_kernel_launches - launches0;
     cudaEventElapsedTime(&out.ms_total, h->ev0, h->ev1);
     cudaEventElapsedTime(&out.ms_init, h->ev0, h->ev2);
     if (warm) warm->rho = rho;
@@ -459,7 +471,8 @@ respca_status respca_create(respca_handle* out, const respca_config* cfg) {
     h->stream = reinterpret_cast<cudaStream_t>(c.stream);
     if (cudaMallocHost(&h->hstat, sizeof(DevStatus)) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
-        cudaEventCreate(&h->ev2) != cudaSuccess) {
+        cudaEventCreate(&h->ev2) != cudaSuccess || cudaEventCreate(&h->evk0) != cudaSuccess ||
+        cudaEventCreate(&h->evk1) != cudaSuccess) {
         respca_destroy(h);
         return RESPCA_ERR_OOM;
     }
@@ -483,6 +496,8 @@ respca_status respca_destroy(respca_handle h) {
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->ev2) cudaEventDestroy(h->ev2);
+    if (h->evk0) cudaEventDestroy(h->evk0);
+    if (h->evk1) cudaEventDestroy(h->evk1);
     delete h;
     return RESPCA_OK;
 }

@@ -60,6 +60,11 @@ struct DevStatus {
 // Mode of the column-group sum kernel.
 enum SumMode : int { kSumX = 0, kSumL = 1, kSumD = 2 };
 
+// Kernels launched by this thread (each launcher adds its count); a solve
+// reports the difference across its body.
+inline thread_local int64_t t_kernel_launches = 0;
+inline void count_launches(int k) { t_kernel_launches += k; }
+
 // ---------------------------------------------------------------- launchers
 // (each returns the launch status; all run on `st`)
 cudaError_t launch_fro2(int dtype, const void* X, int64_t d, int64_t n, int64_t ldx,

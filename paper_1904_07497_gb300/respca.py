@@ -29,7 +29,7 @@ RESPCA_F32, RESPCA_BF16, RESPCA_F16 = 0, 1, 2
 
 class respca_config(ctypes.Structure):
     _fields_ = [("rho0", ctypes.c_double), ("kappa", ctypes.c_double),
-                ("kmeans_max_iter", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("kmeans_max_iter", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
@@ -41,8 +41,10 @@ class respca_stats(ctypes.Structure):
                 ("rho_final", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("label_changes", ctypes.c_int64), ("lloyd_passes", ctypes.c_int64),
                 ("assigned_columns", ctypes.c_int64), ("rechecked_columns", ctypes.c_int64),
-                ("init_lloyd_passes", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("ms_total", ctypes.c_float), ("ms_init", ctypes.c_float)]
+                ("kernel_launches", ctypes.c_int64),
+                ("init_lloyd_passes", ctypes.c_int32), ("fused_launches", ctypes.c_int32),
+                ("ms_total", ctypes.c_float), ("ms_init", ctypes.c_float),
+                ("ms_fused", ctypes.c_float), ("reserved", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {(k[:-1] if k.endswith("_") else k): getattr(self, k) for k, _ in self._fields_
@@ -226,10 +228,11 @@ class Solver:
     """Owns a handle bound to the current torch CUDA stream."""
 
     def __init__(self, rho0: float = 1e-4, kappa: float = 1.5, kmeans_max_iter: int = 100,
-                 seed: int = 0, stream=None, device: int | None = None):
+                 seed: int = 0, stream=None, device: int | None = None, timing: bool = False):
         import torch
         cfg = respca_config_default()
         cfg.rho0, cfg.kappa, cfg.kmeans_max_iter, cfg.seed = rho0, kappa, kmeans_max_iter, seed
+        cfg.timing = 1 if timing else 0
         dev = torch.cuda.current_device() if device is None else device
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         cfg.stream = s.cuda_stream
