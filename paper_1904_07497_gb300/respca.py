@@ -97,6 +97,10 @@ def load():
     lib.respca_solve_batched.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(respca_problem),
                                          ctypes.POINTER(respca_stats)]
     lib.respca_solve_batched.restype = ctypes.c_int
+    lib.respca_init_labels_noalloc.argtypes = [ctypes.c_int32, _VP, _I64, _I64, _I64, ctypes.c_int32,
+                                               ctypes.c_uint64, ctypes.c_int32, _VP,
+                                               ctypes.POINTER(ctypes.c_int32), _VP]
+    lib.respca_init_labels_noalloc.restype = ctypes.c_int
     lib.respca_status_string.argtypes = [ctypes.c_int]
     lib.respca_status_string.restype = ctypes.c_char_p
     lib.respca_last_error.argtypes = [_VP]
@@ -188,6 +192,24 @@ def respca_init_labels(h, X, c: int, p) -> int:
     rc = load().respca_init_labels(h, _dtype_code(X), X.data_ptr(), d, n, ldx, int(c),
                                    p.data_ptr(), ctypes.byref(passes))
     _check(h, rc, "respca_init_labels")
+    return passes.value
+
+
+def respca_init_labels_noalloc(X, c: int, p, *, seed: int = 0, kmeans_max_iter: int = 100,
+                               stream=None) -> int:
+    """Initial labels with no device allocation (scratch in the library's
+    static device array): for callers that must not allocate while this runs,
+    e.g. during CUDA-graph capture or under their own memory pool.  X: (d, n)
+    column-major CUDA tensor; p: int32 (n,) CUDA tensor.  Returns the number
+    of Lloyd passes."""
+    d, n = X.shape
+    ldx = _colmajor(X, "X")
+    passes = ctypes.c_int32(0)
+    s = stream.cuda_stream if stream is not None else None
+    rc = load().respca_init_labels_noalloc(_dtype_code(X), X.data_ptr(), d, n, ldx, int(c),
+                                           int(seed), int(kmeans_max_iter), p.data_ptr(),
+                                           ctypes.byref(passes), s)
+    _check(None, rc, "respca_init_labels_noalloc")
     return passes.value
 
 
