@@ -63,7 +63,8 @@ typedef struct {
     uint64_t seed;           /* seed of the k-means++ draws for the initial labels */
     void *stream;            /* cudaStream_t for all work; NULL = the legacy default stream */
     int32_t device;          /* CUDA device ordinal; -1 = the device current at respca_create */
-    int32_t reserved1;
+    int32_t search_impl;     /* nearest-centroid search: 0 = tensor cores when c <= 256 (default),
+                                1 = CUDA-core kernel always */
 } respca_config;
 
 typedef struct {

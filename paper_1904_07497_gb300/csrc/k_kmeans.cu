@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(kThreads)
     k_assign(const TY* __restrict__ Y, int64_t ldy, int64_t d, int64_t n,
              const int32_t* __restrict__ list, const float* __restrict__ mu,
              const float* __restrict__ mu_normf, const int32_t* __restrict__ counts, int c,
-             int32_t* __restrict__ labels, DevStatus* __restrict__ status) {
+             int32_t* __restrict__ labels, DevStatus* __restrict__ status, float* __restrict__ ub,
+             float* __restrict__ lb) {
     extern __shared__ __align__(16) float smem[];
     constexpr int LS = kAsgCols + 1;          // Ls row stride
     constexpr int MS = kAsgClusters + 4;      // Ms row stride (float4 aligned)
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
 
-    float nrm = 0.f;
+    float nrm = 0.f, nrm_comp = 0.f;
     for (int cb = 0; cb < c; cb += kAsgClusters) {
         float acc[8], comp[8];
 #pragma unroll
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(kThreads)
             }
             __syncthreads();
             float part[8];
+            float npart = 0.f;
 #pragma unroll
             for (int q = 0; q < 8; ++q) part[q] = 0.f;
 #pragma unroll 8
@@ -183,7 +185,13 @@ __global__ void __launch_bounds__(kThreads)
                 part[5] = fmaf(m1.y, lv, part[5]);
                 part[6] = fmaf(m1.z, lv, part[6]);
                 part[7] = fmaf(m1.w, lv, part[7]);
-                if (cb == 0 && ty == 0) nrm = fmaf(lv, lv, nrm);
+                if (cb == 0 && ty == 0) npart = fmaf(lv, lv, npart);
+            }
+            if (cb == 0 && ty == 0) {   // Kahan accumulation of ||y_j||^2
+                const float y = npart - nrm_comp;
+                const float t = nrm + y;
+                nrm_comp = (t - nrm) - y;
+                nrm = t;
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {   // Kahan accumulation of the slab partials
@@ -227,15 +235,28 @@ __global__ void __launch_bounds__(kThreads)
             }
         }
         float ss = INFINITY;
+        int si = INT_MAX;
         for (int i = lane; i < c; i += 32) {
             const float s = scores[i * LS + q];
-            if (i != bi && s < ss) ss = s;
+            if (i != bi && s < ss) {
+                ss = s;
+                si = i;
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss = fminf(ss, __shfl_xor_sync(0xffffffffu, ss, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, ss, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, si, o);
+            if (os < ss || (os == ss && oi < si)) {
+                ss = os;
+                si = oi;
+            }
+        }
         if (bi >= c) continue;   // no finite score: keep the label
         int newlab = bi;
-        const float margin = kTieRel * (nrmL[q] + fabsf(mu_normf[bi]));
+        const float nl = nrmL[q];
+        const float margin = kTieRel * (nl + fabsf(mu_normf[bi]));
+        float ubv, lbv;
         if (ss - bs <= margin) {
             double best = INFINITY;
             int besti = bi;
@@ -254,7 +275,14 @@ __global__ void __launch_bounds__(kThreads)
                 }
             }
             newlab = besti;
+            ubv = (float)(sqrt(best) * (1.0 + 1e-6));
+            lbv = 0.f;          // near tie: search this column again next time
             if (lane == 0) atomicAdd(&status->rechecked, 1);
+        } else {
+            // distances from the scores, widened by their rounding bound
+            ubv = sqrtf(fmaxf(bs + nl + margin, 0.f)) * (1.f + 1e-6f);
+            const float ms = si < c ? kTieRel * (nl + fabsf(mu_normf[si])) : 0.f;
+            lbv = sqrtf(fmaxf(ss + nl - ms, 0.f)) * (1.f - 1e-6f);
         }
         if (lane == 0) {
             const int32_t old = labels[col];
@@ -262,13 +290,19 @@ __global__ void __launch_bounds__(kThreads)
                 labels[col] = newlab;
                 atomicAdd(&status->changed, 1);
             }
+            if (ub) {
+                ub[col] = ubv;
+                lb[col] = lbv;
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------- k-means++
-// D2[j] (= or min=) squared distance of column j to the centre centers[k].
-template <typename TX>
+// D2[j] (= or min=) squared distance of column j to the centre centers[k]:
+// one warp per column, FP32 differences summed per lane with Kahan
+// compensation over 8-element groups, FP64 across lanes.
+template <typename TX, bool VEC>
 __global__ void __launch_bounds__(kThreads)
     k_seed_dist(const TX* __restrict__ X, int64_t ldx, int64_t d, int64_t n,
                 const int32_t* __restrict__ centers, int k, double* __restrict__ D2) {
@@ -279,20 +313,45 @@ __global__ void __launch_bounds__(kThreads)
     for (int64_t j = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); j < n; j += warps) {
         const TX* xj = X + j * ldx;
         float s = 0.f, comp = 0.f;
-        for (int64_t r0 = 0; r0 < d; r0 += 32 * 8) {
-            float part = 0.f;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t r = r0 + u * 32 + lane;
-                if (r < d) {
-                    const float t = XLoad<TX>::one(xj + r) - XLoad<TX>::one(xc + r);
-                    part = fmaf(t, t, part);
+        if (VEC) {
+            for (int64_t r0 = lane * 4; r0 < d; r0 += 32 * 8) {
+                float part = 0.f;
+                const float4 a0 = XLoad<TX>::four(xj + r0), b0 = XLoad<TX>::four(xc + r0);
+                float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = a1;
+                if (r0 + 128 < d) {
+                    a1 = XLoad<TX>::four(xj + r0 + 128);
+                    b1 = XLoad<TX>::four(xc + r0 + 128);
                 }
+                float t;
+                t = a0.x - b0.x; part = fmaf(t, t, part);
+                t = a0.y - b0.y; part = fmaf(t, t, part);
+                t = a0.z - b0.z; part = fmaf(t, t, part);
+                t = a0.w - b0.w; part = fmaf(t, t, part);
+                t = a1.x - b1.x; part = fmaf(t, t, part);
+                t = a1.y - b1.y; part = fmaf(t, t, part);
+                t = a1.z - b1.z; part = fmaf(t, t, part);
+                t = a1.w - b1.w; part = fmaf(t, t, part);
+                const float y = part - comp;
+                const float u = s + y;
+                comp = (u - s) - y;
+                s = u;
             }
-            const float y = part - comp;
-            const float t = s + y;
-            comp = (t - s) - y;
-            s = t;
+        } else {
+            for (int64_t r0 = 0; r0 < d; r0 += 32 * 8) {
+                float part = 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int64_t r = r0 + u * 32 + lane;
+                    if (r < d) {
+                        const float t = XLoad<TX>::one(xj + r) - XLoad<TX>::one(xc + r);
+                        part = fmaf(t, t, part);
+                    }
+                }
+                const float y = part - comp;
+                const float u = s + y;
+                comp = (u - s) - y;
+                s = u;
+            }
         }
         const double v = warp_sum((double)s);
         if (lane == 0) D2[j] = (k == 0) ? v : fmin(D2[j], v);
@@ -412,7 +471,7 @@ size_t assign_smem_bytes(int c) {
 cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
                           const int32_t* list, const float* mu, const float* mu_normf,
                           const int32_t* counts, int c, int32_t* labels, DevStatus* status,
-                          cudaStream_t st) {
+                          cudaStream_t st, float* ub, float* lb) {
     count_launches(1);
     const size_t smem = assign_smem_bytes(c);
     const int grid = grid_for(n, kAsgCols);
@@ -421,7 +480,7 @@ cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int6
         e = cudaFuncSetAttribute(k_assign<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             k_assign<TY><<<grid, kThreads, smem, st>>>((const TY*)Y, ldy, d, n, list, mu, mu_normf,
-                                                       counts, c, labels, status);
+                                                       counts, c, labels, status, ub, lb);
     });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -432,7 +491,12 @@ cudaError_t launch_seed_dist(int dtype, const void* X, int64_t ldx, int64_t d, i
     count_launches(1);
     const int grid = grid_for(n, kThreads / 32);
     RESPCA_DISPATCH_X(dtype, TX, {
-        k_seed_dist<TX><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, centers, k, D2);
+        const bool vec = (ldx % 4 == 0) && (d % 4 == 0) &&
+                         (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(TX)) == 0);
+        if (vec)
+            k_seed_dist<TX, true><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, centers, k, D2);
+        else
+            k_seed_dist<TX, false><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, centers, k, D2);
     });
     return cudaGetLastError();
 }

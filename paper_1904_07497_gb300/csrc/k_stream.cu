@@ -76,7 +76,7 @@ __global__ void k_sum_parts(const double* __restrict__ part, int nparts, double*
 // One element of one ALM iteration.  l, sn, tn are the new L, S, Theta.
 __device__ __forceinline__ void alm_element(float x, float s, float t, float l0, float m,
                                             const IterScalars& sc, float& l, float& sn, float& tn,
-                                            float& own, float& nr, float& ndl, float& nds,
+                                            float& own, float& nr, float& dlc, float& nds,
                                             float& dnext) {
     const float tr = t * sc.inv_rho;
     const float dv = (x - s) + tr;                    // D = X - S + Theta/rho (after Eq. (14))
@@ -91,7 +91,7 @@ __device__ __forceinline__ void alm_element(float x, float s, float t, float l0,
     const float e = l - m;
     own = fmaf(e, e, own);
     nr = fmaf(res, res, nr);
-    ndl = fmaf(dl, dl, ndl);
+    dlc = fmaf(dl, dl, dlc);
     nds = fmaf(ds, ds, nds);
     dnext = (x - sn) + tn * sc.inv_rho_next;          // D of the next iteration
 }
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const int32_t* __restrict__ perm, const TileDesc* __restrict__ tiles,
                 const DevStatus* __restrict__ status, int64_t d, int64_t n, IterScalars sc,
                 float* __restrict__ Dpart, float* __restrict__ own_part,
-                double* __restrict__ norm_part) {
+                float* __restrict__ dl_part, double* __restrict__ norm_part) {
     __shared__ float red[kThreads / 32][kChunkRows];
     __shared__ double nred[kThreads / 32][3];
     const int tile_idx = blockIdx.x;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         float* lc = L + col * lds;
         float* scol = S + col * lds;
         float* tc = Th + col * lds;
-        float own = 0.f;
+        float own = 0.f, dlc = 0.f;
         if (VEC) {
             float4 xv[4], sv[4], tv[4], lv[4];
 #pragma unroll
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     for (int q = 0; q < 4; ++q) {
                         float l, sn, tn, dn;
                         alm_element(f4get(xv[s], q), f4get(sv[s], q), f4get(tv[s], q),
-                                    f4get(lv[s], q), f4get(m[s], q), sc, l, sn, tn, own, nr, ndl,
+                                    f4get(lv[s], q), f4get(m[s], q), sc, l, sn, tn, own, nr, dlc,
                                     nds, dn);
                         f4set(lo, q, l);
                         f4set(so, q, sn);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (rr + q < d) {
                         float l, sn, tn, dn;
                         alm_element(XLoad<TX>::one(xc + rr + q), scol[rr + q], tc[rr + q],
-                                    lc[rr + q], f4get(m[s], q), sc, l, sn, tn, own, nr, ndl, nds,
+                                    lc[rr + q], f4get(m[s], q), sc, l, sn, tn, own, nr, dlc, nds,
                                     dn);
                         lc[rr + q] = l;
                         scol[rr + q] = sn;
@@ -189,8 +189,13 @@ __global__ void __launch_bounds__(kThreads, 2)
                 }
             }
         }
+        ndl += dlc;
         own = warp_sum(own);
-        if (lane == 0) own_part[(int64_t)blockIdx.y * n + col] = own;
+        dlc = warp_sum(dlc);
+        if (lane == 0) {
+            own_part[(int64_t)blockIdx.y * n + col] = own;
+            dl_part[(int64_t)blockIdx.y * n + col] = dlc;
+        }
     }
 
 #pragma unroll
@@ -301,15 +306,86 @@ __global__ void __launch_bounds__(kThreads)
 // in no assignment).
 __global__ void __launch_bounds__(kThreads)
     k_centroids(const float* __restrict__ Dpart, const int32_t* __restrict__ tile_off,
-                const int32_t* __restrict__ counts, int64_t d, float* __restrict__ mu) {
+                const int32_t* __restrict__ counts, int64_t d, float* __restrict__ mu,
+                double* __restrict__ sums_out) {
+    const int i = blockIdx.y;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= d) return;
+    const int cnt = counts[i];
+    const int t0 = tile_off[i], t1 = tile_off[i + 1];
+    double s = 0.0;
+    for (int t = t0; t < t1; ++t) s += (double)Dpart[(int64_t)t * d + r];
+    if (sums_out) sums_out[(int64_t)i * d + r] = s;
+    if (cnt > 0) mu[(int64_t)i * d + r] = (float)(s / (double)cnt);
+}
+
+// Centroids from FP64 cluster sums (kept up to date incrementally).
+__global__ void __launch_bounds__(kThreads)
+    k_centroids_from_sums(const double* __restrict__ sums, const int32_t* __restrict__ counts,
+                          int64_t d, float* __restrict__ mu) {
     const int i = blockIdx.y;
     const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int cnt = counts[i];
     if (cnt == 0 || r >= d) return;
-    const int t0 = tile_off[i], t1 = tile_off[i + 1];
-    double s = 0.0;
-    for (int t = t0; t < t1; ++t) s += (double)Dpart[(int64_t)t * d + r];
-    mu[(int64_t)i * d + r] = (float)(s / (double)cnt);
+    mu[(int64_t)i * d + r] = (float)(sums[(int64_t)i * d + r] / (double)cnt);
+}
+
+// Move the columns listed in `moved` between cluster sums: for each moved
+// column j (in list order, so the FP64 sums are deterministic) subtract its
+// values from its old cluster's sums and add them to the new one's.
+template <int MODE, typename TX>
+__global__ void __launch_bounds__(kThreads)
+    k_delta_sums(const TX* __restrict__ X, int64_t ldx, const float* __restrict__ L, int64_t lds,
+                 const int4* __restrict__ moved, const DevStatus* __restrict__ status, int64_t d,
+                 double* __restrict__ sums) {
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= d) return;
+    const int nm = status->moved;
+    for (int m = 0; m < nm; ++m) {
+        const int4 mv = moved[m];   // column, old label, new label
+        const int64_t j = mv.x;
+        const double v = (MODE == kSumX) ? (double)XLoad<TX>::one(X + j * ldx + r)
+                                         : (double)L[j * lds + r];
+        if (mv.y >= 0) sums[(int64_t)mv.y * d + r] -= v;
+        sums[(int64_t)mv.z * d + r] += v;
+    }
+}
+
+// ||mu_i||^2 and, when mu_old is given, the drift ||mu_i - mu_old_i||.
+__global__ void __launch_bounds__(kThreads)
+    k_mu_stats(const float* __restrict__ mu, const float* __restrict__ mu_old, int64_t d,
+               double* __restrict__ mu_norm2, float* __restrict__ mu_normf,
+               double* __restrict__ drift) {
+    __shared__ double red[kThreads / 32][2];
+    const int i = blockIdx.x;
+    const float* m = mu + (int64_t)i * d;
+    const float* mo = mu_old ? mu_old + (int64_t)i * d : nullptr;
+    double acc = 0.0, dr = 0.0;
+    for (int64_t r = threadIdx.x; r < d; r += kThreads) {
+        const double v = (double)m[r];
+        acc += v * v;
+        if (mo) {
+            const double t = v - (double)mo[r];
+            dr += t * t;
+        }
+    }
+    acc = warp_sum(acc);
+    dr = warp_sum(dr);
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = acc;
+        red[threadIdx.x >> 5][1] = dr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0, u = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            t += red[w][0];
+            u += red[w][1];
+        }
+        mu_norm2[i] = t;
+        mu_normf[i] = (float)t;
+        if (drift) drift[i] = sqrt(u);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -436,6 +512,141 @@ __global__ void __launch_bounds__(kThreads)
     if (flag) flag_list[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)j;
 }
 
+// Hamerly-style exact pruning of the nearest-centroid search.  Per column j
+// with label p: ub[j] >= ||L_j - mu_p|| and lb[j] <= min_{i != p} ||L_j - mu_i||.
+// The own label is provably the strict nearest when ub < lb.
+//   kBoundsIter (after the fused pass): ub = exact own distance to the new
+//     centroids; lb degrades by the column's own movement and by the largest
+//     drift of another centroid, and is raised to sep_p - ub when the
+//     centroid separation gives more.
+//   kBoundsLloyd (centroids moved, points fixed): ub grows by the own
+//     centroid's drift, lb shrinks by the largest drift of another centroid.
+// Columns that fail are queued; the search then resets both bounds exactly.
+constexpr float kRelSlack = 1e-5f;
+
+__global__ void __launch_bounds__(kThreads)
+    k_flag_bounds(int mode, const float* __restrict__ own_part, const float* __restrict__ dl_part,
+                  int nchunks, int64_t n, int c, const int32_t* __restrict__ labels,
+                  const int32_t* __restrict__ counts, const double* __restrict__ sep2,
+                  double safety, const double* __restrict__ drift, float* __restrict__ ub,
+                  float* __restrict__ lb, int32_t* __restrict__ flag_list,
+                  DevStatus* __restrict__ status) {
+    // largest and second largest drift over active clusters (per block)
+    __shared__ double s_d1[kThreads], s_d2[kThreads];
+    __shared__ int s_i1[kThreads];
+    double d1 = 0.0, d2 = 0.0;
+    int i1 = -1;
+    if (drift) {
+        for (int i = threadIdx.x; i < c; i += kThreads) {
+            if (counts[i] == 0) continue;
+            const double v = drift[i];
+            if (v > d1) {
+                d2 = d1;
+                d1 = v;
+                i1 = i;
+            } else if (v > d2) {
+                d2 = v;
+            }
+        }
+    }
+    s_d1[threadIdx.x] = d1;
+    s_d2[threadIdx.x] = d2;
+    s_i1[threadIdx.x] = i1;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double a1 = s_d1[threadIdx.x], a2 = s_d2[threadIdx.x];
+            const double b1 = s_d1[threadIdx.x + o], b2 = s_d2[threadIdx.x + o];
+            if (b1 > a1) {
+                s_d1[threadIdx.x] = b1;
+                s_i1[threadIdx.x] = s_i1[threadIdx.x + o];
+                s_d2[threadIdx.x] = fmax(a1, b2);
+            } else {
+                s_d2[threadIdx.x] = fmax(a2, b1);
+            }
+        }
+        __syncthreads();
+    }
+    d1 = s_d1[0];
+    d2 = s_d2[0];
+    i1 = s_i1[0];
+
+    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    bool flag = false;
+    if (j < n) {
+        const int p = labels[j];
+        const double other = (p == i1) ? d2 : d1;
+        double u, l;
+        if (mode == kBoundsIter) {
+            double own = 0.0, mv = 0.0;
+            for (int ch = 0; ch < nchunks; ++ch) {
+                own += (double)own_part[(int64_t)ch * n + j];
+                mv += (double)dl_part[(int64_t)ch * n + j];
+            }
+            const double eo = sqrt(own);
+            u = eo * (1.0 + kRelSlack) + 1e-30;
+            l = (double)lb[j] - sqrt(mv) * (1.0 + kRelSlack) - other * (1.0 + kRelSlack);
+            const double sp = sep2[p];
+            if (sp > 0.0) l = fmax(l, sqrt(sp * safety) - u);
+        } else {
+            const double own_drift = drift ? drift[p] : 0.0;
+            u = (double)ub[j] + own_drift * (1.0 + kRelSlack);
+            l = (double)lb[j] - other * (1.0 + kRelSlack);
+        }
+        ub[j] = (float)(u * (1.0 + 1e-7));
+        lb[j] = (float)(l > 0.0 ? l * (1.0 - 1e-7) : l);
+        flag = !(u < l);
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && mask) base = atomicAdd(&status->flagged, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (flag) flag_list[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)j;
+}
+
+// Columns whose label differs between `now` and `before`, in column order
+// (single CTA; deterministic), as (column, old, new) triples; the cluster
+// sizes follow the move.
+__global__ void __launch_bounds__(1024)
+    k_moved(const int32_t* __restrict__ now, const int32_t* __restrict__ before, int64_t n,
+            int4* __restrict__ moved, int32_t* __restrict__ counts, DevStatus* __restrict__ status) {
+    __shared__ int wcount[32];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < n; b0 += blockDim.x) {
+        const int64_t j = b0 + threadIdx.x;
+        int a = -1, o = -1;
+        bool mv = false;
+        if (j < n) {
+            a = now[j];
+            o = before[j];
+            mv = a != o;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, mv);
+        if (lane == 0) wcount[warp] = __popc(mask);
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += wcount[w];
+        if (mv) {
+            const int pos = base + off + __popc(mask & ((1u << lane) - 1u));
+            moved[pos] = make_int4((int)j, o, a, 0);
+            if (o >= 0) atomicSub(&counts[o], 1);
+            atomicAdd(&counts[a], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += wcount[w];
+            base += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) status->moved = base;
+}
+
 __global__ void __launch_bounds__(kThreads)
     k_count_changed(const int32_t* __restrict__ labels, const int32_t* __restrict__ prev, int64_t n,
                     DevStatus* __restrict__ status) {
@@ -504,10 +715,59 @@ cudaError_t launch_colsum(int mode, int dtype, const void* X, int64_t ldx, const
 }
 
 cudaError_t launch_centroids(const float* Dpart, const int32_t* tile_off, const int32_t* counts,
-                             int c, int64_t d, float* mu, cudaStream_t st) {
+                             int c, int64_t d, float* mu, cudaStream_t st, double* sums_out) {
     count_launches(1);
     const dim3 grid(grid_for(d, kThreads), c);
-    k_centroids<<<grid, kThreads, 0, st>>>(Dpart, tile_off, counts, d, mu);
+    k_centroids<<<grid, kThreads, 0, st>>>(Dpart, tile_off, counts, d, mu, sums_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centroids_from_sums(const double* sums, const int32_t* counts, int c, int64_t d,
+                                       float* mu, cudaStream_t st) {
+    count_launches(1);
+    const dim3 grid(grid_for(d, kThreads), c);
+    k_centroids_from_sums<<<grid, kThreads, 0, st>>>(sums, counts, d, mu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, const float* L,
+                              int64_t lds, const int4* moved, const DevStatus* status, int64_t d,
+                              double* sums, cudaStream_t st) {
+    count_launches(1);
+    const int grid = grid_for(d, kThreads);
+    if (mode == kSumL) {
+        k_delta_sums<kSumL, float><<<grid, kThreads, 0, st>>>(nullptr, 0, L, lds, moved, status, d, sums);
+    } else {
+        RESPCA_DISPATCH_X(dtype, TX, {
+            k_delta_sums<kSumX, TX><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, nullptr, 0, moved,
+                                                               status, d, sums);
+        });
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t d,
+                            double* mu_norm2, float* mu_normf, double* drift, cudaStream_t st) {
+    count_launches(1);
+    k_mu_stats<<<c, kThreads, 0, st>>>(mu, mu_old, d, mu_norm2, mu_normf, drift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_part, int nchunks,
+                               int64_t n, int c, const int32_t* labels, const int32_t* counts,
+                               const double* sep2, double safety, const double* drift, float* ub,
+                               float* lb, int32_t* flag_list, DevStatus* status, cudaStream_t st) {
+    count_launches(1);
+    k_flag_bounds<<<grid_for(n, kThreads), kThreads, 0, st>>>(mode, own_part, dl_part, nchunks, n, c,
+                                                              labels, counts, sep2, safety, drift,
+                                                              ub, lb, flag_list, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int4* moved,
+                         int32_t* counts, DevStatus* status, cudaStream_t st) {
+    count_launches(1);
+    k_moved<<<1, 1024, 0, st>>>(now, before, n, moved, counts, status);
     return cudaGetLastError();
 }
 
@@ -542,18 +802,18 @@ cudaError_t launch_iteration(int dtype, const void* X, int64_t ldx, float* L, fl
                              int64_t lds, const float* mu, const int32_t* perm,
                              const TileDesc* tiles, int max_tiles, const DevStatus* status,
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
-                             double* norm_part, bool vec, cudaStream_t st) {
+                             float* dl_part, double* norm_part, bool vec, cudaStream_t st) {
     count_launches(1);
     const dim3 grid(max_tiles, grid_for(d, kChunkRows));
     RESPCA_DISPATCH_X(dtype, TX, {
         if (vec)
             k_iteration<TX, true><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, L, S, Th, lds, mu,
                                                              perm, tiles, status, d, n, sc, Dpart,
-                                                             own_part, norm_part);
+                                                             own_part, dl_part, norm_part);
         else
             k_iteration<TX, false><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, L, S, Th, lds, mu,
                                                               perm, tiles, status, d, n, sc, Dpart,
-                                                              own_part, norm_part);
+                                                              own_part, dl_part, norm_part);
     });
     return cudaGetLastError();
 }

@@ -51,7 +51,9 @@ struct respca_ctx {
     // device workspace, grown on demand
     DevBuf theta, mu, mu_norm2, mu_normf, pair_ss, sep2, perm, counts, tile_off, tiles, labels_prev,
         Dpart, own_part, norm_part, flag_list, seedD2, centers, seed_u, fro_part, status,
-        hX, hL, hS, hp, hp0;
+        hX, hL, hS, hp, hp0,
+        mu_next, mu_old, drift, ub, lb, dl_part, sums, moved, labels_pass,
+        mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count;
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -101,7 +103,6 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
     const int mt = max_tiles_for(n, c);
     const int nch = nchunks_for(d);
     if (need_theta) CK(ensure(h->theta, sizeof(float) * (size_t)lds * n));
-    CK(ensure(h->mu, sizeof(float) * (size_t)c * d));
     CK(ensure(h->mu_norm2, sizeof(double) * c));
     CK(ensure(h->mu_normf, sizeof(float) * c));
     CK(ensure(h->pair_ss, sizeof(float) * (size_t)std::min(c, 256) * std::min(c, 256)));
@@ -120,6 +121,33 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
     CK(ensure(h->seed_u, sizeof(double) * c));
     CK(ensure(h->fro_part, sizeof(double) * kFroParts));
     CK(ensure(h->status, sizeof(DevStatus)));
+    // centroid buffers start zeroed so entries of clusters that never had a
+    // member hold finite values
+    for (DevBuf* b : {&h->mu, &h->mu_next, &h->mu_old}) {
+        const bool fresh = b->bytes < sizeof(float) * (size_t)c * d;
+        CK(ensure(*b, sizeof(float) * (size_t)c * d));
+        if (fresh) CK(cudaMemsetAsync(b->p, 0, b->bytes, h->stream));
+    }
+    CK(ensure(h->drift, sizeof(double) * c));
+    CK(ensure(h->ub, sizeof(float) * n));
+    CK(ensure(h->lb, sizeof(float) * n));
+    CK(ensure(h->dl_part, sizeof(float) * (size_t)nch * n));
+    CK(ensure(h->sums, sizeof(double) * (size_t)c * d));
+    CK(ensure(h->moved, sizeof(int4) * n));
+    CK(ensure(h->labels_pass, sizeof(int32_t) * n));
+    if (c <= kTcMaxClusters) {
+        const int Npad = tc_npad(c);
+        const int64_t dpad = (d + 31) / 32 * 32;
+        CK(ensure(h->mu_hi, sizeof(float) * (size_t)Npad * dpad));
+        CK(ensure(h->mu_lo, sizeof(float) * (size_t)Npad * dpad));
+        const int64_t ntile = (n + 127) / 128;
+        CK(ensure(h->Gpart, sizeof(float) * (size_t)tc_splits(n, d) * Npad * ntile * 128));
+        CK(ensure(h->ynorm_part, sizeof(float) * (size_t)tc_splits(n, d) * ntile * 128));
+        const bool fresh = h->tile_count.bytes < sizeof(int32_t) * (size_t)ntile;
+        CK(ensure(h->tile_count, sizeof(int32_t) * ntile));
+        if (fresh) CK(cudaMemsetAsync(h->tile_count.p, 0, h->tile_count.bytes, h->stream));
+    }
+    CK(ensure(h->rc_list, sizeof(int32_t) * n));
     if (h->hseed_cap < (size_t)c) {
         if (h->hseed_u) cudaFreeHost(h->hseed_u);
         h->hseed_u = nullptr;
@@ -133,6 +161,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
 respca_status read_status(respca_ctx* h) {
     CK(cudaMemcpyAsync(h->hstat, h->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (h->hstat->timeout) return fail(h, RESPCA_ERR_TIMEOUT, "a bounded device wait gave up");
     return RESPCA_OK;
 }
 
@@ -142,14 +171,16 @@ cudaError_t zero_counters(respca_ctx* h) {
     return cudaMemsetAsync(&s->flagged, 0, 3 * sizeof(int32_t), h->stream);
 }
 
-// Centroids mu (and their norms and separations) from the tile sums in Dpart.
-respca_status finish_centroids(respca_ctx* h, int c, int64_t d) {
+// Centroids (and their norms, drift from the centroids the last search used,
+// and pairwise separations) from the tile sums in Dpart, written to `dst`;
+// `prev` holds the centroids of the last search.
+respca_status finish_centroids(respca_ctx* h, int c, int64_t d, float* dst, const float* prev) {
     CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c, d,
-                        P<float>(h->mu), h->stream));
-    CK(launch_mu_norms(P<float>(h->mu), c, d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
-                       h->stream));
-    CK(launch_separation(P<float>(h->mu), P<int32_t>(h->counts), c, d, P<float>(h->pair_ss),
-                         P<double>(h->sep2), h->stream));
+                        dst, h->stream));
+    CK(launch_mu_stats(dst, prev, c, d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
+                       prev ? P<double>(h->drift) : nullptr, h->stream));
+    CK(launch_separation(dst, P<int32_t>(h->counts), c, d, P<float>(h->pair_ss), P<double>(h->sep2),
+                         h->stream));
     return RESPCA_OK;
 }
 
@@ -165,6 +196,85 @@ struct Problem {
     int32_t* p;
     bool vec;     // 16-byte vector path usable for X, L, S, Theta, mu
 };
+
+// Nearest-centroid search (Sec. 4.2 assignment) for the listed columns of Y
+// (all columns when list is null) against the centroids in h->mu: tensor
+// cores for c <= 256 unless the handle asks for the CUDA-core kernel.
+respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
+                     const int32_t* list, int c, int32_t* p, bool vec) {
+    DevStatus* ds = P<DevStatus>(h->status);
+    if (c <= kTcMaxClusters && h->cfg.search_impl == 0) {
+        const int Npad = tc_npad(c);
+        const int64_t dpad = (d + 31) / 32 * 32;
+        CK(launch_mu_split(P<float>(h->mu), c, d, Npad, dpad, P<float>(h->mu_hi), P<float>(h->mu_lo),
+                           h->stream));
+        CK(launch_search_tc(dtype, Y, ldy, d, n, list, ds, P<float>(h->mu), P<float>(h->mu_hi),
+                            P<float>(h->mu_lo), dpad, P<float>(h->mu_normf), P<int32_t>(h->counts), c,
+                            p, P<float>(h->ub), P<float>(h->lb), P<float>(h->Gpart),
+                            P<float>(h->ynorm_part), P<int32_t>(h->tile_count), P<int32_t>(h->rc_list),
+                            vec, h->stream));
+    } else {
+        CK(launch_assign(dtype, Y, ldy, d, n, list, P<float>(h->mu), P<float>(h->mu_normf),
+                         P<int32_t>(h->counts), c, p, ds, h->stream, P<float>(h->ub), P<float>(h->lb)));
+    }
+    return RESPCA_OK;
+}
+
+struct SearchCounts {
+    int passes = 0;
+    int64_t assigned = 0;
+    int64_t rechecked = 0;
+};
+
+// Lloyd passes after an assignment moved some labels (Sec. 4.2 p step, or
+// the initial labels): centroids become the means of the columns of Y under
+// the new labels (the first time from a full pass over Y, then by moving only
+// the columns whose label changed), every column's bounds degrade by the
+// centroid drift, and only the columns the bounds cannot settle are searched.
+// Stops when a pass changes no label or after max_passes passes in total.
+respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ldy,
+                             int64_t d, int64_t n, int c, int32_t* p, bool vec, int max_passes,
+                             SearchCounts* sc) {
+    DevStatus* ds = P<DevStatus>(h->status);
+    const int mt = max_tiles_for(n, c);
+    const float* Lp = (mode == kSumL) ? static_cast<const float*>(Y) : nullptr;
+    CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts), P<int32_t>(h->tile_off),
+                          P<TileDesc>(h->tiles), ds, h->stream));
+    CK(launch_colsum(mode, dtype, Y, ldy, Lp, nullptr, nullptr, ldy, 0.f, P<int32_t>(h->perm),
+                     P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart), vec, h->stream));
+    CK(cudaMemcpyAsync(h->mu_old.p, h->mu.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice,
+                       h->stream));
+    CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c, d,
+                        P<float>(h->mu), h->stream, P<double>(h->sums)));
+    CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
+                       P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+    while (sc->passes < max_passes) {
+        CK(zero_counters(h));
+        CK(launch_flag_bounds(kBoundsLloyd, nullptr, nullptr, 0, n, c, p, P<int32_t>(h->counts),
+                              nullptr, 1.0, P<double>(h->drift), P<float>(h->ub), P<float>(h->lb),
+                              P<int32_t>(h->flag_list), ds, h->stream));
+        CK(cudaMemcpyAsync(h->labels_pass.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
+        respca_status rs = search(h, dtype, Y, ldy, d, n, P<int32_t>(h->flag_list), c, p, vec);
+        if (rs != RESPCA_OK) return rs;
+        rs = read_status(h);
+        if (rs != RESPCA_OK) return rs;
+        sc->passes += 1;
+        sc->assigned += h->hstat->flagged;
+        sc->rechecked += h->hstat->rechecked;
+        if (h->hstat->changed == 0 || sc->passes >= max_passes) break;
+        CK(launch_moved(p, P<int32_t>(h->labels_pass), n, P<int4>(h->moved), P<int32_t>(h->counts), ds,
+                        h->stream));
+        CK(launch_delta_sums(mode, dtype, Y, ldy, Lp, ldy, P<int4>(h->moved), ds, d, P<double>(h->sums),
+                             h->stream));
+        CK(cudaMemcpyAsync(h->mu_old.p, h->mu.p, sizeof(float) * (size_t)c * d,
+                           cudaMemcpyDeviceToDevice, h->stream));
+        CK(launch_centroids_from_sums(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
+                                      h->stream));
+        CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
+                           P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+    }
+    return RESPCA_OK;
+}
 
 // Initial labels: k-means++ seeding (D^2 sampling with splitmix64 draws),
 // then Lloyd on the columns of X until no label changes.
@@ -185,35 +295,26 @@ respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out
             CK(launch_seed_dist(pb.dtype, pb.X, pb.ldx, pb.d, pb.n, P<int32_t>(h->centers), k,
                                 P<double>(h->seedD2), h->stream));
     }
-    // the stack value `first` must outlive its async copy
-    CK(cudaStreamSynchronize(h->stream));
     CK(launch_gather_centers(pb.dtype, pb.X, pb.ldx, pb.d, P<int32_t>(h->centers), c, P<float>(h->mu),
                              P<int32_t>(h->counts), h->stream));
-    CK(launch_mu_norms(P<float>(h->mu), c, pb.d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
-                       h->stream));
+    CK(launch_mu_stats(P<float>(h->mu), nullptr, c, pb.d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
+                       nullptr, h->stream));
     CK(cudaMemsetAsync(pb.p, 0xFF, sizeof(int32_t) * pb.n, h->stream));
+    CK(cudaMemsetAsync(h->lb.p, 0, sizeof(float) * pb.n, h->stream));
     DevStatus* ds = P<DevStatus>(h->status);
-    int passes = 0;
     const int km = std::max(1, h->cfg.kmeans_max_iter);
-    while (passes < km) {
-        CK(zero_counters(h));
-        CK(launch_assign(pb.dtype, pb.X, pb.ldx, pb.d, pb.n, nullptr, P<float>(h->mu),
-                         P<float>(h->mu_normf), P<int32_t>(h->counts), c, pb.p, ds, h->stream));
-        ++passes;
-        respca_status rs = read_status(h);
+    SearchCounts sc;
+    CK(zero_counters(h));
+    respca_status rs = search(h, pb.dtype, pb.X, pb.ldx, pb.d, pb.n, nullptr, c, pb.p, pb.vec);
+    if (rs != RESPCA_OK) return rs;
+    rs = read_status(h);
+    if (rs != RESPCA_OK) return rs;
+    sc.passes = 1;
+    if (h->hstat->changed > 0 && km > 1) {
+        rs = lloyd_continue(h, kSumX, pb.dtype, pb.X, pb.ldx, pb.d, pb.n, c, pb.p, pb.vec, km, &sc);
         if (rs != RESPCA_OK) return rs;
-        if (h->hstat->changed == 0) break;
-        CK(launch_sort_labels(pb.p, pb.n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
-                              P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
-        CK(launch_colsum(kSumX, pb.dtype, pb.X, pb.ldx, nullptr, nullptr, nullptr, 0, 0.f,
-                         P<int32_t>(h->perm), P<TileDesc>(h->tiles), max_tiles_for(pb.n, c), ds, pb.d,
-                         P<float>(h->Dpart), pb.vec, h->stream));
-        CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c,
-                            pb.d, P<float>(h->mu), h->stream));
-        CK(launch_mu_norms(P<float>(h->mu), c, pb.d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
-                           h->stream));
     }
-    if (passes_out) *passes_out = passes;
+    if (passes_out) *passes_out = sc.passes;
     return RESPCA_OK;
 }
 
@@ -328,12 +429,15 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         return RESPCA_OK;
     }
 
-    // centroids of D = X - S + Theta/rho under the current labels
+    // centroids of D = X - S + Theta/rho under the current labels; no bound
+    // information yet (lb = 0, no drift)
     CK(launch_colsum(kSumD, dtype, X, ldx, nullptr, S, pb.Th, lds, (float)(1.0 / rho),
                      P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart), pb.vec,
                      h->stream));
-    rs = finish_centroids(h, c, d);
+    rs = finish_centroids(h, c, d, P<float>(h->mu), nullptr);
     if (rs != RESPCA_OK) return rs;
+    CK(cudaMemsetAsync(h->lb.p, 0, sizeof(float) * n, h->stream));
+    CK(cudaMemsetAsync(h->drift.p, 0, sizeof(double) * c, h->stream));
     CK(cudaEventRecord(h->ev2, h->stream));
 
     const int km = std::max(1, h->cfg.kmeans_max_iter);
@@ -350,19 +454,25 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
 
         CK(zero_counters(h));
         CK(cudaMemcpyAsync(h->labels_prev.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
-        // L, S, Theta, norms, own distances and next-D sums in one pass
+        // L, S, Theta, norms, own distances, column movement and next-D sums in one pass
         if (timing) CK(cudaEventRecord(h->evk0, h->stream));
         CK(launch_iteration(dtype, X, ldx, L, S, pb.Th, lds, P<float>(h->mu), P<int32_t>(h->perm),
                             P<TileDesc>(h->tiles), mt, ds, d, n, sc, P<float>(h->Dpart),
-                            P<float>(h->own_part), P<double>(h->norm_part), pb.vec, h->stream));
+                            P<float>(h->own_part), P<float>(h->dl_part), P<double>(h->norm_part),
+                            pb.vec, h->stream));
         if (timing) CK(cudaEventRecord(h->evk1, h->stream));
         out.fused_launches += 1;
         CK(launch_reduce_norms(P<double>(h->norm_part), mt, nch, ds, h->stream));
-        // p step: first Lloyd assignment, searching only the columns the bound cannot settle
-        CK(launch_flag_columns(P<float>(h->own_part), nch, n, p, P<double>(h->sep2), safety,
-                               P<int32_t>(h->flag_list), ds, h->stream));
-        CK(launch_assign(RESPCA_F32, L, lds, d, n, P<int32_t>(h->flag_list), P<float>(h->mu),
-                         P<float>(h->mu_normf), P<int32_t>(h->counts), c, p, ds, h->stream));
+        // p step, first Lloyd assignment: search only the columns the bounds cannot settle
+        CK(launch_flag_bounds(kBoundsIter, P<float>(h->own_part), P<float>(h->dl_part), nch, n, c, p,
+                              P<int32_t>(h->counts), P<double>(h->sep2), safety, P<double>(h->drift),
+                              P<float>(h->ub), P<float>(h->lb), P<int32_t>(h->flag_list), ds,
+                              h->stream));
+        rs = search(h, RESPCA_F32, L, lds, d, n, P<int32_t>(h->flag_list), c, p, pb.vec);
+        if (rs != RESPCA_OK) return rs;
+        // next centroids if every label stays (queued before the check; discarded otherwise)
+        rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
+        if (rs != RESPCA_OK) return rs;
         rs = read_status(h);
         if (rs != RESPCA_OK) return rs;
         if (timing) {
@@ -376,41 +486,25 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         const double r2 = h->hstat->norm2[0], dl2 = h->hstat->norm2[1], ds2 = h->hstat->norm2[2];
 
         if (h->hstat->changed == 0) {
-            // labels kept: the next centroids are the D sums of this pass
-            rs = finish_centroids(h, c, d);
-            if (rs != RESPCA_OK) return rs;
+            std::swap(h->mu, h->mu_next);
         } else {
             // Lloyd on the columns of L until no label changes
-            int passes = 1;
-            while (passes < km) {
-                CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
-                                      P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
-                CK(launch_colsum(kSumL, RESPCA_F32, nullptr, 0, L, nullptr, nullptr, lds, 0.f,
-                                 P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d,
-                                 P<float>(h->Dpart), pb.vec, h->stream));
-                CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts),
-                                    c, d, P<float>(h->mu), h->stream));
-                CK(launch_mu_norms(P<float>(h->mu), c, d, P<double>(h->mu_norm2),
-                                   P<float>(h->mu_normf), h->stream));
-                CK(zero_counters(h));
-                CK(launch_assign(RESPCA_F32, L, lds, d, n, nullptr, P<float>(h->mu),
-                                 P<float>(h->mu_normf), P<int32_t>(h->counts), c, p, ds, h->stream));
-                rs = read_status(h);
-                if (rs != RESPCA_OK) return rs;
-                ++passes;
-                out.lloyd_passes += 1;
-                out.assigned_columns += n;
-                out.rechecked_columns += h->hstat->rechecked;
-                if (h->hstat->changed == 0) break;
-            }
+            SearchCounts scount;
+            scount.passes = 1;
+            rs = lloyd_continue(h, kSumL, RESPCA_F32, L, lds, d, n, c, p, pb.vec, km, &scount);
+            if (rs != RESPCA_OK) return rs;
+            out.lloyd_passes += scount.passes - 1;
+            out.assigned_columns += scount.assigned;
+            out.rechecked_columns += scount.rechecked;
             // next centroids: D = X - S + Theta/rho_{t+1} under the final labels
             CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
                                   P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
             CK(launch_colsum(kSumD, dtype, X, ldx, nullptr, S, pb.Th, lds, sc.inv_rho_next,
                              P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart),
                              pb.vec, h->stream));
-            rs = finish_centroids(h, c, d);
+            rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
             if (rs != RESPCA_OK) return rs;
+            std::swap(h->mu, h->mu_next);
             CK(launch_count_changed(p, P<int32_t>(h->labels_prev), n, ds, h->stream));
         }
         rho = rho_next;
@@ -488,7 +582,9 @@ respca_status respca_destroy(respca_handle h) {
     DevBuf* bufs[] = {&h->theta, &h->mu, &h->mu_norm2, &h->mu_normf, &h->pair_ss, &h->sep2, &h->perm,
                       &h->counts, &h->tile_off, &h->tiles, &h->labels_prev, &h->Dpart, &h->own_part,
                       &h->norm_part, &h->flag_list, &h->seedD2, &h->centers, &h->seed_u, &h->fro_part,
-                      &h->status, &h->hX, &h->hL, &h->hS, &h->hp, &h->hp0};
+                      &h->status, &h->hX, &h->hL, &h->hS, &h->hp, &h->hp0, &h->mu_next, &h->mu_old,
+                      &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->labels_pass,
+                      &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->hstat) cudaFreeHost(h->hstat);

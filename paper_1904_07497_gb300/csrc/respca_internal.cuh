@@ -54,8 +54,13 @@ struct DevStatus {
     int32_t ntiles;         // tiles of the current sort
     int32_t bad_labels;     // labels outside [0, c)
     int32_t label_changes;  // running total of changed labels (vs. start of iteration)
+    int32_t moved;          // entries of the last moved-column list
+    int32_t timeout;        // a bounded device-side wait gave up
     int32_t pad;
 };
+
+// Modes of the bound-based pruning kernel.
+enum BoundsMode : int { kBoundsIter = 0, kBoundsLloyd = 1 };
 
 // Mode of the column-group sum kernel.
 enum SumMode : int { kSumX = 0, kSumL = 1, kSumD = 2 };
@@ -81,7 +86,26 @@ cudaError_t launch_colsum(int mode, int dtype, const void* X, int64_t ldx, const
                           cudaStream_t st);
 
 cudaError_t launch_centroids(const float* Dpart, const int32_t* tile_off, const int32_t* counts,
-                             int c, int64_t d, float* mu, cudaStream_t st);
+                             int c, int64_t d, float* mu, cudaStream_t st,
+                             double* sums_out = nullptr);
+
+cudaError_t launch_centroids_from_sums(const double* sums, const int32_t* counts, int c, int64_t d,
+                                       float* mu, cudaStream_t st);
+
+cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, const float* L,
+                              int64_t lds, const int4* moved, const DevStatus* status, int64_t d,
+                              double* sums, cudaStream_t st);
+
+cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t d,
+                            double* mu_norm2, float* mu_normf, double* drift, cudaStream_t st);
+
+cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_part, int nchunks,
+                               int64_t n, int c, const int32_t* labels, const int32_t* counts,
+                               const double* sep2, double safety, const double* drift, float* ub,
+                               float* lb, int32_t* flag_list, DevStatus* status, cudaStream_t st);
+
+cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int4* moved,
+                         int32_t* counts, DevStatus* status, cudaStream_t st);
 
 cudaError_t launch_mu_norms(const float* mu, int c, int64_t d, double* mu_norm2, float* mu_normf,
                             cudaStream_t st);
@@ -93,7 +117,7 @@ cudaError_t launch_iteration(int dtype, const void* X, int64_t ldx, float* L, fl
                              int64_t lds, const float* mu, const int32_t* perm,
                              const TileDesc* tiles, int max_tiles, const DevStatus* status,
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
-                             double* norm_part, bool vec, cudaStream_t st);
+                             float* dl_part, double* norm_part, bool vec, cudaStream_t st);
 
 cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchunks,
                                 DevStatus* status, cudaStream_t st);
@@ -105,7 +129,7 @@ cudaError_t launch_flag_columns(const float* own_part, int nchunks, int64_t n,
 cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
                           const int32_t* list, const float* mu, const float* mu_normf,
                           const int32_t* counts, int c, int32_t* labels, DevStatus* status,
-                          cudaStream_t st);
+                          cudaStream_t st, float* ub = nullptr, float* lb = nullptr);
 
 cudaError_t launch_count_changed(const int32_t* labels, const int32_t* prev, int64_t n,
                                  DevStatus* status, cudaStream_t st);
@@ -119,6 +143,20 @@ cudaError_t launch_seed_pick(const double* D2, int64_t n, const double* u, int k
 cudaError_t launch_gather_centers(int dtype, const void* X, int64_t ldx, int64_t d,
                                   const int32_t* centers, int c, float* mu, int32_t* counts,
                                   cudaStream_t st);
+
+// Tensor-core nearest-centroid search (k_search_tc.cu), used for c <= 256.
+constexpr int kTcMaxClusters = 256;
+int tc_npad(int c);
+int tc_splits(int64_t n, int64_t d);
+size_t tc_smem_bytes(int Npad);
+cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
+                            float* mu_lo, cudaStream_t st);
+cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
+                             const int32_t* list, DevStatus* status, const float* mu,
+                             const float* mu_hi, const float* mu_lo, int64_t dpad,
+                             const float* mu_normf, const int32_t* counts, int c, int32_t* labels,
+                             float* ub, float* lb, float* Gpart, float* ynorm_part,
+                             int32_t* tile_count, int32_t* rc_list, bool vec, cudaStream_t st);
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float warp_sum(float v) {

@@ -279,3 +279,41 @@ def test_batched_matches_single(solver):
     for q, s in zip(probs, singles):
         np.testing.assert_array_equal(q["p"].cpu().numpy(), s["p"])
         np.testing.assert_array_equal(_host(q["L"]), s["L"])
+
+
+# ------------------------------------------------------------------ search paths
+def _solve_impl(impl, X32, c, T, p0=None, seed=4, dtype=None):
+    from paper_1904_07497_gb300 import respca
+    s = respca.Solver(seed=seed, search_impl=impl)
+    X = _dev(X32, dtype)
+    res = s.solve(X, c, tol=0.0, max_iter=T, p0=None if p0 is None else torch.from_numpy(p0).cuda())
+    torch.cuda.synchronize()
+    out = (res.p.cpu().numpy(), _host(res.L), _host(res.S), res.stats)
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("d,n,c,T", [
+    (2048, 700, 50, 40),     # tensor-core search, several d splits
+    (333, 300, 20, 35),      # ragged d (scalar loads), partial 128-column tile
+    (512, 600, 256, 30),     # largest tensor-core centroid count
+    (256, 400, 257, 25),     # one above: the CUDA-core kernel
+])
+def test_search_paths_agree(d, n, c, T):
+    """The tensor-core search and the CUDA-core search both return the exact
+    argmin of the stored values, so whole solves agree bit for bit."""
+    pr = synth.lowrank_sparse(d, n, min(c, 40), 0.1, seed=d + c)
+    a = _solve_impl(0, pr.X, c, T)
+    b = _solve_impl(1, pr.X, c, T)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[2], b[2])
+    assert a[3]["lloyd_passes"] == b[3]["lloyd_passes"]
+
+
+def test_search_paths_agree_bf16_x():
+    pr = synth.lowrank_sparse(640, 500, 16, 0.1, seed=91)
+    a = _solve_impl(0, pr.X, 16, 30, dtype=torch.bfloat16)
+    b = _solve_impl(1, pr.X, 16, 30, dtype=torch.bfloat16)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
