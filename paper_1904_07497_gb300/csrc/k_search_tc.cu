@@ -2,24 +2,39 @@
 //
 // The p step of Sec. 4.2 (Eq. (21)-(22)) needs, for every searched column y_j,
 // the scores s_ij = ||mu_i||^2 - 2 mu_i . y_j over the c centroids: a
-// (columns x d) . (d x c) product.  k_search_tc computes it with
-// tcgen05.mma kind::tf32: A = 128 columns (M = 128, K-major: a column of Y is
-// contiguous along d), B = the centroids padded to Npad (K-major), the FP32
-// accumulator in tensor memory.  FP32 accuracy comes from the 3-term split
-// y = y_hi + y_lo, mu = mu_hi + mu_lo (hi = TF32-truncated):
+// (columns x d) . (d x c) product.  It runs on tcgen05.mma kind::tf32 with
+// A = 128 columns (M = 128, K-major: a column of Y is contiguous along d),
+// B = the centroids padded to Npad (K-major) and the FP32 accumulator in
+// tensor memory.  FP32 accuracy comes from the 3-term split y = y_hi + y_lo,
+// mu = mu_hi + mu_lo (hi = TF32-truncated):
 //   y.mu ~ y_hi.mu_hi + y_hi.mu_lo + y_lo.mu_hi       (error ~ 2^-20 relative).
-// The d dimension is split over gridDim.y CTAs; each writes its partial dot
-// products, and k_search_finalize adds them, forms the scores, takes the
-// argmin (ties to the lowest index), re-decides near ties in FP64 (through
-// k_search_recheck) and updates the labels and the pruning bounds.
+//
+// Two kernels feed the tensor cores:
+//  * k_search_dense (all columns, FP32 Y): stream-K over (column tile, 32-row
+//    slab) work, split evenly over one CTA per SM.  Warp 0 issues TMA loads
+//    (cp.async.bulk.tensor, 128-byte swizzle) into a ring of stages, warps 2-5
+//    split each Y tile into TF32 hi / lo parts in shared memory, one thread of
+//    warp 1 issues the MMAs into two ping-pong TMEM accumulators, and warps
+//    2-5 drain a finished accumulator to global partial sums.
+//  * k_search_list (a queued subset of columns, or any element type): threads
+//    gather the listed columns with plain loads, d split over gridDim.y.
+// In both, the last CTA to finish a column tile adds the partial products in
+// a fixed order, forms the scores, takes the argmin (ties to the lowest index)
+// and updates the labels and pruning bounds; near ties go to k_search_recheck,
+// which decides them with exact FP64 distances.
 //
 // Shared-memory operands use the canonical K-major 128-byte-swizzle layout:
 // 8-row groups of 1024 bytes, 128 bytes (32 FP32) per row, 16-byte chunk q of
 // row m stored at chunk q ^ (m % 8).  Every wait on an mbarrier is bounded; a
-// wait that gives up sets status->timeout and the kernel returns after
-// releasing its tensor memory.
+// wait that gives up sets status->timeout and the kernel drains its
+// asynchronous work (with bounded waits), releases its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <mutex>
 
 #include "respca_internal.cuh"
 
@@ -27,12 +42,14 @@ namespace respca {
 
 namespace {
 
-constexpr int kTcM = 128;             // columns per CTA (UMMA M)
+constexpr int kTcM = 128;             // columns per tile (UMMA M)
 constexpr int kTcK = 32;              // d rows per slab: one 128-byte swizzle atom of FP32
-constexpr int kTcStages = 2;
-constexpr int kTcThreads = 256;
+constexpr int kTcStages = 2;          // stages of the list kernel
+constexpr int kTcThreads = 256;       // threads of the list kernel
+constexpr int kDnThreads = 192;       // dense kernel: TMA warp, MMA warp, 4 split/epilogue warps
+constexpr int kDnMaxStages = 4;
 constexpr unsigned kSpinLimit = 1u << 22;
-constexpr float kTieRelTc = 6e-5f;    // bound on the score rounding, relative to ||y||^2 + ||mu||^2
+constexpr float kTieRelTc = 6e-5f;    // bound on the score rounding (see score_err)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -78,6 +95,35 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// Wait that also gives up as soon as another role of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
+                                                   volatile int* abort_flag) {
+    for (unsigned i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023u) == 1023u && *abort_flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar,
+                                            int32_t c0, int32_t c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -114,6 +160,17 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t cols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(dst)), "r"(cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols)
+                 : "memory");
+}
+
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // byte offset of 16-byte chunk q of row m in a K-major 128-byte-swizzle tile
@@ -127,6 +184,121 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, float4 v) {
                  : "memory");
 }
 
+__device__ __forceinline__ float4 ld_shared_v4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void named_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Score rounding bound of centroid i for a column y: e_i = kTieRelTc *
+// (2 ||mu_i|| ||y|| + ||mu_i||^2) (Cauchy-Schwarz on the products' error).
+__device__ __forceinline__ float score_err(float mu2, float y2) {
+    return kTieRelTc * (2.f * sqrtf(fmaxf(mu2, 0.f) * y2) + fabsf(mu2));
+}
+
+// Dot products g_i0 .. g_i0+7 of one column: sums over the nslots partial
+// products (slot-major [slot][Npad][128], column m), loads issued together.
+__device__ __forceinline__ void gather8(const float* __restrict__ gbase, int nslots, int Npad, int m,
+                                        int i0, int c, float* g) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) g[q] = 0.f;
+    for (int sl = 0; sl < nslots; ++sl) {
+        const float* b = gbase + ((int64_t)sl * Npad + i0) * kTcM + m;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = (i0 + q < c) ? __ldcg(b + (int64_t)q * kTcM) : 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) g[q] += v[q];
+    }
+}
+
+// Scores s_i = ||mu_i||^2 - 2 g_i of one column from its dot products g_i
+// (partial products summed in a fixed order), argmin with ties to the lowest
+// index, and the update of the label and the bounds; a near tie is queued
+// with its candidate set for the FP64 re-decision.
+__device__ void finalize_column(int64_t col, float y2, const float* __restrict__ gbase, int nslots,
+                                int Npad, int m, const float* __restrict__ mu_normf,
+                                const int32_t* __restrict__ counts, int c,
+                                int32_t* __restrict__ labels, float* __restrict__ ub,
+                                float* __restrict__ lb, DevStatus* __restrict__ status,
+                                RcRec* __restrict__ rc) {
+    float bs = INFINITY, ss = INFINITY, be = 0.f, se = 0.f;
+    int bi = INT_MAX, si = INT_MAX;
+    for (int i0 = 0; i0 < c; i0 += 8) {
+        float g[8];
+        gather8(gbase, nslots, Npad, m, i0, c, g);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = i0 + q;
+            if (i >= c || counts[i] == 0) continue;
+            const float mu2 = mu_normf[i];
+            const float sc = fmaf(-2.f, g[q], mu2);
+            if (sc < bs) {
+                ss = bs;
+                se = be;
+                si = bi;
+                bs = sc;
+                bi = i;
+                be = score_err(mu2, y2);
+            } else if (sc < ss) {
+                ss = sc;
+                si = i;
+                se = score_err(mu2, y2);
+            }
+        }
+    }
+    if (bi >= c) return;
+    if (ss - bs <= be + se) {
+        // candidates: every centroid whose score interval reaches the lowest upper end
+        float best_hi = INFINITY;
+        for (int i0 = 0; i0 < c; i0 += 8) {
+            float g[8];
+            gather8(gbase, nslots, Npad, m, i0, c, g);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q;
+                if (i >= c || counts[i] == 0) continue;
+                const float mu2 = mu_normf[i];
+                best_hi = fminf(best_hi, fmaf(-2.f, g[q], mu2) + score_err(mu2, y2));
+            }
+        }
+        const int slot = atomicAdd(&status->rechecked, 1);
+        RcRec* r = rc + slot;
+        for (int w = 0; w < kTcMaxClusters / 32; ++w) r->mask[w] = 0u;
+        for (int i0 = 0; i0 < c; i0 += 8) {
+            float g[8];
+            gather8(gbase, nslots, Npad, m, i0, c, g);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q;
+                if (i >= c || counts[i] == 0) continue;
+                const float mu2 = mu_normf[i];
+                if (fmaf(-2.f, g[q], mu2) - score_err(mu2, y2) <= best_hi) r->mask[i >> 5] |= 1u << (i & 31);
+            }
+        }
+        r->col = (int32_t)col;
+        return;
+    }
+    const float yerr = 1e-5f * y2;
+    const int32_t old = labels[col];
+    if (old != bi) {
+        labels[col] = bi;
+        atomicAdd(&status->changed, 1);
+    }
+    if (ub) {
+        ub[col] = sqrtf(fmaxf(bs + y2 + be + yerr, 0.f)) * (1.f + 1e-6f);
+        lb[col] = si < c ? sqrtf(fmaxf(ss + y2 - se - yerr, 0.f)) * (1.f - 1e-6f) : INFINITY;
+    }
+}
+
+// ============================================================== list kernel
 template <typename TY, bool VEC>
 __device__ __forceinline__ void load_col16(const TY* __restrict__ colp, int64_t r0, int64_t d,
                                            float4* v) {
@@ -149,30 +321,25 @@ __device__ __forceinline__ void load_col16(const TY* __restrict__ colp, int64_t 
     }
 }
 
-// Score rounding bound of centroid i for a column y: e_i = kTieRelTc *
-// (2 ||mu_i|| ||y|| + ||mu_i||^2) (Cauchy-Schwarz on the products' error).
-__device__ __forceinline__ float score_err(float mu2, float y2) {
-    return kTieRelTc * (2.f * sqrtf(fmaxf(mu2, 0.f) * y2) + fabsf(mu2));
-}
-
 constexpr int kTcBMax = 4;   // prefetched 16-byte chunks of each centroid half per thread
 
 template <typename TY, bool VEC>
 __global__ void __launch_bounds__(kTcThreads, 2)
-    k_search_tc(const TY* __restrict__ Y, int64_t ldy, int64_t d, int64_t n,
-                const int32_t* __restrict__ list, DevStatus* __restrict__ status,
-                const float* __restrict__ mu_hi, const float* __restrict__ mu_lo, int64_t dpad,
-                int Npad, int slabs_per_split, int nsplit, const float* __restrict__ mu_normf,
-                const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
-                float* __restrict__ ub, float* __restrict__ lb, float* __restrict__ Gpart,
-                float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
-                int32_t* __restrict__ rc_list) {
+    k_search_list(const TY* __restrict__ Y, int64_t ldy, int64_t d, int64_t n,
+                  const int32_t* __restrict__ list, int64_t list_max, DevStatus* __restrict__ status,
+                  const float* __restrict__ mu_hi, const float* __restrict__ mu_lo, int64_t dpad,
+                  int Npad, int slabs_per_split, int nsplit, const float* __restrict__ mu_normf,
+                  const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
+                  float* __restrict__ ub, float* __restrict__ lb, float* __restrict__ Gpart,
+                  float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
+                  RcRec* __restrict__ rc_list) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t mbar[kTcStages];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int is_last_sh;
 
     const int64_t total = list ? (int64_t)status->flagged : n;
+    if (list && total > list_max) return;   // the dense kernel searches every column instead
     const int64_t tile0 = (int64_t)blockIdx.x * kTcM;
     if (tile0 >= total) return;
     const int64_t nslabs = (d + kTcK - 1) / kTcK;
@@ -182,7 +349,6 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    // 1024-byte aligned operand tiles
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t a_bytes = kTcM * 128;
@@ -196,9 +362,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     uint32_t tmem_cols = 32;
     while ((int)tmem_cols < Npad) tmem_cols <<= 1;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&tmem_base_sh)), "r"(tmem_cols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tmem_alloc(&tmem_base_sh, tmem_cols);
         tc_fence_before();
     }
     if (tid == 0) {
@@ -217,9 +381,8 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const int64_t col = list ? (int64_t)list[pos] : pos;
         colp = Y + col * ldy;
     }
-    // B mapping: 16-byte chunks e = tid + j * 256 of the Npad x 32 centroid slab
     const int bchunks = Npad * 8;
-    const int bmine = (bchunks - tid + kTcThreads - 1) / kTcThreads;   // chunks of this thread
+    const int bmine = (bchunks - tid + kTcThreads - 1) / kTcThreads;
     const uint32_t idesc = idesc_tf32(kTcM, Npad);
 
     float4 av[4], bh[kTcBMax], bl[kTcBMax];
@@ -243,14 +406,12 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const int st = q & 1;
         const int64_t k0 = (s_begin + q) * kTcK;
         if (q >= kTcStages) {
-            // the MMAs that read this stage two slabs ago must have finished
             if (!mbar_wait(&mbar[st], (uint32_t)(((q - kTcStages) >> 1) & 1))) failed = true;
         }
         if (__syncthreads_or(failed)) {
             failed = true;
             break;
         }
-        // A: split into TF32 hi / lo parts, store swizzled; ||y||^2 with Kahan
         {
             float part = 0.f;
 #pragma unroll
@@ -263,12 +424,11 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 st_shared_v4(a_lo(st) + off, lo);
                 part = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, part))));
             }
-            const float y = part - ycomp;
+            const float y = part - ycomp;   // Kahan accumulation of ||y_j||^2
             const float t = ysq + y;
             ycomp = (t - ysq) - y;
             ysq = t;
         }
-        // B: centroid hi / lo slabs (split and zero-padded to Npad x dpad beforehand)
 #pragma unroll
         for (int j = 0; j < kTcBMax; ++j) {
             if (j < bmine) {
@@ -284,7 +444,6 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             st_shared_v4(b_hi(st) + off, __ldg(reinterpret_cast<const float4*>(mu_hi + g)));
             st_shared_v4(b_lo(st) + off, __ldg(reinterpret_cast<const float4*>(mu_lo + g)));
         }
-        // prefetch the next slab while the tensor cores work on this one
         if (q + 1 < nq) {
             load_col16<TY, VEC>(colp, k0 + kTcK + h * 16, d, av);
             load_b(k0 + kTcK);
@@ -306,19 +465,16 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         }
     }
 
-    // wait for the last commit (it covers every MMA issued before it)
     {
         const int ql = failed ? -1 : nq - 1;
         if (ql >= 0) {
             if (!mbar_wait(&mbar[ql & 1], (uint32_t)((ql >> 1) & 1))) failed = true;
         } else {
-            // a wait gave up: give the tensor cores one more bounded chance to drain
             for (int s = 0; s < kTcStages; ++s) mbar_wait(&mbar[s], 0u);
         }
     }
     failed = __syncthreads_or(failed);
     tc_fence_after();
-    // this split's partial dot products -> Gpart[tile][split][Npad][128]
     float* gtile = Gpart + ((int64_t)blockIdx.x * nsplit + blockIdx.y) * (int64_t)Npad * kTcM;
     if (!failed && warp < 4) {
         const int mm = warp * 32 + lane;
@@ -337,11 +493,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     tc_fence_before();
     __threadfence();
     __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
-                     : "memory");
-    }
-    // the last split CTA of this column tile finishes the search for it
+    if (warp == 0) tmem_dealloc(tmem, tmem_cols);
     if (tid == 0) {
         const int prev = atomicAdd(&tile_count[blockIdx.x], 1);
         is_last_sh = (prev == nsplit - 1);
@@ -358,126 +510,328 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     const float* yt0 = ynorm_part + (int64_t)blockIdx.x * nsplit * kTcM;
     float y2 = 0.f;
     for (int s = 0; s < nsplit; ++s) y2 += __ldcg(yt0 + (int64_t)s * kTcM + tid);
-    float bs = INFINITY, ss = INFINITY, be = 0.f, se = 0.f;
-    int bi = INT_MAX, si = INT_MAX;
-    for (int i = 0; i < c; ++i) {
-        if (counts[i] == 0) continue;
-        float g = 0.f;
-        for (int s = 0; s < nsplit; ++s) g += __ldcg(gt0 + ((int64_t)s * Npad + i) * kTcM + tid);
-        const float mu2 = mu_normf[i];
-        const float sc = fmaf(-2.f, g, mu2);
-        if (sc < bs) {
-            ss = bs;
-            se = be;
-            si = bi;
-            bs = sc;
-            bi = i;
-            be = score_err(mu2, y2);
-        } else if (sc < ss) {
-            ss = sc;
-            si = i;
-            se = score_err(mu2, y2);
-        }
-    }
-    if (bi >= c) return;
-    const float yerr = 1e-5f * y2;
-    if (ss - bs <= be + se) {   // near tie: FP64 re-decision
-        const int slot = atomicAdd(&status->rechecked, 1);
-        rc_list[slot] = (int32_t)p;
-        return;
-    }
-    const int32_t old = labels[col];
-    if (old != bi) {
-        labels[col] = bi;
-        atomicAdd(&status->changed, 1);
-    }
-    if (ub) {
-        ub[col] = sqrtf(fmaxf(bs + y2 + be + yerr, 0.f)) * (1.f + 1e-6f);
-        lb[col] = si < c ? sqrtf(fmaxf(ss + y2 - se - yerr, 0.f)) * (1.f - 1e-6f) : INFINITY;
-    }
+    finalize_column(col, y2, gt0, nsplit, Npad, tid, mu_normf, counts, c, labels, ub, lb, status,
+                    rc_list);
 }
 
+// ============================================================== dense kernel
+// Stream-K split of the (tile, slab) work: CTA b owns [w0(b), w0(b+1)),
+// w0(b) = b W / G, W = tiles * slabs.  owner(w) is the CTA whose range holds w.
+__host__ __device__ __forceinline__ int64_t sk_begin(int64_t b, int64_t W, int64_t G) {
+    return (b * W) / G;
+}
+__host__ __device__ __forceinline__ int64_t sk_owner(int64_t w, int64_t W, int64_t G) {
+    return ((w + 1) * G - 1) / W;
+}
+
+struct DenseArgs {
+    int64_t d, n, Q, T, W;   // rows, columns, slabs per tile, tiles, total work
+    int Npad, stages, cmax;
+    int use_list;            // 1: a queued list was asked for (run only if it is long)
+    int64_t list_min;
+};
+
+__global__ void __launch_bounds__(kDnThreads, 1)
+    k_search_dense(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmBh,
+                   const __grid_constant__ CUtensorMap tmBl, DenseArgs a,
+                   DevStatus* __restrict__ status, const float* __restrict__ mu_normf,
+                   const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
+                   float* __restrict__ ub, float* __restrict__ lb, float* __restrict__ Gpart,
+                   float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
+                   RcRec* __restrict__ rc_list) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full[kDnMaxStages], conv[kDnMaxStages], empty[kDnMaxStages];
+    __shared__ uint64_t acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+    __shared__ int is_last_sh;
+
+    if (a.use_list && (int64_t)status->flagged < a.list_min) return;   // the list kernel handles it
+    const int64_t G = gridDim.x, b = blockIdx.x;
+    const int64_t w0 = sk_begin(b, a.W, G), w1 = sk_begin(b + 1, a.W, G);
+    if (w0 >= w1) return;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int S = a.stages;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t a_bytes = kTcM * 128;
+    const uint32_t b_bytes = (uint32_t)a.Npad * 128;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    auto sA = [&](int s) { return base + s * stage_bytes; };              // raw, then hi
+    auto sAlo = [&](int s) { return base + s * stage_bytes + a_bytes; };
+    auto sBh = [&](int s) { return base + s * stage_bytes + 2 * a_bytes; };
+    auto sBl = [&](int s) { return base + s * stage_bytes + 2 * a_bytes + b_bytes; };
+    const uint32_t tx_bytes = a_bytes + 2 * b_bytes;
+
+    uint32_t tmem_cols = 32;
+    while ((int)tmem_cols < 2 * a.Npad) tmem_cols <<= 1;
+    if (warp == 1) {
+        tmem_alloc(&tmem_base_sh, tmem_cols);
+        tc_fence_before();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], 4);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], 4);
+        }
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int64_t k = 0;
+            for (int64_t w = w0; w < w1; ++w, ++k) {
+                const int st = (int)(k % S);
+                const int64_t u = k / S;
+                if (u > 0 && !mbar_wait_or_abort(&empty[st], (uint32_t)((u - 1) & 1), &abort_sh)) {
+                    abort_sh = 1;
+                    break;
+                }
+                const int64_t tile = w / a.Q, s = w % a.Q;
+                mbar_expect_tx(&full[st], tx_bytes);
+                tma_load_2d(sA(st), &tmY, &full[st], (int32_t)(s * kTcK), (int32_t)(tile * kTcM));
+                tma_load_2d(sBh(st), &tmBh, &full[st], (int32_t)(s * kTcK), 0);
+                tma_load_2d(sBl(st), &tmBl, &full[st], (int32_t)(s * kTcK), 0);
+            }
+            // make sure no copy is still in flight when the CTA leaves
+            const int64_t issued = k;
+            for (int64_t j = (issued > S ? issued - S : 0); j < issued; ++j)
+                mbar_wait(&full[j % S], (uint32_t)((j / S) & 1));
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(kTcM, a.Npad);
+            int64_t k = 0, g = 0;
+            bool issued_any = false;
+            int last_empty = 0;
+            int64_t last_use = 0;
+            for (int64_t w = w0; w < w1; ++w, ++k) {
+                const int st = (int)(k % S);
+                const int64_t u = k / S;
+                const int64_t s = w % a.Q;
+                const bool seg_start = (w == w0) || (s == 0);
+                const bool seg_end = (w == w1 - 1) || (s == a.Q - 1);
+                const int bsel = (int)(g & 1);
+                if (seg_start && (g >> 1) > 0 &&
+                    !mbar_wait_or_abort(&acc_empty[bsel], (uint32_t)(((g >> 1) - 1) & 1), &abort_sh)) {
+                    abort_sh = 1;
+                    break;
+                }
+                if (!mbar_wait_or_abort(&conv[st], (uint32_t)(u & 1), &abort_sh)) {
+                    abort_sh = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(bsel * a.Npad);
+#pragma unroll
+                for (int ks = 0; ks < kTcK / 8; ++ks) {
+                    const uint32_t koff = ks * 32;
+                    const uint64_t dah = sw128_desc(sA(st) + koff), dal = sw128_desc(sAlo(st) + koff);
+                    const uint64_t dbh = sw128_desc(sBh(st) + koff), dbl = sw128_desc(sBl(st) + koff);
+                    tc_mma(acc, dah, dbh, idesc, (seg_start && ks == 0) ? 0u : 1u);
+                    tc_mma(acc, dah, dbl, idesc, 1u);
+                    tc_mma(acc, dal, dbh, idesc, 1u);
+                }
+                tc_commit(&empty[st]);
+                issued_any = true;
+                last_empty = st;
+                last_use = u;
+                if (seg_end) {
+                    tc_commit(&acc_full[bsel]);
+                    ++g;
+                }
+            }
+            // drain: the last commit covers every MMA issued before it
+            if (issued_any) mbar_wait(&empty[last_empty], (uint32_t)(last_use & 1));
+        }
+    } else {
+        // ---------------- TF32 split + epilogue (warps 2-5; row m = TMEM lane)
+        const int m = 32 * (warp & 3) + lane;
+        const int et = tid - 64;   // 0..127
+        int64_t k = 0, g = 0;
+        float ysq = 0.f, ycomp = 0.f;
+        for (int64_t w = w0; w < w1; ++w, ++k) {
+            const int st = (int)(k % S);
+            const int64_t u = k / S;
+            const int64_t tile = w / a.Q, s = w % a.Q;
+            const bool seg_start = (w == w0) || (s == 0);
+            const bool seg_end = (w == w1 - 1) || (s == a.Q - 1);
+            if (seg_start) ysq = ycomp = 0.f;
+            if (!mbar_wait_or_abort(&full[st], (uint32_t)(u & 1), &abort_sh)) {
+                abort_sh = 1;
+                break;
+            }
+            float part = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t off = sw128_off(m, q);
+                const float4 x = ld_shared_v4(sA(st) + off);
+                const float4 hi = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                st_shared_v4(sA(st) + off, hi);
+                st_shared_v4(sAlo(st) + off, make_float4(x.x - hi.x, x.y - hi.y, x.z - hi.z, x.w - hi.w));
+                part = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, part))));
+            }
+            {
+                const float y = part - ycomp;   // Kahan accumulation of ||y_j||^2
+                const float t = ysq + y;
+                ycomp = (t - ysq) - y;
+                ysq = t;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&conv[st]);
+            if (!seg_end) continue;
+
+            // a column tile segment is finished: drain its accumulator
+            const int bsel = (int)(g & 1);
+            if (!mbar_wait_or_abort(&acc_full[bsel], (uint32_t)((g >> 1) & 1), &abort_sh)) {
+                abort_sh = 1;
+                break;
+            }
+            tc_fence_after();
+            const int64_t bfirst = sk_owner(tile * a.Q, a.W, G);
+            const int64_t blast = sk_owner((tile + 1) * a.Q - 1, a.W, G);
+            const int slot = (int)(b - bfirst);
+            const int ncontrib = (int)(blast - bfirst + 1);
+            float* gslot = Gpart + ((int64_t)tile * a.cmax + slot) * (int64_t)a.Npad * kTcM;
+            for (int cb = 0; cb < a.Npad; cb += 16) {
+                float v[16];
+                tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(bsel * a.Npad + cb), v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) gslot[(int64_t)(cb + q) * kTcM + m] = v[q];
+            }
+            ynorm_part[((int64_t)tile * a.cmax + slot) * kTcM + m] = ysq;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[bsel]);
+            ++g;
+            __threadfence();
+            named_sync(1, 128);
+            if (et == 0) {
+                const int prev = atomicAdd(&tile_count[tile], 1);
+                is_last_sh = (prev == ncontrib - 1);
+            }
+            named_sync(1, 128);
+            const bool last = is_last_sh != 0;
+            named_sync(1, 128);
+            if (!last) continue;
+            __threadfence();
+            if (et == 0) tile_count[tile] = 0;
+            const int64_t p = tile * kTcM + m;
+            if (p < a.n) {
+                const float* gt0 = Gpart + (int64_t)tile * a.cmax * (int64_t)a.Npad * kTcM;
+                const float* yt0 = ynorm_part + (int64_t)tile * a.cmax * kTcM;
+                float y2 = 0.f;
+                for (int sl = 0; sl < ncontrib; ++sl) y2 += __ldcg(yt0 + (int64_t)sl * kTcM + m);
+                finalize_column(p, y2, gt0, ncontrib, a.Npad, m, mu_normf, counts, c, labels, ub, lb,
+                                status, rc_list);
+            }
+        }
+    }
+    __syncthreads();
+    if (abort_sh && tid == 0) atomicOr(&status->timeout, 1);
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, tmem_cols);
+}
+
+// ============================================================== FP64 recheck
 // Exact squared distance ||y - mu_i||^2 in FP64 by a whole CTA (the FP32
-// inputs convert exactly; four independent accumulators per thread).
+// inputs convert exactly).  With 16-byte aligned rows every thread issues
+// all of its loads before the arithmetic (d <= 16384 per pass of 4 float4).
 template <typename TY>
 __device__ double block_dist2_fp64(const TY* __restrict__ y, const float* __restrict__ mrow,
-                                   int64_t d, double* red) {
+                                   int64_t d, bool vec, double* red) {
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int64_t r = threadIdx.x;
-    for (; r + 3 * kThreads < d; r += 4 * kThreads) {
-        const double e0 = (double)XLoad<TY>::one(y + r) - (double)mrow[r];
-        const double e1 = (double)XLoad<TY>::one(y + r + kThreads) - (double)mrow[r + kThreads];
-        const double e2 = (double)XLoad<TY>::one(y + r + 2 * kThreads) - (double)mrow[r + 2 * kThreads];
-        const double e3 = (double)XLoad<TY>::one(y + r + 3 * kThreads) - (double)mrow[r + 3 * kThreads];
-        a0 = fma(e0, e0, a0);
-        a1 = fma(e1, e1, a1);
-        a2 = fma(e2, e2, a2);
-        a3 = fma(e3, e3, a3);
-    }
-    for (; r < d; r += kThreads) {
-        const double e0 = (double)XLoad<TY>::one(y + r) - (double)mrow[r];
-        a0 = fma(e0, e0, a0);
-    }
-    double a = warp_sum((a0 + a1) + (a2 + a3));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
-    __syncthreads();
-    double t = 0.0;
+    if (vec && sizeof(TY) == 4) {
+        const float4* y4 = reinterpret_cast<const float4*>(y);
+        const float4* m4 = reinterpret_cast<const float4*>(mrow);
+        const int64_t d4 = d / 4;
+        for (int64_t b0 = threadIdx.x; b0 < d4; b0 += 4 * kThreads) {
+            float4 yv[4], mv[4];
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
-    return t;
+            for (int u = 0; u < 4; ++u) {
+                const int64_t j = b0 + u * kThreads;
+                yv[u] = j < d4 ? __ldg(y4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                mv[u] = j < d4 ? __ldg(m4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double e0 = (double)yv[u].x - (double)mv[u].x;
+                const double e1 = (double)yv[u].y - (double)mv[u].y;
+                const double e2 = (double)yv[u].z - (double)mv[u].z;
+                const double e3 = (double)yv[u].w - (double)mv[u].w;
+                a0 = fma(e0, e0, a0);
+                a1 = fma(e1, e1, a1);
+                a2 = fma(e2, e2, a2);
+                a3 = fma(e3, e3, a3);
+            }
+        }
+        for (int64_t r = d4 * 4 + threadIdx.x; r < d; r += kThreads) {
+            const double e0 = (double)XLoad<TY>::one(y + r) - (double)mrow[r];
+            a0 = fma(e0, e0, a0);
+        }
+    } else {
+        int64_t r = threadIdx.x;
+        for (; r + 3 * kThreads < d; r += 4 * kThreads) {
+            const double e0 = (double)XLoad<TY>::one(y + r) - (double)mrow[r];
+            const double e1 = (double)XLoad<TY>::one(y + r + kThreads) - (double)mrow[r + kThreads];
+            const double e2 = (double)XLoad<TY>::one(y + r + 2 * kThreads) - (double)mrow[r + 2 * kThreads];
+            const double e3 = (double)XLoad<TY>::one(y + r + 3 * kThreads) - (double)mrow[r + 3 * kThreads];
+            a0 = fma(e0, e0, a0);
+            a1 = fma(e1, e1, a1);
+            a2 = fma(e2, e2, a2);
+            a3 = fma(e3, e3, a3);
+        }
+        for (; r < d; r += kThreads) {
+            const double e0 = (double)XLoad<TY>::one(y + r) - (double)mrow[r];
+            a0 = fma(e0, e0, a0);
+        }
+    }
+    double t = warp_sum((a0 + a1) + (a2 + a3));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    return s;
 }
 
-// FP64 re-decision of near ties (one CTA per queued column): every centroid
-// whose score interval can reach the best one gets its exact squared distance.
+// FP64 re-decision of near ties, one CTA per queued column, over the queued
+// candidate set (in increasing index, so ties keep the lowest).
 template <typename TY>
 __global__ void __launch_bounds__(kThreads)
-    k_search_recheck(const TY* __restrict__ Y, int64_t ldy, int64_t d, int64_t n,
-                     const int32_t* __restrict__ list, DevStatus* __restrict__ status,
-                     const float* __restrict__ Gpart, const float* __restrict__ ynorm_part,
-                     int nsplit, int Npad, const float* __restrict__ mu,
-                     const float* __restrict__ mu_normf, const int32_t* __restrict__ counts, int c,
-                     int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
-                     const int32_t* __restrict__ rc_list) {
+    k_search_recheck(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
+                     DevStatus* __restrict__ status, const float* __restrict__ mu, int c,
+                     int32_t* __restrict__ labels,
+                     float* __restrict__ ub, float* __restrict__ lb,
+                     const RcRec* __restrict__ rc_list) {
     __shared__ double red[kThreads / 32];
-    __shared__ float fred[kThreads / 32];
-    __shared__ uint8_t cand[kTcMaxClusters];
     const int nrc = status->rechecked;
     for (int64_t k = blockIdx.x; k < nrc; k += gridDim.x) {
-        const int64_t p = rc_list[k];
-        const int64_t col = list ? (int64_t)list[p] : p;
-        const int64_t tile = p / kTcM, mm = p % kTcM;
-        const float* gt0 = Gpart + tile * nsplit * (int64_t)Npad * kTcM;
-        float y2 = 0.f;
-        for (int s = 0; s < nsplit; ++s) y2 += ynorm_part[(tile * nsplit + s) * kTcM + mm];
-        float sc = INFINITY, er = 0.f;
-        const int i = threadIdx.x;   // c <= 256 = blockDim.x
-        if (i < c && counts[i] > 0) {
-            float g = 0.f;
-            for (int s = 0; s < nsplit; ++s) g += gt0[((int64_t)s * Npad + i) * kTcM + mm];
-            sc = fmaf(-2.f, g, mu_normf[i]);
-            er = score_err(mu_normf[i], y2);
-        }
-        // lowest upper end of the score intervals
-        float hi = sc + er;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) hi = fminf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) fred[threadIdx.x >> 5] = hi;
-        __syncthreads();
-        float best_hi = INFINITY;
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) best_hi = fminf(best_hi, fred[w]);
-        if (i < c) cand[i] = (sc - er <= best_hi) ? 1 : 0;
-        __syncthreads();
+        const RcRec& rec = rc_list[k];
+        const int64_t col = rec.col;
         double best = INFINITY;
         int besti = INT_MAX;
         const TY* y = Y + col * ldy;
-        for (int ci = 0; ci < c; ++ci) {   // candidates in increasing index: ties keep the lowest
-            if (!cand[ci]) continue;
-            const double a = block_dist2_fp64<TY>(y, mu + (int64_t)ci * d, d, red);
-            if (a < best) {
-                best = a;
+        for (int ci = 0; ci < c; ++ci) {
+            if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
+            const double dist = block_dist2_fp64<TY>(y, mu + (int64_t)ci * d, d, vec, red);
+            if (dist < best) {
+                best = dist;
                 besti = ci;
             }
         }
@@ -512,17 +866,9 @@ __global__ void __launch_bounds__(kThreads)
 
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
 
-}  // namespace
-
-int tc_npad(int c) { return ((c + 15) / 16) * 16; }
-
-size_t tc_smem_bytes(int Npad) {
-    return (size_t)kTcStages * (2 * kTcM * 128 + 2 * (size_t)Npad * 128) + 1024;
-}
-
-// Number of d-splits: about two CTAs per SM in total, every split non-empty
-// (the split count is derived back from the slabs per split).
-static int64_t tc_slabs_per_split(int64_t n, int64_t d) {
+// Number of d-splits of the list kernel: about two CTAs per SM in total,
+// every split non-empty (the split count is derived back from the slabs per split).
+int64_t tc_slabs_per_split(int64_t n, int64_t d) {
     const int64_t tiles = (n + kTcM - 1) / kTcM;
     const int64_t nslabs = (d + kTcK - 1) / kTcK;
     int64_t s = (2 * 152) / (tiles > 0 ? tiles : 1);
@@ -532,10 +878,91 @@ static int64_t tc_slabs_per_split(int64_t n, int64_t d) {
     return (nslabs + s - 1) / s;
 }
 
-int tc_splits(int64_t n, int64_t d) {
+int tc_list_splits(int64_t n, int64_t d) {
     const int64_t nslabs = (d + kTcK - 1) / kTcK;
     const int64_t per = tc_slabs_per_split(n, d);
     return (int)((nslabs + per - 1) / per);
+}
+
+int g_num_sms = 0;
+std::mutex g_init_mutex;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int num_sms() {
+    std::lock_guard<std::mutex> lock(g_init_mutex);
+    if (g_num_sms == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        g_num_sms = v;
+    }
+    return g_num_sms;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    std::lock_guard<std::mutex> lock(g_init_mutex);
+    if (!g_encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    return g_encode;
+}
+
+bool encode_2d(CUtensorMap* map, const float* ptr, int64_t inner, int64_t outer, int64_t ld,
+               uint32_t box_inner, uint32_t box_outer) {
+    auto enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct DensePlan {
+    int stages;
+    int64_t Q, T, W;
+    int G, cmax;
+    size_t smem;
+};
+
+DensePlan dense_plan(int64_t n, int64_t d, int Npad) {
+    DensePlan p;
+    const size_t stage_bytes = 2 * kTcM * 128 + 2 * (size_t)Npad * 128;
+    p.stages = (int)std::min<size_t>(kDnMaxStages, (200 * 1024) / stage_bytes);
+    p.Q = (d + kTcK - 1) / kTcK;
+    p.T = (n + kTcM - 1) / kTcM;
+    p.W = p.Q * p.T;
+    p.G = (int)std::min<int64_t>(num_sms(), p.W);
+    p.cmax = 1;
+    for (int64_t t = 0; t < p.T; ++t) {
+        const int64_t nc = sk_owner((t + 1) * p.Q - 1, p.W, p.G) - sk_owner(t * p.Q, p.W, p.G) + 1;
+        if (nc > p.cmax) p.cmax = (int)nc;
+    }
+    p.smem = (size_t)p.stages * stage_bytes + 1024;
+    return p;
+}
+
+}  // namespace
+
+int tc_npad(int c) { return ((c + 15) / 16) * 16; }
+
+TcPlan tc_plan(int64_t n, int64_t d, int c) {
+    TcPlan t;
+    t.Npad = tc_npad(c);
+    t.dpad = (d + 31) / 32 * 32;
+    t.tiles = (n + kTcM - 1) / kTcM;
+    const DensePlan dp = dense_plan(n, d, t.Npad);
+    const int64_t slots = std::max<int64_t>(tc_list_splits(n, d), dp.cmax);
+    t.gpart = (size_t)slots * t.Npad * t.tiles * kTcM;
+    t.ynorm = (size_t)slots * t.tiles * kTcM;
+    return t;
 }
 
 cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
@@ -551,27 +978,68 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              const float* mu_hi, const float* mu_lo, int64_t dpad,
                              const float* mu_normf, const int32_t* counts, int c, int32_t* labels,
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
-                             int32_t* tile_count, int32_t* rc_list, bool vec, cudaStream_t st) {
+                             int32_t* tile_count, RcRec* rc_list, bool vec, cudaStream_t st) {
     const int Npad = tc_npad(c);
-    const int nsplit = tc_splits(n, d);
-    const int per = (int)tc_slabs_per_split(n, d);
-    const size_t smem = tc_smem_bytes(Npad);
-    const dim3 grid((unsigned)((n + kTcM - 1) / kTcM), (unsigned)nsplit);
     cudaError_t e = cudaSuccess;
-    count_launches(2);
-    RESPCA_DISPATCH_X(dtype, TY, {
-        auto kern = vec ? k_search_tc<TY, true> : k_search_tc<TY, false>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) {
-            kern<<<grid, kTcThreads, smem, st>>>((const TY*)Y, ldy, d, n, list, status, mu_hi, mu_lo,
-                                                 dpad, Npad, per, nsplit, mu_normf, counts, c, labels,
-                                                 ub, lb, Gpart, ynorm_part, tile_count, rc_list);
-            k_search_recheck<TY><<<152, kThreads, 0, st>>>(
-                (const TY*)Y, ldy, d, n, list, status, Gpart, ynorm_part, nsplit, Npad, mu, mu_normf,
-                counts, c, labels, ub, lb, rc_list);
+    // dense TMA path: FP32 operand with 16-byte aligned columns
+    const bool dense_ok = dtype == 0 && vec && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
+                          ldy % 4 == 0 && (reinterpret_cast<uintptr_t>(mu_hi) % 16 == 0) &&
+                          (reinterpret_cast<uintptr_t>(mu_lo) % 16 == 0);
+    const int64_t list_max = n / 4;   // larger queued lists use the dense kernel
+    bool dense_launched = false;
+    if (dense_ok) {
+        CUtensorMap tmY, tmBh, tmBl;
+        const DensePlan dp = dense_plan(n, d, Npad);
+        if (encode_2d(&tmY, static_cast<const float*>(Y), d, n, ldy, kTcK, kTcM) &&
+            encode_2d(&tmBh, mu_hi, dpad, Npad, dpad, kTcK, (uint32_t)Npad) &&
+            encode_2d(&tmBl, mu_lo, dpad, Npad, dpad, kTcK, (uint32_t)Npad)) {
+            DenseArgs a;
+            a.d = d;
+            a.n = n;
+            a.Q = dp.Q;
+            a.T = dp.T;
+            a.W = dp.W;
+            a.Npad = Npad;
+            a.stages = dp.stages;
+            a.cmax = dp.cmax;
+            a.use_list = list ? 1 : 0;
+            a.list_min = list_max + 1;
+            e = cudaFuncSetAttribute(k_search_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dp.smem);
+            if (e != cudaSuccess) return e;
+            count_launches(1);
+            k_search_dense<<<dp.G, kDnThreads, dp.smem, st>>>(tmY, tmBh, tmBl, a, status, mu_normf,
+                                                              counts, c, labels, ub, lb, Gpart,
+                                                              ynorm_part, tile_count, rc_list);
+            dense_launched = true;
         }
+    }
+    if (!dense_launched || list) {
+        const int nsplit = tc_list_splits(n, d);
+        const int per = (int)tc_slabs_per_split(n, d);
+        const size_t smem = (size_t)kTcStages * (2 * kTcM * 128 + 2 * (size_t)Npad * 128) + 1024;
+        const dim3 grid((unsigned)((n + kTcM - 1) / kTcM), (unsigned)nsplit);
+        const int64_t lmax = dense_launched ? list_max : n;
+        count_launches(1);
+        RESPCA_DISPATCH_X(dtype, TY, {
+            auto kern = vec ? k_search_list<TY, true> : k_search_list<TY, false>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                kern<<<grid, kTcThreads, smem, st>>>((const TY*)Y, ldy, d, n, list, lmax, status, mu_hi,
+                                                     mu_lo, dpad, Npad, per, nsplit, mu_normf, counts,
+                                                     c, labels, ub, lb, Gpart, ynorm_part, tile_count,
+                                                     rc_list);
+        });
+        if (e != cudaSuccess) return e;
+    }
+    count_launches(1);
+    RESPCA_DISPATCH_X(dtype, TY, {
+        // float4 rows need 16-byte aligned columns of Y and of the centroids (d % 4 == 0)
+        const bool v4 = vec && sizeof(TY) == 4 && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
+                        (reinterpret_cast<uintptr_t>(mu) % 16 == 0);
+        k_search_recheck<TY><<<num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu, c,
+                                                             labels, ub, lb, rc_list);
     });
-    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -136,18 +136,16 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
     CK(ensure(h->moved, sizeof(int4) * n));
     CK(ensure(h->labels_pass, sizeof(int32_t) * n));
     if (c <= kTcMaxClusters) {
-        const int Npad = tc_npad(c);
-        const int64_t dpad = (d + 31) / 32 * 32;
-        CK(ensure(h->mu_hi, sizeof(float) * (size_t)Npad * dpad));
-        CK(ensure(h->mu_lo, sizeof(float) * (size_t)Npad * dpad));
-        const int64_t ntile = (n + 127) / 128;
-        CK(ensure(h->Gpart, sizeof(float) * (size_t)tc_splits(n, d) * Npad * ntile * 128));
-        CK(ensure(h->ynorm_part, sizeof(float) * (size_t)tc_splits(n, d) * ntile * 128));
-        const bool fresh = h->tile_count.bytes < sizeof(int32_t) * (size_t)ntile;
-        CK(ensure(h->tile_count, sizeof(int32_t) * ntile));
-        if (fresh) CK(cudaMemsetAsync(h->tile_count.p, 0, h->tile_count.bytes, h->stream));
+        const TcPlan tp = tc_plan(n, d, c);
+        CK(ensure(h->mu_hi, sizeof(float) * (size_t)tp.Npad * tp.dpad));
+        CK(ensure(h->mu_lo, sizeof(float) * (size_t)tp.Npad * tp.dpad));
+        CK(ensure(h->Gpart, sizeof(float) * tp.gpart));
+        CK(ensure(h->ynorm_part, sizeof(float) * tp.ynorm));
+        CK(ensure(h->tile_count, sizeof(int32_t) * tp.tiles));
+        // per-tile arrival counters of the search kernels start every call at zero
+        CK(cudaMemsetAsync(h->tile_count.p, 0, h->tile_count.bytes, h->stream));
     }
-    CK(ensure(h->rc_list, sizeof(int32_t) * n));
+    CK(ensure(h->rc_list, sizeof(RcRec) * n));
     if (h->hseed_cap < (size_t)c) {
         if (h->hseed_u) cudaFreeHost(h->hseed_u);
         h->hseed_u = nullptr;
@@ -211,7 +209,7 @@ respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64
         CK(launch_search_tc(dtype, Y, ldy, d, n, list, ds, P<float>(h->mu), P<float>(h->mu_hi),
                             P<float>(h->mu_lo), dpad, P<float>(h->mu_normf), P<int32_t>(h->counts), c,
                             p, P<float>(h->ub), P<float>(h->lb), P<float>(h->Gpart),
-                            P<float>(h->ynorm_part), P<int32_t>(h->tile_count), P<int32_t>(h->rc_list),
+                            P<float>(h->ynorm_part), P<int32_t>(h->tile_count), P<RcRec>(h->rc_list),
                             vec, h->stream));
     } else {
         CK(launch_assign(dtype, Y, ldy, d, n, list, P<float>(h->mu), P<float>(h->mu_normf),

@@ -146,17 +146,32 @@ cudaError_t launch_gather_centers(int dtype, const void* X, int64_t ldx, int64_t
 
 // Tensor-core nearest-centroid search (k_search_tc.cu), used for c <= 256.
 constexpr int kTcMaxClusters = 256;
+
+// A column whose best two scores lie within their rounding bounds, queued for
+// the FP64 re-decision, with the candidate centroids as a bit mask.
+struct RcRec {
+    int32_t col;
+    uint32_t mask[kTcMaxClusters / 32];
+    int32_t pad[3];
+};
 int tc_npad(int c);
-int tc_splits(int64_t n, int64_t d);
-size_t tc_smem_bytes(int Npad);
 cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
                             float* mu_lo, cudaStream_t st);
+// Workspace sizes of the tensor-core search for an n-column, d-row operand.
+struct TcPlan {
+    int Npad;          // centroids padded to a multiple of 16
+    int64_t dpad;      // d padded to a multiple of 32
+    size_t gpart;      // floats of partial products
+    size_t ynorm;      // floats of partial squared column norms
+    int64_t tiles;     // 128-column tiles
+};
+TcPlan tc_plan(int64_t n, int64_t d, int c);
 cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
                              const int32_t* list, DevStatus* status, const float* mu,
                              const float* mu_hi, const float* mu_lo, int64_t dpad,
                              const float* mu_normf, const int32_t* counts, int c, int32_t* labels,
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
-                             int32_t* tile_count, int32_t* rc_list, bool vec, cudaStream_t st);
+                             int32_t* tile_count, RcRec* rc_list, bool vec, cudaStream_t st);
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float warp_sum(float v) {
