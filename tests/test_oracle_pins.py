@@ -449,3 +449,10 @@ def test_zero_input_and_invalid_args(oracle_mod):
         oracle_mod.solve(np.ones((4, 5)), 0)
     with pytest.raises(ValueError):
         oracle_mod.solve(np.ones((4, 5)), 2, p0=np.array([0, 1, 2, 0, 1], dtype=np.int32))
+
+
+def test_fro_matches_library_norm(oracle_mod):
+    g = np.random.default_rng(21)
+    A = g.standard_normal((13, 7)) * 3.0
+    assert oracle_mod.fro(A) == pytest.approx(np.linalg.norm(A), rel=1e-14)
+    assert oracle_mod.fro(np.zeros((3, 2))) == 0.0
