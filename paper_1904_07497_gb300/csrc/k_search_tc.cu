@@ -48,6 +48,7 @@ constexpr int kTcStages = 2;          // stages of the list kernel
 constexpr int kTcThreads = 256;       // threads of the list kernel
 constexpr int kDnThreads = 192;       // dense kernel: TMA warp, MMA warp, 4 split/epilogue warps
 constexpr int kDnMaxStages = 4;
+constexpr int kTcMaxSplit = 16;       // largest d split of the list kernel
 constexpr unsigned kSpinLimit = 1u << 22;
 constexpr float kTieRelTc = 6e-5f;    // bound on the score rounding (see score_err)
 
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     k_search_list(const TY* __restrict__ Y, int64_t ldy, int64_t d, int64_t n,
                   const int32_t* __restrict__ list, int64_t list_max, DevStatus* __restrict__ status,
                   const float* __restrict__ mu_hi, const float* __restrict__ mu_lo, int64_t dpad,
-                  int Npad, int slabs_per_split, int nsplit, const float* __restrict__ mu_normf,
+                  int Npad, int max_split, const float* __restrict__ mu_normf,
                   const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
                   float* __restrict__ ub, float* __restrict__ lb, float* __restrict__ Gpart,
                   float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
@@ -342,7 +343,15 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     if (list && total > list_max) return;   // the dense kernel searches every column instead
     const int64_t tile0 = (int64_t)blockIdx.x * kTcM;
     if (tile0 >= total) return;
+    // d split: about two CTAs per SM over the tiles actually queued, every split non-empty
     const int64_t nslabs = (d + kTcK - 1) / kTcK;
+    const int64_t tiles = (total + kTcM - 1) / kTcM;
+    int64_t want = (2 * 152) / tiles;
+    want = want < 1 ? 1 : (want > max_split ? max_split : want);
+    if (want > nslabs) want = nslabs;
+    const int64_t slabs_per_split = (nslabs + want - 1) / want;
+    const int nsplit = (int)((nslabs + slabs_per_split - 1) / slabs_per_split);
+    if ((int)blockIdx.y >= nsplit) return;
     const int64_t s_begin = (int64_t)blockIdx.y * slabs_per_split;
     const int64_t s_end = min(nslabs, s_begin + slabs_per_split);
     const int nq = (int)(s_end - s_begin);   // >= 1: every split is non-empty
@@ -475,7 +484,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     }
     failed = __syncthreads_or(failed);
     tc_fence_after();
-    float* gtile = Gpart + ((int64_t)blockIdx.x * nsplit + blockIdx.y) * (int64_t)Npad * kTcM;
+    float* gtile = Gpart + ((int64_t)blockIdx.x * max_split + blockIdx.y) * (int64_t)Npad * kTcM;
     if (!failed && warp < 4) {
         const int mm = warp * 32 + lane;
         for (int cb = 0; cb < Npad; cb += 16) {
@@ -487,7 +496,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     }
     {
         const float other = __shfl_xor_sync(0xffffffffu, ysq, 1);
-        if (h == 0) ynorm_part[((int64_t)blockIdx.x * nsplit + blockIdx.y) * kTcM + m] = ysq + other;
+        if (h == 0) ynorm_part[((int64_t)blockIdx.x * max_split + blockIdx.y) * kTcM + m] = ysq + other;
     }
     if (failed && tid == 0) atomicOr(&status->timeout, 1);
     tc_fence_before();
@@ -506,8 +515,8 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     const int64_t p = tile0 + tid;
     if (p >= total) return;
     const int64_t col = list ? (int64_t)list[p] : p;
-    const float* gt0 = Gpart + (int64_t)blockIdx.x * nsplit * (int64_t)Npad * kTcM;
-    const float* yt0 = ynorm_part + (int64_t)blockIdx.x * nsplit * kTcM;
+    const float* gt0 = Gpart + (int64_t)blockIdx.x * max_split * (int64_t)Npad * kTcM;
+    const float* yt0 = ynorm_part + (int64_t)blockIdx.x * max_split * kTcM;
     float y2 = 0.f;
     for (int s = 0; s < nsplit; ++s) y2 += __ldcg(yt0 + (int64_t)s * kTcM + tid);
     finalize_column(col, y2, gt0, nsplit, Npad, tid, mu_normf, counts, c, labels, ub, lb, status,
@@ -811,7 +820,9 @@ __device__ double block_dist2_fp64(const TY* __restrict__ y, const float* __rest
 }
 
 // FP64 re-decision of near ties, one CTA per queued column, over the queued
-// candidate set (in increasing index, so ties keep the lowest).
+// candidate set (in increasing index, so ties keep the lowest).  The FP64
+// pipe is the limit here (about 2 FMA per clock per SM on this part), so
+// each candidate's distance uses the whole CTA.
 template <typename TY>
 __global__ void __launch_bounds__(kThreads)
     k_search_recheck(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
@@ -865,24 +876,6 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
-
-// Number of d-splits of the list kernel: about two CTAs per SM in total,
-// every split non-empty (the split count is derived back from the slabs per split).
-int64_t tc_slabs_per_split(int64_t n, int64_t d) {
-    const int64_t tiles = (n + kTcM - 1) / kTcM;
-    const int64_t nslabs = (d + kTcK - 1) / kTcK;
-    int64_t s = (2 * 152) / (tiles > 0 ? tiles : 1);
-    if (s < 1) s = 1;
-    if (s > 16) s = 16;
-    if (s > nslabs) s = nslabs;
-    return (nslabs + s - 1) / s;
-}
-
-int tc_list_splits(int64_t n, int64_t d) {
-    const int64_t nslabs = (d + kTcK - 1) / kTcK;
-    const int64_t per = tc_slabs_per_split(n, d);
-    return (int)((nslabs + per - 1) / per);
-}
 
 int g_num_sms = 0;
 std::mutex g_init_mutex;
@@ -959,7 +952,7 @@ TcPlan tc_plan(int64_t n, int64_t d, int c) {
     t.dpad = (d + 31) / 32 * 32;
     t.tiles = (n + kTcM - 1) / kTcM;
     const DensePlan dp = dense_plan(n, d, t.Npad);
-    const int64_t slots = std::max<int64_t>(tc_list_splits(n, d), dp.cmax);
+    const int64_t slots = std::max<int64_t>(kTcMaxSplit, dp.cmax);
     t.gpart = (size_t)slots * t.Npad * t.tiles * kTcM;
     t.ynorm = (size_t)slots * t.tiles * kTcM;
     return t;
@@ -1015,10 +1008,10 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
         }
     }
     if (!dense_launched || list) {
-        const int nsplit = tc_list_splits(n, d);
-        const int per = (int)tc_slabs_per_split(n, d);
+        const int64_t nslabs = (d + kTcK - 1) / kTcK;
+        const int max_split = (int)std::min<int64_t>(kTcMaxSplit, nslabs);
         const size_t smem = (size_t)kTcStages * (2 * kTcM * 128 + 2 * (size_t)Npad * 128) + 1024;
-        const dim3 grid((unsigned)((n + kTcM - 1) / kTcM), (unsigned)nsplit);
+        const dim3 grid((unsigned)((n + kTcM - 1) / kTcM), (unsigned)max_split);
         const int64_t lmax = dense_launched ? list_max : n;
         count_launches(1);
         RESPCA_DISPATCH_X(dtype, TY, {
@@ -1026,7 +1019,7 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e == cudaSuccess)
                 kern<<<grid, kTcThreads, smem, st>>>((const TY*)Y, ldy, d, n, list, lmax, status, mu_hi,
-                                                     mu_lo, dpad, Npad, per, nsplit, mu_normf, counts,
+                                                     mu_lo, dpad, Npad, kTcMaxSplit, mu_normf, counts,
                                                      c, labels, ub, lb, Gpart, ynorm_part, tile_count,
                                                      rc_list);
         });

@@ -313,10 +313,17 @@ __global__ void __launch_bounds__(kThreads)
     if (r >= d) return;
     const int cnt = counts[i];
     const int t0 = tile_off[i], t1 = tile_off[i + 1];
-    double s = 0.0;
-    for (int t = t0; t < t1; ++t) s += (double)Dpart[(int64_t)t * d + r];
-    if (sums_out) sums_out[(int64_t)i * d + r] = s;
-    if (cnt > 0) mu[(int64_t)i * d + r] = (float)(s / (double)cnt);
+    // compensated FP32 sum of the tile partials (FP64 arithmetic is slow on this part)
+    float s = 0.f, comp = 0.f;
+    for (int t = t0; t < t1; ++t) {
+        const float y = Dpart[(int64_t)t * d + r] - comp;
+        const float u = s + y;
+        comp = (u - s) - y;
+        s = u;
+    }
+    const double sd = (double)s - (double)comp;
+    if (sums_out) sums_out[(int64_t)i * d + r] = sd;
+    if (cnt > 0) mu[(int64_t)i * d + r] = (float)(sd * (1.0 / (double)cnt));
 }
 
 // Centroids from FP64 cluster sums (kept up to date incrementally).
@@ -327,7 +334,7 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int cnt = counts[i];
     if (cnt == 0 || r >= d) return;
-    mu[(int64_t)i * d + r] = (float)(sums[(int64_t)i * d + r] / (double)cnt);
+    mu[(int64_t)i * d + r] = (float)(sums[(int64_t)i * d + r] * (1.0 / (double)cnt));
 }
 
 // Move the columns listed in `moved` between cluster sums: for each moved
@@ -352,16 +359,17 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ||mu_i||^2 and, when mu_old is given, the drift ||mu_i - mu_old_i||.
-__global__ void __launch_bounds__(kThreads)
+constexpr int kStatThreads = 1024;
+__global__ void __launch_bounds__(kStatThreads)
     k_mu_stats(const float* __restrict__ mu, const float* __restrict__ mu_old, int64_t d,
                double* __restrict__ mu_norm2, float* __restrict__ mu_normf,
                double* __restrict__ drift) {
-    __shared__ double red[kThreads / 32][2];
+    __shared__ double red[kStatThreads / 32][2];
     const int i = blockIdx.x;
     const float* m = mu + (int64_t)i * d;
     const float* mo = mu_old ? mu_old + (int64_t)i * d : nullptr;
     double acc = 0.0, dr = 0.0;
-    for (int64_t r = threadIdx.x; r < d; r += kThreads) {
+    for (int64_t r = threadIdx.x; r < d; r += kStatThreads) {
         const double v = (double)m[r];
         acc += v * v;
         if (mo) {
@@ -378,7 +386,7 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0, u = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) {
+        for (int w = 0; w < kStatThreads / 32; ++w) {
             t += red[w][0];
             u += red[w][1];
         }
@@ -749,7 +757,7 @@ cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, c
 cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t d,
                             double* mu_norm2, float* mu_normf, double* drift, cudaStream_t st) {
     count_launches(1);
-    k_mu_stats<<<c, kThreads, 0, st>>>(mu, mu_old, d, mu_norm2, mu_normf, drift);
+    k_mu_stats<<<c, kStatThreads, 0, st>>>(mu, mu_old, d, mu_norm2, mu_normf, drift);
     return cudaGetLastError();
 }
 
