@@ -65,6 +65,10 @@ typedef struct {
     int32_t device;          /* CUDA device ordinal; -1 = the device current at respca_create */
     int32_t search_impl;     /* nearest-centroid search: 0 = tensor cores when c <= 256 (default),
                                 1 = CUDA-core kernel always */
+    int32_t ramp_skip;       /* 1 (default): compute the leading iterations in which S stays 0
+                                and no label moves in closed form (exact; see respca_solve);
+                                0: run every iteration */
+    int32_t reserved2;
 } respca_config;
 
 typedef struct {
@@ -147,6 +151,18 @@ respca_status respca_destroy(respca_handle h);
  *   stats     optional host struct filled on return.
  * ||X||_F = 0 returns L = S = 0 at once.  Hitting max_iter is not an error
  * (stats->converged = 0).
+ *
+ * Ramp skip (cfg.ramp_skip, cold starts only): while every |B| <= 1/rho the S
+ * step of Eq. (24) returns 0, and while no label moves the L step of Eq. (18)
+ * maps X = X_m + X_r (cluster means + residual) to L_{t+1} = X_m + a_t g_t X_r,
+ * Theta_{t+1} = rho_t b_t g_t X_r with g_0 = 1, g_{t+1} = 1 + (b_t/kappa) g_t,
+ * a_t = rho_t/(2 lambda + rho_t), b_t = 1 - a_t.  Both conditions reduce to the
+ * scalars max|X_r| and max_j ||r_j|| / sep(p_j) (sep = distance from a centroid
+ * to the nearest other one), so the solver checks them for each leading
+ * iteration (with a 1e-3 safety margin) and writes the state after the last
+ * iteration that provably keeps S = 0 and every label.  The iterates equal
+ * those of the step-by-step run up to FP32 rounding; stats count the skipped
+ * iterations.
  */
 respca_status respca_solve(respca_handle h, int32_t x_dtype, const void *X, int64_t d,
                            int64_t n, int64_t ldx, double lambda, int32_t c, double tol,

@@ -664,6 +664,62 @@ __global__ void __launch_bounds__(kThreads)
     if ((threadIdx.x & 31) == 0 && mask) atomicAdd(&status->label_changes, __popc(mask));
 }
 
+// Ramp statistics of X against its cluster means (one warp per column):
+// max |X - mu_p| over all elements and max_j ||X_j - mu_p(j)|| / sep(p(j)),
+// with sep^2 = sep2 * safety; both non-negative, combined with integer max on
+// their bit patterns (order-independent).  Also the FP64 sum of ||r_j||^2.
+template <typename TX>
+__global__ void __launch_bounds__(kThreads)
+    k_ramp_stats(const TX* __restrict__ X, int64_t ldx, int64_t d, int64_t n,
+                 const int32_t* __restrict__ labels, const float* __restrict__ mu,
+                 const double* __restrict__ sep2, double safety,
+                 unsigned int* __restrict__ max_abs_bits, unsigned long long* __restrict__ max_ratio_bits,
+                 double* __restrict__ r2_part) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    double r2acc = 0.0;
+    if (w < n) {
+        const int p = labels[w];
+        const TX* xc = X + w * ldx;
+        const float* m = mu + (int64_t)p * d;
+        float mx = 0.f;
+        double s2 = 0.0;
+        for (int64_t r = lane; r < d; r += 32) {
+            const float e = XLoad<TX>::one(xc + r) - m[r];
+            mx = fmaxf(mx, fabsf(e));
+            s2 += (double)e * (double)e;
+        }
+        s2 = warp_sum(s2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+            atomicMax(max_abs_bits, __float_as_uint(mx));
+            const double sp = sep2[p] * safety;
+            const double ratio = sp > 0.0 ? sqrt(s2 / sp) : (s2 > 0.0 ? INFINITY : 0.0);
+            atomicMax(max_ratio_bits, (unsigned long long)__double_as_longlong(ratio));
+            r2acc = s2;
+        }
+    }
+    if (lane == 0 && w < n) r2_part[w] = r2acc;
+}
+
+// State after the skipped ramp: L = mu_p + alpha (X - mu_p), Theta = beta (X - mu_p).
+template <typename TX>
+__global__ void __launch_bounds__(kThreads)
+    k_ramp_state(const TX* __restrict__ X, int64_t ldx, int64_t d, int64_t n,
+                 const int32_t* __restrict__ labels, const float* __restrict__ mu, float alpha,
+                 float beta, float* __restrict__ L, float* __restrict__ Th, int64_t lds) {
+    const int64_t total = d * n;
+    for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * kThreads) {
+        const int64_t j = idx / d, r = idx % d;
+        const float m = mu[(int64_t)labels[j] * d + r];
+        const float e = XLoad<TX>::one(X + j * ldx + r) - m;
+        L[j * lds + r] = fmaf(alpha, e, m);
+        Th[j * lds + r] = beta * e;
+    }
+}
+
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
 
 }  // namespace
@@ -839,6 +895,36 @@ cudaError_t launch_flag_columns(const float* own_part, int nchunks, int64_t n,
     count_launches(1);
     k_flag_columns<<<grid_for(n, kThreads), kThreads, 0, st>>>(own_part, nchunks, n, labels, sep2,
                                                                safety, flag_list, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ramp_stats(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
+                              const int32_t* labels, const float* mu, const double* sep2,
+                              double safety, unsigned int* max_abs_bits,
+                              unsigned long long* max_ratio_bits, double* r2_part, cudaStream_t st) {
+    count_launches(1);
+    const int grid = grid_for(n, kThreads / 32);
+    RESPCA_DISPATCH_X(dtype, TX, {
+        k_ramp_stats<TX><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu, sep2, safety,
+                                                    max_abs_bits, max_ratio_bits, r2_part);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ramp_state(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
+                              const int32_t* labels, const float* mu, float alpha, float beta,
+                              float* L, float* Th, int64_t lds, cudaStream_t st) {
+    count_launches(1);
+    RESPCA_DISPATCH_X(dtype, TX, {
+        k_ramp_state<TX><<<152 * 8, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu, alpha,
+                                                       beta, L, Th, lds);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_doubles(const double* part, int64_t count, double* out, cudaStream_t st) {
+    count_launches(1);
+    k_sum_parts<<<1, kThreads, 0, st>>>(part, (int)count, out);
     return cudaGetLastError();
 }
 

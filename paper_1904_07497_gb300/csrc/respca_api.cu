@@ -436,12 +436,66 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     if (rs != RESPCA_OK) return rs;
     CK(cudaMemsetAsync(h->lb.p, 0, sizeof(float) * n, h->stream));
     CK(cudaMemsetAsync(h->drift.p, 0, sizeof(double) * c, h->stream));
-    CK(cudaEventRecord(h->ev2, h->stream));
 
     const int km = std::max(1, h->cfg.kmeans_max_iter);
     const double kappa = h->cfg.kappa;
     const double safety = safety_factor(d);
-    for (int t = 0; t < max_iter; ++t) {
+    int t_start = 0;
+    if (!is_warm && h->cfg.ramp_skip && max_iter > 0) {
+        // Leading iterations with S = 0 and no label move, in closed form:
+        // L_{t+1} = X_m + a_t g_t X_r, Theta_{t+1} = rho_t b_t g_t X_r.
+        CK(cudaMemsetAsync(&ds->ramp_r2, 0, sizeof(double) + sizeof(unsigned long long) + sizeof(unsigned int),
+                           h->stream));
+        CK(launch_ramp_stats(dtype, X, ldx, d, n, p, P<float>(h->mu), P<double>(h->sep2), safety,
+                             &ds->ramp_abs, &ds->ramp_ratio, P<double>(h->seedD2), h->stream));
+        CK(launch_sum_doubles(P<double>(h->seedD2), n, &ds->ramp_r2, h->stream));
+        rs = read_status(h);
+        if (rs != RESPCA_OK) return rs;
+        float mabs;
+        std::memcpy(&mabs, &h->hstat->ramp_abs, sizeof(float));
+        double ratio;
+        std::memcpy(&ratio, &h->hstat->ramp_ratio, sizeof(double));
+        const double xr2 = h->hstat->ramp_r2;
+        const double xr = std::sqrt(xr2);
+        const double M = (double)mabs, margin = 1e-3;
+        double g = 1.0, r = rho, prev_ag = 0.0, alpha = 0.0, beta = 0.0;
+        int T = 0;
+        double e_res = 0.0, e_dl = 0.0;
+        while (T < max_iter) {
+            const double a = r / (2.0 * lam + r), b = 2.0 * lam / (2.0 * lam + r);
+            if (!(r * b * g * M <= 1.0 - margin)) break;          // S stays 0 (Eq. (24))
+            if (!(a * g * ratio <= 0.5 * (1.0 - margin))) break;  // own centroid stays nearest
+            const double ag = a * g;
+            const double er = (1.0 - ag) * xr / nx;
+            // ||L_{t+1} - L_t||: from L_0 = 0 the first step moves by ||X_m + a g X_r||
+            const double edl = (T == 0)
+                                   ? std::sqrt(std::max(0.0, h->hstat->x_norm2 - xr2 + ag * ag * xr2)) / nx
+                                   : std::fabs(ag - prev_ag) * xr / nx;
+            if (std::max(er, edl) <= tol) break;                  // leave convergence to the loop
+            alpha = ag;
+            beta = r * b * g;
+            e_res = er;
+            e_dl = edl;
+            prev_ag = ag;
+            g = 1.0 + (b / kappa) * g;
+            r *= kappa;
+            ++T;
+        }
+        if (T > 0) {
+            CK(launch_ramp_state(dtype, X, ldx, d, n, p, P<float>(h->mu), (float)alpha, (float)beta, L,
+                                 pb.Th, lds, h->stream));
+            rho = r;
+            t_start = T;
+            out.iters = T;
+            out.err_resid = e_res;
+            out.err_dL = e_dl;
+            out.err_dS = 0.0;
+            out.err = std::max(e_res, e_dl);
+        }
+    }
+    CK(cudaEventRecord(h->ev2, h->stream));
+
+    for (int t = t_start; t < max_iter; ++t) {
         const double rho_next = rho * kappa;
         IterScalars sc;
         sc.a = (float)(rho / (2.0 * lam + rho));
@@ -543,6 +597,8 @@ void respca_config_default(respca_config* cfg) {
     cfg->seed = 0;
     cfg->stream = nullptr;
     cfg->device = -1;
+    cfg->search_impl = 0;
+    cfg->ramp_skip = 1;
 }
 
 respca_status respca_create(respca_handle* out, const respca_config* cfg) {

@@ -47,6 +47,10 @@ struct TileDesc {
 struct DevStatus {
     double norm2[3];        // sums of squares of X-L-S, L-L_prev, S-S_prev
     double x_norm2;         // ||X||_F^2
+    double ramp_r2;         // ||X - mu_p||_F^2 (ramp statistics)
+    unsigned long long ramp_ratio;  // bits of max_j ||X_j - mu_p|| / sep(p)
+    unsigned int ramp_abs;  // bits of max |X - mu_p|
+    int32_t pad0;
     int32_t flagged;        // columns queued for a nearest-centroid search
     int32_t changed;        // labels changed by the last assignment pass
     int32_t rechecked;      // near-tie columns re-decided in FP64
@@ -133,6 +137,17 @@ cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int6
 
 cudaError_t launch_count_changed(const int32_t* labels, const int32_t* prev, int64_t n,
                                  DevStatus* status, cudaStream_t st);
+
+cudaError_t launch_sum_doubles(const double* part, int64_t count, double* out, cudaStream_t st);
+
+// Closed-form ramp: statistics of X - mu_p, and the state after it.
+cudaError_t launch_ramp_stats(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
+                              const int32_t* labels, const float* mu, const double* sep2,
+                              double safety, unsigned int* max_abs_bits,
+                              unsigned long long* max_ratio_bits, double* r2_part, cudaStream_t st);
+cudaError_t launch_ramp_state(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
+                              const int32_t* labels, const float* mu, float alpha, float beta,
+                              float* L, float* Th, int64_t lds, cudaStream_t st);
 
 cudaError_t launch_seed_dist(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
                              const int32_t* centers, int k, double* D2, cudaStream_t st);

@@ -31,7 +31,8 @@ class respca_config(ctypes.Structure):
     _fields_ = [("rho0", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("kmeans_max_iter", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
-                ("device", ctypes.c_int32), ("search_impl", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("search_impl", ctypes.c_int32),
+                ("ramp_skip", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class respca_stats(ctypes.Structure):
@@ -251,10 +252,11 @@ class Solver:
 
     def __init__(self, rho0: float = 1e-4, kappa: float = 1.5, kmeans_max_iter: int = 100,
                  seed: int = 0, stream=None, device: int | None = None, timing: bool = False,
-                 search_impl: int = 0):
+                 search_impl: int = 0, ramp_skip: bool = True):
         import torch
         cfg = respca_config_default()
         cfg.search_impl = search_impl
+        cfg.ramp_skip = 1 if ramp_skip else 0
         cfg.rho0, cfg.kappa, cfg.kmeans_max_iter, cfg.seed = rho0, kappa, kmeans_max_iter, seed
         cfg.timing = 1 if timing else 0
         dev = torch.cuda.current_device() if device is None else device

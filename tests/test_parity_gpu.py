@@ -317,3 +317,32 @@ def test_search_paths_agree_bf16_x():
     b = _solve_impl(1, pr.X, 16, 30, dtype=torch.bfloat16)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+
+
+# ------------------------------------------------------------------ ramp skip
+@pytest.mark.parametrize("kind", ["lowrank", "video"])
+def test_ramp_skip_matches_step_by_step(kind):
+    """The closed-form ramp (S = 0, no label move) gives the same labels and
+    iteration count as running every iteration, and L, S equal to FP32 rounding."""
+    from paper_1904_07497_gb300 import respca
+    if kind == "lowrank":
+        pr = synth.lowrank_sparse(500, 500, 25, 0.05, seed=0)
+        c = 25
+    else:
+        pr = synth.video(n=240, height=48, width=64, n_backgrounds=3, seed=4)
+        c = 3
+    X64 = pr.X.astype(np.float64)
+    p0, _ = oracle.init_labels(X64, c, seed=0)
+    outs = []
+    for skip in (True, False):
+        s = respca.Solver(seed=0, ramp_skip=skip)
+        res = s.solve(_dev(pr.X), c, tol=1e-6, max_iter=500, p0=torch.from_numpy(p0).cuda())
+        torch.cuda.synchronize()
+        outs.append((res.p.cpu().numpy(), _host(res.L), _host(res.S), res.stats))
+        s.close()
+    (pa, La, Sa, sa), (pb, Lb, Sb, sb) = outs
+    assert sa["iters"] == sb["iters"]
+    assert sa["lloyd_passes"] < sb["lloyd_passes"]          # the ramp really was skipped
+    np.testing.assert_array_equal(pa, pb)
+    assert np.linalg.norm(La - Lb) <= 1e-6 * np.linalg.norm(Lb)
+    assert np.linalg.norm(Sa - Sb) <= 1e-6 * max(np.linalg.norm(Sb), 1e-3 * np.linalg.norm(X64))
