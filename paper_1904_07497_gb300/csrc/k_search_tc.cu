@@ -8,12 +8,16 @@
 // tensor memory.  FP32 accuracy comes from the 3-term split y = y_hi + y_lo,
 // mu = mu_hi + mu_lo (hi = TF32-truncated):
 //   y.mu ~ y_hi.mu_hi + y_hi.mu_lo + y_lo.mu_hi       (error ~ 2^-20 relative).
+// kind::tf32 reads an FP32 operand by dropping its 13 low mantissa bits (a
+// truncation, measured on this part with operands whose low bits tell
+// truncation, rounding and full FP32 apart), so an unconverted FP32 tile in
+// shared memory already is its hi part: the dense kernel writes only y_lo.
 //
 // Two kernels feed the tensor cores:
 //  * k_search_dense (all columns, FP32 Y): stream-K over (column tile, 32-row
 //    slab) work, split evenly over one CTA per SM.  Warp 0 issues TMA loads
 //    (cp.async.bulk.tensor, 128-byte swizzle) into a ring of stages, warps 2-5
-//    split each Y tile into TF32 hi / lo parts in shared memory, one thread of
+//    write the TF32 lo part of each Y tile to shared memory, one thread of
 //    warp 1 issues the MMAs into two ping-pong TMEM accumulators, and warps
 //    2-5 drain a finished accumulator to global partial sums.
 //  * k_search_list (a queued subset of columns, or any element type): threads
@@ -46,8 +50,9 @@ constexpr int kTcM = 128;             // columns per tile (UMMA M)
 constexpr int kTcK = 32;              // d rows per slab: one 128-byte swizzle atom of FP32
 constexpr int kTcStages = 2;          // stages of the list kernel
 constexpr int kTcThreads = 256;       // threads of the list kernel
-constexpr int kDnThreads = 192;       // dense kernel: TMA warp, MMA warp, 4 split/epilogue warps
-constexpr int kDnMaxStages = 4;
+constexpr int kDnThreads = 224;       // dense kernel: 2 TMA warps, MMA warp, 4 split/epilogue warps
+constexpr int kDnMaxY = 3;            // Y stages (row blocks)
+constexpr int kDnMaxB = 6;            // centroid slab stages
 constexpr int kTcMaxSplit = 16;       // largest d split of the list kernel
 constexpr unsigned kSpinLimit = 1u << 22;
 constexpr float kTieRelTc = 6e-5f;    // bound on the score rounding (see score_err)
@@ -534,12 +539,79 @@ __host__ __device__ __forceinline__ int64_t sk_owner(int64_t w, int64_t W, int64
 }
 
 struct DenseArgs {
-    int64_t d, n, Q, T, W;   // rows, columns, slabs per tile, tiles, total work
-    int Npad, stages, cmax;
+    int64_t d, n, Q, T, W;   // rows, columns, row blocks per tile, tiles, work units
+    int64_t nslab;           // 32-row slabs in d
+    int Npad, R, YS, BS;     // slabs per row block, Y stages (R slabs each), centroid stages
+    int cmax, nacc;          // partial-sum slots per tile, accumulator buffers
+    uint32_t lo_col;         // first TMEM column of the y_lo ring (BS x 32 columns)
+    uint32_t tmem_cols;      // TMEM columns allocated
     int use_list;            // 1: a queued list was asked for (run only if it is long)
     int64_t list_min;
 };
 
+// A operand read from tensor memory (lane m = row m, column k = K index k).
+__device__ __forceinline__ void tc_mma_tmem_a(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t* r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+          "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+          "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+          "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+          "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+// Position in a ring of n stages: the stage index and the parity of the
+// phase its current use completes (advanced without divisions: the issuing
+// thread of the tensor cores has no cycles to spare).
+struct RingPos {
+    int idx, n;
+    uint32_t phase;
+    __device__ explicit RingPos(int n_) : idx(0), n(n_), phase(0u) {}
+    __device__ __forceinline__ void next() {
+        if (++idx == n) {
+            idx = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
+// Waits for the latest phase of each of the n barriers used by k uses of a
+// ring (the copies in flight when a producer leaves).
+__device__ __forceinline__ void drain_ring(uint64_t* bars, int n, int64_t k) {
+    for (int s = 0; s < n; ++s) {
+        const int64_t uses = (k > s) ? (k - s + n - 1) / n : 0;
+        if (uses > 0) mbar_wait(&bars[s], (uint32_t)((uses - 1) & 1));
+    }
+}
+
+// Dense search.  A work unit is one row block (R slabs of 32 rows) of one
+// 128-column tile; stream-K splits the units evenly over one CTA per SM.
+// Y is staged a whole row block at a time (R boxes issued together, so each
+// column is read in runs of R x 128 bytes), in YS stages; the centroid hi / lo
+// slabs come through their own ring of BS stages, fed by a second producer
+// warp.  The split warps write y_lo into a TMEM ring (BS x 32 columns), from
+// where the third MMA of the split reads it as its A operand; the raw FP32
+// tile in shared memory is the hi operand.
+//   warp 0: Y producer, warp 1: MMA issuer, warps 2-5: split + epilogue,
+//   warp 6: centroid producer.
+// The MMA issuer is a single thread whose loop overhead bounds the tensor
+// core's rate: stage indices and phases advance incrementally and the
+// shared-memory descriptors are formed once and offset by addition (the
+// address field of a descriptor is the byte address / 16).
 __global__ void __launch_bounds__(kDnThreads, 1)
     k_search_dense(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmBh,
                    const __grid_constant__ CUtensorMap tmBl, DenseArgs a,
@@ -549,7 +621,8 @@ __global__ void __launch_bounds__(kDnThreads, 1)
                    float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
                    RcRec* __restrict__ rc_list) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t full[kDnMaxStages], conv[kDnMaxStages], empty[kDnMaxStages];
+    __shared__ uint64_t yfull[kDnMaxY], yempty[kDnMaxY];
+    __shared__ uint64_t bfull[kDnMaxB], bempty[kDnMaxB], conv[kDnMaxB];
     __shared__ uint64_t acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
@@ -562,29 +635,30 @@ __global__ void __launch_bounds__(kDnThreads, 1)
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int S = a.stages;
+    const int R = a.R, YS = a.YS, BS = a.BS, NA = a.nacc;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t a_bytes = kTcM * 128;
     const uint32_t b_bytes = (uint32_t)a.Npad * 128;
-    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
-    auto sA = [&](int s) { return base + s * stage_bytes; };              // raw, then hi
-    auto sAlo = [&](int s) { return base + s * stage_bytes + a_bytes; };
-    auto sBh = [&](int s) { return base + s * stage_bytes + 2 * a_bytes; };
-    auto sBl = [&](int s) { return base + s * stage_bytes + 2 * a_bytes + b_bytes; };
-    const uint32_t tx_bytes = a_bytes + 2 * b_bytes;
+    const uint32_t y_stage = (uint32_t)R * a_bytes;
+    const uint32_t b_base = base + (uint32_t)YS * y_stage;
+    const int64_t w_tile0 = w0 / a.Q, w_blk0 = w0 % a.Q;
+    // slabs of row block blk (the last block of d may be short)
+    auto slabs_of = [&](int64_t blk) { return (int)min((int64_t)R, a.nslab - blk * R); };
 
-    uint32_t tmem_cols = 32;
-    while ((int)tmem_cols < 2 * a.Npad) tmem_cols <<= 1;
     if (warp == 1) {
-        tmem_alloc(&tmem_base_sh, tmem_cols);
+        tmem_alloc(&tmem_base_sh, a.tmem_cols);
         tc_fence_before();
     }
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
+        for (int s = 0; s < YS; ++s) {
+            mbar_init(&yfull[s], 1);
+            mbar_init(&yempty[s], 1);
+        }
+        for (int s = 0; s < BS; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&bempty[s], 1);
             mbar_init(&conv[s], 4);
-            mbar_init(&empty[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&acc_full[s], 1);
@@ -598,139 +672,203 @@ __global__ void __launch_bounds__(kDnThreads, 1)
     const uint32_t tmem = tmem_base_sh;
 
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- Y producer: one row block per stage
         if (lane == 0) {
-            int64_t k = 0;
+            RingPos yr(YS);
+            int64_t k = 0, tile = w_tile0, blk = w_blk0;
             for (int64_t w = w0; w < w1; ++w, ++k) {
-                const int st = (int)(k % S);
-                const int64_t u = k / S;
-                if (u > 0 && !mbar_wait_or_abort(&empty[st], (uint32_t)((u - 1) & 1), &abort_sh)) {
+                if (k >= YS && !mbar_wait_or_abort(&yempty[yr.idx], yr.phase ^ 1u, &abort_sh)) {
                     abort_sh = 1;
                     break;
                 }
-                const int64_t tile = w / a.Q, s = w % a.Q;
-                mbar_expect_tx(&full[st], tx_bytes);
-                tma_load_2d(sA(st), &tmY, &full[st], (int32_t)(s * kTcK), (int32_t)(tile * kTcM));
-                tma_load_2d(sBh(st), &tmBh, &full[st], (int32_t)(s * kTcK), 0);
-                tma_load_2d(sBl(st), &tmBl, &full[st], (int32_t)(s * kTcK), 0);
+                const int rs = slabs_of(blk);
+                const uint32_t dst = base + (uint32_t)yr.idx * y_stage;
+                mbar_expect_tx(&yfull[yr.idx], (uint32_t)rs * a_bytes);
+                for (int q = 0; q < rs; ++q)
+                    tma_load_2d(dst + (uint32_t)q * a_bytes, &tmY, &yfull[yr.idx],
+                                (int32_t)((blk * R + q) * kTcK), (int32_t)(tile * kTcM));
+                yr.next();
+                if (++blk == a.Q) {
+                    blk = 0;
+                    ++tile;
+                }
             }
-            // make sure no copy is still in flight when the CTA leaves
-            const int64_t issued = k;
-            for (int64_t j = (issued > S ? issued - S : 0); j < issued; ++j)
-                mbar_wait(&full[j % S], (uint32_t)((j / S) & 1));
+            drain_ring(yfull, YS, k);   // no copy may be in flight when the CTA leaves
+        }
+    } else if (warp == 6) {
+        // ---------------- centroid producer: one slab per stage
+        if (lane == 0) {
+            RingPos br(BS);
+            int64_t j = 0, blk = w_blk0;
+            bool ok = true;
+            for (int64_t w = w0; w < w1 && ok; ++w) {
+                const int rs = slabs_of(blk);
+                for (int q = 0; q < rs; ++q, ++j) {
+                    if (j >= BS && !mbar_wait_or_abort(&bempty[br.idx], br.phase ^ 1u, &abort_sh)) {
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    const int32_t row = (int32_t)((blk * R + q) * kTcK);
+                    const uint32_t dst = b_base + (uint32_t)br.idx * 2 * b_bytes;
+                    mbar_expect_tx(&bfull[br.idx], 2 * b_bytes);
+                    tma_load_2d(dst, &tmBh, &bfull[br.idx], row, 0);
+                    tma_load_2d(dst + b_bytes, &tmBl, &bfull[br.idx], row, 0);
+                    br.next();
+                }
+                if (++blk == a.Q) blk = 0;
+            }
+            drain_ring(bfull, BS, j);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(kTcM, a.Npad);
-            int64_t k = 0, g = 0;
-            bool issued_any = false;
-            int last_empty = 0;
-            int64_t last_use = 0;
-            for (int64_t w = w0; w < w1; ++w, ++k) {
-                const int st = (int)(k % S);
-                const int64_t u = k / S;
-                const int64_t s = w % a.Q;
-                const bool seg_start = (w == w0) || (s == 0);
-                const bool seg_end = (w == w1 - 1) || (s == a.Q - 1);
-                const int bsel = (int)(g & 1);
-                if (seg_start && (g >> 1) > 0 &&
-                    !mbar_wait_or_abort(&acc_empty[bsel], (uint32_t)(((g >> 1) - 1) & 1), &abort_sh)) {
+            const uint64_t dY = sw128_desc(base), dB = sw128_desc(b_base);
+            const uint32_t y16 = y_stage >> 4, a16 = a_bytes >> 4, b16 = b_bytes >> 4;
+            RingPos yr(YS), br(BS), ar(NA);
+            int64_t g = 0, blk = w_blk0;
+            bool ok = true;
+            uint64_t* last_bar = nullptr;   // barrier of the latest commit and its phase
+            uint32_t last_par = 0;
+            for (int64_t w = w0; w < w1 && ok; ++w) {
+                const int rs = slabs_of(blk);
+                const bool seg_start = (w == w0) || (blk == 0);
+                const bool seg_end = (w == w1 - 1) || (blk == a.Q - 1);
+                if (seg_start && g >= NA &&
+                    !mbar_wait_or_abort(&acc_empty[ar.idx], ar.phase ^ 1u, &abort_sh)) {
                     abort_sh = 1;
                     break;
                 }
-                if (!mbar_wait_or_abort(&conv[st], (uint32_t)(u & 1), &abort_sh)) {
+                if (!mbar_wait_or_abort(&yfull[yr.idx], yr.phase, &abort_sh)) {
                     abort_sh = 1;
                     break;
                 }
-                tc_fence_after();
-                const uint32_t acc = tmem + (uint32_t)(bsel * a.Npad);
+                const uint32_t acc = tmem + (uint32_t)(ar.idx * a.Npad);
+                uint64_t dA = dY + (uint64_t)(yr.idx * y16);
+                for (int q = 0; q < rs; ++q, dA += a16) {
+                    if (!mbar_wait_or_abort(&bfull[br.idx], br.phase, &abort_sh) ||
+                        !mbar_wait_or_abort(&conv[br.idx], br.phase, &abort_sh)) {
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t dBh = dB + (uint64_t)(br.idx * 2 * b16), dBl = dBh + b16;
+                    const uint32_t alo = tmem + a.lo_col + (uint32_t)(br.idx * 32);
+                    const uint32_t first = (seg_start && q == 0) ? 0u : 1u;
 #pragma unroll
-                for (int ks = 0; ks < kTcK / 8; ++ks) {
-                    const uint32_t koff = ks * 32;
-                    const uint64_t dah = sw128_desc(sA(st) + koff), dal = sw128_desc(sAlo(st) + koff);
-                    const uint64_t dbh = sw128_desc(sBh(st) + koff), dbl = sw128_desc(sBl(st) + koff);
-                    tc_mma(acc, dah, dbh, idesc, (seg_start && ks == 0) ? 0u : 1u);
-                    tc_mma(acc, dah, dbl, idesc, 1u);
-                    tc_mma(acc, dal, dbh, idesc, 1u);
+                    for (int ks = 0; ks < kTcK / 8; ++ks) {
+                        // 8 TF32 of K = 32 bytes = 2 descriptor address units
+                        tc_mma(acc, dA + 2 * ks, dBh + 2 * ks, idesc, ks == 0 ? first : 1u);
+                        tc_mma(acc, dA + 2 * ks, dBl + 2 * ks, idesc, 1u);
+                        tc_mma_tmem_a(acc, alo + (uint32_t)(ks * 8), dBh + 2 * ks, idesc, 1u);
+                    }
+                    tc_commit(&bempty[br.idx]);
+                    last_bar = &bempty[br.idx];
+                    last_par = br.phase;
+                    br.next();
                 }
-                tc_commit(&empty[st]);
-                issued_any = true;
-                last_empty = st;
-                last_use = u;
+                if (!ok) break;
+                tc_commit(&yempty[yr.idx]);
+                last_bar = &yempty[yr.idx];
+                last_par = yr.phase;
+                yr.next();
                 if (seg_end) {
-                    tc_commit(&acc_full[bsel]);
+                    tc_commit(&acc_full[ar.idx]);
+                    ar.next();
                     ++g;
                 }
+                if (++blk == a.Q) blk = 0;
             }
             // drain: the last commit covers every MMA issued before it
-            if (issued_any) mbar_wait(&empty[last_empty], (uint32_t)(last_use & 1));
+            if (last_bar) mbar_wait(last_bar, last_par);
         }
     } else {
-        // ---------------- TF32 split + epilogue (warps 2-5; row m = TMEM lane)
+        // ---------------- TF32 lo split + epilogue (warps 2-5; row m = TMEM lane)
         const int m = 32 * (warp & 3) + lane;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int et = tid - 64;   // 0..127
-        int64_t k = 0, g = 0;
+        RingPos yr(YS), br(BS), ar(NA);
+        int64_t j = 0, tile = w_tile0, blk = w_blk0;
         float ysq = 0.f, ycomp = 0.f;
-        for (int64_t w = w0; w < w1; ++w, ++k) {
-            const int st = (int)(k % S);
-            const int64_t u = k / S;
-            const int64_t tile = w / a.Q, s = w % a.Q;
-            const bool seg_start = (w == w0) || (s == 0);
-            const bool seg_end = (w == w1 - 1) || (s == a.Q - 1);
+        bool ok = true;
+        for (int64_t w = w0; w < w1 && ok; ++w) {
+            const int rs = slabs_of(blk);
+            const bool seg_start = (w == w0) || (blk == 0);
+            const bool seg_end = (w == w1 - 1) || (blk == a.Q - 1);
             if (seg_start) ysq = ycomp = 0.f;
-            if (!mbar_wait_or_abort(&full[st], (uint32_t)(u & 1), &abort_sh)) {
+            if (!mbar_wait_or_abort(&yfull[yr.idx], yr.phase, &abort_sh)) {
                 abort_sh = 1;
                 break;
             }
-            float part = 0.f;
+            const uint32_t ybase = base + (uint32_t)yr.idx * y_stage;
+            for (int q = 0; q < rs; ++q, ++j) {
+                // the lo stage is free once the MMAs of slab j - BS are done
+                if (j >= BS && !mbar_wait_or_abort(&bempty[br.idx], br.phase ^ 1u, &abort_sh)) {
+                    abort_sh = 1;
+                    ok = false;
+                    break;
+                }
+                float part = 0.f;
+                uint32_t r[32];
+                const uint32_t src = ybase + (uint32_t)q * a_bytes;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const uint32_t off = sw128_off(m, q);
-                const float4 x = ld_shared_v4(sA(st) + off);
-                const float4 hi = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-                st_shared_v4(sA(st) + off, hi);
-                st_shared_v4(sAlo(st) + off, make_float4(x.x - hi.x, x.y - hi.y, x.z - hi.z, x.w - hi.w));
-                part = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, part))));
-            }
-            {
+                for (int qq = 0; qq < 8; ++qq) {
+                    // the raw tile stays as the hi operand (the MMA truncates it)
+                    const float4 x = ld_shared_v4(src + sw128_off(m, qq));
+                    r[4 * qq + 0] = __float_as_uint(x.x - tf32_hi(x.x));
+                    r[4 * qq + 1] = __float_as_uint(x.y - tf32_hi(x.y));
+                    r[4 * qq + 2] = __float_as_uint(x.z - tf32_hi(x.z));
+                    r[4 * qq + 3] = __float_as_uint(x.w - tf32_hi(x.w));
+                    part = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, part))));
+                }
+                tc_st32(tmem + lane_base + a.lo_col + (uint32_t)(br.idx * 32), r);
                 const float y = part - ycomp;   // Kahan accumulation of ||y_j||^2
                 const float t = ysq + y;
                 ycomp = (t - ysq) - y;
                 ysq = t;
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&conv[br.idx]);
+                br.next();
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&conv[st]);
-            if (!seg_end) continue;
+            yr.next();
+            const int64_t cur_tile = tile;
+            if (++blk == a.Q) {
+                blk = 0;
+                ++tile;
+            }
+            if (!ok || !seg_end) continue;
 
             // a column tile segment is finished: drain its accumulator
-            const int bsel = (int)(g & 1);
-            if (!mbar_wait_or_abort(&acc_full[bsel], (uint32_t)((g >> 1) & 1), &abort_sh)) {
+            if (!mbar_wait_or_abort(&acc_full[ar.idx], ar.phase, &abort_sh)) {
                 abort_sh = 1;
                 break;
             }
             tc_fence_after();
-            const int64_t bfirst = sk_owner(tile * a.Q, a.W, G);
-            const int64_t blast = sk_owner((tile + 1) * a.Q - 1, a.W, G);
+            const int64_t bfirst = sk_owner(cur_tile * a.Q, a.W, G);
+            const int64_t blast = sk_owner((cur_tile + 1) * a.Q - 1, a.W, G);
             const int slot = (int)(b - bfirst);
             const int ncontrib = (int)(blast - bfirst + 1);
-            float* gslot = Gpart + ((int64_t)tile * a.cmax + slot) * (int64_t)a.Npad * kTcM;
+            float* gslot = Gpart + ((int64_t)cur_tile * a.cmax + slot) * (int64_t)a.Npad * kTcM;
+            const uint32_t acc = (uint32_t)(ar.idx * a.Npad);
             for (int cb = 0; cb < a.Npad; cb += 16) {
-                float v[16];
-                tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(bsel * a.Npad + cb), v);
+                float vv[16];
+                tc_ld16(tmem + lane_base + acc + (uint32_t)cb, vv);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) gslot[(int64_t)(cb + q) * kTcM + m] = v[q];
+                for (int q = 0; q < 16; ++q) gslot[(int64_t)(cb + q) * kTcM + m] = vv[q];
             }
-            ynorm_part[((int64_t)tile * a.cmax + slot) * kTcM + m] = ysq;
+            ynorm_part[((int64_t)cur_tile * a.cmax + slot) * kTcM + m] = ysq;
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[bsel]);
-            ++g;
+            if (lane == 0) mbar_arrive(&acc_empty[ar.idx]);
+            ar.next();
             __threadfence();
             named_sync(1, 128);
             if (et == 0) {
-                const int prev = atomicAdd(&tile_count[tile], 1);
+                const int prev = atomicAdd(&tile_count[cur_tile], 1);
                 is_last_sh = (prev == ncontrib - 1);
             }
             named_sync(1, 128);
@@ -738,11 +876,11 @@ __global__ void __launch_bounds__(kDnThreads, 1)
             named_sync(1, 128);
             if (!last) continue;
             __threadfence();
-            if (et == 0) tile_count[tile] = 0;
-            const int64_t p = tile * kTcM + m;
+            if (et == 0) tile_count[cur_tile] = 0;
+            const int64_t p = cur_tile * kTcM + m;
             if (p < a.n) {
-                const float* gt0 = Gpart + (int64_t)tile * a.cmax * (int64_t)a.Npad * kTcM;
-                const float* yt0 = ynorm_part + (int64_t)tile * a.cmax * kTcM;
+                const float* gt0 = Gpart + (int64_t)cur_tile * a.cmax * (int64_t)a.Npad * kTcM;
+                const float* yt0 = ynorm_part + (int64_t)cur_tile * a.cmax * kTcM;
                 float y2 = 0.f;
                 for (int sl = 0; sl < ncontrib; ++sl) y2 += __ldcg(yt0 + (int64_t)sl * kTcM + m);
                 finalize_column(p, y2, gt0, ncontrib, a.Npad, m, mu_normf, counts, c, labels, ub, lb,
@@ -753,7 +891,7 @@ __global__ void __launch_bounds__(kDnThreads, 1)
     __syncthreads();
     if (abort_sh && tid == 0) atomicOr(&status->timeout, 1);
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem, tmem_cols);
+    if (warp == 1) tmem_dealloc(tmem, a.tmem_cols);
 }
 
 // ============================================================== FP64 recheck
@@ -919,17 +1057,39 @@ bool encode_2d(CUtensorMap* map, const float* ptr, int64_t inner, int64_t outer,
 }
 
 struct DensePlan {
-    int stages;
-    int64_t Q, T, W;
+    int R, YS, BS, nacc;
+    uint32_t lo_col, tmem_cols;
+    int64_t nslab, Q, T, W;
     int G, cmax;
     size_t smem;
 };
 
-DensePlan dense_plan(int64_t n, int64_t d, int Npad) {
+// Shape of the dense kernel's pipeline: the longest row block (R slabs, at
+// most 4) whose two Y stages leave room for at least three centroid stages in
+// 200 KB of shared memory (else R = 1 with two), as many centroid stages as
+// fit (at most kDnMaxB), and two accumulators when they fit next to the y_lo
+// ring in 512 TMEM columns.
+DensePlan dense_plan(int64_t n, int64_t d, int Npad, int r_pref = 4, int ys_pref = 2) {
     DensePlan p;
-    const size_t stage_bytes = 2 * kTcM * 128 + 2 * (size_t)Npad * 128;
-    p.stages = (int)std::min<size_t>(kDnMaxStages, (200 * 1024) / stage_bytes);
-    p.Q = (d + kTcK - 1) / kTcK;
+    const size_t budget = 200 * 1024, a_bytes = (size_t)kTcM * 128, b_stage = 2 * (size_t)Npad * 128;
+    p.YS = ys_pref;
+    p.R = 1;
+    for (int R = r_pref; R >= 1; --R) {
+        const size_t y = (size_t)p.YS * R * a_bytes;
+        if (y < budget && (budget - y) / b_stage >= 3) {
+            p.R = R;
+            break;
+        }
+    }
+    p.BS = (int)std::min<size_t>(kDnMaxB, (budget - (size_t)p.YS * p.R * a_bytes) / b_stage);
+    if (p.BS < 2) p.BS = 2;   // Npad <= 256 keeps this inside 227 KB
+    p.nacc = (((2 * Npad + 31) / 32) * 32 + p.BS * 32 <= 512) ? 2 : 1;
+    p.lo_col = (uint32_t)(((p.nacc * Npad) + 31) / 32 * 32);
+    const uint32_t used = p.lo_col + (uint32_t)(p.BS * 32);
+    p.tmem_cols = 32;
+    while (p.tmem_cols < used) p.tmem_cols <<= 1;
+    p.nslab = (d + kTcK - 1) / kTcK;
+    p.Q = (p.nslab + p.R - 1) / p.R;
     p.T = (n + kTcM - 1) / kTcM;
     p.W = p.Q * p.T;
     p.G = (int)std::min<int64_t>(num_sms(), p.W);
@@ -938,7 +1098,7 @@ DensePlan dense_plan(int64_t n, int64_t d, int Npad) {
         const int64_t nc = sk_owner((t + 1) * p.Q - 1, p.W, p.G) - sk_owner(t * p.Q, p.W, p.G) + 1;
         if (nc > p.cmax) p.cmax = (int)nc;
     }
-    p.smem = (size_t)p.stages * stage_bytes + 1024;
+    p.smem = (size_t)p.YS * p.R * a_bytes + (size_t)p.BS * b_stage + 1024;
     return p;
 }
 
@@ -992,9 +1152,15 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             a.Q = dp.Q;
             a.T = dp.T;
             a.W = dp.W;
+            a.nslab = dp.nslab;
             a.Npad = Npad;
-            a.stages = dp.stages;
+            a.R = dp.R;
+            a.YS = dp.YS;
+            a.BS = dp.BS;
             a.cmax = dp.cmax;
+            a.nacc = dp.nacc;
+            a.lo_col = dp.lo_col;
+            a.tmem_cols = dp.tmem_cols;
             a.use_list = list ? 1 : 0;
             a.list_min = list_max + 1;
             e = cudaFuncSetAttribute(k_search_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,

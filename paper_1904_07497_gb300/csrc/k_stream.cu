@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads)
     k_delta_sums(const TX* __restrict__ X, int64_t ldx, const float* __restrict__ L, int64_t lds,
                  const int4* __restrict__ moved, const DevStatus* __restrict__ status, int64_t d,
                  double* __restrict__ sums) {
-    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d) return;
     const int nm = status->moved;
     for (int m = 0; m < nm; ++m) {
@@ -358,23 +358,34 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// ||mu_i||^2 and, when mu_old is given, the drift ||mu_i - mu_old_i||.
+// ||mu_i||^2 and, when mu_old is given, the drift ||mu_i - mu_old_i||, one
+// CTA per centroid: compensated FP32 sums per thread, FP32 tree across the CTA
+// (relative error ~1e-6, well inside the slack of the pruning bounds; the FP64
+// pipe of this part is too slow for a d-long FP64 reduction per centroid).
 constexpr int kStatThreads = 1024;
 __global__ void __launch_bounds__(kStatThreads)
     k_mu_stats(const float* __restrict__ mu, const float* __restrict__ mu_old, int64_t d,
                double* __restrict__ mu_norm2, float* __restrict__ mu_normf,
                double* __restrict__ drift) {
-    __shared__ double red[kStatThreads / 32][2];
+    __shared__ float red[kStatThreads / 32][2];
     const int i = blockIdx.x;
     const float* m = mu + (int64_t)i * d;
     const float* mo = mu_old ? mu_old + (int64_t)i * d : nullptr;
-    double acc = 0.0, dr = 0.0;
+    float acc = 0.f, ca = 0.f, dr = 0.f, cd = 0.f;
     for (int64_t r = threadIdx.x; r < d; r += kStatThreads) {
-        const double v = (double)m[r];
-        acc += v * v;
+        const float v = m[r];
+        {
+            const float y = v * v - ca;
+            const float t = acc + y;
+            ca = (t - acc) - y;
+            acc = t;
+        }
         if (mo) {
-            const double t = v - (double)mo[r];
-            dr += t * t;
+            const float e = v - mo[r];
+            const float y = e * e - cd;
+            const float t = dr + y;
+            cd = (t - dr) - y;
+            dr = t;
         }
     }
     acc = warp_sum(acc);
@@ -384,15 +395,15 @@ __global__ void __launch_bounds__(kStatThreads)
         red[threadIdx.x >> 5][1] = dr;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0, u = 0.0;
-        for (int w = 0; w < kStatThreads / 32; ++w) {
-            t += red[w][0];
-            u += red[w][1];
+    if (threadIdx.x < 32) {
+        float a = red[threadIdx.x][0], b = red[threadIdx.x][1];
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (threadIdx.x == 0) {
+            mu_norm2[i] = (double)a;
+            mu_normf[i] = a;
+            if (drift) drift[i] = sqrt((double)b) * (1.0 + 1e-5);
         }
-        mu_norm2[i] = t;
-        mu_normf[i] = (float)t;
-        if (drift) drift[i] = sqrt(u);
     }
 }
 
@@ -798,13 +809,16 @@ cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, c
                               int64_t lds, const int4* moved, const DevStatus* status, int64_t d,
                               double* sums, cudaStream_t st) {
     count_launches(1);
-    const int grid = grid_for(d, kThreads);
+    // small CTAs: the serial FP64 updates per row spread over every SM
+    constexpr int kDeltaThreads = 64;
+    const int grid = grid_for(d, kDeltaThreads);
     if (mode == kSumL) {
-        k_delta_sums<kSumL, float><<<grid, kThreads, 0, st>>>(nullptr, 0, L, lds, moved, status, d, sums);
+        k_delta_sums<kSumL, float><<<grid, kDeltaThreads, 0, st>>>(nullptr, 0, L, lds, moved, status, d,
+                                                                   sums);
     } else {
         RESPCA_DISPATCH_X(dtype, TX, {
-            k_delta_sums<kSumX, TX><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, nullptr, 0, moved,
-                                                               status, d, sums);
+            k_delta_sums<kSumX, TX><<<grid, kDeltaThreads, 0, st>>>((const TX*)X, ldx, nullptr, 0, moved,
+                                                                    status, d, sums);
         });
     }
     return cudaGetLastError();
