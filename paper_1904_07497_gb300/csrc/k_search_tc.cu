@@ -957,31 +957,66 @@ __device__ double block_dist2_fp64(const TY* __restrict__ y, const float* __rest
     return s;
 }
 
-// FP64 re-decision of near ties, one CTA per queued column, over the queued
-// candidate set (in increasing index, so ties keep the lowest).  The FP64
-// pipe is the limit here (about 2 FMA per clock per SM on this part), so
-// each candidate's distance uses the whole CTA.
+// FP64 re-decision of near ties.  The FP64 pipe is the limit here (about 2
+// FMA per clock per SM on this part), so the candidate distances of the
+// first rc_cap queued columns are spread over every SM, one CTA per
+// (column, candidate) pair; k_search_recheck_pick then decides each column
+// over its candidates in increasing index (ties keep the lowest).  Columns
+// queued beyond rc_cap are decided by one CTA each, candidate after candidate.
 template <typename TY>
 __global__ void __launch_bounds__(kThreads)
-    k_search_recheck(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
-                     DevStatus* __restrict__ status, const float* __restrict__ mu, int c,
-                     int32_t* __restrict__ labels,
-                     float* __restrict__ ub, float* __restrict__ lb,
-                     const RcRec* __restrict__ rc_list) {
+    k_search_recheck_dist(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
+                          const DevStatus* __restrict__ status, const float* __restrict__ mu, int c,
+                          const RcRec* __restrict__ rc_list, double* __restrict__ rc_dist,
+                          int64_t rc_cap) {
     __shared__ double red[kThreads / 32];
-    const int nrc = status->rechecked;
+    const int64_t nrc = min((int64_t)status->rechecked, rc_cap);
+    const int64_t pairs = nrc * c;
+    for (int64_t pr = blockIdx.x; pr < pairs; pr += gridDim.x) {
+        const int64_t k = pr / c;
+        const int ci = (int)(pr - k * c);
+        const RcRec& rec = rc_list[k];
+        if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;   // uniform over the CTA
+        const double dist = block_dist2_fp64<TY>(Y + (int64_t)rec.col * ldy, mu + (int64_t)ci * d, d, vec, red);
+        if (threadIdx.x == 0) rc_dist[pr] = dist;
+        __syncthreads();
+    }
+}
+
+template <typename TY>
+__global__ void __launch_bounds__(kThreads)
+    k_search_recheck_pick(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
+                          DevStatus* __restrict__ status, const float* __restrict__ mu, int c,
+                          int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
+                          const RcRec* __restrict__ rc_list, const double* __restrict__ rc_dist,
+                          int64_t rc_cap) {
+    __shared__ double red[kThreads / 32];
+    const int64_t nrc = status->rechecked;
     for (int64_t k = blockIdx.x; k < nrc; k += gridDim.x) {
         const RcRec& rec = rc_list[k];
         const int64_t col = rec.col;
         double best = INFINITY;
         int besti = INT_MAX;
-        const TY* y = Y + col * ldy;
-        for (int ci = 0; ci < c; ++ci) {
-            if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
-            const double dist = block_dist2_fp64<TY>(y, mu + (int64_t)ci * d, d, vec, red);
-            if (dist < best) {
-                best = dist;
-                besti = ci;
+        if (k < rc_cap) {
+            if (threadIdx.x == 0) {
+                for (int ci = 0; ci < c; ++ci) {
+                    if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
+                    const double dist = rc_dist[k * c + ci];
+                    if (dist < best) {
+                        best = dist;
+                        besti = ci;
+                    }
+                }
+            }
+        } else {
+            const TY* y = Y + col * ldy;
+            for (int ci = 0; ci < c; ++ci) {
+                if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
+                const double dist = block_dist2_fp64<TY>(y, mu + (int64_t)ci * d, d, vec, red);
+                if (dist < best) {
+                    best = dist;
+                    besti = ci;
+                }
             }
         }
         if (threadIdx.x == 0 && besti < c) {
@@ -1115,6 +1150,7 @@ TcPlan tc_plan(int64_t n, int64_t d, int c) {
     const int64_t slots = std::max<int64_t>(kTcMaxSplit, dp.cmax);
     t.gpart = (size_t)slots * t.Npad * t.tiles * kTcM;
     t.ynorm = (size_t)slots * t.tiles * kTcM;
+    t.rc_cap = std::min<int64_t>(n, 2048);
     return t;
 }
 
@@ -1131,7 +1167,8 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              const float* mu_hi, const float* mu_lo, int64_t dpad,
                              const float* mu_normf, const int32_t* counts, int c, int32_t* labels,
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
-                             int32_t* tile_count, RcRec* rc_list, bool vec, cudaStream_t st) {
+                             int32_t* tile_count, RcRec* rc_list, double* rc_dist, int64_t rc_cap,
+                             bool vec, cudaStream_t st) {
     const int Npad = tc_npad(c);
     cudaError_t e = cudaSuccess;
     // dense TMA path: FP32 operand with 16-byte aligned columns
@@ -1191,13 +1228,15 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
         });
         if (e != cudaSuccess) return e;
     }
-    count_launches(1);
+    count_launches(2);
     RESPCA_DISPATCH_X(dtype, TY, {
         // float4 rows need 16-byte aligned columns of Y and of the centroids (d % 4 == 0)
         const bool v4 = vec && sizeof(TY) == 4 && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
                         (reinterpret_cast<uintptr_t>(mu) % 16 == 0);
-        k_search_recheck<TY><<<num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu, c,
-                                                             labels, ub, lb, rc_list);
+        k_search_recheck_dist<TY><<<4 * num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu,
+                                                                    c, rc_list, rc_dist, rc_cap);
+        k_search_recheck_pick<TY><<<num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu, c,
+                                                                  labels, ub, lb, rc_list, rc_dist, rc_cap);
     });
     return cudaGetLastError();
 }

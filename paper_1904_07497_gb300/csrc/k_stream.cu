@@ -7,6 +7,7 @@
 // exact pruning of the K-means search) and the cluster sums of the NEXT
 // iteration's D under the current labels, which become the next centroids
 // whenever the p step keeps every label.
+#include <algorithm>
 #include <cfloat>
 
 #include "respca_internal.cuh"
@@ -337,24 +338,36 @@ __global__ void __launch_bounds__(kThreads)
     mu[(int64_t)i * d + r] = (float)(sums[(int64_t)i * d + r] * (1.0 / (double)cnt));
 }
 
-// Move the columns listed in `moved` between cluster sums: for each moved
-// column j (in list order, so the FP64 sums are deterministic) subtract its
-// values from its old cluster's sums and add them to the new one's.
+// Cluster sums after a Lloyd pass moved some columns: sums_i += (columns that
+// joined i) - (columns that left i).  k_moved lists each cluster's signed
+// contributions contiguously (bucket i = contrib[boff[i] .. boff[i+1])).  A
+// CTA takes 128 rows of one cluster and adds its bucket in double-float
+// FP32 (TwoSum: the running sum is hi + lo to about 2^-44), then makes one
+// FP64 update per row; FP64 adds per moved column would be bound by the slow
+// FP64 pipe.
+constexpr int kDeltaThreads = 128;
 template <int MODE, typename TX>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kDeltaThreads)
     k_delta_sums(const TX* __restrict__ X, int64_t ldx, const float* __restrict__ L, int64_t lds,
-                 const int4* __restrict__ moved, const DevStatus* __restrict__ status, int64_t d,
+                 const int2* __restrict__ contrib, const int32_t* __restrict__ boff, int c, int64_t d,
                  double* __restrict__ sums) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
     if (r >= d) return;
-    const int nm = status->moved;
-    for (int m = 0; m < nm; ++m) {
-        const int4 mv = moved[m];   // column, old label, new label
-        const int64_t j = mv.x;
-        const double v = (MODE == kSumX) ? (double)XLoad<TX>::one(X + j * ldx + r)
-                                         : (double)L[j * lds + r];
-        if (mv.y >= 0) sums[(int64_t)mv.y * d + r] -= v;
-        sums[(int64_t)mv.z * d + r] += v;
+    for (int i = blockIdx.y; i < c; i += gridDim.y) {
+        const int b0 = boff[i], b1 = boff[i + 1];
+        if (b0 == b1) continue;
+        float hi = 0.f, lo = 0.f;
+        for (int q = b0; q < b1; ++q) {
+            const int2 e = contrib[q];   // column, sign
+            const int64_t j = e.x;
+            float x = (MODE == kSumX) ? XLoad<TX>::one(X + j * ldx + r) : L[j * lds + r];
+            if (e.y < 0) x = -x;
+            const float t = hi + x;   // TwoSum(hi, x)
+            const float bp = t - hi;
+            lo += (hi - (t - bp)) + (x - bp);
+            hi = t;
+        }
+        sums[(int64_t)i * d + r] += (double)hi + (double)lo;
     }
 }
 
@@ -626,44 +639,116 @@ __global__ void __launch_bounds__(kThreads)
 
 // Columns whose label differs between `now` and `before`, in column order
 // (single CTA; deterministic), as (column, old, new) triples; the cluster
-// sizes follow the move.
-__global__ void __launch_bounds__(1024)
-    k_moved(const int32_t* __restrict__ now, const int32_t* __restrict__ before, int64_t n,
-            int4* __restrict__ moved, int32_t* __restrict__ counts, DevStatus* __restrict__ status) {
-    __shared__ int wcount[32];
-    __shared__ int base;
+// sizes follow the move.  Each thread takes kMovedK consecutive columns per
+// round, so a round covers 8192 columns with one block-wide scan.  The moves
+// are then bucketed by cluster as signed contributions (-1: left, +1:
+// joined) in a fixed order, for k_delta_sums.
+constexpr int kMovedThreads = 1024, kMovedK = 8;
+__global__ void __launch_bounds__(kMovedThreads)
+    k_moved(const int32_t* __restrict__ now, const int32_t* __restrict__ before, int64_t n, int c,
+            int4* __restrict__ moved, int2* __restrict__ contrib, int32_t* __restrict__ boff,
+            int32_t* __restrict__ counts, DevStatus* __restrict__ status) {
+    __shared__ int wsum[32];
+    __shared__ int base_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) base = 0;
+    if (threadIdx.x == 0) base_sh = 0;
     __syncthreads();
-    for (int64_t b0 = 0; b0 < n; b0 += blockDim.x) {
-        const int64_t j = b0 + threadIdx.x;
-        int a = -1, o = -1;
-        bool mv = false;
-        if (j < n) {
-            a = now[j];
-            o = before[j];
-            mv = a != o;
+    for (int64_t b0 = 0; b0 < n; b0 += (int64_t)kMovedThreads * kMovedK) {
+        const int64_t j0 = b0 + (int64_t)threadIdx.x * kMovedK;
+        int a[kMovedK], o[kMovedK];
+        int cnt = 0;
+#pragma unroll
+        for (int e = 0; e < kMovedK; ++e) {
+            const int64_t j = j0 + e;
+            a[e] = j < n ? now[j] : 0;
+            o[e] = j < n ? before[j] : 0;
+            cnt += (a[e] != o[e]) ? 1 : 0;
         }
-        const unsigned mask = __ballot_sync(0xffffffffu, mv);
-        if (lane == 0) wcount[warp] = __popc(mask);
+        int incl = cnt;   // inclusive scan over the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
         __syncthreads();
-        int off = 0;
-        for (int w = 0; w < warp; ++w) off += wcount[w];
-        if (mv) {
-            const int pos = base + off + __popc(mask & ((1u << lane) - 1u));
-            moved[pos] = make_int4((int)j, o, a, 0);
-            if (o >= 0) atomicSub(&counts[o], 1);
-            atomicAdd(&counts[a], 1);
+        if (warp == 0) {
+            int v = wsum[lane], inc = v;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += t;
+            }
+            wsum[lane] = inc - v;   // exclusive prefix of the warp totals
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int t = 0;
-            for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += wcount[w];
-            base += t;
+        const int base = base_sh;
+        int pos = base + wsum[warp] + incl - cnt;
+#pragma unroll
+        for (int e = 0; e < kMovedK; ++e) {
+            if (a[e] == o[e]) continue;
+            moved[pos++] = make_int4((int)(j0 + e), o[e], a[e], 0);
+            if (o[e] >= 0) atomicSub(&counts[o[e]], 1);
+            atomicAdd(&counts[a[e]], 1);
         }
+        __syncthreads();
+        if (threadIdx.x == kMovedThreads - 1) base_sh = pos;   // the last thread ends the round
         __syncthreads();
     }
-    if (threadIdx.x == 0) status->moved = base;
+    __syncthreads();
+    const int nm = base_sh;
+    if (threadIdx.x == 0) status->moved = nm;
+
+    // bucket the signed contributions by cluster: sizes, offsets, then a stable
+    // placement by one warp (chunk by chunk, lanes ranked by __match_any_sync)
+    __shared__ int off_sh[kMaxClusters + 1];
+    for (int i = threadIdx.x; i <= c; i += kMovedThreads) off_sh[i] = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m < nm; m += kMovedThreads) {
+        const int4 mv = moved[m];
+        if (mv.y >= 0) atomicAdd(&off_sh[mv.y], 1);
+        atomicAdd(&off_sh[mv.z], 1);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int carry = 0;
+        for (int b = 0; b < c; b += 32) {
+            const int v = (b + lane < c) ? off_sh[b + lane] : 0;
+            int inc = v;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += t;
+            }
+            if (b + lane < c) off_sh[b + lane] = carry + inc - v;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) off_sh[c] = carry;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= c; i += kMovedThreads) boff[i] = off_sh[i];
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned below = (1u << lane) - 1u;
+        for (int cb = 0; cb < nm; cb += 32) {
+            const int m = cb + lane;
+            const int4 mv = m < nm ? moved[m] : make_int4(0, -1, -1, 0);
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int key = side == 0 ? mv.y : mv.z;   // the cluster left, then the one joined
+                const bool has = key >= 0;
+                const unsigned act = __ballot_sync(0xffffffffu, has);
+                unsigned peers = 0u;
+                if (has) {
+                    peers = __match_any_sync(act, key);
+                    contrib[off_sh[key] + __popc(peers & below)] = make_int2(mv.x, side == 0 ? -1 : 1);
+                }
+                __syncwarp();
+                if (has && (peers & below) == 0u) off_sh[key] += __popc(peers);
+                __syncwarp();
+            }
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -806,19 +891,17 @@ cudaError_t launch_centroids_from_sums(const double* sums, const int32_t* counts
 }
 
 cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, const float* L,
-                              int64_t lds, const int4* moved, const DevStatus* status, int64_t d,
+                              int64_t lds, const int2* contrib, const int32_t* boff, int c, int64_t d,
                               double* sums, cudaStream_t st) {
     count_launches(1);
-    // small CTAs: the serial FP64 updates per row spread over every SM
-    constexpr int kDeltaThreads = 64;
-    const int grid = grid_for(d, kDeltaThreads);
+    const dim3 grid((unsigned)grid_for(d, kDeltaThreads), (unsigned)std::min(c, 64));
     if (mode == kSumL) {
-        k_delta_sums<kSumL, float><<<grid, kDeltaThreads, 0, st>>>(nullptr, 0, L, lds, moved, status, d,
+        k_delta_sums<kSumL, float><<<grid, kDeltaThreads, 0, st>>>(nullptr, 0, L, lds, contrib, boff, c, d,
                                                                    sums);
     } else {
         RESPCA_DISPATCH_X(dtype, TX, {
-            k_delta_sums<kSumX, TX><<<grid, kDeltaThreads, 0, st>>>((const TX*)X, ldx, nullptr, 0, moved,
-                                                                    status, d, sums);
+            k_delta_sums<kSumX, TX><<<grid, kDeltaThreads, 0, st>>>((const TX*)X, ldx, nullptr, 0, contrib,
+                                                                    boff, c, d, sums);
         });
     }
     return cudaGetLastError();
@@ -842,10 +925,11 @@ cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_
     return cudaGetLastError();
 }
 
-cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int4* moved,
-                         int32_t* counts, DevStatus* status, cudaStream_t st) {
+cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int c, int4* moved,
+                         int2* contrib, int32_t* boff, int32_t* counts, DevStatus* status,
+                         cudaStream_t st) {
     count_launches(1);
-    k_moved<<<1, 1024, 0, st>>>(now, before, n, moved, counts, status);
+    k_moved<<<1, kMovedThreads, 0, st>>>(now, before, n, c, moved, contrib, boff, counts, status);
     return cudaGetLastError();
 }
 

@@ -52,8 +52,8 @@ struct respca_ctx {
     DevBuf theta, mu, mu_norm2, mu_normf, pair_ss, sep2, perm, counts, tile_off, tiles, labels_prev,
         Dpart, own_part, norm_part, flag_list, seedD2, centers, seed_u, fro_part, status,
         hX, hL, hS, hp, hp0,
-        mu_next, mu_old, drift, ub, lb, dl_part, sums, moved, labels_pass,
-        mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count;
+        mu_next, mu_old, drift, ub, lb, dl_part, sums, moved, contrib, boff, labels_pass,
+        mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count, rc_dist;
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -134,6 +134,8 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
     CK(ensure(h->dl_part, sizeof(float) * (size_t)nch * n));
     CK(ensure(h->sums, sizeof(double) * (size_t)c * d));
     CK(ensure(h->moved, sizeof(int4) * n));
+    CK(ensure(h->contrib, sizeof(int2) * 2 * (size_t)n));
+    CK(ensure(h->boff, sizeof(int32_t) * ((size_t)c + 1)));
     CK(ensure(h->labels_pass, sizeof(int32_t) * n));
     if (c <= kTcMaxClusters) {
         const TcPlan tp = tc_plan(n, d, c);
@@ -142,6 +144,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
         CK(ensure(h->Gpart, sizeof(float) * tp.gpart));
         CK(ensure(h->ynorm_part, sizeof(float) * tp.ynorm));
         CK(ensure(h->tile_count, sizeof(int32_t) * tp.tiles));
+        CK(ensure(h->rc_dist, sizeof(double) * (size_t)tp.rc_cap * c));
         // per-tile arrival counters of the search kernels start every call at zero
         CK(cudaMemsetAsync(h->tile_count.p, 0, h->tile_count.bytes, h->stream));
     }
@@ -204,13 +207,14 @@ respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64
     if (c <= kTcMaxClusters && h->cfg.search_impl == 0) {
         const int Npad = tc_npad(c);
         const int64_t dpad = (d + 31) / 32 * 32;
+        const int64_t rc_cap = tc_plan(n, d, c).rc_cap;
         CK(launch_mu_split(P<float>(h->mu), c, d, Npad, dpad, P<float>(h->mu_hi), P<float>(h->mu_lo),
                            h->stream));
         CK(launch_search_tc(dtype, Y, ldy, d, n, list, ds, P<float>(h->mu), P<float>(h->mu_hi),
                             P<float>(h->mu_lo), dpad, P<float>(h->mu_normf), P<int32_t>(h->counts), c,
                             p, P<float>(h->ub), P<float>(h->lb), P<float>(h->Gpart),
                             P<float>(h->ynorm_part), P<int32_t>(h->tile_count), P<RcRec>(h->rc_list),
-                            vec, h->stream));
+                            P<double>(h->rc_dist), rc_cap, vec, h->stream));
     } else {
         CK(launch_assign(dtype, Y, ldy, d, n, list, P<float>(h->mu), P<float>(h->mu_normf),
                          P<int32_t>(h->counts), c, p, ds, h->stream, P<float>(h->ub), P<float>(h->lb)));
@@ -260,10 +264,10 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
         sc->assigned += h->hstat->flagged;
         sc->rechecked += h->hstat->rechecked;
         if (h->hstat->changed == 0 || sc->passes >= max_passes) break;
-        CK(launch_moved(p, P<int32_t>(h->labels_pass), n, P<int4>(h->moved), P<int32_t>(h->counts), ds,
-                        h->stream));
-        CK(launch_delta_sums(mode, dtype, Y, ldy, Lp, ldy, P<int4>(h->moved), ds, d, P<double>(h->sums),
-                             h->stream));
+        CK(launch_moved(p, P<int32_t>(h->labels_pass), n, c, P<int4>(h->moved), P<int2>(h->contrib),
+                        P<int32_t>(h->boff), P<int32_t>(h->counts), ds, h->stream));
+        CK(launch_delta_sums(mode, dtype, Y, ldy, Lp, ldy, P<int2>(h->contrib), P<int32_t>(h->boff), c,
+                             d, P<double>(h->sums), h->stream));
         CK(cudaMemcpyAsync(h->mu_old.p, h->mu.p, sizeof(float) * (size_t)c * d,
                            cudaMemcpyDeviceToDevice, h->stream));
         CK(launch_centroids_from_sums(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
@@ -637,8 +641,10 @@ respca_status respca_destroy(respca_handle h) {
                       &h->counts, &h->tile_off, &h->tiles, &h->labels_prev, &h->Dpart, &h->own_part,
                       &h->norm_part, &h->flag_list, &h->seedD2, &h->centers, &h->seed_u, &h->fro_part,
                       &h->status, &h->hX, &h->hL, &h->hS, &h->hp, &h->hp0, &h->mu_next, &h->mu_old,
-                      &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->labels_pass,
-                      &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count};
+                      &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->contrib, &h->boff,
+                      &h->labels_pass,
+                      &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count,
+                      &h->rc_dist};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->hstat) cudaFreeHost(h->hstat);

@@ -97,7 +97,7 @@ cudaError_t launch_centroids_from_sums(const double* sums, const int32_t* counts
                                        float* mu, cudaStream_t st);
 
 cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, const float* L,
-                              int64_t lds, const int4* moved, const DevStatus* status, int64_t d,
+                              int64_t lds, const int2* contrib, const int32_t* boff, int c, int64_t d,
                               double* sums, cudaStream_t st);
 
 cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t d,
@@ -108,8 +108,9 @@ cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_
                                const double* sep2, double safety, const double* drift, float* ub,
                                float* lb, int32_t* flag_list, DevStatus* status, cudaStream_t st);
 
-cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int4* moved,
-                         int32_t* counts, DevStatus* status, cudaStream_t st);
+cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int c, int4* moved,
+                         int2* contrib, int32_t* boff, int32_t* counts, DevStatus* status,
+                         cudaStream_t st);
 
 cudaError_t launch_mu_norms(const float* mu, int c, int64_t d, double* mu_norm2, float* mu_normf,
                             cudaStream_t st);
@@ -179,6 +180,7 @@ struct TcPlan {
     size_t gpart;      // floats of partial products
     size_t ynorm;      // floats of partial squared column norms
     int64_t tiles;     // 128-column tiles
+    int64_t rc_cap;    // queued near ties whose candidate distances run spread over all SMs
 };
 TcPlan tc_plan(int64_t n, int64_t d, int c);
 cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
@@ -186,7 +188,8 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              const float* mu_hi, const float* mu_lo, int64_t dpad,
                              const float* mu_normf, const int32_t* counts, int c, int32_t* labels,
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
-                             int32_t* tile_count, RcRec* rc_list, bool vec, cudaStream_t st);
+                             int32_t* tile_count, RcRec* rc_list, double* rc_dist, int64_t rc_cap,
+                             bool vec, cudaStream_t st);
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float warp_sum(float v) {
