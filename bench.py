@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-6 rel. err & per-iter HBM GB/s vs peak; BF16+learned vs plain FP32"
 FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_ELEM_FP32 = 28   # read X, S, Theta, L_prev; write L, S, Theta (4 B each)
+SEARCH_BYTES_PER_ELEM = 4  # the all-column search reads the FP32 operand L (or X) once
 
 WORKLOADS = {
     # name: (d, n, rank, sparsity, c)
@@ -46,7 +47,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4"])
+    ap.add_argument("--lanes", type=int, default=8, help="c4: concurrent lanes of the batched solve")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -215,10 +217,10 @@ def run_gpu(args, rank, world, local_rank):
     S = torch.empty((n, d), device=dev).T
     p = torch.empty(n, device=dev, dtype=torch.int32)
     stream = torch.cuda.current_stream(dev)
-    solver = respca.Solver(seed=args.seed, timing=True, stream=stream, device=local_rank)
+    solver = respca.Solver(seed=args.seed, timing=False, stream=stream, device=local_rank)
 
-    def one():
-        return respca.respca_solve(solver.h, X, c, L, S, p, tol=args.tol, max_iter=500)
+    def one(h=None):
+        return respca.respca_solve(h or solver.h, X, c, L, S, p, tol=args.tol, max_iter=500)
 
     for _ in range(args.warmup):
         one()
@@ -247,14 +249,38 @@ def run_gpu(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     ms_per_step = t.item() / args.steps
 
-    fused_ms = sum(s["ms_fused"] for s in stats)
-    fused_n = sum(s["fused_launches"] for s in stats)
     iters = [s["iters"] for s in stats]
     launches = sum(s["kernel_launches"] for s in stats)
-    bytes_per_launch = BYTES_PER_ELEM_FP32 * d * n
-    achieved = bytes_per_launch / (fused_ms / fused_n / 1e3) / 1e9
+    # per-kernel durations from one more solve with the library's event timing on
+    # (kept out of the timed region: the events add host work)
+    tsolver = respca.Solver(seed=args.seed, timing=True, stream=stream, device=local_rank)
+    ts = one(tsolver.h)
+    tsolver.close()
     peak, peak_kind = measured_peak()
-    traffic = kernel_traffic("k_stream.cu", f"k_iteration_{args.workload}.txt")
+    fused_avg = ts["ms_fused"] / max(1, ts["fused_launches"])
+    fused_bytes = BYTES_PER_ELEM_FP32 * d * n
+    fused_gbs = fused_bytes / (fused_avg / 1e3) / 1e9
+    roof_fused = {"bound": "hbm", "kernel": "k_iteration (fused ALM iteration)",
+                  "achieved": round(fused_gbs, 1), "peak": peak, "unit": "GB/s",
+                  "frac": round(fused_gbs / peak, 4), "peak_source": peak_kind,
+                  "traffic": kernel_traffic("k_iteration.cu", f"k_iteration_{args.workload}.txt"),
+                  "algorithmic_bytes_per_launch": fused_bytes, "avg_launch_ms": round(fused_avg, 4),
+                  "launches": ts["fused_launches"], "total_ms": round(ts["ms_fused"], 3)}
+    rooflines = [roof_fused]
+    if ts["dense_passes"] > 0:
+        dense_avg = ts["ms_dense"] / ts["dense_passes"]
+        dense_bytes = SEARCH_BYTES_PER_ELEM * d * n
+        dense_gbs = dense_bytes / (dense_avg / 1e3) / 1e9
+        flops = 2.0 * c * d * n
+        rooflines.append({
+            "bound": "hbm", "kernel": "k_search_dense (tensor-core nearest-centroid search, all columns)",
+            "achieved": round(dense_gbs, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(dense_gbs / peak, 4), "peak_source": peak_kind,
+            "traffic": kernel_traffic("k_search_tc.cu", f"k_search_dense_{args.workload}.txt"),
+            "algorithmic_bytes_per_launch": dense_bytes, "avg_launch_ms": round(dense_avg, 4),
+            "algorithmic_tflops": round(flops / (dense_avg / 1e3) / 1e12, 2),
+            "launches": ts["dense_passes"], "total_ms": round(ts["ms_dense"], 3)})
+    dominant = max(rooflines, key=lambda r: r["total_ms"])
 
     e2e = None
     if not args.no_e2e:
@@ -293,21 +319,103 @@ def run_gpu(args, rank, world, local_rank):
         "config": workload_config(args.workload, args.tol),
         "iters": iters, "converged": last["converged"], "err": last["err"],
         "ms_init": round(last["ms_init"], 3),
-        "per_iter_hbm_gbs": round(achieved, 1),
-        "roofline": {"bound": "hbm", "kernel": "k_iteration (fused ALM iteration)",
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "avg_launch_ms": round(fused_ms / fused_n, 4)},
+        "per_iter_hbm_gbs": roof_fused["achieved"],
+        "roofline": dominant,
+        "rooflines": rooflines,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "label_changes": last["label_changes"], "lloyd_passes": last["lloyd_passes"],
         "assigned_columns": last["assigned_columns"],
     }
 
 
+# ---------------------------------------------------------------- batched workload
+C4_COUNT, C4_SEED = 256, 0
+
+
+def run_batched(args, rank, world, local_rank):
+    """256 uneven problems (d log-uniform in [200, 4000], n in [100, 2000],
+    rank 2..20 = c, sparsity 0.01..0.2) solved to tol in one batched call on
+    concurrent lanes, against the same problems one after another.  Every
+    rank solves its own batch (seeds differ by rank)."""
+    import numpy as np
+    import torch
+    from paper_1904_07497_gb300 import respca, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    entries = synth.batch_table(C4_COUNT, seed=C4_SEED + rank)
+    probs = []
+    elements = 0
+    for e in entries:
+        pr = synth.batch_problem(e)
+        d, n = pr.X.shape
+        elements += d * n
+        probs.append(dict(X=torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(dev).T, c=e.r,
+                          L=torch.empty((n, d), device=dev).T, S=torch.empty((n, d), device=dev).T,
+                          p=torch.empty(n, device=dev, dtype=torch.int32), tol=args.tol, max_iter=500))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(lanes, steps, warmup):
+        solver = respca.Solver(seed=args.seed, stream=stream, device=local_rank, batch_lanes=lanes)
+        for _ in range(warmup):
+            respca.respca_solve_batched(solver.h, probs)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            st = respca.respca_solve_batched(solver.h, probs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        solver.close()
+        t = torch.tensor([e0.elapsed_time(e1) / steps], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return t.item(), st
+
+    gpu_index = local_rank
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    ms_batched, st = timed(args.lanes, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_loop, st_loop = timed(1, 1, 1)
+    iters = [s["iters"] for s in st]
+    same = all(a["iters"] == b["iters"] and a["err"] == b["err"] for a, b in zip(st, st_loop))
+    stream_bytes = sum(28 * q["X"].shape[0] * q["X"].shape[1] * s["iters"] for q, s in zip(probs, st))
+    peak, peak_kind = measured_peak()
+    agg = stream_bytes / (ms_batched / 1e3) / 1e9
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": round(ms_batched, 3), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_batched, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded numpy PCG64)",
+        "config": {"workload": f"batched: {C4_COUNT} problems, d log-uniform [200,4000], n log-uniform "
+                               f"[100,2000], rank 2..20 (= c), sparsity U[0.01,0.2] +-1, tol={args.tol:g}",
+                   "problems": C4_COUNT, "elements": elements, "lanes": args.lanes,
+                   "l2": "most problems are L2-resident; the batch as a whole is not"},
+        "loop_ms": round(ms_loop, 3), "speedup_vs_loop": round(ms_loop / ms_batched, 2),
+        "results_equal_to_loop": same, "iters_total": sum(iters), "converged": sum(s["converged"] for s in st),
+        "roofline": {"bound": "hbm", "kernel": "aggregate: 28 B x elements x iterations of the fused "
+                     "iteration over the batch, divided by the batch wall time (not a single kernel)",
+                     "achieved": round(agg, 1), "peak": peak, "unit": "GB/s", "frac": round(agg / peak, 4),
+                     "peak_source": peak_kind, "traffic": None},
+        "cpu_baseline": None, "e2e": None,
+        "gpu_launches": sum(s["kernel_launches"] for s in st), "clocks": clk,
+    }
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    if args.workload == "c4":
+        return {"impl": "reference", "metric": METRIC,
+                "unavailable": "no oracle arm for the batched workload; its GPU line carries the "
+                               "one-at-a-time loop (loop_ms) beside the batched time"}
     v_steps = []
     v, times, sample = cpu_sample(args.workload, args.seed, steps=args.steps, warmup=args.warmup)
     d, n, r, sp, c = WORKLOADS[args.workload]
@@ -336,7 +444,8 @@ def main():
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
-        out = run_gpu(args, rank, world, local_rank)
+        out = run_batched(args, rank, world, local_rank) if args.workload == "c4" else \
+            run_gpu(args, rank, world, local_rank)
     if world > 1 and args.impl == "gpu":
         import torch
         torch.distributed.destroy_process_group()

@@ -68,7 +68,8 @@ typedef struct {
     int32_t ramp_skip;       /* 1 (default): compute the leading iterations in which S stays 0
                                 and no label moves in closed form (exact; see respca_solve);
                                 0: run every iteration */
-    int32_t reserved2;
+    int32_t batch_lanes;     /* respca_solve_batched: problems solved at once, each lane with its
+                                own stream and workspace (0 = default 8; 1 = one after another) */
 } respca_config;
 
 typedef struct {
@@ -90,7 +91,10 @@ typedef struct {
     float ms_total;          /* wall time of the call on the stream (CUDA events) */
     float ms_init;           /* part of ms_total spent before the first iteration */
     float ms_fused;          /* summed duration of the fused iteration kernel (cfg.timing = 1) */
-    float reserved;
+    float ms_dense;          /* summed duration of the all-column tensor-core search kernel over
+                                the passes in which it ran (cfg.timing = 1) */
+    int32_t dense_passes;    /* passes in which that kernel searched every column */
+    int32_t reserved;
 } respca_stats;
 
 /* Optional warm start / checkpoint-resume state (the paper starts from zero;
@@ -188,8 +192,16 @@ respca_status respca_init_labels(respca_handle h, int32_t x_dtype, const void *X
                                  int32_t *passes);
 
 /* Solve `batch` independent problems (device pointers as in respca_solve).
- * stats: optional host array of `batch` entries.  The first failing problem's
- * status is returned; later problems are still attempted. */
+ * The problems run concurrently on cfg.batch_lanes lanes: each lane is an
+ * internal solver with its own non-blocking stream and workspace, driven by
+ * its own host thread, taking the largest remaining problem (d * n) next.
+ * Every problem runs exactly the single-matrix path, so its results equal
+ * those of respca_solve on it.  Work already queued on cfg.stream is waited
+ * for first, and cfg.stream waits for the lanes when the call returns (it
+ * blocks until all problems are done).  stats: optional host array of `batch`
+ * entries.  The lowest-index failing problem's status is returned; the other
+ * problems are still attempted.  The handle is not thread-safe; the lanes are
+ * its own. */
 respca_status respca_solve_batched(respca_handle h, int32_t batch, const respca_problem *probs,
                                    respca_stats *stats);
 

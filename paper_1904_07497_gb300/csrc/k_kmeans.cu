@@ -455,8 +455,7 @@ cudaError_t launch_sort_labels(const int32_t* labels, int64_t n, int c, int32_t*
     count_launches(1);
     const size_t smem = sizeof(int32_t) * (size_t)(3 * c + 1);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_sort_labels,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_sort_labels));
         if (e != cudaSuccess) return e;
     }
     k_sort_labels<<<1, kSortThreads, smem, st>>>(labels, n, c, perm, counts, tile_off, tiles, status);
@@ -477,7 +476,7 @@ cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int6
     const int grid = grid_for(n, kAsgCols);
     cudaError_t e = cudaSuccess;
     RESPCA_DISPATCH_X(dtype, TY, {
-        e = cudaFuncSetAttribute(k_assign<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_assign<TY>));
         if (e == cudaSuccess)
             k_assign<TY><<<grid, kThreads, smem, st>>>((const TY*)Y, ldy, d, n, list, mu, mu_normf,
                                                        counts, c, labels, status, ub, lb);

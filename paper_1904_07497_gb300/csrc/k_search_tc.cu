@@ -39,6 +39,8 @@
 #include <cfloat>
 #include <climits>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "respca_internal.cuh"
 
@@ -1139,6 +1141,28 @@ DensePlan dense_plan(int64_t n, int64_t d, int Npad, int r_pref = 4, int ys_pref
 
 }  // namespace
 
+cudaError_t allow_max_dynamic_smem(const void* func) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto& d : done)
+        if (d.first == func && d.second == dev) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    done.emplace_back(func, dev);
+    return cudaSuccess;
+}
+
 int tc_npad(int c) { return ((c + 15) / 16) * 16; }
 
 TcPlan tc_plan(int64_t n, int64_t d, int c) {
@@ -1168,7 +1192,8 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              const float* mu_normf, const int32_t* counts, int c, int32_t* labels,
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
                              int32_t* tile_count, RcRec* rc_list, double* rc_dist, int64_t rc_cap,
-                             bool vec, cudaStream_t st) {
+                             bool vec, cudaStream_t st, cudaEvent_t ev_dense0, cudaEvent_t ev_dense1,
+                             bool* dense_launched_out) {
     const int Npad = tc_npad(c);
     cudaError_t e = cudaSuccess;
     // dense TMA path: FP32 operand with 16-byte aligned columns
@@ -1200,13 +1225,14 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             a.tmem_cols = dp.tmem_cols;
             a.use_list = list ? 1 : 0;
             a.list_min = list_max + 1;
-            e = cudaFuncSetAttribute(k_search_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)dp.smem);
+            e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_search_dense));
             if (e != cudaSuccess) return e;
             count_launches(1);
+            if (ev_dense0) cudaEventRecord(ev_dense0, st);
             k_search_dense<<<dp.G, kDnThreads, dp.smem, st>>>(tmY, tmBh, tmBl, a, status, mu_normf,
                                                               counts, c, labels, ub, lb, Gpart,
                                                               ynorm_part, tile_count, rc_list);
+            if (ev_dense1) cudaEventRecord(ev_dense1, st);
             dense_launched = true;
         }
     }
@@ -1219,7 +1245,7 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
         count_launches(1);
         RESPCA_DISPATCH_X(dtype, TY, {
             auto kern = vec ? k_search_list<TY, true> : k_search_list<TY, false>;
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
             if (e == cudaSuccess)
                 kern<<<grid, kTcThreads, smem, st>>>((const TY*)Y, ldy, d, n, list, lmax, status, mu_hi,
                                                      mu_lo, dpad, Npad, kTcMaxSplit, mu_normf, counts,
@@ -1228,6 +1254,7 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
         });
         if (e != cudaSuccess) return e;
     }
+    if (dense_launched_out) *dense_launched_out = dense_launched;
     count_launches(2);
     RESPCA_DISPATCH_X(dtype, TY, {
         // float4 rows need 16-byte aligned columns of Y and of the centroids (d % 4 == 0)

@@ -9,12 +9,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/respca.h"
@@ -45,6 +47,8 @@ struct DevBuf {
 struct respca_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;      // a batch lane's stream, created and destroyed with it
+    std::vector<respca_ctx*> lanes;         // batch lanes (respca_solve_batched), made on first use
     respca_config cfg{};
     std::string last_error;
 
@@ -58,6 +62,10 @@ struct respca_ctx {
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evk0 = nullptr, evk1 = nullptr;
+    cudaEvent_t evd0 = nullptr, evd1 = nullptr;   // around the all-column search (timing mode)
+    bool dense_recorded = false;                  // evd0 / evd1 bracket the last search's dense launch
+    float ms_dense = 0.f;                         // per-solve accumulators of that kernel's time
+    int32_t dense_passes = 0;
 };
 
 namespace {
@@ -210,15 +218,31 @@ respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64
         const int64_t rc_cap = tc_plan(n, d, c).rc_cap;
         CK(launch_mu_split(P<float>(h->mu), c, d, Npad, dpad, P<float>(h->mu_hi), P<float>(h->mu_lo),
                            h->stream));
+        const bool timing = h->cfg.timing != 0;
         CK(launch_search_tc(dtype, Y, ldy, d, n, list, ds, P<float>(h->mu), P<float>(h->mu_hi),
                             P<float>(h->mu_lo), dpad, P<float>(h->mu_normf), P<int32_t>(h->counts), c,
                             p, P<float>(h->ub), P<float>(h->lb), P<float>(h->Gpart),
                             P<float>(h->ynorm_part), P<int32_t>(h->tile_count), P<RcRec>(h->rc_list),
-                            P<double>(h->rc_dist), rc_cap, vec, h->stream));
+                            P<double>(h->rc_dist), rc_cap, vec, h->stream, timing ? h->evd0 : nullptr,
+                            timing ? h->evd1 : nullptr, timing ? &h->dense_recorded : nullptr));
     } else {
         CK(launch_assign(dtype, Y, ldy, d, n, list, P<float>(h->mu), P<float>(h->mu_normf),
                          P<int32_t>(h->counts), c, p, ds, h->stream, P<float>(h->ub), P<float>(h->lb)));
     }
+    return RESPCA_OK;
+}
+
+// Timing mode: after the status of a search pass is read, adds the dense
+// kernel's duration if it searched every column in this pass (no queue given,
+// or a queue longer than n / 4: otherwise that kernel returned at once).
+respca_status account_dense(respca_ctx* h, bool list_given, int64_t n) {
+    if (!h->dense_recorded) return RESPCA_OK;
+    h->dense_recorded = false;
+    if (list_given && (int64_t)h->hstat->flagged <= n / 4) return RESPCA_OK;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->evd0, h->evd1));
+    h->ms_dense += ms;
+    h->dense_passes += 1;
     return RESPCA_OK;
 }
 
@@ -259,6 +283,8 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
         respca_status rs = search(h, dtype, Y, ldy, d, n, P<int32_t>(h->flag_list), c, p, vec);
         if (rs != RESPCA_OK) return rs;
         rs = read_status(h);
+        if (rs != RESPCA_OK) return rs;
+        rs = account_dense(h, true, n);
         if (rs != RESPCA_OK) return rs;
         sc->passes += 1;
         sc->assigned += h->hstat->flagged;
@@ -310,6 +336,8 @@ respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out
     respca_status rs = search(h, pb.dtype, pb.X, pb.ldx, pb.d, pb.n, nullptr, c, pb.p, pb.vec);
     if (rs != RESPCA_OK) return rs;
     rs = read_status(h);
+    if (rs != RESPCA_OK) return rs;
+    rs = account_dense(h, false, pb.n);
     if (rs != RESPCA_OK) return rs;
     sc.passes = 1;
     if (h->hstat->changed > 0 && km > 1) {
@@ -366,6 +394,9 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     respca_stats out{};
     const int64_t launches0 = t_kernel_launches;
     const bool timing = h->cfg.timing != 0;
+    h->ms_dense = 0.f;
+    h->dense_passes = 0;
+    h->dense_recorded = false;
     CK(cudaEventRecord(h->ev0, h->stream));
     DevStatus* ds = P<DevStatus>(h->status);
     CK(cudaMemsetAsync(ds, 0, sizeof(DevStatus), h->stream));
@@ -425,6 +456,10 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         out.converged = 1;
         out.rho_final = rho;
         out.kernel_launches = t_kernel_launches - launches0;
+        out.ms_dense = h->ms_dense;
+        out.dense_passes = h->dense_passes;
+    out.ms_dense = h->ms_dense;
+    out.dense_passes = h->dense_passes;
         cudaEventElapsedTime(&out.ms_total, h->ev0, h->ev1);
         if (warm) warm->rho = rho;
         if (stats) *stats = out;
@@ -531,6 +566,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         if (rs != RESPCA_OK) return rs;
         rs = read_status(h);
         if (rs != RESPCA_OK) return rs;
+        rs = account_dense(h, true, n);
+        if (rs != RESPCA_OK) return rs;
         if (timing) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, h->evk0, h->evk1));
@@ -580,6 +617,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     out.label_changes = h->hstat->label_changes;
     out.rho_final = rho;
     out.kernel_launches = t_kernel_launches - launches0;
+    out.ms_dense = h->ms_dense;
+    out.dense_passes = h->dense_passes;
     cudaEventElapsedTime(&out.ms_total, h->ev0, h->ev1);
     cudaEventElapsedTime(&out.ms_init, h->ev0, h->ev2);
     if (warm) warm->rho = rho;
@@ -624,7 +663,8 @@ respca_status respca_create(respca_handle* out, const respca_config* cfg) {
     if (cudaMallocHost(&h->hstat, sizeof(DevStatus)) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
         cudaEventCreate(&h->ev2) != cudaSuccess || cudaEventCreate(&h->evk0) != cudaSuccess ||
-        cudaEventCreate(&h->evk1) != cudaSuccess) {
+        cudaEventCreate(&h->evk1) != cudaSuccess || cudaEventCreate(&h->evd0) != cudaSuccess ||
+        cudaEventCreate(&h->evd1) != cudaSuccess) {
         respca_destroy(h);
         return RESPCA_ERR_OOM;
     }
@@ -634,6 +674,8 @@ respca_status respca_create(respca_handle* out, const respca_config* cfg) {
 
 respca_status respca_destroy(respca_handle h) {
     if (!h) return RESPCA_OK;
+    for (respca_ctx* lane : h->lanes) respca_destroy(lane);
+    h->lanes.clear();
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
@@ -654,6 +696,9 @@ respca_status respca_destroy(respca_handle h) {
     if (h->ev2) cudaEventDestroy(h->ev2);
     if (h->evk0) cudaEventDestroy(h->evk0);
     if (h->evk1) cudaEventDestroy(h->evk1);
+    if (h->evd0) cudaEventDestroy(h->evd0);
+    if (h->evd1) cudaEventDestroy(h->evd1);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
     return RESPCA_OK;
 }
@@ -728,15 +773,81 @@ respca_status respca_init_labels(respca_handle h, int32_t x_dtype, const void* X
 respca_status respca_solve_batched(respca_handle h, int32_t batch, const respca_problem* probs,
                                    respca_stats* stats) {
     if (!h || batch < 0 || (batch > 0 && !probs)) return RESPCA_ERR_INVALID_ARG;
-    respca_status first = RESPCA_OK;
-    for (int32_t b = 0; b < batch; ++b) {
+    if (batch == 0) return RESPCA_OK;
+    auto solve_one = [&](respca_ctx* ctx, int32_t b) {
         const respca_problem& q = probs[b];
-        respca_status rs = respca_solve(h, q.x_dtype, q.X, q.d, q.n, q.ldx, q.lambda, q.c, q.tol,
-                                        q.max_iter, q.p0, q.L, q.S, q.lds, q.p, nullptr,
-                                        stats ? &stats[b] : nullptr);
-        if (rs != RESPCA_OK && first == RESPCA_OK) first = rs;
+        return respca_solve(ctx, q.x_dtype, q.X, q.d, q.n, q.ldx, q.lambda, q.c, q.tol, q.max_iter,
+                            q.p0, q.L, q.S, q.lds, q.p, nullptr, stats ? &stats[b] : nullptr);
+    };
+    const int lanes = std::min<int>(h->cfg.batch_lanes > 0 ? h->cfg.batch_lanes : 8, batch);
+    if (lanes <= 1) {
+        respca_status first = RESPCA_OK;
+        for (int32_t b = 0; b < batch; ++b) {
+            const respca_status rs = solve_one(h, b);
+            if (rs != RESPCA_OK && first == RESPCA_OK) first = rs;
+        }
+        return first;
     }
-    return first;
+    if (cudaSetDevice(h->device) != cudaSuccess) return RESPCA_ERR_CUDA;
+    while ((int)h->lanes.size() < lanes) {
+        respca_config lc = h->cfg;
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return RESPCA_ERR_CUDA;
+        lc.stream = s;
+        lc.device = h->device;
+        respca_handle lane = nullptr;
+        const respca_status rs = respca_create(&lane, &lc);
+        if (rs != RESPCA_OK) {
+            cudaStreamDestroy(s);
+            return rs;
+        }
+        lane->own_stream = s;
+        h->lanes.push_back(lane);
+    }
+    // largest problems first, so the lanes finish together
+    std::vector<int32_t> order(batch);
+    for (int32_t b = 0; b < batch; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return probs[x].d * probs[x].n > probs[y].d * probs[y].n;
+    });
+    // the lanes start after the work already queued on the caller's stream
+    if (cudaEventRecord(h->ev0, h->stream) != cudaSuccess) return RESPCA_ERR_CUDA;
+    for (int w = 0; w < lanes; ++w)
+        if (cudaStreamWaitEvent(h->lanes[w]->stream, h->ev0, 0) != cudaSuccess) return RESPCA_ERR_CUDA;
+    std::vector<respca_status> result(batch, RESPCA_OK);
+    std::vector<std::string> message(batch);
+    std::atomic<int32_t> next{0};
+    auto run_lane = [&](int w) {
+        cudaSetDevice(h->device);
+        respca_ctx* ctx = h->lanes[w];
+        for (;;) {
+            const int32_t k = next.fetch_add(1);
+            if (k >= batch) break;
+            result[order[k]] = solve_one(ctx, order[k]);
+            if (result[order[k]] != RESPCA_OK) message[order[k]] = ctx->last_error;
+        }
+    };
+    std::vector<std::thread> threads;
+    try {
+        for (int w = 1; w < lanes; ++w) threads.emplace_back(run_lane, w);
+    } catch (...) {
+        // fewer host threads than lanes: the remaining lanes' share goes to the others
+    }
+    run_lane(0);
+    for (std::thread& t : threads) t.join();
+    // the caller's stream sees the lanes' work as done
+    for (int w = 0; w < lanes; ++w) {
+        if (cudaEventRecord(h->lanes[w]->ev1, h->lanes[w]->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(h->stream, h->lanes[w]->ev1, 0) != cudaSuccess)
+            return RESPCA_ERR_CUDA;
+    }
+    for (int32_t b = 0; b < batch; ++b) {
+        if (result[b] != RESPCA_OK) {
+            h->last_error = std::string("problem ") + std::to_string(b) + ": " + message[b];
+            return result[b];
+        }
+    }
+    return RESPCA_OK;
 }
 
 const char* respca_status_string(respca_status s) {

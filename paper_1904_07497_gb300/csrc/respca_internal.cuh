@@ -171,6 +171,12 @@ struct RcRec {
     int32_t pad[3];
 };
 int tc_npad(int c);
+// Raises a kernel's dynamic shared memory cap to the device's opt-in limit,
+// once per (kernel, device).  The cap then no longer depends on the launch,
+// so launches of one kernel from several host threads, each with its own
+// size, cannot see the cap lowered by another thread between setting it and
+// launching.
+cudaError_t allow_max_dynamic_smem(const void* func);
 cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
                             float* mu_lo, cudaStream_t st);
 // Workspace sizes of the tensor-core search for an n-column, d-row operand.
@@ -189,7 +195,8 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              const float* mu_normf, const int32_t* counts, int c, int32_t* labels,
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
                              int32_t* tile_count, RcRec* rc_list, double* rc_dist, int64_t rc_cap,
-                             bool vec, cudaStream_t st);
+                             bool vec, cudaStream_t st, cudaEvent_t ev_dense0 = nullptr,
+                             cudaEvent_t ev_dense1 = nullptr, bool* dense_launched = nullptr);
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float warp_sum(float v) {

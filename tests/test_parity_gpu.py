@@ -281,6 +281,38 @@ def test_batched_matches_single(solver):
         np.testing.assert_array_equal(_host(q["L"]), s["L"])
 
 
+def _batch(entries, lanes, tol, max_iter):
+    from paper_1904_07497_gb300 import respca
+    s = respca.Solver(seed=7, batch_lanes=lanes)
+    probs = []
+    for e in entries:
+        pr = synth.batch_problem(e)
+        d, n = pr.X.shape
+        probs.append(dict(X=_dev(pr.X), c=e.r, L=torch.zeros((n, d), device="cuda").T,
+                          S=torch.zeros((n, d), device="cuda").T,
+                          p=torch.zeros(n, device="cuda", dtype=torch.int32), tol=tol,
+                          max_iter=max_iter))
+    stats = respca.respca_solve_batched(s.h, probs)
+    torch.cuda.synchronize()
+    out = [(q["p"].cpu().numpy(), _host(q["L"]), _host(q["S"]), st) for q, st in zip(probs, stats)]
+    s.close()
+    return out
+
+
+def test_batched_lanes_match_one_at_a_time():
+    """Concurrent lanes (each with its own stream and workspace, problems taken
+    largest first) give every problem exactly its one-at-a-time result."""
+    entries = synth.batch_table(12, seed=5, d_range=(100, 900), n_range=(60, 500))
+    seq = _batch(entries, 1, 1e-6, 300)
+    par = _batch(entries, 5, 1e-6, 300)
+    for a, b in zip(seq, par):
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+        np.testing.assert_array_equal(a[2], b[2])
+        assert a[3]["iters"] == b[3]["iters"] and a[3]["converged"] == b[3]["converged"] == 1
+        assert a[3]["err"] == b[3]["err"]
+
+
 # ------------------------------------------------------------------ search paths
 def _solve_impl(impl, X32, c, T, p0=None, seed=4, dtype=None):
     from paper_1904_07497_gb300 import respca
