@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4"])
     ap.add_argument("--lanes", type=int, default=8, help="c4: concurrent lanes of the batched solve")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="1: BF16 storage of X and the state until err <= 1e-2, then FP32")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -217,7 +219,8 @@ def run_gpu(args, rank, world, local_rank):
     S = torch.empty((n, d), device=dev).T
     p = torch.empty(n, device=dev, dtype=torch.int32)
     stream = torch.cuda.current_stream(dev)
-    solver = respca.Solver(seed=args.seed, timing=False, stream=stream, device=local_rank)
+    solver = respca.Solver(seed=args.seed, timing=False, stream=stream, device=local_rank,
+                           precision=args.precision)
 
     def one(h=None):
         return respca.respca_solve(h or solver.h, X, c, L, S, p, tol=args.tol, max_iter=500)
@@ -253,12 +256,15 @@ def run_gpu(args, rank, world, local_rank):
     launches = sum(s["kernel_launches"] for s in stats)
     # per-kernel durations from one more solve with the library's event timing on
     # (kept out of the timed region: the events add host work)
-    tsolver = respca.Solver(seed=args.seed, timing=True, stream=stream, device=local_rank)
+    tsolver = respca.Solver(seed=args.seed, timing=True, stream=stream, device=local_rank,
+                            precision=args.precision)
     ts = one(tsolver.h)
     tsolver.close()
     peak, peak_kind = measured_peak()
     fused_avg = ts["ms_fused"] / max(1, ts["fused_launches"])
-    fused_bytes = BYTES_PER_ELEM_FP32 * d * n
+    # bf16-phase launches move 14 B per element (X, L, S, Theta in BF16), FP32 ones 28 B
+    nf, nb = max(1, ts["fused_launches"]), ts["bf16_iters"]
+    fused_bytes = int(d * n * (BYTES_PER_ELEM_FP32 * (nf - nb) + (BYTES_PER_ELEM_FP32 // 2) * nb) / nf)
     fused_gbs = fused_bytes / (fused_avg / 1e3) / 1e9
     roof_fused = {"bound": "hbm", "kernel": "k_iteration (fused ALM iteration)",
                   "achieved": round(fused_gbs, 1), "peak": peak, "unit": "GB/s",
@@ -316,8 +322,11 @@ def run_gpu(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded numpy PCG64)",
-        "config": workload_config(args.workload, args.tol),
+        "config": dict(workload_config(args.workload, args.tol),
+                       storage="bf16 phase (X, L, S, Theta in BF16) then FP32" if args.precision
+                       else "fp32"),
         "iters": iters, "converged": last["converged"], "err": last["err"],
+        "bf16_iters": last["bf16_iters"],
         "ms_init": round(last["ms_init"], 3),
         "per_iter_hbm_gbs": roof_fused["achieved"],
         "roofline": dominant,

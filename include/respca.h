@@ -70,6 +70,14 @@ typedef struct {
                                 0: run every iteration */
     int32_t batch_lanes;     /* respca_solve_batched: problems solved at once, each lane with its
                                 own stream and workspace (0 = default 8; 1 = one after another) */
+    int32_t precision;       /* 0 (default): FP32 state throughout.  1: a bf16 phase first --
+                                L, S, Theta (and an FP32 X, copied once) stored in BF16 in the
+                                workspace, arithmetic in FP32, 14 instead of 28 bytes per
+                                element and iteration -- until err <= switch_tol or err stops
+                                falling; then the state is widened to FP32 and the iterations
+                                continue on the FP32 X to tol.  Warm starts run in FP32. */
+    int32_t reserved3;
+    double switch_tol;       /* end of the bf16 phase (default 1e-2) */
 } respca_config;
 
 typedef struct {
@@ -94,7 +102,7 @@ typedef struct {
     float ms_dense;          /* summed duration of the all-column tensor-core search kernel over
                                 the passes in which it ran (cfg.timing = 1) */
     int32_t dense_passes;    /* passes in which that kernel searched every column */
-    int32_t reserved;
+    int32_t bf16_iters;      /* iterations run with BF16 state (precision = 1) */
 } respca_stats;
 
 /* Optional warm start / checkpoint-resume state (the paper starts from zero;

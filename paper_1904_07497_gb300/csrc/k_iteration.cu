@@ -6,7 +6,10 @@
 // squared distance to its own centroid (for the exact pruning of the K-means
 // search) and the cluster sums of the NEXT iteration's D under the current
 // labels, which become the next centroids whenever the p step keeps every
-// label.  28 bytes move per element (4 loads, 3 stores of 4 bytes).
+// label.  28 bytes move per element (4 loads, 3 stores of 4 bytes) with FP32
+// state; 14 with BF16 X and BF16 state (TS), where every stored value is the
+// FP32 result rounded to BF16 and the norms, own distances and next sums are
+// formed from the stored values (so the state is exactly what is stored).
 #include "respca_internal.cuh"
 
 namespace respca {
@@ -14,18 +17,20 @@ namespace respca {
 namespace {
 
 // ---------------------------------------------------------------- fused iteration
-// One element of one ALM iteration.  l, sn, tn are the new L, S, Theta.
+// One element of one ALM iteration.  l, sn, tn are the new L, S, Theta as
+// stored (rounded to TS).
+template <typename TS>
 __device__ __forceinline__ void alm_element(float x, float s, float t, float l0, float m,
                                             const IterScalars& sc, float& l, float& sn, float& tn,
                                             float& own, float& nr, float& dlc, float& nds,
                                             float& dnext) {
     const float tr = t * sc.inv_rho;
     const float dv = (x - s) + tr;                    // D = X - S + Theta/rho (after Eq. (14))
-    l = fmaf(sc.a, dv, sc.b * m);                     // Eq. (18): a D_j + (1-a) mean of cluster
+    l = StateIO<TS>::round(fmaf(sc.a, dv, sc.b * m)); // Eq. (18): a D_j + (1-a) mean of cluster
     const float bb = (x - l) + tr;                    // B = X - L + Theta/rho
     const float mag = fabsf(bb) - sc.inv_rho;
-    sn = mag > 0.f ? copysignf(mag, bb) : 0.f;        // Eq. (24), sign(0) = 0
-    tn = fminf(fmaxf(sc.rho * bb, -1.f), 1.f);        // Eq. (25): Theta + rho(X-L-S) = clip(rho B)
+    sn = StateIO<TS>::round(mag > 0.f ? copysignf(mag, bb) : 0.f);   // Eq. (24), sign(0) = 0
+    tn = StateIO<TS>::round(fminf(fmaxf(sc.rho * bb, -1.f), 1.f));   // Eq. (25): clip(rho B)
     const float res = (x - l) - sn;
     const float dl = l - l0;
     const float ds = sn - s;
@@ -37,10 +42,10 @@ __device__ __forceinline__ void alm_element(float x, float s, float t, float l0,
     dnext = (x - sn) + tn * sc.inv_rho_next;          // D of the next iteration
 }
 
-template <typename TX, bool VEC>
+template <typename TX, typename TS, bool VEC>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_iteration(const TX* __restrict__ X, int64_t ldx, float* __restrict__ L, float* __restrict__ S,
-                float* __restrict__ Th, int64_t lds, const float* __restrict__ mu,
+    k_iteration(const TX* __restrict__ X, int64_t ldx, TS* __restrict__ L, TS* __restrict__ S,
+                TS* __restrict__ Th, int64_t lds, const float* __restrict__ mu,
                 const int32_t* __restrict__ perm, const TileDesc* __restrict__ tiles,
                 const DevStatus* __restrict__ status, int64_t d, int64_t n, IterScalars sc,
                 float* __restrict__ Dpart, float* __restrict__ own_part,
@@ -74,9 +79,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int k = warp; k < td.len; k += kThreads / 32) {
         const int64_t col = perm[td.start + k];
         const TX* xc = X + col * ldx;
-        float* lc = L + col * lds;
-        float* scol = S + col * lds;
-        float* tc = Th + col * lds;
+        TS* lc = L + col * lds;
+        TS* scol = S + col * lds;
+        TS* tc = Th + col * lds;
         float own = 0.f, dlc = 0.f;
         if (VEC) {
             float4 xv[4], sv[4], tv[4], lv[4];
@@ -85,9 +90,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const int64_t rr = r0 + s * 128 + lane * 4;
                 if (rr < d) {
                     xv[s] = XLoad<TX>::four(xc + rr);
-                    sv[s] = __ldcs(reinterpret_cast<const float4*>(scol + rr));
-                    tv[s] = __ldcs(reinterpret_cast<const float4*>(tc + rr));
-                    lv[s] = __ldcs(reinterpret_cast<const float4*>(lc + rr));
+                    sv[s] = StateIO<TS>::load4(scol + rr);
+                    tv[s] = StateIO<TS>::load4(tc + rr);
+                    lv[s] = StateIO<TS>::load4(lc + rr);
                 }
             }
 #pragma unroll
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         float l, sn, tn, dn;
-                        alm_element(f4get(xv[s], q), f4get(sv[s], q), f4get(tv[s], q),
+                        alm_element<TS>(f4get(xv[s], q), f4get(sv[s], q), f4get(tv[s], q),
                                     f4get(lv[s], q), f4get(m[s], q), sc, l, sn, tn, own, nr, dlc,
                                     nds, dn);
                         f4set(lo, q, l);
@@ -106,9 +111,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                         f4set(to, q, tn);
                         f4set(acc[s], q, f4get(acc[s], q) + dn);
                     }
-                    __stcs(reinterpret_cast<float4*>(lc + rr), lo);
-                    __stcs(reinterpret_cast<float4*>(scol + rr), so);
-                    __stcs(reinterpret_cast<float4*>(tc + rr), to);
+                    StateIO<TS>::store4(lc + rr, lo);
+                    StateIO<TS>::store4(scol + rr, so);
+                    StateIO<TS>::store4(tc + rr, to);
                 }
             }
         } else {
@@ -119,12 +124,12 @@ __global__ void __launch_bounds__(kThreads, 2)
                 for (int q = 0; q < 4; ++q) {
                     if (rr + q < d) {
                         float l, sn, tn, dn;
-                        alm_element(XLoad<TX>::one(xc + rr + q), scol[rr + q], tc[rr + q],
-                                    lc[rr + q], f4get(m[s], q), sc, l, sn, tn, own, nr, dlc, nds,
-                                    dn);
-                        lc[rr + q] = l;
-                        scol[rr + q] = sn;
-                        tc[rr + q] = tn;
+                        alm_element<TS>(XLoad<TX>::one(xc + rr + q), StateIO<TS>::load1(scol + rr + q),
+                                        StateIO<TS>::load1(tc + rr + q), StateIO<TS>::load1(lc + rr + q),
+                                        f4get(m[s], q), sc, l, sn, tn, own, nr, dlc, nds, dn);
+                        StateIO<TS>::store1(lc + rr + q, l);
+                        StateIO<TS>::store1(scol + rr + q, sn);
+                        StateIO<TS>::store1(tc + rr + q, tn);
                         f4set(acc[s], q, f4get(acc[s], q) + dn);
                     }
                 }
@@ -170,22 +175,24 @@ inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per
 
 }  // namespace
 
-cudaError_t launch_iteration(int dtype, const void* X, int64_t ldx, float* L, float* S, float* Th,
-                             int64_t lds, const float* mu, const int32_t* perm,
+cudaError_t launch_iteration(int dtype, int sdtype, const void* X, int64_t ldx, void* L, void* S,
+                             void* Th, int64_t lds, const float* mu, const int32_t* perm,
                              const TileDesc* tiles, int max_tiles, const DevStatus* status,
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
                              float* dl_part, double* norm_part, bool vec, cudaStream_t st) {
     count_launches(1);
     const dim3 grid(max_tiles, grid_for(d, kChunkRows));
     RESPCA_DISPATCH_X(dtype, TX, {
-        if (vec)
-            k_iteration<TX, true><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, L, S, Th, lds, mu,
-                                                             perm, tiles, status, d, n, sc, Dpart,
-                                                             own_part, dl_part, norm_part);
-        else
-            k_iteration<TX, false><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, L, S, Th, lds, mu,
-                                                              perm, tiles, status, d, n, sc, Dpart,
-                                                              own_part, dl_part, norm_part);
+        RESPCA_DISPATCH_S(sdtype, TS, {
+            if (vec)
+                k_iteration<TX, TS, true><<<grid, kThreads, 0, st>>>(
+                    (const TX*)X, ldx, (TS*)L, (TS*)S, (TS*)Th, lds, mu, perm, tiles, status, d, n, sc,
+                    Dpart, own_part, dl_part, norm_part);
+            else
+                k_iteration<TX, TS, false><<<grid, kThreads, 0, st>>>(
+                    (const TX*)X, ldx, (TS*)L, (TS*)S, (TS*)Th, lds, mu, perm, tiles, status, d, n, sc,
+                    Dpart, own_part, dl_part, norm_part);
+        });
     });
     return cudaGetLastError();
 }

@@ -70,11 +70,11 @@ __global__ void k_sum_parts(const double* __restrict__ part, int nparts, double*
 
 // ---------------------------------------------------------------- cluster sums
 // Sum, per tile and row, the columns of X (kSumX), L (kSumL) or
-// D = X - S + Theta * inv_rho (kSumD).
-template <int MODE, typename TX, bool VEC>
+// D = X - S + Theta * inv_rho (kSumD; S and Theta stored as TS).
+template <int MODE, typename TX, typename TS, bool VEC>
 __global__ void __launch_bounds__(kThreads)
     k_colsum(const TX* __restrict__ X, int64_t ldx, const float* __restrict__ L,
-             const float* __restrict__ S, const float* __restrict__ Th, int64_t lds,
+             const TS* __restrict__ S, const TS* __restrict__ Th, int64_t lds,
              float inv_rho, const int32_t* __restrict__ perm, const TileDesc* __restrict__ tiles,
              const DevStatus* __restrict__ status, int64_t d, float* __restrict__ Dpart) {
     __shared__ float red[kThreads / 32][kChunkRows];
@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(kThreads)
                         v = *reinterpret_cast<const float4*>(L + col * lds + rr);
                     } else {
                         const float4 x = XLoad<TX>::four(X + col * ldx + rr);
-                        const float4 sv = *reinterpret_cast<const float4*>(S + col * lds + rr);
-                        const float4 tv = *reinterpret_cast<const float4*>(Th + col * lds + rr);
+                        const float4 sv = XLoad<TS>::four(S + col * lds + rr);
+                        const float4 tv = XLoad<TS>::four(Th + col * lds + rr);
                         v = make_float4((x.x - sv.x) + tv.x * inv_rho, (x.y - sv.y) + tv.y * inv_rho,
                                         (x.z - sv.z) + tv.z * inv_rho, (x.w - sv.w) + tv.w * inv_rho);
                     }
@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(kThreads)
                         float v;
                         if (MODE == kSumX) v = XLoad<TX>::one(X + col * ldx + r);
                         else if (MODE == kSumL) v = L[col * lds + r];
-                        else v = (XLoad<TX>::one(X + col * ldx + r) - S[col * lds + r]) +
-                                 Th[col * lds + r] * inv_rho;
+                        else v = (XLoad<TX>::one(X + col * ldx + r) - XLoad<TS>::one(S + col * lds + r)) +
+                                 XLoad<TS>::one(Th + col * lds + r) * inv_rho;
                         f4set(acc[s], q, f4get(acc[s], q) + v);
                     }
                 }
@@ -642,19 +642,33 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // State after the skipped ramp: L = mu_p + alpha (X - mu_p), Theta = beta (X - mu_p).
-template <typename TX>
+template <typename TX, typename TS>
 __global__ void __launch_bounds__(kThreads)
     k_ramp_state(const TX* __restrict__ X, int64_t ldx, int64_t d, int64_t n,
                  const int32_t* __restrict__ labels, const float* __restrict__ mu, float alpha,
-                 float beta, float* __restrict__ L, float* __restrict__ Th, int64_t lds) {
+                 float beta, TS* __restrict__ L, TS* __restrict__ Th, int64_t lds) {
     const int64_t total = d * n;
     for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * kThreads) {
         const int64_t j = idx / d, r = idx % d;
         const float m = mu[(int64_t)labels[j] * d + r];
         const float e = XLoad<TX>::one(X + j * ldx + r) - m;
-        L[j * lds + r] = fmaf(alpha, e, m);
-        Th[j * lds + r] = beta * e;
+        StateIO<TS>::store1(L + j * lds + r, fmaf(alpha, e, m));
+        StateIO<TS>::store1(Th + j * lds + r, beta * e);
+    }
+}
+
+// Element-type conversion of a d x n column-major matrix (one CTA per column
+// at a time): the BF16 copy of an FP32 X, and the BF16 state widened to FP32
+// when the bf16 phase ends.
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kThreads)
+    k_convert(const TI* __restrict__ src, int64_t lds, TO* __restrict__ dst, int64_t ldd, int64_t d,
+              int64_t n) {
+    for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+        const TI* s = src + j * lds;
+        TO* o = dst + j * ldd;
+        for (int64_t r = threadIdx.x; r < d; r += kThreads) StateIO<TO>::store1(o + r, XLoad<TI>::one(s + r));
     }
 }
 
@@ -681,37 +695,40 @@ cudaError_t launch_fro2(int dtype, const void* X, int64_t d, int64_t n, int64_t 
     return cudaGetLastError();
 }
 
-template <int M, typename TX>
-void colsum_mode(dim3 grid, const TX* x, int64_t ldx, const float* L, const float* S, const float* Th,
+template <int M, typename TX, typename TS>
+void colsum_mode(dim3 grid, const TX* x, int64_t ldx, const float* L, const TS* S, const TS* Th,
                  int64_t lds, float inv_rho, const int32_t* perm, const TileDesc* tiles,
                  const DevStatus* status, int64_t d, float* Dpart, bool vec, cudaStream_t st) {
     if (vec)
-        k_colsum<M, TX, true><<<grid, kThreads, 0, st>>>(x, ldx, L, S, Th, lds, inv_rho, perm, tiles,
-                                                         status, d, Dpart);
+        k_colsum<M, TX, TS, true><<<grid, kThreads, 0, st>>>(x, ldx, L, S, Th, lds, inv_rho, perm,
+                                                             tiles, status, d, Dpart);
     else
-        k_colsum<M, TX, false><<<grid, kThreads, 0, st>>>(x, ldx, L, S, Th, lds, inv_rho, perm, tiles,
-                                                          status, d, Dpart);
+        k_colsum<M, TX, TS, false><<<grid, kThreads, 0, st>>>(x, ldx, L, S, Th, lds, inv_rho, perm,
+                                                              tiles, status, d, Dpart);
 }
 
 cudaError_t launch_colsum(int mode, int dtype, const void* X, int64_t ldx, const float* L,
-                          const float* S, const float* Th, int64_t lds, float inv_rho,
+                          const void* S, const void* Th, int64_t lds, float inv_rho,
                           const int32_t* perm, const TileDesc* tiles, int max_tiles,
                           const DevStatus* status, int64_t d, float* Dpart, bool vec,
-                          cudaStream_t st) {
+                          cudaStream_t st, int sdtype) {
     count_launches(1);
     const dim3 grid(max_tiles, grid_for(d, kChunkRows));
     if (mode == kSumL) {
-        colsum_mode<kSumL, float>(grid, nullptr, 0, L, S, Th, lds, inv_rho, perm, tiles, status, d,
-                                  Dpart, vec, st);
+        colsum_mode<kSumL, float, float>(grid, nullptr, 0, L, nullptr, nullptr, lds, inv_rho, perm,
+                                         tiles, status, d, Dpart, vec, st);
         return cudaGetLastError();
     }
     RESPCA_DISPATCH_X(dtype, TX, {
-        if (mode == kSumX)
-            colsum_mode<kSumX, TX>(grid, (const TX*)X, ldx, L, S, Th, lds, inv_rho, perm, tiles,
-                                   status, d, Dpart, vec, st);
-        else
-            colsum_mode<kSumD, TX>(grid, (const TX*)X, ldx, L, S, Th, lds, inv_rho, perm, tiles,
-                                   status, d, Dpart, vec, st);
+        if (mode == kSumX) {
+            colsum_mode<kSumX, TX, float>(grid, (const TX*)X, ldx, L, nullptr, nullptr, lds, inv_rho,
+                                          perm, tiles, status, d, Dpart, vec, st);
+        } else {
+            RESPCA_DISPATCH_S(sdtype, TS, {
+                colsum_mode<kSumD, TX, TS>(grid, (const TX*)X, ldx, L, (const TS*)S, (const TS*)Th, lds,
+                                           inv_rho, perm, tiles, status, d, Dpart, vec, st);
+            });
+        }
     });
     return cudaGetLastError();
 }
@@ -833,11 +850,25 @@ cudaError_t launch_ramp_stats(int dtype, const void* X, int64_t ldx, int64_t d, 
 
 cudaError_t launch_ramp_state(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
                               const int32_t* labels, const float* mu, float alpha, float beta,
-                              float* L, float* Th, int64_t lds, cudaStream_t st) {
+                              void* L, void* Th, int64_t lds, cudaStream_t st, int sdtype) {
     count_launches(1);
     RESPCA_DISPATCH_X(dtype, TX, {
-        k_ramp_state<TX><<<152 * 8, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu, alpha,
-                                                       beta, L, Th, lds);
+        RESPCA_DISPATCH_S(sdtype, TS, {
+            k_ramp_state<TX, TS><<<152 * 8, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu, alpha,
+                                                               beta, (TS*)L, (TS*)Th, lds);
+        });
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int src_dtype, const void* src, int64_t lds, int dst_sdtype, void* dst,
+                           int64_t ldd, int64_t d, int64_t n, cudaStream_t st) {
+    count_launches(1);
+    const int grid = (int)std::min<int64_t>(n, 152 * 16);
+    RESPCA_DISPATCH_X(src_dtype, TI, {
+        RESPCA_DISPATCH_S(dst_sdtype, TO, {
+            k_convert<TI, TO><<<grid, kThreads, 0, st>>>((const TI*)src, lds, (TO*)dst, ldd, d, n);
+        });
     });
     return cudaGetLastError();
 }

@@ -57,7 +57,8 @@ struct respca_ctx {
         Dpart, own_part, norm_part, flag_list, seedD2, centers, seed_u, fro_part, status,
         hX, hL, hS, hp, hp0,
         mu_next, mu_old, drift, ub, lb, dl_part, sums, moved, contrib, boff, labels_pass,
-        mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count, rc_dist;
+        mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count, rc_dist,
+        L16, S16, T16, X16;   // BF16 state and X of the bf16 phase (precision = 1)
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -377,6 +378,17 @@ double safety_factor(int64_t d) {
     return s < 0.5 ? 0.5 : s;
 }
 
+// End of the bf16 phase: the BF16 state becomes the caller's FP32 L and S and
+// the FP32 Theta.
+respca_status widen_state(respca_ctx* h, const void* L16, const void* S16, const void* T16,
+                          int64_t ld16, float* L, float* S, float* Th, int64_t lds, int64_t d,
+                          int64_t n) {
+    CK(launch_convert(RESPCA_BF16, L16, ld16, 0, L, lds, d, n, h->stream));
+    CK(launch_convert(RESPCA_BF16, S16, ld16, 0, S, lds, d, n, h->stream));
+    CK(launch_convert(RESPCA_BF16, T16, ld16, 0, Th, lds, d, n, h->stream));
+    return RESPCA_OK;
+}
+
 respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int64_t n, int64_t ldx,
                          double lambda, int c, double tol, int max_iter, const int32_t* p0, float* L,
                          float* S, int64_t lds, int32_t* p, respca_warm* warm, respca_stats* stats) {
@@ -423,6 +435,38 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     pb.vec = vec_ok(X, ldx, elem_size(dtype)) && vec_ok(L, lds, 4) && vec_ok(S, lds, 4) &&
              vec_ok(pb.Th, lds, 4) && (d % 4 == 0);
 
+    // The views the iterations run on: FP32 state in the caller's L, S and
+    // Theta, or (precision = 1, not warm) BF16 state and X in the workspace
+    // until the bf16 phase ends.
+    struct View {
+        int xd;            // element type of the X the iterations read
+        const void* X;
+        int64_t ldx;
+        int sd;            // state storage: 0 FP32, 1 BF16
+        void *L, *S, *Th;
+        int64_t ld;
+        bool vec;
+    } v{dtype, X, ldx, 0, L, S, pb.Th, lds, pb.vec};
+    if (h->cfg.precision == 1 && !is_warm) {
+        const int64_t ld16 = (d + 7) / 8 * 8;
+        const size_t bytes = sizeof(uint16_t) * (size_t)ld16 * n;
+        CK(ensure(h->L16, bytes));
+        CK(ensure(h->S16, bytes));
+        CK(ensure(h->T16, bytes));
+        if (dtype == RESPCA_F32) {
+            CK(ensure(h->X16, bytes));
+            CK(launch_convert(dtype, X, ldx, 1, h->X16.p, ld16, d, n, h->stream));
+            v.xd = RESPCA_BF16;
+            v.X = h->X16.p;
+            v.ldx = ld16;
+        }
+        v.sd = 1;
+        v.L = h->L16.p;
+        v.S = h->S16.p;
+        v.Th = h->T16.p;
+        v.ld = ld16;
+        v.vec = (d % 4 == 0) && vec_ok(v.X, v.ldx, elem_size(v.xd));
+    }
     double rho = is_warm ? warm->rho : h->cfg.rho0;
     if (!is_warm) {
         if (p0) {
@@ -438,6 +482,12 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         CK(cudaMemset2DAsync(L, sizeof(float) * lds, 0, sizeof(float) * d, n, h->stream));
         CK(cudaMemset2DAsync(S, sizeof(float) * lds, 0, sizeof(float) * d, n, h->stream));
         CK(cudaMemset2DAsync(pb.Th, sizeof(float) * lds, 0, sizeof(float) * d, n, h->stream));
+        if (v.sd == 1) {
+            const size_t es = sizeof(uint16_t);
+            CK(cudaMemset2DAsync(v.L, es * v.ld, 0, es * d, n, h->stream));
+            CK(cudaMemset2DAsync(v.S, es * v.ld, 0, es * d, n, h->stream));
+            CK(cudaMemset2DAsync(v.Th, es * v.ld, 0, es * d, n, h->stream));
+        }
     }
     // sort the labels into tiles (and validate caller labels)
     const int mt = max_tiles_for(n, c);
@@ -458,8 +508,6 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         out.kernel_launches = t_kernel_launches - launches0;
         out.ms_dense = h->ms_dense;
         out.dense_passes = h->dense_passes;
-    out.ms_dense = h->ms_dense;
-    out.dense_passes = h->dense_passes;
         cudaEventElapsedTime(&out.ms_total, h->ev0, h->ev1);
         if (warm) warm->rho = rho;
         if (stats) *stats = out;
@@ -468,9 +516,9 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
 
     // centroids of D = X - S + Theta/rho under the current labels; no bound
     // information yet (lb = 0, no drift)
-    CK(launch_colsum(kSumD, dtype, X, ldx, nullptr, S, pb.Th, lds, (float)(1.0 / rho),
-                     P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart), pb.vec,
-                     h->stream));
+    CK(launch_colsum(kSumD, v.xd, v.X, v.ldx, nullptr, v.S, v.Th, v.ld, (float)(1.0 / rho),
+                     P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart), v.vec,
+                     h->stream, v.sd));
     rs = finish_centroids(h, c, d, P<float>(h->mu), nullptr);
     if (rs != RESPCA_OK) return rs;
     CK(cudaMemsetAsync(h->lb.p, 0, sizeof(float) * n, h->stream));
@@ -485,7 +533,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         // L_{t+1} = X_m + a_t g_t X_r, Theta_{t+1} = rho_t b_t g_t X_r.
         CK(cudaMemsetAsync(&ds->ramp_r2, 0, sizeof(double) + sizeof(unsigned long long) + sizeof(unsigned int),
                            h->stream));
-        CK(launch_ramp_stats(dtype, X, ldx, d, n, p, P<float>(h->mu), P<double>(h->sep2), safety,
+        CK(launch_ramp_stats(v.xd, v.X, v.ldx, d, n, p, P<float>(h->mu), P<double>(h->sep2), safety,
                              &ds->ramp_abs, &ds->ramp_ratio, P<double>(h->seedD2), h->stream));
         CK(launch_sum_doubles(P<double>(h->seedD2), n, &ds->ramp_r2, h->stream));
         rs = read_status(h);
@@ -521,8 +569,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             ++T;
         }
         if (T > 0) {
-            CK(launch_ramp_state(dtype, X, ldx, d, n, p, P<float>(h->mu), (float)alpha, (float)beta, L,
-                                 pb.Th, lds, h->stream));
+            CK(launch_ramp_state(v.xd, v.X, v.ldx, d, n, p, P<float>(h->mu), (float)alpha, (float)beta,
+                                 v.L, v.Th, v.ld, h->stream, v.sd));
             rho = r;
             t_start = T;
             out.iters = T;
@@ -534,6 +582,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     }
     CK(cudaEventRecord(h->ev2, h->stream));
 
+    double err_hist[2] = {INFINITY, INFINITY};   // err of the last two bf16 iterations
     for (int t = t_start; t < max_iter; ++t) {
         const double rho_next = rho * kappa;
         IterScalars sc;
@@ -547,10 +596,10 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         CK(cudaMemcpyAsync(h->labels_prev.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
         // L, S, Theta, norms, own distances, column movement and next-D sums in one pass
         if (timing) CK(cudaEventRecord(h->evk0, h->stream));
-        CK(launch_iteration(dtype, X, ldx, L, S, pb.Th, lds, P<float>(h->mu), P<int32_t>(h->perm),
-                            P<TileDesc>(h->tiles), mt, ds, d, n, sc, P<float>(h->Dpart),
-                            P<float>(h->own_part), P<float>(h->dl_part), P<double>(h->norm_part),
-                            pb.vec, h->stream));
+        CK(launch_iteration(v.xd, v.sd, v.X, v.ldx, v.L, v.S, v.Th, v.ld, P<float>(h->mu),
+                            P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, n, sc,
+                            P<float>(h->Dpart), P<float>(h->own_part), P<float>(h->dl_part),
+                            P<double>(h->norm_part), v.vec, h->stream));
         if (timing) CK(cudaEventRecord(h->evk1, h->stream));
         out.fused_launches += 1;
         CK(launch_reduce_norms(P<double>(h->norm_part), mt, nch, ds, h->stream));
@@ -559,7 +608,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
                               P<int32_t>(h->counts), P<double>(h->sep2), safety, P<double>(h->drift),
                               P<float>(h->ub), P<float>(h->lb), P<int32_t>(h->flag_list), ds,
                               h->stream));
-        rs = search(h, RESPCA_F32, L, lds, d, n, P<int32_t>(h->flag_list), c, p, pb.vec);
+        rs = search(h, v.sd == 1 ? RESPCA_BF16 : RESPCA_F32, v.L, v.ld, d, n, P<int32_t>(h->flag_list),
+                    c, p, v.vec);
         if (rs != RESPCA_OK) return rs;
         // next centroids if every label stays (queued before the check; discarded otherwise)
         rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
@@ -584,7 +634,9 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             // Lloyd on the columns of L until no label changes
             SearchCounts scount;
             scount.passes = 1;
-            rs = lloyd_continue(h, kSumL, RESPCA_F32, L, lds, d, n, c, p, pb.vec, km, &scount);
+            // (BF16 L is summed as the "X" operand: the sums only need its element type)
+            rs = v.sd == 1 ? lloyd_continue(h, kSumX, RESPCA_BF16, v.L, v.ld, d, n, c, p, v.vec, km, &scount)
+                           : lloyd_continue(h, kSumL, RESPCA_F32, v.L, v.ld, d, n, c, p, v.vec, km, &scount);
             if (rs != RESPCA_OK) return rs;
             out.lloyd_passes += scount.passes - 1;
             out.assigned_columns += scount.assigned;
@@ -592,9 +644,9 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             // next centroids: D = X - S + Theta/rho_{t+1} under the final labels
             CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
                                   P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
-            CK(launch_colsum(kSumD, dtype, X, ldx, nullptr, S, pb.Th, lds, sc.inv_rho_next,
+            CK(launch_colsum(kSumD, v.xd, v.X, v.ldx, nullptr, v.S, v.Th, v.ld, sc.inv_rho_next,
                              P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart),
-                             pb.vec, h->stream));
+                             v.vec, h->stream, v.sd));
             rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
             if (rs != RESPCA_OK) return rs;
             std::swap(h->mu, h->mu_next);
@@ -610,6 +662,32 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             out.converged = 1;
             break;
         }
+        if (v.sd == 1) {
+            out.bf16_iters += 1;
+            // the bf16 phase ends at switch_tol, or once err stops falling (BF16
+            // rounding of the state puts a floor under it)
+            const bool stalled = out.bf16_iters >= 3 && out.err >= err_hist[1];
+            err_hist[1] = err_hist[0];
+            err_hist[0] = out.err;
+            if (out.err <= h->cfg.switch_tol || stalled) {
+                rs = widen_state(h, v.L, v.S, v.Th, v.ld, L, S, pb.Th, lds, d, n);
+                if (rs != RESPCA_OK) return rs;
+                v = View{dtype, X, ldx, 0, L, S, pb.Th, lds, pb.vec};
+                // centroids of the next iteration from the FP32 X and the widened state
+                CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
+                                      P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
+                CK(launch_colsum(kSumD, v.xd, v.X, v.ldx, nullptr, v.S, v.Th, v.ld, (float)(1.0 / rho),
+                                 P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d,
+                                 P<float>(h->Dpart), v.vec, h->stream, 0));
+                rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
+                if (rs != RESPCA_OK) return rs;
+                std::swap(h->mu, h->mu_next);
+            }
+        }
+    }
+    if (v.sd == 1) {   // stopped inside the bf16 phase: the outputs are FP32
+        rs = widen_state(h, v.L, v.S, v.Th, v.ld, L, S, pb.Th, lds, d, n);
+        if (rs != RESPCA_OK) return rs;
     }
     CK(cudaEventRecord(h->ev1, h->stream));
     rs = read_status(h);
@@ -642,6 +720,8 @@ void respca_config_default(respca_config* cfg) {
     cfg->device = -1;
     cfg->search_impl = 0;
     cfg->ramp_skip = 1;
+    cfg->precision = 0;
+    cfg->switch_tol = 1e-2;
 }
 
 respca_status respca_create(respca_handle* out, const respca_config* cfg) {
@@ -686,7 +766,7 @@ respca_status respca_destroy(respca_handle h) {
                       &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->contrib, &h->boff,
                       &h->labels_pass,
                       &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count,
-                      &h->rc_dist};
+                      &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->hstat) cudaFreeHost(h->hstat);

@@ -84,10 +84,10 @@ cudaError_t launch_sort_labels(const int32_t* labels, int64_t n, int c, int32_t*
                                DevStatus* status, cudaStream_t st);
 
 cudaError_t launch_colsum(int mode, int dtype, const void* X, int64_t ldx, const float* L,
-                          const float* S, const float* Th, int64_t lds, float inv_rho,
+                          const void* S, const void* Th, int64_t lds, float inv_rho,
                           const int32_t* perm, const TileDesc* tiles, int max_tiles,
                           const DevStatus* status, int64_t d, float* Dpart, bool vec,
-                          cudaStream_t st);
+                          cudaStream_t st, int sdtype = 0);
 
 cudaError_t launch_centroids(const float* Dpart, const int32_t* tile_off, const int32_t* counts,
                              int c, int64_t d, float* mu, cudaStream_t st,
@@ -118,8 +118,8 @@ cudaError_t launch_mu_norms(const float* mu, int c, int64_t d, double* mu_norm2,
 cudaError_t launch_separation(const float* mu, const int32_t* counts, int c, int64_t d,
                               float* pair_ss, double* sep2, cudaStream_t st);
 
-cudaError_t launch_iteration(int dtype, const void* X, int64_t ldx, float* L, float* S, float* Th,
-                             int64_t lds, const float* mu, const int32_t* perm,
+cudaError_t launch_iteration(int dtype, int sdtype, const void* X, int64_t ldx, void* L, void* S,
+                             void* Th, int64_t lds, const float* mu, const int32_t* perm,
                              const TileDesc* tiles, int max_tiles, const DevStatus* status,
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
                              float* dl_part, double* norm_part, bool vec, cudaStream_t st);
@@ -148,7 +148,10 @@ cudaError_t launch_ramp_stats(int dtype, const void* X, int64_t ldx, int64_t d, 
                               unsigned long long* max_ratio_bits, double* r2_part, cudaStream_t st);
 cudaError_t launch_ramp_state(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
                               const int32_t* labels, const float* mu, float alpha, float beta,
-                              float* L, float* Th, int64_t lds, cudaStream_t st);
+                              void* L, void* Th, int64_t lds, cudaStream_t st, int sdtype = 0);
+// dst (FP32 or BF16 per dst_sdtype, leading dimension ldd) = src (respca_dtype src_dtype)
+cudaError_t launch_convert(int src_dtype, const void* src, int64_t lds, int dst_sdtype, void* dst,
+                           int64_t ldd, int64_t d, int64_t n, cudaStream_t st);
 
 cudaError_t launch_seed_dist(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n,
                              const int32_t* centers, int k, double* D2, cudaStream_t st);
@@ -246,6 +249,61 @@ struct XLoad<__half> {
         return make_float4(lo.x, lo.y, hi.x, hi.y);
     }
 };
+
+// Loads and stores of the iteration state (L, S, Theta) in its storage type:
+// FP32, or BF16 in the bf16 phase of the precision=1 schedule.  Streaming
+// cache hints (each element is read and written once per pass).  round()
+// gives the value that storing and reloading returns.
+template <typename TS>
+struct StateIO;
+
+template <>
+struct StateIO<float> {
+    static __device__ __forceinline__ float4 load4(const float* p) {
+        return __ldcs(reinterpret_cast<const float4*>(p));
+    }
+    static __device__ __forceinline__ void store4(float* p, float4 v) {
+        __stcs(reinterpret_cast<float4*>(p), v);
+    }
+    static __device__ __forceinline__ float load1(const float* p) { return *p; }
+    static __device__ __forceinline__ void store1(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ float round(float v) { return v; }
+};
+
+template <>
+struct StateIO<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
+        const uint2 u = __ldcs(reinterpret_cast<const uint2*>(p));
+        const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+        const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+    static __device__ __forceinline__ void store4(__nv_bfloat16* p, float4 v) {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t*>(&lo);
+        u.y = *reinterpret_cast<const uint32_t*>(&hi);
+        __stcs(reinterpret_cast<uint2*>(p), u);
+    }
+    static __device__ __forceinline__ float load1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void store1(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float round(float v) {
+        return __bfloat162float(__float2bfloat16_rn(v));
+    }
+};
+
+// Dispatch a state storage type (0 f32, 1 bf16).
+#define RESPCA_DISPATCH_S(sdtype, TS, ...)  \
+    do {                                    \
+        if ((sdtype) == 1) {                \
+            using TS = __nv_bfloat16;       \
+            __VA_ARGS__;                    \
+        } else {                            \
+            using TS = float;               \
+            __VA_ARGS__;                    \
+        }                                   \
+    } while (0)
 
 __device__ __forceinline__ float f4get(const float4& v, int q) {
     return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));

@@ -32,7 +32,9 @@ class respca_config(ctypes.Structure):
                 ("kmeans_max_iter", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("search_impl", ctypes.c_int32),
-                ("ramp_skip", ctypes.c_int32), ("batch_lanes", ctypes.c_int32)]
+                ("ramp_skip", ctypes.c_int32), ("batch_lanes", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("reserved3", ctypes.c_int32),
+                ("switch_tol", ctypes.c_double)]
 
 
 class respca_stats(ctypes.Structure):
@@ -46,7 +48,7 @@ class respca_stats(ctypes.Structure):
                 ("init_lloyd_passes", ctypes.c_int32), ("fused_launches", ctypes.c_int32),
                 ("ms_total", ctypes.c_float), ("ms_init", ctypes.c_float),
                 ("ms_fused", ctypes.c_float), ("ms_dense", ctypes.c_float),
-                ("dense_passes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("dense_passes", ctypes.c_int32), ("bf16_iters", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {(k[:-1] if k.endswith("_") else k): getattr(self, k) for k, _ in self._fields_
@@ -253,12 +255,16 @@ class Solver:
 
     def __init__(self, rho0: float = 1e-4, kappa: float = 1.5, kmeans_max_iter: int = 100,
                  seed: int = 0, stream=None, device: int | None = None, timing: bool = False,
-                 search_impl: int = 0, ramp_skip: bool = True, batch_lanes: int = 0):
+                 search_impl: int = 0, ramp_skip: bool = True, batch_lanes: int = 0,
+                 precision: int = 0, switch_tol: float | None = None):
         import torch
         cfg = respca_config_default()
         cfg.search_impl = search_impl
         cfg.ramp_skip = 1 if ramp_skip else 0
         cfg.batch_lanes = batch_lanes
+        cfg.precision = precision
+        if switch_tol is not None:
+            cfg.switch_tol = switch_tol
         cfg.rho0, cfg.kappa, cfg.kmeans_max_iter, cfg.seed = rho0, kappa, kmeans_max_iter, seed
         cfg.timing = 1 if timing else 0
         dev = torch.cuda.current_device() if device is None else device
