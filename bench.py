@@ -279,10 +279,14 @@ def run_gpu(args, rank, world, local_rank):
         dense_gbs = dense_bytes / (dense_avg / 1e3) / 1e9
         flops = 2.0 * c * d * n
         rooflines.append({
-            "bound": "hbm", "kernel": "k_search_dense (tensor-core nearest-centroid search, all columns)",
+            "bound": "hbm",
+            "kernel": ("k_search_dense_t (tensor-core nearest-centroid search, all columns; centroids as "
+                       "the M operand, 256 columns per MMA)") if c <= 128 else
+                      "k_search_dense (tensor-core nearest-centroid search, all columns; N = centroids)",
             "achieved": round(dense_gbs, 1), "peak": peak, "unit": "GB/s",
             "frac": round(dense_gbs / peak, 4), "peak_source": peak_kind,
-            "traffic": kernel_traffic("k_search_tc.cu", f"k_search_dense_{args.workload}.txt"),
+            "traffic": kernel_traffic("k_search_tc.cu", ("k_search_dense_t_" if c <= 128 else "k_search_dense_")
+                                      + f"{args.workload}.txt"),
             "algorithmic_bytes_per_launch": dense_bytes, "avg_launch_ms": round(dense_avg, 4),
             "algorithmic_tflops": round(flops / (dense_avg / 1e3) / 1e12, 2),
             "launches": ts["dense_passes"], "total_ms": round(ts["ms_dense"], 3)})

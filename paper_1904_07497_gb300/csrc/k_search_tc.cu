@@ -231,8 +231,10 @@ __device__ __forceinline__ void gather8(const float* __restrict__ gbase, int nsl
 // (partial products summed in a fixed order), argmin with ties to the lowest
 // index, and the update of the label and the bounds; a near tie is queued
 // with its candidate set for the FP64 re-decision.
-__device__ void finalize_column(int64_t col, float y2, const float* __restrict__ gbase, int nslots,
-                                int Npad, int m, const float* __restrict__ mu_normf,
+// gather(i0, g) fills g[0..7] with the dot products of centroids i0 .. i0+7.
+template <typename Gather>
+__device__ void finalize_scores(int64_t col, float y2, Gather gather,
+                                const float* __restrict__ mu_normf,
                                 const int32_t* __restrict__ counts, int c,
                                 int32_t* __restrict__ labels, float* __restrict__ ub,
                                 float* __restrict__ lb, DevStatus* __restrict__ status,
@@ -241,7 +243,7 @@ __device__ void finalize_column(int64_t col, float y2, const float* __restrict__
     int bi = INT_MAX, si = INT_MAX;
     for (int i0 = 0; i0 < c; i0 += 8) {
         float g[8];
-        gather8(gbase, nslots, Npad, m, i0, c, g);
+        gather(i0, g);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int i = i0 + q;
@@ -268,7 +270,7 @@ __device__ void finalize_column(int64_t col, float y2, const float* __restrict__
         float best_hi = INFINITY;
         for (int i0 = 0; i0 < c; i0 += 8) {
             float g[8];
-            gather8(gbase, nslots, Npad, m, i0, c, g);
+            gather(i0, g);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int i = i0 + q;
@@ -282,7 +284,7 @@ __device__ void finalize_column(int64_t col, float y2, const float* __restrict__
         for (int w = 0; w < kTcMaxClusters / 32; ++w) r->mask[w] = 0u;
         for (int i0 = 0; i0 < c; i0 += 8) {
             float g[8];
-            gather8(gbase, nslots, Npad, m, i0, c, g);
+            gather(i0, g);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int i = i0 + q;
@@ -304,6 +306,18 @@ __device__ void finalize_column(int64_t col, float y2, const float* __restrict__
         ub[col] = sqrtf(fmaxf(bs + y2 + be + yerr, 0.f)) * (1.f + 1e-6f);
         lb[col] = si < c ? sqrtf(fmaxf(ss + y2 - se - yerr, 0.f)) * (1.f - 1e-6f) : INFINITY;
     }
+}
+
+// Partial products slot-major [slot][Npad][128], column m of a 128-column tile.
+__device__ __forceinline__ void finalize_column(int64_t col, float y2, const float* __restrict__ gbase,
+                                                int nslots, int Npad, int m,
+                                                const float* __restrict__ mu_normf,
+                                                const int32_t* __restrict__ counts, int c,
+                                                int32_t* __restrict__ labels, float* __restrict__ ub,
+                                                float* __restrict__ lb, DevStatus* __restrict__ status,
+                                                RcRec* __restrict__ rc) {
+    finalize_scores(col, y2, [&](int i0, float* g) { gather8(gbase, nslots, Npad, m, i0, c, g); },
+                    mu_normf, counts, c, labels, ub, lb, status, rc);
 }
 
 // ============================================================== list kernel
@@ -896,6 +910,296 @@ __global__ void __launch_bounds__(kDnThreads, 1)
     if (warp == 1) tmem_dealloc(tmem, a.tmem_cols);
 }
 
+// ============================================================== dense kernel, operands swapped
+// For c <= 128 the centroids are the M = 128 operand and 256 data columns the
+// N operand, so each MMA instruction covers four times the columns of the
+// N = Npad form above (whose rate the issuing thread's per-instruction cost
+// bounds).  A = mu_a slabs: for Npad <= 64 ("stacked") rows 0..63 hold the raw
+// centroids (the MMA's hi part) and rows 64..127 their TF32 lo parts, so
+//   D[i] + D[64 + i] = mu_hi.y_hi + mu_lo.y_hi + mu_hi.y_lo + mu_lo.y_lo
+// from two MMAs per 8 rows (A.Y_raw and A.Y_lo); otherwise A1 = raw centroids
+// and A2 = lo parts, three MMAs (A1.Y_raw, A1.Y_lo, A2.Y_raw) into D[i].
+// Y_lo is a B operand and so lives in shared memory (a ring of 2 slabs).
+//   warp 0: TMA producer (Y slab + A slab(s) per stage), warp 1: MMA issuer,
+//   warps 2-5: split (2 columns per thread) + epilogue (partials to Gpart).
+// The scores, argmin and bounds follow in k_finalize_t, one thread per
+// column: done by the last CTA of a tile, the slot sums of 256 columns sat
+// on that CTA's critical path.
+constexpr int kTtN = 256;          // data columns per tile (MMA N)
+constexpr int kTtThreads = 192;
+constexpr int kTtMaxS = 4;
+
+struct DenseTArgs {
+    int64_t d, n, Q, T, W;   // rows, columns, slabs per tile, 256-column tiles, work units
+    int Npad, stacked, S, cmax;
+    int use_list;
+    int64_t list_min;
+};
+
+__global__ void __launch_bounds__(kTtThreads, 1)
+    k_search_dense_t(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmA,
+                     DenseTArgs a, DevStatus* __restrict__ status, const float* __restrict__ mu_normf,
+                     const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
+                     float* __restrict__ ub, float* __restrict__ lb, float* __restrict__ Gpart,
+                     float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
+                     RcRec* __restrict__ rc_list) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full[kTtMaxS], empty[kTtMaxS], conv[2], loempty[2], acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+
+    if (a.use_list && (int64_t)status->flagged < a.list_min) return;   // the list kernel handles it
+    const int64_t G = gridDim.x, b = blockIdx.x;
+    const int64_t w0 = sk_begin(b, a.W, G), w1 = sk_begin(b + 1, a.W, G);
+    if (w0 >= w1) return;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int S = a.S;
+    const int na = a.stacked ? 1 : 2;                 // A slabs per stage
+    const uint32_t y_bytes = kTtN * 128;              // 256 columns x 32 rows of FP32
+    const uint32_t a_bytes = 128 * 128;               // 128 centroid rows x 32 rows
+    const uint32_t stage_bytes = y_bytes + (uint32_t)na * a_bytes;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t lo_base = base + (uint32_t)S * stage_bytes;
+    const int64_t w_tile0 = w0 / a.Q, w_blk0 = w0 % a.Q;
+    constexpr uint32_t kTmemCols = 512;                // two 128 x 256 FP32 accumulators
+
+    if (warp == 1) {
+        tmem_alloc(&tmem_base_sh, kTmemCols);
+        tc_fence_before();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&conv[s], 4);
+            mbar_init(&loempty[s], 1);
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], 4);
+        }
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            RingPos sr(S);
+            int64_t k = 0, tile = w_tile0, blk = w_blk0;
+            for (int64_t w = w0; w < w1; ++w, ++k) {
+                if (k >= S && !mbar_wait_or_abort(&empty[sr.idx], sr.phase ^ 1u, &abort_sh)) {
+                    abort_sh = 1;
+                    break;
+                }
+                const uint32_t dst = base + (uint32_t)sr.idx * stage_bytes;
+                const int32_t row = (int32_t)(blk * kTcK);
+                mbar_expect_tx(&full[sr.idx], stage_bytes);
+                tma_load_2d(dst, &tmY, &full[sr.idx], row, (int32_t)(tile * kTtN));
+                tma_load_2d(dst + y_bytes, &tmA, &full[sr.idx], row, 0);
+                if (na == 2) tma_load_2d(dst + y_bytes + a_bytes, &tmA, &full[sr.idx], row, 128);
+                sr.next();
+                if (++blk == a.Q) {
+                    blk = 0;
+                    ++tile;
+                }
+            }
+            drain_ring(full, S, k);   // no copy may be in flight when the CTA leaves
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(128, kTtN);
+            const uint64_t dY0 = sw128_desc(base), dLo0 = sw128_desc(lo_base);
+            const uint32_t st16 = stage_bytes >> 4, y16 = y_bytes >> 4, a16 = a_bytes >> 4;
+            RingPos sr(S), lr(2), ar(2);
+            int64_t g = 0, blk = w_blk0;
+            uint64_t* last_bar = nullptr;
+            uint32_t last_par = 0;
+            for (int64_t w = w0; w < w1; ++w) {
+                const bool seg_start = (w == w0) || (blk == 0);
+                const bool seg_end = (w == w1 - 1) || (blk == a.Q - 1);
+                if (seg_start && g >= 2 &&
+                    !mbar_wait_or_abort(&acc_empty[ar.idx], ar.phase ^ 1u, &abort_sh)) {
+                    abort_sh = 1;
+                    break;
+                }
+                if (!mbar_wait_or_abort(&full[sr.idx], sr.phase, &abort_sh) ||
+                    !mbar_wait_or_abort(&conv[lr.idx], lr.phase, &abort_sh)) {
+                    abort_sh = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t dY = dY0 + (uint64_t)(sr.idx * st16);
+                const uint64_t dA1 = dY + y16, dA2 = dA1 + a16;
+                const uint64_t dLo = dLo0 + (uint64_t)(lr.idx * y16);
+                const uint32_t acc = tmem + (uint32_t)(ar.idx * kTtN);
+#pragma unroll
+                for (int ks = 0; ks < kTcK / 8; ++ks) {
+                    // 8 TF32 of K = 32 bytes = 2 descriptor address units
+                    tc_mma(acc, dA1 + 2 * ks, dY + 2 * ks, idesc, (seg_start && ks == 0) ? 0u : 1u);
+                    tc_mma(acc, dA1 + 2 * ks, dLo + 2 * ks, idesc, 1u);
+                    if (na == 2) tc_mma(acc, dA2 + 2 * ks, dY + 2 * ks, idesc, 1u);
+                }
+                tc_commit(&empty[sr.idx]);
+                tc_commit(&loempty[lr.idx]);
+                last_bar = &loempty[lr.idx];
+                last_par = lr.phase;
+                sr.next();
+                lr.next();
+                if (seg_end) {
+                    tc_commit(&acc_full[ar.idx]);
+                    ar.next();
+                    ++g;
+                }
+                if (++blk == a.Q) blk = 0;
+            }
+            // drain: the last commit covers every MMA issued before it
+            if (last_bar) mbar_wait(last_bar, last_par);
+        }
+    } else {
+        // ---------------- TF32 lo split + epilogue (warps 2-5)
+        const int m = 32 * (warp & 3) + lane;          // this thread's columns: m and m + 128
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        RingPos sr(S), lr(2), ar(2);
+        int64_t j = 0, tile = w_tile0, blk = w_blk0;
+        float ysq[2] = {0.f, 0.f}, ycomp[2] = {0.f, 0.f};
+        for (int64_t w = w0; w < w1; ++w, ++j) {
+            const bool seg_start = (w == w0) || (blk == 0);
+            const bool seg_end = (w == w1 - 1) || (blk == a.Q - 1);
+            if (seg_start) ysq[0] = ysq[1] = ycomp[0] = ycomp[1] = 0.f;
+            if (!mbar_wait_or_abort(&full[sr.idx], sr.phase, &abort_sh)) {
+                abort_sh = 1;
+                break;
+            }
+            // the lo slab is free once the MMAs of slab j - 2 are done
+            if (j >= 2 && !mbar_wait_or_abort(&loempty[lr.idx], lr.phase ^ 1u, &abort_sh)) {
+                abort_sh = 1;
+                break;
+            }
+            const uint32_t ysrc = base + (uint32_t)sr.idx * stage_bytes;
+            const uint32_t lodst = lo_base + (uint32_t)lr.idx * y_bytes;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = m + 128 * h;
+                float part = 0.f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t off = sw128_off(row, q);
+                    const float4 x = ld_shared_v4(ysrc + off);
+                    st_shared_v4(lodst + off, make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y),
+                                                          x.z - tf32_hi(x.z), x.w - tf32_hi(x.w)));
+                    part = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, part))));
+                }
+                const float y = part - ycomp[h];   // Kahan accumulation of ||y_j||^2
+                const float t = ysq[h] + y;
+                ycomp[h] = (t - ysq[h]) - y;
+                ysq[h] = t;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&conv[lr.idx]);
+            sr.next();
+            lr.next();
+            const int64_t cur_tile = tile;
+            if (++blk == a.Q) {
+                blk = 0;
+                ++tile;
+            }
+            if (!seg_end) continue;
+
+            // a tile segment is finished: drain its accumulator (lane = A row)
+            if (!mbar_wait_or_abort(&acc_full[ar.idx], ar.phase, &abort_sh)) {
+                abort_sh = 1;
+                break;
+            }
+            tc_fence_after();
+            const int slot = (int)(b - sk_owner(cur_tile * a.Q, a.W, G));
+            float* grow = Gpart + (((int64_t)cur_tile * a.cmax + slot) * 128 + m) * kTtN;
+            for (int cb = 0; cb < kTtN; cb += 16) {
+                float vv[16];
+                tc_ld16(tmem + lane_base + (uint32_t)(ar.idx * kTtN + cb), vv);
+#pragma unroll
+                for (int q = 0; q < 16; q += 4)
+                    *reinterpret_cast<float4*>(grow + cb + q) = make_float4(vv[q], vv[q + 1], vv[q + 2], vv[q + 3]);
+            }
+            float* yn = ynorm_part + ((int64_t)cur_tile * a.cmax + slot) * kTtN;
+            yn[m] = ysq[0];
+            yn[m + 128] = ysq[1];
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ar.idx]);
+            ar.next();
+        }
+    }
+    __syncthreads();
+    if (abort_sh && tid == 0) atomicOr(&status->timeout, 1);
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+// Scores, argmin (ties to the lowest index), near-tie queue and bounds of
+// every column from the swapped kernel's partials [tile][slot][128][256].
+// A block takes 64 columns of one tile: its 1024 threads first sum the
+// partials over the tile's slots (in slot order, hi and lo rows together)
+// into shared memory, with coalesced and mutually independent loads; then one
+// thread per column scores it from there.
+constexpr int kFinCols = 64, kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads)
+    k_finalize_t(DenseTArgs a, int G, DevStatus* __restrict__ status, const float* __restrict__ mu_normf,
+                 const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
+                 float* __restrict__ ub, float* __restrict__ lb, const float* __restrict__ Gpart,
+                 const float* __restrict__ ynorm_part, RcRec* __restrict__ rc_list) {
+    __shared__ float gs[128 * kFinCols];   // [centroid][column]
+    __shared__ float ys[kFinCols];
+    if (a.use_list && (int64_t)status->flagged < a.list_min) return;   // the dense kernel did not run
+    const int64_t col0 = (int64_t)blockIdx.x * kFinCols;
+    const int64_t tile = col0 / kTtN;                 // kFinCols divides kTtN
+    const int jc0 = (int)(col0 - tile * kTtN);
+    const int64_t bfirst = sk_owner(tile * a.Q, a.W, G);
+    const int64_t blast = sk_owner((tile + 1) * a.Q - 1, a.W, G);
+    const int ncontrib = (int)(blast - bfirst + 1);
+    const int t = threadIdx.x;
+    const int jl = t % kFinCols;
+    const float* gt = Gpart + (int64_t)tile * a.cmax * 128 * kTtN + jc0 + jl;
+    const int64_t slot_stride = (int64_t)128 * kTtN;
+    const bool stacked = a.stacked != 0;
+    for (int i = t / kFinCols; i < c; i += kFinThreads / kFinCols) {
+        float v = 0.f;
+#pragma unroll 4
+        for (int sl = 0; sl < ncontrib; ++sl) {
+            const float* bs = gt + sl * slot_stride;
+            const float hi = __ldcg(bs + (int64_t)i * kTtN);
+            const float lo = stacked ? __ldcg(bs + (int64_t)(64 + i) * kTtN) : 0.f;
+            v += hi + lo;
+        }
+        gs[i * kFinCols + jl] = v;
+    }
+    if (t < kFinCols) {
+        const float* yt = ynorm_part + (int64_t)tile * a.cmax * kTtN + jc0 + t;
+        float y2 = 0.f;
+        for (int sl = 0; sl < ncontrib; ++sl) y2 += __ldcg(yt + (int64_t)sl * kTtN);
+        ys[t] = y2;
+    }
+    __syncthreads();
+    if (t >= kFinCols) return;
+    const int64_t p = col0 + t;
+    if (p >= a.n) return;
+    finalize_scores(
+        p, ys[t],
+        [&](int i0, float* gq) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) gq[q] = (i0 + q < c) ? gs[(i0 + q) * kFinCols + t] : 0.f;
+        },
+        mu_normf, counts, c, labels, ub, lb, status, rc_list);
+}
+
 // ============================================================== FP64 recheck
 // Exact squared distance ||y - mu_i||^2 in FP64 by a whole CTA (the FP32
 // inputs convert exactly).  With 16-byte aligned rows every thread issues
@@ -1036,18 +1340,30 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// TF32 hi / lo parts of the centroids, zero-padded to Npad rows of dpad.
+// TF32 hi / lo parts of the centroids, zero-padded to Npad rows of dpad; and,
+// when mu_a is given, the A operand of the swapped dense kernel: for
+// stacked (Npad <= 64) rows i = raw mu_i and 64 + i = lo(mu_i) over 64 rows,
+// otherwise rows i = raw mu_i and 128 + i = lo(mu_i) over 128 rows (rows
+// beyond c zero).
 __global__ void __launch_bounds__(kThreads)
     k_mu_split(const float* __restrict__ mu, int c, int64_t d, int Npad, int64_t dpad,
-               float* __restrict__ mu_hi, float* __restrict__ mu_lo) {
+               float* __restrict__ mu_hi, float* __restrict__ mu_lo, float* __restrict__ mu_a,
+               int arows) {
+    const int rows = mu_a ? arows : Npad;
     const int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (idx >= (int64_t)Npad * dpad) return;
+    if (idx >= (int64_t)rows * dpad) return;
     const int i = (int)(idx / dpad);
     const int64_t r = idx % dpad;
     const float v = (i < c && r < d) ? mu[(int64_t)i * d + r] : 0.f;
     const float hi = tf32_hi(v);
-    mu_hi[idx] = hi;
-    mu_lo[idx] = v - hi;
+    if (i < Npad) {
+        mu_hi[idx] = hi;
+        mu_lo[idx] = v - hi;
+    }
+    if (mu_a) {
+        mu_a[idx] = v;
+        mu_a[(int64_t)arows * dpad + idx] = v - hi;
+    }
 }
 
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
@@ -1139,6 +1455,34 @@ DensePlan dense_plan(int64_t n, int64_t d, int Npad, int r_pref = 4, int ys_pref
     return p;
 }
 
+struct DenseTPlan {
+    int stacked, S, G, cmax;
+    int64_t Q, T, W;
+    size_t smem;
+};
+
+// Swapped dense kernel: 256-column tiles, 32-row slabs; stages of (Y slab,
+// A slab(s)), three when the centroids stack into one 128-row A, else two;
+// two y_lo slabs.
+DenseTPlan dense_t_plan(int64_t n, int64_t d, int Npad) {
+    DenseTPlan p;
+    p.stacked = Npad <= 64 ? 1 : 0;
+    p.S = p.stacked ? 3 : 2;
+    const size_t y_bytes = (size_t)kTtN * 128, a_bytes = 128 * 128;
+    const size_t stage = y_bytes + (p.stacked ? 1 : 2) * a_bytes;
+    p.Q = (d + kTcK - 1) / kTcK;
+    p.T = (n + kTtN - 1) / kTtN;
+    p.W = p.Q * p.T;
+    p.G = (int)std::min<int64_t>(num_sms(), p.W);
+    p.cmax = 1;
+    for (int64_t t = 0; t < p.T; ++t) {
+        const int64_t nc = sk_owner((t + 1) * p.Q - 1, p.W, p.G) - sk_owner(t * p.Q, p.W, p.G) + 1;
+        if (nc > p.cmax) p.cmax = (int)nc;
+    }
+    p.smem = (size_t)p.S * stage + 2 * y_bytes + 1024;
+    return p;
+}
+
 }  // namespace
 
 cudaError_t allow_max_dynamic_smem(const void* func) {
@@ -1174,15 +1518,24 @@ TcPlan tc_plan(int64_t n, int64_t d, int c) {
     const int64_t slots = std::max<int64_t>(kTcMaxSplit, dp.cmax);
     t.gpart = (size_t)slots * t.Npad * t.tiles * kTcM;
     t.ynorm = (size_t)slots * t.tiles * kTcM;
+    if (t.Npad <= 128) {   // the swapped kernel's partials: [tile][slot][128 rows][256 columns]
+        const DenseTPlan tp = dense_t_plan(n, d, t.Npad);
+        t.gpart = std::max(t.gpart, (size_t)tp.T * tp.cmax * 128 * kTtN);
+        t.ynorm = std::max(t.ynorm, (size_t)tp.T * tp.cmax * kTtN);
+    }
+    t.mu_a = (size_t)256 * t.dpad;
     t.rc_cap = std::min<int64_t>(n, 2048);
     return t;
 }
 
 cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
-                            float* mu_lo, cudaStream_t st) {
+                            float* mu_lo, cudaStream_t st, float* mu_a) {
     count_launches(1);
-    k_mu_split<<<grid_for((int64_t)Npad * dpad, kThreads), kThreads, 0, st>>>(mu, c, d, Npad, dpad,
-                                                                            mu_hi, mu_lo);
+    const int arows = Npad <= 64 ? 64 : 128;
+    const bool with_a = mu_a != nullptr && Npad <= 128;
+    const int rows = with_a ? arows : Npad;
+    k_mu_split<<<grid_for((int64_t)rows * dpad, kThreads), kThreads, 0, st>>>(
+        mu, c, d, Npad, dpad, mu_hi, mu_lo, with_a ? mu_a : nullptr, arows);
     return cudaGetLastError();
 }
 
@@ -1193,7 +1546,7 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
                              int32_t* tile_count, RcRec* rc_list, double* rc_dist, int64_t rc_cap,
                              bool vec, cudaStream_t st, cudaEvent_t ev_dense0, cudaEvent_t ev_dense1,
-                             bool* dense_launched_out) {
+                             bool* dense_launched_out, const float* mu_a) {
     const int Npad = tc_npad(c);
     cudaError_t e = cudaSuccess;
     // dense TMA path: FP32 operand with 16-byte aligned columns
@@ -1202,7 +1555,38 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                           (reinterpret_cast<uintptr_t>(mu_lo) % 16 == 0);
     const int64_t list_max = n / 4;   // larger queued lists use the dense kernel
     bool dense_launched = false;
-    if (dense_ok) {
+    if (dense_ok && Npad <= 128 && mu_a && (reinterpret_cast<uintptr_t>(mu_a) % 16 == 0)) {
+        CUtensorMap tmY, tmA;
+        const DenseTPlan dp = dense_t_plan(n, d, Npad);
+        if (encode_2d(&tmY, static_cast<const float*>(Y), d, n, ldy, kTcK, kTtN) &&
+            encode_2d(&tmA, mu_a, dpad, 256, dpad, kTcK, 128)) {
+            DenseTArgs a;
+            a.d = d;
+            a.n = n;
+            a.Q = dp.Q;
+            a.T = dp.T;
+            a.W = dp.W;
+            a.Npad = Npad;
+            a.stacked = dp.stacked;
+            a.S = dp.S;
+            a.cmax = dp.cmax;
+            a.use_list = list ? 1 : 0;
+            a.list_min = list_max + 1;
+            e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_search_dense_t));
+            if (e != cudaSuccess) return e;
+            count_launches(1);
+            if (ev_dense0) cudaEventRecord(ev_dense0, st);
+            k_search_dense_t<<<dp.G, kTtThreads, dp.smem, st>>>(tmY, tmA, a, status, mu_normf, counts, c,
+                                                                labels, ub, lb, Gpart, ynorm_part,
+                                                                tile_count, rc_list);
+            if (ev_dense1) cudaEventRecord(ev_dense1, st);
+            count_launches(1);
+            k_finalize_t<<<grid_for(n, kFinCols), kFinThreads, 0, st>>>(a, dp.G, status, mu_normf, counts, c,
+                                                                        labels, ub, lb, Gpart, ynorm_part,
+                                                                        rc_list);
+            dense_launched = true;
+        }
+    } else if (dense_ok) {
         CUtensorMap tmY, tmBh, tmBl;
         const DensePlan dp = dense_plan(n, d, Npad);
         if (encode_2d(&tmY, static_cast<const float*>(Y), d, n, ldy, kTcK, kTcM) &&

@@ -58,7 +58,8 @@ struct respca_ctx {
         hX, hL, hS, hp, hp0,
         mu_next, mu_old, drift, ub, lb, dl_part, sums, moved, contrib, boff, labels_pass,
         mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count, rc_dist,
-        L16, S16, T16, X16;   // BF16 state and X of the bf16 phase (precision = 1)
+        L16, S16, T16, X16,   // BF16 state and X of the bf16 phase (precision = 1)
+        mu_a;                 // centroid operand of the swapped dense search
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -154,6 +155,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
         CK(ensure(h->ynorm_part, sizeof(float) * tp.ynorm));
         CK(ensure(h->tile_count, sizeof(int32_t) * tp.tiles));
         CK(ensure(h->rc_dist, sizeof(double) * (size_t)tp.rc_cap * c));
+        CK(ensure(h->mu_a, sizeof(float) * tp.mu_a));
         // per-tile arrival counters of the search kernels start every call at zero
         CK(cudaMemsetAsync(h->tile_count.p, 0, h->tile_count.bytes, h->stream));
     }
@@ -218,14 +220,15 @@ respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64
         const int64_t dpad = (d + 31) / 32 * 32;
         const int64_t rc_cap = tc_plan(n, d, c).rc_cap;
         CK(launch_mu_split(P<float>(h->mu), c, d, Npad, dpad, P<float>(h->mu_hi), P<float>(h->mu_lo),
-                           h->stream));
+                           h->stream, P<float>(h->mu_a)));
         const bool timing = h->cfg.timing != 0;
         CK(launch_search_tc(dtype, Y, ldy, d, n, list, ds, P<float>(h->mu), P<float>(h->mu_hi),
                             P<float>(h->mu_lo), dpad, P<float>(h->mu_normf), P<int32_t>(h->counts), c,
                             p, P<float>(h->ub), P<float>(h->lb), P<float>(h->Gpart),
                             P<float>(h->ynorm_part), P<int32_t>(h->tile_count), P<RcRec>(h->rc_list),
                             P<double>(h->rc_dist), rc_cap, vec, h->stream, timing ? h->evd0 : nullptr,
-                            timing ? h->evd1 : nullptr, timing ? &h->dense_recorded : nullptr));
+                            timing ? h->evd1 : nullptr, timing ? &h->dense_recorded : nullptr,
+                            P<float>(h->mu_a)));
     } else {
         CK(launch_assign(dtype, Y, ldy, d, n, list, P<float>(h->mu), P<float>(h->mu_normf),
                          P<int32_t>(h->counts), c, p, ds, h->stream, P<float>(h->ub), P<float>(h->lb)));
@@ -766,7 +769,7 @@ respca_status respca_destroy(respca_handle h) {
                       &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->contrib, &h->boff,
                       &h->labels_pass,
                       &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count,
-                      &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16};
+                      &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->hstat) cudaFreeHost(h->hstat);

@@ -181,7 +181,7 @@ int tc_npad(int c);
 // launching.
 cudaError_t allow_max_dynamic_smem(const void* func);
 cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
-                            float* mu_lo, cudaStream_t st);
+                            float* mu_lo, cudaStream_t st, float* mu_a = nullptr);
 // Workspace sizes of the tensor-core search for an n-column, d-row operand.
 struct TcPlan {
     int Npad;          // centroids padded to a multiple of 16
@@ -190,6 +190,7 @@ struct TcPlan {
     size_t ynorm;      // floats of partial squared column norms
     int64_t tiles;     // 128-column tiles
     int64_t rc_cap;    // queued near ties whose candidate distances run spread over all SMs
+    size_t mu_a;       // floats of the swapped dense kernel's centroid operand (256 x dpad)
 };
 TcPlan tc_plan(int64_t n, int64_t d, int c);
 cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
@@ -199,7 +200,8 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
                              int32_t* tile_count, RcRec* rc_list, double* rc_dist, int64_t rc_cap,
                              bool vec, cudaStream_t st, cudaEvent_t ev_dense0 = nullptr,
-                             cudaEvent_t ev_dense1 = nullptr, bool* dense_launched = nullptr);
+                             cudaEvent_t ev_dense1 = nullptr, bool* dense_launched = nullptr,
+                             const float* mu_a = nullptr);
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float warp_sum(float v) {
