@@ -73,6 +73,8 @@ def _load():
         lib.oracle_uniform.restype = ctypes.c_double
         lib.oracle_fro.argtypes = [_D, ctypes.c_int64]
         lib.oracle_fro.restype = ctypes.c_double
+        lib.oracle_column_norms.argtypes = [_D, ctypes.c_int64, ctypes.c_int64, _D]
+        lib.oracle_column_norms.restype = None
         lib.oracle_cluster_means.argtypes = [_D, ctypes.c_int64, ctypes.c_int64, _I32,
                                              ctypes.c_int32, _D, _I64]
         lib.oracle_cluster_means.restype = None
@@ -111,6 +113,12 @@ def _load():
                                      ctypes.c_uint64, _I32, ctypes.c_int32, _D,
                                      _D, _D, _D, _I32, ctypes.POINTER(OracleStats)]
         lib.oracle_solve.restype = ctypes.c_int32
+        lib.oracle_s_step_l21.argtypes = [_D, _D, _D, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _D]
+        lib.oracle_s_step_l21.restype = None
+        lib.oracle_iteration_ex.argtypes = lib.oracle_iteration.argtypes + [ctypes.c_int32]
+        lib.oracle_iteration_ex.restype = ctypes.c_int64
+        lib.oracle_solve_ex.argtypes = lib.oracle_solve.argtypes + [ctypes.c_int32]
+        lib.oracle_solve_ex.restype = ctypes.c_int32
         _lib = lib
     return _lib
 
@@ -146,6 +154,15 @@ def uniform_stream(seed: int, count: int) -> list[float]:
 def fro(A) -> float:
     A = _f64(A)
     return _load().oracle_fro(_ptr(A, _D), A.size)
+
+
+def column_norms(S) -> np.ndarray:
+    """Sec. 6 anomaly score ||S_j||_2 per column."""
+    S = _f64(S)
+    d, n = S.shape
+    out = np.zeros(n)
+    _load().oracle_column_norms(_ptr(S, _D), d, n, _ptr(out, _D))
+    return out
 
 
 def cluster_means(Y, labels, c, mu=None):
@@ -236,7 +253,16 @@ class State:
                      self.labels.copy(), float(self.rho))
 
 
-def iteration(X, state: State, c, lam, kappa=1.5, km_max=100):
+def s_step_l21(X, L, Theta, rho):
+    """S step with the l2,1 norm (block soft-thresholding of every column)."""
+    X, L, Theta = _f64(X), _f64(L), _f64(Theta)
+    d, n = X.shape
+    S = np.zeros(X.shape, order="F")
+    _load().oracle_s_step_l21(_ptr(X, _D), _ptr(L, _D), _ptr(Theta, _D), rho, d, n, _ptr(S, _D))
+    return S
+
+
+def iteration(X, state: State, c, lam, kappa=1.5, km_max=100, snorm=0):
     """One ALM iteration (L, p, S, Theta/rho) applied to a copy of ``state``."""
     X = _f64(X)
     d, n = X.shape
@@ -244,9 +270,9 @@ def iteration(X, state: State, c, lam, kappa=1.5, km_max=100):
     rho = ctypes.c_double(s.rho)
     norms = np.zeros(3)
     steps = ctypes.c_int32(0)
-    ch = _load().oracle_iteration(_ptr(X, _D), d, n, c, lam, kappa, km_max, _ptr(s.L, _D),
+    ch = _load().oracle_iteration_ex(_ptr(X, _D), d, n, c, lam, kappa, km_max, _ptr(s.L, _D),
                                   _ptr(s.S, _D), _ptr(s.Theta, _D), _ptr(s.labels, _I32),
-                                  ctypes.byref(rho), _ptr(norms, _D), ctypes.byref(steps))
+                                  ctypes.byref(rho), _ptr(norms, _D), ctypes.byref(steps), int(snorm))
     s.rho = rho.value
     return s, norms, int(ch), int(steps.value)
 
@@ -267,7 +293,7 @@ def lagrangian(X, L, S, Theta, labels, c, lam, rho):
 
 
 def solve(X, c, lam=0.0, rho0=1e-4, kappa=1.5, tol=1e-6, max_iter=500, km_max=100, seed=0,
-          p0=None, warm: State | None = None):
+          p0=None, warm: State | None = None, snorm=0):
     """Whole RES-PCA solve. Returns (State, stats dict)."""
     X = _f64(X)
     d, n = X.shape
@@ -279,10 +305,10 @@ def solve(X, c, lam=0.0, rho0=1e-4, kappa=1.5, tol=1e-6, max_iter=500, km_max=10
     p0a = None if p0 is None else _labels(p0, n)
     rho = ctypes.c_double(s.rho)
     st = OracleStats()
-    rc = _load().oracle_solve(_ptr(X, _D), d, n, c, lam, rho0, kappa, tol, max_iter, km_max, seed,
+    rc = _load().oracle_solve_ex(_ptr(X, _D), d, n, c, lam, rho0, kappa, tol, max_iter, km_max, seed,
                               None if p0a is None else _ptr(p0a, _I32), 1 if warm is not None else 0,
                               ctypes.byref(rho), _ptr(s.L, _D), _ptr(s.S, _D), _ptr(s.Theta, _D),
-                              _ptr(s.labels, _I32), ctypes.byref(st))
+                              _ptr(s.labels, _I32), ctypes.byref(st), int(snorm))
     if rc != 0:
         raise ValueError("oracle_solve: invalid arguments")
     s.rho = rho.value

@@ -38,6 +38,16 @@ double oracle_fro(const double *A, int64_t count)
     return sqrt(s);
 }
 
+/* Sec. 6 anomaly score: ||S_j||_2 for each column j. */
+void oracle_column_norms(const double *S, int64_t d, int64_t n, double *out)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int64_t r = 0; r < d; ++r) s += S[j * d + r] * S[j * d + r];
+        out[j] = sqrt(s);
+    }
+}
+
 /* Eq. (18): the cluster-mean term 1^T P_i(D) / n_i, n_i = ||p_i|| read as the
  * number of columns in cluster i. */
 void oracle_cluster_means(const double *Y, int64_t d, int64_t n,
@@ -251,6 +261,26 @@ void oracle_s_step(const double *X, const double *L, const double *Theta,
     }
 }
 
+/* Block soft-thresholding: the prox of (1/rho)||.||_{2,1}, column by column. */
+void oracle_s_step_l21(const double *X, const double *L, const double *Theta,
+                       double rho, int64_t d, int64_t n, double *S)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double nb2 = 0.0;
+        for (int64_t r = 0; r < d; ++r) {
+            const int64_t k = j * d + r;
+            const double B = X[k] - L[k] + Theta[k] / rho;
+            nb2 += B * B;
+        }
+        const double nb = sqrt(nb2);
+        const double f = (nb > 1.0 / rho) ? 1.0 - 1.0 / (rho * nb) : 0.0;
+        for (int64_t r = 0; r < d; ++r) {
+            const int64_t k = j * d + r;
+            S[k] = f * (X[k] - L[k] + Theta[k] / rho);
+        }
+    }
+}
+
 /* Sec. 4.4, Eq. (25): Theta = Theta + rho (X - L - S). */
 void oracle_theta_step(const double *X, const double *L, const double *S,
                        double rho, int64_t count, double *Theta)
@@ -262,6 +292,15 @@ int64_t oracle_iteration(const double *X, int64_t d, int64_t n, int32_t c,
                          double lambda, double kappa, int32_t km_max,
                          double *L, double *S, double *Theta, int32_t *labels,
                          double *rho, double norms[3], int32_t *lloyd_out)
+{
+    return oracle_iteration_ex(X, d, n, c, lambda, kappa, km_max, L, S, Theta, labels, rho, norms,
+                               lloyd_out, 0);
+}
+
+int64_t oracle_iteration_ex(const double *X, int64_t d, int64_t n, int32_t c,
+                            double lambda, double kappa, int32_t km_max,
+                            double *L, double *S, double *Theta, int32_t *labels,
+                            double *rho, double norms[3], int32_t *lloyd_out, int32_t snorm)
 {
     const int64_t N = d * n;
     double *Lprev = (double *)malloc((size_t)N * sizeof(double));
@@ -279,8 +318,9 @@ int64_t oracle_iteration(const double *X, int64_t d, int64_t n, int32_t c,
     for (int32_t i = 0; i < c; ++i) active[i] = (uint8_t)(cnt[i] > 0);
     int64_t changed = 0;
     const int32_t steps = oracle_lloyd(L, d, n, c, labels, mu, active, km_max, &changed);
-    /* Sec. 4.3: S step. */
-    oracle_s_step(X, L, Theta, *rho, N, S);
+    /* Sec. 4.3: S step (l1, Eq. (24); or l2,1). */
+    if (snorm == 1) oracle_s_step_l21(X, L, Theta, *rho, d, n, S);
+    else oracle_s_step(X, L, Theta, *rho, N, S);
     /* Sec. 4.4: Theta and rho. */
     oracle_theta_step(X, L, S, *rho, N, Theta);
 
@@ -350,6 +390,18 @@ int32_t oracle_solve(const double *X, int64_t d, int64_t n, int32_t c,
                      double *L, double *S, double *Theta, int32_t *labels,
                      oracle_stats *stats)
 {
+    return oracle_solve_ex(X, d, n, c, lambda, rho0, kappa, tol, max_iter, km_max, seed, p0, warm,
+                           rho_io, L, S, Theta, labels, stats, 0);
+}
+
+int32_t oracle_solve_ex(const double *X, int64_t d, int64_t n, int32_t c,
+                        double lambda, double rho0, double kappa, double tol,
+                        int32_t max_iter, int32_t km_max, uint64_t seed,
+                        const int32_t *p0, int32_t warm, double *rho_io,
+                        double *L, double *S, double *Theta, int32_t *labels,
+                        oracle_stats *stats, int32_t snorm)
+{
+    if (snorm != 0 && snorm != 1) return -1;
     if (d <= 0 || n <= 0 || c < 1 || c > n || max_iter < 0 || km_max < 1) return -1;
     if (!(tol >= 0.0) || !isfinite(tol) || !isfinite(lambda)) return -1;
     if (!(rho0 > 0.0) || !(kappa > 0.0)) return -1;
@@ -389,8 +441,8 @@ int32_t oracle_solve(const double *X, int64_t d, int64_t n, int32_t c,
     double norms[3];
     for (int32_t t = 0; t < max_iter; ++t) {
         int32_t steps = 0;
-        st.label_changes += oracle_iteration(X, d, n, c, lambda, kappa, km_max, L, S,
-                                             Theta, labels, &rho, norms, &steps);
+        st.label_changes += oracle_iteration_ex(X, d, n, c, lambda, kappa, km_max, L, S,
+                                                Theta, labels, &rho, norms, &steps, snorm);
         st.lloyd_steps += steps;
         st.iters = t + 1;
         st.err_resid = norms[0] / nx;

@@ -52,6 +52,11 @@ double oracle_uniform(uint64_t *state);
 /* Frobenius norm, plain sequential sum of squares. */
 double oracle_fro(const double *A, int64_t count);
 
+/* Sec. 6 (anomaly detection): the l2 norm of every column of S, the score by
+ * which columns whose S is large are flagged as outliers.  S is d x n
+ * column-major; out has n entries. */
+void oracle_column_norms(const double *S, int64_t d, int64_t n, double *out);
+
 /* Cluster sizes and means of the columns of Y under labels (Eq. (18): the
  * vector 1^T P_i(D) / n_i).  Clusters with no member leave mu untouched and
  * get count 0. mu is d x c. */
@@ -96,6 +101,12 @@ int32_t oracle_init_labels(const double *X, int64_t d, int64_t n, int32_t c,
 void oracle_s_step(const double *X, const double *L, const double *Theta,
                    double rho, int64_t count, double *S);
 
+/* S step with the l2,1 norm on S, the alternative Sec. 3 names in place of
+ * l1: S = argmin (1/rho)||S||_{2,1} + 1/2 ||S - B||_F^2, column by column
+ * S_j = B_j max(0, 1 - 1/(rho ||B_j||_2)), B = X - L + Theta/rho. */
+void oracle_s_step_l21(const double *X, const double *L, const double *Theta,
+                       double rho, int64_t d, int64_t n, double *S);
+
 /* Multiplier step, Eq. (25): Theta += rho (X - L - S). */
 void oracle_theta_step(const double *X, const double *L, const double *S,
                        double rho, int64_t count, double *Theta);
@@ -110,6 +121,11 @@ int64_t oracle_iteration(const double *X, int64_t d, int64_t n, int32_t c,
                          double lambda, double kappa, int32_t km_max,
                          double *L, double *S, double *Theta, int32_t *labels,
                          double *rho, double norms[3], int32_t *lloyd_out);
+/* The same with the S norm chosen: snorm 0 = l1 (Eq. (24)), 1 = l2,1. */
+int64_t oracle_iteration_ex(const double *X, int64_t d, int64_t n, int32_t c,
+                            double lambda, double kappa, int32_t km_max,
+                            double *L, double *S, double *Theta, int32_t *labels,
+                            double *rho, double norms[3], int32_t *lloyd_out, int32_t snorm);
 
 /* Model objective, Eq. (8), through the sum-of-squares identity of Eq. (20):
  * lambda * sum_i sum_{j in i} ||L_j - mean_i(L)||^2 + ||S||_1. */
@@ -132,6 +148,13 @@ int32_t oracle_solve(const double *X, int64_t d, int64_t n, int32_t c,
                      const int32_t *p0, int32_t warm, double *rho_io,
                      double *L, double *S, double *Theta, int32_t *labels,
                      oracle_stats *stats);
+/* The same with the S norm chosen (snorm as in oracle_iteration_ex). */
+int32_t oracle_solve_ex(const double *X, int64_t d, int64_t n, int32_t c,
+                        double lambda, double rho0, double kappa, double tol,
+                        int32_t max_iter, int32_t km_max, uint64_t seed,
+                        const int32_t *p0, int32_t warm, double *rho_io,
+                        double *L, double *S, double *Theta, int32_t *labels,
+                        oracle_stats *stats, int32_t snorm);
 
 #ifdef __cplusplus
 }

@@ -456,3 +456,71 @@ def test_fro_matches_library_norm(oracle_mod):
     A = g.standard_normal((13, 7)) * 3.0
     assert oracle_mod.fro(A) == pytest.approx(np.linalg.norm(A), rel=1e-14)
     assert oracle_mod.fro(np.zeros((3, 2))) == 0.0
+
+
+# ------------------------------------------------------------------ Sec. 6 anomaly score
+def test_column_norms_match_library_and_special_cases(oracle_mod):
+    """||S_j||_2 per column: against numpy's norm, a one-hot column gives |v|,
+    a zero column 0, and scaling S scales every score."""
+    g = np.random.default_rng(21)
+    S = np.asfortranarray(g.standard_normal((53, 17)))
+    S[:, 3] = 0.0
+    S[:, 5] = 0.0
+    S[7, 5] = -2.5
+    got = oracle_mod.column_norms(S)
+    np.testing.assert_allclose(got, np.linalg.norm(S, axis=0), rtol=1e-14, atol=0)
+    assert got[3] == 0.0 and got[5] == 2.5
+    np.testing.assert_allclose(oracle_mod.column_norms(3.0 * S), 3.0 * got, rtol=1e-14)
+
+
+# ------------------------------------------------------------------ l2,1 S norm (Sec. 3 alternative)
+def test_l21_s_step_is_the_prox(oracle_mod):
+    """Block soft-thresholding minimises (1/rho)||S||_{2,1} + 1/2||S - B||^2
+    column by column: no random perturbation lowers the objective, a column
+    with rho ||B_j|| <= 1 is zeroed, and with d = 1 it reduces to the l1 step."""
+    g = np.random.default_rng(5)
+    d, n, rho = 6, 9, 1.7
+    X = np.asfortranarray(g.standard_normal((d, n)))
+    L = np.asfortranarray(g.standard_normal((d, n)) * 0.3)
+    T = np.asfortranarray(np.clip(g.standard_normal((d, n)), -1, 1))
+    B = X - L + T / rho
+    B[:, 2] *= 0.2 / (rho * np.linalg.norm(B[:, 2]))   # a column below the threshold
+    X2 = np.asfortranarray(B + L - T / rho)
+    S = oracle_mod.s_step_l21(X2, L, T, rho)
+    obj = lambda s, b: np.linalg.norm(s) / rho + 0.5 * np.sum((s - b) ** 2)
+    for j in range(n):
+        b = X2[:, j] - L[:, j] + T[:, j] / rho
+        f0 = obj(S[:, j], b)
+        for _ in range(200):
+            pert = S[:, j] + g.standard_normal(d) * 10.0 ** g.uniform(-6, -1)
+            assert obj(pert, b) >= f0 - 1e-12
+    assert np.all(S[:, 2] == 0.0)
+    X1 = np.asfortranarray(g.standard_normal((1, 40)))
+    L1 = np.asfortranarray(g.standard_normal((1, 40)) * 0.1)
+    T1 = np.asfortranarray(np.zeros((1, 40)))
+    np.testing.assert_allclose(oracle_mod.s_step_l21(X1, L1, T1, 2.0), oracle_mod.s_step(X1, L1, T1, 2.0),
+                               rtol=1e-14, atol=1e-15)
+
+
+def test_l21_theta_is_a_subgradient(oracle_mod):
+    """After an l2,1 iteration, every column of Theta lies in the subdifferential
+    of ||.||_2 at S_j: S_j / ||S_j|| where S_j != 0, otherwise inside the unit ball."""
+    g = np.random.default_rng(8)
+    d, n, c = 12, 30, 3
+    X = np.asfortranarray(g.standard_normal((d, n)))
+    X[:, 5] += 6.0   # a strongly outlying column
+    st = oracle_mod.State(np.zeros((d, n), order="F"), np.zeros((d, n), order="F"),
+                          np.zeros((d, n), order="F"), (np.arange(n) % c).astype(np.int32), 0.8)
+    for _ in range(4):
+        st, _, _, _ = oracle_mod.iteration(X, st, c, 2.0, snorm=1)
+    nz = 0
+    for j in range(n):
+        s = st.S[:, j]
+        t = st.Theta[:, j]
+        ns = np.linalg.norm(s)
+        if ns > 0:
+            nz += 1
+            np.testing.assert_allclose(t, s / ns, rtol=1e-10, atol=1e-12)
+        else:
+            assert np.linalg.norm(t) <= 1.0 + 1e-12
+    assert nz >= 1
