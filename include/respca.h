@@ -76,7 +76,12 @@ typedef struct {
                                 element and iteration -- until err <= switch_tol or err stops
                                 falling; then the state is widened to FP32 and the iterations
                                 continue on the FP32 X to tol.  Warm starts run in FP32. */
-    int32_t reserved3;
+    int32_t s_norm;          /* norm on S: 0 (default) = l1, the paper's choice (Eq. (24));
+                                1 = l2,1, the alternative Sec. 3 names: block soft-thresholding
+                                S_j = B_j max(0, 1 - 1/(rho ||B_j||)) and Theta_j = rho B_j /
+                                max(1, rho ||B_j||), in two passes per iteration (44 bytes per
+                                element).  With 1 the closed-form leading iterations and the
+                                bf16 phase are not used. */
     double switch_tol;       /* end of the bf16 phase (default 1e-2) */
 } respca_config;
 
@@ -212,6 +217,14 @@ respca_status respca_init_labels(respca_handle h, int32_t x_dtype, const void *X
  * its own. */
 respca_status respca_solve_batched(respca_handle h, int32_t batch, const respca_problem *probs,
                                    respca_stats *stats);
+
+/* Anomaly score of Sec. 6: out[j] = ||S_j||_2 for every column j of a d x n
+ * device matrix S (leading dimension lds >= d), e.g. the S of a solve; the
+ * columns with large scores are the outlying samples.  out: n device floats.
+ * Runs on `stream` (cudaStream_t, NULL = legacy default stream); asynchronous.
+ * Returns RESPCA_ERR_INVALID_ARG for null pointers or d, n < 1, lds < d. */
+respca_status respca_column_norms(const float *S, int64_t d, int64_t n, int64_t lds, float *out,
+                                  void *stream);
 
 /*
  * Initial labels WITHOUT ANY ALLOCATION.  The paper has no counterpart: this

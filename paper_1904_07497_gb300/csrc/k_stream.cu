@@ -672,6 +672,28 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Sec. 6 anomaly score ||S_j||_2, one warp per column: compensated FP32 sums
+// per lane (d / 32 squares each), then a tree over the warp.
+__global__ void __launch_bounds__(kThreads)
+    k_column_norms(const float* __restrict__ S, int64_t lds, int64_t d, int64_t n,
+                   float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t j = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); j < n; j += warps) {
+        const float* col = S + j * lds;
+        float acc = 0.f, comp = 0.f;
+        for (int64_t r = lane; r < d; r += 32) {
+            const float v = col[r];
+            const float y = fmaf(v, v, -comp);
+            const float t = acc + y;
+            comp = (t - acc) - y;
+            acc = t;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) out[j] = sqrtf(acc);
+    }
+}
+
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
 
 }  // namespace
@@ -870,6 +892,14 @@ cudaError_t launch_convert(int src_dtype, const void* src, int64_t lds, int dst_
             k_convert<TI, TO><<<grid, kThreads, 0, st>>>((const TI*)src, lds, (TO*)dst, ldd, d, n);
         });
     });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_column_norms(const float* S, int64_t lds, int64_t d, int64_t n, float* out,
+                                cudaStream_t st) {
+    count_launches(1);
+    const int grid = (int)std::min<int64_t>(grid_for(n, kThreads / 32), 152 * 32);
+    k_column_norms<<<grid, kThreads, 0, st>>>(S, lds, d, n, out);
     return cudaGetLastError();
 }
 

@@ -59,7 +59,8 @@ struct respca_ctx {
         mu_next, mu_old, drift, ub, lb, dl_part, sums, moved, contrib, boff, labels_pass,
         mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count, rc_dist,
         L16, S16, T16, X16,   // BF16 state and X of the bf16 phase (precision = 1)
-        mu_a;                 // centroid operand of the swapped dense search
+        mu_a,                 // centroid operand of the swapped dense search
+        bn_part;              // per-chunk ||B_j||^2 of the l2,1 iteration
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -124,6 +125,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
     CK(ensure(h->labels_prev, sizeof(int32_t) * n));
     CK(ensure(h->Dpart, sizeof(float) * (size_t)mt * d));
     CK(ensure(h->own_part, sizeof(float) * (size_t)nch * n));
+    CK(ensure(h->bn_part, sizeof(float) * (size_t)nch * n));
     CK(ensure(h->norm_part, sizeof(double) * 3 * (size_t)mt * nch));
     CK(ensure(h->flag_list, sizeof(int32_t) * n));
     CK(ensure(h->seedD2, sizeof(double) * n));
@@ -450,7 +452,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         int64_t ld;
         bool vec;
     } v{dtype, X, ldx, 0, L, S, pb.Th, lds, pb.vec};
-    if (h->cfg.precision == 1 && !is_warm) {
+    const bool l21 = h->cfg.s_norm == 1;
+    if (h->cfg.precision == 1 && !is_warm && !l21) {
         const int64_t ld16 = (d + 7) / 8 * 8;
         const size_t bytes = sizeof(uint16_t) * (size_t)ld16 * n;
         CK(ensure(h->L16, bytes));
@@ -531,7 +534,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     const double kappa = h->cfg.kappa;
     const double safety = safety_factor(d);
     int t_start = 0;
-    if (!is_warm && h->cfg.ramp_skip && max_iter > 0) {
+    if (!is_warm && h->cfg.ramp_skip && max_iter > 0 && !l21) {
         // Leading iterations with S = 0 and no label move, in closed form:
         // L_{t+1} = X_m + a_t g_t X_r, Theta_{t+1} = rho_t b_t g_t X_r.
         CK(cudaMemsetAsync(&ds->ramp_r2, 0, sizeof(double) + sizeof(unsigned long long) + sizeof(unsigned int),
@@ -599,10 +602,16 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         CK(cudaMemcpyAsync(h->labels_prev.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
         // L, S, Theta, norms, own distances, column movement and next-D sums in one pass
         if (timing) CK(cudaEventRecord(h->evk0, h->stream));
-        CK(launch_iteration(v.xd, v.sd, v.X, v.ldx, v.L, v.S, v.Th, v.ld, P<float>(h->mu),
-                            P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, n, sc,
-                            P<float>(h->Dpart), P<float>(h->own_part), P<float>(h->dl_part),
-                            P<double>(h->norm_part), v.vec, h->stream));
+        if (l21)
+            CK(launch_iteration_l21(v.xd, v.X, v.ldx, L, S, pb.Th, lds, P<float>(h->mu),
+                                    P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, n, sc,
+                                    P<float>(h->Dpart), P<float>(h->own_part), P<float>(h->dl_part),
+                                    P<float>(h->bn_part), P<double>(h->norm_part), v.vec, h->stream));
+        else
+            CK(launch_iteration(v.xd, v.sd, v.X, v.ldx, v.L, v.S, v.Th, v.ld, P<float>(h->mu),
+                                P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, n, sc,
+                                P<float>(h->Dpart), P<float>(h->own_part), P<float>(h->dl_part),
+                                P<double>(h->norm_part), v.vec, h->stream));
         if (timing) CK(cudaEventRecord(h->evk1, h->stream));
         out.fused_launches += 1;
         CK(launch_reduce_norms(P<double>(h->norm_part), mt, nch, ds, h->stream));
@@ -735,6 +744,8 @@ respca_status respca_create(respca_handle* out, const respca_config* cfg) {
     else respca_config_default(&c);
     if (!(c.rho0 > 0.0) || !(c.kappa > 0.0) || !std::isfinite(c.rho0) || !std::isfinite(c.kappa))
         return RESPCA_ERR_INVALID_ARG;
+    if (c.s_norm != 0 && c.s_norm != 1) return RESPCA_ERR_INVALID_ARG;
+    if (c.precision != 0 && c.precision != 1) return RESPCA_ERR_INVALID_ARG;
     int dev = c.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return RESPCA_ERR_CUDA;
     if (cudaSetDevice(dev) != cudaSuccess) return RESPCA_ERR_CUDA;
@@ -769,7 +780,8 @@ respca_status respca_destroy(respca_handle h) {
                       &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->contrib, &h->boff,
                       &h->labels_pass,
                       &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count,
-                      &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a};
+                      &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
+                      &h->bn_part};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->hstat) cudaFreeHost(h->hstat);
@@ -930,6 +942,14 @@ respca_status respca_solve_batched(respca_handle h, int32_t batch, const respca_
             return result[b];
         }
     }
+    return RESPCA_OK;
+}
+
+respca_status respca_column_norms(const float* S, int64_t d, int64_t n, int64_t lds, float* out,
+                                  void* stream) {
+    if (!S || !out || d < 1 || n < 1 || lds < d) return RESPCA_ERR_INVALID_ARG;
+    if (launch_column_norms(S, lds, d, n, out, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return RESPCA_ERR_CUDA;
     return RESPCA_OK;
 }
 

@@ -150,6 +150,16 @@ cudaError_t launch_ramp_state(int dtype, const void* X, int64_t ldx, int64_t d, 
                               const int32_t* labels, const float* mu, float alpha, float beta,
                               void* L, void* Th, int64_t lds, cudaStream_t st, int sdtype = 0);
 // dst (FP32 or BF16 per dst_sdtype, leading dimension ldd) = src (respca_dtype src_dtype)
+// The iteration with the l2,1 norm on S: two passes (L and ||B_j||; then S,
+// Theta, norms and next D sums).  bn_part: nchunks x n.
+cudaError_t launch_iteration_l21(int dtype, const void* X, int64_t ldx, float* L, float* S, float* Th,
+                                 int64_t lds, const float* mu, const int32_t* perm,
+                                 const TileDesc* tiles, int max_tiles, const DevStatus* status,
+                                 int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
+                                 float* dl_part, float* bn_part, double* norm_part, bool vec,
+                                 cudaStream_t st);
+cudaError_t launch_column_norms(const float* S, int64_t lds, int64_t d, int64_t n, float* out,
+                                cudaStream_t st);
 cudaError_t launch_convert(int src_dtype, const void* src, int64_t lds, int dst_sdtype, void* dst,
                            int64_t ldd, int64_t d, int64_t n, cudaStream_t st);
 

@@ -33,7 +33,7 @@ class respca_config(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("search_impl", ctypes.c_int32),
                 ("ramp_skip", ctypes.c_int32), ("batch_lanes", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved3", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("s_norm", ctypes.c_int32),
                 ("switch_tol", ctypes.c_double)]
 
 
@@ -105,6 +105,8 @@ def load():
                                                ctypes.c_uint64, ctypes.c_int32, _VP,
                                                ctypes.POINTER(ctypes.c_int32), _VP]
     lib.respca_init_labels_noalloc.restype = ctypes.c_int
+    lib.respca_column_norms.argtypes = [_VP, _I64, _I64, _I64, _VP, _VP]
+    lib.respca_column_norms.restype = ctypes.c_int
     lib.respca_status_string.argtypes = [ctypes.c_int]
     lib.respca_status_string.restype = ctypes.c_char_p
     lib.respca_last_error.argtypes = [_VP]
@@ -217,6 +219,20 @@ def respca_init_labels_noalloc(X, c: int, p, *, seed: int = 0, kmeans_max_iter: 
     return passes.value
 
 
+def respca_column_norms(S, out=None, stream=None):
+    """Sec. 6 anomaly score ||S_j||_2 of every column of a column-major CUDA
+    tensor S (d, n).  Returns a float32 tensor of n scores."""
+    import torch
+    d, n = S.shape
+    if out is None:
+        out = torch.empty(n, device=S.device, dtype=torch.float32)
+    s = stream if stream is not None else torch.cuda.current_stream(S.device)
+    rc = load().respca_column_norms(ctypes.c_void_p(S.data_ptr()), d, n, _colmajor(S, "S"),
+                                    ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    _check(None, rc, "respca_column_norms")
+    return out
+
+
 def respca_solve_batched(h, problems: list[dict]) -> list[dict]:
     """problems: dicts with X, c, L, S, p (and optional lam, tol, max_iter, p0)."""
     arr = (respca_problem * len(problems))()
@@ -256,13 +272,14 @@ class Solver:
     def __init__(self, rho0: float = 1e-4, kappa: float = 1.5, kmeans_max_iter: int = 100,
                  seed: int = 0, stream=None, device: int | None = None, timing: bool = False,
                  search_impl: int = 0, ramp_skip: bool = True, batch_lanes: int = 0,
-                 precision: int = 0, switch_tol: float | None = None):
+                 precision: int = 0, switch_tol: float | None = None, s_norm: int = 0):
         import torch
         cfg = respca_config_default()
         cfg.search_impl = search_impl
         cfg.ramp_skip = 1 if ramp_skip else 0
         cfg.batch_lanes = batch_lanes
         cfg.precision = precision
+        cfg.s_norm = s_norm
         if switch_tol is not None:
             cfg.switch_tol = switch_tol
         cfg.rho0, cfg.kappa, cfg.kmeans_max_iter, cfg.seed = rho0, kappa, kmeans_max_iter, seed

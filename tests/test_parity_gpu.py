@@ -378,3 +378,88 @@ def test_ramp_skip_matches_step_by_step(kind):
     np.testing.assert_array_equal(pa, pb)
     assert np.linalg.norm(La - Lb) <= 1e-6 * np.linalg.norm(Lb)
     assert np.linalg.norm(Sa - Sb) <= 1e-6 * max(np.linalg.norm(Sb), 1e-3 * np.linalg.norm(X64))
+
+
+def test_column_norms_match_oracle():
+    """Sec. 6 anomaly score ||S_j||_2 of a solve's S, against the oracle's on
+    the same FP32 values (ragged d, a column of zeros, strided leading dim)."""
+    from paper_1904_07497_gb300 import respca
+    g = np.random.default_rng(4)
+    d, n = 333, 257
+    S32 = (g.standard_normal((d, n)) * (g.random((d, n)) < 0.1)).astype(np.float32)
+    S32[:, 9] = 0.0
+    big = torch.zeros((n, d + 3), device="cuda")
+    big[:, :d].copy_(torch.from_numpy(np.ascontiguousarray(S32.T)))
+    S = big[:, :d].T                                        # lds = d + 3
+    got = respca.respca_column_norms(S).cpu().numpy().astype(np.float64)
+    ref = oracle.column_norms(S32.astype(np.float64))
+    np.testing.assert_allclose(got, ref, rtol=2e-6, atol=0)
+    assert got[9] == 0.0
+
+
+# ------------------------------------------------------------------ l2,1 S norm
+def _outlier_columns(d, n, r, n_out, seed):
+    """Rank-r columns plus n_out whole columns replaced by unrelated values
+    (sample-specific corruption, the case the l2,1 norm models)."""
+    g = np.random.default_rng(seed)
+    L0 = g.standard_normal((d, r)) @ g.standard_normal((r, n)) / np.sqrt(r)
+    X = L0.copy()
+    out = g.choice(n, n_out, replace=False)
+    X[:, out] = 3.0 * g.standard_normal((d, n_out))
+    return np.asfortranarray(X.astype(np.float32)), out
+
+
+@pytest.fixture(scope="module")
+def solver_l21():
+    from paper_1904_07497_gb300 import respca
+    s = respca.Solver(seed=3, s_norm=1)
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("T", [0, 14, 30])
+def test_l21_single_iteration_from_oracle_state(solver_l21, T):
+    """One GPU l2,1 iteration from an oracle state equals the oracle's."""
+    X32, _ = _outlier_columns(300, 260, 6, 12, seed=2)
+    X64 = X32.astype(np.float64)
+    c, lam = 6, np.sqrt(300)
+    p0, _ = oracle.init_labels(X64, c, seed=0)
+    st = oracle.State(np.zeros((300, 260), order="F"), np.zeros((300, 260), order="F"),
+                      np.zeros((300, 260), order="F"), p0, 1e-2)
+    for _ in range(T):
+        st, *_ = oracle.iteration(X64, st, c, lam, snorm=1)
+    st = _rounded(st)
+    ref, norms, _, _ = oracle.iteration(X64, st, c, lam, snorm=1)
+    got = _run(solver_l21, X32, c, 1, None, warm=st)
+    np.testing.assert_array_equal(got["p"], ref.labels)
+    _check_state(got["L"], got["S"], ref, X64)
+    tr_ref = ref.Theta / st.rho
+    tr_got = got["Theta"] / st.rho
+    assert np.abs(tr_got - tr_ref).max() <= 1e-5 * max(np.abs(X64).max(), 1.0)
+    e_ref = max(norms) / np.linalg.norm(X64)
+    assert got["stats"]["err"] == pytest.approx(e_ref, rel=1e-4, abs=1e-7)
+
+
+def test_l21_fixed_iterations_and_convergence():
+    """40 l2,1 iterations from the same labels match the oracle; a solve to
+    1e-6 converges, with the outlying columns carrying the largest
+    ||S_j||_2 (the Sec. 6 score)."""
+    from paper_1904_07497_gb300 import respca
+    X32, out = _outlier_columns(300, 260, 6, 12, seed=2)
+    X64 = X32.astype(np.float64)
+    c = 6
+    p0, _ = oracle.init_labels(X64, c, seed=0)
+    ref, _ = oracle.solve(X64, c, tol=0.0, max_iter=40, p0=p0, snorm=1)
+    s = respca.Solver(seed=3, s_norm=1)
+    X = _dev(X32)
+    r = s.solve(X, c, tol=0.0, max_iter=40, p0=torch.from_numpy(p0).cuda())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(r.p.cpu().numpy(), ref.labels)
+    _check_state(_host(r.L), _host(r.S), ref, X64)
+    r2 = s.solve(X, c, tol=1e-6, max_iter=500)
+    torch.cuda.synchronize()
+    assert r2.stats["converged"] == 1 and r2.stats["err"] <= 1e-6
+    score = respca.respca_column_norms(r2.S).cpu().numpy()
+    top = set(np.argsort(-score)[:len(out)].tolist())
+    assert top == set(out.tolist())
+    s.close()
