@@ -694,6 +694,21 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+__global__ void k_lloyd_init(DevStatus* __restrict__ status, int passes0) {
+    status->acc_flagged = 0;
+    status->acc_passes = passes0;
+    status->acc_rechecked = 0;
+}
+
+__global__ void k_lloyd_pass_end(DevStatus* __restrict__ status, cudaGraphConditionalHandle cond,
+                                 int max_passes) {
+    status->acc_flagged += status->flagged;
+    status->acc_rechecked += status->rechecked;
+    const int passes = ++status->acc_passes;
+    const bool more = status->changed != 0 && passes < max_passes && status->timeout == 0;
+    cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
 
 }  // namespace
@@ -900,6 +915,19 @@ cudaError_t launch_column_norms(const float* S, int64_t lds, int64_t d, int64_t 
     count_launches(1);
     const int grid = (int)std::min<int64_t>(grid_for(n, kThreads / 32), 152 * 32);
     k_column_norms<<<grid, kThreads, 0, st>>>(S, lds, d, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lloyd_init(DevStatus* status, int passes0, cudaStream_t st) {
+    count_launches(1);
+    k_lloyd_init<<<1, 1, 0, st>>>(status, passes0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lloyd_pass_end(DevStatus* status, cudaGraphConditionalHandle cond, int max_passes,
+                                  cudaStream_t st) {
+    count_launches(1);
+    k_lloyd_pass_end<<<1, 1, 0, st>>>(status, cond, max_passes);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,14 @@ struct respca_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;      // a batch lane's stream, created and destroyed with it
+    cudaStream_t cap_stream = nullptr;      // private stream the Lloyd-pass graph is captured on
+    struct LloydGraph {                     // device-run Lloyd loop, reused while its key holds
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t key = 0;
+        int64_t launches_per_pass = 0;
+    } lloyd_graph[2];
+    int lloyd_graph_next = 0;               // slot the next new graph replaces
     std::vector<respca_ctx*> lanes;         // batch lanes (respca_solve_batched), made on first use
     respca_config cfg{};
     std::string last_error;
@@ -108,6 +116,19 @@ int max_tiles_for(int64_t n, int c) { return (int)((n + kTileCols - 1) / kTileCo
 int nchunks_for(int64_t d) { return (int)((d + kChunkRows - 1) / kChunkRows); }
 
 size_t elem_size(int dtype) { return dtype == RESPCA_F32 ? 4 : 2; }
+
+// Every device buffer of the workspace.
+std::vector<DevBuf*> all_bufs(respca_ctx* h) {
+    return {&h->theta, &h->mu, &h->mu_norm2, &h->mu_normf, &h->pair_ss, &h->sep2, &h->perm,
+                      &h->counts, &h->tile_off, &h->tiles, &h->labels_prev, &h->Dpart, &h->own_part,
+                      &h->norm_part, &h->flag_list, &h->seedD2, &h->centers, &h->seed_u, &h->fro_part,
+                      &h->status, &h->hX, &h->hL, &h->hS, &h->hp, &h->hp0, &h->mu_next, &h->mu_old,
+                      &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->contrib, &h->boff,
+                      &h->labels_pass,
+                      &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count,
+                      &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
+                      &h->bn_part};
+}
 
 respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64_t lds,
                                bool need_theta) {
@@ -258,6 +279,150 @@ struct SearchCounts {
     int64_t rechecked = 0;
 };
 
+// One Lloyd pass, first half: degrade the bounds by the centroid drift,
+// queue the columns they cannot settle, search them.
+respca_status lloyd_pass_search(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ldy,
+                                int64_t d, int64_t n, int c, int32_t* p, bool vec) {
+    (void)mode;
+    DevStatus* ds = P<DevStatus>(h->status);
+    CK(zero_counters(h));
+    CK(launch_flag_bounds(kBoundsLloyd, nullptr, nullptr, 0, n, c, p, P<int32_t>(h->counts), nullptr,
+                          1.0, P<double>(h->drift), P<float>(h->ub), P<float>(h->lb),
+                          P<int32_t>(h->flag_list), ds, h->stream));
+    CK(cudaMemcpyAsync(h->labels_pass.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
+    return search(h, dtype, Y, ldy, d, n, P<int32_t>(h->flag_list), c, p, vec);
+}
+
+// Second half: move the changed columns between the cluster sums and form the
+// new centroids, their norms and drift.
+respca_status lloyd_pass_update(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ldy,
+                                int64_t d, int64_t n, int c, int32_t* p) {
+    DevStatus* ds = P<DevStatus>(h->status);
+    const float* Lp = (mode == kSumL) ? static_cast<const float*>(Y) : nullptr;
+    CK(launch_moved(p, P<int32_t>(h->labels_pass), n, c, P<int4>(h->moved), P<int2>(h->contrib),
+                    P<int32_t>(h->boff), P<int32_t>(h->counts), ds, h->stream));
+    CK(launch_delta_sums(mode, dtype, Y, ldy, Lp, ldy, P<int2>(h->contrib), P<int32_t>(h->boff), c, d,
+                         P<double>(h->sums), h->stream));
+    CK(cudaMemcpyAsync(h->mu_old.p, h->mu.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice,
+                       h->stream));
+    CK(launch_centroids_from_sums(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
+                                  h->stream));
+    CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
+                       P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+    return RESPCA_OK;
+}
+
+// Fingerprint of everything a captured pass depends on: the call's arguments
+// and every workspace pointer (a reallocation changes it).
+uint64_t lloyd_key(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
+                   int c, const int32_t* p, bool vec, int max_passes) {
+    uint64_t k = 1469598103934665603ULL;
+    auto mix = [&](uint64_t v) { k = (k ^ v) * 1099511628211ULL; };
+    mix((uint64_t)mode);
+    mix((uint64_t)dtype);
+    mix(reinterpret_cast<uintptr_t>(Y));
+    mix((uint64_t)ldy);
+    mix((uint64_t)d);
+    mix((uint64_t)n);
+    mix((uint64_t)c);
+    mix(reinterpret_cast<uintptr_t>(p));
+    mix(vec ? 1u : 0u);
+    mix((uint64_t)max_passes);
+    mix((uint64_t)h->cfg.search_impl);
+    mix(reinterpret_cast<uintptr_t>(h->stream));
+    for (DevBuf* b : all_bufs(h)) mix(reinterpret_cast<uintptr_t>(b->p));
+    return k;
+}
+
+// The Lloyd loop run on the device: one pass is captured once into the body
+// of a conditional while node; a one-thread kernel at the end of each pass's
+// search adds the pass counters and sets the condition.  The host reads the
+// status once, after the loop.  The centroid update runs after the last pass
+// too; when the loop stopped at max_passes with labels still moving, the
+// centroids of that pass's search are put back (the host loop stops before
+// that update).  RESPCA_ERR_UNSUPPORTED: no graph could be made here.
+respca_status lloyd_loop_on_device(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ldy,
+                                   int64_t d, int64_t n, int c, int32_t* p, bool vec, int max_passes,
+                                   SearchCounts* sc) {
+    const uint64_t key = lloyd_key(h, mode, dtype, Y, ldy, d, n, c, p, vec, max_passes);
+    respca_ctx::LloydGraph* g = nullptr;
+    for (auto& e : h->lloyd_graph)
+        if (e.exec && e.key == key) g = &e;
+    if (!g) {
+        if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return RESPCA_ERR_UNSUPPORTED;
+        g = &h->lloyd_graph[h->lloyd_graph_next];
+        h->lloyd_graph_next ^= 1;
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        *g = respca_ctx::LloydGraph{};
+        cudaGraph_t graph = nullptr;
+        cudaGraphConditionalHandle cond;
+        cudaGraphNodeParams cp = {};
+        cudaGraphNode_t node;
+        if (cudaGraphCreate(&graph, 0) != cudaSuccess) return RESPCA_ERR_UNSUPPORTED;
+        if (cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return RESPCA_ERR_UNSUPPORTED;
+        }
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return RESPCA_ERR_UNSUPPORTED;
+        }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        // capture one pass on the private stream
+        cudaStream_t user = h->stream;
+        h->stream = h->cap_stream;
+        const int64_t l0 = t_kernel_launches;
+        respca_status rs = RESPCA_OK;
+        if (cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            rs = RESPCA_ERR_UNSUPPORTED;
+        } else {
+            rs = lloyd_pass_search(h, mode, dtype, Y, ldy, d, n, c, p, vec);
+            if (rs == RESPCA_OK && launch_lloyd_pass_end(P<DevStatus>(h->status), cond, max_passes,
+                                                         h->stream) != cudaSuccess)
+                rs = RESPCA_ERR_CUDA;
+            if (rs == RESPCA_OK) rs = lloyd_pass_update(h, mode, dtype, Y, ldy, d, n, c, p);
+            cudaGraph_t captured = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(h->stream, &captured);
+            if (rs == RESPCA_OK && ec != cudaSuccess) rs = RESPCA_ERR_UNSUPPORTED;
+        }
+        h->stream = user;
+        g->launches_per_pass = t_kernel_launches - l0;
+        t_kernel_launches = l0;
+        cudaGetLastError();
+        if (rs == RESPCA_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) rs = RESPCA_ERR_UNSUPPORTED;
+        if (rs != RESPCA_OK) {
+            cudaGetLastError();
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+            cudaGraphDestroy(graph);
+            *g = respca_ctx::LloydGraph{};
+            return rs == RESPCA_ERR_CUDA ? RESPCA_ERR_UNSUPPORTED : rs;
+        }
+        g->graph = graph;
+        g->key = key;
+    }
+    DevStatus* ds = P<DevStatus>(h->status);
+    CK(launch_lloyd_init(ds, sc->passes, h->stream));
+    CK(cudaGraphLaunch(g->exec, h->stream));
+    respca_status rs = read_status(h);
+    if (rs != RESPCA_OK) return rs;
+    const int run = h->hstat->acc_passes - sc->passes;
+    t_kernel_launches += (int64_t)run * g->launches_per_pass;
+    sc->passes = h->hstat->acc_passes;
+    sc->assigned += h->hstat->acc_flagged;
+    sc->rechecked += h->hstat->acc_rechecked;
+    if (h->hstat->changed != 0)   // stopped at max_passes: back to the last search's centroids
+        CK(cudaMemcpyAsync(h->mu.p, h->mu_old.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice,
+                           h->stream));
+    return RESPCA_OK;
+}
+
 // Lloyd passes after an assignment moved some labels (Sec. 4.2 p step, or
 // the initial labels): centroids become the means of the columns of Y under
 // the new labels (the first time from a full pass over Y, then by moving only
@@ -280,13 +445,13 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
                         P<float>(h->mu), h->stream, P<double>(h->sums)));
     CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
                        P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+    if (h->cfg.timing == 0 && sc->passes < max_passes) {
+        const respca_status rs = lloyd_loop_on_device(h, mode, dtype, Y, ldy, d, n, c, p, vec, max_passes, sc);
+        if (rs != RESPCA_ERR_UNSUPPORTED) return rs;
+        h->last_error.clear();   // no graph on this setup: the host runs the loop below
+    }
     while (sc->passes < max_passes) {
-        CK(zero_counters(h));
-        CK(launch_flag_bounds(kBoundsLloyd, nullptr, nullptr, 0, n, c, p, P<int32_t>(h->counts),
-                              nullptr, 1.0, P<double>(h->drift), P<float>(h->ub), P<float>(h->lb),
-                              P<int32_t>(h->flag_list), ds, h->stream));
-        CK(cudaMemcpyAsync(h->labels_pass.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
-        respca_status rs = search(h, dtype, Y, ldy, d, n, P<int32_t>(h->flag_list), c, p, vec);
+        respca_status rs = lloyd_pass_search(h, mode, dtype, Y, ldy, d, n, c, p, vec);
         if (rs != RESPCA_OK) return rs;
         rs = read_status(h);
         if (rs != RESPCA_OK) return rs;
@@ -296,16 +461,8 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
         sc->assigned += h->hstat->flagged;
         sc->rechecked += h->hstat->rechecked;
         if (h->hstat->changed == 0 || sc->passes >= max_passes) break;
-        CK(launch_moved(p, P<int32_t>(h->labels_pass), n, c, P<int4>(h->moved), P<int2>(h->contrib),
-                        P<int32_t>(h->boff), P<int32_t>(h->counts), ds, h->stream));
-        CK(launch_delta_sums(mode, dtype, Y, ldy, Lp, ldy, P<int2>(h->contrib), P<int32_t>(h->boff), c,
-                             d, P<double>(h->sums), h->stream));
-        CK(cudaMemcpyAsync(h->mu_old.p, h->mu.p, sizeof(float) * (size_t)c * d,
-                           cudaMemcpyDeviceToDevice, h->stream));
-        CK(launch_centroids_from_sums(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
-                                      h->stream));
-        CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
-                           P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+        rs = lloyd_pass_update(h, mode, dtype, Y, ldy, d, n, c, p);
+        if (rs != RESPCA_OK) return rs;
     }
     return RESPCA_OK;
 }
@@ -641,7 +798,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         const double r2 = h->hstat->norm2[0], dl2 = h->hstat->norm2[1], ds2 = h->hstat->norm2[2];
 
         if (h->hstat->changed == 0) {
-            std::swap(h->mu, h->mu_next);
+            CK(cudaMemcpyAsync(h->mu.p, h->mu_next.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice, h->stream));
         } else {
             // Lloyd on the columns of L until no label changes
             SearchCounts scount;
@@ -661,7 +818,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
                              v.vec, h->stream, v.sd));
             rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
             if (rs != RESPCA_OK) return rs;
-            std::swap(h->mu, h->mu_next);
+            CK(cudaMemcpyAsync(h->mu.p, h->mu_next.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice, h->stream));
             CK(launch_count_changed(p, P<int32_t>(h->labels_prev), n, ds, h->stream));
         }
         rho = rho_next;
@@ -693,7 +850,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
                                  P<float>(h->Dpart), v.vec, h->stream, 0));
                 rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
                 if (rs != RESPCA_OK) return rs;
-                std::swap(h->mu, h->mu_next);
+                CK(cudaMemcpyAsync(h->mu.p, h->mu_next.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice, h->stream));
             }
         }
     }
@@ -773,16 +930,7 @@ respca_status respca_destroy(respca_handle h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&h->theta, &h->mu, &h->mu_norm2, &h->mu_normf, &h->pair_ss, &h->sep2, &h->perm,
-                      &h->counts, &h->tile_off, &h->tiles, &h->labels_prev, &h->Dpart, &h->own_part,
-                      &h->norm_part, &h->flag_list, &h->seedD2, &h->centers, &h->seed_u, &h->fro_part,
-                      &h->status, &h->hX, &h->hL, &h->hS, &h->hp, &h->hp0, &h->mu_next, &h->mu_old,
-                      &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->contrib, &h->boff,
-                      &h->labels_pass,
-                      &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count,
-                      &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
-                      &h->bn_part};
-    for (DevBuf* b : bufs)
+    for (DevBuf* b : all_bufs(h))
         if (b->p) cudaFree(b->p);
     if (h->hstat) cudaFreeHost(h->hstat);
     if (h->hseed_u) cudaFreeHost(h->hseed_u);
@@ -793,6 +941,11 @@ respca_status respca_destroy(respca_handle h) {
     if (h->evk1) cudaEventDestroy(h->evk1);
     if (h->evd0) cudaEventDestroy(h->evd0);
     if (h->evd1) cudaEventDestroy(h->evd1);
+    for (auto& g : h->lloyd_graph) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
     return RESPCA_OK;

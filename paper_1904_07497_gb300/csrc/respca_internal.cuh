@@ -61,6 +61,9 @@ struct DevStatus {
     int32_t moved;          // entries of the last moved-column list
     int32_t timeout;        // a bounded device-side wait gave up
     int32_t pad;
+    int64_t acc_flagged;    // device-run Lloyd loop: columns searched over its passes
+    int32_t acc_passes;     //   passes run (including those before the loop)
+    int32_t acc_rechecked;  //   near ties re-decided
 };
 
 // Modes of the bound-based pruning kernel.
@@ -158,6 +161,12 @@ cudaError_t launch_iteration_l21(int dtype, const void* X, int64_t ldx, float* L
                                  int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
                                  float* dl_part, float* bn_part, double* norm_part, bool vec,
                                  cudaStream_t st);
+// Device-run Lloyd loop: start its counters at `passes0` passes; at the end
+// of each pass, add the pass's counters and set the loop's condition (labels
+// changed, fewer than max_passes passes, no wait gave up).
+cudaError_t launch_lloyd_init(DevStatus* status, int passes0, cudaStream_t st);
+cudaError_t launch_lloyd_pass_end(DevStatus* status, cudaGraphConditionalHandle cond, int max_passes,
+                                  cudaStream_t st);
 cudaError_t launch_column_norms(const float* S, int64_t lds, int64_t d, int64_t n, float* out,
                                 cudaStream_t st);
 cudaError_t launch_convert(int src_dtype, const void* src, int64_t lds, int dst_sdtype, void* dst,
