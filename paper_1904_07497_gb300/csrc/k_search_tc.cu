@@ -1200,14 +1200,38 @@ __global__ void __launch_bounds__(kFinThreads)
         mu_normf, counts, c, labels, ub, lb, status, rc_list);
 }
 
-// ============================================================== FP64 recheck
-// Exact squared distance ||y - mu_i||^2 in FP64 by a whole CTA (the FP32
-// inputs convert exactly).  With 16-byte aligned rows every thread issues
-// all of its loads before the arithmetic (d <= 16384 per pass of 4 float4).
+// ============================================================== exact recheck
+// Squared distance ||y - mu_i||^2 by a whole CTA, to about 2^-43 relative, in
+// double-float FP32 arithmetic (the FP64 pipe of this part runs about 2 FMA
+// per clock per SM, 64 times below FP32):
+//   e_h + e_l = y - mu exactly (Knuth's TwoSum), e_h^2 = p + p_err exactly
+//   (product with an FMA), the rest 2 e_h e_l + e_l^2 + p_err is < 2^-22 of
+//   p; the running sum is carried as s_h + s_l with TwoSum on s_h + p.
+// Each thread's (s_h, s_l) becomes one FP64 value; the CTA adds those in FP64.
+// Equal inputs give bit-identical results, so exact ties (repeated columns)
+// stay ties and go to the lowest index.
+struct DfSum {
+    float h = 0.f, l = 0.f;
+    // explicitly rounded operations: a contraction into an FMA would break
+    // the error-free transformations
+    __device__ __forceinline__ void add_sq_diff(float yv, float mv) {
+        const float e = __fsub_rn(yv, mv);
+        const float bv = __fsub_rn(e, yv);
+        const float el = __fadd_rn(__fsub_rn(yv, __fsub_rn(e, bv)), __fsub_rn(-mv, bv));  // e + el = yv - mv
+        const float p = __fmul_rn(e, e);
+        const float pe = fmaf(e, e, -p);                                               // e^2 = p + pe
+        const float low = fmaf(2.f * e, el, pe) + el * el;
+        const float t = __fadd_rn(h, p);                                               // TwoSum(h, p)
+        const float bp = __fsub_rn(t, h);
+        l += __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(p, bp)) + low;
+        h = t;
+    }
+};
+
 template <typename TY>
-__device__ double block_dist2_fp64(const TY* __restrict__ y, const float* __restrict__ mrow,
-                                   int64_t d, bool vec, double* red) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+__device__ double block_dist2_exact(const TY* __restrict__ y, const float* __restrict__ mrow, int64_t d,
+                                    bool vec, double* red) {
+    DfSum a0, a1;
     if (vec && sizeof(TY) == 4) {
         const float4* y4 = reinterpret_cast<const float4*>(y);
         const float4* m4 = reinterpret_cast<const float4*>(mrow);
@@ -1222,38 +1246,17 @@ __device__ double block_dist2_fp64(const TY* __restrict__ y, const float* __rest
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const double e0 = (double)yv[u].x - (double)mv[u].x;
-                const double e1 = (double)yv[u].y - (double)mv[u].y;
-                const double e2 = (double)yv[u].z - (double)mv[u].z;
-                const double e3 = (double)yv[u].w - (double)mv[u].w;
-                a0 = fma(e0, e0, a0);
-                a1 = fma(e1, e1, a1);
-                a2 = fma(e2, e2, a2);
-                a3 = fma(e3, e3, a3);
+                a0.add_sq_diff(yv[u].x, mv[u].x);
+                a1.add_sq_diff(yv[u].y, mv[u].y);
+                a0.add_sq_diff(yv[u].z, mv[u].z);
+                a1.add_sq_diff(yv[u].w, mv[u].w);
             }
         }
-        for (int64_t r = d4 * 4 + threadIdx.x; r < d; r += kThreads) {
-            const double e0 = (double)XLoad<TY>::one(y + r) - (double)mrow[r];
-            a0 = fma(e0, e0, a0);
-        }
+        for (int64_t r = d4 * 4 + threadIdx.x; r < d; r += kThreads) a0.add_sq_diff(XLoad<TY>::one(y + r), mrow[r]);
     } else {
-        int64_t r = threadIdx.x;
-        for (; r + 3 * kThreads < d; r += 4 * kThreads) {
-            const double e0 = (double)XLoad<TY>::one(y + r) - (double)mrow[r];
-            const double e1 = (double)XLoad<TY>::one(y + r + kThreads) - (double)mrow[r + kThreads];
-            const double e2 = (double)XLoad<TY>::one(y + r + 2 * kThreads) - (double)mrow[r + 2 * kThreads];
-            const double e3 = (double)XLoad<TY>::one(y + r + 3 * kThreads) - (double)mrow[r + 3 * kThreads];
-            a0 = fma(e0, e0, a0);
-            a1 = fma(e1, e1, a1);
-            a2 = fma(e2, e2, a2);
-            a3 = fma(e3, e3, a3);
-        }
-        for (; r < d; r += kThreads) {
-            const double e0 = (double)XLoad<TY>::one(y + r) - (double)mrow[r];
-            a0 = fma(e0, e0, a0);
-        }
+        for (int64_t r = threadIdx.x; r < d; r += kThreads) a0.add_sq_diff(XLoad<TY>::one(y + r), mrow[r]);
     }
-    double t = warp_sum((a0 + a1) + (a2 + a3));
+    double t = warp_sum(((double)a0.h + (double)a0.l) + ((double)a1.h + (double)a1.l));
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
@@ -1263,8 +1266,7 @@ __device__ double block_dist2_fp64(const TY* __restrict__ y, const float* __rest
     return s;
 }
 
-// FP64 re-decision of near ties.  The FP64 pipe is the limit here (about 2
-// FMA per clock per SM on this part), so the candidate distances of the
+// Exact re-decision of near ties.  The candidate distances of the
 // first rc_cap queued columns are spread over every SM, one CTA per
 // (column, candidate) pair; k_search_recheck_pick then decides each column
 // over its candidates in increasing index (ties keep the lowest).  Columns
@@ -1283,7 +1285,7 @@ __global__ void __launch_bounds__(kThreads)
         const int ci = (int)(pr - k * c);
         const RcRec& rec = rc_list[k];
         if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;   // uniform over the CTA
-        const double dist = block_dist2_fp64<TY>(Y + (int64_t)rec.col * ldy, mu + (int64_t)ci * d, d, vec, red);
+        const double dist = block_dist2_exact<TY>(Y + (int64_t)rec.col * ldy, mu + (int64_t)ci * d, d, vec, red);
         if (threadIdx.x == 0) rc_dist[pr] = dist;
         __syncthreads();
     }
@@ -1318,7 +1320,7 @@ __global__ void __launch_bounds__(kThreads)
             const TY* y = Y + col * ldy;
             for (int ci = 0; ci < c; ++ci) {
                 if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
-                const double dist = block_dist2_fp64<TY>(y, mu + (int64_t)ci * d, d, vec, red);
+                const double dist = block_dist2_exact<TY>(y, mu + (int64_t)ci * d, d, vec, red);
                 if (dist < best) {
                     best = dist;
                     besti = ci;
