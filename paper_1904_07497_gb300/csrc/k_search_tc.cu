@@ -945,6 +945,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                      RcRec* __restrict__ rc_list) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full[kTtMaxS], empty[kTtMaxS], conv[2], loempty[2], acc_full[2], acc_empty[2];
+    __shared__ float xch[64][17];   // lo rows handed to the hi rows in the epilogue (stacked)
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
 
@@ -1121,13 +1122,30 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             }
             tc_fence_after();
             const int slot = (int)(b - sk_owner(cur_tile * a.Q, a.W, G));
-            float* grow = Gpart + (((int64_t)cur_tile * a.cmax + slot) * 128 + m) * kTtN;
+            // stacked: row i + 64 (lo part) is added into row i before the store
+            const int rows_out = a.stacked ? 64 : 128;
+            const bool lo_row = a.stacked && m >= 64;
+            float* grow = Gpart + (((int64_t)cur_tile * a.cmax + slot) * rows_out + (m & (rows_out - 1))) * kTtN;
             for (int cb = 0; cb < kTtN; cb += 16) {
                 float vv[16];
                 tc_ld16(tmem + lane_base + (uint32_t)(ar.idx * kTtN + cb), vv);
+                if (a.stacked) {
+                    if (lo_row) {
 #pragma unroll
-                for (int q = 0; q < 16; q += 4)
-                    *reinterpret_cast<float4*>(grow + cb + q) = make_float4(vv[q], vv[q + 1], vv[q + 2], vv[q + 3]);
+                        for (int q = 0; q < 16; ++q) xch[m - 64][q] = vv[q];
+                    }
+                    named_sync(1, 128);
+                    if (!lo_row) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) vv[q] += xch[m][q];
+                    }
+                    named_sync(1, 128);
+                }
+                if (!lo_row) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4*>(grow + cb + q) = make_float4(vv[q], vv[q + 1], vv[q + 2], vv[q + 3]);
+                }
             }
             float* yn = ynorm_part + ((int64_t)cur_tile * a.cmax + slot) * kTtN;
             yn[m] = ysq[0];
@@ -1145,7 +1163,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
 }
 
 // Scores, argmin (ties to the lowest index), near-tie queue and bounds of
-// every column from the swapped kernel's partials [tile][slot][128][256].
+// every column from the swapped kernel's partials [tile][slot][rows][256]
+// (rows = 64 when stacked, hi and lo parts already added; else 128).
 // A block takes 64 columns of one tile: its 1024 threads first sum the
 // partials over the tile's slots (in slot order, hi and lo rows together)
 // into shared memory, with coalesced and mutually independent loads; then one
@@ -1167,18 +1186,13 @@ __global__ void __launch_bounds__(kFinThreads)
     const int ncontrib = (int)(blast - bfirst + 1);
     const int t = threadIdx.x;
     const int jl = t % kFinCols;
-    const float* gt = Gpart + (int64_t)tile * a.cmax * 128 * kTtN + jc0 + jl;
-    const int64_t slot_stride = (int64_t)128 * kTtN;
-    const bool stacked = a.stacked != 0;
+    const int rows = a.stacked ? 64 : 128;   // the stacked kernel has added the lo rows in
+    const float* gt = Gpart + (int64_t)tile * a.cmax * rows * kTtN + jc0 + jl;
+    const int64_t slot_stride = (int64_t)rows * kTtN;
     for (int i = t / kFinCols; i < c; i += kFinThreads / kFinCols) {
         float v = 0.f;
 #pragma unroll 4
-        for (int sl = 0; sl < ncontrib; ++sl) {
-            const float* bs = gt + sl * slot_stride;
-            const float hi = __ldcg(bs + (int64_t)i * kTtN);
-            const float lo = stacked ? __ldcg(bs + (int64_t)(64 + i) * kTtN) : 0.f;
-            v += hi + lo;
-        }
+        for (int sl = 0; sl < ncontrib; ++sl) v += __ldcg(gt + sl * slot_stride + (int64_t)i * kTtN);
         gs[i * kFinCols + jl] = v;
     }
     if (t < kFinCols) {
