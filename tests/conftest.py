@@ -10,7 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
-    config.addinivalue_line("markers", "slow: longer CPU-only oracle runs")
+    config.addinivalue_line("markers", "slow: long oracle runs (minutes of one host core)")
 
 
 @pytest.fixture(scope="session")
