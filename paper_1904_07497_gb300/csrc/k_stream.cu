@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // Cluster sums after a Lloyd pass moved some columns: sums_i += (columns that
-// joined i) - (columns that left i).  k_moved lists each cluster's signed
+// joined i) - (columns that left i), of X, L or D = X - S + Theta inv_rho.  k_moved lists each cluster's signed
 // contributions contiguously (bucket i = contrib[boff[i] .. boff[i+1])).  A
 // CTA takes 128 rows of one cluster and adds its bucket in double-float
 // FP32 (TwoSum: the running sum is hi + lo to about 2^-44), then makes one
@@ -191,6 +191,7 @@ constexpr int kDeltaThreads = 128;
 template <int MODE, typename TX>
 __global__ void __launch_bounds__(kDeltaThreads)
     k_delta_sums(const TX* __restrict__ X, int64_t ldx, const float* __restrict__ L, int64_t lds,
+                 const float* __restrict__ S, const float* __restrict__ Th, float inv_rho,
                  const int2* __restrict__ contrib, const int32_t* __restrict__ boff, int c, int64_t d,
                  double* __restrict__ sums) {
     const int64_t r = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
@@ -202,7 +203,10 @@ __global__ void __launch_bounds__(kDeltaThreads)
         for (int q = b0; q < b1; ++q) {
             const int2 e = contrib[q];   // column, sign
             const int64_t j = e.x;
-            float x = (MODE == kSumX) ? XLoad<TX>::one(X + j * ldx + r) : L[j * lds + r];
+            float x;
+            if (MODE == kSumX) x = XLoad<TX>::one(X + j * ldx + r);
+            else if (MODE == kSumL) x = L[j * lds + r];
+            else x = (XLoad<TX>::one(X + j * ldx + r) - S[j * lds + r]) + Th[j * lds + r] * inv_rho;
             if (e.y < 0) x = -x;
             const float t = hi + x;   // TwoSum(hi, x)
             const float bp = t - hi;
@@ -788,16 +792,22 @@ cudaError_t launch_centroids_from_sums(const double* sums, const int32_t* counts
 
 cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, const float* L,
                               int64_t lds, const int2* contrib, const int32_t* boff, int c, int64_t d,
-                              double* sums, cudaStream_t st) {
+                              double* sums, cudaStream_t st, const float* S, const float* Th,
+                              float inv_rho) {
     count_launches(1);
     const dim3 grid((unsigned)grid_for(d, kDeltaThreads), (unsigned)std::min(c, 64));
     if (mode == kSumL) {
-        k_delta_sums<kSumL, float><<<grid, kDeltaThreads, 0, st>>>(nullptr, 0, L, lds, contrib, boff, c, d,
-                                                                   sums);
+        k_delta_sums<kSumL, float><<<grid, kDeltaThreads, 0, st>>>(nullptr, 0, L, lds, nullptr, nullptr,
+                                                                   0.f, contrib, boff, c, d, sums);
     } else {
         RESPCA_DISPATCH_X(dtype, TX, {
-            k_delta_sums<kSumX, TX><<<grid, kDeltaThreads, 0, st>>>((const TX*)X, ldx, nullptr, 0, contrib,
-                                                                    boff, c, d, sums);
+            if (mode == kSumX)
+                k_delta_sums<kSumX, TX><<<grid, kDeltaThreads, 0, st>>>((const TX*)X, ldx, nullptr, 0, nullptr,
+                                                                        nullptr, 0.f, contrib, boff, c, d,
+                                                                        sums);
+            else
+                k_delta_sums<kSumD, TX><<<grid, kDeltaThreads, 0, st>>>((const TX*)X, ldx, nullptr, lds, S, Th,
+                                                                        inv_rho, contrib, boff, c, d, sums);
         });
     }
     return cudaGetLastError();

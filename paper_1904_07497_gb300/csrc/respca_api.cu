@@ -68,7 +68,8 @@ struct respca_ctx {
         mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count, rc_dist,
         L16, S16, T16, X16,   // BF16 state and X of the bf16 phase (precision = 1)
         mu_a,                 // centroid operand of the swapped dense search
-        bn_part;              // per-chunk ||B_j||^2 of the l2,1 iteration
+        bn_part,              // per-chunk ||B_j||^2 of the l2,1 iteration
+        sumsD;                // FP64 sums of the next D under the iteration's starting labels
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -127,7 +128,7 @@ std::vector<DevBuf*> all_bufs(respca_ctx* h) {
                       &h->labels_pass,
                       &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count,
                       &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
-                      &h->bn_part};
+                      &h->bn_part, &h->sumsD};
 }
 
 respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64_t lds,
@@ -166,6 +167,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
     CK(ensure(h->lb, sizeof(float) * n));
     CK(ensure(h->dl_part, sizeof(float) * (size_t)nch * n));
     CK(ensure(h->sums, sizeof(double) * (size_t)c * d));
+    CK(ensure(h->sumsD, sizeof(double) * (size_t)c * d));
     CK(ensure(h->moved, sizeof(int4) * n));
     CK(ensure(h->contrib, sizeof(int2) * 2 * (size_t)n));
     CK(ensure(h->boff, sizeof(int32_t) * ((size_t)c + 1)));
@@ -209,9 +211,10 @@ cudaError_t zero_counters(respca_ctx* h) {
 // Centroids (and their norms, drift from the centroids the last search used,
 // and pairwise separations) from the tile sums in Dpart, written to `dst`;
 // `prev` holds the centroids of the last search.
-respca_status finish_centroids(respca_ctx* h, int c, int64_t d, float* dst, const float* prev) {
+respca_status finish_centroids(respca_ctx* h, int c, int64_t d, float* dst, const float* prev,
+                               double* sums_out = nullptr) {
     CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c, d,
-                        dst, h->stream));
+                        dst, h->stream, sums_out));
     CK(launch_mu_stats(dst, prev, c, d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
                        prev ? P<double>(h->drift) : nullptr, h->stream));
     CK(launch_separation(dst, P<int32_t>(h->counts), c, d, P<float>(h->pair_ss), P<double>(h->sep2),
@@ -780,8 +783,10 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         rs = search(h, v.sd == 1 ? RESPCA_BF16 : RESPCA_F32, v.L, v.ld, d, n, P<int32_t>(h->flag_list),
                     c, p, v.vec);
         if (rs != RESPCA_OK) return rs;
-        // next centroids if every label stays (queued before the check; discarded otherwise)
-        rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
+        // next centroids if every label stays (queued before the check; discarded
+        // otherwise, but its FP64 sums then start the incremental update below)
+        rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu),
+                              v.sd == 0 ? P<double>(h->sumsD) : nullptr);
         if (rs != RESPCA_OK) return rs;
         rs = read_status(h);
         if (rs != RESPCA_OK) return rs;
@@ -811,13 +816,33 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             out.assigned_columns += scount.assigned;
             out.rechecked_columns += scount.rechecked;
             // next centroids: D = X - S + Theta/rho_{t+1} under the final labels
-            CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
-                                  P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
-            CK(launch_colsum(kSumD, v.xd, v.X, v.ldx, nullptr, v.S, v.Th, v.ld, sc.inv_rho_next,
-                             P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart),
-                             v.vec, h->stream, v.sd));
-            rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
-            if (rs != RESPCA_OK) return rs;
+            if (v.sd == 0) {
+                // the fused pass's sums under the starting labels, corrected by
+                // the columns whose label the p step changed
+                CK(launch_moved(p, P<int32_t>(h->labels_prev), n, c, P<int4>(h->moved),
+                                P<int2>(h->contrib), P<int32_t>(h->boff), P<int32_t>(h->counts), ds,
+                                h->stream));
+                CK(launch_delta_sums(kSumD, v.xd, v.X, v.ldx, nullptr, v.ld, P<int2>(h->contrib),
+                                     P<int32_t>(h->boff), c, d, P<double>(h->sumsD), h->stream,
+                                     static_cast<const float*>(v.S), static_cast<const float*>(v.Th),
+                                     sc.inv_rho_next));
+                CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
+                                      P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
+                CK(launch_centroids_from_sums(P<double>(h->sumsD), P<int32_t>(h->counts), c, d,
+                                              P<float>(h->mu_next), h->stream));
+                CK(launch_mu_stats(P<float>(h->mu_next), P<float>(h->mu), c, d, P<double>(h->mu_norm2),
+                                   P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+                CK(launch_separation(P<float>(h->mu_next), P<int32_t>(h->counts), c, d,
+                                     P<float>(h->pair_ss), P<double>(h->sep2), h->stream));
+            } else {
+                CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
+                                      P<int32_t>(h->tile_off), P<TileDesc>(h->tiles), ds, h->stream));
+                CK(launch_colsum(kSumD, v.xd, v.X, v.ldx, nullptr, v.S, v.Th, v.ld, sc.inv_rho_next,
+                                 P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart),
+                                 v.vec, h->stream, v.sd));
+                rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu));
+                if (rs != RESPCA_OK) return rs;
+            }
             CK(cudaMemcpyAsync(h->mu.p, h->mu_next.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice, h->stream));
             CK(launch_count_changed(p, P<int32_t>(h->labels_prev), n, ds, h->stream));
         }

@@ -101,7 +101,8 @@ cudaError_t launch_centroids_from_sums(const double* sums, const int32_t* counts
 
 cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, const float* L,
                               int64_t lds, const int2* contrib, const int32_t* boff, int c, int64_t d,
-                              double* sums, cudaStream_t st);
+                              double* sums, cudaStream_t st, const float* S = nullptr,
+                              const float* Th = nullptr, float inv_rho = 0.f);
 
 cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t d,
                             double* mu_norm2, float* mu_normf, double* drift, cudaStream_t st);
