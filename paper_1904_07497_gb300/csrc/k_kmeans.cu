@@ -12,6 +12,7 @@ namespace {
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
 
 // ---------------------------------------------------------------- label sort
+constexpr int kSortParMaxC = 256;   // per-warp histograms fit shared memory up to here
 // Stable counting sort of the columns by label (single CTA).  Produces the
 // sorted column order perm, the cluster sizes n_i, and the label-pure tiles
 // of at most kTileCols sorted columns; flags labels outside [0, c).
@@ -86,6 +87,45 @@ __global__ void __launch_bounds__(kSortThreads)
     }
     if (threadIdx.x == 0) tile_off[c] = toff[c];
     __syncthreads();
+    const int nwarps = blockDim.x / 32;
+    if (c <= kSortParMaxC) {
+        // stable scatter by all warps: warp w takes the w-th contiguous segment
+        // of columns; its start for label l is run[l] plus the count of l in
+        // the segments before it (per-warp histograms in hw[w][l])
+        int32_t* hw = sh + 3 * c + 1;   // [nwarps][c]
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int64_t seg = (n + nwarps - 1) / nwarps;
+        const int64_t j0 = (int64_t)warp * seg, j1 = min(n, j0 + seg);
+        for (int i = lane; i < c; i += 32) hw[warp * c + i] = 0;
+        __syncwarp();
+        for (int64_t j = j0 + lane; j < j1; j += 32) atomicAdd(&hw[warp * c + labels[j]], 1);
+        __syncthreads();
+        for (int i = threadIdx.x; i < c; i += blockDim.x) {
+            int32_t acc = run[i];
+            for (int w = 0; w < nwarps; ++w) {
+                const int32_t v = hw[w * c + i];
+                hw[w * c + i] = acc;
+                acc += v;
+            }
+        }
+        __syncthreads();
+        const unsigned lt = (1u << lane) - 1u;
+        for (int64_t base = j0; base < j1; base += 32) {
+            const int64_t j = base + lane;
+            const int32_t l = (j < j1) ? labels[j] : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, l);
+            const int rank = __popc(peers & lt);
+            int32_t pos = 0;
+            if (l >= 0) pos = hw[warp * c + l] + rank;
+            __syncwarp();
+            if (l >= 0) {
+                perm[pos] = (int32_t)j;
+                if (rank == 0) hw[warp * c + l] += __popc(peers);
+            }
+            __syncwarp();
+        }
+        return;
+    }
     // stable scatter, one warp, 32 columns at a time in column order
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
@@ -453,7 +493,8 @@ cudaError_t launch_sort_labels(const int32_t* labels, int64_t n, int c, int32_t*
                                int32_t* counts, int32_t* tile_off, TileDesc* tiles,
                                DevStatus* status, cudaStream_t st) {
     count_launches(1);
-    const size_t smem = sizeof(int32_t) * (size_t)(3 * c + 1);
+    size_t smem = sizeof(int32_t) * (size_t)(3 * c + 1);
+    if (c <= kSortParMaxC) smem += sizeof(int32_t) * (size_t)(kSortThreads / 32) * c;
     if (smem > 48 * 1024) {
         cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_sort_labels));
         if (e != cudaSuccess) return e;
