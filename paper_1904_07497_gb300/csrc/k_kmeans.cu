@@ -354,27 +354,35 @@ __global__ void __launch_bounds__(kThreads)
         const TX* xj = X + j * ldx;
         float s = 0.f, comp = 0.f;
         if (VEC) {
-            for (int64_t r0 = lane * 4; r0 < d; r0 += 32 * 8) {
-                float part = 0.f;
-                const float4 a0 = XLoad<TX>::four(xj + r0), b0 = XLoad<TX>::four(xc + r0);
-                float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = a1;
-                if (r0 + 128 < d) {
-                    a1 = XLoad<TX>::four(xj + r0 + 128);
-                    b1 = XLoad<TX>::four(xc + r0 + 128);
+            // two 256-row steps per trip: all eight loads are issued first, then the
+            // steps are added in the same order as one step per trip would add them
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int64_t r0 = lane * 4; r0 < d; r0 += 2 * 32 * 8) {
+                float4 a[4], bq[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int64_t r = r0 + h * 128;
+                    a[h] = r < d ? XLoad<TX>::four(xj + r) : z;
+                    bq[h] = r < d ? XLoad<TX>::four(xc + r) : z;
                 }
-                float t;
-                t = a0.x - b0.x; part = fmaf(t, t, part);
-                t = a0.y - b0.y; part = fmaf(t, t, part);
-                t = a0.z - b0.z; part = fmaf(t, t, part);
-                t = a0.w - b0.w; part = fmaf(t, t, part);
-                t = a1.x - b1.x; part = fmaf(t, t, part);
-                t = a1.y - b1.y; part = fmaf(t, t, part);
-                t = a1.z - b1.z; part = fmaf(t, t, part);
-                t = a1.w - b1.w; part = fmaf(t, t, part);
-                const float y = part - comp;
-                const float u = s + y;
-                comp = (u - s) - y;
-                s = u;
+#pragma unroll
+                for (int st = 0; st < 2; ++st) {
+                    if (r0 + st * 256 >= d) break;
+                    float part = 0.f, t;
+                    const float4 a0 = a[2 * st], b0 = bq[2 * st], a1 = a[2 * st + 1], b1 = bq[2 * st + 1];
+                    t = a0.x - b0.x; part = fmaf(t, t, part);
+                    t = a0.y - b0.y; part = fmaf(t, t, part);
+                    t = a0.z - b0.z; part = fmaf(t, t, part);
+                    t = a0.w - b0.w; part = fmaf(t, t, part);
+                    t = a1.x - b1.x; part = fmaf(t, t, part);
+                    t = a1.y - b1.y; part = fmaf(t, t, part);
+                    t = a1.z - b1.z; part = fmaf(t, t, part);
+                    t = a1.w - b1.w; part = fmaf(t, t, part);
+                    const float y = part - comp;
+                    const float u = s + y;
+                    comp = (u - s) - y;
+                    s = u;
+                }
             }
         } else {
             for (int64_t r0 = 0; r0 < d; r0 += 32 * 8) {

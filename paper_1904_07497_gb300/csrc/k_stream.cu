@@ -315,19 +315,22 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// One warp per centroid, lanes over the other centroids.
 __global__ void k_sep_min(const float* __restrict__ pair_ss, const int32_t* __restrict__ counts,
                           int c, double* __restrict__ sep2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (i >= c) return;
-    double best = INFINITY;
+    float best = INFINITY;
     if (counts[i] > 0)
-        for (int j = 0; j < c; ++j) {
+        for (int j = lane; j < c; j += 32) {
             if (j == i || counts[j] == 0) continue;
             const int a = min(i, j), b = max(i, j);
-            const double v = (double)pair_ss[(int64_t)a * c + b];
-            if (v < best) best = v;
+            best = fminf(best, pair_ss[(int64_t)a * c + b]);
         }
-    sep2[i] = best;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) sep2[i] = (double)best;
 }
 
 __global__ void k_fill_double(double* __restrict__ p, int count, double v) {
@@ -862,7 +865,7 @@ cudaError_t launch_separation(const float* mu, const int32_t* counts, int c, int
         if (e != cudaSuccess) return e;
     }
     k_pair_dist<<<grid_for(d, kSepRows), kThreads, smem, st>>>(mu, counts, c, d, pair_ss);
-    k_sep_min<<<grid_for(c, kThreads), kThreads, 0, st>>>(pair_ss, counts, c, sep2);
+    k_sep_min<<<grid_for(c, kThreads / 32), kThreads, 0, st>>>(pair_ss, counts, c, sep2);
     return cudaGetLastError();
 }
 
