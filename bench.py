@@ -204,6 +204,25 @@ def kernel_traffic(kernel_file, profile_name):
         return None
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of the ranks' values (every rank gets it).  Replicas each
+    solve their own problem; the job's time is the slowest rank's."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of a replica's problem: every rank solves a different instance."""
+    return base + rank
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
@@ -212,7 +231,7 @@ def run_gpu(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    pr, c = make_problem(args.workload, args.seed + rank)
+    pr, c = make_problem(args.workload, replica_seed(args.seed, rank))
     d, n = pr.X.shape
     X = torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(dev).T          # (d, n) col-major
     L = torch.empty((n, d), device=dev).T
@@ -246,11 +265,8 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_per_step = t.item() / args.steps
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    ms_per_step = ms_total / args.steps
 
     iters = [s["iters"] for s in stats]
     launches = sum(s["kernel_launches"] for s in stats)
@@ -304,11 +320,8 @@ def run_gpu(args, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(ke):
             respca.respca_solve_host(solver.h, Xh, c, Lh, Sh, ph, tol=args.tol, max_iter=500)
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / ke
-        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": round(te.item(), 3), "unit": "ms", "h2d_bytes_per_step": 4 * d * n,
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / ke, world, dev)
+        e2e = {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": 4 * d * n,
                "d2h_bytes_per_step": 8 * d * n + 4 * n,
                "note": "respca_solve_host on pinned host buffers; copies inside the timed region"}
 
@@ -356,7 +369,7 @@ def run_batched(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    entries = synth.batch_table(C4_COUNT, seed=C4_SEED + rank)
+    entries = synth.batch_table(C4_COUNT, seed=replica_seed(C4_SEED, rank))
     probs = []
     elements = 0
     for e in entries:
@@ -383,10 +396,7 @@ def run_batched(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         solver.close()
-        t = torch.tensor([e0.elapsed_time(e1) / steps], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return t.item(), st
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world, dev), st
 
     gpu_index = local_rank
     clocks = ClockSampler(gpu_index)
