@@ -448,7 +448,11 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
                         P<float>(h->mu), h->stream, P<double>(h->sums)));
     CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
                        P<float>(h->mu_normf), P<double>(h->drift), h->stream));
-    if (h->cfg.timing == 0 && sc->passes < max_passes) {
+    // the device loop pays off where a pass is long enough for the launches and
+    // status reads it saves to matter; building the graph costs about as much
+    // as a few passes of a small problem
+    constexpr int64_t kDeviceLoopMinElems = int64_t(1) << 22;
+    if (h->cfg.timing == 0 && sc->passes < max_passes && d * n >= kDeviceLoopMinElems) {
         const respca_status rs = lloyd_loop_on_device(h, mode, dtype, Y, ldy, d, n, c, p, vec, max_passes, sc);
         if (rs != RESPCA_ERR_UNSUPPORTED) return rs;
         h->last_error.clear();   // no graph on this setup: the host runs the loop below

@@ -463,3 +463,26 @@ def test_l21_fixed_iterations_and_convergence():
     top = set(np.argsort(-score)[:len(out)].tolist())
     assert top == set(out.tolist())
     s.close()
+
+
+def test_device_lloyd_loop_matches_host_loop():
+    """The Lloyd passes run as a device loop (CUDA graph, problems of >= 4M
+    elements) or, with the library's event timing on, driven by the host; the
+    two run the same kernels in the same order, so whole solves agree bit for
+    bit, pass counts included."""
+    from paper_1904_07497_gb300 import respca
+    pr = synth.lowrank_sparse(2048, 2048, 20, 0.1, seed=17)
+    X = _dev(pr.X)
+    out = []
+    for timing in (False, True):
+        s = respca.Solver(seed=5, timing=timing)
+        r = s.solve(X, 20, tol=1e-6, max_iter=300)
+        torch.cuda.synchronize()
+        out.append((r.p.cpu().numpy(), _host(r.L), _host(r.S), r.stats))
+        s.close()
+    (pa, La, Sa, sa), (pb, Lb, Sb, sb) = out
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(La, Lb)
+    np.testing.assert_array_equal(Sa, Sb)
+    assert sa["iters"] == sb["iters"] and sa["converged"] == 1
+    assert sa["lloyd_passes"] == sb["lloyd_passes"] and sa["lloyd_passes"] > sa["iters"]
