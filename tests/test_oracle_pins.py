@@ -524,3 +524,36 @@ def test_l21_theta_is_a_subgradient(oracle_mod):
         else:
             assert np.linalg.norm(t) <= 1.0 + 1e-12
     assert nz >= 1
+
+
+# ------------------------------------------------------------------ warm-start network (oracle)
+def test_warmnet_plain_schedule_equals_oracle_iterations(oracle_mod):
+    """With zero log multipliers the network's layers are the plain iterations
+    with the labels fixed: on well-separated groups (where the p step keeps
+    every label) K layers equal K oracle iterations."""
+    from oracle import warmnet
+    pr = synth.clustered_columns(40, 36, 3, seed=4, sparsity=0.1)
+    X = pr.X.astype(np.float64)
+    c, lam, kappa = 3, 3.0, 1.5
+    st = oracle_mod.State(np.zeros(X.shape, order="F"), np.zeros(X.shape, order="F"),
+                          np.zeros(X.shape, order="F"), pr.truth_labels.astype(np.int32), 0.9)
+    for _ in range(3):
+        st, *_ = oracle_mod.iteration(X, st, c, lam)
+    assert np.array_equal(st.labels, pr.truth_labels)
+    K = 4
+    rho_k, tau_k = warmnet.schedule(st.rho, kappa, np.zeros(K), np.zeros(K))
+    L, S, T = warmnet.forward(X, st.labels, c, lam, st.S, st.Theta, rho_k, tau_k)
+    ref = st
+    for _ in range(K):
+        ref, *_ = oracle_mod.iteration(X, ref, c, lam)
+    assert np.array_equal(ref.labels, pr.truth_labels)
+    np.testing.assert_allclose(L, ref.L, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(S, ref.S, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(T, ref.Theta, rtol=1e-10, atol=1e-12)
+
+
+def test_warmnet_schedule_multipliers():
+    from oracle import warmnet
+    r, t = warmnet.schedule(2.0, 1.5, [0.0, np.log(3.0)], [0.0, np.log(0.5)])
+    np.testing.assert_allclose(r, [2.0, 2.0 * 1.5 * 3.0])
+    np.testing.assert_allclose(t, [0.5, 0.5 / (2.0 * 1.5 * 3.0)])
