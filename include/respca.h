@@ -83,6 +83,11 @@ typedef struct {
                                 element).  With 1 the closed-form leading iterations and the
                                 bf16 phase are not used. */
     double switch_tol;       /* end of the bf16 phase (default 1e-2) */
+    int32_t stop_after_ramp; /* 1: return after the closed-form leading iterations (ramp_skip;
+                                cold starts), with L, Theta (respca_warm), p and rho of the
+                                next iteration written out -- the state a learned warm start
+                                (respca_net_forward) continues from; 0 (default): solve to tol */
+    int32_t reserved4;
 } respca_config;
 
 typedef struct {
@@ -260,6 +265,84 @@ respca_status respca_init_labels_noalloc(int32_t x_dtype, const void *X, int64_t
                                          int64_t ldx, int32_t c, uint64_t seed,
                                          int32_t kmeans_max_iter, int32_t *p, int32_t *passes,
                                          void *stream);
+
+/*
+ * Learned warm start.  Not in the paper: an unrolled continuation of the
+ * Sec. 4 iteration that a caller trains to carry a state further than the
+ * same number of plain iterations would, after which respca_solve continues
+ * from its output (respca_warm).  The labels p are held fixed.  Layer k, with
+ * its own step rho_k and soft threshold tau_k (all FP32 arithmetic):
+ *   D = X - S + Theta/rho_k;  mu_i = mean of D over group i;  a = rho_k/(2 lambda + rho_k)
+ *   L = a D + (1 - a) mu_p                                  (Eq. (18))
+ *   B = X - L + Theta/rho_k;  S' = sign(B) max(|B| - tau_k, 0)  (Eq. (24), tau_k in place of 1/rho_k)
+ *   Theta' = Theta + rho_k (X - L - S')                     (Eq. (25))
+ * With tau_k = 1/rho_k and rho_{k+1} = kappa rho_k the layers are the plain
+ * iterations with p fixed.  The parameters a caller learns are log
+ * multipliers m = [theta_0..theta_{K-1}, phi_0..phi_{K-1}] on that schedule:
+ * rho_k = rho kappa^k exp(theta_k), tau_k = exp(phi_k) / rho_k.
+ */
+typedef struct respca_net_s *respca_net;
+
+/* Create a network context on `device` (-1 = current) working on `stream`
+ * (cudaStream_t, NULL = legacy default).  It owns its device workspace: the
+ * inputs of every layer (2 (K+1) d n floats) are kept for the backward pass. */
+respca_status respca_net_create(respca_net *net, int32_t device, void *stream);
+respca_status respca_net_destroy(respca_net net);
+
+/* Host arithmetic: (rho_k, tau_k), k < layers, from rho, kappa and the 2 K
+ * multipliers m (host floats, layout above).  rho > 0, kappa > 0. */
+respca_status respca_net_schedule(double rho, double kappa, int32_t layers, const float *m,
+                                  double *rho_k, double *tau_k);
+
+/* Forward pass through `layers` layers from (S0, Theta0).
+ *   X          d x n device FP32, leading dimension ldx >= d (read only).
+ *   p          n device int32 labels in [0, c) (read only; fixed in every layer).
+ *   lambda     weight of the variance term (> 0).
+ *   S0, Theta0 d x n device FP32 input state, leading dimension lds >= d (copied).
+ *   rho_k, tau_k  host arrays of `layers` positive values.
+ *   L, S, Theta   d x n device FP32 outputs of the last layer (leading dimension
+ *              lds; may be NULL).  The call is asynchronous on the stream.
+ * The context keeps the pointer X (not a copy): X must stay allocated and
+ * unchanged until the matching respca_net_backward returns.
+ * Errors: RESPCA_ERR_INVALID_ARG (null or inconsistent sizes, non-positive
+ * scalars, layers < 1, labels outside [0, c)), RESPCA_ERR_OOM, RESPCA_ERR_CUDA. */
+respca_status respca_net_forward(respca_net net, const float *X, int64_t d, int64_t n, int64_t ldx,
+                                 const int32_t *p, int32_t c, double lambda, const float *S0,
+                                 const float *Theta0, int64_t lds, int32_t layers,
+                                 const double *rho_k, const double *tau_k, float *L, float *S,
+                                 float *Theta);
+
+/* Loss and exact gradient of the last forward pass:
+ *   loss = scale (||L - Lt||_F^2 + ||S - St||_F^2)
+ * for targets Lt, St (d x n device FP32, leading dimension ldt >= d).  Writes
+ * host *loss, g_rho[k] = dloss/drho_k and g_tau[k] = dloss/dtau_k (FP32 sums
+ * per element, FP64 across CTAs); g_m (optional, 2 K host floats) receives
+ * dloss/dm for the multipliers of respca_net_schedule.  Synchronises the
+ * stream.  RESPCA_ERR_INVALID_ARG without a preceding forward pass. */
+respca_status respca_net_backward(respca_net net, const float *Lt, const float *St, int64_t ldt,
+                                  double scale, double *loss, double *g_rho, double *g_tau,
+                                  float *g_m);
+
+/* The multipliers' predictor: a 2-layer MLP out = W2 tanh(W1 z + b1) + b2 on
+ * nz statistics z of the state, hidden width H, nout outputs.  Parameters are
+ * one device FP32 array [W1 (H x nz, row-major) | b1 (H) | W2 (nout x H) | b2
+ * (nout)] of H nz + H + nout H + nout floats.  z, out, hidden (H floats, the
+ * tanh activations kept for the backward pass) are device arrays.  Async on
+ * `stream`.  nz, H, nout in [1, 1024]. */
+respca_status respca_mlp_forward(const float *params, int32_t nz, int32_t H, int32_t nout,
+                                 const float *z, float *out, float *hidden, void *stream);
+
+/* Gradient of <gout, out> with respect to params into grad (same layout);
+ * accumulate = 1 adds to grad instead of overwriting it. */
+respca_status respca_mlp_backward(const float *params, int32_t nz, int32_t H, int32_t nout,
+                                  const float *z, const float *hidden, const float *gout,
+                                  float *grad, int32_t accumulate, void *stream);
+
+/* One Adam step (Kingma and Ba) over `count` device floats: moments m, v
+ * updated in place, bias correction for step t >= 1. */
+respca_status respca_adam_step(float *params, const float *grad, float *m, float *v, int64_t count,
+                               double lr, double beta1, double beta2, double eps, int32_t t,
+                               void *stream);
 
 /* Static description of a status code. */
 const char *respca_status_string(respca_status s);

@@ -53,3 +53,41 @@ def forward(X, labels, c, lam, S0, T0, rho_k, tau_k):
 def loss(L, S, Lt, St, scale):
     """scale (||L - Lt||^2 + ||S - St||^2)."""
     return scale * (np.sum((L - Lt) ** 2) + np.sum((S - St) ** 2))
+
+
+def mlp_unpack(P, nz, H, nout):
+    """Packed parameters [W1 (H x nz) | b1 | W2 (nout x H) | b2] as arrays."""
+    P = np.asarray(P, dtype=np.float64)
+    o = 0
+    W1 = P[o:o + H * nz].reshape(H, nz); o += H * nz
+    b1 = P[o:o + H]; o += H
+    W2 = P[o:o + nout * H].reshape(nout, H); o += nout * H
+    b2 = P[o:o + nout]
+    return W1, b1, W2, b2
+
+
+def mlp_forward(P, z, nz, H, nout):
+    """out = W2 tanh(W1 z + b1) + b2; returns (out, hidden)."""
+    W1, b1, W2, b2 = mlp_unpack(P, nz, H, nout)
+    h = np.tanh(W1 @ np.asarray(z, dtype=np.float64) + b1)
+    return W2 @ h + b2, h
+
+
+def mlp_grad(P, z, gout, nz, H, nout):
+    """Gradient of <gout, out> with respect to the packed parameters (chain
+    rule through the two affine maps and tanh' = 1 - tanh^2)."""
+    W1, b1, W2, b2 = mlp_unpack(P, nz, H, nout)
+    z = np.asarray(z, dtype=np.float64)
+    gout = np.asarray(gout, dtype=np.float64)
+    _, h = mlp_forward(P, z, nz, H, nout)
+    gh = (W2.T @ gout) * (1.0 - h * h)
+    return np.concatenate([np.outer(gh, z).ravel(), gh, np.outer(gout, h).ravel(), gout])
+
+
+def adam_step(P, G, M, V, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (Kingma and Ba, Algorithm 1); returns (P, M, V)."""
+    M = b1 * M + (1.0 - b1) * G
+    V = b2 * V + (1.0 - b2) * G * G
+    mh = M / (1.0 - b1 ** t)
+    vh = V / (1.0 - b2 ** t)
+    return P - lr * mh / (np.sqrt(vh) + eps), M, V

@@ -751,9 +751,11 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         }
     }
     CK(cudaEventRecord(h->ev2, h->stream));
+    // stop_after_ramp: the closed-form leading iterations only
+    const int iter_cap = (h->cfg.stop_after_ramp && !is_warm) ? t_start : max_iter;
 
     double err_hist[2] = {INFINITY, INFINITY};   // err of the last two bf16 iterations
-    for (int t = t_start; t < max_iter; ++t) {
+    for (int t = t_start; t < iter_cap; ++t) {
         const double rho_next = rho * kappa;
         IterScalars sc;
         sc.a = (float)(rho / (2.0 * lam + rho));
@@ -932,6 +934,7 @@ respca_status respca_create(respca_handle* out, const respca_config* cfg) {
         return RESPCA_ERR_INVALID_ARG;
     if (c.s_norm != 0 && c.s_norm != 1) return RESPCA_ERR_INVALID_ARG;
     if (c.precision != 0 && c.precision != 1) return RESPCA_ERR_INVALID_ARG;
+    if (c.stop_after_ramp != 0 && c.stop_after_ramp != 1) return RESPCA_ERR_INVALID_ARG;
     int dev = c.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return RESPCA_ERR_CUDA;
     if (cudaSetDevice(dev) != cudaSuccess) return RESPCA_ERR_CUDA;

@@ -338,6 +338,37 @@ __device__ __forceinline__ void f4set(float4& v, int q, float x) {
     else v.w = x;
 }
 
+// ---------------------------------------------------------------- learned warm start
+// Scalars of one unrolled layer (rho_k, tau_k learned; labels fixed).
+struct NetScalars {
+    float a;             // rho_k / (2 lambda + rho_k)
+    float b;             // 2 lambda / (2 lambda + rho_k)
+    float rho;           // rho_k
+    float inv_rho;       // 1 / rho_k
+    float tau;           // soft threshold of the layer's S step
+    float inv_rho_next;  // 1 / rho_{k+1}: weight of Theta' in the next layer's D sums
+};
+
+int net_row_chunks(int64_t d);
+cudaError_t launch_net_layer(const float* X, int64_t ldx, const float* S, const float* Th, float* L,
+                             float* Sn, float* Thn, int64_t lds, const float* mu, const int32_t* perm,
+                             const TileDesc* tiles, int max_tiles, const DevStatus* status, int64_t d,
+                             const NetScalars& sc, float* Dpart, cudaStream_t st);
+cudaError_t launch_net_back(int pass, const float* X, int64_t ldx, const float* S, const float* Th,
+                            int64_t lds, const float* mu, const int32_t* perm, const TileDesc* tiles,
+                            int max_tiles, const DevStatus* status, int64_t d, const NetScalars& sc,
+                            const float* gLext, float* gS, float* gT, const float* gmean, float* Gpart,
+                            double* scal_part, double* scal_out, cudaStream_t st);
+cudaError_t launch_net_loss(const float* L, const float* S, int64_t lds, const float* Lt, const float* St,
+                            int64_t ldt, int64_t d, int64_t n, float scale, float* gL, float* gS, float* gT,
+                            double* part, int parts, double* out, cudaStream_t st);
+cudaError_t launch_mlp_forward(const float* P, int nz, int H, int nout, const float* z, float* out,
+                               float* hidden, cudaStream_t st);
+cudaError_t launch_mlp_backward(const float* P, int nz, int H, int nout, const float* z, const float* hidden,
+                                const float* gout, float* G, int accumulate, cudaStream_t st);
+cudaError_t launch_adam(float* P, const float* G, float* M, float* V, int64_t count, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t st);
+
 // Dispatch a runtime dtype (0 f32, 1 bf16, 2 f16) to a template lambda.
 #define RESPCA_DISPATCH_X(dtype, TX, ...)                       \
     do {                                                        \

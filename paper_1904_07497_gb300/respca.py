@@ -34,7 +34,8 @@ class respca_config(ctypes.Structure):
                 ("device", ctypes.c_int32), ("search_impl", ctypes.c_int32),
                 ("ramp_skip", ctypes.c_int32), ("batch_lanes", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("s_norm", ctypes.c_int32),
-                ("switch_tol", ctypes.c_double)]
+                ("switch_tol", ctypes.c_double), ("stop_after_ramp", ctypes.c_int32),
+                ("reserved4", ctypes.c_int32)]
 
 
 class respca_stats(ctypes.Structure):
@@ -107,6 +108,28 @@ def load():
     lib.respca_init_labels_noalloc.restype = ctypes.c_int
     lib.respca_column_norms.argtypes = [_VP, _I64, _I64, _I64, _VP, _VP]
     lib.respca_column_norms.restype = ctypes.c_int
+    _D = ctypes.c_double
+    _PD = ctypes.POINTER(ctypes.c_double)
+    _PF = ctypes.POINTER(ctypes.c_float)
+    lib.respca_net_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, _VP]
+    lib.respca_net_create.restype = ctypes.c_int
+    lib.respca_net_destroy.argtypes = [_VP]
+    lib.respca_net_destroy.restype = ctypes.c_int
+    lib.respca_net_schedule.argtypes = [_D, _D, ctypes.c_int32, _PF, _PD, _PD]
+    lib.respca_net_schedule.restype = ctypes.c_int
+    lib.respca_net_forward.argtypes = [_VP, _VP, _I64, _I64, _I64, _VP, ctypes.c_int32, _D, _VP, _VP,
+                                       _I64, ctypes.c_int32, _PD, _PD, _VP, _VP, _VP]
+    lib.respca_net_forward.restype = ctypes.c_int
+    lib.respca_net_backward.argtypes = [_VP, _VP, _VP, _I64, _D, _PD, _PD, _PD, _PF]
+    lib.respca_net_backward.restype = ctypes.c_int
+    lib.respca_mlp_forward.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP,
+                                       _VP, _VP]
+    lib.respca_mlp_forward.restype = ctypes.c_int
+    lib.respca_mlp_backward.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP,
+                                        _VP, _VP, ctypes.c_int32, _VP]
+    lib.respca_mlp_backward.restype = ctypes.c_int
+    lib.respca_adam_step.argtypes = [_VP, _VP, _VP, _VP, _I64, _D, _D, _D, _D, ctypes.c_int32, _VP]
+    lib.respca_adam_step.restype = ctypes.c_int
     lib.respca_status_string.argtypes = [ctypes.c_int]
     lib.respca_status_string.restype = ctypes.c_char_p
     lib.respca_last_error.argtypes = [_VP]
@@ -272,9 +295,11 @@ class Solver:
     def __init__(self, rho0: float = 1e-4, kappa: float = 1.5, kmeans_max_iter: int = 100,
                  seed: int = 0, stream=None, device: int | None = None, timing: bool = False,
                  search_impl: int = 0, ramp_skip: bool = True, batch_lanes: int = 0,
-                 precision: int = 0, switch_tol: float | None = None, s_norm: int = 0):
+                 precision: int = 0, switch_tol: float | None = None, s_norm: int = 0,
+                 stop_after_ramp: bool = False):
         import torch
         cfg = respca_config_default()
+        cfg.stop_after_ramp = 1 if stop_after_ramp else 0
         cfg.search_impl = search_impl
         cfg.ramp_skip = 1 if ramp_skip else 0
         cfg.batch_lanes = batch_lanes
@@ -322,3 +347,89 @@ class Solver:
         p = torch.empty(X.shape[1], device=X.device, dtype=torch.int32)
         passes = respca_init_labels(self.h, X, c, p)
         return p, passes
+
+
+# ------------------------------------------------------------------ learned warm start
+def respca_net_create(device: int = -1, stream=None):
+    net = _VP()
+    _check(None, load().respca_net_create(ctypes.byref(net), int(device),
+                                          stream.cuda_stream if stream is not None else None),
+           "respca_net_create")
+    return net
+
+
+def respca_net_destroy(net) -> None:
+    _check(None, load().respca_net_destroy(net), "respca_net_destroy")
+
+
+def respca_net_schedule(rho: float, kappa: float, m) -> tuple[list[float], list[float]]:
+    """(rho_k, tau_k) from the 2 K log multipliers m (a sequence of floats)."""
+    K = len(m) // 2
+    mm = (ctypes.c_float * (2 * K))(*[float(v) for v in m])
+    r = (ctypes.c_double * K)()
+    t = (ctypes.c_double * K)()
+    _check(None, load().respca_net_schedule(float(rho), float(kappa), K, mm, r, t),
+           "respca_net_schedule")
+    return list(r), list(t)
+
+
+def respca_net_forward(net, X, p, c: int, lam: float, S0, Theta0, rho_k, tau_k, L=None, S=None,
+                       Theta=None) -> None:
+    """X, S0, Theta0 (and the outputs): (d, n) column-major FP32 CUDA tensors;
+    p: int32 (n,) labels.  S0, Theta0 and the outputs share a leading dimension."""
+    d, n = X.shape
+    ldx = _colmajor(X, "X")
+    lds = _colmajor(S0, "S0")
+    for name, t in (("Theta0", Theta0), ("L", L), ("S", S), ("Theta", Theta)):
+        if t is not None and _colmajor(t, name) != lds:
+            raise ValueError(f"{name} must share the leading dimension of S0")
+    K = len(rho_k)
+    r = (ctypes.c_double * K)(*rho_k)
+    t = (ctypes.c_double * K)(*tau_k)
+    ptr = (lambda a: a.data_ptr() if a is not None else None)
+    rc = load().respca_net_forward(net, X.data_ptr(), d, n, ldx, p.data_ptr(), int(c), float(lam),
+                                   S0.data_ptr(), Theta0.data_ptr(), lds, K, r, t, ptr(L), ptr(S),
+                                   ptr(Theta))
+    _check(None, rc, "respca_net_forward")
+
+
+def respca_net_backward(net, Lt, St, scale: float, layers: int):
+    """Loss and gradients of the last forward pass: returns
+    (loss, g_rho [K], g_tau [K], g_m [2K])."""
+    ldt = _colmajor(Lt, "Lt")
+    if _colmajor(St, "St") != ldt:
+        raise ValueError("Lt and St must share a leading dimension")
+    K = int(layers)
+    loss = ctypes.c_double(0.0)
+    gr = (ctypes.c_double * K)()
+    gt = (ctypes.c_double * K)()
+    gm = (ctypes.c_float * (2 * K))()
+    rc = load().respca_net_backward(net, Lt.data_ptr(), St.data_ptr(), ldt, float(scale),
+                                    ctypes.byref(loss), gr, gt, gm)
+    _check(None, rc, "respca_net_backward")
+    return loss.value, list(gr), list(gt), list(gm)
+
+
+def respca_mlp_forward(params, nz: int, H: int, nout: int, z, out, hidden, stream=None) -> None:
+    s = stream.cuda_stream if stream is not None else None
+    _check(None, load().respca_mlp_forward(params.data_ptr(), nz, H, nout, z.data_ptr(),
+                                           out.data_ptr(), hidden.data_ptr(), s),
+           "respca_mlp_forward")
+
+
+def respca_mlp_backward(params, nz: int, H: int, nout: int, z, hidden, gout, grad,
+                        accumulate: bool = False, stream=None) -> None:
+    s = stream.cuda_stream if stream is not None else None
+    _check(None, load().respca_mlp_backward(params.data_ptr(), nz, H, nout, z.data_ptr(),
+                                            hidden.data_ptr(), gout.data_ptr(), grad.data_ptr(),
+                                            1 if accumulate else 0, s),
+           "respca_mlp_backward")
+
+
+def respca_adam_step(params, grad, m, v, *, lr: float, t: int, beta1: float = 0.9,
+                     beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+    s = stream.cuda_stream if stream is not None else None
+    _check(None, load().respca_adam_step(params.data_ptr(), grad.data_ptr(), m.data_ptr(),
+                                         v.data_ptr(), params.numel(), float(lr), float(beta1),
+                                         float(beta2), float(eps), int(t), s),
+           "respca_adam_step")

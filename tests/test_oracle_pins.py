@@ -557,3 +557,32 @@ def test_warmnet_schedule_multipliers():
     r, t = warmnet.schedule(2.0, 1.5, [0.0, np.log(3.0)], [0.0, np.log(0.5)])
     np.testing.assert_allclose(r, [2.0, 2.0 * 1.5 * 3.0])
     np.testing.assert_allclose(t, [0.5, 0.5 / (2.0 * 1.5 * 3.0)])
+
+
+def test_warmnet_mlp_grad_matches_finite_differences():
+    """The MLP's analytic gradient against central differences of its forward."""
+    from oracle import warmnet
+    nz, H, nout = 3, 5, 4
+    g = np.random.default_rng(7)
+    P = g.standard_normal(H * nz + H + nout * H + nout)
+    z = g.standard_normal(nz)
+    gout = g.standard_normal(nout)
+    G = warmnet.mlp_grad(P, z, gout, nz, H, nout)
+    h = 1e-6
+    fd = np.empty_like(P)
+    for i in range(P.size):
+        e = np.zeros_like(P)
+        e[i] = h
+        fp = gout @ warmnet.mlp_forward(P + e, z, nz, H, nout)[0]
+        fm = gout @ warmnet.mlp_forward(P - e, z, nz, H, nout)[0]
+        fd[i] = (fp - fm) / (2 * h)
+    np.testing.assert_allclose(G, fd, rtol=1e-7, atol=1e-8)
+
+
+def test_warmnet_adam_first_step_is_signed_lr():
+    """With bias correction, Adam's first step moves every parameter by
+    lr * g / (|g| + eps): lr times the sign of its gradient."""
+    from oracle import warmnet
+    g = np.array([3.0, -0.5, 1e-3, -20.0])
+    P, _, _ = warmnet.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, 0.01, eps=1e-12)
+    np.testing.assert_allclose(P, -0.01 * np.sign(g), rtol=1e-8)
