@@ -203,7 +203,12 @@ class WarmStart:
                             max_iter=max(0, max_iter - rs.iters - layers), warm=warm)
         ev1.record(self.stream)
         ev1.synchronize()
-        info = dict(ramp_iters=rs.iters, layers=layers, cont_iters=int(st["iters"]),
+        # kernels: the two solver calls count their own; column norms (1), and with the
+        # network the MLP (1), the label sort, the first D sums and 2 per layer
+        launches = int(rs.stats["kernel_launches"]) + int(st["kernel_launches"]) + 1
+        if use_net:
+            launches += 1 + 2 + 2 * self.K
+        info = dict(ramp_iters=rs.iters, layers=layers, cont_iters=int(st["iters"]), launches=launches,
                     total_iters=rs.iters + layers + int(st["iters"]), converged=int(st["converged"]),
                     err=float(st["err"]), ms=float(ev0.elapsed_time(ev1)))
         return L, S, p, info
