@@ -87,7 +87,14 @@ typedef struct {
                                 cold starts), with L, Theta (respca_warm), p and rho of the
                                 next iteration written out -- the state a learned warm start
                                 (respca_net_forward) continues from; 0 (default): solve to tol */
-    int32_t reserved4;
+    int32_t p_step;          /* clustering of the p step (Sec. 4.2): 0 (default) = K-means, the
+                                paper's choice; 1 = spectral clustering, the nonlinear alternative
+                                Sec. 4.2 names (see respca_spectral_labels).  With 1, X must be
+                                FP32, precision must be 0, the closed-form leading iterations are
+                                not used, and the initial labels (p0 = NULL) are the spectral
+                                labels of the columns of X. */
+    double spectral_scale;   /* p_step = 1: sigma^2 of the Gaussian affinity as a multiple of the
+                                mean squared distance between columns (default 0.125) */
 } respca_config;
 
 typedef struct {
@@ -265,6 +272,38 @@ respca_status respca_init_labels_noalloc(int32_t x_dtype, const void *X, int64_t
                                          int64_t ldx, int32_t c, uint64_t seed,
                                          int32_t kmeans_max_iter, int32_t *p, int32_t *passes,
                                          void *stream);
+
+/* Result of one spectral clustering (respca_spectral_labels). */
+typedef struct {
+    int32_t outer_iters;     /* Rayleigh-Ritz steps of the eigensolver */
+    int32_t matvecs;         /* products of M with the search block */
+    double residual;         /* max_j ||M u_j - theta_j u_j|| over the c eigenpairs kept */
+    double sigma2;           /* the affinity's sigma^2 */
+    double theta_c;          /* c-th largest Ritz value */
+    double theta_next;       /* (c+1)-th largest Ritz value (eigen-gap = theta_c - theta_next) */
+    int32_t lloyd_passes;    /* K-means passes on the embedding */
+    int32_t converged;       /* 1 if residual <= 1e-5 within the iteration cap */
+} respca_spectral_info;
+
+/*
+ * The spectral p step alone: labels of the n columns of Y (d x n device FP32,
+ * leading dimension ldy >= d) in c groups by normalised spectral clustering
+ * (Ng, Jordan and Weiss), the nonlinear clustering Sec. 4.2 offers in place of
+ * K-means:
+ *   A_ij = exp(-||y_i - y_j||^2 / (2 sigma^2)) for i != j, A_ii = 0, with
+ *   sigma^2 = cfg.spectral_scale x the mean of ||y_i - y_j||^2 over i != j;
+ *   M = D^{-1/2} A D^{-1/2} (D = row sums of A); U = the eigenvectors of M's
+ *   c largest eigenvalues; rows of U scaled to unit length; K-means (k-means++
+ *   with cfg.seed, then Lloyd, as respca_init_labels) on those rows.
+ * The eigenvectors come from Chebyshev-filtered subspace iteration with
+ * Rayleigh-Ritz on a block of c + 8 vectors (at most 100 steps of degree 8).
+ * The handle keeps an n x n FP32 matrix in its workspace.  Limits: 1 <= c <= 64,
+ * c < n <= 32768 (RESPCA_ERR_UNSUPPORTED beyond).  p: n device int32 outputs;
+ * info: optional host output.  Synchronises the handle's stream.
+ */
+respca_status respca_spectral_labels(respca_handle h, const float *Y, int64_t d, int64_t n,
+                                     int64_t ldy, int32_t c, int32_t *p,
+                                     respca_spectral_info *info);
 
 /*
  * Learned warm start.  Not in the paper: an unrolled continuation of the

@@ -57,6 +57,7 @@ struct respca_ctx {
     } lloyd_graph[2];
     int lloyd_graph_next = 0;               // slot the next new graph replaces
     std::vector<respca_ctx*> lanes;         // batch lanes (respca_solve_batched), made on first use
+    respca_ctx* spec_km = nullptr;          // K-means on the spectral embedding (own workspace)
     respca_config cfg{};
     std::string last_error;
 
@@ -69,7 +70,9 @@ struct respca_ctx {
         L16, S16, T16, X16,   // BF16 state and X of the bf16 phase (precision = 1)
         mu_a,                 // centroid operand of the swapped dense search
         bn_part,              // per-chunk ||B_j||^2 of the l2,1 iteration
-        sumsD;                // FP64 sums of the next D under the iteration's starting labels
+        sumsD,                // FP64 sums of the next D under the iteration's starting labels
+        sp_M, sp_sqn, sp_part, sp_gsum, sp_sig, sp_deg, sp_Y, sp_W, sp_T, sp_Z, sp_H, sp_Q, sp_ev,
+        sp_res, sp_E;         // spectral p step: affinity, search blocks, Rayleigh-Ritz, embedding
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -128,7 +131,9 @@ std::vector<DevBuf*> all_bufs(respca_ctx* h) {
                       &h->labels_pass,
                       &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count,
                       &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
-                      &h->bn_part, &h->sumsD};
+                      &h->bn_part, &h->sumsD, &h->sp_M, &h->sp_sqn, &h->sp_part, &h->sp_gsum,
+                      &h->sp_sig, &h->sp_deg, &h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z, &h->sp_H, &h->sp_Q,
+                      &h->sp_ev, &h->sp_res, &h->sp_E};
 }
 
 respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64_t lds,
@@ -219,6 +224,125 @@ respca_status finish_centroids(respca_ctx* h, int c, int64_t d, float* dst, cons
                        prev ? P<double>(h->drift) : nullptr, h->stream));
     CK(launch_separation(dst, P<int32_t>(h->counts), c, d, P<float>(h->pair_ss), P<double>(h->sep2),
                          h->stream));
+    return RESPCA_OK;
+}
+
+// ---------------------------------------------------------------- spectral p step
+// Normalised spectral clustering of the columns of Y (Sec. 4.2 alternative to
+// K-means): affinity and M = D^{-1/2} A D^{-1/2} (k_spectral.cu), the top-c
+// eigenvectors of M by Chebyshev-filtered subspace iteration with
+// Rayleigh-Ritz, the row-normalised embedding, and K-means on it in a second
+// context whose workspace does not disturb the solver's.
+constexpr int kSpecMaxC = 64;
+constexpr int64_t kSpecMaxN = 32768;
+constexpr int kSpecGuard = 8;       // extra vectors in the search block
+constexpr int kSpecDegree = 8;      // Chebyshev degree per Rayleigh-Ritz step
+constexpr int kSpecMaxOuter = 100;
+// residual ||M u - theta u|| of the kept eigenpairs at which the eigensolver
+// stops: about ten times the FP32 rounding of one product with M
+double spec_tol(int64_t n) { return std::max(1e-5, 1e-6 * std::sqrt((double)n)); }
+
+respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, int64_t d, int64_t n, int c,
+                                   int32_t* p, respca_spectral_info* info) {
+    if (c < 1 || c > kSpecMaxC || n > kSpecMaxN || n <= c)
+        return fail(h, RESPCA_ERR_UNSUPPORTED, "spectral p step: needs 1 <= c <= 64 and c < n <= 32768");
+    const int b = (int)std::min<int64_t>(n, c + kSpecGuard);
+    const int parts = 152;
+    cudaStream_t st = h->stream;
+    CK(ensure(h->sp_M, sizeof(float) * (size_t)n * n));
+    CK(ensure(h->sp_sqn, sizeof(float) * n));
+    CK(ensure(h->sp_part, sizeof(double) * parts));
+    CK(ensure(h->sp_gsum, sizeof(double) * n));
+    CK(ensure(h->sp_sig, sizeof(double) * 2));
+    CK(ensure(h->sp_deg, sizeof(double) * n));
+    for (DevBuf* bb : {&h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z}) CK(ensure(*bb, sizeof(float) * (size_t)n * b));
+    CK(ensure(h->sp_H, sizeof(float) * b * b));
+    CK(ensure(h->sp_Q, sizeof(float) * b * b));
+    CK(ensure(h->sp_ev, sizeof(double) * b));
+    CK(ensure(h->sp_res, sizeof(double) * c));
+    CK(ensure(h->sp_E, sizeof(float) * (size_t)n * c));
+    if (!h->spec_km) {
+        respca_config kc = h->cfg;
+        kc.stream = h->stream;
+        kc.device = h->device;
+        kc.timing = 0;
+        kc.p_step = 0;
+        respca_status cs = respca_create(&h->spec_km, &kc);
+        if (cs != RESPCA_OK) return fail(h, cs, "spectral p step: K-means context");
+    }
+    float* M = P<float>(h->sp_M);
+    CK(launch_spec_affinity(Y, ldy, d, n, h->cfg.spectral_scale, M, P<float>(h->sp_sqn), P<double>(h->sp_part),
+                            parts, P<double>(h->sp_gsum), P<double>(h->sp_sig), P<double>(h->sp_deg), st));
+    float* Yb = P<float>(h->sp_Y);   // current orthonormal block (n x b)
+    float* W = P<float>(h->sp_W);    // M Yb
+    float* T = P<float>(h->sp_T);    // scratch
+    float* Z = P<float>(h->sp_Z);    // scratch
+    const int64_t nb = n * (int64_t)b;
+    CK(launch_spec_start(Yb, n, b, h->cfg.seed, st));
+    CK(launch_spec_cgs2(Yb, n, b, h->cfg.seed, st));
+    std::vector<double> ev(b), res(c);
+    double sig2 = 0.0;
+    int outer = 0, matvecs = 0;
+    double rmax = INFINITY;
+    double lo = -1.0;   // the spectrum of M lies in [-1, 1]
+    for (;;) {
+        // Rayleigh-Ritz on span(Yb): H = Yb^T M Yb, rotate to the Ritz vectors
+        CK(launch_spec_gemm_tn(M, n, Yb, n, W, n, n, b, n, 1.f, st));
+        ++matvecs;
+        CK(launch_spec_gemm_tn(Yb, n, W, n, P<float>(h->sp_H), b, b, b, n, 1.f, st));
+        CK(launch_spec_jacobi(P<float>(h->sp_H), b, P<float>(h->sp_Q), P<double>(h->sp_ev), st));
+        CK(launch_spec_rotate(Yb, P<float>(h->sp_Q), T, n, b, st));
+        CK(launch_spec_rotate(W, P<float>(h->sp_Q), Z, n, b, st));
+        std::swap(Yb, T);
+        std::swap(W, Z);
+        CK(launch_spec_residual(W, Yb, P<double>(h->sp_ev), n, c, P<double>(h->sp_res), st));
+        CK(cudaMemcpyAsync(ev.data(), h->sp_ev.p, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(res.data(), h->sp_res.p, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&sig2, h->sp_sig.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        rmax = 0.0;
+        for (double r : res) rmax = std::max(rmax, r);
+        if (!(rmax > spec_tol(n)) || outer >= kSpecMaxOuter || b == n) break;
+        ++outer;
+        // Chebyshev filter of degree kSpecDegree damping [lo, a], a = the smallest
+        // Ritz value of the block: Y_{k+1} = (2/e)(M - cen) Y_k - Y_{k-1}
+        const double a = std::max(ev[b - 1], lo + 0.05);
+        const double e = 0.5 * (a - lo), cen = 0.5 * (a + lo);
+        // Y1 = (M Y0 - cen Y0) / e, with M Y0 = W from the Rayleigh-Ritz step
+        float* y0 = Yb;
+        float* y1 = T;
+        float* y2 = Z;
+        CK(launch_spec_axpby(y1, W, y0, nullptr, nb, (float)(1.0 / e), (float)(-cen / e), 0.f, st));
+        for (int k = 2; k <= kSpecDegree; ++k) {
+            CK(launch_spec_gemm_tn(M, n, y1, n, W, n, n, b, n, 1.f, st));   // W as scratch: M y1
+            ++matvecs;
+            CK(launch_spec_axpby(y2, W, y1, y0, nb, (float)(2.0 / e), (float)(-2.0 * cen / e), -1.f, st));
+            float* t = y0;
+            y0 = y1;
+            y1 = y2;
+            y2 = t;
+        }
+        // the filtered block y1 becomes the new (orthonormalised) search block
+        CK(launch_spec_cgs2(y1, n, b, h->cfg.seed + (uint64_t)outer, st));
+        if (y1 != Yb) {
+            // keep the buffer roles fixed: Yb holds the block, T and Z are scratch
+            CK(cudaMemcpyAsync(Yb, y1, sizeof(float) * nb, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    CK(launch_spec_embed(Yb, n, c, P<float>(h->sp_E), st));
+    int32_t passes = 0;
+    respca_status ks = respca_init_labels(h->spec_km, RESPCA_F32, h->sp_E.p, c, n, c, c, p, &passes);
+    if (ks != RESPCA_OK) return fail(h, ks, "spectral p step: K-means on the embedding");
+    if (info) {
+        info->outer_iters = outer;
+        info->matvecs = matvecs;
+        info->residual = rmax;
+        info->sigma2 = sig2;
+        info->theta_c = ev[c - 1];
+        info->theta_next = (c < b) ? ev[c] : NAN;
+        info->lloyd_passes = passes;
+        info->converged = (rmax <= spec_tol(n)) ? 1 : 0;
+    }
     return RESPCA_OK;
 }
 
@@ -617,6 +741,9 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         bool vec;
     } v{dtype, X, ldx, 0, L, S, pb.Th, lds, pb.vec};
     const bool l21 = h->cfg.s_norm == 1;
+    const bool spectral = h->cfg.p_step == 1;
+    if (spectral && dtype != RESPCA_F32)
+        return fail(h, RESPCA_ERR_UNSUPPORTED, "spectral p step: X must be FP32");
     if (h->cfg.precision == 1 && !is_warm && !l21) {
         const int64_t ld16 = (d + 7) / 8 * 8;
         const size_t bytes = sizeof(uint16_t) * (size_t)ld16 * n;
@@ -641,6 +768,11 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     if (!is_warm) {
         if (p0) {
             CK(cudaMemcpyAsync(p, p0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
+        } else if (nx > 0.0 && spectral) {
+            respca_spectral_info si{};
+            rs = spectral_labels_impl(h, static_cast<const float*>(X), ldx, d, n, c, p, &si);
+            if (rs != RESPCA_OK) return rs;
+            out.init_lloyd_passes = si.lloyd_passes;
         } else if (nx > 0.0) {
             int passes = 0;
             rs = init_labels_impl(h, pb, &passes);
@@ -698,7 +830,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     const double kappa = h->cfg.kappa;
     const double safety = safety_factor(d);
     int t_start = 0;
-    if (!is_warm && h->cfg.ramp_skip && max_iter > 0 && !l21) {
+    if (!is_warm && h->cfg.ramp_skip && max_iter > 0 && !l21 && !spectral) {
         // Leading iterations with S = 0 and no label move, in closed form:
         // L_{t+1} = X_m + a_t g_t X_r, Theta_{t+1} = rho_t b_t g_t X_r.
         CK(cudaMemsetAsync(&ds->ramp_r2, 0, sizeof(double) + sizeof(unsigned long long) + sizeof(unsigned int),
@@ -781,6 +913,27 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         if (timing) CK(cudaEventRecord(h->evk1, h->stream));
         out.fused_launches += 1;
         CK(launch_reduce_norms(P<double>(h->norm_part), mt, nch, ds, h->stream));
+        double r2, dl2, ds2;
+        if (spectral) {
+            // p step by spectral clustering of the columns of L (Sec. 4.2), then the
+            // next centroids: D = X - S + Theta/rho_{t+1} under the new labels
+            respca_spectral_info si{};
+            rs = spectral_labels_impl(h, L, lds, d, n, c, p, &si);
+            if (rs != RESPCA_OK) return rs;
+            CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts), P<int32_t>(h->tile_off),
+                                  P<TileDesc>(h->tiles), ds, h->stream));
+            CK(launch_colsum(kSumD, v.xd, v.X, v.ldx, nullptr, v.S, v.Th, v.ld, sc.inv_rho_next,
+                             P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart), v.vec,
+                             h->stream, v.sd));
+            rs = finish_centroids(h, c, d, P<float>(h->mu), nullptr);
+            if (rs != RESPCA_OK) return rs;
+            rs = read_status(h);
+            if (rs != RESPCA_OK) return rs;
+            out.lloyd_passes += si.lloyd_passes;
+            r2 = h->hstat->norm2[0];
+            dl2 = h->hstat->norm2[1];
+            ds2 = h->hstat->norm2[2];
+        } else {
         // p step, first Lloyd assignment: search only the columns the bounds cannot settle
         CK(launch_flag_bounds(kBoundsIter, P<float>(h->own_part), P<float>(h->dl_part), nch, n, c, p,
                               P<int32_t>(h->counts), P<double>(h->sep2), safety, P<double>(h->drift),
@@ -806,7 +959,9 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         out.lloyd_passes += 1;
         out.assigned_columns += h->hstat->flagged;
         out.rechecked_columns += h->hstat->rechecked;
-        const double r2 = h->hstat->norm2[0], dl2 = h->hstat->norm2[1], ds2 = h->hstat->norm2[2];
+        r2 = h->hstat->norm2[0];
+        dl2 = h->hstat->norm2[1];
+        ds2 = h->hstat->norm2[2];
 
         if (h->hstat->changed == 0) {
             CK(cudaMemcpyAsync(h->mu.p, h->mu_next.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice, h->stream));
@@ -852,6 +1007,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             CK(cudaMemcpyAsync(h->mu.p, h->mu_next.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice, h->stream));
             CK(launch_count_changed(p, P<int32_t>(h->labels_prev), n, ds, h->stream));
         }
+        }   // K-means p step
         rho = rho_next;
         out.iters = t + 1;
         out.err_resid = std::sqrt(r2) / nx;
@@ -922,6 +1078,8 @@ void respca_config_default(respca_config* cfg) {
     cfg->ramp_skip = 1;
     cfg->precision = 0;
     cfg->switch_tol = 1e-2;
+    cfg->p_step = 0;
+    cfg->spectral_scale = 0.125;
 }
 
 respca_status respca_create(respca_handle* out, const respca_config* cfg) {
@@ -934,6 +1092,9 @@ respca_status respca_create(respca_handle* out, const respca_config* cfg) {
         return RESPCA_ERR_INVALID_ARG;
     if (c.s_norm != 0 && c.s_norm != 1) return RESPCA_ERR_INVALID_ARG;
     if (c.precision != 0 && c.precision != 1) return RESPCA_ERR_INVALID_ARG;
+    if (c.p_step != 0 && c.p_step != 1) return RESPCA_ERR_INVALID_ARG;
+    if (c.p_step == 1 && (c.precision != 0 || !(c.spectral_scale > 0.0) || !std::isfinite(c.spectral_scale)))
+        return RESPCA_ERR_INVALID_ARG;
     if (c.stop_after_ramp != 0 && c.stop_after_ramp != 1) return RESPCA_ERR_INVALID_ARG;
     int dev = c.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return RESPCA_ERR_CUDA;
@@ -959,6 +1120,8 @@ respca_status respca_destroy(respca_handle h) {
     if (!h) return RESPCA_OK;
     for (respca_ctx* lane : h->lanes) respca_destroy(lane);
     h->lanes.clear();
+    if (h->spec_km) respca_destroy(h->spec_km);
+    h->spec_km = nullptr;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
@@ -1136,6 +1299,14 @@ respca_status respca_column_norms(const float* S, int64_t d, int64_t n, int64_t 
     if (launch_column_norms(S, lds, d, n, out, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
         return RESPCA_ERR_CUDA;
     return RESPCA_OK;
+}
+
+respca_status respca_spectral_labels(respca_handle h, const float* Y, int64_t d, int64_t n, int64_t ldy,
+                                     int32_t c, int32_t* p, respca_spectral_info* info) {
+    if (!h || !Y || !p || d < 1 || n < 1 || ldy < d || c < 1) return fail(h, RESPCA_ERR_INVALID_ARG, "bad arguments");
+    if (!(h->cfg.spectral_scale > 0.0)) return fail(h, RESPCA_ERR_INVALID_ARG, "spectral_scale must be > 0");
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, RESPCA_ERR_CUDA, "cudaSetDevice");
+    return spectral_labels_impl(h, Y, ldy, d, n, c, p, info);
 }
 
 const char* respca_status_string(respca_status s) {

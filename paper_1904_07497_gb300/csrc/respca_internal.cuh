@@ -369,6 +369,23 @@ cudaError_t launch_mlp_backward(const float* P, int nz, int H, int nout, const f
 cudaError_t launch_adam(float* P, const float* G, float* M, float* V, int64_t count, float lr, float b1,
                         float b2, float eps, float c1, float c2, cudaStream_t st);
 
+// ---------------------------------------------------------------- spectral p step
+cudaError_t launch_spec_gemm_tn(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc,
+                                int64_t m, int64_t n, int64_t K, float alpha, cudaStream_t st);
+cudaError_t launch_spec_affinity(const float* Y, int64_t ldy, int64_t d, int64_t n, double scale, float* G,
+                                 float* sqn, double* part, int parts, double* gsum, double* sig, double* deg,
+                                 cudaStream_t st);
+cudaError_t launch_spec_start(float* Y, int64_t n, int b, uint64_t seed, cudaStream_t st);
+cudaError_t launch_spec_axpby(float* out, const float* T, const float* Y, const float* Yp, int64_t count,
+                              float alpha, float beta, float gamma, cudaStream_t st);
+cudaError_t launch_spec_cgs2(float* Y, int64_t n, int b, uint64_t seed, cudaStream_t st);
+size_t spec_jacobi_smem(int b);
+cudaError_t launch_spec_jacobi(const float* H, int b, float* Q, double* evals, cudaStream_t st);
+cudaError_t launch_spec_rotate(const float* Y, const float* Q, float* out, int64_t n, int b, cudaStream_t st);
+cudaError_t launch_spec_residual(const float* W, const float* Y, const double* evals, int64_t n, int c,
+                                 double* res, cudaStream_t st);
+cudaError_t launch_spec_embed(const float* Y, int64_t n, int c, float* E, cudaStream_t st);
+
 // Dispatch a runtime dtype (0 f32, 1 bf16, 2 f16) to a template lambda.
 #define RESPCA_DISPATCH_X(dtype, TX, ...)                       \
     do {                                                        \

@@ -35,7 +35,17 @@ class respca_config(ctypes.Structure):
                 ("ramp_skip", ctypes.c_int32), ("batch_lanes", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("s_norm", ctypes.c_int32),
                 ("switch_tol", ctypes.c_double), ("stop_after_ramp", ctypes.c_int32),
-                ("reserved4", ctypes.c_int32)]
+                ("p_step", ctypes.c_int32), ("spectral_scale", ctypes.c_double)]
+
+
+class respca_spectral_info(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int32), ("matvecs", ctypes.c_int32),
+                ("residual", ctypes.c_double), ("sigma2", ctypes.c_double),
+                ("theta_c", ctypes.c_double), ("theta_next", ctypes.c_double),
+                ("lloyd_passes", ctypes.c_int32), ("converged", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class respca_stats(ctypes.Structure):
@@ -130,6 +140,9 @@ def load():
     lib.respca_mlp_backward.restype = ctypes.c_int
     lib.respca_adam_step.argtypes = [_VP, _VP, _VP, _VP, _I64, _D, _D, _D, _D, ctypes.c_int32, _VP]
     lib.respca_adam_step.restype = ctypes.c_int
+    lib.respca_spectral_labels.argtypes = [_VP, _VP, _I64, _I64, _I64, ctypes.c_int32, _VP,
+                                           ctypes.POINTER(respca_spectral_info)]
+    lib.respca_spectral_labels.restype = ctypes.c_int
     lib.respca_status_string.argtypes = [ctypes.c_int]
     lib.respca_status_string.restype = ctypes.c_char_p
     lib.respca_last_error.argtypes = [_VP]
@@ -296,10 +309,13 @@ class Solver:
                  seed: int = 0, stream=None, device: int | None = None, timing: bool = False,
                  search_impl: int = 0, ramp_skip: bool = True, batch_lanes: int = 0,
                  precision: int = 0, switch_tol: float | None = None, s_norm: int = 0,
-                 stop_after_ramp: bool = False):
+                 stop_after_ramp: bool = False, p_step: int = 0, spectral_scale: float | None = None):
         import torch
         cfg = respca_config_default()
         cfg.stop_after_ramp = 1 if stop_after_ramp else 0
+        cfg.p_step = p_step
+        if spectral_scale is not None:
+            cfg.spectral_scale = spectral_scale
         cfg.search_impl = search_impl
         cfg.ramp_skip = 1 if ramp_skip else 0
         cfg.batch_lanes = batch_lanes
@@ -347,6 +363,20 @@ class Solver:
         p = torch.empty(X.shape[1], device=X.device, dtype=torch.int32)
         passes = respca_init_labels(self.h, X, c, p)
         return p, passes
+
+
+def respca_spectral_labels(h, Y, c: int, p=None) -> tuple[object, dict]:
+    """Spectral p step alone (Sec. 4.2 alternative to K-means): labels of the
+    columns of a column-major FP32 CUDA tensor Y (d, n).  Returns (p, info)."""
+    import torch
+    d, n = Y.shape
+    ldy = _colmajor(Y, "Y")
+    if p is None:
+        p = torch.empty(n, device=Y.device, dtype=torch.int32)
+    info = respca_spectral_info()
+    rc = load().respca_spectral_labels(h, Y.data_ptr(), d, n, ldy, int(c), p.data_ptr(), ctypes.byref(info))
+    _check(h, rc, "respca_spectral_labels")
+    return p, info.as_dict()
 
 
 # ------------------------------------------------------------------ learned warm start

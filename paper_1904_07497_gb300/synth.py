@@ -73,6 +73,25 @@ def clustered_columns(d: int, n: int, c: int, seed: int, sparsity: float = 0.0) 
     return Problem(X=X, L0=L0, S0=S0, rank=c, truth_labels=labels)
 
 
+def rings(d: int, n: int, c: int, seed: int, noise: float = 0.05) -> Problem:
+    """Nonlinear groups: c concentric circles (radii 1..c) in a random 2-D
+    plane of R^d, n points spread over them as evenly as possible at uniform
+    angles, plus isotropic N(0, noise^2) noise.  No hyperplane or centroid
+    rule separates the groups; a neighbourhood graph does.  truth_labels is
+    the circle of every point.
+
+    Drawing order: plane basis, angles, noise."""
+    g = _rng(seed)
+    Q, _ = np.linalg.qr(g.standard_normal((d, 2)))
+    labels = (np.arange(n) % c).astype(np.int32)
+    ang = g.uniform(0.0, 2.0 * np.pi, size=n)
+    r = labels.astype(np.float64) + 1.0
+    P2 = np.stack([r * np.cos(ang), r * np.sin(ang)])          # 2 x n
+    X = Q @ P2 + noise * g.standard_normal((d, n))
+    X = np.asfortranarray(X.astype(np.float32))
+    return Problem(X=X, L0=None, S0=None, rank=c, truth_labels=labels)
+
+
 def _smooth_image(g: np.random.Generator, h: int, w: int, sigma: float) -> np.ndarray:
     """Gaussian-blurred white noise, min-max scaled to [0, 1]."""
     noise = g.random((h, w))

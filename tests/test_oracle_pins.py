@@ -586,3 +586,60 @@ def test_warmnet_adam_first_step_is_signed_lr():
     g = np.array([3.0, -0.5, 1e-3, -20.0])
     P, _, _ = warmnet.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, 0.01, eps=1e-12)
     np.testing.assert_allclose(P, -0.01 * np.sign(g), rtol=1e-8)
+
+
+def _same_partition(a, b):
+    m = {}
+    for x, y in zip(np.asarray(a).tolist(), np.asarray(b).tolist()):
+        if m.setdefault(x, y) != y:
+            return False
+    return len(set(m.values())) == len(m)
+
+
+def test_spectral_mean_sq_distance_closed_form():
+    """Mean squared distance over pairs i != j equals
+    2n/(n-1) (mean ||y||^2 - ||mean y||^2)."""
+    from oracle import spectral
+    Y = np.random.default_rng(3).standard_normal((4, 37)) + 2.0
+    n = Y.shape[1]
+    closed = 2 * n / (n - 1) * (np.mean(np.sum(Y * Y, axis=0)) - np.sum(Y.mean(axis=1) ** 2))
+    assert spectral.mean_sq_distance(Y) == pytest.approx(closed, rel=1e-12)
+
+
+def test_spectral_block_diagonal_affinity_gives_indicator_subspace():
+    """Groups so far apart that every cross affinity underflows to 0: M is
+    block diagonal, its top c eigenvalues are exactly 1, and their
+    eigenspace is spanned by D^{1/2} 1_g of each group g (M D^{1/2} 1_g =
+    D^{-1/2} A 1_g = D^{1/2} 1_g)."""
+    from oracle import spectral
+    g = np.random.default_rng(8)
+    c, per, d = 3, 15, 5
+    Y = np.concatenate([100.0 * k + 0.1 * g.standard_normal((d, per)) for k in range(c)], axis=1)
+    truth = np.repeat(np.arange(c), per)
+    scale = 0.05 / spectral.mean_sq_distance(Y)
+    A, deg, _ = spectral.affinity(Y, scale)
+    assert np.all(A[truth[:, None] != truth[None, :]] == 0.0)
+    U, w, E = spectral.embedding(Y, c, scale)
+    np.testing.assert_allclose(w, 1.0, atol=1e-12)
+    P = np.zeros((c * per, c * per))
+    for k in range(c):
+        v = np.where(truth == k, np.sqrt(deg), 0.0)
+        v /= np.linalg.norm(v)
+        P += np.outer(v, v)
+    np.testing.assert_allclose(U @ U.T, P, atol=1e-10)
+    # the row-normalised embedding collapses every group to one point
+    for k in range(c):
+        Ek = E[:, truth == k]
+        assert np.abs(Ek - Ek[:, :1]).max() < 1e-10
+    assert _same_partition(spectral.labels(Y, c, scale, seed=0), truth)
+
+
+def test_spectral_labels_recover_rings_where_kmeans_fails(oracle_mod):
+    """Concentric circles: the spectral p step finds the circles, K-means on
+    the columns does not (Sec. 4.2's reason for a nonlinear p step)."""
+    from oracle import spectral
+    pr = synth.rings(10, 600, 3, seed=3, noise=0.05)
+    X = pr.X.astype(np.float64)
+    assert _same_partition(spectral.labels(X, 3, 0.004, seed=0), pr.truth_labels)
+    pk, _ = oracle_mod.init_labels(X, 3, 0)
+    assert not _same_partition(pk, pr.truth_labels)
