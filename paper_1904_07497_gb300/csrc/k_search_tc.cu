@@ -179,7 +179,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
                  : "memory");
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // byte offset of 16-byte chunk q of row m in a K-major 128-byte-swizzle tile
 __device__ __forceinline__ uint32_t sw128_off(int m, int q) {

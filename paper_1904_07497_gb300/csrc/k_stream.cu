@@ -172,12 +172,15 @@ __global__ void __launch_bounds__(kThreads)
 // Centroids from FP64 cluster sums (kept up to date incrementally).
 __global__ void __launch_bounds__(kThreads)
     k_centroids_from_sums(const double* __restrict__ sums, const int32_t* __restrict__ counts,
-                          int64_t d, float* __restrict__ mu) {
+                          int64_t d, float* __restrict__ mu, float* __restrict__ mu_old) {
     const int i = blockIdx.y;
     const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= d) return;
+    const int64_t e = (int64_t)i * d + r;
+    if (mu_old) mu_old[e] = mu[e];   // the previous centroids, for the drift
     const int cnt = counts[i];
-    if (cnt == 0 || r >= d) return;
-    mu[(int64_t)i * d + r] = (float)(sums[(int64_t)i * d + r] * (1.0 / (double)cnt));
+    if (cnt == 0) return;
+    mu[e] = (float)(sums[e] * (1.0 / (double)cnt));
 }
 
 // Cluster sums after a Lloyd pass moved some columns: sums_i += (columns that
@@ -262,6 +265,72 @@ __global__ void __launch_bounds__(kStatThreads)
             mu_norm2[i] = (double)a;
             mu_normf[i] = a;
             if (drift) drift[i] = sqrt((double)b) * (1.0 + 1e-5);
+        }
+    }
+}
+
+// k_centroids_from_sums, the previous-centroid copy, k_mu_stats and the TF32
+// split in one CTA per centroid.  The stats use k_mu_stats' thread mapping and
+// summation order, so they are bit-identical to the separate kernels.
+__global__ void __launch_bounds__(kStatThreads)
+    k_centroids_stats(const double* __restrict__ sums, const int32_t* __restrict__ counts, int64_t d,
+                      float* __restrict__ mu, float* __restrict__ mu_old, double* __restrict__ mu_norm2,
+                      float* __restrict__ mu_normf, double* __restrict__ drift, MuSplitOut sp) {
+    __shared__ float red[kStatThreads / 32][2];
+    const int i = blockIdx.x;
+    const int cnt = counts[i];
+    float* m = mu + (int64_t)i * d;
+    float* mo = mu_old + (int64_t)i * d;
+    float acc = 0.f, ca = 0.f, dr = 0.f, cd = 0.f;
+    for (int64_t r = threadIdx.x; r < d; r += kStatThreads) {
+        const float old = m[r];
+        mo[r] = old;
+        float v = old;
+        if (cnt != 0) {
+            v = (float)(sums[(int64_t)i * d + r] * (1.0 / (double)cnt));
+            m[r] = v;
+        }
+        {
+            const float y = v * v - ca;
+            const float t = acc + y;
+            ca = (t - acc) - y;
+            acc = t;
+        }
+        {
+            const float e = v - old;
+            const float y = e * e - cd;
+            const float t = dr + y;
+            cd = (t - dr) - y;
+            dr = t;
+        }
+        if (sp.hi) {
+            const int64_t idx = (int64_t)i * sp.dpad + r;
+            const float hi = tf32_hi(v);
+            if (i < sp.Npad) {
+                sp.hi[idx] = hi;
+                sp.lo[idx] = v - hi;
+            }
+            if (sp.a) {
+                sp.a[idx] = v;
+                sp.a[(int64_t)sp.arows * sp.dpad + idx] = v - hi;
+            }
+        }
+    }
+    acc = warp_sum(acc);
+    dr = warp_sum(dr);
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = acc;
+        red[threadIdx.x >> 5][1] = dr;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float a = red[threadIdx.x][0], b = red[threadIdx.x][1];
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (threadIdx.x == 0) {
+            mu_norm2[i] = (double)a;
+            mu_normf[i] = a;
+            drift[i] = sqrt((double)b) * (1.0 + 1e-5);
         }
     }
 }
@@ -411,7 +480,7 @@ __global__ void __launch_bounds__(kThreads)
                   const int32_t* __restrict__ counts, const double* __restrict__ sep2,
                   double safety, const double* __restrict__ drift, float* __restrict__ ub,
                   float* __restrict__ lb, int32_t* __restrict__ flag_list,
-                  DevStatus* __restrict__ status) {
+                  DevStatus* __restrict__ status, int32_t* __restrict__ labels_copy) {
     // largest and second largest drift over active clusters (per block)
     __shared__ double s_d1[kThreads], s_d2[kThreads];
     __shared__ int s_i1[kThreads];
@@ -456,6 +525,7 @@ __global__ void __launch_bounds__(kThreads)
     bool flag = false;
     if (j < n) {
         const int p = labels[j];
+        if (labels_copy) labels_copy[j] = p;   // the labels before this pass's search
         const double other = (p == i1) ? d2 : d1;
         double u, l;
         if (mode == kBoundsIter) {
@@ -705,6 +775,10 @@ __global__ void k_lloyd_init(DevStatus* __restrict__ status, int passes0) {
     status->acc_flagged = 0;
     status->acc_passes = passes0;
     status->acc_rechecked = 0;
+    status->flagged = 0;   // the per-pass counters start at zero (k_lloyd_pass_end re-zeroes them)
+    status->changed = 0;
+    status->rechecked = 0;
+    status->last_changed = 0;
 }
 
 __global__ void k_lloyd_pass_end(DevStatus* __restrict__ status, cudaGraphConditionalHandle cond,
@@ -714,6 +788,11 @@ __global__ void k_lloyd_pass_end(DevStatus* __restrict__ status, cudaGraphCondit
     const int passes = ++status->acc_passes;
     const bool more = status->changed != 0 && passes < max_passes && status->timeout == 0;
     cudaGraphSetConditional(cond, more ? 1u : 0u);
+    // hand the pass's result to the host and clear the counters for the next pass
+    status->last_changed = status->changed;
+    status->flagged = 0;
+    status->changed = 0;
+    status->rechecked = 0;
 }
 
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
@@ -786,10 +865,10 @@ cudaError_t launch_centroids(const float* Dpart, const int32_t* tile_off, const 
 }
 
 cudaError_t launch_centroids_from_sums(const double* sums, const int32_t* counts, int c, int64_t d,
-                                       float* mu, cudaStream_t st) {
+                                       float* mu, cudaStream_t st, float* mu_old) {
     count_launches(1);
     const dim3 grid(grid_for(d, kThreads), c);
-    k_centroids_from_sums<<<grid, kThreads, 0, st>>>(sums, counts, d, mu);
+    k_centroids_from_sums<<<grid, kThreads, 0, st>>>(sums, counts, d, mu, mu_old);
     return cudaGetLastError();
 }
 
@@ -823,14 +902,23 @@ cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t
     return cudaGetLastError();
 }
 
+cudaError_t launch_centroids_stats(const double* sums, const int32_t* counts, int c, int64_t d, float* mu,
+                                   float* mu_old, double* mu_norm2, float* mu_normf, double* drift,
+                                   const MuSplitOut& sp, cudaStream_t st) {
+    count_launches(1);
+    k_centroids_stats<<<c, kStatThreads, 0, st>>>(sums, counts, d, mu, mu_old, mu_norm2, mu_normf, drift, sp);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_part, int nchunks,
                                int64_t n, int c, const int32_t* labels, const int32_t* counts,
                                const double* sep2, double safety, const double* drift, float* ub,
-                               float* lb, int32_t* flag_list, DevStatus* status, cudaStream_t st) {
+                               float* lb, int32_t* flag_list, DevStatus* status, cudaStream_t st,
+                               int32_t* labels_copy) {
     count_launches(1);
     k_flag_bounds<<<grid_for(n, kThreads), kThreads, 0, st>>>(mode, own_part, dl_part, nchunks, n, c,
                                                               labels, counts, sep2, safety, drift,
-                                                              ub, lb, flag_list, status);
+                                                              ub, lb, flag_list, status, labels_copy);
     return cudaGetLastError();
 }
 

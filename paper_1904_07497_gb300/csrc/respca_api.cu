@@ -362,15 +362,28 @@ struct Problem {
 // Nearest-centroid search (Sec. 4.2 assignment) for the listed columns of Y
 // (all columns when list is null) against the centroids in h->mu: tensor
 // cores for c <= 256 unless the handle asks for the CUDA-core kernel.
+bool tc_search(respca_ctx* h, int c) { return c <= kTcMaxClusters && h->cfg.search_impl == 0; }
+
+// The TF32 split of the centroids in h->mu (for the tensor-core search).
+respca_status split_centroids(respca_ctx* h, int c, int64_t d) {
+    const int64_t dpad = (d + 31) / 32 * 32;
+    CK(launch_mu_split(P<float>(h->mu), c, d, tc_npad(c), dpad, P<float>(h->mu_hi), P<float>(h->mu_lo),
+                       h->stream, P<float>(h->mu_a)));
+    return RESPCA_OK;
+}
+
+// split_ready: the split of the current centroids is already in place (the
+// device-run Lloyd loop's update writes it).
 respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
-                     const int32_t* list, int c, int32_t* p, bool vec) {
+                     const int32_t* list, int c, int32_t* p, bool vec, bool split_ready = false) {
     DevStatus* ds = P<DevStatus>(h->status);
-    if (c <= kTcMaxClusters && h->cfg.search_impl == 0) {
-        const int Npad = tc_npad(c);
+    if (tc_search(h, c)) {
         const int64_t dpad = (d + 31) / 32 * 32;
         const int64_t rc_cap = tc_plan(n, d, c).rc_cap;
-        CK(launch_mu_split(P<float>(h->mu), c, d, Npad, dpad, P<float>(h->mu_hi), P<float>(h->mu_lo),
-                           h->stream, P<float>(h->mu_a)));
+        if (!split_ready) {
+            const respca_status rs = split_centroids(h, c, d);
+            if (rs != RESPCA_OK) return rs;
+        }
         const bool timing = h->cfg.timing != 0;
         CK(launch_search_tc(dtype, Y, ldy, d, n, list, ds, P<float>(h->mu), P<float>(h->mu_hi),
                             P<float>(h->mu_lo), dpad, P<float>(h->mu_normf), P<int32_t>(h->counts), c,
@@ -408,16 +421,17 @@ struct SearchCounts {
 
 // One Lloyd pass, first half: degrade the bounds by the centroid drift,
 // queue the columns they cannot settle, search them.
+// In the device-run loop the counters are cleared by the previous pass's
+// k_lloyd_pass_end (and by k_lloyd_init before the first), not here.
 respca_status lloyd_pass_search(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ldy,
-                                int64_t d, int64_t n, int c, int32_t* p, bool vec) {
+                                int64_t d, int64_t n, int c, int32_t* p, bool vec, bool in_graph = false) {
     (void)mode;
     DevStatus* ds = P<DevStatus>(h->status);
-    CK(zero_counters(h));
+    if (!in_graph) CK(zero_counters(h));
     CK(launch_flag_bounds(kBoundsLloyd, nullptr, nullptr, 0, n, c, p, P<int32_t>(h->counts), nullptr,
                           1.0, P<double>(h->drift), P<float>(h->ub), P<float>(h->lb),
-                          P<int32_t>(h->flag_list), ds, h->stream));
-    CK(cudaMemcpyAsync(h->labels_pass.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
-    return search(h, dtype, Y, ldy, d, n, P<int32_t>(h->flag_list), c, p, vec);
+                          P<int32_t>(h->flag_list), ds, h->stream, P<int32_t>(h->labels_pass)));
+    return search(h, dtype, Y, ldy, d, n, P<int32_t>(h->flag_list), c, p, vec, in_graph);
 }
 
 // Second half: move the changed columns between the cluster sums and form the
@@ -430,12 +444,18 @@ respca_status lloyd_pass_update(respca_ctx* h, int mode, int dtype, const void* 
                     P<int32_t>(h->boff), P<int32_t>(h->counts), ds, h->stream));
     CK(launch_delta_sums(mode, dtype, Y, ldy, Lp, ldy, P<int2>(h->contrib), P<int32_t>(h->boff), c, d,
                          P<double>(h->sums), h->stream));
-    CK(cudaMemcpyAsync(h->mu_old.p, h->mu.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice,
-                       h->stream));
-    CK(launch_centroids_from_sums(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
-                                  h->stream));
-    CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
-                       P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+    MuSplitOut sp;
+    if (tc_search(h, c)) {
+        sp.Npad = tc_npad(c);
+        sp.dpad = (d + 31) / 32 * 32;
+        sp.arows = sp.Npad <= 64 ? 64 : 128;
+        sp.hi = P<float>(h->mu_hi);
+        sp.lo = P<float>(h->mu_lo);
+        sp.a = sp.Npad <= 128 ? P<float>(h->mu_a) : nullptr;
+    }
+    CK(launch_centroids_stats(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
+                              P<float>(h->mu_old), P<double>(h->mu_norm2), P<float>(h->mu_normf),
+                              P<double>(h->drift), sp, h->stream));
     return RESPCA_OK;
 }
 
@@ -510,7 +530,7 @@ respca_status lloyd_loop_on_device(respca_ctx* h, int mode, int dtype, const voi
                                           cudaStreamCaptureModeRelaxed) != cudaSuccess) {
             rs = RESPCA_ERR_UNSUPPORTED;
         } else {
-            rs = lloyd_pass_search(h, mode, dtype, Y, ldy, d, n, c, p, vec);
+            rs = lloyd_pass_search(h, mode, dtype, Y, ldy, d, n, c, p, vec, true);
             if (rs == RESPCA_OK && launch_lloyd_pass_end(P<DevStatus>(h->status), cond, max_passes,
                                                          h->stream) != cudaSuccess)
                 rs = RESPCA_ERR_CUDA;
@@ -536,6 +556,10 @@ respca_status lloyd_loop_on_device(respca_ctx* h, int mode, int dtype, const voi
     }
     DevStatus* ds = P<DevStatus>(h->status);
     CK(launch_lloyd_init(ds, sc->passes, h->stream));
+    if (tc_search(h, c)) {   // the loop's searches use the split its updates write
+        const respca_status rs = split_centroids(h, c, d);
+        if (rs != RESPCA_OK) return rs;
+    }
     CK(cudaGraphLaunch(g->exec, h->stream));
     respca_status rs = read_status(h);
     if (rs != RESPCA_OK) return rs;
@@ -544,7 +568,7 @@ respca_status lloyd_loop_on_device(respca_ctx* h, int mode, int dtype, const voi
     sc->passes = h->hstat->acc_passes;
     sc->assigned += h->hstat->acc_flagged;
     sc->rechecked += h->hstat->acc_rechecked;
-    if (h->hstat->changed != 0)   // stopped at max_passes: back to the last search's centroids
+    if (h->hstat->last_changed != 0)   // stopped at max_passes: back to the last search's centroids
         CK(cudaMemcpyAsync(h->mu.p, h->mu_old.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice,
                            h->stream));
     return RESPCA_OK;

@@ -60,7 +60,7 @@ struct DevStatus {
     int32_t label_changes;  // running total of changed labels (vs. start of iteration)
     int32_t moved;          // entries of the last moved-column list
     int32_t timeout;        // a bounded device-side wait gave up
-    int32_t pad;
+    int32_t last_changed;   // device-run Lloyd loop: labels changed by its last pass
     int64_t acc_flagged;    // device-run Lloyd loop: columns searched over its passes
     int32_t acc_passes;     //   passes run (including those before the loop)
     int32_t acc_rechecked;  //   near ties re-decided
@@ -97,7 +97,7 @@ cudaError_t launch_centroids(const float* Dpart, const int32_t* tile_off, const 
                              double* sums_out = nullptr);
 
 cudaError_t launch_centroids_from_sums(const double* sums, const int32_t* counts, int c, int64_t d,
-                                       float* mu, cudaStream_t st);
+                                       float* mu, cudaStream_t st, float* mu_old = nullptr);
 
 cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, const float* L,
                               int64_t lds, const int2* contrib, const int32_t* boff, int c, int64_t d,
@@ -107,10 +107,28 @@ cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, c
 cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t d,
                             double* mu_norm2, float* mu_normf, double* drift, cudaStream_t st);
 
+// TF32 split of the centroids for the tensor-core search (layout of launch_mu_split).
+struct MuSplitOut {
+    float* hi = nullptr;   // Npad x dpad
+    float* lo = nullptr;   // Npad x dpad
+    float* a = nullptr;    // 2 arows x dpad (raw rows, then lo rows), or null
+    int64_t dpad = 0;
+    int Npad = 0;
+    int arows = 0;
+};
+
+// One Lloyd update in one launch: centroids from the FP64 sums (previous values
+// to mu_old), then exactly the statistics of launch_mu_stats, and the TF32
+// split when sp.hi is set.
+cudaError_t launch_centroids_stats(const double* sums, const int32_t* counts, int c, int64_t d, float* mu,
+                                   float* mu_old, double* mu_norm2, float* mu_normf, double* drift,
+                                   const MuSplitOut& sp, cudaStream_t st);
+
 cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_part, int nchunks,
                                int64_t n, int c, const int32_t* labels, const int32_t* counts,
                                const double* sep2, double safety, const double* drift, float* ub,
-                               float* lb, int32_t* flag_list, DevStatus* status, cudaStream_t st);
+                               float* lb, int32_t* flag_list, DevStatus* status, cudaStream_t st,
+                               int32_t* labels_copy = nullptr);
 
 cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int c, int4* moved,
                          int2* contrib, int32_t* boff, int32_t* counts, DevStatus* status,
@@ -337,6 +355,10 @@ __device__ __forceinline__ void f4set(float4& v, int q, float x) {
     else if (q == 2) v.z = x;
     else v.w = x;
 }
+
+// The TF32 part of an FP32 value as the tensor cores read it (mantissa truncated
+// to 10 bits).
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // ---------------------------------------------------------------- learned warm start
 // Scalars of one unrolled layer (rho_k, tau_k learned; labels fixed).
