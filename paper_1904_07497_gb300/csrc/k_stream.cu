@@ -183,6 +183,17 @@ __global__ void __launch_bounds__(kThreads)
     mu[e] = (float)(sums[e] * (1.0 / (double)cnt));
 }
 
+// sums_i = n_i mu_i (FP64) for every row: the cluster sums that the centroids
+// mu were formed from, recovered without reading the columns.
+__global__ void __launch_bounds__(kThreads)
+    k_sums_from_means(const float* __restrict__ mu, const int32_t* __restrict__ counts, int64_t d,
+                      double* __restrict__ sums) {
+    const int i = blockIdx.y;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= d) return;
+    sums[(int64_t)i * d + r] = (double)mu[(int64_t)i * d + r] * (double)counts[i];
+}
+
 // Cluster sums after a Lloyd pass moved some columns: sums_i += (columns that
 // joined i) - (columns that left i), of X, L or D = X - S + Theta inv_rho.  k_moved lists each cluster's signed
 // contributions contiguously (bucket i = contrib[boff[i] .. boff[i+1])).  A
@@ -899,6 +910,14 @@ cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t
                             double* mu_norm2, float* mu_normf, double* drift, cudaStream_t st) {
     count_launches(1);
     k_mu_stats<<<c, kStatThreads, 0, st>>>(mu, mu_old, d, mu_norm2, mu_normf, drift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sums_from_means(const float* mu, const int32_t* counts, int c, int64_t d, double* sums,
+                                   cudaStream_t st) {
+    count_launches(1);
+    const dim3 grid(grid_for(d, kThreads), c);
+    k_sums_from_means<<<grid, kThreads, 0, st>>>(mu, counts, d, sums);
     return cudaGetLastError();
 }
 

@@ -580,22 +580,40 @@ respca_status lloyd_loop_on_device(respca_ctx* h, int mode, int dtype, const voi
 // the columns whose label changed), every column's bounds degrade by the
 // centroid drift, and only the columns the bounds cannot settle are searched.
 // Stops when a pass changes no label or after max_passes passes in total.
+//
+// from_means (the p step of an iteration, FP32 L): h->mu holds the means of D
+// under the labels the iteration started with (h->labels_prev, h->counts), and
+// the mean of L = a D + (1 - a) mu_p over a cluster is that same mean, so the
+// cluster sums of L under those labels are n_i mu_i; the columns the first
+// search moved are then added and removed, instead of reading L again.
 respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ldy,
                              int64_t d, int64_t n, int c, int32_t* p, bool vec, int max_passes,
-                             SearchCounts* sc) {
+                             SearchCounts* sc, bool from_means = false) {
     DevStatus* ds = P<DevStatus>(h->status);
     const int mt = max_tiles_for(n, c);
     const float* Lp = (mode == kSumL) ? static_cast<const float*>(Y) : nullptr;
-    CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts), P<int32_t>(h->tile_off),
-                          P<TileDesc>(h->tiles), ds, h->stream));
-    CK(launch_colsum(mode, dtype, Y, ldy, Lp, nullptr, nullptr, ldy, 0.f, P<int32_t>(h->perm),
-                     P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart), vec, h->stream));
-    CK(cudaMemcpyAsync(h->mu_old.p, h->mu.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice,
-                       h->stream));
-    CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c, d,
-                        P<float>(h->mu), h->stream, P<double>(h->sums)));
-    CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
-                       P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+    if (from_means) {
+        CK(launch_sums_from_means(P<float>(h->mu), P<int32_t>(h->counts), c, d, P<double>(h->sums), h->stream));
+        CK(launch_moved(p, P<int32_t>(h->labels_prev), n, c, P<int4>(h->moved), P<int2>(h->contrib),
+                        P<int32_t>(h->boff), P<int32_t>(h->counts), ds, h->stream));
+        CK(launch_delta_sums(mode, dtype, Y, ldy, Lp, ldy, P<int2>(h->contrib), P<int32_t>(h->boff), c, d,
+                             P<double>(h->sums), h->stream));
+        MuSplitOut none;
+        CK(launch_centroids_stats(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
+                                  P<float>(h->mu_old), P<double>(h->mu_norm2), P<float>(h->mu_normf),
+                                  P<double>(h->drift), none, h->stream));
+    } else {
+        CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts), P<int32_t>(h->tile_off),
+                              P<TileDesc>(h->tiles), ds, h->stream));
+        CK(launch_colsum(mode, dtype, Y, ldy, Lp, nullptr, nullptr, ldy, 0.f, P<int32_t>(h->perm),
+                         P<TileDesc>(h->tiles), mt, ds, d, P<float>(h->Dpart), vec, h->stream));
+        CK(cudaMemcpyAsync(h->mu_old.p, h->mu.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice,
+                           h->stream));
+        CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c, d,
+                            P<float>(h->mu), h->stream, P<double>(h->sums)));
+        CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
+                           P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+    }
     // the device loop pays off where a pass is long enough for the launches and
     // status reads it saves to matter; building the graph costs about as much
     // as a few passes of a small problem
@@ -995,7 +1013,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             scount.passes = 1;
             // (BF16 L is summed as the "X" operand: the sums only need its element type)
             rs = v.sd == 1 ? lloyd_continue(h, kSumX, RESPCA_BF16, v.L, v.ld, d, n, c, p, v.vec, km, &scount)
-                           : lloyd_continue(h, kSumL, RESPCA_F32, v.L, v.ld, d, n, c, p, v.vec, km, &scount);
+                           : lloyd_continue(h, kSumL, RESPCA_F32, v.L, v.ld, d, n, c, p, v.vec, km, &scount,
+                                            true);
             if (rs != RESPCA_OK) return rs;
             out.lloyd_passes += scount.passes - 1;
             out.assigned_columns += scount.assigned;

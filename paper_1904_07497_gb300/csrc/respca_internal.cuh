@@ -117,6 +117,9 @@ struct MuSplitOut {
     int arows = 0;
 };
 
+cudaError_t launch_sums_from_means(const float* mu, const int32_t* counts, int c, int64_t d, double* sums,
+                                   cudaStream_t st);
+
 // One Lloyd update in one launch: centroids from the FP64 sums (previous values
 // to mu_old), then exactly the statistics of launch_mu_stats, and the TF32
 // split when sp.hi is set.
