@@ -31,6 +31,8 @@ METRIC = "time to 1e-6 rel. err & per-iter HBM GB/s vs peak; BF16+learned vs pla
 FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_ELEM_FP32 = 28   # read X, S, Theta, L_prev; write L, S, Theta (4 B each)
 SEARCH_BYTES_PER_ELEM = 4  # the all-column search reads the FP32 operand L (or X) once
+BYTES_PER_ELEM_L21 = 44    # l2,1 iteration: pass A 20 B (reads X, S, Theta, L_prev; writes L), pass B 24 B
+FP32_LANES_PER_SM, SMS = 128, 152   # CUDA-core FP32 lanes per SM and SMs of a GB300
 
 WORKLOADS = {
     # name: (d, n, rank, sparsity, c)
@@ -47,10 +49,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4", "c5", "spectral"])
     ap.add_argument("--lanes", type=int, default=8, help="c4: concurrent lanes of the batched solve")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="1: BF16 storage of X and the state until err <= 1e-2, then FP32")
+    ap.add_argument("--s-norm", type=int, default=0, choices=[0, 1],
+                    help="1: the l2,1 norm on S (column shrinkage; two passes per iteration)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -76,7 +80,7 @@ def make_problem(name, seed):
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def cpu_sample(name, seed, steps=1, warmup=0):
+def cpu_sample(name, seed, steps=1, warmup=0, snorm=0):
     """Time the FP64 oracle on a bounded sample of the workload.
 
     Sample: one ALM iteration (L step, one K-means assignment pass, S and
@@ -95,7 +99,7 @@ def cpu_sample(name, seed, steps=1, warmup=0):
     Xs = np.asfortranarray(pr.X[:, :n_s].astype(np.float64))
     from paper_1904_07497_gb300 import synth
     small = synth.lowrank_sparse(min(d, 1000), min(n, 1000), r, sp, seed + 1)
-    _, st_small = oracle.solve(small.X.astype(np.float64), c, tol=1e-6, max_iter=500, seed=seed)
+    _, st_small = oracle.solve(small.X.astype(np.float64), c, tol=1e-6, max_iter=500, seed=seed, snorm=snorm)
     iters = st_small["iters"]
     lam = np.sqrt(max(d, n))
     labels = (np.arange(n_s) % c).astype(np.int32)
@@ -105,7 +109,7 @@ def cpu_sample(name, seed, steps=1, warmup=0):
         state = oracle.State(zero.copy(order="F"), zero.copy(order="F"), zero.copy(order="F"),
                              labels.copy(), 1e-4)
         t0 = time.perf_counter()
-        oracle.iteration(Xs, state, c, lam, km_max=1)
+        oracle.iteration(Xs, state, c, lam, km_max=1, snorm=snorm)
         dt = time.perf_counter() - t0
         if k >= warmup:
             times.append(dt)
@@ -239,7 +243,7 @@ def run_gpu(args, rank, world, local_rank):
     p = torch.empty(n, device=dev, dtype=torch.int32)
     stream = torch.cuda.current_stream(dev)
     solver = respca.Solver(seed=args.seed, timing=False, stream=stream, device=local_rank,
-                           precision=args.precision)
+                           precision=args.precision, s_norm=args.s_norm)
 
     def one(h=None):
         return respca.respca_solve(h or solver.h, X, c, L, S, p, tol=args.tol, max_iter=500)
@@ -273,19 +277,26 @@ def run_gpu(args, rank, world, local_rank):
     # per-kernel durations from one more solve with the library's event timing on
     # (kept out of the timed region: the events add host work)
     tsolver = respca.Solver(seed=args.seed, timing=True, stream=stream, device=local_rank,
-                            precision=args.precision)
+                            precision=args.precision, s_norm=args.s_norm)
     ts = one(tsolver.h)
     tsolver.close()
     peak, peak_kind = measured_peak()
     fused_avg = ts["ms_fused"] / max(1, ts["fused_launches"])
-    # bf16-phase launches move 14 B per element (X, L, S, Theta in BF16), FP32 ones 28 B
+    # bf16-phase launches move 14 B per element (X, L, S, Theta in BF16), FP32 ones 28 B;
+    # the l2,1 iteration's two passes 44 B (A: X, S, Theta, L_prev in, L out; B: X, L, S,
+    # Theta in, S, Theta out)
     nf, nb = max(1, ts["fused_launches"]), ts["bf16_iters"]
-    fused_bytes = int(d * n * (BYTES_PER_ELEM_FP32 * (nf - nb) + (BYTES_PER_ELEM_FP32 // 2) * nb) / nf)
+    if args.s_norm:
+        fused_bytes = d * n * BYTES_PER_ELEM_L21
+    else:
+        fused_bytes = int(d * n * (BYTES_PER_ELEM_FP32 * (nf - nb) + (BYTES_PER_ELEM_FP32 // 2) * nb) / nf)
     fused_gbs = fused_bytes / (fused_avg / 1e3) / 1e9
-    roof_fused = {"bound": "hbm", "kernel": "k_iteration (fused ALM iteration)",
+    roof_fused = {"bound": "hbm", "kernel": "k_l21_pass_a + k_l21_pass_b (l2,1 ALM iteration, two passes)"
+                  if args.s_norm else "k_iteration (fused ALM iteration)",
                   "achieved": round(fused_gbs, 1), "peak": peak, "unit": "GB/s",
                   "frac": round(fused_gbs / peak, 4), "peak_source": peak_kind,
-                  "traffic": kernel_traffic("k_iteration.cu", f"k_iteration_{args.workload}.txt"),
+                  "traffic": None if args.s_norm else
+                  kernel_traffic("k_iteration.cu", f"k_iteration_{args.workload}.txt"),
                   "algorithmic_bytes_per_launch": fused_bytes, "avg_launch_ms": round(fused_avg, 4),
                   "launches": ts["fused_launches"], "total_ms": round(ts["ms_fused"], 3)}
     rooflines = [roof_fused]
@@ -327,7 +338,7 @@ def run_gpu(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, times, sample = cpu_sample(args.workload, args.seed)
+        v, times, sample = cpu_sample(args.workload, args.seed, snorm=args.s_norm)
         cpu = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
 
     solver.close()
@@ -341,7 +352,7 @@ def run_gpu(args, rank, world, local_rank):
         "data": "synthetic (seeded numpy PCG64)",
         "config": dict(workload_config(args.workload, args.tol),
                        storage="bf16 phase (X, L, S, Theta in BF16) then FP32" if args.precision
-                       else "fp32"),
+                       else "fp32", s_norm="l2,1" if args.s_norm else "l1"),
         "iters": iters, "converged": last["converged"], "err": last["err"],
         "bf16_iters": last["bf16_iters"],
         "ms_init": round(last["ms_init"], 3),
@@ -429,6 +440,92 @@ def run_batched(args, rank, world, local_rank):
                      "peak_source": peak_kind, "traffic": None},
         "cpu_baseline": None, "e2e": None,
         "gpu_launches": sum(s["kernel_launches"] for s in st), "clocks": clk,
+    }
+
+
+SPEC_D, SPEC_N, SPEC_C, SPEC_SCALE = 256, 8192, 8, 0.05
+
+
+def spectral_problem(seed, n=SPEC_N):
+    """c Gaussian blobs (unit noise) around centres 10 N(0, 1) apart in d = 256."""
+    import numpy as np
+    g = np.random.Generator(np.random.PCG64(seed))
+    truth = g.integers(0, SPEC_C, size=n)
+    centres = 10.0 * g.standard_normal((SPEC_D, SPEC_C))
+    X = (centres[:, truth] + g.standard_normal((SPEC_D, n))).astype(np.float32)
+    return np.asfortranarray(X), truth
+
+
+def run_spectral(args, rank, world, local_rank):
+    """The spectral p step alone (Sec. 4.2's nonlinear alternative to
+    K-means): one step = the labels of 8192 columns (d = 256) in 8 groups."""
+    import numpy as np
+    import torch
+    from paper_1904_07497_gb300 import respca
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    Xn, truth = spectral_problem(replica_seed(args.seed, rank))
+    d, n = Xn.shape
+    X = torch.from_numpy(np.ascontiguousarray(Xn.T)).to(dev).T
+    solver = respca.Solver(seed=args.seed, stream=stream, device=local_rank, p_step=1,
+                           spectral_scale=SPEC_SCALE)
+    for _ in range(args.warmup):
+        respca.respca_spectral_labels(solver.h, X, SPEC_C)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos = []
+    for _ in range(args.steps):
+        p, info = respca.respca_spectral_labels(solver.h, X, SPEC_C)
+        infos.append(info)
+    torch.cuda.synchronize()
+    ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world, dev)
+    clk = clocks.stop()
+    solver.close()
+    pn = p.cpu().numpy()
+    m = {}
+    recovered = all(m.setdefault(a, b) == b for a, b in zip(pn.tolist(), truth.tolist())) and \
+        len(set(m.values())) == len(m)
+    info = infos[-1]
+    b = SPEC_C + 8
+    flops = 2.0 * n * n * d + 2.0 * n * n * b * info["matvecs"]   # Gram + products with M
+    mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = FP32_LANES_PER_SM * SMS * 2 * mhz * 1e6 / 1e12
+    ach = flops / (ms / 1e3) / 1e12
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        from oracle import spectral as osp
+        oracle.build()
+        n_s = 2048
+        t1 = time.perf_counter()
+        osp.labels(Xn[:, :n_s].astype(np.float64), SPEC_C, SPEC_SCALE, seed=args.seed)
+        dt = time.perf_counter() - t1
+        cpu = {"value": round(dt * 1e3 * (n / n_s) ** 3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"oracle spectral labels on {n_s} of the {n} columns ({dt:.1f} s, FP64, dense "
+                         f"eigh), scaled by (n/{n_s})^3, the eigensolver's cost"}
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded numpy PCG64)",
+        "config": {"workload": f"spectral p step alone: {SPEC_C} Gaussian blobs, d={d}, n={n}, "
+                               f"sigma^2 = {SPEC_SCALE} x mean squared distance; value = ms per p step",
+                   "l2": "the n x n affinity (256 MB) is larger than L2"},
+        "info": info, "labels_recover_blobs": bool(recovered),
+        "roofline": {"bound": "alu", "kernel": "k_gemm_tn products (Gram n^2 d and the eigensolver's M Y, "
+                     f"{info['matvecs']} products of n x n by n x {b}) over the whole p step",
+                     "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                     "frac": round(ach / peak, 4),
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock", "traffic": None},
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clk,
     }
 
 
@@ -542,6 +639,10 @@ def run_learned(args, rank, world, local_rank):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    if args.workload == "spectral":
+        return {"impl": "reference", "metric": METRIC,
+                "unavailable": "no separate oracle arm for the spectral p step; its GPU line carries the "
+                               "oracle's time on a sample (cpu_baseline)"}
     if args.workload == "c5":
         return {"impl": "reference", "metric": METRIC,
                 "unavailable": "no oracle arm for the learned warm start; its GPU line carries the "
@@ -582,6 +683,8 @@ def main():
             out = run_batched(args, rank, world, local_rank)
         elif args.workload == "c5":
             out = run_learned(args, rank, world, local_rank)
+        elif args.workload == "spectral":
+            out = run_spectral(args, rank, world, local_rank)
         else:
             out = run_gpu(args, rank, world, local_rank)
     if world > 1 and args.impl == "gpu":
