@@ -520,8 +520,8 @@ def run_spectral(args, rank, world, local_rank):
                                f"sigma^2 = {SPEC_SCALE} x mean squared distance; value = ms per p step",
                    "l2": "the n x n affinity (256 MB) is larger than L2"},
         "info": info, "labels_recover_blobs": bool(recovered),
-        "roofline": {"bound": "alu", "kernel": "k_gemm_tn products (Gram n^2 d and the eigensolver's M Y, "
-                     f"{info['matvecs']} products of n x n by n x {b}) over the whole p step",
+        "roofline": {"bound": "alu", "kernel": "k_gemm_tn (Gram, 2 n^2 d) and k_spec_symm (the eigensolver's "
+                     f"{info['matvecs']} products M Y, n x n by n x {b}) over the whole p step",
                      "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
                      "frac": round(ach / peak, 4),
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock", "traffic": None},

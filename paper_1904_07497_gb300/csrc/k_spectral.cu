@@ -163,17 +163,20 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// M_ij = A_ij / sqrt(deg_i deg_j) (isolated points keep a zero row).
+// r_j = deg_j^{-1/2} (FP64, rounded once; isolated points get 0).
+__global__ void k_spec_rinv(const double* __restrict__ deg, int64_t n, float* __restrict__ r) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double dj = deg[j];
+    r[j] = dj > 0.0 ? (float)(1.0 / sqrt(dj)) : 0.f;
+}
+
+// M_ij = A_ij r_i r_j.
 __global__ void __launch_bounds__(kThreads)
-    k_spec_normalise(float* __restrict__ A, int64_t n, const double* __restrict__ deg) {
+    k_spec_normalise(float* __restrict__ A, int64_t n, const float* __restrict__ r) {
     const int64_t i = blockIdx.x;
-    const double di = deg[i];
-    const double ri = di > 0.0 ? 1.0 / sqrt(di) : 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += kThreads) {
-        const double dj = deg[j];
-        const double rj = dj > 0.0 ? 1.0 / sqrt(dj) : 0.0;
-        A[i * n + j] = (float)((double)A[i * n + j] * ri * rj);
-    }
+    const float ri = r[i];
+    for (int64_t j = threadIdx.x; j < n; j += kThreads) A[i * n + j] = A[i * n + j] * ri * r[j];
 }
 
 // splitmix64 (Steele, Lea, Flood 2014) of a counter: the start block.
@@ -201,83 +204,113 @@ __global__ void k_spec_axpby(float* __restrict__ out, const float* __restrict__ 
     out[e] = v;
 }
 
-// Classical Gram-Schmidt twice ("twice is enough"), one CTA, columns of Y (n x b,
-// leading dimension n) in order; a column that projection annihilates is
-// replaced by a fresh counter-based vector.  FP32 data, FP64 dot products.
-constexpr int kCgsThreads = 1024;
-constexpr int kCgsChunk = 8;
-
-__device__ double cgs_block_sum(double v, double* red) {
-    v = warp_sum(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < kCgsThreads / 32; ++w) t += red[w];
-    return t;
-}
-
-__global__ void __launch_bounds__(kCgsThreads)
-    k_spec_cgs2(float* __restrict__ Y, int64_t n, int b, uint64_t seed) {
-    __shared__ double red[kCgsThreads / 32];
-    __shared__ double redc[kCgsThreads / 32][kCgsChunk];
-    __shared__ double h[128];
-    for (int j = 0; j < b; ++j) {
-        float* yj = Y + (int64_t)j * n;
-        for (int attempt = 0; attempt < 4; ++attempt) {
-            double n0 = 0.0;
-            for (int64_t r = threadIdx.x; r < n; r += kCgsThreads) n0 += (double)yj[r] * yj[r];
-            n0 = cgs_block_sum(n0, red);
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int k0 = 0; k0 < j; k0 += kCgsChunk) {
-                    double acc[kCgsChunk];
+// W = M Y for the symmetric n x n matrix M and the n x b block Y (both
+// column-major): one warp per row i of M (contiguous, = column i), lanes over
+// k, the block's rows of Y staged in shared memory 128 at a time; M is read
+// once.  BMAX >= b accumulators per lane, reduced across the warp at the end.
+constexpr int kSymRows = 16;        // rows of M (warps) per CTA
+constexpr int kSymK = 128;          // rows of Y per shared-memory stage
+template <int BMAX>
+__global__ void __launch_bounds__(kSymRows * 32)
+    k_spec_symm(const float* __restrict__ M, int64_t n, const float* __restrict__ Y, int b,
+                float* __restrict__ W) {
+    __shared__ float ys[kSymK][BMAX + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kSymRows + warp;
+    const float* mrow = M + (i < n ? i : 0) * n;
+    float acc[BMAX];
 #pragma unroll
-                    for (int q = 0; q < kCgsChunk; ++q) acc[q] = 0.0;
-                    for (int64_t r = threadIdx.x; r < n; r += kCgsThreads) {
-                        const double v = yj[r];
+    for (int q = 0; q < BMAX; ++q) acc[q] = 0.f;
+    for (int64_t k0 = 0; k0 < n; k0 += kSymK) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kSymK * BMAX; e += kSymRows * 32) {
+            const int kk = e % kSymK, q = e / kSymK;
+            ys[kk][q] = (q < b && k0 + kk < n) ? Y[k0 + kk + (int64_t)q * n] : 0.f;
+        }
+        __syncthreads();
 #pragma unroll
-                        for (int q = 0; q < kCgsChunk; ++q)
-                            if (k0 + q < j) acc[q] += (double)Y[(int64_t)(k0 + q) * n + r] * v;
-                    }
+        for (int t = 0; t < kSymK / 32; ++t) {
+            const int kk = t * 32 + lane;
+            const float m = (k0 + kk < n) ? mrow[k0 + kk] : 0.f;
 #pragma unroll
-                    for (int q = 0; q < kCgsChunk; ++q) acc[q] = warp_sum(acc[q]);
-                    __syncthreads();
-                    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-                        for (int q = 0; q < kCgsChunk; ++q) redc[threadIdx.x >> 5][q] = acc[q];
-                    __syncthreads();
-                    if (threadIdx.x < kCgsChunk && k0 + threadIdx.x < j) {
-                        double t = 0.0;
-                        for (int w = 0; w < kCgsThreads / 32; ++w) t += redc[w][threadIdx.x];
-                        h[k0 + threadIdx.x] = t;
-                    }
-                }
-                __syncthreads();
-                for (int64_t r = threadIdx.x; r < n; r += kCgsThreads) {
-                    double v = yj[r];
-                    for (int k = 0; k < j; ++k) v -= h[k] * (double)Y[(int64_t)k * n + r];
-                    yj[r] = (float)v;
-                }
-                __syncthreads();
-            }
-            double n1 = 0.0;
-            for (int64_t r = threadIdx.x; r < n; r += kCgsThreads) n1 += (double)yj[r] * yj[r];
-            n1 = cgs_block_sum(n1, red);
-            if (n1 > 1e-8 * n0 && n1 > 0.0) {
-                const float inv = (float)(1.0 / sqrt(n1));
-                for (int64_t r = threadIdx.x; r < n; r += kCgsThreads) yj[r] *= inv;
-                __syncthreads();
-                break;
-            }
-            // the column lay (numerically) in the span of the earlier ones: redraw it
-            for (int64_t r = threadIdx.x; r < n; r += kCgsThreads) {
-                const uint64_t u = spec_mix((seed + 0x51ED270B27F3A1D5ULL * (uint64_t)(attempt + 1)) ^
-                                            ((uint64_t)j * (uint64_t)n + (uint64_t)r));
-                yj[r] = (float)((double)(u >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
-            }
-            __syncthreads();
+            for (int q = 0; q < BMAX; ++q) acc[q] = fmaf(m, ys[kk][q], acc[q]);
         }
     }
+#pragma unroll
+    for (int q = 0; q < BMAX; ++q) {
+        const float v = warp_sum(acc[q]);
+        if (lane == 0 && i < n && q < b) W[i + (int64_t)q * n] = v;
+    }
+}
+
+// out[i + j b1] = sum_k A[k + i n] B[k + j n] in FP64 (one CTA per entry):
+// the b1 x b2 Gram or Rayleigh-quotient matrices of n-row blocks.
+__global__ void __launch_bounds__(kThreads)
+    k_spec_gram_small(const float* __restrict__ A, const float* __restrict__ B, int64_t n, int b1,
+                      double* __restrict__ out) {
+    __shared__ double red[kThreads / 32];
+    const int i = blockIdx.x, j = blockIdx.y;
+    const float* a = A + (int64_t)i * n;
+    const float* bb = B + (int64_t)j * n;
+    double acc = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += kThreads) acc += (double)a[k] * (double)bb[k];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        out[i + (int64_t)j * b1] = t;
+    }
+}
+
+// One step of Cholesky QR: G = Y^T Y (b x b, FP64) plus a shift of 1e-12
+// times its largest diagonal entry (so that rounding cannot break the
+// factorisation of a numerically rank-deficient block), G = R^T R, and
+// Q = R^{-1} (upper triangular, column-major FP32) for Y <- Y Q.  One CTA.
+constexpr int kCholThreads = 256;
+__global__ void __launch_bounds__(kCholThreads)
+    k_spec_chol_inv(const double* __restrict__ G, int b, float* __restrict__ Q) {
+    extern __shared__ double cm[];
+    double* R = cm;             // b x b, column-major, upper triangle used
+    double* V = cm + b * b;     // R^{-1}
+    __shared__ double shift;
+    for (int e = threadIdx.x; e < b * b; e += kCholThreads) {
+        R[e] = G[e];
+        V[e] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int q = 0; q < b; ++q) mx = fmax(mx, R[q + q * b]);
+        shift = 1e-12 * mx + 1e-300;
+    }
+    __syncthreads();
+    // right-looking Cholesky on the upper triangle: R[k][j] for j >= k
+    for (int k = 0; k < b; ++k) {
+        __syncthreads();
+        const double piv = sqrt(fmax(R[k + k * b] + shift, 1e-300));
+        __syncthreads();
+        for (int j = k + threadIdx.x; j < b; j += kCholThreads) R[k + j * b] = (j == k) ? piv : R[k + j * b] / piv;
+        __syncthreads();
+        // trailing update: R[i][j] -= R[k][i] R[k][j], k < i <= j
+        for (int e = threadIdx.x; e < b * b; e += kCholThreads) {
+            const int ii = e % b, jj = e / b;
+            if (ii > k && jj >= ii) R[ii + jj * b] -= R[k + ii * b] * R[k + jj * b];
+        }
+    }
+    __syncthreads();
+    // V = R^{-1}, column by column: V[j][j] = 1/R[j][j], V[i][j] = -(sum_{k=i+1..j} R[i][k] V[k][j]) / R[i][i]
+    for (int j = threadIdx.x; j < b; j += kCholThreads) {
+        V[j + j * b] = 1.0 / R[j + j * b];
+        for (int i = j - 1; i >= 0; --i) {
+            double sacc = 0.0;
+            for (int k = i + 1; k <= j; ++k) sacc += R[i + k * b] * V[k + j * b];
+            V[i + j * b] = -sacc / R[i + i * b];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += kCholThreads) Q[e] = (float)V[e];
 }
 
 // Symmetric eigen-decomposition of H (b x b, FP32 in, symmetrised in FP64) by
@@ -287,7 +320,7 @@ __global__ void __launch_bounds__(kCgsThreads)
 constexpr int kJacThreads = 256;
 
 __global__ void __launch_bounds__(kJacThreads)
-    k_spec_jacobi(const float* __restrict__ H, int b, float* __restrict__ Q, double* __restrict__ evals,
+    k_spec_jacobi(const double* __restrict__ H, int b, float* __restrict__ Q, double* __restrict__ evals,
                   int max_sweeps) {
     extern __shared__ double sm[];
     const int bp = b + (b & 1);          // padded to even (a zero row and column)
@@ -300,7 +333,7 @@ __global__ void __launch_bounds__(kJacThreads)
     for (int e = threadIdx.x; e < bp * bp; e += kJacThreads) {
         const int i = e % bp, j = e / bp;
         double x = 0.0;
-        if (i < b && j < b) x = 0.5 * ((double)H[i + j * b] + (double)H[j + i * b]);
+        if (i < b && j < b) x = 0.5 * (H[i + j * b] + H[j + i * b]);
         a[e] = x;
         v[e] = (i == j) ? 1.0 : 0.0;
     }
@@ -450,15 +483,16 @@ cudaError_t launch_spec_gemm_tn(const float* A, int64_t lda, const float* B, int
 
 cudaError_t launch_spec_affinity(const float* Y, int64_t ldy, int64_t d, int64_t n, double scale, float* G,
                                  float* sqn, double* part, int parts, double* gsum, double* sig, double* deg,
-                                 cudaStream_t st) {
-    count_launches(6);
+                                 float* rinv, cudaStream_t st) {
+    count_launches(7);
     k_spec_norms<<<parts, kThreads, 0, st>>>(Y, ldy, d, n, sqn, part);
     const dim3 grid(blocks_for(n, kGT), blocks_for(n, kGT));
     k_gemm_tn<<<grid, kGThreads, 0, st>>>(Y, ldy, Y, ldy, G, n, n, n, d, 1.f);
     k_spec_gsum<<<(unsigned)n, kThreads, 0, st>>>(G, n, gsum);
     k_spec_sigma<<<1, kThreads, 0, st>>>(part, parts, gsum, n, scale, sig);
     k_spec_affinity<<<(unsigned)n, kThreads, 0, st>>>(G, n, sqn, sig, deg);
-    k_spec_normalise<<<(unsigned)n, kThreads, 0, st>>>(G, n, deg);
+    k_spec_rinv<<<blocks_for(n, kThreads), kThreads, 0, st>>>(deg, n, rinv);
+    k_spec_normalise<<<(unsigned)n, kThreads, 0, st>>>(G, n, rinv);
     return cudaGetLastError();
 }
 
@@ -475,9 +509,38 @@ cudaError_t launch_spec_axpby(float* out, const float* T, const float* Y, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_spec_cgs2(float* Y, int64_t n, int b, uint64_t seed, cudaStream_t st) {
+cudaError_t launch_spec_symm(const float* M, int64_t n, const float* Y, int b, float* W, cudaStream_t st) {
     count_launches(1);
-    k_spec_cgs2<<<1, kCgsThreads, 0, st>>>(Y, n, b, seed);
+    const unsigned grid = blocks_for(n, kSymRows);
+    if (b <= 16) k_spec_symm<16><<<grid, kSymRows * 32, 0, st>>>(M, n, Y, b, W);
+    else if (b <= 32) k_spec_symm<32><<<grid, kSymRows * 32, 0, st>>>(M, n, Y, b, W);
+    else if (b <= 48) k_spec_symm<48><<<grid, kSymRows * 32, 0, st>>>(M, n, Y, b, W);
+    else k_spec_symm<72><<<grid, kSymRows * 32, 0, st>>>(M, n, Y, b, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_gram_small(const float* A, const float* B, int64_t n, int b1, int b2, double* out,
+                                   cudaStream_t st) {
+    count_launches(1);
+    k_spec_gram_small<<<dim3(b1, b2), kThreads, 0, st>>>(A, B, n, b1, out);
+    return cudaGetLastError();
+}
+
+// Y <- Y R^{-1} twice (Cholesky QR2): Y becomes orthonormal with the span of
+// its leading columns kept.  T is n x b scratch.
+cudaError_t launch_spec_cholqr2(float* Y, float* T, int64_t n, int b, double* G, float* Q, cudaStream_t st) {
+    for (int pass = 0; pass < 2; ++pass) {
+        cudaError_t e = launch_spec_gram_small(Y, Y, n, b, b, G, st);
+        if (e != cudaSuccess) return e;
+        count_launches(1);
+        e = allow_max_dynamic_smem((const void*)k_spec_chol_inv);
+        if (e != cudaSuccess) return e;
+        k_spec_chol_inv<<<1, kCholThreads, sizeof(double) * 2 * b * b, st>>>(G, b, Q);
+        e = launch_spec_rotate(Y, Q, T, n, b, st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(Y, T, sizeof(float) * (size_t)n * b, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
@@ -486,7 +549,7 @@ size_t spec_jacobi_smem(int b) {
     return sizeof(double) * (2 * (size_t)bp * bp + bp) + sizeof(int) * bp;
 }
 
-cudaError_t launch_spec_jacobi(const float* H, int b, float* Q, double* evals, cudaStream_t st) {
+cudaError_t launch_spec_jacobi(const double* H, int b, float* Q, double* evals, cudaStream_t st) {
     count_launches(1);
     const size_t smem = spec_jacobi_smem(b);
     cudaError_t e = allow_max_dynamic_smem((const void*)k_spec_jacobi);

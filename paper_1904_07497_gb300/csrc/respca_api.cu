@@ -256,7 +256,7 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
     CK(ensure(h->sp_sig, sizeof(double) * 2));
     CK(ensure(h->sp_deg, sizeof(double) * n));
     for (DevBuf* bb : {&h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z}) CK(ensure(*bb, sizeof(float) * (size_t)n * b));
-    CK(ensure(h->sp_H, sizeof(float) * b * b));
+    CK(ensure(h->sp_H, sizeof(double) * b * b));
     CK(ensure(h->sp_Q, sizeof(float) * b * b));
     CK(ensure(h->sp_ev, sizeof(double) * b));
     CK(ensure(h->sp_res, sizeof(double) * c));
@@ -272,14 +272,15 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
     }
     float* M = P<float>(h->sp_M);
     CK(launch_spec_affinity(Y, ldy, d, n, h->cfg.spectral_scale, M, P<float>(h->sp_sqn), P<double>(h->sp_part),
-                            parts, P<double>(h->sp_gsum), P<double>(h->sp_sig), P<double>(h->sp_deg), st));
+                            parts, P<double>(h->sp_gsum), P<double>(h->sp_sig), P<double>(h->sp_deg),
+                            P<float>(h->sp_sqn), st));
     float* Yb = P<float>(h->sp_Y);   // current orthonormal block (n x b)
     float* W = P<float>(h->sp_W);    // M Yb
     float* T = P<float>(h->sp_T);    // scratch
     float* Z = P<float>(h->sp_Z);    // scratch
     const int64_t nb = n * (int64_t)b;
     CK(launch_spec_start(Yb, n, b, h->cfg.seed, st));
-    CK(launch_spec_cgs2(Yb, n, b, h->cfg.seed, st));
+    CK(launch_spec_cholqr2(Yb, T, n, b, P<double>(h->sp_H), P<float>(h->sp_Q), st));
     std::vector<double> ev(b), res(c);
     double sig2 = 0.0;
     int outer = 0, matvecs = 0;
@@ -287,10 +288,10 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
     double lo = -1.0;   // the spectrum of M lies in [-1, 1]
     for (;;) {
         // Rayleigh-Ritz on span(Yb): H = Yb^T M Yb, rotate to the Ritz vectors
-        CK(launch_spec_gemm_tn(M, n, Yb, n, W, n, n, b, n, 1.f, st));
+        CK(launch_spec_symm(M, n, Yb, b, W, st));
         ++matvecs;
-        CK(launch_spec_gemm_tn(Yb, n, W, n, P<float>(h->sp_H), b, b, b, n, 1.f, st));
-        CK(launch_spec_jacobi(P<float>(h->sp_H), b, P<float>(h->sp_Q), P<double>(h->sp_ev), st));
+        CK(launch_spec_gram_small(Yb, W, n, b, b, P<double>(h->sp_H), st));
+        CK(launch_spec_jacobi(P<double>(h->sp_H), b, P<float>(h->sp_Q), P<double>(h->sp_ev), st));
         CK(launch_spec_rotate(Yb, P<float>(h->sp_Q), T, n, b, st));
         CK(launch_spec_rotate(W, P<float>(h->sp_Q), Z, n, b, st));
         std::swap(Yb, T);
@@ -314,7 +315,7 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
         float* y2 = Z;
         CK(launch_spec_axpby(y1, W, y0, nullptr, nb, (float)(1.0 / e), (float)(-cen / e), 0.f, st));
         for (int k = 2; k <= kSpecDegree; ++k) {
-            CK(launch_spec_gemm_tn(M, n, y1, n, W, n, n, b, n, 1.f, st));   // W as scratch: M y1
+            CK(launch_spec_symm(M, n, y1, b, W, st));   // W as scratch: M y1
             ++matvecs;
             CK(launch_spec_axpby(y2, W, y1, y0, nb, (float)(2.0 / e), (float)(-2.0 * cen / e), -1.f, st));
             float* t = y0;
@@ -323,7 +324,7 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
             y2 = t;
         }
         // the filtered block y1 becomes the new (orthonormalised) search block
-        CK(launch_spec_cgs2(y1, n, b, h->cfg.seed + (uint64_t)outer, st));
+        CK(launch_spec_cholqr2(y1, y2, n, b, P<double>(h->sp_H), P<float>(h->sp_Q), st));
         if (y1 != Yb) {
             // keep the buffer roles fixed: Yb holds the block, T and Z are scratch
             CK(cudaMemcpyAsync(Yb, y1, sizeof(float) * nb, cudaMemcpyDeviceToDevice, st));

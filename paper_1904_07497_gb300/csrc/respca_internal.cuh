@@ -399,13 +399,16 @@ cudaError_t launch_spec_gemm_tn(const float* A, int64_t lda, const float* B, int
                                 int64_t m, int64_t n, int64_t K, float alpha, cudaStream_t st);
 cudaError_t launch_spec_affinity(const float* Y, int64_t ldy, int64_t d, int64_t n, double scale, float* G,
                                  float* sqn, double* part, int parts, double* gsum, double* sig, double* deg,
-                                 cudaStream_t st);
+                                 float* rinv, cudaStream_t st);
 cudaError_t launch_spec_start(float* Y, int64_t n, int b, uint64_t seed, cudaStream_t st);
 cudaError_t launch_spec_axpby(float* out, const float* T, const float* Y, const float* Yp, int64_t count,
                               float alpha, float beta, float gamma, cudaStream_t st);
-cudaError_t launch_spec_cgs2(float* Y, int64_t n, int b, uint64_t seed, cudaStream_t st);
+cudaError_t launch_spec_symm(const float* M, int64_t n, const float* Y, int b, float* W, cudaStream_t st);
+cudaError_t launch_spec_gram_small(const float* A, const float* B, int64_t n, int b1, int b2, double* out,
+                                   cudaStream_t st);
+cudaError_t launch_spec_cholqr2(float* Y, float* T, int64_t n, int b, double* G, float* Q, cudaStream_t st);
 size_t spec_jacobi_smem(int b);
-cudaError_t launch_spec_jacobi(const float* H, int b, float* Q, double* evals, cudaStream_t st);
+cudaError_t launch_spec_jacobi(const double* H, int b, float* Q, double* evals, cudaStream_t st);
 cudaError_t launch_spec_rotate(const float* Y, const float* Q, float* out, int64_t n, int b, cudaStream_t st);
 cudaError_t launch_spec_residual(const float* W, const float* Y, const double* evals, int64_t n, int c,
                                  double* res, cudaStream_t st);
