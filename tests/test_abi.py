@@ -61,9 +61,10 @@ def test_binding_struct_sizes_match_header(lib):
     import tempfile
     from paper_1904_07497_gb300 import respca
     src = ('#include "respca.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-           'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(respca_config),'
+           'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(respca_config),'
            ' sizeof(respca_stats), sizeof(respca_warm), sizeof(respca_problem),'
-           ' offsetof(respca_stats, ms_total), offsetof(respca_problem, p));return 0;}\n')
+           ' offsetof(respca_stats, ms_total), offsetof(respca_problem, p),'
+           ' sizeof(respca_spectral_info), offsetof(respca_config, spectral_scale));return 0;}\n')
     with tempfile.TemporaryDirectory() as td:
         c = os.path.join(td, "probe.c")
         exe = os.path.join(td, "probe")
@@ -72,7 +73,8 @@ def test_binding_struct_sizes_match_header(lib):
         got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(respca.respca_config), ctypes.sizeof(respca.respca_stats),
             ctypes.sizeof(respca.respca_warm), ctypes.sizeof(respca.respca_problem),
-            respca.respca_stats.ms_total.offset, respca.respca_problem.p.offset]
+            respca.respca_stats.ms_total.offset, respca.respca_problem.p.offset,
+            ctypes.sizeof(respca.respca_spectral_info), respca.respca_config.spectral_scale.offset]
     assert got == want
 
 
@@ -82,3 +84,36 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(respca, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="not built"):
         respca.load()
+
+
+def test_config_validation_needs_no_gpu(lib):
+    """respca_create rejects inconsistent settings before touching a device."""
+    from paper_1904_07497_gb300 import respca
+    l = respca.load()
+    h = ctypes.c_void_p()
+    for field, value in (("p_step", 2), ("precision", 3), ("s_norm", 5), ("stop_after_ramp", 7)):
+        cfg = respca.respca_config_default()
+        setattr(cfg, field, value)
+        assert l.respca_create(ctypes.byref(h), ctypes.byref(cfg)) == respca.RESPCA_ERR_INVALID_ARG, field
+    cfg = respca.respca_config_default()
+    cfg.p_step, cfg.precision = 1, 1          # the spectral p step runs in FP32 only
+    assert l.respca_create(ctypes.byref(h), ctypes.byref(cfg)) == respca.RESPCA_ERR_INVALID_ARG
+    cfg = respca.respca_config_default()
+    cfg.p_step, cfg.spectral_scale = 1, 0.0
+    assert l.respca_create(ctypes.byref(h), ctypes.byref(cfg)) == respca.RESPCA_ERR_INVALID_ARG
+
+
+def test_net_schedule_matches_oracle(lib):
+    """respca_net_schedule is host arithmetic: rho_k = rho kappa^k e^theta_k,
+    tau_k = e^phi_k / rho_k, checked against the FP64 network oracle."""
+    import numpy as np
+    from oracle import warmnet
+    from paper_1904_07497_gb300 import respca
+    g = np.random.default_rng(4)
+    m = g.uniform(-1.0, 1.0, 16).astype(np.float32)
+    r, t = respca.respca_net_schedule(0.37, 1.5, m.tolist())
+    r_ref, t_ref = warmnet.schedule(0.37, 1.5, m[:8].astype(np.float64), m[8:].astype(np.float64))
+    np.testing.assert_allclose(r, r_ref, rtol=1e-14)
+    np.testing.assert_allclose(t, t_ref, rtol=1e-14)
+    with pytest.raises(respca.RespcaError):
+        respca.respca_net_schedule(-1.0, 1.5, m.tolist())
