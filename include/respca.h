@@ -340,7 +340,8 @@ respca_status respca_net_schedule(double rho, double kappa, int32_t layers, cons
  *   S0, Theta0 d x n device FP32 input state, leading dimension lds >= d (copied).
  *   rho_k, tau_k  host arrays of `layers` positive values.
  *   L, S, Theta   d x n device FP32 outputs of the last layer (leading dimension
- *              lds; may be NULL).  The call is asynchronous on the stream.
+ *              lds; may be NULL).  The call waits once for the label check (after the
+ *              label sort); the layers themselves are queued on the stream.
  * The context keeps the pointer X (not a copy): X must stay allocated and
  * unchanged until the matching respca_net_backward returns.
  * Errors: RESPCA_ERR_INVALID_ARG (null or inconsistent sizes, non-positive
