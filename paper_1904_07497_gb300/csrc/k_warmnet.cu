@@ -23,7 +23,34 @@ namespace {
 
 constexpr int kNetRows = 512;   // rows per CTA (one chunk), as the fused iteration
 
+// Row mapping of a CTA's 512-row chunk: with VEC (d, the leading dimensions
+// and the bases 16-byte aligned) each lane takes 4 slots of 4 consecutive rows
+// through 16-byte accesses, otherwise 16 slots of one row; the arithmetic per
+// element is the same either way.
+template <bool VEC>
+struct NetRows {
+    static constexpr int kSlots = VEC ? 4 : 16;
+    static constexpr int kW = VEC ? 4 : 1;
+    static __device__ __forceinline__ int row(int q, int lane) { return VEC ? (q * 32 + lane) * 4 : q * 32 + lane; }
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        if (VEC) {
+            const float4 t = *reinterpret_cast<const float4*>(p);
+            v[0] = t.x;
+            v[1] = t.y;
+            v[2] = t.z;
+            v[3] = t.w;
+        } else {
+            v[0] = *p;
+        }
+    }
+    static __device__ __forceinline__ void st(float* p, const float* v) {
+        if (VEC) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        else *p = v[0];
+    }
+};
+
 // ---------------------------------------------------------------- forward
+template <bool VEC>
 __global__ void __launch_bounds__(kThreads)
     k_net_layer(const float* __restrict__ X, int64_t ldx, const float* __restrict__ S,
                 const float* __restrict__ Th, float* __restrict__ L, float* __restrict__ Sn,
@@ -31,6 +58,8 @@ __global__ void __launch_bounds__(kThreads)
                 const int32_t* __restrict__ perm, const TileDesc* __restrict__ tiles,
                 const DevStatus* __restrict__ status, int64_t d, NetScalars sc,
                 float* __restrict__ Dpart) {
+    using RM = NetRows<VEC>;
+    constexpr int W = RM::kW;
     __shared__ float red[kThreads / 32][kNetRows];
     const int tile_idx = blockIdx.x;
     if (tile_idx >= status->ntiles) return;
@@ -44,25 +73,33 @@ __global__ void __launch_bounds__(kThreads)
     for (int k = warp; k < td.len; k += kThreads / 32) {
         const int64_t col = perm[td.start + k];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int64_t r = r0 + q * 32 + lane;
+        for (int q = 0; q < RM::kSlots; ++q) {
+            const int64_t r = r0 + RM::row(q, lane);
             if (r >= d) continue;
-            const float x = X[col * ldx + r];
-            const float s = S[col * lds + r], t = Th[col * lds + r];
-            const float dv = (x - s) + t * sc.inv_rho;
-            const float l = fmaf(sc.a, dv, sc.b * mup[r]);
-            const float bb = (x - l) + t * sc.inv_rho;
-            const float mag = fabsf(bb) - sc.tau;
-            const float sn = mag > 0.f ? copysignf(mag, bb) : 0.f;
-            const float tn = t + sc.rho * ((x - l) - sn);
-            L[col * lds + r] = l;
-            Sn[col * lds + r] = sn;
-            Thn[col * lds + r] = tn;
-            acc[q] += (x - sn) + tn * sc.inv_rho_next;   // D of the next layer
+            float x[W], s[W], t[W], m[W], l[W], sn[W], tn[W];
+            RM::ld(X + col * ldx + r, x);
+            RM::ld(S + col * lds + r, s);
+            RM::ld(Th + col * lds + r, t);
+            RM::ld(mup + r, m);
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const float dv = (x[e] - s[e]) + t[e] * sc.inv_rho;
+                l[e] = fmaf(sc.a, dv, sc.b * m[e]);
+                const float bb = (x[e] - l[e]) + t[e] * sc.inv_rho;
+                const float mag = fabsf(bb) - sc.tau;
+                sn[e] = mag > 0.f ? copysignf(mag, bb) : 0.f;
+                tn[e] = t[e] + sc.rho * ((x[e] - l[e]) - sn[e]);
+                acc[q * W + e] += (x[e] - sn[e]) + tn[e] * sc.inv_rho_next;   // D of the next layer
+            }
+            RM::st(L + col * lds + r, l);
+            RM::st(Sn + col * lds + r, sn);
+            RM::st(Thn + col * lds + r, tn);
         }
     }
 #pragma unroll
-    for (int q = 0; q < 16; ++q) red[warp][q * 32 + lane] = acc[q];
+    for (int q = 0; q < RM::kSlots; ++q)
+#pragma unroll
+        for (int e = 0; e < W; ++e) red[warp][RM::row(q, lane) + e] = acc[q * W + e];
     __syncthreads();
     for (int i = threadIdx.x; i < kNetRows; i += kThreads) {
         const int64_t r = r0 + i;
@@ -79,7 +116,7 @@ __global__ void __launch_bounds__(kThreads)
 // 2: ga, 3: sum (gB + gD) Theta (pass 2 adds its gD part).
 constexpr int kNetScal = 4;
 
-template <int PASS>
+template <int PASS, bool VEC>
 __global__ void __launch_bounds__(kThreads)
     k_net_back(const float* __restrict__ X, int64_t ldx, const float* __restrict__ S,
                const float* __restrict__ Th, int64_t lds, const float* __restrict__ mu,
@@ -88,6 +125,8 @@ __global__ void __launch_bounds__(kThreads)
                NetScalars sc, const float* __restrict__ gLext, float* __restrict__ gS,
                float* __restrict__ gT, const float* __restrict__ gmean, float* __restrict__ Gpart,
                double* __restrict__ scal_part) {
+    using RM = NetRows<VEC>;
+    constexpr int W = RM::kW;
     __shared__ float red[kThreads / 32][kNetRows];
     __shared__ double sred[kThreads / 32][kNetScal];
     const int tile_idx = blockIdx.x;
@@ -108,39 +147,56 @@ __global__ void __launch_bounds__(kThreads)
     for (int k = warp; k < td.len; k += kThreads / 32) {
         const int64_t col = perm[td.start + k];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int64_t r = r0 + q * 32 + lane;
+        for (int q = 0; q < RM::kSlots; ++q) {
+            const int64_t r = r0 + RM::row(q, lane);
             if (r >= d) continue;
-            const int64_t e = col * lds + r;
-            const float x = X[col * ldx + r];
-            const float s = S[e], t = Th[e];
-            const float m = mup[r];
-            const float dv = (x - s) + t * sc.inv_rho;
-            const float l = fmaf(sc.a, dv, sc.b * m);
-            const float bb = (x - l) + t * sc.inv_rho;
-            const bool on = fabsf(bb) > sc.tau;
-            const float sn = on ? copysignf(fabsf(bb) - sc.tau, bb) : 0.f;
-            const float gso = gS[e], gto = gT[e];
-            const float gsc = gso - sc.rho * gto;
-            const float gb = on ? gsc : 0.f;
-            const float gl = (gLext ? gLext[e] : 0.f) - sc.rho * gto - gb;
-            if (PASS == 1) {
-                s_tr = fmaf(gto, (x - l) - sn, s_tr);
-                if (on) s_tau -= gsc * (bb > 0.f ? 1.f : -1.f);
-                s_a = fmaf(gl, dv - m, s_a);
-                s_rt = fmaf(gb, t, s_rt);
-                acc[q] += gl;
-            } else {
-                const float gd = fmaf(sc.a, gl, sc.b * gmp[r]);
-                s_rt = fmaf(gd, t, s_rt);
-                gS[e] = -gd;
-                gT[e] = gto + (gb + gd) * sc.inv_rho;
+            const int64_t e0 = col * lds + r;
+            float x[W], s[W], t[W], m[W], gso[W], gto[W], gle[W], gm[W];
+            RM::ld(X + col * ldx + r, x);
+            RM::ld(S + e0, s);
+            RM::ld(Th + e0, t);
+            RM::ld(mup + r, m);
+            RM::ld(gS + e0, gso);
+            RM::ld(gT + e0, gto);
+            if (gLext) RM::ld(gLext + e0, gle);
+            else
+#pragma unroll
+                for (int e = 0; e < W; ++e) gle[e] = 0.f;
+            if (PASS == 2) RM::ld(gmp + r, gm);
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const float dv = (x[e] - s[e]) + t[e] * sc.inv_rho;
+                const float l = fmaf(sc.a, dv, sc.b * m[e]);
+                const float bb = (x[e] - l) + t[e] * sc.inv_rho;
+                const bool on = fabsf(bb) > sc.tau;
+                const float sn = on ? copysignf(fabsf(bb) - sc.tau, bb) : 0.f;
+                const float gsc = gso[e] - sc.rho * gto[e];
+                const float gb = on ? gsc : 0.f;
+                const float gl = gle[e] - sc.rho * gto[e] - gb;
+                if (PASS == 1) {
+                    s_tr = fmaf(gto[e], (x[e] - l) - sn, s_tr);
+                    if (on) s_tau -= gsc * (bb > 0.f ? 1.f : -1.f);
+                    s_a = fmaf(gl, dv - m[e], s_a);
+                    s_rt = fmaf(gb, t[e], s_rt);
+                    acc[q * W + e] += gl;
+                } else {
+                    const float gd = fmaf(sc.a, gl, sc.b * gm[e]);
+                    s_rt = fmaf(gd, t[e], s_rt);
+                    gso[e] = -gd;                                   // becomes dloss/dS of the layer input
+                    gto[e] = gto[e] + (gb + gd) * sc.inv_rho;       // and dloss/dTheta
+                }
+            }
+            if (PASS == 2) {
+                RM::st(gS + e0, gso);
+                RM::st(gT + e0, gto);
             }
         }
     }
     if (PASS == 1) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) red[warp][q * 32 + lane] = acc[q];
+        for (int q = 0; q < RM::kSlots; ++q)
+#pragma unroll
+            for (int e = 0; e < W; ++e) red[warp][RM::row(q, lane) + e] = acc[q * W + e];
     }
     const double w0 = warp_sum((double)s_tr), w1 = warp_sum((double)s_tau), w2 = warp_sum((double)s_a),
                  w3 = warp_sum((double)s_rt);
@@ -298,6 +354,18 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
 
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
 
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// 16-byte row accesses: d and both leading dimensions multiples of 4 floats and
+// every base 16-byte aligned (the rows of mu are then aligned too).
+template <typename... Ptrs>
+bool net_vec(int64_t d, int64_t ldx, int64_t lds, const Ptrs*... ptrs) {
+    if (d % 4 != 0 || ldx % 4 != 0 || lds % 4 != 0) return false;
+    bool ok = true;
+    ((ok = ok && aligned16(ptrs)), ...);
+    return ok;
+}
+
 }  // namespace
 
 int net_row_chunks(int64_t d) { return grid_for(d, kNetRows); }
@@ -308,8 +376,12 @@ cudaError_t launch_net_layer(const float* X, int64_t ldx, const float* S, const 
                              const NetScalars& sc, float* Dpart, cudaStream_t st) {
     count_launches(1);
     const dim3 grid(max_tiles, grid_for(d, kNetRows));
-    k_net_layer<<<grid, kThreads, 0, st>>>(X, ldx, S, Th, L, Sn, Thn, lds, mu, perm, tiles, status, d, sc,
-                                           Dpart);
+    if (net_vec(d, ldx, lds, X, S, Th, L, Sn, Thn, mu))
+        k_net_layer<true><<<grid, kThreads, 0, st>>>(X, ldx, S, Th, L, Sn, Thn, lds, mu, perm, tiles, status, d,
+                                                     sc, Dpart);
+    else
+        k_net_layer<false><<<grid, kThreads, 0, st>>>(X, ldx, S, Th, L, Sn, Thn, lds, mu, perm, tiles, status, d,
+                                                      sc, Dpart);
     return cudaGetLastError();
 }
 
@@ -320,12 +392,20 @@ cudaError_t launch_net_back(int pass, const float* X, int64_t ldx, const float* 
                             double* scal_part, double* scal_out, cudaStream_t st) {
     count_launches(2);
     const dim3 grid(max_tiles, grid_for(d, kNetRows));
-    if (pass == 1)
-        k_net_back<1><<<grid, kThreads, 0, st>>>(X, ldx, S, Th, lds, mu, perm, tiles, status, d, sc, gLext,
-                                                 gS, gT, nullptr, Gpart, scal_part);
+    const bool vec = net_vec(d, ldx, lds, X, S, Th, gS, gT, mu) && (!gLext || aligned16(gLext)) &&
+                     (!gmean || aligned16(gmean));
+    if (pass == 1 && vec)
+        k_net_back<1, true><<<grid, kThreads, 0, st>>>(X, ldx, S, Th, lds, mu, perm, tiles, status, d, sc, gLext,
+                                                       gS, gT, nullptr, Gpart, scal_part);
+    else if (pass == 1)
+        k_net_back<1, false><<<grid, kThreads, 0, st>>>(X, ldx, S, Th, lds, mu, perm, tiles, status, d, sc, gLext,
+                                                        gS, gT, nullptr, Gpart, scal_part);
+    else if (vec)
+        k_net_back<2, true><<<grid, kThreads, 0, st>>>(X, ldx, S, Th, lds, mu, perm, tiles, status, d, sc, gLext,
+                                                       gS, gT, gmean, nullptr, scal_part);
     else
-        k_net_back<2><<<grid, kThreads, 0, st>>>(X, ldx, S, Th, lds, mu, perm, tiles, status, d, sc, gLext,
-                                                 gS, gT, gmean, nullptr, scal_part);
+        k_net_back<2, false><<<grid, kThreads, 0, st>>>(X, ldx, S, Th, lds, mu, perm, tiles, status, d, sc, gLext,
+                                                        gS, gT, gmean, nullptr, scal_part);
     k_net_scal_sum<<<1, kThreads, 0, st>>>(scal_part, (int64_t)grid.x * grid.y, scal_out);
     return cudaGetLastError();
 }

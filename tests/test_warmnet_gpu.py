@@ -94,6 +94,31 @@ def test_net_forward_matches_oracle(lib, case):
         lib.respca_net_destroy(net)
 
 
+def test_net_forward_scalar_rows_match_oracle(lib):
+    """d = 514 (not a multiple of 4): the kernels take one row per slot
+    instead of 16-byte accesses; same check as above on two row chunks."""
+    pr = synth.clustered_columns(514, 90, 3, seed=2, sparsity=0.1)
+    X = pr.X.astype(np.float32).astype(np.float64)
+    st = oracle.State(np.zeros(X.shape, order="F"), np.zeros(X.shape, order="F"),
+                      np.zeros(X.shape, order="F"), pr.truth_labels.astype(np.int32), 0.9)
+    for _ in range(3):
+        st, *_ = oracle.iteration(X, st, 3, 3.0)
+    cs = dict(X=X, p=st.labels, c=3, lam=3.0, S0=st.S.astype(np.float32).astype(np.float64),
+              T0=st.Theta.astype(np.float32).astype(np.float64))
+    m = np.random.default_rng(6).uniform(-0.5, 0.5, 2 * K)
+    rho_k, tau_k = lib.respca_net_schedule(st.rho, 1.5, m)
+    net = lib.respca_net_create()
+    try:
+        _, _, L, S, T = _gpu_forward(lib, net, cs, rho_k, tau_k)
+    finally:
+        lib.respca_net_destroy(net)
+    Lr, Sr, Tr = onet.forward(X, st.labels, 3, 3.0, cs["S0"], cs["T0"], rho_k, tau_k)
+    xs = np.abs(X).max()
+    assert np.abs(_host(L) - Lr).max() <= 2e-5 * xs
+    assert np.abs(_host(S) - Sr).max() <= 2e-5 * xs
+    assert np.abs(_host(T) - Tr).max() <= 2e-5 * max(np.abs(Tr).max(), 1e-30)
+
+
 def _oracle_loss(cs, rho_k, tau_k):
     L, S, _ = onet.forward(cs["X"], cs["p"], cs["c"], cs["lam"], cs["S0"], cs["T0"], rho_k, tau_k)
     return onet.loss(L, S, cs["Lt"], cs["St"], cs["scale"])
