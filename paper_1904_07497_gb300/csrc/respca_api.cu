@@ -217,13 +217,14 @@ cudaError_t zero_counters(respca_ctx* h) {
 // and pairwise separations) from the tile sums in Dpart, written to `dst`;
 // `prev` holds the centroids of the last search.
 respca_status finish_centroids(respca_ctx* h, int c, int64_t d, float* dst, const float* prev,
-                               double* sums_out = nullptr) {
+                               double* sums_out = nullptr, bool with_separation = true) {
     CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c, d,
                         dst, h->stream, sums_out));
     CK(launch_mu_stats(dst, prev, c, d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
                        prev ? P<double>(h->drift) : nullptr, h->stream));
-    CK(launch_separation(dst, P<int32_t>(h->counts), c, d, P<float>(h->pair_ss), P<double>(h->sep2),
-                         h->stream));
+    if (with_separation)
+        CK(launch_separation(dst, P<int32_t>(h->counts), c, d, P<float>(h->pair_ss), P<double>(h->sep2),
+                             h->stream));
     return RESPCA_OK;
 }
 
@@ -986,9 +987,11 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
                     c, p, v.vec);
         if (rs != RESPCA_OK) return rs;
         // next centroids if every label stays (queued before the check; discarded
-        // otherwise, but its FP64 sums then start the incremental update below)
+        // otherwise, but its FP64 sums then start the incremental update below).
+        // Their separations are formed only once the labels are known to stay:
+        // when some move, the final centroids get theirs at the end.
         rs = finish_centroids(h, c, d, P<float>(h->mu_next), P<float>(h->mu),
-                              v.sd == 0 ? P<double>(h->sumsD) : nullptr);
+                              v.sd == 0 ? P<double>(h->sumsD) : nullptr, false);
         if (rs != RESPCA_OK) return rs;
         rs = read_status(h);
         if (rs != RESPCA_OK) return rs;
@@ -1008,6 +1011,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
 
         if (h->hstat->changed == 0) {
             CK(cudaMemcpyAsync(h->mu.p, h->mu_next.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice, h->stream));
+            CK(launch_separation(P<float>(h->mu), P<int32_t>(h->counts), c, d, P<float>(h->pair_ss),
+                                 P<double>(h->sep2), h->stream));
         } else {
             // Lloyd on the columns of L until no label changes
             SearchCounts scount;
