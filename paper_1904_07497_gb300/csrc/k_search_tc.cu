@@ -1279,19 +1279,23 @@ __device__ double block_dist2_exact(const TY* __restrict__ y, const float* __res
     return s;
 }
 
-// Exact re-decision of near ties.  The candidate distances of the
+// Exact re-decision of near ties, one launch.  The candidate distances of the
 // first rc_cap queued columns are spread over every SM, one CTA per
-// (column, candidate) pair; k_search_recheck_pick then decides each column
-// over its candidates in increasing index (ties keep the lowest).  Columns
-// queued beyond rc_cap are decided by one CTA each, candidate after candidate.
+// (column, candidate) pair; columns queued beyond rc_cap are decided by one CTA
+// each, candidate after candidate.  The CTA that finishes last (a counter in
+// the status block) then decides the first rc_cap columns over their
+// candidates in increasing index (ties keep the lowest).
 template <typename TY>
 __global__ void __launch_bounds__(kThreads)
-    k_search_recheck_dist(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
-                          const DevStatus* __restrict__ status, const float* __restrict__ mu, int c,
-                          const RcRec* __restrict__ rc_list, double* __restrict__ rc_dist,
-                          int64_t rc_cap) {
+    k_search_recheck(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
+                     DevStatus* __restrict__ status, const float* __restrict__ mu, int c,
+                     int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
+                     const RcRec* __restrict__ rc_list, double* __restrict__ rc_dist, int64_t rc_cap) {
     __shared__ double red[kThreads / 32];
-    const int64_t nrc = min((int64_t)status->rechecked, rc_cap);
+    __shared__ int last_sh;
+    const int64_t nall = status->rechecked;
+    if (nall == 0) return;   // the same for every CTA: nobody counts, nothing to decide
+    const int64_t nrc = min(nall, rc_cap);
     const int64_t pairs = nrc * c;
     for (int64_t pr = blockIdx.x; pr < pairs; pr += gridDim.x) {
         const int64_t k = pr / c;
@@ -1302,47 +1306,22 @@ __global__ void __launch_bounds__(kThreads)
         if (threadIdx.x == 0) rc_dist[pr] = dist;
         __syncthreads();
     }
-}
-
-template <typename TY>
-__global__ void __launch_bounds__(kThreads)
-    k_search_recheck_pick(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
-                          DevStatus* __restrict__ status, const float* __restrict__ mu, int c,
-                          int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
-                          const RcRec* __restrict__ rc_list, const double* __restrict__ rc_dist,
-                          int64_t rc_cap) {
-    __shared__ double red[kThreads / 32];
-    const int64_t nrc = status->rechecked;
-    for (int64_t k = blockIdx.x; k < nrc; k += gridDim.x) {
+    for (int64_t k = rc_cap + blockIdx.x; k < nall; k += gridDim.x) {
         const RcRec& rec = rc_list[k];
         const int64_t col = rec.col;
+        const TY* y = Y + col * ldy;
         double best = INFINITY;
         int besti = INT_MAX;
-        if (k < rc_cap) {
-            if (threadIdx.x == 0) {
-                for (int ci = 0; ci < c; ++ci) {
-                    if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
-                    const double dist = rc_dist[k * c + ci];
-                    if (dist < best) {
-                        best = dist;
-                        besti = ci;
-                    }
-                }
-            }
-        } else {
-            const TY* y = Y + col * ldy;
-            for (int ci = 0; ci < c; ++ci) {
-                if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
-                const double dist = block_dist2_exact<TY>(y, mu + (int64_t)ci * d, d, vec, red);
-                if (dist < best) {
-                    best = dist;
-                    besti = ci;
-                }
+        for (int ci = 0; ci < c; ++ci) {
+            if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
+            const double dist = block_dist2_exact<TY>(y, mu + (int64_t)ci * d, d, vec, red);
+            if (dist < best) {
+                best = dist;
+                besti = ci;
             }
         }
         if (threadIdx.x == 0 && besti < c) {
-            const int32_t old = labels[col];
-            if (old != besti) {
+            if (labels[col] != besti) {
                 labels[col] = besti;
                 atomicAdd(&status->changed, 1);
             }
@@ -1353,6 +1332,39 @@ __global__ void __launch_bounds__(kThreads)
         }
         __syncthreads();
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_sh = (atomicAdd(&status->recheck_done, 1) == (int)gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last_sh) return;
+    __threadfence();
+    for (int64_t k = threadIdx.x; k < nrc; k += kThreads) {
+        const RcRec& rec = rc_list[k];
+        const int64_t col = rec.col;
+        double best = INFINITY;
+        int besti = INT_MAX;
+        for (int ci = 0; ci < c; ++ci) {
+            if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
+            const double dist = __ldcg(rc_dist + k * c + ci);
+            if (dist < best) {
+                best = dist;
+                besti = ci;
+            }
+        }
+        if (besti < c) {
+            if (labels[col] != besti) {
+                labels[col] = besti;
+                atomicAdd(&status->changed, 1);
+            }
+            if (ub) {
+                ub[col] = (float)(sqrt(best) * (1.0 + 1e-6));
+                lb[col] = 0.f;
+            }
+        }
+    }
+    if (threadIdx.x == 0) status->recheck_done = 0;
 }
 
 // TF32 hi / lo parts of the centroids, zero-padded to Npad rows of dpad; and,
@@ -1654,15 +1666,13 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
         if (e != cudaSuccess) return e;
     }
     if (dense_launched_out) *dense_launched_out = dense_launched;
-    count_launches(2);
+    count_launches(1);
     RESPCA_DISPATCH_X(dtype, TY, {
         // float4 rows need 16-byte aligned columns of Y and of the centroids (d % 4 == 0)
         const bool v4 = vec && sizeof(TY) == 4 && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
                         (reinterpret_cast<uintptr_t>(mu) % 16 == 0);
-        k_search_recheck_dist<TY><<<4 * num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu,
-                                                                    c, rc_list, rc_dist, rc_cap);
-        k_search_recheck_pick<TY><<<num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu, c,
-                                                                  labels, ub, lb, rc_list, rc_dist, rc_cap);
+        k_search_recheck<TY><<<4 * num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu, c,
+                                                               labels, ub, lb, rc_list, rc_dist, rc_cap);
     });
     return cudaGetLastError();
 }

@@ -50,7 +50,7 @@ struct DevStatus {
     double ramp_r2;         // ||X - mu_p||_F^2 (ramp statistics)
     unsigned long long ramp_ratio;  // bits of max_j ||X_j - mu_p|| / sep(p)
     unsigned int ramp_abs;  // bits of max |X - mu_p|
-    int32_t pad0;
+    int32_t recheck_done;   // CTAs of the near-tie re-decision that finished their distances
     int32_t flagged;        // columns queued for a nearest-centroid search
     int32_t changed;        // labels changed by the last assignment pass
     int32_t rechecked;      // near-tie columns re-decided in FP64
