@@ -473,14 +473,6 @@ inline unsigned blocks_for(int64_t work, int per) { return (unsigned)((work + pe
 
 }  // namespace
 
-cudaError_t launch_spec_gemm_tn(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc,
-                                int64_t m, int64_t n, int64_t K, float alpha, cudaStream_t st) {
-    count_launches(1);
-    const dim3 grid(blocks_for(m, kGT), blocks_for(n, kGT));
-    k_gemm_tn<<<grid, kGThreads, 0, st>>>(A, lda, B, ldb, C, ldc, m, n, K, alpha);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_spec_affinity(const float* Y, int64_t ldy, int64_t d, int64_t n, double scale, float* G,
                                  float* sqn, double* part, int parts, double* gsum, double* sig, double* deg,
                                  float* rinv, cudaStream_t st) {

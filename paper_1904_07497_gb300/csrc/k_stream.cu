@@ -449,30 +449,6 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// A column keeps its label for sure when its distance to its own centroid is
-// less than half the distance from that centroid to every other active one
-// (triangle inequality): ||L_j - mu_p|| < sep_p / 2.  All others are queued
-// for the nearest-centroid search.
-__global__ void __launch_bounds__(kThreads)
-    k_flag_columns(const float* __restrict__ own_part, int nchunks, int64_t n,
-                   const int32_t* __restrict__ labels, const double* __restrict__ sep2,
-                   double safety, int32_t* __restrict__ flag_list, DevStatus* __restrict__ status) {
-    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    bool flag = false;
-    if (j < n) {
-        double own = 0.0;
-        for (int ch = 0; ch < nchunks; ++ch) own += (double)own_part[(int64_t)ch * n + j];
-        const double sep = sep2[labels[j]];
-        flag = !(4.0 * own * (1.0 + 1e-5) < sep * safety);
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, flag);
-    const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0 && mask) base = atomicAdd(&status->flagged, __popc(mask));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (flag) flag_list[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)j;
-}
-
 // Hamerly-style exact pruning of the nearest-centroid search.  Per column j
 // with label p: ub[j] >= ||L_j - mu_p|| and lb[j] <= min_{i != p} ||L_j - mu_i||.
 // The own label is provably the strict nearest when ub < lb.
@@ -980,15 +956,6 @@ cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchu
                                 DevStatus* status, cudaStream_t st) {
     count_launches(1);
     k_reduce_norms<<<1, kThreads, 0, st>>>(norm_part, max_tiles, nchunks, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_flag_columns(const float* own_part, int nchunks, int64_t n,
-                                const int32_t* labels, const double* sep2, double safety,
-                                int32_t* flag_list, DevStatus* status, cudaStream_t st) {
-    count_launches(1);
-    k_flag_columns<<<grid_for(n, kThreads), kThreads, 0, st>>>(own_part, nchunks, n, labels, sep2,
-                                                               safety, flag_list, status);
     return cudaGetLastError();
 }
 

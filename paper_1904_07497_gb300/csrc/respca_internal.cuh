@@ -152,10 +152,6 @@ cudaError_t launch_iteration(int dtype, int sdtype, const void* X, int64_t ldx, 
 cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchunks,
                                 DevStatus* status, cudaStream_t st);
 
-cudaError_t launch_flag_columns(const float* own_part, int nchunks, int64_t n,
-                                const int32_t* labels, const double* sep2, double safety,
-                                int32_t* flag_list, DevStatus* status, cudaStream_t st);
-
 cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
                           const int32_t* list, const float* mu, const float* mu_normf,
                           const int32_t* counts, int c, int32_t* labels, DevStatus* status,
@@ -395,8 +391,6 @@ cudaError_t launch_adam(float* P, const float* G, float* M, float* V, int64_t co
                         float b2, float eps, float c1, float c2, cudaStream_t st);
 
 // ---------------------------------------------------------------- spectral p step
-cudaError_t launch_spec_gemm_tn(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc,
-                                int64_t m, int64_t n, int64_t K, float alpha, cudaStream_t st);
 cudaError_t launch_spec_affinity(const float* Y, int64_t ldy, int64_t d, int64_t n, double scale, float* G,
                                  float* sqn, double* part, int parts, double* gsum, double* sig, double* deg,
                                  float* rinv, cudaStream_t st);
