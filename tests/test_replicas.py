@@ -50,3 +50,18 @@ def test_single_rank_needs_no_group():
     import bench
     assert bench.max_over_ranks(3.25, 1) == 3.25
     assert bench.replica_seed(5, 0) == 5 and bench.replica_seed(5, 3) == 8
+
+
+@pytest.mark.parametrize("workload", ["c4", "c5", "spectral"])
+def test_reference_arm_without_oracle_workload_says_unavailable(workload):
+    """bench.py --impl reference prints one JSON line with an `unavailable`
+    reason (and exits 0) for the workloads that have no oracle arm."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--workload", workload], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unavailable"]
