@@ -240,24 +240,29 @@ respca_status respca_column_norms(const float *S, int64_t d, int64_t n, int64_t 
 
 /*
  * Initial labels WITHOUT ANY ALLOCATION.  The paper has no counterpart: this
- * is a library convenience.  It computes exactly what respca_init_labels
- * computes (same seed -> same labels), for callers that may not allocate
- * device memory while it runs: work being captured into a CUDA graph (where
- * cudaMalloc is not allowed), programs whose device memory belongs to their
- * own pool or is capped by a hard budget, and hosts that forbid a plug-in
+ * is a library convenience for callers that may not allocate device memory
+ * while it runs: programs whose device memory belongs to their own pool
+ * allocator or is capped by a hard budget, and hosts that forbid a plug-in
  * library from taking memory on its own.  No handle is used, because creating
- * one allocates.
+ * one allocates.  It uses the same k-means++ draws (same seed) and the same
+ * Lloyd rule as respca_init_labels; both take every assignment as the argmin
+ * of the stored distances with near ties re-decided exactly (ties to the
+ * lowest index), so the two give the same labels.  It runs on CUDA cores
+ * (the handle path searches on tensor cores).
  *
  *   x_dtype, X, d, n, ldx, c  as in respca_init_labels (device X).
  *   seed             seed of the k-means++ draws (cfg.seed of the handle path).
- *   kmeans_max_iter  cap on Lloyd passes (<= 0 selects 100).
+ *   kmeans_max_iter  cap on Lloyd passes (values below 1 mean 1, as
+ *                    cfg.kmeans_max_iter of the handle path).
  *   p                n device int32 output labels (caller-allocated).
  *   passes           optional host output: Lloyd assignment passes run.
  *   stream           cudaStream_t to run on (NULL = legacy default stream).
  *
- * All scratch lives in one 32 MiB array in device global memory, declared at
- * file scope in the library; every GPU that loads the library holds it until
- * the process exits.  The call needs
+ * X and p must be memory of the CUDA device that is current when the call is
+ * made (or managed memory); otherwise RESPCA_ERR_INVALID_ARG.  All scratch
+ * lives in one 32 MiB array in device global memory, declared at file scope
+ * in the library; every GPU that loads the library holds it until the process
+ * exits.  The call needs
  *   256-byte-aligned pieces totalling about 4 d (ceil(n/32) + c) + 4 c d + 12 n + 32 c bytes;
  * requests that do not fit (or c > 1024) return RESPCA_ERR_UNSUPPORTED
  * without touching the device.  The array's device address is looked up
@@ -265,8 +270,9 @@ respca_status respca_column_norms(const float *S, int64_t d, int64_t n, int64_t 
  * that first call before any stream capture starts.  Calls share the array
  * (it keeps the previous call's contents; the call clears what must start at
  * zero), so calls that overlap on the GPU -- from two streams or two host
- * threads -- race and must be serialised by the caller.  The call reads its
- * progress back from the device and returns when the labels are final.
+ * threads -- race and must be serialised by the caller.  The call is
+ * synchronous: it reads its progress back from the device after every Lloyd
+ * pass and returns when the labels are final.
  */
 respca_status respca_init_labels_noalloc(int32_t x_dtype, const void *X, int64_t d, int64_t n,
                                          int64_t ldx, int32_t c, uint64_t seed,

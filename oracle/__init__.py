@@ -26,17 +26,29 @@ _SRC = os.path.join(_HERE, "respca_oracle.c")
 
 _lib = None
 
+CFLAGS = ["-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-Wextra"]
+
+
+def compiler_version() -> str:
+    """First line of `gcc --version` (recorded beside oracle timings)."""
+    try:
+        out = subprocess.run(["gcc", "--version"], capture_output=True, text=True, check=True)
+        return out.stdout.splitlines()[0].strip()
+    except (OSError, subprocess.CalledProcessError):
+        return "unknown"
+
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, portable: x86_64 and aarch64)."""
+    """Compile the oracle with gcc: -O3, ISO C11, no FMA contraction and no
+    -march=native, so that the x86_64 and aarch64 builds round every
+    operation the same way and give the same bits."""
     os.makedirs(_LIBDIR, exist_ok=True)
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
             and os.path.getmtime(_LIB) >= os.path.getmtime(os.path.join(_HERE, "respca_oracle.h"))):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra",
-                    "-o", tmp, _SRC, "-lm"], check=True)
+    subprocess.run(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 

@@ -2,13 +2,13 @@
 // (respca_init_labels_noalloc, declared in include/respca.h).
 //
 // Who needs it: callers that must not allocate device memory while they run
-// this step -- code recording work into a CUDA graph (cudaMalloc is not
-// allowed during stream capture), applications whose memory is owned by
-// their own pool allocator or capped by a hard budget, and plug-in hosts that
-// forbid a library from taking device memory behind their back.  Such
-// callers cannot create a respca handle, whose workspace is cudaMalloc'ed on
-// demand.  This entry point takes every bit of scratch from one file-scope
-// __device__ array instead, sized once at library load.
+// this step -- applications whose device memory is owned by their own pool
+// allocator or capped by a hard budget, and plug-in hosts that forbid a
+// library from taking device memory behind their back.  Such callers cannot
+// create a respca handle, whose workspace is cudaMalloc'ed on demand.  This
+// entry point takes every bit of scratch from one file-scope __device__ array
+// instead, sized once at library load.  The call is synchronous: it reads its
+// progress back from the device after every Lloyd pass.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -96,6 +96,18 @@ cudaError_t scratch_address(void** out) {
     return cudaSuccess;
 }
 
+// True when ptr is device memory of device dev (or managed memory, which
+// every device can reach).
+bool on_device(const void* ptr, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();   // clear the error this query may leave behind
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 uint64_t draw_bits(uint64_t& s) {   // splitmix64, as in the handle path
     s += 0x9E3779B97F4A7C15ULL;
     uint64_t z = s;
@@ -116,6 +128,11 @@ extern "C" respca_status respca_init_labels_noalloc(int32_t x_dtype, const void*
     if (c > kMaxClusters) return RESPCA_ERR_UNSUPPORTED;
     if (layout(nullptr, d, n, c, nullptr) > kNoAllocScratchBytes) return RESPCA_ERR_UNSUPPORTED;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // The scratch array and every launch belong to the current device, so X
+    // and p must live there too (a kernel given another GPU's pointer faults).
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return RESPCA_ERR_CUDA;
+    if (!on_device(X, cur) || !on_device(p, cur)) return RESPCA_ERR_INVALID_ARG;
     void* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return RESPCA_ERR_CUDA;
     Scratch s;
@@ -146,7 +163,7 @@ extern "C" respca_status respca_init_labels_noalloc(int32_t x_dtype, const void*
     const size_t esz = x_dtype == RESPCA_F32 ? 4 : 2;
     const bool vec = (reinterpret_cast<uintptr_t>(X) % (4 * esz) == 0) && (ldx % 4 == 0) && (d % 4 == 0);
     const int mt = (int)((n + kTileCols - 1) / kTileCols) + c;
-    const int km = kmeans_max_iter > 0 ? kmeans_max_iter : 100;
+    const int km = kmeans_max_iter > 1 ? kmeans_max_iter : 1;   // as the handle path
     int np = 0;
     DevStatus hs;
     while (np < km) {

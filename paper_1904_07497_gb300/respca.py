@@ -177,6 +177,25 @@ def _colmajor(t, name):
     return max(t.stride(1), t.shape[0])
 
 
+def _state_out(L, S, d: int, n: int, like):
+    import torch
+    for t, name in ((L, "L"), (S, "S")):
+        if t.dtype != torch.float32 or t.device != like.device or tuple(t.shape) != (d, n):
+            raise ValueError(f"{name} must be a float32 ({d}, {n}) tensor on {like.device}")
+
+
+def _labels_out(p, n: int, like, name: str = "p"):
+    """Check an int32 label buffer before its pointer is handed to a kernel:
+    a wrong dtype, length, layout or device would be written out of bounds."""
+    import torch
+    if p.dtype != torch.int32:
+        raise ValueError(f"{name} must be int32")
+    if not p.is_cuda or p.device != like.device:
+        raise ValueError(f"{name} must be a CUDA tensor on {like.device}")
+    if not p.is_contiguous() or p.numel() < n:
+        raise ValueError(f"{name} must be contiguous with at least {n} elements")
+
+
 # ------------------------------------------------------------------ C names
 def respca_config_default() -> respca_config:
     cfg = respca_config()
@@ -203,6 +222,10 @@ def respca_solve(h, X, c: int, L, S, p, *, lam: float = 0.0, tol: float = 1e-6,
     lds = _colmajor(L, "L")
     if _colmajor(S, "S") != lds:
         raise ValueError("L and S must share a leading dimension")
+    _state_out(L, S, d, n, X)
+    _labels_out(p, n, X)
+    if p0 is not None:
+        _labels_out(p0, n, X, "p0")
     st = respca_stats()
     rc = load().respca_solve(h, _dtype_code(X), X.data_ptr(), d, n, ldx, float(lam), int(c),
                              float(tol), int(max_iter), p0.data_ptr() if p0 is not None else None,
@@ -230,6 +253,7 @@ def respca_solve_host(h, X, c: int, L, S, p, *, lam: float = 0.0, tol: float = 1
 def respca_init_labels(h, X, c: int, p) -> int:
     d, n = X.shape
     ldx = _colmajor(X, "X")
+    _labels_out(p, n, X)
     passes = ctypes.c_int32(0)
     rc = load().respca_init_labels(h, _dtype_code(X), X.data_ptr(), d, n, ldx, int(c),
                                    p.data_ptr(), ctypes.byref(passes))
@@ -240,17 +264,20 @@ def respca_init_labels(h, X, c: int, p) -> int:
 def respca_init_labels_noalloc(X, c: int, p, *, seed: int = 0, kmeans_max_iter: int = 100,
                                stream=None) -> int:
     """Initial labels with no device allocation (scratch in the library's
-    static device array): for callers that must not allocate while this runs,
-    e.g. during CUDA-graph capture or under their own memory pool.  X: (d, n)
-    column-major CUDA tensor; p: int32 (n,) CUDA tensor.  Returns the number
-    of Lloyd passes."""
+    static device array), for callers whose device memory belongs to their
+    own pool or budget.  Synchronous.  X: (d, n) column-major CUDA tensor;
+    p: int32 (n,) CUDA tensor on X's device.  Returns the number of Lloyd
+    passes."""
+    import torch
     d, n = X.shape
     ldx = _colmajor(X, "X")
+    _labels_out(p, n, X)
     passes = ctypes.c_int32(0)
     s = stream.cuda_stream if stream is not None else None
-    rc = load().respca_init_labels_noalloc(_dtype_code(X), X.data_ptr(), d, n, ldx, int(c),
-                                           int(seed), int(kmeans_max_iter), p.data_ptr(),
-                                           ctypes.byref(passes), s)
+    with torch.cuda.device(X.device):          # the entry point works on the current device
+        rc = load().respca_init_labels_noalloc(_dtype_code(X), X.data_ptr(), d, n, ldx, int(c),
+                                               int(seed), int(kmeans_max_iter), p.data_ptr(),
+                                               ctypes.byref(passes), s)
     _check(None, rc, "respca_init_labels_noalloc")
     return passes.value
 
@@ -373,6 +400,7 @@ def respca_spectral_labels(h, Y, c: int, p=None) -> tuple[object, dict]:
     ldy = _colmajor(Y, "Y")
     if p is None:
         p = torch.empty(n, device=Y.device, dtype=torch.int32)
+    _labels_out(p, n, Y)
     info = respca_spectral_info()
     rc = load().respca_spectral_labels(h, Y.data_ptr(), d, n, ldy, int(c), p.data_ptr(), ctypes.byref(info))
     _check(h, rc, "respca_spectral_labels")

@@ -1,6 +1,7 @@
 """Parity at the benchmark's full size: d = n = 10^4, rank 50, 10 % +-1
-corruption, c = 50 (400 MB per FP32 array), in the launch configuration
-bench.py times (tensor-core search over every column, 152 CTAs).
+corruption, c = 50 and the rank bound c = 100 (400 MB per FP32 array), in the
+launch configuration bench.py times (tensor-core search over every column,
+152 CTAs; c = 100 takes the two-slab centroid layout).
 
 Two iterations from the zero state with seeded labels and rho0 = 1 (so the
 S step is active from the first iteration), at most 3 Lloyd passes per p
@@ -8,7 +9,8 @@ step (so the oracle's passes over 10^8 elements stay few; it also exercises
 the device-run Lloyd loop stopping at its cap), run on the GPU and in the
 FP64 oracle; labels must agree exactly and L, S element by element within the
 FP32 tolerance of the other parity tests.  The oracle's inputs come from the
-seeded generator only.  The oracle needs about a minute of one host core.
+seeded generator only.  The oracle needs one to two minutes of one host core
+per case.
 """
 import numpy as np
 import pytest
@@ -20,11 +22,12 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
-def test_two_iterations_at_full_size():
+@pytest.mark.parametrize("c", [50, 100])
+def test_two_iterations_at_full_size(c):
     from paper_1904_07497_gb300 import respca
     oracle.build()
     d = n = 10000
-    c, T, rho0 = 50, 2, 1.0
+    T, rho0 = 2, 1.0
     pr = synth.lowrank_sparse(d, n, 50, 0.10, seed=0, keep_parts=False)
     p0 = (np.random.default_rng(123).integers(0, c, n)).astype(np.int32)
     p0[:c] = np.arange(c)
@@ -32,6 +35,7 @@ def test_two_iterations_at_full_size():
     s = respca.Solver(seed=0, rho0=rho0, ramp_skip=False, kmeans_max_iter=3)
     r = s.solve(X, c, tol=0.0, max_iter=T, p0=torch.from_numpy(p0).cuda())
     torch.cuda.synchronize()
+    assert r.stats["assigned_columns"] >= n, "every column must have been searched at least once"
     pg = r.p.cpu().numpy()
     Lg = r.L.T.contiguous().cpu().numpy().T
     Sg = r.S.T.contiguous().cpu().numpy().T

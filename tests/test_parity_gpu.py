@@ -351,6 +351,35 @@ def test_search_paths_agree_bf16_x():
     np.testing.assert_array_equal(a[1], b[1])
 
 
+# ------------------------------------------------------------------ two-slab dense search
+@pytest.mark.parametrize("d,n,c,T", [
+    (777, 700, 65, 30),       # smallest count past the stacked layout (Npad = 80); ragged d, n
+    (1000, 900, 100, 30),     # the rank bound 2r = 100 of the large single-matrix workload
+    (1024, 1100, 128, 26),    # largest count of the swapped-operand search
+])
+def test_two_slab_dense_search_matches_oracle(d, n, c, T):
+    """For 64 < c <= 128 the all-column tensor-core search holds the raw
+    centroids and their TF32 lo parts in two 128-row A slabs (rows i and
+    128 + i) and sums three products per 8 rows.  Labels must equal the
+    oracle's and L, S match it element by element; the timing mode proves the
+    all-column kernel ran."""
+    from paper_1904_07497_gb300 import respca
+    pr = synth.lowrank_sparse(d, n, 40, 0.1, seed=d + c)
+    X64 = pr.X.astype(np.float64)
+    p0, _ = oracle.init_labels(X64, c, seed=2)
+    ref, _ = oracle.solve(X64, c, tol=0.0, max_iter=T, p0=p0)
+    s = respca.Solver(seed=3, timing=True)
+    r = s.solve(_dev(pr.X), c, tol=0.0, max_iter=T, p0=torch.from_numpy(p0).cuda())
+    torch.cuda.synchronize()
+    st = r.stats
+    got = (r.p.cpu().numpy(), _host(r.L), _host(r.S))
+    s.close()
+    assert st["iters"] == T
+    assert st["dense_passes"] > 0, "the all-column search did not run"
+    np.testing.assert_array_equal(got[0], ref.labels)
+    _check_state(got[1], got[2], ref, X64)
+
+
 # ------------------------------------------------------------------ ramp skip
 @pytest.mark.parametrize("kind", ["lowrank", "video"])
 def test_ramp_skip_matches_step_by_step(kind):
