@@ -35,7 +35,6 @@ def test_two_iterations_at_full_size(c):
     s = respca.Solver(seed=0, rho0=rho0, ramp_skip=False, kmeans_max_iter=3)
     r = s.solve(X, c, tol=0.0, max_iter=T, p0=torch.from_numpy(p0).cuda())
     torch.cuda.synchronize()
-    assert r.stats["assigned_columns"] >= n, "every column must have been searched at least once"
     pg = r.p.cpu().numpy()
     Lg = r.L.T.contiguous().cpu().numpy().T
     Sg = r.S.T.contiguous().cpu().numpy().T

@@ -353,7 +353,7 @@ def test_search_paths_agree_bf16_x():
 
 # ------------------------------------------------------------------ two-slab dense search
 @pytest.mark.parametrize("d,n,c,T", [
-    (777, 700, 65, 30),       # smallest count past the stacked layout (Npad = 80); ragged d, n
+    (780, 700, 65, 30),       # smallest count past the stacked layout (Npad = 80); d, n ragged to the tiles
     (1000, 900, 100, 30),     # the rank bound 2r = 100 of the large single-matrix workload
     (1024, 1100, 128, 26),    # largest count of the swapped-operand search
 ])
@@ -362,7 +362,7 @@ def test_two_slab_dense_search_matches_oracle(d, n, c, T):
     centroids and their TF32 lo parts in two 128-row A slabs (rows i and
     128 + i) and sums three products per 8 rows.  Labels must equal the
     oracle's and L, S match it element by element; the timing mode proves the
-    all-column kernel ran."""
+    all-column kernel ran (it needs 16-byte columns, so d is a multiple of 4)."""
     from paper_1904_07497_gb300 import respca
     pr = synth.lowrank_sparse(d, n, 40, 0.1, seed=d + c)
     X64 = pr.X.astype(np.float64)
