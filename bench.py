@@ -41,6 +41,23 @@ WORKLOADS = {
     "small": (6000, 6000, 50, 0.10, 50),
     "c1": (500, 500, 25, 0.05, 25),
 }
+# video-shaped workloads: frames of height x width pixels as columns, n frames,
+# `backgrounds` static backgrounds in contiguous segments (c = backgrounds),
+# moving textured rectangles covering 2-10 % of a frame; X stored in BF16
+VIDEO = {
+    # name: (height, width, n, backgrounds, x dtype)
+    "c3": (240, 320, 2000, 3, "bf16"),
+}
+ESIZE = {"f32": 4, "bf16": 2, "f16": 2}
+
+
+def shape_of(name):
+    """(d, n, c, x dtype) of a workload."""
+    if name in VIDEO:
+        hgt, wid, n, nb, xdt = VIDEO[name]
+        return hgt * wid, n, nb, xdt
+    d, n, r, sp, c = WORKLOADS[name]
+    return d, n, c, "f32"
 
 
 def parse_args():
@@ -49,7 +66,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4", "c5", "spectral"])
+    ap.add_argument("--workload", default="c2",
+                    choices=sorted(WORKLOADS) + sorted(VIDEO) + ["c4", "c5", "spectral"])
     ap.add_argument("--lanes", type=int, default=8, help="c4: concurrent lanes of the batched solve")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="1: BF16 storage of X and the state until err <= 1e-2, then FP32")
@@ -63,13 +81,21 @@ def parse_args():
 
 
 def workload_config(name, tol):
+    d, n, c, xdt = shape_of(name)
+    l2 = ("inputs larger than L2 (each d x n FP32 array exceeds 129 MB)" if d * n * 4 > 129e6
+          else "inputs L2-resident (latency-bound size)")
+    if name in VIDEO:
+        hgt, wid, n, nb, xdt = VIDEO[name]
+        return {"workload": f"video-shaped: d={d} ({hgt}x{wid} frames) n={n}, {nb} smooth random "
+                            f"backgrounds in contiguous segments, moving textured rectangles on 2-10% of "
+                            f"pixels, X in {xdt.upper()}, c={c}, lambda=sqrt(max(d,n)), rho0=1e-4, "
+                            f"kappa=1.5, tol={tol:g}",
+                "d": d, "n": n, "c": c, "tol": tol, "x_dtype": xdt, "l2": l2}
     d, n, r, sp, c = WORKLOADS[name]
     return {
         "workload": f"lowrank+sparse d={d} n={n} rank={r} sparsity={sp} +-1, c={c}, "
                     f"lambda=sqrt(max(d,n)), rho0=1e-4, kappa=1.5, tol={tol:g}",
-        "d": d, "n": n, "rank": r, "sparsity": sp, "c": c, "tol": tol, "x_dtype": "f32",
-        "l2": "inputs larger than L2 (each d x n FP32 array exceeds 129 MB)"
-        if d * n * 4 > 129e6 else "inputs L2-resident (latency-bound size)",
+        "d": d, "n": n, "rank": r, "sparsity": sp, "c": c, "tol": tol, "x_dtype": "f32", "l2": l2,
     }
 
 
@@ -81,9 +107,30 @@ def arm_config(args):
 
 
 def make_problem(name, seed):
+    """(problem, c); for a video workload X is FP32 holding values exactly
+    representable in its storage type (the GPU reads the stored copy)."""
     from paper_1904_07497_gb300 import synth
+    if name in VIDEO:
+        import numpy as np
+        import torch
+        hgt, wid, n, nb, xdt = VIDEO[name]
+        pr = synth.video(n=n, height=hgt, width=wid, n_backgrounds=nb, seed=seed)
+        tdt = torch.bfloat16 if xdt == "bf16" else torch.float16
+        Xr = torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(tdt).float().numpy().T
+        return synth.Problem(X=Xr, L0=None, S0=None, rank=nb, truth_labels=pr.truth_labels), nb
     d, n, r, sp, c = WORKLOADS[name]
     return synth.lowrank_sparse(d, n, r, sp, seed, keep_parts=False), c
+
+
+def small_instance(name, seed):
+    """A smaller problem of the same family (d and n capped near 1000) whose
+    whole oracle solve gives the iteration and pass counts."""
+    from paper_1904_07497_gb300 import synth
+    if name in VIDEO:
+        hgt, wid, n, nb, xdt = VIDEO[name]
+        return synth.video(n=min(n, 1000), height=hgt // 8, width=wid // 8, n_backgrounds=nb, seed=seed)
+    d, n, r, sp, c = WORKLOADS[name]
+    return synth.lowrank_sparse(min(d, 1000), min(n, 1000), r, sp, seed)
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -133,13 +180,12 @@ def cpu_sample(name, seed, steps=1, warmup=0, snorm=0):
     import numpy as np
     import oracle
     oracle.build()
-    d, n, r, sp, c = WORKLOADS[name]
+    d, n, c, _ = shape_of(name)
     pr, _ = make_problem(name, seed)
     n_s = min(n, 1000)
     Xs = np.asfortranarray(pr.X[:, :n_s].astype(np.float64))
     del pr
-    from paper_1904_07497_gb300 import synth
-    small = synth.lowrank_sparse(min(d, 1000), min(n, 1000), r, sp, seed + 1)
+    small = small_instance(name, seed + 1)
     _, st_small = oracle.solve(small.X.astype(np.float64), c, tol=1e-6, max_iter=500, seed=seed, snorm=snorm)
     iters, passes, init_passes = st_small["iters"], st_small["lloyd_steps"], st_small["init_lloyd_steps"]
     lam = np.sqrt(max(d, n))
@@ -289,7 +335,10 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     pr, c = make_problem(args.workload, replica_seed(args.seed, rank))
     d, n = pr.X.shape
-    X = torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(dev).T          # (d, n) col-major
+    xdt = shape_of(args.workload)[3]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[xdt]
+    esz = ESIZE[xdt]
+    X = torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(tdt).to(dev).T   # (d, n) col-major
     L = torch.empty((n, d), device=dev).T
     S = torch.empty((n, d), device=dev).T
     p = torch.empty(n, device=dev, dtype=torch.int32)
@@ -341,7 +390,9 @@ def run_gpu(args, rank, world, local_rank):
     if args.s_norm:
         fused_bytes = d * n * BYTES_PER_ELEM_L21
     else:
-        fused_bytes = int(d * n * (BYTES_PER_ELEM_FP32 * (nf - nb) + (BYTES_PER_ELEM_FP32 // 2) * nb) / nf)
+        # FP32 state: X (esz) + S, Theta, L_prev read + L, S, Theta written (24 B)
+        fp32_bytes = BYTES_PER_ELEM_FP32 - 4 + esz
+        fused_bytes = int(d * n * (fp32_bytes * (nf - nb) + (BYTES_PER_ELEM_FP32 // 2) * nb) / nf)
     fused_gbs = fused_bytes / (fused_avg / 1e3) / 1e9
     roof_fused = {"bound": "hbm", "kernel": "k_l21_pass_a + k_l21_pass_b (l2,1 ALM iteration, two passes)"
                   if args.s_norm else "k_iteration (fused ALM iteration)",
@@ -373,7 +424,7 @@ def run_gpu(args, rank, world, local_rank):
 
     e2e = None
     if not args.no_e2e:
-        Xh = torch.from_numpy(np.ascontiguousarray(pr.X.T)).pin_memory().T
+        Xh = torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(tdt).pin_memory().T
         Lh = torch.empty((n, d), pin_memory=True).T
         Sh = torch.empty((n, d), pin_memory=True).T
         ph = torch.empty(n, dtype=torch.int32, pin_memory=True)
@@ -384,7 +435,7 @@ def run_gpu(args, rank, world, local_rank):
         for _ in range(ke):
             respca.respca_solve_host(solver.h, Xh, c, Lh, Sh, ph, tol=args.tol, max_iter=500)
         e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / ke, world, dev)
-        e2e = {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": 4 * d * n,
+        e2e = {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": esz * d * n,
                "d2h_bytes_per_step": 8 * d * n + 4 * n,
                "note": "respca_solve_host on pinned host buffers; copies inside the timed region"}
 
@@ -402,7 +453,7 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": round(ms_per_step, 3), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded numpy PCG64)",
+        "data": "synthetic (seeded numpy PCG64)" + (", X stored in " + xdt.upper() if xdt != "f32" else ""),
         "config": arm_config(args),
         "iters": iters, "converged": last["converged"], "err": last["err"],
         "bf16_iters": last["bf16_iters"],

@@ -175,6 +175,32 @@ def test_video_shaped(solver):
     _check_state(got["L"], got["S"], ref, X64)
 
 
+@pytest.mark.parametrize("dt", ["bf16", "f32"])
+def test_tall_video_frames(solver, dt):
+    """Full-size video frames (d = 76800 = 240 x 320 pixels) as columns: each
+    column spans many row chunks of the fused pass, whose partial sums are
+    combined across CTAs.  64 frames, 3 backgrounds, X in BF16 (the video
+    workload's storage) or FP32; the oracle runs on the same stored values."""
+    from paper_1904_07497_gb300 import respca
+    pr = synth.video(n=64, height=240, width=320, n_backgrounds=3, seed=6)
+    tdt = torch.bfloat16 if dt == "bf16" else torch.float32
+    Xh = torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(tdt)
+    X64 = Xh.float().numpy().T.astype(np.float64)
+    p0, _ = oracle.init_labels(X64, 3, seed=1)
+    ref, _ = oracle.solve(X64, 3, tol=0.0, max_iter=30, p0=p0)
+    X = Xh.cuda().T
+    d, n = X.shape
+    L = torch.zeros((n, d), device="cuda").T
+    S = torch.zeros((n, d), device="cuda").T
+    p = torch.zeros(n, device="cuda", dtype=torch.int32)
+    st = respca.respca_solve(solver.h, X, 3, L, S, p, tol=0.0, max_iter=30,
+                             p0=torch.from_numpy(p0).cuda())
+    assert st["iters"] == 30
+    assert np.count_nonzero(ref.S) > 0
+    np.testing.assert_array_equal(p.cpu().numpy(), ref.labels)
+    _check_state(_host(L), _host(S), ref, X64)
+
+
 @pytest.mark.parametrize("dt", ["bf16", "f16"])
 def test_half_precision_x(solver, dt):
     """X stored in BF16 / FP16: the oracle runs on the same rounded values."""
