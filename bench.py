@@ -635,12 +635,20 @@ C5_TRAIN, C5_HELD, C5_HELD_SEED = 8, 4, 10**6
 
 
 def run_learned(args, rank, world, local_rank):
-    """Learned warm start on the d = n = 2000 family (rank 10..50 = c,
-    sparsity 0.05..0.2): the network is trained (untimed) on 8 problems,
-    then each timed step solves 4 held-out problems to tol through it --
-    closed-form ramp, 8 learned layers, plain continuation -- against the
-    plain solver on the same problems.  Every rank trains and solves its own
-    problems (seeds differ by rank)."""
+    """The metric's comparison on the d = n = 2000 family (rank 10..50 = c,
+    sparsity 0.05..0.2), on the same held-out problems, each form solved to
+    tol:
+      fp32          the plain solver, FP32 state throughout;
+      bf16          the precision = 1 schedule (BF16 X and state until err <=
+                    1e-2, then FP32 on the FP32 X);
+      learned       closed-form ramp, 8 learned layers (FP32 state), plain
+                    FP32 continuation;
+      bf16_learned  the same with the layers' intermediate S, Theta stored in
+                    BF16 (respca_net_infer storage 1), FP32 continuation.
+    The network is trained (untimed) on 8 problems.  `value` is the
+    bf16_learned time per held-out problem.  Rank 0 alone (N = 1) also runs
+    the FP64 oracle's plain solve of the first held-out problem, and every
+    form's final L and S are compared with it."""
     import numpy as np
     import torch
     from paper_1904_07497_gb300 import respca, synth
@@ -656,21 +664,28 @@ def run_learned(args, rank, world, local_rank):
         return torch.from_numpy(np.ascontiguousarray(pr.X.T)).to(dev).T, pr.rank
 
     ws = WarmStart(layers=8, seed=args.seed, device=local_rank)
+    bf = respca.Solver(precision=1, device=local_rank)
     t0 = time.time()
     train = [ws.sample(*prob(base + s)) for s in range(C5_TRAIN)]
     hist = ws.fit(train, steps=600, lr=3e-2)
     train_s = time.time() - t0
     held = [prob(C5_HELD_SEED + base + s) for s in range(C5_HELD)]
 
-    def plain_step():
-        return [ws.plain.solve(X, c, tol=args.tol) for X, c in held]
+    def as_tuple(r):
+        return (r.L, r.S, r.p, {"total_iters": int(r.stats["iters"]), "converged": int(r.stats["converged"]),
+                                "err": float(r.stats["err"]), "launches": int(r.stats["kernel_launches"]),
+                                "bf16_iters": int(r.stats["bf16_iters"])})
 
-    def learned_step():
-        return [ws.solve(X, c, tol=args.tol) for X, c in held]
+    forms = {
+        "fp32": lambda X, c: as_tuple(ws.plain.solve(X, c, tol=args.tol)),
+        "bf16": lambda X, c: as_tuple(bf.solve(X, c, tol=args.tol)),
+        "learned": lambda X, c: ws.solve(X, c, tol=args.tol, storage=0),
+        "bf16_learned": lambda X, c: ws.solve(X, c, tol=args.tol, storage=1),
+    }
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
-            fn()
+            [fn(X, c) for X, c in held]
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -678,7 +693,7 @@ def run_learned(args, rank, world, local_rank):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            out = fn()
+            out = [fn(X, c) for X, c in held]
         e1.record(stream)
         torch.cuda.synchronize()
         return max_over_ranks(e0.elapsed_time(e1) / steps / C5_HELD, world, dev), out
@@ -686,55 +701,101 @@ def run_learned(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
-    ms_learned, res_l = timed(learned_step, args.steps, args.warmup)
+    results = {}
+    for name, fn in forms.items():
+        results[name] = timed(fn, args.steps, args.warmup)
     clk = clocks.stop()
-    ms_plain, res_p = timed(plain_step, args.steps, args.warmup)
-    it_l = [info["total_iters"] for *_, info in res_l]
-    it_p = [r.stats["iters"] for r in res_p]
-    dist = []
-    for (L, S, p, info), r, (X, c) in zip(res_l, res_p, held):
-        xn = float(torch.linalg.vector_norm(X.double()))
-        dist.append(float(torch.linalg.vector_norm((L - r.L).double())) / xn)
-    # the unrolled layers as one group: each reads X, S, Theta and writes L, S', Theta' (24 B/element)
+
+    summary = {}
+    plain_out = results["fp32"][1]
+    for name, (ms, out) in results.items():
+        dist = []
+        for (L, S, p, info), (Lp, Sp, pp, ip), (X, c) in zip(out, plain_out, held):
+            xn = float(torch.linalg.vector_norm(X.double()))
+            dist.append(float(torch.linalg.vector_norm((L - Lp).double())) / xn)
+        summary[name] = {"ms_per_problem": round(ms, 3), "iters": [o[3]["total_iters"] for o in out],
+                         "converged": sum(o[3]["converged"] for o in out),
+                         "dist_L_to_fp32_over_x": [float(f"{x:.3g}") for x in dist]}
+    # the layers alone, both storages: each layer reads X (4 B), S and Theta, writes
+    # S' and Theta' (BF16 in the intermediate layers with storage 1), and the last
+    # writes L; the first reads an FP32 state and the last writes one
     X, c = held[0]
+    d, n = X.shape
     rs = ws.ramp_state(X, c)
     m = ws.multipliers(rs.z)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(3):
-        ws.forward(X, c, rs, m)
-    e0.record(stream)
-    reps = 20
-    for _ in range(reps):
-        ws.forward(X, c, rs, m)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_fwd = e0.elapsed_time(e1) / reps
-    d, n = X.shape
-    fwd_bytes = 24 * d * n * ws.K
+    rho_k, tau_k = ws.schedule(rs, m)
+    Lb, Sb, Tb = (torch.empty((n, d), device=dev).T for _ in range(3))
     peak, peak_kind = measured_peak()
-    ach = fwd_bytes / (ms_fwd / 1e3) / 1e9
-    launches = sum(int(info.get("launches", 0)) for *_, info in res_l)
+    layer_roofs = []
+    for storage in (0, 1):
+        esz = 2 if storage else 4
+        nbytes = 0
+        for k in range(ws.K):
+            first, last = k == 0, k + 1 == ws.K
+            nbytes += d * n * (4 + (8 if first else 2 * esz) + (12 if last else 2 * esz))
+        for _ in range(3):
+            respca.respca_net_infer(ws.net, X, rs.p, c, rs.lam, rs.S, rs.Theta, rho_k, tau_k, Lb, Sb, Tb,
+                                    storage=storage)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps):
+            respca.respca_net_infer(ws.net, X, rs.p, c, rs.lam, rs.S, rs.Theta, rho_k, tau_k, Lb, Sb, Tb,
+                                    storage=storage)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_fwd = e0.elapsed_time(e1) / reps
+        ach = nbytes / (ms_fwd / 1e3) / 1e9
+        layer_roofs.append({"bound": "hbm", "kernel": f"k_net_infer x {ws.K} layers + centroids, "
+                            f"{'BF16' if storage else 'FP32'} intermediate state (L2-resident at this size)",
+                            "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                            "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,
+                            "avg_launch_ms": round(ms_fwd, 4)})
+    oracle_cmp = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        X64 = X.T.contiguous().cpu().numpy().T.astype(np.float64)
+        t1 = time.perf_counter()
+        ref, rst = oracle.solve(X64, c, tol=args.tol, max_iter=500, seed=0)
+        o_s = time.perf_counter() - t1
+        xn = float(np.linalg.norm(X64))
+        oracle_cmp = {"problem": f"held-out problem 0 (d=n={d}, c={c})", "oracle_iters": rst["iters"],
+                      "oracle_s": round(o_s, 1), "cores": 1, "host": host_info()}
+        for name, (ms, out) in results.items():
+            L, S, p, info = out[0]
+            Lh = L.T.contiguous().cpu().numpy().T.astype(np.float64)
+            Sh = S.T.contiguous().cpu().numpy().T.astype(np.float64)
+            oracle_cmp[name] = {"err_L_over_x": float(f"{np.linalg.norm(Lh - ref.L) / xn:.3g}"),
+                                "err_S_over_x": float(f"{np.linalg.norm(Sh - ref.S) / xn:.3g}"),
+                                "labels_equal": bool(np.array_equal(p.cpu().numpy(), ref.labels))}
+    launches = sum(int(info.get("launches", 0)) for *_, info in results["bf16_learned"][1])
     ws.close()
+    bf.close()
     if rank != 0:
         return None
+    ms_bl = results["bf16_learned"][0]
+    ms_fp = results["fp32"][0]
     return {
-        "metric": METRIC, "value": round(ms_learned, 3), "unit": "ms", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_learned * C5_HELD, 3),
+        "metric": METRIC, "value": round(ms_bl, 3), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_bl * C5_HELD, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded numpy PCG64)",
-        "config": {"workload": "learned warm start: d=n=2000, rank U{10..50} (= c), sparsity U[0.05,0.2] "
-                               f"+-1, {C5_TRAIN} training problems, {C5_HELD} held-out problems per step, "
-                               f"8 layers + MLP(64), tol={args.tol:g}; value = ms per held-out problem",
+        "config": {"workload": "BF16+learned vs plain FP32: d=n=2000, rank U{10..50} (= c), sparsity "
+                               f"U[0.05,0.2] +-1, {C5_TRAIN} training problems, {C5_HELD} held-out problems per "
+                               f"step, 8 layers + MLP(64), tol={args.tol:g}; value = ms per held-out problem "
+                               "of the bf16_learned form",
                    "l2": "each problem's arrays (16 MB each) fit in L2; steps repeat the same problems"},
-        "plain_ms": round(ms_plain, 3), "speedup_vs_plain": round(ms_plain / ms_learned, 2),
-        "iters_learned": it_l, "iters_plain": it_p, "dist_to_plain": [float(f"{x:.3g}") for x in dist],
-        "converged": sum(info["converged"] for *_, info in res_l), "train_s": round(train_s, 1),
+        "forms": summary, "speedup_bf16_learned_vs_fp32": round(ms_fp / ms_bl, 2),
+        "error_vs_fp64_oracle": oracle_cmp, "train_s": round(train_s, 1),
         "train_loss": [float(f"{hist[0]:.3g}"), float(f"{hist[-1]:.3g}")],
-        "roofline": {"bound": "hbm", "kernel": "net forward (8 layers: k_net_layer + centroids, 24 B/element "
-                     "per layer), L2-resident at this size", "achieved": round(ach, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind, "traffic": None},
-        "cpu_baseline": None, "e2e": None, "gpu_launches": launches or None, "clocks": clk,
+        "roofline": layer_roofs[1], "rooflines": layer_roofs,
+        "cpu_baseline": None if oracle_cmp is None else
+        {"value": round(oracle_cmp["oracle_s"] * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+         "sample": "the FP64 oracle's whole plain solve of held-out problem 0 (one problem, not the "
+                   "per-problem mean of the GPU line)", "host": oracle_cmp["host"]},
+        "e2e": None, "gpu_launches": launches or None, "clocks": clk,
     }
 
 

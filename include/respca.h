@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define RESPCA_ABI_VERSION 1
+#define RESPCA_ABI_VERSION 2
 
 typedef struct respca_ctx *respca_handle;
 
@@ -120,6 +120,7 @@ typedef struct {
                                 the passes in which it ran (cfg.timing = 1) */
     int32_t dense_passes;    /* passes in which that kernel searched every column */
     int32_t bf16_iters;      /* iterations run with BF16 state (precision = 1) */
+    double x_norm;           /* ||X||_F, the denominator of the Sec. 5 quantities */
 } respca_stats;
 
 /* Optional warm start / checkpoint-resume state (the paper starts from zero;
@@ -357,6 +358,24 @@ respca_status respca_net_forward(respca_net net, const float *X, int64_t d, int6
                                  const float *Theta0, int64_t lds, int32_t layers,
                                  const double *rho_k, const double *tau_k, float *L, float *S,
                                  float *Theta);
+
+/* Inference-only forward pass through the same layers (nothing is kept for
+ * respca_net_backward, and a preceding forward pass is forgotten).
+ *   x_dtype    element type of X (respca_dtype; FP32, BF16 or FP16), read as given.
+ *   storage    0: the intermediate layers' S and Theta are stored in FP32;
+ *              1: in BF16 (each stored value is the layer's FP32 result rounded to
+ *              BF16; the layers then move 2 instead of 4 bytes per stored element).
+ *              The arithmetic of every layer is FP32 either way.
+ *   S0, Theta0 d x n device FP32 input state, leading dimension lds (read only).
+ *   L, S, Theta d x n device FP32 outputs of the last layer (leading dimension lds),
+ *              required; L of the intermediate layers is never formed.
+ * Other arguments as respca_net_forward.  The call waits once for the label
+ * check; the layers are queued on the stream.  Errors as respca_net_forward. */
+respca_status respca_net_infer(respca_net net, int32_t x_dtype, const void *X, int64_t d, int64_t n,
+                               int64_t ldx, const int32_t *p, int32_t c, double lambda,
+                               const float *S0, const float *Theta0, int64_t lds, int32_t layers,
+                               const double *rho_k, const double *tau_k, int32_t storage, float *L,
+                               float *S, float *Theta);
 
 /* Loss and exact gradient of the last forward pass:
  *   loss = scale (||L - Lt||_F^2 + ||S - St||_F^2)

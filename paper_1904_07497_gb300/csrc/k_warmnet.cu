@@ -111,6 +111,104 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// ---------------------------------------------------------------- inference forward
+// The layer of k_net_layer for inference (no state is kept for a reverse
+// pass): X is read in its own type, the input state (S, Theta) and the output
+// state (S', Theta') are stored as TIN / TOUT (FP32, or BF16 holding the FP32
+// result rounded once), and L is written only when WRITE_L (the last layer;
+// the intermediate layers' L is never read).  Arithmetic is FP32 and the same
+// as k_net_layer's per element.  With VEC (d, the leading dimensions and the
+// bases aligned to 4 elements) each lane takes 4 slots of 4 consecutive rows.
+template <bool VEC, typename TX, typename TIN, typename TOUT, bool WRITE_L>
+__global__ void __launch_bounds__(kThreads)
+    k_net_infer(const TX* __restrict__ X, int64_t ldx, const TIN* __restrict__ S,
+                const TIN* __restrict__ Th, int64_t ldin, float* __restrict__ L,
+                TOUT* __restrict__ Sn, TOUT* __restrict__ Thn, int64_t ldout,
+                const float* __restrict__ mu, const int32_t* __restrict__ perm,
+                const TileDesc* __restrict__ tiles, const DevStatus* __restrict__ status, int64_t d,
+                NetScalars sc, float* __restrict__ Dpart) {
+    constexpr int kSlots = VEC ? 4 : 16;
+    constexpr int W = VEC ? 4 : 1;
+    __shared__ float red[kThreads / 32][kNetRows];
+    const int tile_idx = blockIdx.x;
+    if (tile_idx >= status->ntiles) return;
+    const TileDesc td = tiles[tile_idx];
+    const int64_t r0 = (int64_t)blockIdx.y * kNetRows;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float* mup = mu + (int64_t)td.label * d;
+    float acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+    for (int k = warp; k < td.len; k += kThreads / 32) {
+        const int64_t col = perm[td.start + k];
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+            const int64_t r = r0 + (VEC ? (q * 32 + lane) * 4 : q * 32 + lane);
+            if (r >= d) continue;
+            float x[W], s[W], t[W], m[W], l[W], sn[W], tn[W];
+            if (VEC) {
+                const float4 xv = XLoad<TX>::four(X + col * ldx + r);
+                const float4 sv = StateIO<TIN>::load4(S + col * ldin + r);
+                const float4 tv = StateIO<TIN>::load4(Th + col * ldin + r);
+                const float4 mv = *reinterpret_cast<const float4*>(mup + r);
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    x[e] = f4get(xv, e);
+                    s[e] = f4get(sv, e);
+                    t[e] = f4get(tv, e);
+                    m[e] = f4get(mv, e);
+                }
+            } else {
+                x[0] = XLoad<TX>::one(X + col * ldx + r);
+                s[0] = StateIO<TIN>::load1(S + col * ldin + r);
+                t[0] = StateIO<TIN>::load1(Th + col * ldin + r);
+                m[0] = mup[r];
+            }
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const float dv = (x[e] - s[e]) + t[e] * sc.inv_rho;
+                l[e] = fmaf(sc.a, dv, sc.b * m[e]);
+                const float bb = (x[e] - l[e]) + t[e] * sc.inv_rho;
+                const float mag = fabsf(bb) - sc.tau;
+                sn[e] = mag > 0.f ? copysignf(mag, bb) : 0.f;
+                tn[e] = t[e] + sc.rho * ((x[e] - l[e]) - sn[e]);
+                // the next layer reads the stored values: sum its D from them
+                acc[q * W + e] += (x[e] - StateIO<TOUT>::round(sn[e])) +
+                                  StateIO<TOUT>::round(tn[e]) * sc.inv_rho_next;
+            }
+            if (VEC) {
+                float4 lv, sv, tv;
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    f4set(lv, e, l[e]);
+                    f4set(sv, e, sn[e]);
+                    f4set(tv, e, tn[e]);
+                }
+                if (WRITE_L) StateIO<float>::store4(L + col * ldout + r, lv);
+                StateIO<TOUT>::store4(Sn + col * ldout + r, sv);
+                StateIO<TOUT>::store4(Thn + col * ldout + r, tv);
+            } else {
+                if (WRITE_L) L[col * ldout + r] = l[0];
+                StateIO<TOUT>::store1(Sn + col * ldout + r, sn[0]);
+                StateIO<TOUT>::store1(Thn + col * ldout + r, tn[0]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q)
+#pragma unroll
+        for (int e = 0; e < W; ++e) red[warp][(VEC ? (q * 32 + lane) * 4 : q * 32 + lane) + e] = acc[q * W + e];
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNetRows; i += kThreads) {
+        const int64_t r = r0 + i;
+        if (r >= d) continue;
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) v += red[w][i];
+        Dpart[(int64_t)tile_idx * d + r] = v;
+    }
+}
+
 // ---------------------------------------------------------------- backward
 // Per-CTA partial sums of the scalar gradients: 0: sum gTheta' R, 1: gtau,
 // 2: ga, 3: sum (gB + gD) Theta (pass 2 adds its gD part).
@@ -382,6 +480,66 @@ cudaError_t launch_net_layer(const float* X, int64_t ldx, const float* S, const 
     else
         k_net_layer<false><<<grid, kThreads, 0, st>>>(X, ldx, S, Th, L, Sn, Thn, lds, mu, perm, tiles, status, d,
                                                       sc, Dpart);
+    return cudaGetLastError();
+}
+
+template <typename TX, typename TI, typename TO, bool WL>
+void net_infer_go(bool vec, dim3 grid, cudaStream_t st, const void* X, int64_t ldx, const void* S,
+                  const void* Th, int64_t ldin, float* L, void* Sn, void* Thn, int64_t ldout, const float* mu,
+                  const int32_t* perm, const TileDesc* tiles, const DevStatus* status, int64_t d,
+                  const NetScalars& sc, float* Dpart) {
+    const TX* x = static_cast<const TX*>(X);
+    const TI* s = static_cast<const TI*>(S);
+    const TI* t = static_cast<const TI*>(Th);
+    TO* sn = static_cast<TO*>(Sn);
+    TO* tn = static_cast<TO*>(Thn);
+    if (vec)
+        k_net_infer<true, TX, TI, TO, WL><<<grid, kThreads, 0, st>>>(x, ldx, s, t, ldin, L, sn, tn, ldout, mu,
+                                                                      perm, tiles, status, d, sc, Dpart);
+    else
+        k_net_infer<false, TX, TI, TO, WL><<<grid, kThreads, 0, st>>>(x, ldx, s, t, ldin, L, sn, tn, ldout, mu,
+                                                                       perm, tiles, status, d, sc, Dpart);
+}
+
+// Inference layer: xdt / sin / sout are the element types of X (0 f32, 1 bf16,
+// 2 f16), of the input state and of the output state (0 f32, 1 bf16); L
+// (FP32, leading dimension ldout) is written when non-null, which requires
+// sout = 0.
+cudaError_t launch_net_infer(int xdt, int sin, int sout, const void* X, int64_t ldx, const void* S,
+                             const void* Th, int64_t ldin, float* L, void* Sn, void* Thn, int64_t ldout,
+                             const float* mu, const int32_t* perm, const TileDesc* tiles, int max_tiles,
+                             const DevStatus* status, int64_t d, const NetScalars& sc, float* Dpart,
+                             cudaStream_t st) {
+    if (L && sout != 0) return cudaErrorInvalidValue;
+    count_launches(1);
+    const dim3 grid(max_tiles, grid_for(d, kNetRows));
+    auto al = [](const void* p, size_t esz) { return (reinterpret_cast<uintptr_t>(p) % (4 * esz)) == 0; };
+    const size_t ex = xdt == 0 ? 4 : 2, ei = sin == 0 ? 4 : 2, eo = sout == 0 ? 4 : 2;
+    const bool vec = (d % 4 == 0) && (ldx % 4 == 0) && (ldin % 4 == 0) && (ldout % 4 == 0) && al(X, ex) &&
+                     al(S, ei) && al(Th, ei) && al(Sn, eo) && al(Thn, eo) && (!L || al(L, 4)) && al(mu, 4);
+    using BF = __nv_bfloat16;
+    RESPCA_DISPATCH_X(xdt, TX, {
+        if (sin == 0 && sout == 0) {
+            if (L)
+                net_infer_go<TX, float, float, true>(vec, grid, st, X, ldx, S, Th, ldin, L, Sn, Thn, ldout, mu,
+                                                     perm, tiles, status, d, sc, Dpart);
+            else
+                net_infer_go<TX, float, float, false>(vec, grid, st, X, ldx, S, Th, ldin, L, Sn, Thn, ldout, mu,
+                                                      perm, tiles, status, d, sc, Dpart);
+        } else if (sin == 0) {
+            net_infer_go<TX, float, BF, false>(vec, grid, st, X, ldx, S, Th, ldin, L, Sn, Thn, ldout, mu, perm,
+                                               tiles, status, d, sc, Dpart);
+        } else if (sout == 1) {
+            net_infer_go<TX, BF, BF, false>(vec, grid, st, X, ldx, S, Th, ldin, L, Sn, Thn, ldout, mu, perm,
+                                            tiles, status, d, sc, Dpart);
+        } else if (L) {
+            net_infer_go<TX, BF, float, true>(vec, grid, st, X, ldx, S, Th, ldin, L, Sn, Thn, ldout, mu, perm,
+                                              tiles, status, d, sc, Dpart);
+        } else {
+            net_infer_go<TX, BF, float, false>(vec, grid, st, X, ldx, S, Th, ldin, L, Sn, Thn, ldout, mu, perm,
+                                               tiles, status, d, sc, Dpart);
+        }
+    });
     return cudaGetLastError();
 }
 

@@ -53,6 +53,7 @@ struct respca_net_s {
     NetBuf mu;              // layers x c x d centroids of D, one set per layer
     NetBuf perm, counts, tile_off, tiles, status, part;   // label sort and tile partials
     NetBuf gS, gT, gL, gmean, scal_part, scal_out, loss_part, loss_out;
+    NetBuf ping;            // inference: two (S, Theta) states of the intermediate layers
 };
 
 namespace {
@@ -110,7 +111,7 @@ respca_status respca_net_destroy(respca_net h) {
     cudaSetDevice(h->device);
     for (NetBuf* b : {&h->state, &h->L, &h->mu, &h->perm, &h->counts, &h->tile_off, &h->tiles, &h->status,
                       &h->part, &h->gS, &h->gT, &h->gL, &h->gmean, &h->scal_part, &h->scal_out,
-                      &h->loss_part, &h->loss_out})
+                      &h->loss_part, &h->loss_out, &h->ping})
         if (b->p) cudaFree(b->p);
     delete h;
     return RESPCA_OK;
@@ -286,6 +287,72 @@ respca_status respca_adam_step(float* params, const float* grad, float* m, float
                        (float)c2, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
                ? RESPCA_OK
                : RESPCA_ERR_CUDA;
+}
+
+respca_status respca_net_infer(respca_net h, int32_t x_dtype, const void* X, int64_t d, int64_t n, int64_t ldx,
+                               const int32_t* p, int32_t c, double lambda, const float* S0, const float* Theta0,
+                               int64_t lds, int32_t layers, const double* rho_k, const double* tau_k,
+                               int32_t storage, float* L, float* S, float* Theta) {
+    if (!h || !X || !p || !S0 || !Theta0 || !rho_k || !tau_k || !L || !S || !Theta)
+        return RESPCA_ERR_INVALID_ARG;
+    if (x_dtype < 0 || x_dtype > 2 || (storage != 0 && storage != 1)) return RESPCA_ERR_INVALID_ARG;
+    if (d < 1 || n < 1 || ldx < d || lds < d || c < 1 || c > kMaxClusters || c > n || layers < 1 ||
+        !(lambda > 0.0))
+        return RESPCA_ERR_INVALID_ARG;
+    if (n > INT32_MAX / 2) return RESPCA_ERR_UNSUPPORTED;
+    for (int k = 0; k < layers; ++k)
+        if (!(rho_k[k] > 0.0) || !(tau_k[k] >= 0.0) || !std::isfinite(rho_k[k])) return RESPCA_ERR_INVALID_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return RESPCA_ERR_CUDA;
+    h->have_forward = false;     // nothing is kept for a reverse pass
+    const int mt = (int)((n + kTileCols - 1) / kTileCols) + c;
+    const int64_t ldm = (d + 7) / 8 * 8;             // intermediate states: 16-byte aligned columns
+    const size_t esz = storage == 1 ? 2 : 4;
+    cudaStream_t st = h->stream;
+    NK(grow(h->ping, esz * (size_t)ldm * n * (layers > 1 ? 4 : 0) + 16));
+    NK(grow(h->mu, sizeof(float) * (size_t)c * d));
+    NK(grow(h->perm, sizeof(int32_t) * n));
+    NK(grow(h->counts, sizeof(int32_t) * c));
+    NK(grow(h->tile_off, sizeof(int32_t) * (c + 1)));
+    NK(grow(h->tiles, sizeof(TileDesc) * mt));
+    NK(grow(h->status, sizeof(DevStatus)));
+    NK(grow(h->part, sizeof(float) * (size_t)mt * d));
+    DevStatus* ds = F<DevStatus>(h->status);
+    NK(cudaMemsetAsync(ds, 0, sizeof(DevStatus), st));
+    NK(launch_sort_labels(p, n, c, F<int32_t>(h->perm), F<int32_t>(h->counts), F<int32_t>(h->tile_off),
+                          F<TileDesc>(h->tiles), ds, st));
+    int32_t bad = 0;
+    NK(cudaMemcpyAsync(&bad, &ds->bad_labels, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NK(cudaStreamSynchronize(st));
+    if (bad) return RESPCA_ERR_INVALID_ARG;
+    // buffer k of the ping-pong pair: (S, Theta) of an intermediate layer
+    char* base = static_cast<char*>(h->ping.p);
+    auto Sb = [&](int k) { return base + esz * (size_t)ldm * n * (2 * (k & 1)); };
+    auto Tb = [&](int k) { return base + esz * (size_t)ldm * n * (2 * (k & 1) + 1); };
+    const bool vec_in = (d % 4 == 0) && (lds % 4 == 0) && (reinterpret_cast<uintptr_t>(S0) % 16 == 0) &&
+                        (reinterpret_cast<uintptr_t>(Theta0) % 16 == 0) && (ldx % 4 == 0) &&
+                        (reinterpret_cast<uintptr_t>(X) % (x_dtype == 0 ? 16 : 8) == 0);
+    NK(launch_colsum(kSumD, x_dtype, X, ldx, nullptr, S0, Theta0, lds, (float)(1.0 / rho_k[0]), F<int32_t>(h->perm),
+                     F<TileDesc>(h->tiles), mt, ds, d, F<float>(h->part), vec_in, st));
+    for (int k = 0; k < layers; ++k) {
+        NetScalars sc;
+        const double rho = rho_k[k], rho_next = (k + 1 < layers) ? rho_k[k + 1] : rho;
+        sc.a = (float)(rho / (2.0 * lambda + rho));
+        sc.b = (float)(2.0 * lambda / (2.0 * lambda + rho));
+        sc.rho = (float)rho;
+        sc.inv_rho = (float)(1.0 / rho);
+        sc.tau = (float)tau_k[k];
+        sc.inv_rho_next = (float)(1.0 / rho_next);
+        NK(launch_centroids(F<float>(h->part), F<int32_t>(h->tile_off), F<int32_t>(h->counts), c, d,
+                            F<float>(h->mu), st));
+        const bool first = k == 0, last = k + 1 == layers;
+        NK(launch_net_infer(x_dtype, first ? 0 : storage, last ? 0 : storage, X, ldx,
+                            first ? static_cast<const void*>(S0) : Sb(k - 1),
+                            first ? static_cast<const void*>(Theta0) : Tb(k - 1), first ? lds : ldm,
+                            last ? L : nullptr, last ? static_cast<void*>(S) : Sb(k),
+                            last ? static_cast<void*>(Theta) : Tb(k), last ? lds : ldm, F<float>(h->mu),
+                            F<int32_t>(h->perm), F<TileDesc>(h->tiles), mt, ds, d, sc, F<float>(h->part), st));
+    }
+    return RESPCA_OK;
 }
 
 }  // extern "C"

@@ -756,6 +756,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     const double nx = std::sqrt(h->hstat->x_norm2);
     const double lam = lambda > 0.0 ? lambda : std::sqrt((double)std::max(d, n));
     out.lambda = lam;
+    out.x_norm = nx;
 
     Problem pb;
     pb.dtype = dtype;

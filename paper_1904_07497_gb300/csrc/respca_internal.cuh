@@ -375,6 +375,11 @@ cudaError_t launch_net_layer(const float* X, int64_t ldx, const float* S, const 
                              float* Sn, float* Thn, int64_t lds, const float* mu, const int32_t* perm,
                              const TileDesc* tiles, int max_tiles, const DevStatus* status, int64_t d,
                              const NetScalars& sc, float* Dpart, cudaStream_t st);
+cudaError_t launch_net_infer(int xdt, int sin, int sout, const void* X, int64_t ldx, const void* S,
+                             const void* Th, int64_t ldin, float* L, void* Sn, void* Thn, int64_t ldout,
+                             const float* mu, const int32_t* perm, const TileDesc* tiles, int max_tiles,
+                             const DevStatus* status, int64_t d, const NetScalars& sc, float* Dpart,
+                             cudaStream_t st);
 cudaError_t launch_net_back(int pass, const float* X, int64_t ldx, const float* S, const float* Th,
                             int64_t lds, const float* mu, const int32_t* perm, const TileDesc* tiles,
                             int max_tiles, const DevStatus* status, int64_t d, const NetScalars& sc,

@@ -59,7 +59,8 @@ class respca_stats(ctypes.Structure):
                 ("init_lloyd_passes", ctypes.c_int32), ("fused_launches", ctypes.c_int32),
                 ("ms_total", ctypes.c_float), ("ms_init", ctypes.c_float),
                 ("ms_fused", ctypes.c_float), ("ms_dense", ctypes.c_float),
-                ("dense_passes", ctypes.c_int32), ("bf16_iters", ctypes.c_int32)]
+                ("dense_passes", ctypes.c_int32), ("bf16_iters", ctypes.c_int32),
+                ("x_norm", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {(k[:-1] if k.endswith("_") else k): getattr(self, k) for k, _ in self._fields_
@@ -130,6 +131,9 @@ def load():
     lib.respca_net_forward.argtypes = [_VP, _VP, _I64, _I64, _I64, _VP, ctypes.c_int32, _D, _VP, _VP,
                                        _I64, ctypes.c_int32, _PD, _PD, _VP, _VP, _VP]
     lib.respca_net_forward.restype = ctypes.c_int
+    lib.respca_net_infer.argtypes = [_VP, ctypes.c_int32, _VP, _I64, _I64, _I64, _VP, ctypes.c_int32, _D,
+                                     _VP, _VP, _I64, ctypes.c_int32, _PD, _PD, ctypes.c_int32, _VP, _VP, _VP]
+    lib.respca_net_infer.restype = ctypes.c_int
     lib.respca_net_backward.argtypes = [_VP, _VP, _VP, _I64, _D, _PD, _PD, _PD, _PF]
     lib.respca_net_backward.restype = ctypes.c_int
     lib.respca_mlp_forward.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP,
@@ -449,6 +453,27 @@ def respca_net_forward(net, X, p, c: int, lam: float, S0, Theta0, rho_k, tau_k, 
                                    S0.data_ptr(), Theta0.data_ptr(), lds, K, r, t, ptr(L), ptr(S),
                                    ptr(Theta))
     _check(None, rc, "respca_net_forward")
+
+
+def respca_net_infer(net, X, p, c: int, lam: float, S0, Theta0, rho_k, tau_k, L, S, Theta,
+                     storage: int = 0) -> None:
+    """Inference-only forward pass (respca_net_infer): X in FP32, BF16 or FP16;
+    intermediate layer states in FP32 (storage 0) or BF16 (storage 1); the
+    last layer's L, S, Theta (FP32, column-major like S0) are written."""
+    d, n = X.shape
+    ldx = _colmajor(X, "X")
+    lds = _colmajor(S0, "S0")
+    for t, name in ((Theta0, "Theta0"), (L, "L"), (S, "S"), (Theta, "Theta")):
+        if _colmajor(t, name) != lds:
+            raise ValueError(f"{name} must share S0's leading dimension")
+    _labels_out(p, n, X)
+    K = len(rho_k)
+    rk = (ctypes.c_double * K)(*rho_k)
+    tk = (ctypes.c_double * K)(*tau_k)
+    rc = load().respca_net_infer(net, _dtype_code(X), X.data_ptr(), d, n, ldx, p.data_ptr(), int(c),
+                                 float(lam), S0.data_ptr(), Theta0.data_ptr(), lds, K, rk, tk, int(storage),
+                                 L.data_ptr(), S.data_ptr(), Theta.data_ptr())
+    _check(None, rc, "respca_net_infer")
 
 
 def respca_net_backward(net, Lt, St, scale: float, layers: int):

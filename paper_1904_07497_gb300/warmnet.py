@@ -118,8 +118,7 @@ class WarmStart:
         warm.Theta = Th.data_ptr()
         warm.warm = 0
         st = R.respca_solve(self.ramp_solver.h, X, c, L, S, p, lam=lam, tol=1e-6, max_iter=500, warm=warm)
-        cn = R.respca_column_norms(X).double().cpu().numpy()
-        x_norm = float(np.sqrt(np.sum(cn * cn)))
+        x_norm = float(st["x_norm"])
         tiny = 1e-30
         z = np.array([math.log(warm.rho), math.log(st["lambda"]), math.log(x_norm / math.sqrt(d * n) + tiny),
                       math.log(st["err_resid"] + tiny), math.log(st["err_dL"] + tiny), math.log(c / n)])
@@ -177,10 +176,14 @@ class WarmStart:
         return history
 
     # ------------------------------------------------------------ inference
-    def solve(self, X, c: int, lam: float = 0.0, tol: float = 1e-6, max_iter: int = 500, use_net: bool = True):
+    def solve(self, X, c: int, lam: float = 0.0, tol: float = 1e-6, max_iter: int = 500, use_net: bool = True,
+              storage: int = 0):
         """Ramp (closed form) -> K layers -> plain iterations to tol.
-        Returns (L, S, p, info) with the iteration counts of each phase and
-        the wall time of the whole call on the stream."""
+        X may be FP32, BF16 or FP16 (read as given by every phase).  storage 1
+        keeps the intermediate layers' S and Theta in BF16 (respca_net_infer);
+        the continuation always runs with FP32 state.  Returns (L, S, p, info)
+        with the iteration counts of each phase and the wall time of the whole
+        call on the stream."""
         import torch
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -190,7 +193,9 @@ class WarmStart:
         if use_net:
             L, S, Th = (_empty_cm(d, n, X.device) for _ in range(3))
             m = self.multipliers(rs.z)
-            rho_k, _ = self.forward(X, c, rs, m, L, S, Th)
+            rho_k, tau_k = self.schedule(rs, m)
+            R.respca_net_infer(self.net, X, rs.p, c, rs.lam, rs.S, rs.Theta, rho_k, tau_k, L, S, Th,
+                               storage=storage)
             rho_next, layers = rho_k[-1] * self.kappa, self.K
         else:
             L, S, Th, rho_next, layers = rs.L, rs.S, rs.Theta, rs.rho, 0
@@ -203,9 +208,9 @@ class WarmStart:
                             max_iter=max(0, max_iter - rs.iters - layers), warm=warm)
         ev1.record(self.stream)
         ev1.synchronize()
-        # kernels: the two solver calls count their own; column norms (1), and with the
-        # network the MLP (1), the label sort, the first D sums and 2 per layer
-        launches = int(rs.stats["kernel_launches"]) + int(st["kernel_launches"]) + 1
+        # kernels: the two solver calls count their own; with the network the MLP (1),
+        # the label sort, the first D sums and 2 per layer
+        launches = int(rs.stats["kernel_launches"]) + int(st["kernel_launches"])
         if use_net:
             launches += 1 + 2 + 2 * self.K
         info = dict(ramp_iters=rs.iters, layers=layers, cont_iters=int(st["iters"]), launches=launches,

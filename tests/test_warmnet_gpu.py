@@ -256,3 +256,69 @@ def test_warm_start_gain_on_held_out_problems(lib):
         assert r[1] < r[0] and r[3] < r[2]
     finally:
         ws.close()
+
+
+# ------------------------------------------------------------------ inference forward
+def _bf16(A):
+    """FP64 values rounded to BF16 (torch's round-to-nearest-even) and back."""
+    t = torch.from_numpy(np.ascontiguousarray(A)).to(torch.bfloat16).to(torch.float64)
+    return t.numpy()
+
+
+def _infer(lib, cs, X, rho_k, tau_k, storage):
+    d, n = cs["X"].shape
+    p = torch.from_numpy(cs["p"].astype(np.int32)).cuda()
+    L, S, T = (torch.empty((n, d), device="cuda").T for _ in range(3))
+    net = lib.respca_net_create()
+    try:
+        lib.respca_net_infer(net, X, p, cs["c"], cs["lam"], _dev(cs["S0"]), _dev(cs["T0"]), rho_k, tau_k,
+                             L, S, T, storage=storage)
+        torch.cuda.synchronize()
+    finally:
+        lib.respca_net_destroy(net)
+    return _host(L), _host(S), _host(T)
+
+
+def test_net_infer_fp32_matches_oracle_and_forward(lib, case):
+    """Inference with FP32 intermediate states: the same layers as the
+    training forward pass (same per-element arithmetic), so it matches the
+    FP64 oracle within the forward tolerance and the training forward to
+    FP32 rounding of the D sums."""
+    rho_k, tau_k = lib.respca_net_schedule(case["rho"], 1.5, case["m"])
+    L, S, T = _infer(lib, case, _dev(case["X"]), rho_k, tau_k, 0)
+    Lr, Sr, Tr = onet.forward(case["X"], case["p"], case["c"], case["lam"], case["S0"], case["T0"],
+                              rho_k, tau_k)
+    xs = np.abs(case["X"]).max()
+    assert np.abs(L - Lr).max() <= 2e-5 * xs
+    assert np.abs(S - Sr).max() <= 2e-5 * xs
+    assert np.abs(T - Tr).max() <= 2e-5 * max(np.abs(Tr).max(), 1e-30)
+    net = lib.respca_net_create()
+    try:
+        _, _, Lf, Sf, Tf = _gpu_forward(lib, net, case, rho_k, tau_k)
+    finally:
+        lib.respca_net_destroy(net)
+    assert np.abs(L - _host(Lf)).max() <= 1e-6 * xs
+    assert np.abs(S - _host(Sf)).max() <= 1e-6 * xs
+
+
+def test_net_infer_bf16_storage_matches_rounded_oracle(lib, case):
+    """X in BF16 and the intermediate layers' S, Theta stored in BF16: the
+    oracle runs the same layers in FP64 on the same BF16 X and rounds S and
+    Theta to BF16 where the GPU stores them.  An FP32 and an FP64 result may
+    round to neighbouring BF16 values, so stored values differ by at most one
+    BF16 ulp (2^-8 relative) in a few elements; the last layer's FP32 outputs
+    must then lie within 2^-9 relative Frobenius error (the per-store rounding
+    bound) and 4 BF16 ulps of the largest entry element-wise."""
+    rho_k, tau_k = lib.respca_net_schedule(case["rho"], 1.5, case["m"])
+    Xb64 = _bf16(case["X"])
+    Xb = torch.from_numpy(np.ascontiguousarray(case["X"].T)).to(torch.bfloat16).cuda().T
+    L, S, T = _infer(lib, case, Xb, rho_k, tau_k, 1)
+    Sr, Tr = case["S0"], case["T0"]
+    for k in range(K):
+        Lr, Sr, Tr = onet.forward(Xb64, case["p"], case["c"], case["lam"], Sr, Tr, [rho_k[k]], [tau_k[k]])
+        if k + 1 < K:
+            Sr, Tr = _bf16(Sr), _bf16(Tr)
+    for got, want in ((L, Lr), (S, Sr), (T, Tr)):
+        scale = max(np.abs(want).max(), np.abs(Xb64).max())
+        assert np.linalg.norm(got - want) <= 2.0 ** -9 * max(np.linalg.norm(want), 1e-30)
+        assert np.abs(got - want).max() <= 2.0 ** -6 * scale
