@@ -231,6 +231,49 @@ respca_status respca_init_labels(respca_handle h, int32_t x_dtype, const void *X
 respca_status respca_solve_batched(respca_handle h, int32_t batch, const respca_problem *probs,
                                    respca_stats *stats);
 
+/* Options and results of respca_solve_batched_persistent. */
+typedef struct {
+    int32_t tile_rows;          /* in: rows per row-block work item, 64 or 128; 0 = autotuned */
+    int32_t ctas_per_sm;        /* in: resident CTAs per SM, 1 or 2; 0 = autotuned */
+    int64_t spin_limit;         /* in: empty polls of the work queue after which a CTA gives up
+                                   (RESPCA_ERR_TIMEOUT); 0 = default (2^23, about a second or more) */
+    int32_t tuned_rows;         /* out: the rows per row item used */
+    int32_t tuned_ctas_per_sm;  /* out: the CTAs per SM used */
+    float ms_kernel;            /* out: duration of the persistent launch (CUDA events) */
+    int32_t reserved;
+} respca_batch_options;
+
+/*
+ * Solve `batch` independent problems (as respca_solve_batched) in ONE
+ * persistent kernel launch, replayed from a CUDA graph while the batch's
+ * pointers and sizes stay the same.  Each problem runs the iteration of
+ * Sec. 4 -- Eq. (18), Lloyd's method for the p step of Sec. 4.2, Eq. (24),
+ * Eq. (25) and the Sec. 5 stopping rule, every iteration (no closed-form
+ * leading iterations) -- after k-means++ (cfg.seed, the same draws as
+ * respca_init_labels) and Lloyd on X, or from the problem's p0.  The work of
+ * all problems is split into row-block and column-block items that the
+ * launch's CTAs (one or two per SM) pull from a per-problem claim word; the
+ * CTA that completes a phase runs its serial tail and publishes the next
+ * phase, so problems of any size mix in one launch.  Results match the FP64
+ * oracle to FP32 rounding (labels identical to respca_solve's except where two
+ * distances agree to about 1e-5); they are not bit-identical to respca_solve,
+ * whose kernels sum in other orders.
+ *
+ * Limits: FP32 X, 1 <= c <= 64, d, n <= 2^22 (RESPCA_ERR_UNSUPPORTED beyond).
+ * Tile rows and CTAs per SM are chosen by timing the candidates on a run of
+ * the batch capped at 3 iterations, once per batch shape and handle, unless
+ * opt fixes them.  A CTA that finds no work for spin_limit polls sets a
+ * timeout flag; every CTA then leaves at its next item boundary and the call
+ * returns RESPCA_ERR_TIMEOUT (outputs unspecified).  Per-problem errors (NaN
+ * or Inf in X: RESPCA_ERR_NONFINITE_INPUT; p0 labels outside [0, c):
+ * RESPCA_ERR_INVALID_ARG) end that problem only; the lowest-index one is
+ * returned.  stats (optional, `batch` entries): per problem; kernel_launches
+ * is 1 on entry 0 and ms_total the launch's duration on every entry.
+ * opt: optional.  Synchronous: returns when every problem is done.
+ */
+respca_status respca_solve_batched_persistent(respca_handle h, int32_t batch, const respca_problem *probs,
+                                              respca_stats *stats, respca_batch_options *opt);
+
 /* Anomaly score of Sec. 6: out[j] = ||S_j||_2 for every column j of a d x n
  * device matrix S (leading dimension lds >= d), e.g. the S of a solve; the
  * columns with large scores are the outlying samples.  out: n device floats.

@@ -58,6 +58,7 @@ struct respca_ctx {
     int lloyd_graph_next = 0;               // slot the next new graph replaces
     std::vector<respca_ctx*> lanes;         // batch lanes (respca_solve_batched), made on first use
     respca_ctx* spec_km = nullptr;          // K-means on the spectral embedding (own workspace)
+    respca::BatchedState* batched = nullptr; // the persistent batched solve's buffers and graph
     respca_config cfg{};
     std::string last_error;
 
@@ -1177,6 +1178,8 @@ respca_status respca_destroy(respca_handle h) {
     else cudaDeviceSynchronize();
     for (DevBuf* b : all_bufs(h))
         if (b->p) cudaFree(b->p);
+    respca::batched_state_free(h->batched);
+    h->batched = nullptr;
     if (h->hstat) cudaFreeHost(h->hstat);
     if (h->hseed_u) cudaFreeHost(h->hseed_u);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -1341,6 +1344,14 @@ respca_status respca_solve_batched(respca_handle h, int32_t batch, const respca_
         }
     }
     return RESPCA_OK;
+}
+
+respca_status respca_solve_batched_persistent(respca_handle h, int32_t batch, const respca_problem* probs,
+                                              respca_stats* stats, respca_batch_options* opt) {
+    if (!h) return RESPCA_ERR_INVALID_ARG;
+    h->last_error.clear();
+    return respca::batched_persistent(&h->batched, h->device, h->stream, h->cfg.seed, h->cfg.rho0, h->cfg.kappa,
+                                      h->cfg.kmeans_max_iter, batch, probs, stats, opt, &h->last_error);
 }
 
 respca_status respca_column_norms(const float* S, int64_t d, int64_t n, int64_t lds, float* out,

@@ -13,8 +13,11 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <string>
 #include <cuda_fp16.h>
 #include <stdint.h>
+
+#include "../../include/respca.h"
 
 namespace respca {
 
@@ -412,6 +415,13 @@ cudaError_t launch_spec_rotate(const float* Y, const float* Q, float* out, int64
 cudaError_t launch_spec_residual(const float* W, const float* Y, const double* evals, int64_t n, int c,
                                  double* res, cudaStream_t st);
 cudaError_t launch_spec_embed(const float* Y, int64_t n, int c, float* E, cudaStream_t st);
+
+// ---------------------------------------------------------------- batched persistent solve
+struct BatchedState;
+void batched_state_free(BatchedState* s);
+respca_status batched_persistent(BatchedState** sp, int device, cudaStream_t st, uint64_t seed, double rho0,
+                                 double kappa, int km_max, int32_t batch, const respca_problem* probs,
+                                 respca_stats* stats, respca_batch_options* opt, std::string* err);
 
 // Dispatch a runtime dtype (0 f32, 1 bf16, 2 f16) to a template lambda.
 #define RESPCA_DISPATCH_X(dtype, TX, ...)                       \

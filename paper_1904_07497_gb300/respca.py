@@ -81,6 +81,13 @@ class respca_problem(ctypes.Structure):
                 ("lds", ctypes.c_int64), ("p", ctypes.c_void_p)]
 
 
+class respca_batch_options(ctypes.Structure):
+    _fields_ = [("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64), ("tuned_rows", ctypes.c_int32),
+                ("tuned_ctas_per_sm", ctypes.c_int32), ("ms_kernel", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 _I64 = ctypes.c_int64
 _VP = ctypes.c_void_p
@@ -113,6 +120,10 @@ def load():
     lib.respca_solve_batched.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(respca_problem),
                                          ctypes.POINTER(respca_stats)]
     lib.respca_solve_batched.restype = ctypes.c_int
+    lib.respca_solve_batched_persistent.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(respca_problem),
+                                                    ctypes.POINTER(respca_stats),
+                                                    ctypes.POINTER(respca_batch_options)]
+    lib.respca_solve_batched_persistent.restype = ctypes.c_int
     lib.respca_init_labels_noalloc.argtypes = [ctypes.c_int32, _VP, _I64, _I64, _I64, ctypes.c_int32,
                                                ctypes.c_uint64, ctypes.c_int32, _VP,
                                                ctypes.POINTER(ctypes.c_int32), _VP]
@@ -300,8 +311,7 @@ def respca_column_norms(S, out=None, stream=None):
     return out
 
 
-def respca_solve_batched(h, problems: list[dict]) -> list[dict]:
-    """problems: dicts with X, c, L, S, p (and optional lam, tol, max_iter, p0)."""
+def _problem_table(problems: list[dict]):
     arr = (respca_problem * len(problems))()
     for i, q in enumerate(problems):
         X = q["X"]
@@ -318,10 +328,30 @@ def respca_solve_batched(h, problems: list[dict]) -> list[dict]:
         arr[i].S = q["S"].data_ptr()
         arr[i].lds = _colmajor(q["L"], "L")
         arr[i].p = q["p"].data_ptr()
+    return arr
+
+
+def respca_solve_batched(h, problems: list[dict]) -> list[dict]:
+    """problems: dicts with X, c, L, S, p (and optional lam, tol, max_iter, p0)."""
+    arr = _problem_table(problems)
     stats = (respca_stats * len(problems))()
     rc = load().respca_solve_batched(h, len(problems), arr, stats)
     _check(h, rc, "respca_solve_batched")
     return [s.as_dict() for s in stats]
+
+
+def respca_solve_batched_persistent(h, problems: list[dict], opt: respca_batch_options | None = None):
+    """All problems in one persistent launch (respca_solve_batched_persistent).
+    Returns (per-problem stats, options with the tile choice and kernel time)."""
+    arr = _problem_table(problems)
+    for q in problems:
+        _state_out(q["L"], q["S"], q["X"].shape[0], q["X"].shape[1], q["X"])
+        _labels_out(q["p"], q["X"].shape[1], q["X"])
+    stats = (respca_stats * len(problems))()
+    o = opt if opt is not None else respca_batch_options()
+    rc = load().respca_solve_batched_persistent(h, len(problems), arr, stats, ctypes.byref(o))
+    _check(h, rc, "respca_solve_batched_persistent")
+    return [s.as_dict() for s in stats], o
 
 
 # ------------------------------------------------------------------ convenience

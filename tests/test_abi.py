@@ -61,10 +61,12 @@ def test_binding_struct_sizes_match_header(lib):
     import tempfile
     from paper_1904_07497_gb300 import respca
     src = ('#include "respca.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-           'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(respca_config),'
+           'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(respca_config),'
            ' sizeof(respca_stats), sizeof(respca_warm), sizeof(respca_problem),'
            ' offsetof(respca_stats, ms_total), offsetof(respca_problem, p),'
-           ' sizeof(respca_spectral_info), offsetof(respca_config, spectral_scale));return 0;}\n')
+           ' sizeof(respca_spectral_info), offsetof(respca_config, spectral_scale),'
+           ' offsetof(respca_stats, x_norm), sizeof(respca_batch_options),'
+           ' offsetof(respca_batch_options, ms_kernel));return 0;}\n')
     with tempfile.TemporaryDirectory() as td:
         c = os.path.join(td, "probe.c")
         exe = os.path.join(td, "probe")
@@ -74,7 +76,9 @@ def test_binding_struct_sizes_match_header(lib):
     want = [ctypes.sizeof(respca.respca_config), ctypes.sizeof(respca.respca_stats),
             ctypes.sizeof(respca.respca_warm), ctypes.sizeof(respca.respca_problem),
             respca.respca_stats.ms_total.offset, respca.respca_problem.p.offset,
-            ctypes.sizeof(respca.respca_spectral_info), respca.respca_config.spectral_scale.offset]
+            ctypes.sizeof(respca.respca_spectral_info), respca.respca_config.spectral_scale.offset,
+            respca.respca_stats.x_norm.offset, ctypes.sizeof(respca.respca_batch_options),
+            respca.respca_batch_options.ms_kernel.offset]
     assert got == want
 
 
