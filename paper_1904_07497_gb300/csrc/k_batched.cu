@@ -45,9 +45,9 @@ enum Phase : int32_t {
     PH_ASSIGN_X,     // col: nearest centroid of the columns of X (initial Lloyd)
     PH_MEANS_X,      // row: cluster means of X
     PH_SUMS_D,       // row: cluster means of D = X - S + Theta/rho (start of the iterations)
-    PH_LSTEP,        // col: L step (Eq. (18)) and the first assignment of the p step
+    PH_LSTEP,        // row: L step (Eq. (18)), ||L_{t+1} - L_t||^2
     PH_MEANS_L,      // row: cluster means of L (further Lloyd passes)
-    PH_ASSIGN_L,     // col: nearest centroid of the columns of L
+    PH_ASSIGN_L,     // col: nearest centroid of the columns of L (every pass of the p step)
     PH_STHETA,       // row: S step, Theta step, norms, means of the next D
     PH_DONE
 };
@@ -187,13 +187,15 @@ struct BSmem {
     union {
         struct {
             float cs[kMaxC * kChunk];    // 32 KB: centroid chunk of a column item
-            double red[kBW][kChunk];     // 8 KB: per-warp row partials of a row item
+            double red[kBW][kChunk];     // 8 KB: per-warp row partials
         } it;
+        float slot[(kMaxC + kBW) * kChunk];   // 36 KB: run sums of a row item, slot = label + warp
         int32_t hist[kMaxC * kBT];       // 64 KB: per-thread label histograms of the sort
     };
     double dscan[kBT + 1];
     double dred[kBW + 1];
     int32_t offs_s[kMaxC + 1];
+    int32_t wlo[kBW], whi[kBW];          // first and last label of each warp's range (row items)
     int32_t pick;
     int32_t item;
     int32_t nitems;
@@ -207,197 +209,331 @@ struct BSmem {
 // ---------------------------------------------------------------- row items
 // Rows [r0, r0 + KR*32) of every column; lane l takes rows r0 + l + 32 q.
 // Cluster sums visit the columns in label-sorted order: for each cluster, warp
-// w takes its columns w, w + 8, ...; per-lane FP32 sums are flushed to FP64
-// every 8 columns and the 8 warps' partials are added in warp order, so every
-// sum has one fixed order.
+// w takes its columns in groups of kRG (loads of the group issued before the
+// arithmetic), groups w, w + 8, ...; per-lane FP32 sums are flushed to FP64
+// after every group and the 8 warps' partials are added in warp order, so
+// every sum has one fixed order.  The descriptor's fields are copied to
+// locals first: a store through L, S or Theta could otherwise alias them and
+// force a reload after every store.
+constexpr int kRG = 4;
+
 template <int KR>
-__device__ void row_item(const BProb& pb, double rho, int phase, int item, BSmem& sm) {
+__device__ void row_item(const BProb& pbr, double rho, int phase, int item, BSmem& sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r0 = (int64_t)item * KR * 32;
-    const int d = pb.d, n = pb.n;
+    const float* __restrict__ X = pbr.X;
+    float* __restrict__ L = pbr.L;
+    float* __restrict__ S = pbr.S;
+    float* __restrict__ Th = pbr.Th;
+    float* __restrict__ mu = pbr.mu;
+    const int32_t* __restrict__ perm = pbr.perm;
+    const int32_t* __restrict__ offs = pbr.offs;
+    const int64_t ldx = pbr.ldx, lds = pbr.lds, ldt = pbr.ldt;
+    const int d = pbr.d, n = pbr.n, c = pbr.c;
+    double* __restrict__ rpart = pbr.rpart;
+    const double kappa = pbr.kappa;
     if (phase == PH_FRO) {
+        // FP32 squares summed per lane, flushed to FP64 every 8 columns (the FP64
+        // pipe is far slower than the FP32 one)
         double acc = 0.0, bad = 0.0;
+        float fa = 0.f;
+        int cols = 0;
         for (int j = warp; j < n; j += kBW) {
 #pragma unroll
             for (int q = 0; q < KR; ++q) {
                 const int64_t r = r0 + lane + 32 * q;
                 if (r >= d) continue;
-                const float x = __ldg(pb.X + (int64_t)j * pb.ldx + r);
+                const float x = __ldg(X + (int64_t)j * ldx + r);
                 if (!isfinite(x)) bad += 1.0;
-                acc += (double)x * (double)x;
-                pb.L[(int64_t)j * pb.lds + r] = 0.f;
-                pb.S[(int64_t)j * pb.lds + r] = 0.f;
-                pb.Th[(int64_t)j * pb.ldt + r] = 0.f;
+                fa = fmaf(x, x, fa);
+                L[(int64_t)j * lds + r] = 0.f;
+                S[(int64_t)j * lds + r] = 0.f;
+                Th[(int64_t)j * ldt + r] = 0.f;
+            }
+            if (++cols == 8) {
+                acc += (double)fa;
+                fa = 0.f;
+                cols = 0;
             }
         }
+        acc += (double)fa;
         acc = block_sum(acc, sm.dred);
         bad = block_sum(bad, sm.dred);
         if (threadIdx.x == 0) {
-            pb.rpart[item * 3 + 0] = acc;
-            pb.rpart[item * 3 + 1] = bad;
+            rpart[item * 3 + 0] = acc;
+            rpart[item * 3 + 1] = bad;
         }
         return;
     }
-    // phases with cluster sums
+    // phases over the label-sorted columns: warp w streams positions
+    // [w n / 8, (w + 1) n / 8) of perm in groups of kRG, keeps the run sum of
+    // the current label per lane (FP32, into FP64 every 8 groups) and stores
+    // it to shared slot (label + w) when the label changes; labels never
+    // decrease inside a warp's range, so each (warp, label) pair has its own
+    // slot.  The slots of a label are then added in warp order.
     const float inv_rho = (float)(1.0 / rho);
-    const float inv_rho_next = (float)(1.0 / (rho * pb.kappa));   // D of the next iteration (PH_STHETA)
+    const float inv_rho_next = (float)(1.0 / (rho * kappa));   // D of the next iteration (PH_STHETA)
     const float rho_f = (float)fmin(rho, (double)FLT_MAX);
+    const double lam = pbr.lam;
+    const float a_f = (float)(rho / (2.0 * lam + rho)), b_f = (float)(2.0 * lam / (2.0 * lam + rho));
+    const bool sums = phase != PH_LSTEP;
     double r2 = 0.0, ds2 = 0.0;
-    for (int i = 0; i < pb.c; ++i) {
-        const int b = ldi(pb.offs + i), e = ldi(pb.offs + i + 1);
-        if (b == e) continue;                        // uniform over the CTA
-        float facc[KR];
-        double dacc[KR];
+    float r2f = 0.f, ds2f = 0.f;
+    const int p0 = (int)(((int64_t)warp * n) / kBW), p1 = (int)(((int64_t)(warp + 1) * n) / kBW);
+    int l = 0;                      // label of position p0 (uniform over the warp)
+    while (l + 1 < c && ldi(offs + l + 1) <= p0) ++l;
+    int lend = ldi(offs + l + 1);
+    if (lane == 0) {
+        sm.wlo[warp] = (p0 < p1) ? l : 1 << 30;
+        sm.whi[warp] = -1;
+    }
+    float mp[KR];                   // mu_p rows of the current label (PH_LSTEP)
+    auto load_mu = [&]() {
+#pragma unroll
+        for (int q = 0; q < KR; ++q) {
+            const int64_t r = r0 + lane + 32 * q;
+            mp[q] = (phase == PH_LSTEP && r < d) ? ldf(mu + (int64_t)l * d + r) : 0.f;
+        }
+    };
+    load_mu();
+    float facc[KR];
+    double dacc[KR];
+#pragma unroll
+    for (int q = 0; q < KR; ++q) {
+        facc[q] = 0.f;
+        dacc[q] = 0.0;
+    }
+    auto flush_run = [&]() {       // the run of label l ends
+        if (sums) {
+#pragma unroll
+            for (int q = 0; q < KR; ++q)
+                sm.slot[(l + warp) * kChunk + lane + 32 * q] = (float)(dacc[q] + (double)facc[q]);
+        }
 #pragma unroll
         for (int q = 0; q < KR; ++q) {
             facc[q] = 0.f;
             dacc[q] = 0.0;
         }
-        int cnt8 = 0;
-        for (int k = b + warp; k < e; k += kBW) {
-            const int64_t j = ldi(pb.perm + k);
+    };
+    int groups = 0;
+    for (int k0 = p0; k0 < p1; k0 += kRG) {
+        int64_t js[kRG];
+#pragma unroll
+        for (int g = 0; g < kRG; ++g) js[g] = (k0 + g < p1) ? (int64_t)ldi(perm + k0 + g) : -1;
+        // loads of the group (issued together)
+        float x[kRG][KR], s1[kRG][KR], s2[kRG][KR], s3[kRG][KR];
+#pragma unroll
+        for (int g = 0; g < kRG; ++g)
+#pragma unroll
+            for (int q = 0; q < KR; ++q) {
+                const int64_t r = r0 + lane + 32 * q;
+                const bool ok = js[g] >= 0 && r < d;
+                const int64_t j = js[g];
+                x[g][q] = (ok && phase != PH_MEANS_L) ? __ldg(X + j * ldx + r) : 0.f;
+                s1[g][q] = (ok && (phase == PH_MEANS_L || phase == PH_LSTEP || phase == PH_STHETA))
+                               ? ldf(L + j * lds + r) : 0.f;
+                s2[g][q] = (ok && phase != PH_MEANS_X && phase != PH_MEANS_L) ? ldf(S + j * lds + r) : 0.f;
+                s3[g][q] = (ok && phase != PH_MEANS_X && phase != PH_MEANS_L) ? ldf(Th + j * ldt + r) : 0.f;
+            }
+#pragma unroll
+        for (int g = 0; g < kRG; ++g) {
+            if (js[g] < 0) break;
+            const int k = k0 + g;
+            if (k >= lend) {        // label boundary (uniform over the warp)
+                flush_run();
+                while (k >= lend) {
+                    ++l;
+                    lend = ldi(offs + l + 1);
+                }
+                load_mu();
+            }
+            const int64_t j = js[g];
 #pragma unroll
             for (int q = 0; q < KR; ++q) {
                 const int64_t r = r0 + lane + 32 * q;
                 if (r >= d) continue;
-                const float x = __ldg(pb.X + j * pb.ldx + r);
                 float v;
                 if (phase == PH_MEANS_X) {
-                    v = x;
+                    v = x[g][q];
                 } else if (phase == PH_MEANS_L) {
-                    v = ldf(pb.L + j * pb.lds + r);
+                    v = s1[g][q];
                 } else if (phase == PH_SUMS_D) {
-                    v = (x - ldf(pb.S + j * pb.lds + r)) + ldf(pb.Th + j * pb.ldt + r) * inv_rho;
+                    v = (x[g][q] - s2[g][q]) + s3[g][q] * inv_rho;
+                } else if (phase == PH_LSTEP) {   // Eq. (18): L = a D + (1 - a) mu_p
+                    const float dv = (x[g][q] - s2[g][q]) + s3[g][q] * inv_rho;
+                    const float lv = fmaf(a_f, dv, b_f * mp[q]);
+                    r2f = fmaf(lv - s1[g][q], lv - s1[g][q], r2f);     // ||L_{t+1} - L_t||^2
+                    L[j * lds + r] = lv;
+                    v = 0.f;
                 } else {   // PH_STHETA: Eq. (24), Eq. (25) as clip(rho B, -1, 1), norms, next D
-                    const float l = ldf(pb.L + j * pb.lds + r);
-                    const float so = ldf(pb.S + j * pb.lds + r);
-                    const float t = ldf(pb.Th + j * pb.ldt + r);
-                    const float B = (x - l) + t * inv_rho;
+                    const float xl = x[g][q] - s1[g][q];
+                    const float B = xl + s3[g][q] * inv_rho;
                     const float mag = fabsf(B) - inv_rho;
                     const float sn = mag > 0.f ? copysignf(mag, B) : 0.f;
                     const float tn = fminf(1.f, fmaxf(-1.f, rho_f * B));
-                    const float res = (x - l) - sn;
-                    r2 += (double)(res * res);
-                    ds2 += (double)((sn - so) * (sn - so));
-                    pb.S[j * pb.lds + r] = sn;
-                    pb.Th[j * pb.ldt + r] = tn;
-                    v = (x - sn) + tn * inv_rho_next;
+                    const float res = xl - sn;
+                    r2f = fmaf(res, res, r2f);
+                    ds2f = fmaf(sn - s2[g][q], sn - s2[g][q], ds2f);
+                    S[j * lds + r] = sn;
+                    Th[j * ldt + r] = tn;
+                    v = (x[g][q] - sn) + tn * inv_rho_next;
                 }
                 facc[q] += v;
             }
-            if (++cnt8 == 8) {
-#pragma unroll
-                for (int q = 0; q < KR; ++q) {
-                    dacc[q] += (double)facc[q];
-                    facc[q] = 0.f;
-                }
-                cnt8 = 0;
-            }
         }
+        if (++groups == 8) {   // FP32 over 32 columns, then FP64
 #pragma unroll
-        for (int q = 0; q < KR; ++q) sm.it.red[warp][lane + 32 * q] = dacc[q] + (double)facc[q];
-        __syncthreads();
-        for (int t = threadIdx.x; t < KR * 32; t += kBT) {
-            const int64_t r = r0 + t;
-            if (r < d) {
-                double sum = 0.0;
-#pragma unroll
-                for (int w = 0; w < kBW; ++w) sum += sm.it.red[w][t];
-                pb.mu[(int64_t)i * d + r] = (float)(sum / (double)(e - b));
+            for (int q = 0; q < KR; ++q) {
+                dacc[q] += (double)facc[q];
+                facc[q] = 0.f;
             }
+            r2 += (double)r2f;
+            ds2 += (double)ds2f;
+            r2f = ds2f = 0.f;
+            groups = 0;
         }
-        __syncthreads();
     }
-    if (phase == PH_STHETA) {
+    if (p0 < p1) {
+        flush_run();
+        if (lane == 0) sm.whi[warp] = l;
+    }
+    r2 += (double)r2f;
+    ds2 += (double)ds2f;
+    __syncthreads();
+    if (sums) {
+        // mean of label i over rows: its slots (i + w) for the warps whose range held i
+        for (int e = threadIdx.x; e < c * KR * 32; e += kBT) {
+            const int i = e / (KR * 32), t = e - i * (KR * 32);
+            const int64_t r = r0 + t;
+            const int cnt = ldi(offs + i + 1) - ldi(offs + i);
+            if (cnt == 0 || r >= d) continue;
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < kBW; ++w)
+                if (sm.wlo[w] <= i && i <= sm.whi[w]) sum += (double)sm.slot[(i + w) * kChunk + t];
+            mu[(int64_t)i * d + r] = (float)(sum / (double)cnt);
+        }
+    }
+    __syncthreads();
+    if (phase == PH_STHETA || phase == PH_LSTEP) {
         r2 = block_sum(r2, sm.dred);
         ds2 = block_sum(ds2, sm.dred);
         if (threadIdx.x == 0) {
-            pb.rpart[item * 3 + 0] = r2;
-            pb.rpart[item * 3 + 1] = ds2;
+            rpart[item * 3 + 0] = r2;
+            rpart[item * 3 + 1] = ds2;
         }
     }
 }
 
 // ---------------------------------------------------------------- column items
 // Columns [item W, item W + W): warp w takes CPW = 64 / CMAX consecutive
-// columns; the rows are visited in chunks of 128 (lane l: rows l + 32 q),
-// with the chunk of every centroid staged in shared memory.  Squared
-// distances are summed per lane in FP32 (ceil(d/32) terms at most) and across
-// lanes in FP64, so each carries a relative error below
-// eps = (ceil(d/32) + 4) 2^-23; candidates whose distance lies within that
-// bound of the best one are re-decided in FP64 from the stored values (the
-// plain sum of squared differences, ties to the lowest index).
+// columns; the rows are visited in chunks of 128 (lane l: rows l + 32 q), with
+// the chunk of every centroid (or, for k-means++, of the centre column)
+// staged in shared memory.  Software pipelined one chunk ahead: the next
+// chunk's column values and staged values are loaded into registers while the
+// current chunk is computed.  Rows past d and columns past n read as 0 on
+// both sides, so they add nothing.  Squared distances are summed per lane in
+// FP32 (ceil(d/32) terms at most) and across lanes by an FP32 tree (FP64 runs
+// far slower), so each carries a relative error below eps = (ceil(d/32) + 9)
+// 2^-23; candidates whose distance
+// lies within that bound of the best one are re-decided in FP64 from the
+// stored values (the plain sum of squared differences, ties to the lowest
+// index).
 template <int CMAX>
-__device__ void col_item(const BProb& pb, double rho, int seed_k, int phase, int item, BSmem& sm) {
+__device__ void col_item(const BProb& pbr, int seed_k, int phase, int item, BSmem& sm) {
     constexpr int CPW = 64 / CMAX;
+    constexpr int NQ = kChunk / 32;
+    constexpr int MP = (CMAX * kChunk) / kBT;        // staged values per thread
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int d = pb.d, n = pb.n;
-    const bool seed = phase == PH_SEED, lstep = phase == PH_LSTEP;
-    const int ce = seed ? 1 : pb.c;
-    const int64_t center = seed ? (int64_t)ldi(pb.centers + seed_k) : 0;
+    const float* __restrict__ X = pbr.X;
+    const float* __restrict__ Lm = pbr.L;
+    const float* __restrict__ mu = pbr.mu;
+    int32_t* __restrict__ lbl = pbr.p;
+    double* __restrict__ D2 = pbr.D2;
+    double* __restrict__ cpart = pbr.cpart;
+    const int64_t ldx = pbr.ldx, lds = pbr.lds;
+    const int W = pbr.W;
+    const int d = pbr.d, n = pbr.n;
+    const bool seed = phase == PH_SEED, fromL = phase == PH_ASSIGN_L;
+    const int ce = seed ? 1 : pbr.c;
+    const int64_t center = seed ? (int64_t)ldi(pbr.centers + seed_k) : 0;
     unsigned long long amask = 0ull;
     if (!seed)
-        for (int i = 0; i < pb.c; ++i)
-            if (ldu8(pb.active + i)) amask |= 1ull << i;
-    const float a = (float)(rho / (2.0 * pb.lam + rho)), b = (float)(2.0 * pb.lam / (2.0 * pb.lam + rho));
-    const float inv_rho = (float)(1.0 / rho);
+        for (int i = 0; i < pbr.c; ++i)
+            if (ldu8(pbr.active + i)) amask |= 1ull << i;
     int64_t col[CPW];
     int lab[CPW];
     float acc[CPW][CMAX];
 #pragma unroll
     for (int k = 0; k < CPW; ++k) {
-        col[k] = (int64_t)item * pb.W + warp * CPW + k;
-        lab[k] = (col[k] < n && !seed) ? ldi(pb.p + col[k]) : 0;
+        col[k] = (int64_t)item * W + warp * CPW + k;
+        lab[k] = (col[k] < n && !seed) ? ldi(lbl + col[k]) : 0;
 #pragma unroll
         for (int i = 0; i < CMAX; ++i) acc[k][i] = 0.f;
     }
-    float dl = 0.f;
-    for (int64_t r0 = 0; r0 < d; r0 += kChunk) {
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < ce * kChunk; idx += kBT) {
+    float cur[CPW][NQ], nxt[CPW][NQ], mp[MP];
+    auto data_load = [&](int64_t r0, float (&v)[CPW][NQ]) {
+#pragma unroll
+        for (int k = 0; k < CPW; ++k)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int64_t r = r0 + lane + 32 * q;
+                const bool ok = col[k] < n && r < d;
+                v[k][q] = !ok ? 0.f : (fromL ? ldf(Lm + col[k] * lds + r) : __ldg(X + col[k] * ldx + r));
+            }
+    };
+    auto stage_load = [&](int64_t r0) {
+#pragma unroll
+        for (int u = 0; u < MP; ++u) {
+            const int idx = threadIdx.x + u * kBT;
             const int i = idx / kChunk, t = idx - i * kChunk;
             const int64_t r = r0 + t;
             float v = 0.f;
-            if (r < d) v = seed ? __ldg(pb.X + center * pb.ldx + r) : ldf(pb.mu + (int64_t)i * d + r);
-            sm.it.cs[idx] = v;
+            if (i < ce && r < d) v = seed ? __ldg(X + center * ldx + r) : ldf(mu + (int64_t)i * d + r);
+            mp[u] = v;
         }
-        __syncthreads();
+    };
+    auto stage_store = [&]() {
 #pragma unroll
-        for (int k = 0; k < CPW; ++k) {
-            const int64_t j = col[k];
-            if (j >= n) continue;
+        for (int u = 0; u < MP; ++u) sm.it.cs[threadIdx.x + u * kBT] = mp[u];
+    };
+    data_load(0, cur);
+    stage_load(0);
+    stage_store();
+    __syncthreads();
+    for (int64_t r0 = 0; r0 < d; r0 += kChunk) {
+        const bool more = r0 + kChunk < d;
+        if (more) {
+            data_load(r0 + kChunk, nxt);
+            stage_load(r0 + kChunk);
+        }
 #pragma unroll
-            for (int q = 0; q < kChunk / 32; ++q) {
-                const int t = lane + 32 * q;
-                const int64_t r = r0 + t;
-                if (r >= d) continue;
-                float y;
-                if (lstep) {   // Eq. (18): L = a D + (1 - a) mu_p, D = X - S + Theta/rho
-                    const float x = __ldg(pb.X + j * pb.ldx + r);
-                    const float sv = ldf(pb.S + j * pb.lds + r);
-                    const float tv = ldf(pb.Th + j * pb.ldt + r);
-                    const float dv = (x - sv) + tv * inv_rho;
-                    const float l = fmaf(a, dv, b * sm.it.cs[lab[k] * kChunk + t]);
-                    const float lo = ldf(pb.L + j * pb.lds + r);
-                    dl = fmaf(l - lo, l - lo, dl);
-                    pb.L[j * pb.lds + r] = l;
-                    y = l;
-                } else if (phase == PH_ASSIGN_L) {
-                    y = ldf(pb.L + j * pb.lds + r);
-                } else {
-                    y = __ldg(pb.X + j * pb.ldx + r);
-                }
+        for (int q = 0; q < NQ; ++q) {
+            const int t = lane + 32 * q;
 #pragma unroll
-                for (int i = 0; i < CMAX; ++i) {
-                    if (i < ce) {
-                        const float df = y - sm.it.cs[i * kChunk + t];
+            for (int i = 0; i < CMAX; ++i) {
+                if (i < ce) {
+                    const float m = sm.it.cs[i * kChunk + t];
+#pragma unroll
+                    for (int k = 0; k < CPW; ++k) {
+                        const float df = cur[k][q] - m;
                         acc[k][i] = fmaf(df, df, acc[k][i]);
                     }
                 }
             }
         }
+        __syncthreads();
+        if (more) {
+            stage_store();
+#pragma unroll
+            for (int k = 0; k < CPW; ++k)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) cur[k][q] = nxt[k][q];
+        }
+        __syncthreads();
     }
-    const double eps = (double)((d + 31) / 32 + 4) * 1.1920928955078125e-7;
+    // per-lane FP32 sums (ceil(d/32) terms), a 5-level FP32 tree across lanes
+    const double eps = (double)((d + 31) / 32 + 9) * 1.1920928955078125e-7;
     double changes = 0.0;
 #pragma unroll
     for (int k = 0; k < CPW; ++k) {
@@ -407,7 +543,7 @@ __device__ void col_item(const BProb& pb, double rho, int seed_k, int phase, int
 #pragma unroll
         for (int i = 0; i < CMAX; ++i) {
             if (i < ce) {
-                const double v = warp_sum((double)acc[k][i]);
+                const double v = (double)warp_sum(acc[k][i]);
                 if (lane == (i & 31)) mine[i >> 5] = v;
             }
         }
@@ -415,7 +551,7 @@ __device__ void col_item(const BProb& pb, double rho, int seed_k, int phase, int
         if (seed) {
             if (lane == 0) {
                 const double v = mine[0];
-                pb.D2[j] = (seed_k == 0) ? v : fmin(ldd(pb.D2 + j), v);
+                D2[j] = (seed_k == 0) ? v : fmin(ldd(D2 + j), v);
             }
             continue;
         }
@@ -458,9 +594,8 @@ __device__ void col_item(const BProb& pb, double rho, int seed_k, int phase, int
                 m &= m - 1;
                 double sacc = 0.0;
                 for (int64_t r = lane; r < d; r += 32) {
-                    const double y = (phase == PH_ASSIGN_X) ? (double)__ldg(pb.X + j * pb.ldx + r)
-                                                            : (double)ldf(pb.L + j * pb.lds + r);
-                    const double df = y - (double)ldf(pb.mu + (int64_t)i * d + r);
+                    const double y = fromL ? (double)ldf(Lm + j * lds + r) : (double)__ldg(X + j * ldx + r);
+                    const double df = y - (double)ldf(mu + (int64_t)i * d + r);
                     sacc += df * df;
                 }
                 sacc = warp_sum(sacc);
@@ -473,18 +608,16 @@ __device__ void col_item(const BProb& pb, double rho, int seed_k, int phase, int
         }
         if (bi < 0) bi = lab[k] >= 0 ? lab[k] : 0;   // no active centroid cannot occur; keep labels in range
         if (lane == 0) {
-            if (lstep) pb.pstart[j] = lab[k];
             if (bi != lab[k]) {
-                pb.p[j] = bi;
+                lbl[j] = bi;
                 changes += 1.0;
             }
         }
     }
-    const double dls = block_sum((double)dl, sm.dred);
     changes = block_sum(changes, sm.dred);
     if (threadIdx.x == 0) {
-        pb.cpart[item * 2 + 0] = dls;
-        pb.cpart[item * 2 + 1] = changes;
+        cpart[item * 2 + 0] = 0.0;
+        cpart[item * 2 + 1] = changes;
     }
 }
 
@@ -590,7 +723,6 @@ __device__ unsigned items_of(const BProb& pb, int phase) {
     switch (phase) {
         case PH_SEED:
         case PH_ASSIGN_X:
-        case PH_LSTEP:
         case PH_ASSIGN_L: return (unsigned)pb.col_items;
         case PH_DONE: return 0u;
         default: return (unsigned)pb.row_items;
@@ -668,13 +800,18 @@ __device__ void phase_tail(const BProb& pb, BCtl* gctl, BGlobal* g, int phase, B
                 sm.next = PH_ASSIGN_X;
             }
         }
-    } else if (phase == PH_ASSIGN_X || phase == PH_LSTEP || phase == PH_ASSIGN_L) {
+    } else if (phase == PH_LSTEP) {
+        // the labels the p step starts from
+        for (int j = t; j < n; j += kBT) pb.pstart[j] = ldi(pb.p + j);
+        if (t == 0) {
+            ctl.dl2 = item_sum(pb.rpart, pb.row_items, 3, 0);
+            ctl.passes = 0;
+            sm.next = PH_ASSIGN_L;
+        }
+    } else if (phase == PH_ASSIGN_X || phase == PH_ASSIGN_L) {
         if (t == 0) {
             const double ch = item_sum(pb.cpart, pb.col_items, 2, 1);
-            if (phase == PH_LSTEP) {
-                ctl.dl2 = item_sum(pb.cpart, pb.col_items, 2, 0);
-                ctl.passes = 1;
-            } else if (phase == PH_ASSIGN_L) {
+            if (phase == PH_ASSIGN_L) {
                 ctl.passes += 1;
             } else {
                 ctl.init_passes += 1;
@@ -800,11 +937,10 @@ __global__ void __launch_bounds__(kBT, MINB)
         switch (phase) {
             case PH_SEED:
             case PH_ASSIGN_X:
-            case PH_LSTEP:
             case PH_ASSIGN_L:
-                if (pb.cmax <= 16) col_item<16>(pb, rho, seed_k, phase, item, sm);
-                else if (pb.cmax <= 32) col_item<32>(pb, rho, seed_k, phase, item, sm);
-                else col_item<64>(pb, rho, seed_k, phase, item, sm);
+                if (pb.cmax <= 16) col_item<16>(pb, seed_k, phase, item, sm);
+                else if (pb.cmax <= 32) col_item<32>(pb, seed_k, phase, item, sm);
+                else col_item<64>(pb, seed_k, phase, item, sm);
                 break;
             default:
                 if (KR == 2) row_item<2>(pb, rho, phase, item, sm);

@@ -74,7 +74,9 @@ def test_persistent_batch_matches_oracle_fixed_iterations(solver):
         assert st["init_lloyd_passes"] == rs["init_lloyd_steps"]
         np.testing.assert_array_equal(q["p"].cpu().numpy(), ref.labels)
         _check_state(_host(q["L"]), _host(q["S"]), ref, X64)
-        assert st["x_norm"] == pytest.approx(np.linalg.norm(X64), rel=1e-12)
+        # FP32 squares in per-lane partial sums of at most 32 terms, then FP64:
+        # relative error below 33 * 2^-24
+        assert st["x_norm"] == pytest.approx(np.linalg.norm(X64), rel=2e-6)
 
 
 def test_persistent_batch_to_tolerance(solver):
