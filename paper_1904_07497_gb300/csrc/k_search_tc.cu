@@ -1582,7 +1582,12 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                           (reinterpret_cast<uintptr_t>(mu_lo) % 16 == 0);
     const int64_t list_max = n / 4;   // larger queued lists use the dense kernel
     bool dense_launched = false;
-    if (dense_ok && Npad <= 128 && mu_a && (reinterpret_cast<uintptr_t>(mu_a) % 16 == 0)) {
+    // The start event goes into the stream before the host-side preparation of
+    // the launch (tensor-map encoding, attributes), so that it is reached while
+    // the preceding kernel still runs and brackets this kernel, not the host.
+    const bool dense_t_path = dense_ok && Npad <= 128 && mu_a && (reinterpret_cast<uintptr_t>(mu_a) % 16 == 0);
+    if (ev_dense0 && dense_ok) cudaEventRecord(ev_dense0, st);
+    if (dense_t_path) {
         CUtensorMap tmY, tmA;
         const DenseTPlan dp = dense_t_plan(n, d, Npad);
         if (encode_2d(&tmY, static_cast<const float*>(Y), d, n, ldy, kTcK, kTtN) &&
@@ -1602,7 +1607,6 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_search_dense_t));
             if (e != cudaSuccess) return e;
             count_launches(1);
-            if (ev_dense0) cudaEventRecord(ev_dense0, st);
             k_search_dense_t<<<dp.G, kTtThreads, dp.smem, st>>>(tmY, tmA, a, status, mu_normf, counts, c,
                                                                 labels, ub, lb, Gpart, ynorm_part,
                                                                 tile_count, rc_list);
@@ -1639,7 +1643,6 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_search_dense));
             if (e != cudaSuccess) return e;
             count_launches(1);
-            if (ev_dense0) cudaEventRecord(ev_dense0, st);
             k_search_dense<<<dp.G, kDnThreads, dp.smem, st>>>(tmY, tmBh, tmBl, a, status, mu_normf,
                                                               counts, c, labels, ub, lb, Gpart,
                                                               ynorm_part, tile_count, rc_list);
