@@ -233,7 +233,8 @@ respca_status respca_solve_batched(respca_handle h, int32_t batch, const respca_
 
 /* Options and results of respca_solve_batched_persistent. */
 typedef struct {
-    int32_t tile_rows;          /* in: rows per row-block work item, 64 or 128; 0 = autotuned */
+    int32_t tile_rows;          /* in: rows per row-block work item, 64 or 128; 0 = autotuned
+                                   (with two CTAs per SM the items are 64 rows) */
     int32_t ctas_per_sm;        /* in: resident CTAs per SM, 1 or 2; 0 = autotuned */
     int64_t spin_limit;         /* in: empty polls of the work queue after which a CTA gives up
                                    (RESPCA_ERR_TIMEOUT); 0 = default (2^23, about a second or more) */

@@ -439,11 +439,11 @@ __device__ void row_item(const BProb& pbr, double rho, int phase, int item, BSme
 // lies within that bound of the best one are re-decided in FP64 from the
 // stored values (the plain sum of squared differences, ties to the lowest
 // index).
-template <int CMAX>
+template <int CMAX, int CPW, bool PREF>
 __device__ void col_item(const BProb& pbr, int seed_k, int phase, int item, BSmem& sm) {
-    constexpr int CPW = 64 / CMAX;
     constexpr int NQ = kChunk / 32;
-    constexpr int MP = (CMAX * kChunk) / kBT;        // staged values per thread
+    constexpr int MS = (CMAX * kChunk) / kBT;        // staged values per thread
+    constexpr int MP = PREF ? MS : 1;                // of them prefetched into registers
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float* __restrict__ X = pbr.X;
     const float* __restrict__ Lm = pbr.L;
@@ -497,15 +497,31 @@ __device__ void col_item(const BProb& pbr, int seed_k, int phase, int item, BSme
 #pragma unroll
         for (int u = 0; u < MP; ++u) sm.it.cs[threadIdx.x + u * kBT] = mp[u];
     };
+    // without the prefetch (too many registers), the chunk is staged directly
+    auto stage_direct = [&](int64_t r0) {
+#pragma unroll 4
+        for (int u = 0; u < MS; ++u) {
+            const int idx = threadIdx.x + u * kBT;
+            const int i = idx / kChunk, t = idx - i * kChunk;
+            const int64_t r = r0 + t;
+            float v = 0.f;
+            if (i < ce && r < d) v = seed ? __ldg(X + center * ldx + r) : ldf(mu + (int64_t)i * d + r);
+            sm.it.cs[idx] = v;
+        }
+    };
     data_load(0, cur);
-    stage_load(0);
-    stage_store();
+    if (PREF) {
+        stage_load(0);
+        stage_store();
+    } else {
+        stage_direct(0);
+    }
     __syncthreads();
     for (int64_t r0 = 0; r0 < d; r0 += kChunk) {
         const bool more = r0 + kChunk < d;
         if (more) {
             data_load(r0 + kChunk, nxt);
-            stage_load(r0 + kChunk);
+            if (PREF) stage_load(r0 + kChunk);
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -524,7 +540,8 @@ __device__ void col_item(const BProb& pbr, int seed_k, int phase, int item, BSme
         }
         __syncthreads();
         if (more) {
-            stage_store();
+            if (PREF) stage_store();
+            else stage_direct(r0 + kChunk);
 #pragma unroll
             for (int k = 0; k < CPW; ++k)
 #pragma unroll
@@ -938,12 +955,23 @@ __global__ void __launch_bounds__(kBT, MINB)
             case PH_SEED:
             case PH_ASSIGN_X:
             case PH_ASSIGN_L:
-                if (pb.cmax <= 16) col_item<16>(pb, seed_k, phase, item, sm);
-                else if (pb.cmax <= 32) col_item<32>(pb, seed_k, phase, item, sm);
-                else col_item<64>(pb, seed_k, phase, item, sm);
+                // columns per warp: 64 / CMAX with one CTA per SM, half that with two
+                // (the register budget halves); must match cpw_of on the host
+                if (pb.cmax <= 16) {
+                    if (MINB == 1) col_item<16, 4, true>(pb, seed_k, phase, item, sm);
+                    else col_item<16, 2, true>(pb, seed_k, phase, item, sm);
+                } else if (pb.cmax <= 32) {
+                    if (MINB == 1) col_item<32, 2, true>(pb, seed_k, phase, item, sm);
+                    else col_item<32, 1, true>(pb, seed_k, phase, item, sm);
+                } else {
+                    if (MINB == 1) col_item<64, 1, true>(pb, seed_k, phase, item, sm);
+                    else col_item<64, 1, false>(pb, seed_k, phase, item, sm);
+                }
                 break;
             default:
-                if (KR == 2) row_item<2>(pb, rho, phase, item, sm);
+                // two CTAs per SM take 64-row items only (the 128-row form's loads
+                // do not fit their registers)
+                if (MINB == 2 || KR == 2) row_item<2>(pb, rho, phase, item, sm);
                 else row_item<4>(pb, rho, phase, item, sm);
                 break;
         }
@@ -991,6 +1019,9 @@ cudaError_t hgrow(HBuf& b, size_t bytes, bool pinned) {
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int cmax_of(int c) { return c <= 16 ? 16 : (c <= 32 ? 32 : 64); }
+
+// Columns per warp of a column item (the kernel's choice for MINB CTAs per SM).
+int cpw_of(int cmax, int minb) { return minb == 1 ? 64 / cmax : std::max(1, 32 / cmax); }
 
 struct Tuned {
     uint64_t key;
@@ -1041,15 +1072,15 @@ uint64_t fnv(uint64_t h, uint64_t v) { return (h ^ v) * 1099511628211ULL; }
 
 // Workspace offsets of every problem (sized for the smallest row block, so
 // every tile choice fits) and the table for one tile choice.
-size_t layout(int32_t batch, const respca_problem* probs, char* base, int kr, int iter_cap, int km_max,
-              double kappa, const double* draws, BProb* out) {
+size_t layout(int32_t batch, const respca_problem* probs, char* base, int kr, int minb, int iter_cap,
+              int km_max, double kappa, const double* draws, BProb* out) {
     size_t off = 0;
     for (int32_t b = 0; b < batch; ++b) {
         const respca_problem& q = probs[b];
         const int64_t d = q.d, n = q.n;
         const int c = q.c;
         const int cm = cmax_of(c);
-        const int W = 8 * (64 / cm);
+        const int W = 8 * cpw_of(cm, minb);
         const int rows_min = 64;
         const int64_t ri_max = (d + rows_min - 1) / rows_min;
         const int64_t ci = (n + W - 1) / W;
@@ -1162,7 +1193,8 @@ respca_status batched_persistent(BatchedState** sp, int device, cudaStream_t st,
         S.attrs_set = true;
     }
     // device memory: workspace, the k-means++ draws (the same seed as the single path)
-    const size_t wbytes = layout(batch, probs, nullptr, 2, -1, ra.km_max, kappa, nullptr, nullptr);
+    // sized for the smallest items (64 rows, the narrower column items of two CTAs per SM)
+    const size_t wbytes = layout(batch, probs, nullptr, 2, 2, -1, ra.km_max, kappa, nullptr, nullptr);
     BK(hgrow(S.work, wbytes, false));
     BK(hgrow(S.draws, sizeof(double) * kMaxC, false));
     BK(hgrow(S.dprobs, sizeof(BProb) * batch, false));
@@ -1190,7 +1222,8 @@ respca_status batched_persistent(BatchedState** sp, int device, cudaStream_t st,
     const double* du = static_cast<const double*>(S.draws.p);
     // one launch of the whole batch with tile rows 32 kr, minb CTAs per SM
     auto run = [&](int kr, int minb, int iter_cap, bool use_graph, float* ms) -> respca_status {
-        layout(batch, probs, static_cast<char*>(S.work.p), kr, iter_cap, ra.km_max, kappa, du, hp);
+        if (minb == 2) kr = 2;
+        layout(batch, probs, static_cast<char*>(S.work.p), kr, minb, iter_cap, ra.km_max, kappa, du, hp);
         for (int32_t b = 0; b < batch; ++b) {
             std::memset(&hc[b], 0, sizeof(BCtl));
             hc[b].claim = ((unsigned long long)1 << 48) | ((unsigned long long)(hp[b].row_items & 0xFFFFFF) << 24);
@@ -1293,6 +1326,7 @@ respca_status batched_persistent(BatchedState** sp, int device, cudaStream_t st,
                 if (kr && ck != kr) continue;
                 for (int cm : {1, 2}) {
                     if (minb && cm != minb) continue;
+                    if (cm == 2 && ck == 4) continue;   // two CTAs per SM take 64-row items
                     float ms = 0.f;
                     respca_status rs = run(ck, cm, 3, false, &ms);
                     if (rs != RESPCA_OK) return rs;
@@ -1310,6 +1344,7 @@ respca_status batched_persistent(BatchedState** sp, int device, cudaStream_t st,
             S.tuned.push_back(Tuned{skey, kr, minb});
         }
     }
+    if (minb == 2) kr = 2;
     float ms = 0.f;
     respca_status rs = run(kr, minb, -1, true, &ms);
     if (rs != RESPCA_OK) return rs;
