@@ -555,7 +555,8 @@ def run_batched(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": "k_batched (one persistent launch over all problems); "
                      "algorithmic bytes = 28 B x elements x iterations summed over the batch",
                      "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                     "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_source": peak_kind, "traffic": kernel_traffic("k_batched.cu", "k_batched_c4.txt"),
+                     "algorithmic_bytes_per_launch": alg_bytes,
                      "avg_launch_ms": round(opt.ms_kernel, 3), "launches": 1},
         "cpu_baseline": None, "e2e": None,
         "gpu_launches": sum(s["kernel_launches"] for s in st), "clocks": clk,
