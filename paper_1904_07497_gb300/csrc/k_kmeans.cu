@@ -406,6 +406,172 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// One k-means++ step in one launch: D2 against centre k (as k_seed_dist, one
+// warp per column, grid = ceil(n / 8) so each warp takes one column), then
+// centre kpick (kpick < 0: none) picked by the CTA that finishes last.  Each
+// CTA writes the sum of its 8 columns' D2 (in column order) to part[b]; the
+// last one (an atomic count of finished CTAs, reset for the next launch) finds
+// the first column whose running sum exceeds u[kpick] times the total: the
+// crossing block from the block sums (each thread scans a contiguous range
+// of blocks, ranges in order), then the column inside it.  If rounding leaves
+// no crossing, the last column with D2 > 0; with D2 all zero, floor(u n).
+template <typename TX, bool VEC>
+__global__ void __launch_bounds__(kThreads)
+    k_seed_step(const TX* __restrict__ X, int64_t ldx, int64_t d, int64_t n,
+                int32_t* __restrict__ centers, int k, int kpick, const double* __restrict__ u,
+                double* __restrict__ D2, double* __restrict__ part, int32_t* __restrict__ done) {
+    constexpr int W = kThreads / 32;
+    __shared__ double colv[W];
+    __shared__ double tsum[kThreads + 1];
+    __shared__ long long s_block, s_pick;
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t ctr = centers[k];
+    const TX* xc = X + ctr * ldx;
+    const int64_t j = (int64_t)blockIdx.x * W + warp;
+    double v = 0.0;
+    if (j < n) {
+        const TX* xj = X + j * ldx;
+        float s = 0.f, comp = 0.f;
+        if (VEC) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int64_t r0 = lane * 4; r0 < d; r0 += 2 * 32 * 8) {
+                float4 a[4], bq[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int64_t r = r0 + h * 128;
+                    a[h] = r < d ? XLoad<TX>::four(xj + r) : z;
+                    bq[h] = r < d ? XLoad<TX>::four(xc + r) : z;
+                }
+#pragma unroll
+                for (int st = 0; st < 2; ++st) {
+                    if (r0 + st * 256 >= d) break;
+                    float part8 = 0.f, t;
+                    const float4 a0 = a[2 * st], b0 = bq[2 * st], a1 = a[2 * st + 1], b1 = bq[2 * st + 1];
+                    t = a0.x - b0.x; part8 = fmaf(t, t, part8);
+                    t = a0.y - b0.y; part8 = fmaf(t, t, part8);
+                    t = a0.z - b0.z; part8 = fmaf(t, t, part8);
+                    t = a0.w - b0.w; part8 = fmaf(t, t, part8);
+                    t = a1.x - b1.x; part8 = fmaf(t, t, part8);
+                    t = a1.y - b1.y; part8 = fmaf(t, t, part8);
+                    t = a1.z - b1.z; part8 = fmaf(t, t, part8);
+                    t = a1.w - b1.w; part8 = fmaf(t, t, part8);
+                    const float y = part8 - comp;
+                    const float uu = s + y;
+                    comp = (uu - s) - y;
+                    s = uu;
+                }
+            }
+        } else {
+            for (int64_t r0 = 0; r0 < d; r0 += 32 * 8) {
+                float part8 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int64_t r = r0 + q * 32 + lane;
+                    if (r < d) {
+                        const float t = XLoad<TX>::one(xj + r) - XLoad<TX>::one(xc + r);
+                        part8 = fmaf(t, t, part8);
+                    }
+                }
+                const float y = part8 - comp;
+                const float uu = s + y;
+                comp = (uu - s) - y;
+                s = uu;
+            }
+        }
+        v = warp_sum((double)s);
+        if (k > 0) v = fmin(D2[j], v);
+        if (lane == 0) D2[j] = v;
+    }
+    if (kpick < 0) return;
+    __threadfence();   // this warp's D2 is visible before the CTA counts as finished
+    if (lane == 0) colv[warp] = (j < n) ? v : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < W; ++w) b += colv[w];
+        part[blockIdx.x] = b;
+        __threadfence();
+        s_last = (atomicAdd(done, 1) == (int)gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last CTA: the pick
+    const int64_t nb = gridDim.x;
+    const int64_t chunk = (nb + kThreads - 1) / kThreads;
+    const int64_t b0 = min(nb, (int64_t)threadIdx.x * chunk), b1 = min(nb, b0 + chunk);
+    double t = 0.0;
+    for (int64_t b = b0; b < b1; ++b) t += __ldcg(part + b);
+    tsum[threadIdx.x] = t;
+    if (threadIdx.x == 0) {
+        *done = 0;
+        s_block = LLONG_MAX;
+        s_pick = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // exclusive prefix over the threads' ranges, in order
+        double run = 0.0;
+        for (int q = 0; q < kThreads; ++q) {
+            const double x = tsum[q];
+            tsum[q] = run;
+            run += x;
+        }
+        tsum[kThreads] = run;
+    }
+    __syncthreads();
+    const double total = tsum[kThreads];
+    const double uk = u[kpick];
+    if (!(total > 0.0)) {
+        if (threadIdx.x == 0) {
+            int64_t pk = (int64_t)(uk * (double)n);
+            centers[kpick] = (int32_t)(pk >= n ? n - 1 : pk);
+        }
+        return;
+    }
+    const double target = uk * total;
+    double cum = tsum[threadIdx.x];
+    for (int64_t b = b0; b < b1; ++b) {
+        const double pb = __ldcg(part + b);
+        if (cum + pb > target) {
+            atomicMin(&s_block, (long long)b);
+            break;
+        }
+        cum += pb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long pick = -1;
+        if (s_block != LLONG_MAX) {
+            // running sum up to the crossing block, in the same order as above
+            const int64_t bq = s_block;
+            const int owner = (int)(bq / chunk);
+            double c2 = tsum[owner];
+            for (int64_t b = (int64_t)owner * chunk; b < bq; ++b) c2 += __ldcg(part + b);
+            long long lastpos = -1;
+            for (int64_t jj = bq * W; jj < min(n, (bq + 1) * (int64_t)W); ++jj) {
+                const double dj = __ldcg(D2 + jj);
+                if (dj > 0.0) lastpos = jj;
+                c2 += dj;
+                if (c2 > target) {
+                    pick = jj;
+                    break;
+                }
+            }
+            // the block's sum crossed but its running sum did not (rounding): the
+            // crossing is at the block's end
+            if (pick < 0) pick = lastpos;
+        }
+        if (pick < 0)
+            for (int64_t jj = n - 1; jj >= 0; --jj)
+                if (__ldcg(D2 + jj) > 0.0) {
+                    pick = jj;
+                    break;
+                }
+        centers[kpick] = (int32_t)(pick < 0 ? n - 1 : pick);
+    }
+}
+
 // Pick centre k: the first column whose running sum of D2 exceeds u_k times
 // the total (single CTA; FP64 block scans in column order).
 __global__ void __launch_bounds__(1024)
@@ -545,6 +711,24 @@ cudaError_t launch_seed_dist(int dtype, const void* X, int64_t ldx, int64_t d, i
             k_seed_dist<TX, true><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, centers, k, D2);
         else
             k_seed_dist<TX, false><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, centers, k, D2);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_step(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n, int32_t* centers,
+                             int k, int kpick, const double* u, double* D2, double* part, int32_t* done,
+                             cudaStream_t st) {
+    count_launches(1);
+    const int grid = grid_for(n, kThreads / 32);
+    RESPCA_DISPATCH_X(dtype, TX, {
+        const bool vec = (ldx % 4 == 0) && (d % 4 == 0) &&
+                         (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(TX)) == 0);
+        if (vec)
+            k_seed_step<TX, true><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, centers, k, kpick, u, D2,
+                                                             part, done);
+        else
+            k_seed_step<TX, false><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, centers, k, kpick, u, D2,
+                                                              part, done);
     });
     return cudaGetLastError();
 }

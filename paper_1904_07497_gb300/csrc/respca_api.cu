@@ -64,7 +64,7 @@ struct respca_ctx {
 
     // device workspace, grown on demand
     DevBuf theta, mu, mu_norm2, mu_normf, pair_ss, sep2, perm, counts, tile_off, tiles, labels_prev,
-        Dpart, own_part, norm_part, flag_list, seedD2, centers, seed_u, fro_part, status,
+        Dpart, own_part, norm_part, flag_list, seedD2, seed_part, centers, seed_u, fro_part, status,
         hX, hL, hS, hp, hp0,
         mu_next, mu_old, drift, ub, lb, dl_part, sums, moved, contrib, boff, labels_pass,
         mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count, rc_dist,
@@ -126,7 +126,8 @@ size_t elem_size(int dtype) { return dtype == RESPCA_F32 ? 4 : 2; }
 std::vector<DevBuf*> all_bufs(respca_ctx* h) {
     return {&h->theta, &h->mu, &h->mu_norm2, &h->mu_normf, &h->pair_ss, &h->sep2, &h->perm,
                       &h->counts, &h->tile_off, &h->tiles, &h->labels_prev, &h->Dpart, &h->own_part,
-                      &h->norm_part, &h->flag_list, &h->seedD2, &h->centers, &h->seed_u, &h->fro_part,
+                      &h->norm_part, &h->flag_list, &h->seedD2, &h->seed_part, &h->centers, &h->seed_u,
+                      &h->fro_part,
                       &h->status, &h->hX, &h->hL, &h->hS, &h->hp, &h->hp0, &h->mu_next, &h->mu_old,
                       &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->contrib, &h->boff,
                       &h->labels_pass,
@@ -157,6 +158,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
     CK(ensure(h->norm_part, sizeof(double) * 3 * (size_t)mt * nch));
     CK(ensure(h->flag_list, sizeof(int32_t) * n));
     CK(ensure(h->seedD2, sizeof(double) * n));
+    CK(ensure(h->seed_part, sizeof(double) * ((n + 7) / 8 + 1)));
     CK(ensure(h->centers, sizeof(int32_t) * c));
     CK(ensure(h->seed_u, sizeof(double) * c));
     CK(ensure(h->fro_part, sizeof(double) * kFroParts));
@@ -653,15 +655,12 @@ respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out
     if (first >= pb.n) first = (int)pb.n - 1;
     CK(cudaMemcpyAsync(h->seed_u.p, h->hseed_u, sizeof(double) * c, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->centers.p, &first, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
-    CK(launch_seed_dist(pb.dtype, pb.X, pb.ldx, pb.d, pb.n, P<int32_t>(h->centers), 0,
-                        P<double>(h->seedD2), h->stream));
-    for (int k = 1; k < c; ++k) {
-        CK(launch_seed_pick(P<double>(h->seedD2), pb.n, P<double>(h->seed_u), k, P<int32_t>(h->centers),
-                            h->stream));
-        if (k + 1 < c)
-            CK(launch_seed_dist(pb.dtype, pb.X, pb.ldx, pb.d, pb.n, P<int32_t>(h->centers), k,
-                                P<double>(h->seedD2), h->stream));
-    }
+    // step k: D2 against centre k, then the pick of centre k + 1 (one launch)
+    CK(cudaMemsetAsync(&P<DevStatus>(h->status)->seed_done, 0, sizeof(int32_t), h->stream));
+    for (int k = 0; k + 1 < c; ++k)
+        CK(launch_seed_step(pb.dtype, pb.X, pb.ldx, pb.d, pb.n, P<int32_t>(h->centers), k, k + 1,
+                            P<double>(h->seed_u), P<double>(h->seedD2), P<double>(h->seed_part),
+                            &P<DevStatus>(h->status)->seed_done, h->stream));
     CK(launch_gather_centers(pb.dtype, pb.X, pb.ldx, pb.d, P<int32_t>(h->centers), c, P<float>(h->mu),
                              P<int32_t>(h->counts), h->stream));
     CK(launch_mu_stats(P<float>(h->mu), nullptr, c, pb.d, P<double>(h->mu_norm2), P<float>(h->mu_normf),

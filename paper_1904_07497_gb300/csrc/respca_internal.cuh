@@ -67,6 +67,7 @@ struct DevStatus {
     int64_t acc_flagged;    // device-run Lloyd loop: columns searched over its passes
     int32_t acc_passes;     //   passes run (including those before the loop)
     int32_t acc_rechecked;  //   near ties re-decided
+    int32_t seed_done;      // CTAs of the current k-means++ step that finished (reset by the last)
 };
 
 // Modes of the bound-based pruning kernel.
@@ -82,6 +83,11 @@ inline void count_launches(int k) { t_kernel_launches += k; }
 
 // ---------------------------------------------------------------- launchers
 // (each returns the launch status; all run on `st`)
+// One k-means++ step: D2 against centre k, then centre kpick (< 0: none)
+// picked by the CTA that finishes last.  part: ceil(n / 8) doubles.
+cudaError_t launch_seed_step(int dtype, const void* X, int64_t ldx, int64_t d, int64_t n, int32_t* centers,
+                             int k, int kpick, const double* u, double* D2, double* part, int32_t* done,
+                             cudaStream_t st);
 cudaError_t launch_fro2(int dtype, const void* X, int64_t d, int64_t n, int64_t ldx,
                         double* part, int nparts, DevStatus* status, cudaStream_t st);
 
