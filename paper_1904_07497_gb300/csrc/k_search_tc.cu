@@ -206,8 +206,11 @@ __device__ __forceinline__ void named_sync(int id, int threads) {
 
 // Score rounding bound of centroid i for a column y: e_i = kTieRelTc *
 // (2 ||mu_i|| ||y|| + ||mu_i||^2) (Cauchy-Schwarz on the products' error).
-__device__ __forceinline__ float score_err(float mu2, float y2) {
-    return kTieRelTc * (2.f * sqrtf(fmaxf(mu2, 0.f) * y2) + fabsf(mu2));
+// When the products use y truncated to TF32 (no y_lo term), ylo bounds
+// ||y - tf32(y)|| and |mu_i . (y - tf32(y))| <= ||mu_i|| ylo adds 2 ||mu_i|| ylo.
+__device__ __forceinline__ float score_err(float mu2, float y2, float ylo = 0.f) {
+    const float mn = sqrtf(fmaxf(mu2, 0.f));
+    return kTieRelTc * (2.f * mn * sqrtf(y2) + fabsf(mu2)) + 2.f * mn * ylo;
 }
 
 // Dot products g_i0 .. g_i0+7 of one column: sums over the nslots partial
@@ -237,7 +240,7 @@ __device__ void finalize_scores(int64_t col, float y2, Gather gather,
                                 const int32_t* __restrict__ counts, int c,
                                 int32_t* __restrict__ labels, float* __restrict__ ub,
                                 float* __restrict__ lb, DevStatus* __restrict__ status,
-                                RcRec* __restrict__ rc) {
+                                RcRec* __restrict__ rc, float ylo = 0.f) {
     float bs = INFINITY, ss = INFINITY, be = 0.f, se = 0.f;
     int bi = INT_MAX, si = INT_MAX;
     for (int i0 = 0; i0 < c; i0 += 8) {
@@ -255,11 +258,11 @@ __device__ void finalize_scores(int64_t col, float y2, Gather gather,
                 si = bi;
                 bs = sc;
                 bi = i;
-                be = score_err(mu2, y2);
+                be = score_err(mu2, y2, ylo);
             } else if (sc < ss) {
                 ss = sc;
                 si = i;
-                se = score_err(mu2, y2);
+                se = score_err(mu2, y2, ylo);
             }
         }
     }
@@ -275,7 +278,7 @@ __device__ void finalize_scores(int64_t col, float y2, Gather gather,
                 const int i = i0 + q;
                 if (i >= c || counts[i] == 0) continue;
                 const float mu2 = mu_normf[i];
-                best_hi = fminf(best_hi, fmaf(-2.f, g[q], mu2) + score_err(mu2, y2));
+                best_hi = fminf(best_hi, fmaf(-2.f, g[q], mu2) + score_err(mu2, y2, ylo));
             }
         }
         const int slot = atomicAdd(&status->rechecked, 1);
@@ -289,12 +292,105 @@ __device__ void finalize_scores(int64_t col, float y2, Gather gather,
                 const int i = i0 + q;
                 if (i >= c || counts[i] == 0) continue;
                 const float mu2 = mu_normf[i];
-                if (fmaf(-2.f, g[q], mu2) - score_err(mu2, y2) <= best_hi) r->mask[i >> 5] |= 1u << (i & 31);
+                if (fmaf(-2.f, g[q], mu2) - score_err(mu2, y2, ylo) <= best_hi)
+                    r->mask[i >> 5] |= 1u << (i & 31);
             }
         }
         r->col = (int32_t)col;
         return;
     }
+    const float yerr = 1e-5f * y2;
+    const int32_t old = labels[col];
+    if (old != bi) {
+        labels[col] = bi;
+        atomicAdd(&status->changed, 1);
+    }
+    if (ub) {
+        ub[col] = sqrtf(fmaxf(bs + y2 + be + yerr, 0.f)) * (1.f + 1e-6f);
+        lb[col] = si < c ? sqrtf(fmaxf(ss + y2 - se - yerr, 0.f)) * (1.f - 1e-6f) : INFINITY;
+    }
+}
+
+// The decision of finalize_scores by one warp for one column (c <= 128): lane
+// l holds centroids l, l + 32, l + 64, l + 96.  Same scores, bounds and rules:
+// best = the lowest score, ties to the lowest index; second = the lowest
+// score among the others, ties to the lowest index; a near tie queues every
+// centroid whose score interval reaches the lowest upper end.  g(i) returns
+// the dot product of centroid i.
+__device__ __forceinline__ void warp_best(float& v, int& i, float& e) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        const float oe = __shfl_xor_sync(0xffffffffu, e, o);
+        if (ov < v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+            e = oe;
+        }
+    }
+}
+
+template <typename G>
+__device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float* __restrict__ mu_normf,
+                              const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
+                              float* __restrict__ ub, float* __restrict__ lb, DevStatus* __restrict__ status,
+                              RcRec* __restrict__ rc) {
+    const int lane = threadIdx.x & 31;
+    float sc[4], er[4];
+    bool ok[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        ok[q] = i < c && counts[i] != 0;
+        sc[q] = INFINITY;
+        er[q] = 0.f;
+        if (ok[q]) {
+            const float mu2 = mu_normf[i];
+            sc[q] = fmaf(-2.f, g(i), mu2);
+            er[q] = score_err(mu2, y2, ylo);
+        }
+    }
+    float bs = INFINITY, be = 0.f;
+    int bi = INT_MAX;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (ok[q] && sc[q] < bs) {
+            bs = sc[q];
+            bi = lane + 32 * q;
+            be = er[q];
+        }
+    warp_best(bs, bi, be);
+    if (bi >= c) return;
+    float ss = INFINITY, se = 0.f;
+    int si = INT_MAX;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (ok[q] && lane + 32 * q != bi && sc[q] < ss) {
+            ss = sc[q];
+            si = lane + 32 * q;
+            se = er[q];
+        }
+    warp_best(ss, si, se);
+    if (ss - bs <= be + se) {
+        float hi = INFINITY;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (ok[q]) hi = fminf(hi, sc[q] + er[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hi = fminf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        uint32_t m[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) m[q] = __ballot_sync(0xffffffffu, ok[q] && sc[q] - er[q] <= hi);
+        if (lane == 0) {
+            const int slot = atomicAdd(&status->rechecked, 1);
+            RcRec* r = rc + slot;
+            for (int w = 0; w < kTcMaxClusters / 32; ++w) r->mask[w] = w < 4 ? m[w] : 0u;
+            r->col = (int32_t)col;
+        }
+        return;
+    }
+    if (lane != 0) return;
     const float yerr = 1e-5f * y2;
     const int32_t old = labels[col];
     if (old != bi) {
@@ -914,11 +1010,16 @@ __global__ void __launch_bounds__(kDnThreads, 1)
 // N operand, so each MMA instruction covers four times the columns of the
 // N = Npad form above (whose rate the issuing thread's per-instruction cost
 // bounds).  A = mu_a slabs: for Npad <= 64 ("stacked") rows 0..63 hold the raw
-// centroids (the MMA's hi part) and rows 64..127 their TF32 lo parts, so
-//   D[i] + D[64 + i] = mu_hi.y_hi + mu_lo.y_hi + mu_hi.y_lo + mu_lo.y_lo
-// from two MMAs per 8 rows (A.Y_raw and A.Y_lo); otherwise A1 = raw centroids
-// and A2 = lo parts, three MMAs (A1.Y_raw, A1.Y_lo, A2.Y_raw) into D[i].
-// Y_lo is a B operand and so lives in shared memory (a ring of 2 slabs).
+// centroids (the MMA's hi part) and rows 64..127 their TF32 lo parts, and one
+// MMA per 8 rows against the raw Y (which the MMA truncates to TF32) gives
+//   D[i] + D[64 + i] = mu_hi.y_hi + mu_lo.y_hi;
+// the missing mu.y_lo is at most ||mu|| ||y - tf32(y)|| (Cauchy-Schwarz; the
+// split warps sum ||y - tf32(y)||^2 per column, at most 2^-10 ||y||) and widens
+// the score bound (score_err's ylo), so the near ties it can hide are
+// re-decided exactly.  Without
+// y_lo slabs the stacked form keeps four stages in flight.  Otherwise A1 =
+// raw centroids and A2 = lo parts, three MMAs (A1.Y_raw, A1.Y_lo, A2.Y_raw)
+// into D[i]; Y_lo is a B operand and lives in shared memory (a ring of 2 slabs).
 //   warp 0: TMA producer (Y slab + A slab(s) per stage), warp 1: MMA issuer,
 //   warps 2-5: split (2 columns per thread) + epilogue (partials to Gpart).
 // The scores, argmin and bounds follow in k_finalize_t, one thread per
@@ -931,6 +1032,7 @@ constexpr int kTtMaxS = 4;
 struct DenseTArgs {
     int64_t d, n, Q, T, W;   // rows, columns, slabs per tile, 256-column tiles, work units
     int Npad, stacked, S, cmax;
+    int two_term;            // products with y truncated to TF32 only (no y_lo slabs)
     int use_list;
     int64_t list_min;
 };
@@ -943,7 +1045,10 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                      float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
                      RcRec* __restrict__ rc_list) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t full[kTtMaxS], empty[kTtMaxS], conv[2], loempty[2], acc_full[2], acc_empty[2];
+    // conv: the split warps are done with a slab -- one per y_lo slot (a ring of 2), or, in
+    // the two-term form (no y_lo ring to pace them), one per stage, so that a barrier can
+    // never complete twice before the MMA warp waits on it
+    __shared__ uint64_t full[kTtMaxS], empty[kTtMaxS], conv[kTtMaxS], loempty[2], acc_full[2], acc_empty[2];
     __shared__ float xch[64][17];   // lo rows handed to the hi rows in the epilogue (stacked)
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
@@ -971,12 +1076,12 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         tc_fence_before();
     }
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
+        for (int s = 0; s < S; ++s) {   // S >= 2: covers conv[0..1] of the y_lo ring too
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
+            mbar_init(&conv[s], 4);
         }
         for (int s = 0; s < 2; ++s) {
-            mbar_init(&conv[s], 4);
             mbar_init(&loempty[s], 1);
             mbar_init(&acc_full[s], 1);
             mbar_init(&acc_empty[s], 4);
@@ -1031,7 +1136,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                     break;
                 }
                 if (!mbar_wait_or_abort(&full[sr.idx], sr.phase, &abort_sh) ||
-                    !mbar_wait_or_abort(&conv[lr.idx], lr.phase, &abort_sh)) {
+                    !mbar_wait_or_abort(a.two_term ? &conv[sr.idx] : &conv[lr.idx],
+                                        a.two_term ? sr.phase : lr.phase, &abort_sh)) {
                     abort_sh = 1;
                     break;
                 }
@@ -1044,7 +1150,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                 for (int ks = 0; ks < kTcK / 8; ++ks) {
                     // 8 TF32 of K = 32 bytes = 2 descriptor address units
                     tc_mma(acc, dA1 + 2 * ks, dY + 2 * ks, idesc, (seg_start && ks == 0) ? 0u : 1u);
-                    tc_mma(acc, dA1 + 2 * ks, dLo + 2 * ks, idesc, 1u);
+                    if (!a.two_term) tc_mma(acc, dA1 + 2 * ks, dLo + 2 * ks, idesc, 1u);
                     if (na == 2) tc_mma(acc, dA2 + 2 * ks, dY + 2 * ks, idesc, 1u);
                 }
                 tc_commit(&empty[sr.idx]);
@@ -1069,17 +1175,17 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         RingPos sr(S), lr(2), ar(2);
         int64_t j = 0, tile = w_tile0, blk = w_blk0;
-        float ysq[2] = {0.f, 0.f}, ycomp[2] = {0.f, 0.f};
+        float ysq[2] = {0.f, 0.f}, ycomp[2] = {0.f, 0.f}, ylo2[2] = {0.f, 0.f};
         for (int64_t w = w0; w < w1; ++w, ++j) {
             const bool seg_start = (w == w0) || (blk == 0);
             const bool seg_end = (w == w1 - 1) || (blk == a.Q - 1);
-            if (seg_start) ysq[0] = ysq[1] = ycomp[0] = ycomp[1] = 0.f;
+            if (seg_start) ysq[0] = ysq[1] = ycomp[0] = ycomp[1] = ylo2[0] = ylo2[1] = 0.f;
             if (!mbar_wait_or_abort(&full[sr.idx], sr.phase, &abort_sh)) {
                 abort_sh = 1;
                 break;
             }
             // the lo slab is free once the MMAs of slab j - 2 are done
-            if (j >= 2 && !mbar_wait_or_abort(&loempty[lr.idx], lr.phase ^ 1u, &abort_sh)) {
+            if (!a.two_term && j >= 2 && !mbar_wait_or_abort(&loempty[lr.idx], lr.phase ^ 1u, &abort_sh)) {
                 abort_sh = 1;
                 break;
             }
@@ -1093,8 +1199,10 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                 for (int q = 0; q < 8; ++q) {
                     const uint32_t off = sw128_off(row, q);
                     const float4 x = ld_shared_v4(ysrc + off);
-                    st_shared_v4(lodst + off, make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y),
-                                                          x.z - tf32_hi(x.z), x.w - tf32_hi(x.w)));
+                    const float4 lo = make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y), x.z - tf32_hi(x.z),
+                                                  x.w - tf32_hi(x.w));
+                    if (!a.two_term) st_shared_v4(lodst + off, lo);
+                    else ylo2[h] = fmaf(lo.x, lo.x, fmaf(lo.y, lo.y, fmaf(lo.z, lo.z, fmaf(lo.w, lo.w, ylo2[h]))));
                     part = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, part))));
                 }
                 const float y = part - ycomp[h];   // Kahan accumulation of ||y_j||^2
@@ -1104,7 +1212,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&conv[lr.idx]);
+            if (lane == 0) mbar_arrive(a.two_term ? &conv[sr.idx] : &conv[lr.idx]);
             sr.next();
             lr.next();
             const int64_t cur_tile = tile;
@@ -1149,6 +1257,11 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             float* yn = ynorm_part + ((int64_t)cur_tile * a.cmax + slot) * kTtN;
             yn[m] = ysq[0];
             yn[m + 128] = ysq[1];
+            if (a.two_term) {   // ||y - tf32(y)||^2 partials in the second half
+                float* yl = yn + a.T * a.cmax * kTtN;
+                yl[m] = ylo2[0];
+                yl[m + 128] = ylo2[1];
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ar.idx]);
@@ -1174,8 +1287,9 @@ __global__ void __launch_bounds__(kFinThreads)
                  const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
                  float* __restrict__ ub, float* __restrict__ lb, const float* __restrict__ Gpart,
                  const float* __restrict__ ynorm_part, RcRec* __restrict__ rc_list) {
-    __shared__ float gs[128 * kFinCols];   // [centroid][column]
-    __shared__ float ys[kFinCols];
+    constexpr int kGs = kFinCols + 1;       // row stride: the warps' lanes read down a column
+    __shared__ float gs[128 * kGs];        // [centroid][column]
+    __shared__ float ys[kFinCols], ylos[kFinCols];
     if (a.use_list && (int64_t)status->flagged < a.list_min) return;   // the dense kernel did not run
     const int64_t col0 = (int64_t)blockIdx.x * kFinCols;
     const int64_t tile = col0 / kTtN;                 // kFinCols divides kTtN
@@ -1192,25 +1306,36 @@ __global__ void __launch_bounds__(kFinThreads)
         float v = 0.f;
 #pragma unroll 4
         for (int sl = 0; sl < ncontrib; ++sl) v += __ldcg(gt + sl * slot_stride + (int64_t)i * kTtN);
-        gs[i * kFinCols + jl] = v;
+        gs[i * kGs + jl] = v;
     }
     if (t < kFinCols) {
         const float* yt = ynorm_part + (int64_t)tile * a.cmax * kTtN + jc0 + t;
         float y2 = 0.f;
         for (int sl = 0; sl < ncontrib; ++sl) y2 += __ldcg(yt + (int64_t)sl * kTtN);
         ys[t] = y2;
+        float yl = 0.f;
+        if (a.two_term) {
+            // ||y - tf32(y)||: FP32 sums of at most d squares, so the norm is
+            // inflated by d 2^-24 to stay an upper bound
+            const float* ylt = yt + a.T * a.cmax * kTtN;
+            float l2 = 0.f;
+            for (int sl = 0; sl < ncontrib; ++sl) l2 += __ldcg(ylt + (int64_t)sl * kTtN);
+            yl = sqrtf(l2) * (1.f + (float)(a.d + 64) * 5.9604645e-8f);
+        }
+        ylos[t] = yl;
     }
     __syncthreads();
-    if (t >= kFinCols) return;
-    const int64_t p = col0 + t;
-    if (p >= a.n) return;
-    finalize_scores(
-        p, ys[t],
-        [&](int i0, float* gq) {
+    // one warp per column (two columns per warp), lanes over the centroids
+    constexpr int kColsPerWarp = kFinCols / (kFinThreads / 32);
+    const int warp = t >> 5;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) gq[q] = (i0 + q < c) ? gs[(i0 + q) * kFinCols + t] : 0.f;
-        },
-        mu_normf, counts, c, labels, ub, lb, status, rc_list);
+    for (int k2 = 0; k2 < kColsPerWarp; ++k2) {
+        const int jw = warp * kColsPerWarp + k2;
+        const int64_t p = col0 + jw;
+        if (p >= a.n) break;
+        finalize_warp(p, ys[jw], ylos[jw], [&](int i) { return gs[i * kGs + jw]; }, mu_normf, counts, c,
+                      labels, ub, lb, status, rc_list);
+    }
 }
 
 // ============================================================== exact recheck
@@ -1489,12 +1614,13 @@ struct DenseTPlan {
 };
 
 // Swapped dense kernel: 256-column tiles, 32-row slabs; stages of (Y slab,
-// A slab(s)), three when the centroids stack into one 128-row A, else two;
-// two y_lo slabs.
+// A slab(s)): four when the centroids stack into one 128-row A (no y_lo
+// slabs), else two plus two y_lo slabs.
 DenseTPlan dense_t_plan(int64_t n, int64_t d, int Npad) {
     DenseTPlan p;
     p.stacked = Npad <= 64 ? 1 : 0;
-    p.S = p.stacked ? 3 : 2;
+    // the stacked form multiplies by y truncated to TF32 only: no y_lo ring, four stages
+    p.S = p.stacked ? 4 : 2;
     const size_t y_bytes = (size_t)kTtN * 128, a_bytes = 128 * 128;
     const size_t stage = y_bytes + (p.stacked ? 1 : 2) * a_bytes;
     p.Q = (d + kTcK - 1) / kTcK;
@@ -1506,7 +1632,7 @@ DenseTPlan dense_t_plan(int64_t n, int64_t d, int Npad) {
         const int64_t nc = sk_owner((t + 1) * p.Q - 1, p.W, p.G) - sk_owner(t * p.Q, p.W, p.G) + 1;
         if (nc > p.cmax) p.cmax = (int)nc;
     }
-    p.smem = (size_t)p.S * stage + 2 * y_bytes + 1024;
+    p.smem = (size_t)p.S * stage + (p.stacked ? 0 : 2 * y_bytes) + 1024;
     return p;
 }
 
@@ -1548,7 +1674,8 @@ TcPlan tc_plan(int64_t n, int64_t d, int c) {
     if (t.Npad <= 128) {   // the swapped kernel's partials: [tile][slot][128 rows][256 columns]
         const DenseTPlan tp = dense_t_plan(n, d, t.Npad);
         t.gpart = std::max(t.gpart, (size_t)tp.T * tp.cmax * 128 * kTtN);
-        t.ynorm = std::max(t.ynorm, (size_t)tp.T * tp.cmax * kTtN);
+        // two halves when stacked: ||y||^2 and ||y - tf32(y)||^2 partials
+        t.ynorm = std::max(t.ynorm, (size_t)tp.T * tp.cmax * kTtN * (tp.stacked ? 2 : 1));
     }
     t.mu_a = (size_t)256 * t.dpad;
     t.rc_cap = std::min<int64_t>(n, 2048);
@@ -1600,6 +1727,7 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             a.W = dp.W;
             a.Npad = Npad;
             a.stacked = dp.stacked;
+            a.two_term = dp.stacked;
             a.S = dp.S;
             a.cmax = dp.cmax;
             a.use_list = list ? 1 : 0;
