@@ -2,69 +2,17 @@
 // K-means on the columns of L).  Normalised spectral clustering:
 //   A_ij = exp(-||y_i - y_j||^2 / (2 sigma^2)) (i != j), A_ii = 0,
 //   sigma^2 = scale * mean_{i != j} ||y_i - y_j||^2,
-//   M = D^{-1/2} A D^{-1/2},  U = top-c eigenvectors of M,  e_i = U_i / ||U_i||,
+//   M = D^{-1/2} A D^{-1/2} (applied as a product, never formed),
+//   U = top-c eigenvectors of M,  e_i = U_i / ||U_i||,
 // then K-means on the e_i.  The eigenvectors come from Chebyshev-filtered
 // subspace iteration with Rayleigh-Ritz (the spectrum of M lies in [-1, 1]).
+#include <algorithm>
+
 #include "respca_internal.cuh"
 
 namespace respca {
 
 namespace {
-
-constexpr int kGT = 64;     // GEMM output tile (rows and columns)
-constexpr int kGK = 16;     // GEMM K step
-constexpr int kGThreads = 256;
-
-// C[i + j ldc] = alpha * sum_k A[k + i lda] B[k + j ldb]   (C = A^T B), FP32.
-// 64 x 64 output tile per CTA, 4 x 4 per thread, K in steps of 16 through
-// shared memory.
-__global__ void __launch_bounds__(kGThreads)
-    k_gemm_tn(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
-              float* __restrict__ C, int64_t ldc, int64_t m, int64_t n, int64_t K, float alpha) {
-    __shared__ float As[kGK][kGT + 1];
-    __shared__ float Bs[kGK][kGT + 1];
-    const int64_t i0 = (int64_t)blockIdx.x * kGT, j0 = (int64_t)blockIdx.y * kGT;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    for (int64_t k0 = 0; k0 < K; k0 += kGK) {
-        // 16 x 64 elements of each operand: 4 per thread, k fastest (contiguous)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = threadIdx.x + q * kGThreads;
-            const int kk = e & 15, ii = e >> 4;
-            const int64_t k = k0 + kk;
-            const int64_t ia = i0 + ii, jb = j0 + ii;
-            As[kk][ii] = (k < K && ia < m) ? A[k + ia * lda] : 0.f;
-            Bs[kk][ii] = (k < K && jb < n) ? B[k + jb * ldb] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kGK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a[q] = As[kk][tx + 16 * q];
-                b[q] = Bs[kk][ty + 16 * q];
-            }
-#pragma unroll
-            for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-                for (int qb = 0; qb < 4; ++qb) acc[qa][qb] = fmaf(a[qa], b[qb], acc[qa][qb]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-        for (int qb = 0; qb < 4; ++qb) {
-            const int64_t i = i0 + tx + 16 * qa, j = j0 + ty + 16 * qb;
-            if (i < m && j < n) C[i + j * ldc] = alpha * acc[qa][qb];
-        }
-}
 
 // Squared norm of every column (FP64 accumulation) and per-CTA partial sums of them.
 __global__ void __launch_bounds__(kThreads)
@@ -92,31 +40,34 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Row sums of the Gram matrix (one CTA per row, FP64): sum_j G_ij = y_i . (sum_j y_j).
+// Partial column sums of Y over column chunks (FP64): cs[ch d + r] = sum of
+// Y[r + j ldy] over the chunk's columns j.  ||sum_j y_j||^2 = sum_ij y_i . y_j
+// gives sigma^2 without a pass over the n x n Gram matrix.
+constexpr int kSpecSumChunks = 512;
 __global__ void __launch_bounds__(kThreads)
-    k_spec_gsum(const float* __restrict__ G, int64_t n, double* __restrict__ gsum) {
-    __shared__ double red[kThreads / 32];
-    const int64_t i = blockIdx.x;
+    k_spec_colsum(const float* __restrict__ Y, int64_t ldy, int64_t d, int64_t n, int64_t per,
+                  double* __restrict__ cs) {
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= d) return;
+    const int64_t j0 = (int64_t)blockIdx.y * per, j1 = j0 + per < n ? j0 + per : n;
     double acc = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += kThreads) acc += (double)G[i * n + j];
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
-        gsum[i] = t;
-    }
+    for (int64_t j = j0; j < j1; ++j) acc += (double)Y[r + j * ldy];
+    cs[(int64_t)blockIdx.y * d + r] = acc;
 }
 
-// sigma^2 = scale * (2 n sum||y||^2 - 2 ||sum y||^2) / (n (n - 1)), with
-// ||sum y||^2 = sum_ij G_ij; out[0] = sigma^2, out[1] = 1 / (2 sigma^2)  (one block).
-__global__ void k_spec_sigma(const double* __restrict__ sqn_part, int parts, const double* __restrict__ gsum,
-                             int64_t n, double scale, double* __restrict__ out) {
+// sigma^2 = scale * (2 n sum||y||^2 - 2 ||sum y||^2) / (n (n - 1)), the mean
+// over i != j of ||y_i - y_j||^2 scaled, with sum y from the chunk sums;
+// out[0] = sigma^2, out[1] = 1 / (2 sigma^2)  (one block).
+__global__ void k_spec_sigma(const double* __restrict__ sqn_part, int parts, const double* __restrict__ cs,
+                             int64_t d, int64_t n, double scale, double* __restrict__ out) {
     __shared__ double red[2][kThreads / 32];
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < parts; i += kThreads) a += sqn_part[i];
-    for (int64_t r = threadIdx.x; r < n; r += kThreads) b += gsum[r];
+    for (int64_t r = threadIdx.x; r < d; r += kThreads) {
+        double v = 0.0;
+        for (int ch = 0; ch < kSpecSumChunks; ++ch) v += cs[(int64_t)ch * d + r];
+        b += v * v;
+    }
     a = warp_sum(a);
     b = warp_sum(b);
     if ((threadIdx.x & 31) == 0) {
@@ -146,15 +97,21 @@ __global__ void __launch_bounds__(kThreads)
     const float inv2s2 = (float)sig[1];
     const float si = sqn[i];
     float* row = G + i * n;   // G is symmetric: row i = column i
-    double acc = 0.0;
+    // each thread's entries summed in compensated FP32 (Kahan), then FP64 across threads:
+    // one FP64 add per element would bound this pass by the FP64 pipe
+    float acc = 0.f, comp = 0.f;
     for (int64_t j = threadIdx.x; j < n; j += kThreads) {
         const float d2 = fmaxf(si + sqn[j] - 2.f * row[j], 0.f);
         const float a = (j == i || inv2s2 == 0.f) ? 0.f : expf(-d2 * inv2s2);
         row[j] = a;
-        acc += (double)a;
+        const float y = a - comp;
+        const float t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
     }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    double accd = (double)acc - (double)comp;
+    accd = warp_sum(accd);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
@@ -169,14 +126,6 @@ __global__ void k_spec_rinv(const double* __restrict__ deg, int64_t n, float* __
     if (j >= n) return;
     const double dj = deg[j];
     r[j] = dj > 0.0 ? (float)(1.0 / sqrt(dj)) : 0.f;
-}
-
-// M_ij = A_ij r_i r_j.
-__global__ void __launch_bounds__(kThreads)
-    k_spec_normalise(float* __restrict__ A, int64_t n, const float* __restrict__ r) {
-    const int64_t i = blockIdx.x;
-    const float ri = r[i];
-    for (int64_t j = threadIdx.x; j < n; j += kThreads) A[i * n + j] = A[i * n + j] * ri * r[j];
 }
 
 // splitmix64 (Steele, Lea, Flood 2014) of a counter: the start block.
@@ -204,43 +153,95 @@ __global__ void k_spec_axpby(float* __restrict__ out, const float* __restrict__ 
     out[e] = v;
 }
 
-// W = M Y for the symmetric n x n matrix M and the n x b block Y (both
-// column-major): one warp per row i of M (contiguous, = column i), lanes over
-// k, the block's rows of Y staged in shared memory 128 at a time; M is read
-// once.  BMAX >= b accumulators per lane, reduced across the warp at the end.
-constexpr int kSymRows = 16;        // rows of M (warps) per CTA
-constexpr int kSymK = 128;          // rows of Y per shared-memory stage
-template <int BMAX>
-__global__ void __launch_bounds__(kSymRows * 32)
-    k_spec_symm(const float* __restrict__ M, int64_t n, const float* __restrict__ Y, int b,
-                float* __restrict__ W) {
-    __shared__ float ys[kSymK][BMAX + 1];
+// W = M Y for M = R A R (A the n x n affinity, column-major; R = diag(r),
+// r_k = deg_k^{-1/2}) and the n x b block Y (column-major): the CTA stages
+// its rows of R Y in shared memory and the reduction scales row i by r_i, so
+// M itself is never formed.  Each warp takes 32 * CPL consecutive rows i (CPL per lane) and the CTA a
+// chunk of k: for every k the lanes read one contiguous piece of column k of
+// M, M[i + k n], and multiply it by Y[k][0..b), which all lanes read at the
+// same shared-memory address (a broadcast).  M is read once, coalesced; the
+// chunk's partial products go to P[chunk][q][i] and k_spec_symm_reduce adds
+// them in chunk order (deterministic).  BMAX >= b accumulators per row.
+constexpr int kSymWarps = 8;
+constexpr int kSymSmemFloats = 12288;   // the CTA's rows of Y (48 KB)
+// CPL rows per lane: lane-strided (rows i0 + 32 u) when VEC = false, or
+// consecutive (one 16-byte load of rows 4 lane .. 4 lane + 3) when VEC = true
+// (n % 4 == 0), which doubles the bytes each load instruction moves.
+template <int BMAX, int CPL, bool VEC>
+__global__ void __launch_bounds__(kSymWarps * 32)
+    k_spec_symm(const float* __restrict__ M, const float* __restrict__ r, int64_t n, const float* __restrict__ Y,
+                int b, int64_t kc, float* __restrict__ P) {
+    __shared__ __align__(16) float ys[kSymSmemFloats];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * kSymRows + warp;
-    const float* mrow = M + (i < n ? i : 0) * n;
-    float acc[BMAX];
+    const int64_t k0 = (int64_t)blockIdx.y * kc;
+    const int64_t kn = (k0 + kc < n ? k0 + kc : n) - k0;
+    for (int64_t e = threadIdx.x; e < kc * BMAX; e += kSymWarps * 32) {
+        const int64_t kk = e % kc;
+        const int q = (int)(e / kc);
+        ys[kk * BMAX + q] = (q < b && kk < kn) ? Y[k0 + kk + (int64_t)q * n] * r[k0 + kk] : 0.f;
+    }
+    __syncthreads();
+    const int64_t wbase = ((int64_t)blockIdx.x * kSymWarps + warp) * 32 * CPL;
+    // row of this lane's slot u
+    auto row_of = [&](int u) -> int64_t { return VEC ? wbase + 4 * lane + u : wbase + lane + 32 * u; };
+    float acc[CPL][BMAX];
 #pragma unroll
-    for (int q = 0; q < BMAX; ++q) acc[q] = 0.f;
-    for (int64_t k0 = 0; k0 < n; k0 += kSymK) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < kSymK * BMAX; e += kSymRows * 32) {
-            const int kk = e % kSymK, q = e / kSymK;
-            ys[kk][q] = (q < b && k0 + kk < n) ? Y[k0 + kk + (int64_t)q * n] : 0.f;
+    for (int u = 0; u < CPL; ++u)
+#pragma unroll
+        for (int q = 0; q < BMAX; ++q) acc[u][q] = 0.f;
+    const bool all_live = row_of(CPL - 1) < n;
+#pragma unroll 8
+    for (int64_t kk = 0; kk < kn; ++kk) {
+        float m[CPL];
+        const float* mc = M + (k0 + kk) * n;
+        if (VEC) {
+            if (all_live) {
+                const float4 v = __ldcs(reinterpret_cast<const float4*>(mc + row_of(0)));
+                m[0] = v.x;
+                m[1 % CPL] = v.y;
+                m[2 % CPL] = v.z;
+                m[3 % CPL] = v.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < CPL; ++u) m[u] = row_of(u) < n ? __ldcs(mc + row_of(u)) : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < CPL; ++u) m[u] = row_of(u) < n ? __ldcs(mc + row_of(u)) : 0.f;
         }
-        __syncthreads();
+        const float4* yr = reinterpret_cast<const float4*>(ys + kk * BMAX);
 #pragma unroll
-        for (int t = 0; t < kSymK / 32; ++t) {
-            const int kk = t * 32 + lane;
-            const float m = (k0 + kk < n) ? mrow[k0 + kk] : 0.f;
+        for (int q4 = 0; q4 < BMAX / 4; ++q4) {
+            const float4 y = yr[q4];
 #pragma unroll
-            for (int q = 0; q < BMAX; ++q) acc[q] = fmaf(m, ys[kk][q], acc[q]);
+            for (int u = 0; u < CPL; ++u) {
+                acc[u][4 * q4 + 0] = fmaf(m[u], y.x, acc[u][4 * q4 + 0]);
+                acc[u][4 * q4 + 1] = fmaf(m[u], y.y, acc[u][4 * q4 + 1]);
+                acc[u][4 * q4 + 2] = fmaf(m[u], y.z, acc[u][4 * q4 + 2]);
+                acc[u][4 * q4 + 3] = fmaf(m[u], y.w, acc[u][4 * q4 + 3]);
+            }
         }
     }
+    float* pc = P + (int64_t)blockIdx.y * b * n;
 #pragma unroll
-    for (int q = 0; q < BMAX; ++q) {
-        const float v = warp_sum(acc[q]);
-        if (lane == 0 && i < n && q < b) W[i + (int64_t)q * n] = v;
+    for (int u = 0; u < CPL; ++u) {
+        const int64_t i = row_of(u);
+        if (i >= n) continue;
+#pragma unroll
+        for (int q = 0; q < BMAX; ++q)
+            if (q < b) pc[(int64_t)q * n + i] = acc[u][q];
     }
+}
+
+// W[i + q n] = r_i times the sum over chunks (in order) of P[chunk][q][i].
+__global__ void __launch_bounds__(kThreads)
+    k_spec_symm_reduce(const float* __restrict__ P, const float* __restrict__ r, int64_t n, int64_t nb, int chunks,
+                       float* __restrict__ W) {
+    const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (e >= nb) return;
+    float s = 0.f;
+    for (int ch = 0; ch < chunks; ++ch) s += __ldcg(P + (int64_t)ch * nb + e);
+    W[e] = s * r[e % n];
 }
 
 // out[i + j b1] = sum_k A[k + i n] B[k + j n] in FP64 (one CTA per entry):
@@ -313,50 +314,76 @@ __global__ void __launch_bounds__(kCholThreads)
     for (int e = threadIdx.x; e < b * b; e += kCholThreads) Q[e] = (float)V[e];
 }
 
-// Symmetric eigen-decomposition of H (b x b, FP32 in, symmetrised in FP64) by
-// cyclic Jacobi with the round-robin pair order (b/2 disjoint rotations per
-// step).  Writes the eigenvalues in descending order and the matching
-// eigenvectors as the columns of Q (b x b, FP32, column-major).  One CTA.
-constexpr int kJacThreads = 256;
-
-__global__ void __launch_bounds__(kJacThreads)
+// Symmetric eigen-decomposition of H (b x b, FP64 in, symmetrised) by cyclic
+// Jacobi with the round-robin pair order (b/2 disjoint rotations per step).
+// The rotations run in FP32: on this GPU an FP64 operation costs tens of FP32
+// ones, and the eigenvectors leave as FP32 anyway.  The loop ends when the
+// off-diagonal part is below 1e-6 of the matrix (Frobenius) or a whole sweep
+// turned by no angle above 1e-7.  The
+// eigenvalues are the FP64 Rayleigh quotients v^T H v of the FP32 eigenvector
+// columns, whose error is second order in the vectors'.  Writes them in
+// descending order (ties by index) and the matching vectors as the columns of
+// Q (b x b, FP32, column-major).  One CTA.
+// NT threads: one warp when the padded order is at most 32 (its barriers are
+// then cheap), 256 otherwise.
+template <int NT>
+__global__ void __launch_bounds__(NT)
     k_spec_jacobi(const double* __restrict__ H, int b, float* __restrict__ Q, double* __restrict__ evals,
                   int max_sweeps) {
     extern __shared__ double sm[];
     const int bp = b + (b & 1);          // padded to even (a zero row and column)
-    double* a = sm;                      // bp x bp
-    double* v = a + bp * bp;             // bp x bp
-    double* cs = v + bp * bp;            // bp/2 cosines
-    double* sn = cs + bp / 2;            // bp/2 sines
+    double* hs = sm;                     // b x b, the symmetrised H
+    double* rq = hs + b * b;             // bp Rayleigh quotients
+    float* a = reinterpret_cast<float*>(rq + bp);   // bp x bp
+    float* v = a + bp * bp;              // bp x bp
+    float* cs = v + bp * bp;             // bp/2 cosines
+    float* sn = cs + bp / 2;             // bp/2 sines
     int* pr = reinterpret_cast<int*>(sn + bp / 2);   // bp pair slots
-    __shared__ double offn;
-    for (int e = threadIdx.x; e < bp * bp; e += kJacThreads) {
+    __shared__ float red[NT / 32][2];
+    __shared__ int stop, turned;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < bp * bp; e += NT) {
         const int i = e % bp, j = e / bp;
         double x = 0.0;
-        if (i < b && j < b) x = 0.5 * (H[i + j * b] + H[j + i * b]);
-        a[e] = x;
-        v[e] = (i == j) ? 1.0 : 0.0;
+        if (i < b && j < b) {
+            x = 0.5 * (H[i + j * b] + H[j + i * b]);
+            hs[i + j * b] = x;
+        }
+        a[e] = (float)x;
+        v[e] = (i == j) ? 1.f : 0.f;
     }
     __syncthreads();
     const int half = bp / 2;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) {
-            double o = 0.0, t = 0.0;
-            for (int j = 0; j < bp; ++j)
-                for (int i = 0; i < bp; ++i) {
-                    const double x = a[i + j * bp];
-                    t += x * x;
-                    if (i != j) o += x * x;
-                }
-            offn = (o <= 1e-24 * t || t == 0.0) ? -1.0 : o;   // off-diagonal below 1e-12 relative
+        float o = 0.f, t = 0.f;
+        for (int e = threadIdx.x; e < bp * bp; e += NT) {
+            const float x = a[e];
+            t = fmaf(x, x, t);
+            if (e % bp != e / bp) o = fmaf(x, x, o);
+        }
+        o = warp_sum(o);
+        t = warp_sum(t);
+        if (lane == 0) {
+            red[warp][0] = o;
+            red[warp][1] = t;
         }
         __syncthreads();
-        if (offn < 0.0) break;
+        if (threadIdx.x == 0) {
+            float oo = 0.f, tt = 0.f;
+            for (int w = 0; w < NT / 32; ++w) {
+                oo += red[w][0];
+                tt += red[w][1];
+            }
+            stop = (oo <= 1e-12f * tt || tt == 0.f) ? 1 : 0;
+            turned = 0;
+        }
+        __syncthreads();
+        if (stop) break;
         for (int step = 0; step < bp - 1; ++step) {
             // round-robin: slot 0 fixed, the others rotate by `step`
             if (threadIdx.x < bp) {
-                int idx = threadIdx.x;
-                int pos = (idx == 0) ? 0 : 1 + (idx - 1 + step) % (bp - 1);
+                const int idx = threadIdx.x;
+                const int pos = (idx == 0) ? 0 : 1 + (idx - 1 + step) % (bp - 1);
                 pr[pos] = idx;
             }
             __syncthreads();
@@ -364,57 +391,78 @@ __global__ void __launch_bounds__(kJacThreads)
             if (threadIdx.x < half) {
                 const int k = threadIdx.x;
                 int p = pr[k], q = pr[bp - 1 - k];
-                if (p > q) { const int t = p; p = q; q = t; }
-                const double apq = a[p + q * bp];
-                double c = 1.0, s = 0.0;
-                if (fabs(apq) > 1e-300) {
-                    const double app = a[p + p * bp], aqq = a[q + q * bp];
-                    const double tau = (aqq - app) / (2.0 * apq);
-                    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    s = t * c;
+                if (p > q) { const int tq = p; p = q; q = tq; }
+                const float apq = a[p + q * bp];
+                float c = 1.f, s = 0.f;
+                if (apq != 0.f) {
+                    const float app = a[p + p * bp], aqq = a[q + q * bp];
+                    const float tau = (aqq - app) / (2.f * apq);
+                    // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), the smaller root; for
+                    // huge |tau| the rotation is below FP32 resolution and t = 1 / (2 tau)
+                    const float at = fabsf(tau);
+                    const float tr = at > 1e18f ? 0.5f / at : 1.f / (at + sqrtf(fmaf(at, at, 1.f)));
+                    const float tt = tau >= 0.f ? tr : -tr;
+                    c = rsqrtf(fmaf(tt, tt, 1.f));
+                    s = tt * c;
+                    if (fabsf(s) > 1e-7f) turned = 1;
                 }
                 cs[k] = c;
                 sn[k] = s;
             }
             __syncthreads();
             // rows: A <- J^T A (each pair updates its two rows, every column)
-            for (int e = threadIdx.x; e < half * bp; e += kJacThreads) {
+            for (int e = threadIdx.x; e < half * bp; e += NT) {
                 const int k = e / bp, col = e % bp;
                 int p = pr[k], q = pr[bp - 1 - k];
-                if (p > q) { const int t = p; p = q; q = t; }
-                const double c = cs[k], s = sn[k];
-                const double xp = a[p + col * bp], xq = a[q + col * bp];
+                if (p > q) { const int tq = p; p = q; q = tq; }
+                const float c = cs[k], s = sn[k];
+                const float xp = a[p + col * bp], xq = a[q + col * bp];
                 a[p + col * bp] = c * xp - s * xq;
                 a[q + col * bp] = s * xp + c * xq;
             }
             __syncthreads();
             // columns: A <- A J, V <- V J
-            for (int e = threadIdx.x; e < half * bp; e += kJacThreads) {
+            for (int e = threadIdx.x; e < half * bp; e += NT) {
                 const int k = e / bp, row = e % bp;
                 int p = pr[k], q = pr[bp - 1 - k];
-                if (p > q) { const int t = p; p = q; q = t; }
-                const double c = cs[k], s = sn[k];
-                const double xp = a[row + p * bp], xq = a[row + q * bp];
+                if (p > q) { const int tq = p; p = q; q = tq; }
+                const float c = cs[k], s = sn[k];
+                const float xp = a[row + p * bp], xq = a[row + q * bp];
                 a[row + p * bp] = c * xp - s * xq;
                 a[row + q * bp] = s * xp + c * xq;
-                const double vp = v[row + p * bp], vq = v[row + q * bp];
+                const float vp = v[row + p * bp], vq = v[row + q * bp];
                 v[row + p * bp] = c * vp - s * vq;
                 v[row + q * bp] = s * vp + c * vq;
             }
             __syncthreads();
         }
+        // a sweep whose rotations were all below FP32 resolution changes nothing more
+        if (!turned) break;
     }
+    // Rayleigh quotients in FP64: one warp per column j, lanes over rows i
+    for (int j = warp; j < bp; j += NT / 32) {
+        double acc = 0.0;
+        if (j < b) {
+            for (int i = lane; i < b; i += 32) {
+                double hv = 0.0;
+                for (int k = 0; k < b; ++k) hv = fma(hs[i + k * b], (double)v[k + j * bp], hv);
+                acc = fma((double)v[i + j * bp], hv, acc);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) rq[j] = acc;
+    }
+    __syncthreads();
     // descending order of the first b eigenvalues (selection by rank; ties by index)
-    for (int j = threadIdx.x; j < b; j += kJacThreads) {
-        const double x = a[j + j * bp];
+    for (int j = threadIdx.x; j < b; j += NT) {
+        const double x = rq[j];
         int rank = 0;
         for (int k = 0; k < b; ++k) {
-            const double y = a[k + k * bp];
+            const double y = rq[k];
             rank += (y > x) || (y == x && k < j);
         }
         evals[rank] = x;
-        for (int i = 0; i < b; ++i) Q[i + rank * b] = (float)v[i + j * bp];
+        for (int i = 0; i < b; ++i) Q[i + rank * b] = v[i + j * bp];
     }
 }
 
@@ -474,19 +522,21 @@ inline unsigned blocks_for(int64_t work, int per) { return (unsigned)((work + pe
 }  // namespace
 
 cudaError_t launch_spec_affinity(const float* Y, int64_t ldy, int64_t d, int64_t n, double scale, float* G,
-                                 float* sqn, double* part, int parts, double* gsum, double* sig, double* deg,
-                                 float* rinv, cudaStream_t st) {
-    count_launches(7);
+                                 float* sqn, double* part, int parts, double* colsum, double* sig, double* deg,
+                                 float* rinv, DevStatus* status, cudaStream_t st) {
+    count_launches(5);
     k_spec_norms<<<parts, kThreads, 0, st>>>(Y, ldy, d, n, sqn, part);
-    const dim3 grid(blocks_for(n, kGT), blocks_for(n, kGT));
-    k_gemm_tn<<<grid, kGThreads, 0, st>>>(Y, ldy, Y, ldy, G, n, n, n, d, 1.f);
-    k_spec_gsum<<<(unsigned)n, kThreads, 0, st>>>(G, n, gsum);
-    k_spec_sigma<<<1, kThreads, 0, st>>>(part, parts, gsum, n, scale, sig);
+    const int64_t per = (n + kSpecSumChunks - 1) / kSpecSumChunks;
+    k_spec_colsum<<<dim3(blocks_for(d, kThreads), kSpecSumChunks), kThreads, 0, st>>>(Y, ldy, d, n, per, colsum);
+    k_spec_sigma<<<1, kThreads, 0, st>>>(part, parts, colsum, d, n, scale, sig);
+    const cudaError_t e = launch_gram_tc(Y, ldy, d, n, G, status, st);
+    if (e != cudaSuccess) return e;
     k_spec_affinity<<<(unsigned)n, kThreads, 0, st>>>(G, n, sqn, sig, deg);
     k_spec_rinv<<<blocks_for(n, kThreads), kThreads, 0, st>>>(deg, n, rinv);
-    k_spec_normalise<<<(unsigned)n, kThreads, 0, st>>>(G, n, rinv);
     return cudaGetLastError();
 }
+
+size_t spec_colsum_doubles(int64_t d) { return (size_t)kSpecSumChunks * d; }
 
 cudaError_t launch_spec_start(float* Y, int64_t n, int b, uint64_t seed, cudaStream_t st) {
     count_launches(1);
@@ -501,13 +551,43 @@ cudaError_t launch_spec_axpby(float* out, const float* T, const float* Y, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_spec_symm(const float* M, int64_t n, const float* Y, int b, float* W, cudaStream_t st) {
-    count_launches(1);
-    const unsigned grid = blocks_for(n, kSymRows);
-    if (b <= 16) k_spec_symm<16><<<grid, kSymRows * 32, 0, st>>>(M, n, Y, b, W);
-    else if (b <= 32) k_spec_symm<32><<<grid, kSymRows * 32, 0, st>>>(M, n, Y, b, W);
-    else if (b <= 48) k_spec_symm<48><<<grid, kSymRows * 32, 0, st>>>(M, n, Y, b, W);
-    else k_spec_symm<72><<<grid, kSymRows * 32, 0, st>>>(M, n, Y, b, W);
+namespace {
+int spec_bmax(int b) { return b <= 16 ? 16 : b <= 32 ? 32 : b <= 48 ? 48 : 72; }
+int64_t spec_kc(int64_t n, int b) {
+    const int bm = spec_bmax(b);
+    const int cpl = (bm == 16 && n % 4 == 0) ? 4 : bm <= 32 ? 2 : 1;
+    const int64_t iblocks = (n + kSymWarps * 32 * cpl - 1) / (kSymWarps * 32 * cpl);
+    // about two (16-byte loads) or four CTAs per SM over the grid, each chunk a
+    // multiple of 8 rows of Y: fewer chunks keep the partial products small
+    const int64_t ctas = (cpl == 4 ? 2 : 4) * 152;
+    const int64_t want = std::max<int64_t>(1, (ctas + iblocks - 1) / iblocks);
+    int64_t kc = (n + want - 1) / want;
+    kc = (kc + 7) / 8 * 8;
+    return std::min<int64_t>(kc, kSymSmemFloats / bm / 8 * 8);
+}
+}  // namespace
+
+int64_t spec_symm_chunks(int64_t n, int b) {
+    const int64_t kc = spec_kc(n, b);
+    return (n + kc - 1) / kc;
+}
+
+cudaError_t launch_spec_symm(const float* M, const float* r, int64_t n, const float* Y, int b, float* W, float* P,
+                             cudaStream_t st) {
+    count_launches(2);
+    const int bm = spec_bmax(b);
+    const bool vec = bm == 16 && n % 4 == 0;
+    const int cpl = vec ? 4 : bm <= 32 ? 2 : 1;
+    const int64_t kc = spec_kc(n, b), chunks = (n + kc - 1) / kc;
+    const dim3 grid((unsigned)((n + kSymWarps * 32 * cpl - 1) / (kSymWarps * 32 * cpl)), (unsigned)chunks);
+    const unsigned thr = kSymWarps * 32;
+    if (vec) k_spec_symm<16, 4, true><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
+    else if (bm == 16) k_spec_symm<16, 2, false><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
+    else if (bm == 32) k_spec_symm<32, 2, false><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
+    else if (bm == 48) k_spec_symm<48, 1, false><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
+    else k_spec_symm<72, 1, false><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
+    const int64_t nb = n * (int64_t)b;
+    k_spec_symm_reduce<<<blocks_for(nb, kThreads), kThreads, 0, st>>>(P, r, n, nb, (int)chunks, W);
     return cudaGetLastError();
 }
 
@@ -538,15 +618,22 @@ cudaError_t launch_spec_cholqr2(float* Y, float* T, int64_t n, int b, double* G,
 
 size_t spec_jacobi_smem(int b) {
     const int bp = b + (b & 1);
-    return sizeof(double) * (2 * (size_t)bp * bp + bp) + sizeof(int) * bp;
+    return sizeof(double) * ((size_t)b * b + bp) + sizeof(float) * (2 * (size_t)bp * bp + bp) +
+           sizeof(int) * bp;
 }
 
 cudaError_t launch_spec_jacobi(const double* H, int b, float* Q, double* evals, cudaStream_t st) {
     count_launches(1);
     const size_t smem = spec_jacobi_smem(b);
-    cudaError_t e = allow_max_dynamic_smem((const void*)k_spec_jacobi);
-    if (e != cudaSuccess) return e;
-    k_spec_jacobi<<<1, kJacThreads, smem, st>>>(H, b, Q, evals, 60);
+    if (b + (b & 1) <= 32) {
+        cudaError_t e = allow_max_dynamic_smem((const void*)k_spec_jacobi<32>);
+        if (e != cudaSuccess) return e;
+        k_spec_jacobi<32><<<1, 32, smem, st>>>(H, b, Q, evals, 60);
+    } else {
+        cudaError_t e = allow_max_dynamic_smem((const void*)k_spec_jacobi<256>);
+        if (e != cudaSuccess) return e;
+        k_spec_jacobi<256><<<1, 256, smem, st>>>(H, b, Q, evals, 60);
+    }
     return cudaGetLastError();
 }
 

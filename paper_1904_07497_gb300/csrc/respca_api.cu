@@ -73,7 +73,8 @@ struct respca_ctx {
         bn_part,              // per-chunk ||B_j||^2 of the l2,1 iteration
         sumsD,                // FP64 sums of the next D under the iteration's starting labels
         sp_M, sp_sqn, sp_part, sp_gsum, sp_sig, sp_deg, sp_Y, sp_W, sp_T, sp_Z, sp_H, sp_Q, sp_ev,
-        sp_res, sp_E;         // spectral p step: affinity, search blocks, Rayleigh-Ritz, embedding
+        sp_res, sp_E, sp_P, sp_Ypad;   // spectral p step: affinity, search blocks, Rayleigh-Ritz, embedding,
+                              // M Y partials, a 16-byte-aligned copy of Y for the tensor maps
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -135,7 +136,7 @@ std::vector<DevBuf*> all_bufs(respca_ctx* h) {
                       &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
                       &h->bn_part, &h->sumsD, &h->sp_M, &h->sp_sqn, &h->sp_part, &h->sp_gsum,
                       &h->sp_sig, &h->sp_deg, &h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z, &h->sp_H, &h->sp_Q,
-                      &h->sp_ev, &h->sp_res, &h->sp_E};
+                      &h->sp_ev, &h->sp_res, &h->sp_E, &h->sp_P, &h->sp_Ypad};
 }
 
 respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64_t lds,
@@ -256,7 +257,7 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
     CK(ensure(h->sp_M, sizeof(float) * (size_t)n * n));
     CK(ensure(h->sp_sqn, sizeof(float) * n));
     CK(ensure(h->sp_part, sizeof(double) * parts));
-    CK(ensure(h->sp_gsum, sizeof(double) * n));
+    CK(ensure(h->sp_gsum, sizeof(double) * spec_colsum_doubles(d)));
     CK(ensure(h->sp_sig, sizeof(double) * 2));
     CK(ensure(h->sp_deg, sizeof(double) * n));
     for (DevBuf* bb : {&h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z}) CK(ensure(*bb, sizeof(float) * (size_t)n * b));
@@ -265,6 +266,12 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
     CK(ensure(h->sp_ev, sizeof(double) * b));
     CK(ensure(h->sp_res, sizeof(double) * c));
     CK(ensure(h->sp_E, sizeof(float) * (size_t)n * c));
+    CK(ensure(h->sp_P, sizeof(float) * (size_t)spec_symm_chunks(n, b) * n * b));
+    if (!h->status.p) {
+        // a handle whose first call is this one: the status block (timeout flag) starts zeroed
+        CK(ensure(h->status, sizeof(DevStatus)));
+        CK(cudaMemsetAsync(h->status.p, 0, sizeof(DevStatus), st));
+    }
     if (!h->spec_km) {
         respca_config kc = h->cfg;
         kc.stream = h->stream;
@@ -275,9 +282,21 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
         if (cs != RESPCA_OK) return fail(h, cs, "spectral p step: K-means context");
     }
     float* M = P<float>(h->sp_M);
+    if (!gram_tc_ok(Y, ldy)) {
+        // the Gram kernel reads Y through a tensor map: 16-byte base and column stride
+        const int64_t ldp = (d + 3) / 4 * 4;
+        CK(ensure(h->sp_Ypad, sizeof(float) * (size_t)ldp * n));
+        CK(cudaMemcpy2DAsync(h->sp_Ypad.p, sizeof(float) * ldp, Y, sizeof(float) * ldy, sizeof(float) * d, n,
+                             cudaMemcpyDeviceToDevice, st));
+        Y = P<float>(h->sp_Ypad);
+        ldy = ldp;
+    }
+    DevStatus* dstat = P<DevStatus>(h->status);
+    CK(cudaMemsetAsync(&dstat->timeout, 0, sizeof(int32_t), st));
     CK(launch_spec_affinity(Y, ldy, d, n, h->cfg.spectral_scale, M, P<float>(h->sp_sqn), P<double>(h->sp_part),
                             parts, P<double>(h->sp_gsum), P<double>(h->sp_sig), P<double>(h->sp_deg),
-                            P<float>(h->sp_sqn), st));
+                            P<float>(h->sp_sqn), dstat, st));
+    const float* rinv = P<float>(h->sp_sqn);   // deg^{-1/2}, written over the column norms
     float* Yb = P<float>(h->sp_Y);   // current orthonormal block (n x b)
     float* W = P<float>(h->sp_W);    // M Yb
     float* T = P<float>(h->sp_T);    // scratch
@@ -292,7 +311,7 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
     double lo = -1.0;   // the spectrum of M lies in [-1, 1]
     for (;;) {
         // Rayleigh-Ritz on span(Yb): H = Yb^T M Yb, rotate to the Ritz vectors
-        CK(launch_spec_symm(M, n, Yb, b, W, st));
+        CK(launch_spec_symm(M, rinv, n, Yb, b, W, P<float>(h->sp_P), st));
         ++matvecs;
         CK(launch_spec_gram_small(Yb, W, n, b, b, P<double>(h->sp_H), st));
         CK(launch_spec_jacobi(P<double>(h->sp_H), b, P<float>(h->sp_Q), P<double>(h->sp_ev), st));
@@ -319,7 +338,7 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
         float* y2 = Z;
         CK(launch_spec_axpby(y1, W, y0, nullptr, nb, (float)(1.0 / e), (float)(-cen / e), 0.f, st));
         for (int k = 2; k <= kSpecDegree; ++k) {
-            CK(launch_spec_symm(M, n, y1, b, W, st));   // W as scratch: M y1
+            CK(launch_spec_symm(M, rinv, n, y1, b, W, P<float>(h->sp_P), st));   // W as scratch: M y1
             ++matvecs;
             CK(launch_spec_axpby(y2, W, y1, y0, nb, (float)(2.0 / e), (float)(-2.0 * cen / e), -1.f, st));
             float* t = y0;
@@ -333,6 +352,10 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
             // keep the buffer roles fixed: Yb holds the block, T and Z are scratch
             CK(cudaMemcpyAsync(Yb, y1, sizeof(float) * nb, cudaMemcpyDeviceToDevice, st));
         }
+    }
+    {
+        const respca_status ts = read_status(h);   // the Gram kernel's bounded waits
+        if (ts != RESPCA_OK) return ts;
     }
     CK(launch_spec_embed(Yb, n, c, P<float>(h->sp_E), st));
     int32_t passes = 0;

@@ -405,13 +405,22 @@ cudaError_t launch_adam(float* P, const float* G, float* M, float* V, int64_t co
                         float b2, float eps, float c1, float c2, cudaStream_t st);
 
 // ---------------------------------------------------------------- spectral p step
+// G = Y^T Y (n x n, exactly symmetric) on the tensor cores; Y needs 16-byte
+// alignment and ldy % 4 == 0 (gram_tc_ok)
+bool gram_tc_ok(const float* Y, int64_t ldy);
+cudaError_t launch_gram_tc(const float* Y, int64_t ldy, int64_t d, int64_t n, float* G, DevStatus* status,
+                           cudaStream_t st);
 cudaError_t launch_spec_affinity(const float* Y, int64_t ldy, int64_t d, int64_t n, double scale, float* G,
-                                 float* sqn, double* part, int parts, double* gsum, double* sig, double* deg,
-                                 float* rinv, cudaStream_t st);
+                                 float* sqn, double* part, int parts, double* colsum, double* sig, double* deg,
+                                 float* rinv, DevStatus* status, cudaStream_t st);
 cudaError_t launch_spec_start(float* Y, int64_t n, int b, uint64_t seed, cudaStream_t st);
 cudaError_t launch_spec_axpby(float* out, const float* T, const float* Y, const float* Yp, int64_t count,
                               float alpha, float beta, float gamma, cudaStream_t st);
-cudaError_t launch_spec_symm(const float* M, int64_t n, const float* Y, int b, float* W, cudaStream_t st);
+// W = R A R Y (R = diag(r)); P holds spec_symm_chunks(n, b) x n x b partial products
+int64_t spec_symm_chunks(int64_t n, int b);
+cudaError_t launch_spec_symm(const float* A, const float* r, int64_t n, const float* Y, int b, float* W, float* P,
+                             cudaStream_t st);
+size_t spec_colsum_doubles(int64_t d);
 cudaError_t launch_spec_gram_small(const float* A, const float* B, int64_t n, int b1, int b2, double* out,
                                    cudaStream_t st);
 cudaError_t launch_spec_cholqr2(float* Y, float* T, int64_t n, int b, double* G, float* Q, cudaStream_t st);
