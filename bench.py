@@ -32,7 +32,6 @@ FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_ELEM_FP32 = 28   # read X, S, Theta, L_prev; write L, S, Theta (4 B each)
 SEARCH_BYTES_PER_ELEM = 4  # the all-column search reads the FP32 operand L (or X) once
 BYTES_PER_ELEM_L21 = 44    # l2,1 iteration: pass A 20 B (reads X, S, Theta, L_prev; writes L), pass B 24 B
-FP32_LANES_PER_SM, SMS = 128, 152   # CUDA-core FP32 lanes per SM and SMs of a GB300
 
 WORKLOADS = {
     # name: (d, n, rank, sparsity, c)
@@ -272,6 +271,16 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r["max"] for r in rows),
                 "reasons": sorted(reasons), "samples": len(rows),
                 "power_w_max": max(r["power"] for r in rows)}
+
+
+def tf32_peak_tflops():
+    """Dense TF32 tensor peak: the measured BF16 burst figure times the nominal
+    TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x nominal tf32/bf16"
+    except (OSError, KeyError, ValueError):
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x nominal tf32/bf16"
 
 
 def measured_peak():
@@ -614,10 +623,38 @@ def run_spectral(args, rank, world, local_rank):
         len(set(m.values())) == len(m)
     info = infos[-1]
     b = SPEC_C + 8
-    flops = 2.0 * n * n * d + 2.0 * n * n * b * info["matvecs"]   # Gram + products with M
-    mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak = FP32_LANES_PER_SM * SMS * 2 * mhz * 1e6 / 1e12
-    ach = flops / (ms / 1e3) / 1e12
+    # one more p step with the library's event timing on: the Gram kernel and the
+    # products with M, each bracketed by CUDA events on the handle's stream
+    tsolver = respca.Solver(seed=args.seed, stream=stream, device=local_rank, p_step=1,
+                            spectral_scale=SPEC_SCALE, timing=1)
+    respca.respca_spectral_labels(tsolver.h, X, SPEC_C)
+    _, tinfo = respca.respca_spectral_labels(tsolver.h, X, SPEC_C)
+    tsolver.close()
+    peak_hbm, peak_kind = measured_peak()
+    # products W = M Y: M (n x n FP32) read once per product, Y and W (n x b) once
+    prod_bytes = 4.0 * n * n + 2 * 4.0 * n * b
+    prod_ms = tinfo["ms_products"] / max(tinfo["matvecs"], 1)
+    prod_gbs = prod_bytes / (prod_ms / 1e3) / 1e9
+    # Gram Y^T Y: the symmetric product's n (n + 1) / 2 dot products of length d
+    # (FP32-equivalent flops; the kernel issues three TF32 MMAs per product
+    # for FP32 accuracy), against the TF32 dense peak = measured BF16 peak x
+    # the nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)
+    gram_flops = float(n) * (n + 1) * d
+    tf32_peak, tf32_kind = tf32_peak_tflops()
+    gram_tflops = gram_flops / (tinfo["ms_gram"] / 1e3) / 1e12
+    rooflines = [
+        {"bound": "hbm", "kernel": f"k_spec_symm + k_spec_symm_reduce (W = D^-1/2 A D^-1/2 Y, n x n by n x {b})",
+         "achieved": round(prod_gbs, 1), "peak": peak_hbm, "unit": "GB/s", "frac": round(prod_gbs / peak_hbm, 4),
+         "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": prod_bytes,
+         "avg_launch_ms": round(prod_ms, 4), "launches": tinfo["matvecs"],
+         "total_ms": round(tinfo["ms_products"], 3)},
+        {"bound": "tensor", "kernel": "k_gram_tc (Y^T Y on tcgen05 kind::tf32, 3-term split, upper-triangle tiles)",
+         "achieved": round(gram_tflops, 2), "peak": round(tf32_peak, 1), "unit": "TFLOP/s",
+         "frac": round(gram_tflops / tf32_peak, 4), "peak_source": tf32_kind, "traffic": None,
+         "algorithmic_flops_per_launch": gram_flops, "tensor_flops_per_launch": 3 * gram_flops,
+         "avg_launch_ms": round(tinfo["ms_gram"], 4), "launches": 1, "total_ms": round(tinfo["ms_gram"], 3)},
+    ]
+    dominant = max(rooflines, key=lambda r: r["total_ms"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
@@ -640,11 +677,7 @@ def run_spectral(args, rank, world, local_rank):
                                f"sigma^2 = {SPEC_SCALE} x mean squared distance; value = ms per p step",
                    "l2": "the n x n affinity (256 MB) is larger than L2"},
         "info": info, "labels_recover_blobs": bool(recovered),
-        "roofline": {"bound": "alu", "kernel": "k_gemm_tn (Gram, 2 n^2 d) and k_spec_symm (the eigensolver's "
-                     f"{info['matvecs']} products M Y, n x n by n x {b}) over the whole p step",
-                     "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
-                     "frac": round(ach / peak, 4),
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock", "traffic": None},
+        "roofline": dominant, "rooflines": rooflines,
         "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clk,
     }
 

@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define RESPCA_ABI_VERSION 2
+#define RESPCA_ABI_VERSION 3
 
 typedef struct respca_ctx *respca_handle;
 
@@ -334,6 +334,8 @@ typedef struct {
     double theta_next;       /* (c+1)-th largest Ritz value (eigen-gap = theta_c - theta_next) */
     int32_t lloyd_passes;    /* K-means passes on the embedding */
     int32_t converged;       /* 1 if residual <= 1e-5 within the iteration cap */
+    double ms_gram;          /* with cfg.timing: device time of the Gram matrix Y^T Y (else 0) */
+    double ms_products;      /* with cfg.timing: device time of the matvecs products with M (else 0) */
 } respca_spectral_info;
 
 /*

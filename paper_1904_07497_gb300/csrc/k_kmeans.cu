@@ -503,22 +503,34 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t b0 = min(nb, (int64_t)threadIdx.x * chunk), b1 = min(nb, b0 + chunk);
     double t = 0.0;
     for (int64_t b = b0; b < b1; ++b) t += __ldcg(part + b);
-    tsum[threadIdx.x] = t;
+    // exclusive prefix of the threads' range sums: a shuffle scan within each warp,
+    // then the warps' totals in order (a chain of 5 + 8 FP64 additions instead of 256)
+    double incl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.0;
+    if (lane == 31) colv[warp] = incl;
     if (threadIdx.x == 0) {
         *done = 0;
         s_block = LLONG_MAX;
         s_pick = -1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {   // exclusive prefix over the threads' ranges, in order
+    if (threadIdx.x == 0) {
         double run = 0.0;
-        for (int q = 0; q < kThreads; ++q) {
-            const double x = tsum[q];
-            tsum[q] = run;
+        for (int w = 0; w < W; ++w) {
+            const double x = colv[w];
+            colv[w] = run;
             run += x;
         }
         tsum[kThreads] = run;
     }
+    __syncthreads();
+    tsum[threadIdx.x] = colv[warp] + excl;
     __syncthreads();
     const double total = tsum[kThreads];
     const double uk = u[kpick];

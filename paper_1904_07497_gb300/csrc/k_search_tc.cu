@@ -152,6 +152,7 @@ __device__ void finalize_scores(int64_t col, float y2, Gather gather,
             }
         }
         r->col = (int32_t)col;
+        r->done = 0;
         return;
     }
     const float yerr = 1e-5f * y2;
@@ -186,22 +187,23 @@ __device__ __forceinline__ void warp_best(float& v, int& i, float& e) {
     }
 }
 
+// mu2v[q], okv[q]: ||mu_i||^2 and "cluster i is not empty" for i = lane + 32 q,
+// loaded by the caller.
 template <typename G>
-__device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float* __restrict__ mu_normf,
-                              const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
-                              float* __restrict__ ub, float* __restrict__ lb, DevStatus* __restrict__ status,
-                              RcRec* __restrict__ rc) {
+__device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float (&mu2v)[4], const bool (&okv)[4],
+                              int c, int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
+                              DevStatus* __restrict__ status, RcRec* __restrict__ rc) {
     const int lane = threadIdx.x & 31;
     float sc[4], er[4];
     bool ok[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i = lane + 32 * q;
-        ok[q] = i < c && counts[i] != 0;
+        ok[q] = okv[q];
         sc[q] = INFINITY;
         er[q] = 0.f;
         if (ok[q]) {
-            const float mu2 = mu_normf[i];
+            const float mu2 = mu2v[q];
             sc[q] = fmaf(-2.f, g(i), mu2);
             er[q] = score_err(mu2, y2, ylo);
         }
@@ -242,6 +244,7 @@ __device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float
             RcRec* r = rc + slot;
             for (int w = 0; w < kTcMaxClusters / 32; ++w) r->mask[w] = w < 4 ? m[w] : 0u;
             r->col = (int32_t)col;
+            r->done = 0;
         }
         return;
     }
@@ -1108,11 +1111,12 @@ __global__ void __launch_bounds__(kTtThreads, 1)
 // Scores, argmin (ties to the lowest index), near-tie queue and bounds of
 // every column from the swapped kernel's partials [tile][slot][rows][256]
 // (rows = 64 when stacked, hi and lo parts already added; else 128).
-// A block takes 64 columns of one tile: its 1024 threads first sum the
+// A block takes 16 columns of one tile: its 256 threads first sum the
 // partials over the tile's slots (in slot order, hi and lo rows together)
 // into shared memory, with coalesced and mutually independent loads; then one
-// thread per column scores it from there.
-constexpr int kFinCols = 64, kFinThreads = 1024;
+// warp per column scores it from there.  Small blocks keep several per SM
+// resident, so one wave covers n = 10^4 and their latencies overlap.
+constexpr int kFinCols = 16, kFinThreads = 256;
 __global__ void __launch_bounds__(kFinThreads)
     k_finalize_t(DenseTArgs a, int G, DevStatus* __restrict__ status, const float* __restrict__ mu_normf,
                  const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
@@ -1130,6 +1134,15 @@ __global__ void __launch_bounds__(kFinThreads)
     const int ncontrib = (int)(blast - bfirst + 1);
     const int t = threadIdx.x;
     const int jl = t % kFinCols;
+    // the centroids' norms and counts first: their loads overlap the partial sums'
+    float mu2v[4];
+    bool okv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = (t & 31) + 32 * q;
+        okv[q] = i < c && __ldg(counts + i) != 0;
+        mu2v[q] = i < c ? __ldg(mu_normf + i) : 0.f;
+    }
     const int rows = a.stacked ? 64 : 128;   // the stacked kernel has added the lo rows in
     const float* gt = Gpart + (int64_t)tile * a.cmax * rows * kTtN + jc0 + jl;
     const int64_t slot_stride = (int64_t)rows * kTtN;
@@ -1164,8 +1177,8 @@ __global__ void __launch_bounds__(kFinThreads)
         const int jw = warp * kColsPerWarp + k2;
         const int64_t p = col0 + jw;
         if (p >= a.n) break;
-        finalize_warp(p, ys[jw], ylos[jw], [&](int i) { return gs[i * kGs + jw]; }, mu_normf, counts, c,
-                      labels, ub, lb, status, rc_list);
+        finalize_warp(p, ys[jw], ylos[jw], [&](int i) { return gs[i * kGs + jw]; }, mu2v, okv, c, labels, ub, lb,
+                      status, rc_list);
     }
 }
 
@@ -1176,7 +1189,9 @@ __global__ void __launch_bounds__(kFinThreads)
 //   e_h + e_l = y - mu exactly (Knuth's TwoSum), e_h^2 = p + p_err exactly
 //   (product with an FMA), the rest 2 e_h e_l + e_l^2 + p_err is < 2^-22 of
 //   p; the running sum is carried as s_h + s_l with TwoSum on s_h + p.
-// Each thread's (s_h, s_l) becomes one FP64 value; the CTA adds those in FP64.
+// The threads' (s_h, s_l) pairs meet across each warp in the same double-float
+// form (TwoSum on the high parts, which is exact and symmetric, so every lane of
+// the butterfly ends with the same pair); thread 0 adds the 8 warp totals in FP64.
 // Equal inputs give bit-identical results, so exact ties (repeated columns)
 // stay ties and go to the lowest index.
 struct DfSum {
@@ -1195,8 +1210,16 @@ struct DfSum {
         l += __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(p, bp)) + low;
         h = t;
     }
+    // (h, l) += (oh, ol): TwoSum on the high parts, the low parts added
+    __device__ __forceinline__ void merge(float oh, float ol) {
+        const float t = __fadd_rn(h, oh);
+        const float bp = __fsub_rn(t, h);
+        l = __fadd_rn(__fadd_rn(l, ol), __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(oh, bp)));
+        h = t;
+    }
 };
 
+// Returns the distance in thread 0 (0 in the other threads).
 template <typename TY>
 __device__ double block_dist2_exact(const TY* __restrict__ y, const float* __restrict__ mrow, int64_t d,
                                     bool vec, double* red) {
@@ -1205,16 +1228,17 @@ __device__ double block_dist2_exact(const TY* __restrict__ y, const float* __res
         const float4* y4 = reinterpret_cast<const float4*>(y);
         const float4* m4 = reinterpret_cast<const float4*>(mrow);
         const int64_t d4 = d / 4;
-        for (int64_t b0 = threadIdx.x; b0 < d4; b0 += 4 * kThreads) {
-            float4 yv[4], mv[4];
+        // eight 16-byte loads of each operand in flight per round: d = 10^4 is two rounds
+        for (int64_t b0 = threadIdx.x; b0 < d4; b0 += 8 * kThreads) {
+            float4 yv[8], mv[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const int64_t j = b0 + u * kThreads;
                 yv[u] = j < d4 ? __ldg(y4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
                 mv[u] = j < d4 ? __ldg(m4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 a0.add_sq_diff(yv[u].x, mv[u].x);
                 a1.add_sq_diff(yv[u].y, mv[u].y);
                 a0.add_sq_diff(yv[u].z, mv[u].z);
@@ -1225,43 +1249,109 @@ __device__ double block_dist2_exact(const TY* __restrict__ y, const float* __res
     } else {
         for (int64_t r = threadIdx.x; r < d; r += kThreads) a0.add_sq_diff(XLoad<TY>::one(y + r), mrow[r]);
     }
-    double t = warp_sum(((double)a0.h + (double)a0.l) + ((double)a1.h + (double)a1.l));
+    // the threads' sums meet in double-float FP32 across the warp (FP64 per thread
+    // would load this GPU's narrow FP64 pipe with a whole block's worth of work);
+    // only the warps' totals are added in FP64, by thread 0
+    a0.merge(a1.h, a1.l);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, a0.h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, a0.l, o);
+        a0.merge(oh, ol);
+    }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)a0.h + (double)a0.l;
     __syncthreads();
     double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w];
     return s;
 }
 
 // Exact re-decision of near ties, one launch.  The candidate distances of the
 // first rc_cap queued columns are spread over every SM, one CTA per
-// (column, candidate) pair; columns queued beyond rc_cap are decided by one CTA
-// each, candidate after candidate.  The CTA that finishes last (a counter in
-// the status block) then decides the first rc_cap columns over their
-// candidates in increasing index (ties keep the lowest).
+// (column, candidate) pair; the CTA that computes a column's last candidate
+// (a counter in the column's record) decides that column over its candidates
+// in increasing index (ties keep the lowest), so no single CTA decides them
+// all.  Columns queued beyond rc_cap are decided by one CTA each, candidate
+// after candidate.
 template <typename TY>
 __global__ void __launch_bounds__(kThreads)
     k_search_recheck(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
                      DevStatus* __restrict__ status, const float* __restrict__ mu, int c,
                      int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
-                     const RcRec* __restrict__ rc_list, double* __restrict__ rc_dist, int64_t rc_cap) {
+                     RcRec* __restrict__ rc_list, double* __restrict__ rc_dist, int64_t rc_cap) {
     __shared__ double red[kThreads / 32];
-    __shared__ int last_sh;
+    __shared__ int64_t vlist[kThreads];
+    __shared__ int wcount[kThreads / 32];
     const int64_t nall = status->rechecked;
-    if (nall == 0) return;   // the same for every CTA: nobody counts, nothing to decide
+    if (nall == 0) return;
     const int64_t nrc = min(nall, rc_cap);
     const int64_t pairs = nrc * c;
-    for (int64_t pr = blockIdx.x; pr < pairs; pr += gridDim.x) {
-        const int64_t k = pr / c;
-        const int ci = (int)(pr - k * c);
-        const RcRec& rec = rc_list[k];
-        if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;   // uniform over the CTA
-        const double dist = block_dist2_exact<TY>(Y + (int64_t)rec.col * ldy, mu + (int64_t)ci * d, d, vec, red);
-        if (threadIdx.x == 0) rc_dist[pr] = dist;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = blockIdx.x; base < pairs; base += (int64_t)gridDim.x * kThreads) {
+        // the next kThreads pairs of this CTA (pr = base + t G) are tested at once and
+        // the candidates listed in order: a test per pair in turn would cost a
+        // memory round trip each
+        const int64_t pt = base + (int64_t)threadIdx.x * gridDim.x;
+        bool cand_t = false;
+        if (pt < pairs) {
+            const int64_t k = pt / c;
+            const int ci = (int)(pt - k * c);
+            cand_t = (__ldcg(&rc_list[k].mask[ci >> 5]) >> (ci & 31)) & 1u;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, cand_t);
+        if (lane == 0) wcount[warp] = __popc(bal);
         __syncthreads();
+        int off = 0, nv = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            off += w < warp ? wcount[w] : 0;
+            nv += wcount[w];
+        }
+        if (cand_t) vlist[off + __popc(bal & ((1u << lane) - 1u))] = pt;
+        __syncthreads();
+        for (int v = 0; v < nv; ++v) {
+            const int64_t pr = vlist[v];
+            const int64_t k = pr / c;
+            const int ci = (int)(pr - k * c);
+            RcRec* rec = rc_list + k;
+            const double dist = block_dist2_exact<TY>(Y + (int64_t)rec->col * ldy, mu + (int64_t)ci * d, d, vec, red);
+            if (threadIdx.x == 0) {
+                rc_dist[pr] = dist;
+                __threadfence();   // the distance is visible before this candidate counts as done
+                int cand = 0;
+                for (int w = 0; w < kTcMaxClusters / 32; ++w) cand += __popc(rec->mask[w]);
+                if (atomicAdd(&rec->done, 1) == cand - 1) {
+                    // this CTA computed the column's last candidate: it decides the column
+                    // (lowest distance, ties to the lowest index)
+                    __threadfence();
+                    const int64_t col = rec->col;
+                    double best = INFINITY;
+                    int besti = INT_MAX;
+                    for (int cj = 0; cj < c; ++cj) {
+                        if (!((rec->mask[cj >> 5] >> (cj & 31)) & 1u)) continue;
+                        const double dj = cj == ci ? dist : __ldcg(rc_dist + k * c + cj);
+                        if (dj < best) {
+                            best = dj;
+                            besti = cj;
+                        }
+                    }
+                    if (besti < c) {
+                        if (labels[col] != besti) {
+                            labels[col] = besti;
+                            atomicAdd(&status->changed, 1);
+                        }
+                        if (ub) {
+                            ub[col] = (float)(sqrt(best) * (1.0 + 1e-6));
+                            lb[col] = 0.f;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
     }
+    // records beyond the distance buffer: one CTA per column, every candidate in turn
     for (int64_t k = rc_cap + blockIdx.x; k < nall; k += gridDim.x) {
         const RcRec& rec = rc_list[k];
         const int64_t col = rec.col;
@@ -1288,39 +1378,6 @@ __global__ void __launch_bounds__(kThreads)
         }
         __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last_sh = (atomicAdd(&status->recheck_done, 1) == (int)gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last_sh) return;
-    __threadfence();
-    for (int64_t k = threadIdx.x; k < nrc; k += kThreads) {
-        const RcRec& rec = rc_list[k];
-        const int64_t col = rec.col;
-        double best = INFINITY;
-        int besti = INT_MAX;
-        for (int ci = 0; ci < c; ++ci) {
-            if (!((rec.mask[ci >> 5] >> (ci & 31)) & 1u)) continue;
-            const double dist = __ldcg(rc_dist + k * c + ci);
-            if (dist < best) {
-                best = dist;
-                besti = ci;
-            }
-        }
-        if (besti < c) {
-            if (labels[col] != besti) {
-                labels[col] = besti;
-                atomicAdd(&status->changed, 1);
-            }
-            if (ub) {
-                ub[col] = (float)(sqrt(best) * (1.0 + 1e-6));
-                lb[col] = 0.f;
-            }
-        }
-    }
-    if (threadIdx.x == 0) status->recheck_done = 0;
 }
 
 // TF32 hi / lo parts of the centroids, zero-padded to Npad rows of dpad; and,
@@ -1497,7 +1554,10 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
     const bool dense_ok = dtype == 0 && vec && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
                           ldy % 4 == 0 && (reinterpret_cast<uintptr_t>(mu_hi) % 16 == 0) &&
                           (reinterpret_cast<uintptr_t>(mu_lo) % 16 == 0);
-    const int64_t list_max = n / 4;   // larger queued lists use the dense kernel
+    // larger queued lists use the dense kernel: for c <= 128 (256 columns per MMA)
+    // the all-column pass plus its finalize (~97 us at d = n = 10^4) beats the
+    // gathered list kernel from about n / 6 queued columns on
+    const int64_t list_max = (Npad <= 128) ? n / 6 : n / 4;
     bool dense_launched = false;
     // The start event goes into the stream before the host-side preparation of
     // the launch (tensor-map encoding, attributes), so that it is reached while

@@ -42,17 +42,27 @@ __global__ void __launch_bounds__(kThreads)
 
 // Partial column sums of Y over column chunks (FP64): cs[ch d + r] = sum of
 // Y[r + j ldy] over the chunk's columns j.  ||sum_j y_j||^2 = sum_ij y_i . y_j
-// gives sigma^2 without a pass over the n x n Gram matrix.
-constexpr int kSpecSumChunks = 512;
+// gives sigma^2 without a pass over the n x n Gram matrix.  Block (rb, ch):
+// rows 32 rb .. 32 rb + 31 (lanes, coalesced), the chunk's columns split over
+// the 8 warps, the warps' sums added in warp order.
+constexpr int kSpecSumChunks = 64;
 __global__ void __launch_bounds__(kThreads)
     k_spec_colsum(const float* __restrict__ Y, int64_t ldy, int64_t d, int64_t n, int64_t per,
                   double* __restrict__ cs) {
-    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (r >= d) return;
+    __shared__ double part[kThreads / 32][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * 32 + lane;
     const int64_t j0 = (int64_t)blockIdx.y * per, j1 = j0 + per < n ? j0 + per : n;
     double acc = 0.0;
-    for (int64_t j = j0; j < j1; ++j) acc += (double)Y[r + j * ldy];
-    cs[(int64_t)blockIdx.y * d + r] = acc;
+    if (r < d)
+        for (int64_t j = j0 + warp; j < j1; j += kThreads / 32) acc += (double)Y[r + j * ldy];
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && r < d) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += part[w][lane];
+        cs[(int64_t)blockIdx.y * d + r] = t;
+    }
 }
 
 // sigma^2 = scale * (2 n sum||y||^2 - 2 ||sum y||^2) / (n (n - 1)), the mean
@@ -168,7 +178,7 @@ constexpr int kSymSmemFloats = 12288;   // the CTA's rows of Y (48 KB)
 // consecutive (one 16-byte load of rows 4 lane .. 4 lane + 3) when VEC = true
 // (n % 4 == 0), which doubles the bytes each load instruction moves.
 template <int BMAX, int CPL, bool VEC>
-__global__ void __launch_bounds__(kSymWarps * 32)
+__global__ void __launch_bounds__(kSymWarps * 32, 2)
     k_spec_symm(const float* __restrict__ M, const float* __restrict__ r, int64_t n, const float* __restrict__ Y,
                 int b, int64_t kc, float* __restrict__ P) {
     __shared__ __align__(16) float ys[kSymSmemFloats];
@@ -190,25 +200,8 @@ __global__ void __launch_bounds__(kSymWarps * 32)
 #pragma unroll
         for (int q = 0; q < BMAX; ++q) acc[u][q] = 0.f;
     const bool all_live = row_of(CPL - 1) < n;
-#pragma unroll 8
-    for (int64_t kk = 0; kk < kn; ++kk) {
-        float m[CPL];
-        const float* mc = M + (k0 + kk) * n;
-        if (VEC) {
-            if (all_live) {
-                const float4 v = __ldcs(reinterpret_cast<const float4*>(mc + row_of(0)));
-                m[0] = v.x;
-                m[1 % CPL] = v.y;
-                m[2 % CPL] = v.z;
-                m[3 % CPL] = v.w;
-            } else {
-#pragma unroll
-                for (int u = 0; u < CPL; ++u) m[u] = row_of(u) < n ? __ldcs(mc + row_of(u)) : 0.f;
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < CPL; ++u) m[u] = row_of(u) < n ? __ldcs(mc + row_of(u)) : 0.f;
-        }
+    // acc[u][q] += m[u] * y[q] for one row kk of Y (broadcast from shared memory)
+    auto fma_row = [&](const float* m, int64_t kk) {
         const float4* yr = reinterpret_cast<const float4*>(ys + kk * BMAX);
 #pragma unroll
         for (int q4 = 0; q4 < BMAX / 4; ++q4) {
@@ -221,6 +214,29 @@ __global__ void __launch_bounds__(kSymWarps * 32)
                 acc[u][4 * q4 + 3] = fmaf(m[u], y.w, acc[u][4 * q4 + 3]);
             }
         }
+    };
+    int64_t kk = 0;
+    if (VEC && all_live) {
+        // eight columns' loads issued together, then their products: the loads of
+        // one batch overlap each other (and other warps' products)
+        const float* mc0 = M + k0 * n + row_of(0);
+        for (; kk + 8 <= kn; kk += 8) {
+            float4 mv[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) mv[t] = __ldcs(reinterpret_cast<const float4*>(mc0 + (kk + t) * n));
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float m4[4] = {mv[t].x, mv[t].y, mv[t].z, mv[t].w};
+                fma_row(m4, kk + t);
+            }
+        }
+    }
+    for (; kk < kn; ++kk) {
+        float m[CPL];
+        const float* mc = M + (k0 + kk) * n;
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) m[u] = row_of(u) < n ? __ldcs(mc + row_of(u)) : 0.f;
+        fma_row(m, kk);
     }
     float* pc = P + (int64_t)blockIdx.y * b * n;
 #pragma unroll
@@ -244,8 +260,12 @@ __global__ void __launch_bounds__(kThreads)
     W[e] = s * r[e % n];
 }
 
-// out[i + j b1] = sum_k A[k + i n] B[k + j n] in FP64 (one CTA per entry):
-// the b1 x b2 Gram or Rayleigh-quotient matrices of n-row blocks.
+// out[i + j b1] = sum_k A[k + i n] B[k + j n] (one CTA per entry): the b1 x b2
+// Gram or Rayleigh-quotient matrices of n-row blocks.  Each product is exact
+// as an FP32 pair (hi = a b, lo = fma(a, b, -hi)); a thread adds its share in
+// double-float FP32 (TwoSum on the hi parts, error about 2^-44 of the sum of
+// |products|), and the threads' sums are added in FP64 in a fixed order.  One
+// FP64 operation per element would be bound by this GPU's narrow FP64 pipe.
 __global__ void __launch_bounds__(kThreads)
     k_spec_gram_small(const float* __restrict__ A, const float* __restrict__ B, int64_t n, int b1,
                       double* __restrict__ out) {
@@ -253,8 +273,17 @@ __global__ void __launch_bounds__(kThreads)
     const int i = blockIdx.x, j = blockIdx.y;
     const float* a = A + (int64_t)i * n;
     const float* bb = B + (int64_t)j * n;
-    double acc = 0.0;
-    for (int64_t k = threadIdx.x; k < n; k += kThreads) acc += (double)a[k] * (double)bb[k];
+    float sh = 0.f, sl = 0.f;
+    for (int64_t k = threadIdx.x; k < n; k += kThreads) {
+        const float x = a[k], y = bb[k];
+        const float ph = x * y, pl = fmaf(x, y, -ph);
+        const float t = sh + ph, bv = t - sh;
+        float e = (sh - (t - bv)) + (ph - bv);
+        e += sl + pl;
+        sh = t + e;
+        sl = e - (sh - t);
+    }
+    double acc = (double)sh + (double)sl;
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -269,13 +298,17 @@ __global__ void __launch_bounds__(kThreads)
 // times its largest diagonal entry (so that rounding cannot break the
 // factorisation of a numerically rank-deficient block), G = R^T R, and
 // Q = R^{-1} (upper triangular, column-major FP32) for Y <- Y Q.  One CTA.
+// Each square root and reciprocal is taken once, by one thread: on this GPU
+// the FP64 pipe is narrow, and the same operation in every thread would cost
+// the whole block's worth of it.
 constexpr int kCholThreads = 256;
 __global__ void __launch_bounds__(kCholThreads)
     k_spec_chol_inv(const double* __restrict__ G, int b, float* __restrict__ Q) {
     extern __shared__ double cm[];
     double* R = cm;             // b x b, column-major, upper triangle used
     double* V = cm + b * b;     // R^{-1}
-    __shared__ double shift;
+    double* rd = V + b * b;     // 1 / R[i][i]
+    __shared__ double shift, pinv;
     for (int e = threadIdx.x; e < b * b; e += kCholThreads) {
         R[e] = G[e];
         V[e] = 0.0;
@@ -289,25 +322,30 @@ __global__ void __launch_bounds__(kCholThreads)
     __syncthreads();
     // right-looking Cholesky on the upper triangle: R[k][j] for j >= k
     for (int k = 0; k < b; ++k) {
-        __syncthreads();
-        const double piv = sqrt(fmax(R[k + k * b] + shift, 1e-300));
-        __syncthreads();
-        for (int j = k + threadIdx.x; j < b; j += kCholThreads) R[k + j * b] = (j == k) ? piv : R[k + j * b] / piv;
-        __syncthreads();
-        // trailing update: R[i][j] -= R[k][i] R[k][j], k < i <= j
-        for (int e = threadIdx.x; e < b * b; e += kCholThreads) {
-            const int ii = e % b, jj = e / b;
-            if (ii > k && jj >= ii) R[ii + jj * b] -= R[k + ii * b] * R[k + jj * b];
+        if (threadIdx.x == 0) {
+            const double piv = sqrt(fmax(R[k + k * b] + shift, 1e-300));
+            R[k + k * b] = piv;
+            pinv = 1.0 / piv;
+            rd[k] = pinv;
         }
+        __syncthreads();
+        for (int j = k + 1 + threadIdx.x; j < b; j += kCholThreads) R[k + j * b] *= pinv;
+        __syncthreads();
+        // trailing update: R[i][j] -= R[k][i] R[k][j], k < i <= j (thread per (i, j) of the trailing block)
+        const int m = b - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += kCholThreads) {
+            const int ii = k + 1 + e % m, jj = k + 1 + e / m;
+            if (jj >= ii) R[ii + jj * b] -= R[k + ii * b] * R[k + jj * b];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // V = R^{-1}, column by column: V[j][j] = 1/R[j][j], V[i][j] = -(sum_{k=i+1..j} R[i][k] V[k][j]) / R[i][i]
     for (int j = threadIdx.x; j < b; j += kCholThreads) {
-        V[j + j * b] = 1.0 / R[j + j * b];
+        V[j + j * b] = rd[j];
         for (int i = j - 1; i >= 0; --i) {
             double sacc = 0.0;
             for (int k = i + 1; k <= j; ++k) sacc += R[i + k * b] * V[k + j * b];
-            V[i + j * b] = -sacc / R[i + i * b];
+            V[i + j * b] = -sacc * rd[i];
         }
     }
     __syncthreads();
@@ -315,34 +353,41 @@ __global__ void __launch_bounds__(kCholThreads)
 }
 
 // Symmetric eigen-decomposition of H (b x b, FP64 in, symmetrised) by cyclic
-// Jacobi with the round-robin pair order (b/2 disjoint rotations per step).
+// Jacobi with the round-robin pair order (bp/2 disjoint rotations per step,
+// bp = b rounded up to even; the schedule of every step is tabulated once).
 // The rotations run in FP32: on this GPU an FP64 operation costs tens of FP32
-// ones, and the eigenvectors leave as FP32 anyway.  The loop ends when the
-// off-diagonal part is below 1e-6 of the matrix (Frobenius) or a whole sweep
-// turned by no angle above 1e-7.  The
-// eigenvalues are the FP64 Rayleigh quotients v^T H v of the FP32 eigenvector
-// columns, whose error is second order in the vectors'.  Writes them in
-// descending order (ties by index) and the matching vectors as the columns of
-// Q (b x b, FP32, column-major).  One CTA.
-// NT threads: one warp when the padded order is at most 32 (its barriers are
-// then cheap), 256 otherwise.
+// ones, and the eigenvectors leave as FP32 anyway.  A pair is rotated only
+// when |a_pq| > max(1e-6 sqrt(|a_pp a_qq|), 2e-7 ||A||_F); the loop ends after a sweep with no
+// rotation, or when the off-diagonal part is below 1e-6 of the matrix
+// (Frobenius).  The eigenvalues are the FP64 Rayleigh quotients
+// v^T H v / v^T v of the FP32 eigenvector columns, whose error is second order
+// in the vectors'.  Writes them in descending order (ties by index) and
+// the matching vectors as the columns of Q (b x b, FP32, column-major).
+// One CTA of NT threads.  A step is one phase after the angles: the pairs
+// partition the indices, so every entry of A lies in exactly one 2 x 2 block
+// (pair k1's rows, pair k2's columns), which a thread turns by both rotations
+// (rows first, then columns, the same operations as two separate passes).
+constexpr float kJacRel = 1e-6f, kJacAbs = 2e-7f;
 template <int NT>
 __global__ void __launch_bounds__(NT)
     k_spec_jacobi(const double* __restrict__ H, int b, float* __restrict__ Q, double* __restrict__ evals,
                   int max_sweeps) {
     extern __shared__ double sm[];
     const int bp = b + (b & 1);          // padded to even (a zero row and column)
+    const int half = bp / 2;
     double* hs = sm;                     // b x b, the symmetrised H
     double* rq = hs + b * b;             // bp Rayleigh quotients
     float* a = reinterpret_cast<float*>(rq + bp);   // bp x bp
     float* v = a + bp * bp;              // bp x bp
-    float* cs = v + bp * bp;             // bp/2 cosines
-    float* sn = cs + bp / 2;             // bp/2 sines
-    int* pr = reinterpret_cast<int*>(sn + bp / 2);   // bp pair slots
+    float* cs = v + bp * bp;             // half cosines
+    float* sn = cs + half;               // half sines
+    int2* sched = reinterpret_cast<int2*>(sn + half);   // (bp - 1) x half pairs (p < q); 8-byte aligned:
+                                                       // 2 bp^2 + 2 half floats precede it
     __shared__ float red[NT / 32][2];
     __shared__ int stop, turned;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int e = threadIdx.x; e < bp * bp; e += NT) {
+    __shared__ float anorm;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < bp * bp; e += NT) {
         const int i = e % bp, j = e / bp;
         double x = 0.0;
         if (i < b && j < b) {
@@ -352,23 +397,31 @@ __global__ void __launch_bounds__(NT)
         a[e] = (float)x;
         v[e] = (i == j) ? 1.f : 0.f;
     }
+    // step t: slot 0 holds index 0, slot s >= 1 holds 1 + (s - 1 - t) mod (bp - 1);
+    // pair k joins slots k and bp - 1 - k
+    for (int e = tid; e < (bp - 1) * half; e += NT) {
+        const int t = e / half, k = e % half;
+        auto at = [&](int slot) { return slot == 0 ? 0 : 1 + ((slot - 1 - t) % (bp - 1) + (bp - 1)) % (bp - 1); };
+        int p = at(k), q = at(bp - 1 - k);
+        if (p > q) { const int x = p; p = q; q = x; }
+        sched[e] = make_int2(p, q);
+    }
     __syncthreads();
-    const int half = bp / 2;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        float o = 0.f, t = 0.f;
-        for (int e = threadIdx.x; e < bp * bp; e += NT) {
+        float o = 0.f, t2 = 0.f;
+        for (int e = tid; e < bp * bp; e += NT) {
             const float x = a[e];
-            t = fmaf(x, x, t);
+            t2 = fmaf(x, x, t2);
             if (e % bp != e / bp) o = fmaf(x, x, o);
         }
         o = warp_sum(o);
-        t = warp_sum(t);
+        t2 = warp_sum(t2);
         if (lane == 0) {
             red[warp][0] = o;
-            red[warp][1] = t;
+            red[warp][1] = t2;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             float oo = 0.f, tt = 0.f;
             for (int w = 0; w < NT / 32; ++w) {
                 oo += red[w][0];
@@ -376,85 +429,84 @@ __global__ void __launch_bounds__(NT)
             }
             stop = (oo <= 1e-12f * tt || tt == 0.f) ? 1 : 0;
             turned = 0;
+            anorm = sqrtf(tt);
         }
         __syncthreads();
         if (stop) break;
         for (int step = 0; step < bp - 1; ++step) {
-            // round-robin: slot 0 fixed, the others rotate by `step`
-            if (threadIdx.x < bp) {
-                const int idx = threadIdx.x;
-                const int pos = (idx == 0) ? 0 : 1 + (idx - 1 + step) % (bp - 1);
-                pr[pos] = idx;
-            }
-            __syncthreads();
-            // pair k = (pr[k], pr[bp - 1 - k])
-            if (threadIdx.x < half) {
-                const int k = threadIdx.x;
-                int p = pr[k], q = pr[bp - 1 - k];
-                if (p > q) { const int tq = p; p = q; q = tq; }
+            const int2* pairs = sched + step * half;
+            for (int k = tid; k < half; k += NT) {
+                const int p = pairs[k].x, q = pairs[k].y;
                 const float apq = a[p + q * bp];
+                const float app = a[p + p * bp], aqq = a[q + q * bp];
                 float c = 1.f, s = 0.f;
-                if (apq != 0.f) {
-                    const float app = a[p + p * bp], aqq = a[q + q * bp];
-                    const float tau = (aqq - app) / (2.f * apq);
+                // rotate only where a_pq stands above FP32 rounding noise: relative to its
+                // diagonal pair (the classical threshold for Jacobi in finite precision) and
+                // to the whole matrix (rotations leave noise of that size in every entry)
+                if (fabsf(apq) > fmaxf(kJacRel * sqrtf(fabsf(app) * fabsf(aqq)), kJacAbs * anorm)) {
                     // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), the smaller root; for
-                    // huge |tau| the rotation is below FP32 resolution and t = 1 / (2 tau)
+                    // huge |tau| the rotation is below FP32 resolution and t = 1 / (2 tau).
+                    // Approximate divisions: any (c, s) with c^2 + s^2 = 1 is a rotation,
+                    // and one that leaves an ulp of a_pq behind is as good as exact here
+                    const float tau = __fdividef(aqq - app, 2.f * apq);
                     const float at = fabsf(tau);
-                    const float tr = at > 1e18f ? 0.5f / at : 1.f / (at + sqrtf(fmaf(at, at, 1.f)));
+                    const float tr = at > 1e18f ? __fdividef(0.5f, at) : __fdividef(1.f, at + sqrtf(fmaf(at, at, 1.f)));
                     const float tt = tau >= 0.f ? tr : -tr;
                     c = rsqrtf(fmaf(tt, tt, 1.f));
                     s = tt * c;
-                    if (fabsf(s) > 1e-7f) turned = 1;
+                    turned = 1;
                 }
                 cs[k] = c;
                 sn[k] = s;
             }
             __syncthreads();
-            // rows: A <- J^T A (each pair updates its two rows, every column)
-            for (int e = threadIdx.x; e < half * bp; e += NT) {
-                const int k = e / bp, col = e % bp;
-                int p = pr[k], q = pr[bp - 1 - k];
-                if (p > q) { const int tq = p; p = q; q = tq; }
-                const float c = cs[k], s = sn[k];
-                const float xp = a[p + col * bp], xq = a[q + col * bp];
-                a[p + col * bp] = c * xp - s * xq;
-                a[q + col * bp] = s * xp + c * xq;
+            // A <- J^T A J by 2 x 2 blocks: rows of pair k1, columns of pair k2
+            for (int e = tid; e < half * half; e += NT) {
+                const int k2 = e / half, k1 = e - k2 * half;
+                const int p1 = pairs[k1].x, q1 = pairs[k1].y, p2 = pairs[k2].x, q2 = pairs[k2].y;
+                const float c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+                const float xpp = a[p1 + p2 * bp], xpq = a[p1 + q2 * bp];
+                const float xqp = a[q1 + p2 * bp], xqq = a[q1 + q2 * bp];
+                const float rpp = c1 * xpp - s1 * xqp, rqp = s1 * xpp + c1 * xqp;   // rows (J^T A)
+                const float rpq = c1 * xpq - s1 * xqq, rqq = s1 * xpq + c1 * xqq;
+                a[p1 + p2 * bp] = c2 * rpp - s2 * rpq;                                 // columns (. J)
+                a[p1 + q2 * bp] = s2 * rpp + c2 * rpq;
+                a[q1 + p2 * bp] = c2 * rqp - s2 * rqq;
+                a[q1 + q2 * bp] = s2 * rqp + c2 * rqq;
             }
-            __syncthreads();
-            // columns: A <- A J, V <- V J
-            for (int e = threadIdx.x; e < half * bp; e += NT) {
-                const int k = e / bp, row = e % bp;
-                int p = pr[k], q = pr[bp - 1 - k];
-                if (p > q) { const int tq = p; p = q; q = tq; }
+            // V <- V J (pair k's two columns, row i)
+            for (int e = tid; e < bp * half; e += NT) {
+                const int k = e / bp, i = e - k * bp;
+                const int p = pairs[k].x, q = pairs[k].y;
                 const float c = cs[k], s = sn[k];
-                const float xp = a[row + p * bp], xq = a[row + q * bp];
-                a[row + p * bp] = c * xp - s * xq;
-                a[row + q * bp] = s * xp + c * xq;
-                const float vp = v[row + p * bp], vq = v[row + q * bp];
-                v[row + p * bp] = c * vp - s * vq;
-                v[row + q * bp] = s * vp + c * vq;
+                const float vp = v[i + p * bp], vq = v[i + q * bp];
+                v[i + p * bp] = c * vp - s * vq;
+                v[i + q * bp] = s * vp + c * vq;
             }
             __syncthreads();
         }
-        // a sweep whose rotations were all below FP32 resolution changes nothing more
+        // a sweep without a rotation changes nothing more
         if (!turned) break;
     }
-    // Rayleigh quotients in FP64: one warp per column j, lanes over rows i
+    // Rayleigh quotients v^T H v / v^T v in FP64: one warp per column j, lanes over rows i
     for (int j = warp; j < bp; j += NT / 32) {
-        double acc = 0.0;
+        double acc = 0.0, nrm = 0.0;
         if (j < b) {
             for (int i = lane; i < b; i += 32) {
                 double hv = 0.0;
                 for (int k = 0; k < b; ++k) hv = fma(hs[i + k * b], (double)v[k + j * bp], hv);
-                acc = fma((double)v[i + j * bp], hv, acc);
+                const double vi = (double)v[i + j * bp];
+                acc = fma(vi, hv, acc);
+                nrm = fma(vi, vi, nrm);
             }
         }
         acc = warp_sum(acc);
-        if (lane == 0) rq[j] = acc;
+        nrm = warp_sum(nrm);
+        if (lane == 0) rq[j] = nrm > 0.0 ? acc / nrm : 0.0;
     }
     __syncthreads();
     // descending order of the first b eigenvalues (selection by rank; ties by index)
-    for (int j = threadIdx.x; j < b; j += NT) {
+    for (int j = tid; j < b; j += NT) {
         const double x = rq[j];
         int rank = 0;
         for (int k = 0; k < b; ++k) {
@@ -523,14 +575,16 @@ inline unsigned blocks_for(int64_t work, int per) { return (unsigned)((work + pe
 
 cudaError_t launch_spec_affinity(const float* Y, int64_t ldy, int64_t d, int64_t n, double scale, float* G,
                                  float* sqn, double* part, int parts, double* colsum, double* sig, double* deg,
-                                 float* rinv, DevStatus* status, cudaStream_t st) {
+                                 float* rinv, DevStatus* status, cudaEvent_t g0, cudaEvent_t g1, cudaStream_t st) {
     count_launches(5);
     k_spec_norms<<<parts, kThreads, 0, st>>>(Y, ldy, d, n, sqn, part);
     const int64_t per = (n + kSpecSumChunks - 1) / kSpecSumChunks;
-    k_spec_colsum<<<dim3(blocks_for(d, kThreads), kSpecSumChunks), kThreads, 0, st>>>(Y, ldy, d, n, per, colsum);
+    k_spec_colsum<<<dim3(blocks_for(d, 32), kSpecSumChunks), kThreads, 0, st>>>(Y, ldy, d, n, per, colsum);
     k_spec_sigma<<<1, kThreads, 0, st>>>(part, parts, colsum, d, n, scale, sig);
+    if (g0 && cudaEventRecord(g0, st) != cudaSuccess) return cudaGetLastError();
     const cudaError_t e = launch_gram_tc(Y, ldy, d, n, G, status, st);
     if (e != cudaSuccess) return e;
+    if (g1 && cudaEventRecord(g1, st) != cudaSuccess) return cudaGetLastError();
     k_spec_affinity<<<(unsigned)n, kThreads, 0, st>>>(G, n, sqn, sig, deg);
     k_spec_rinv<<<blocks_for(n, kThreads), kThreads, 0, st>>>(deg, n, rinv);
     return cudaGetLastError();
@@ -555,7 +609,7 @@ namespace {
 int spec_bmax(int b) { return b <= 16 ? 16 : b <= 32 ? 32 : b <= 48 ? 48 : 72; }
 int64_t spec_kc(int64_t n, int b) {
     const int bm = spec_bmax(b);
-    const int cpl = (bm == 16 && n % 4 == 0) ? 4 : bm <= 32 ? 2 : 1;
+    const int cpl = (bm == 16 && n % 4 == 0) ? 4 : bm <= 16 ? 2 : 1;
     const int64_t iblocks = (n + kSymWarps * 32 * cpl - 1) / (kSymWarps * 32 * cpl);
     // about two (16-byte loads) or four CTAs per SM over the grid, each chunk a
     // multiple of 8 rows of Y: fewer chunks keep the partial products small
@@ -577,13 +631,13 @@ cudaError_t launch_spec_symm(const float* M, const float* r, int64_t n, const fl
     count_launches(2);
     const int bm = spec_bmax(b);
     const bool vec = bm == 16 && n % 4 == 0;
-    const int cpl = vec ? 4 : bm <= 32 ? 2 : 1;
+    const int cpl = vec ? 4 : bm <= 16 ? 2 : 1;
     const int64_t kc = spec_kc(n, b), chunks = (n + kc - 1) / kc;
     const dim3 grid((unsigned)((n + kSymWarps * 32 * cpl - 1) / (kSymWarps * 32 * cpl)), (unsigned)chunks);
     const unsigned thr = kSymWarps * 32;
     if (vec) k_spec_symm<16, 4, true><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
     else if (bm == 16) k_spec_symm<16, 2, false><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
-    else if (bm == 32) k_spec_symm<32, 2, false><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
+    else if (bm == 32) k_spec_symm<32, 1, false><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
     else if (bm == 48) k_spec_symm<48, 1, false><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
     else k_spec_symm<72, 1, false><<<grid, thr, 0, st>>>(M, r, n, Y, b, kc, P);
     const int64_t nb = n * (int64_t)b;
@@ -607,7 +661,7 @@ cudaError_t launch_spec_cholqr2(float* Y, float* T, int64_t n, int b, double* G,
         count_launches(1);
         e = allow_max_dynamic_smem((const void*)k_spec_chol_inv);
         if (e != cudaSuccess) return e;
-        k_spec_chol_inv<<<1, kCholThreads, sizeof(double) * 2 * b * b, st>>>(G, b, Q);
+        k_spec_chol_inv<<<1, kCholThreads, sizeof(double) * (2 * b * b + b), st>>>(G, b, Q);
         e = launch_spec_rotate(Y, Q, T, n, b, st);
         if (e != cudaSuccess) return e;
         e = cudaMemcpyAsync(Y, T, sizeof(float) * (size_t)n * b, cudaMemcpyDeviceToDevice, st);
@@ -617,22 +671,28 @@ cudaError_t launch_spec_cholqr2(float* Y, float* T, int64_t n, int b, double* G,
 }
 
 size_t spec_jacobi_smem(int b) {
-    const int bp = b + (b & 1);
-    return sizeof(double) * ((size_t)b * b + bp) + sizeof(float) * (2 * (size_t)bp * bp + bp) +
-           sizeof(int) * bp;
+    const int bp = b + (b & 1), half = bp / 2;
+    return sizeof(double) * ((size_t)b * b + bp) + sizeof(float) * (2 * (size_t)bp * bp + 2 * half) +
+           sizeof(int2) * (size_t)(bp - 1) * half;
 }
 
 cudaError_t launch_spec_jacobi(const double* H, int b, float* Q, double* evals, cudaStream_t st) {
     count_launches(1);
     const size_t smem = spec_jacobi_smem(b);
-    if (b + (b & 1) <= 32) {
-        cudaError_t e = allow_max_dynamic_smem((const void*)k_spec_jacobi<32>);
+    const int bp = b + (b & 1);
+    // threads: at least max(half^2, bp half) (one block entry or V entry each) where it fits
+    if (bp <= 16) {
+        cudaError_t e = allow_max_dynamic_smem((const void*)k_spec_jacobi<128>);
         if (e != cudaSuccess) return e;
-        k_spec_jacobi<32><<<1, 32, smem, st>>>(H, b, Q, evals, 60);
+        k_spec_jacobi<128><<<1, 128, smem, st>>>(H, b, Q, evals, 60);
+    } else if (bp <= 32) {
+        cudaError_t e = allow_max_dynamic_smem((const void*)k_spec_jacobi<512>);
+        if (e != cudaSuccess) return e;
+        k_spec_jacobi<512><<<1, 512, smem, st>>>(H, b, Q, evals, 60);
     } else {
-        cudaError_t e = allow_max_dynamic_smem((const void*)k_spec_jacobi<256>);
+        cudaError_t e = allow_max_dynamic_smem((const void*)k_spec_jacobi<1024>);
         if (e != cudaSuccess) return e;
-        k_spec_jacobi<256><<<1, 256, smem, st>>>(H, b, Q, evals, 60);
+        k_spec_jacobi<1024><<<1, 1024, smem, st>>>(H, b, Q, evals, 60);
     }
     return cudaGetLastError();
 }

@@ -214,19 +214,35 @@ __global__ void __launch_bounds__(kDeltaThreads)
         const int b0 = boff[i], b1 = boff[i + 1];
         if (b0 == b1) continue;
         float hi = 0.f, lo = 0.f;
-        for (int q = b0; q < b1; ++q) {
-            const int2 e = contrib[q];   // column, sign
+        // the value of bucket entry q at row r, signed
+        auto value = [&](int2 e) -> float {   // (column, sign)
             const int64_t j = e.x;
             float x;
             if (MODE == kSumX) x = XLoad<TX>::one(X + j * ldx + r);
             else if (MODE == kSumL) x = L[j * lds + r];
             else x = (XLoad<TX>::one(X + j * ldx + r) - S[j * lds + r]) + Th[j * lds + r] * inv_rho;
-            if (e.y < 0) x = -x;
-            const float t = hi + x;   // TwoSum(hi, x)
+            return e.y < 0 ? -x : x;
+        };
+        auto add = [&](float x) {   // TwoSum(hi, x)
+            const float t = hi + x;
             const float bp = t - hi;
             lo += (hi - (t - bp)) + (x - bp);
             hi = t;
+        };
+        // eight entries' loads in flight at once, added in bucket order (a load per
+        // entry in turn would cost a memory round trip each)
+        int q = b0;
+        for (; q + 8 <= b1; q += 8) {
+            int2 e[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) e[u] = contrib[q + u];
+            float x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = value(e[u]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) add(x[u]);
         }
+        for (; q < b1; ++q) add(value(contrib[q]));
         sums[(int64_t)i * d + r] += (double)hi + (double)lo;
     }
 }

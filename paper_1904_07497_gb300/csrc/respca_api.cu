@@ -293,10 +293,35 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
     }
     DevStatus* dstat = P<DevStatus>(h->status);
     CK(cudaMemsetAsync(&dstat->timeout, 0, sizeof(int32_t), st));
+    // with cfg.timing, events around the Gram kernel and each product with M (a
+    // synchronisation per product: timing mode only)
+    const bool timing = h->cfg.timing != 0;
+    double ms_gram = 0.0, ms_prod = 0.0;
     CK(launch_spec_affinity(Y, ldy, d, n, h->cfg.spectral_scale, M, P<float>(h->sp_sqn), P<double>(h->sp_part),
                             parts, P<double>(h->sp_gsum), P<double>(h->sp_sig), P<double>(h->sp_deg),
-                            P<float>(h->sp_sqn), dstat, st));
+                            P<float>(h->sp_sqn), dstat, timing ? h->evk0 : nullptr, timing ? h->evk1 : nullptr,
+                            st));
+    if (timing) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(h->evk1));
+        CK(cudaEventElapsedTime(&ms, h->evk0, h->evk1));
+        ms_gram = ms;
+    }
     const float* rinv = P<float>(h->sp_sqn);   // deg^{-1/2}, written over the column norms
+    auto product = [&](const float* Yin, float* Wout) -> cudaError_t {
+        if (timing) {
+            cudaError_t e = cudaEventRecord(h->evk0, st);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = launch_spec_symm(M, rinv, n, Yin, b, Wout, P<float>(h->sp_P), st);
+        if (e != cudaSuccess || !timing) return e;
+        if ((e = cudaEventRecord(h->evk1, st)) != cudaSuccess || (e = cudaEventSynchronize(h->evk1)) != cudaSuccess)
+            return e;
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, h->evk0, h->evk1);
+        ms_prod += ms;
+        return e;
+    };
     float* Yb = P<float>(h->sp_Y);   // current orthonormal block (n x b)
     float* W = P<float>(h->sp_W);    // M Yb
     float* T = P<float>(h->sp_T);    // scratch
@@ -311,7 +336,7 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
     double lo = -1.0;   // the spectrum of M lies in [-1, 1]
     for (;;) {
         // Rayleigh-Ritz on span(Yb): H = Yb^T M Yb, rotate to the Ritz vectors
-        CK(launch_spec_symm(M, rinv, n, Yb, b, W, P<float>(h->sp_P), st));
+        CK(product(Yb, W));
         ++matvecs;
         CK(launch_spec_gram_small(Yb, W, n, b, b, P<double>(h->sp_H), st));
         CK(launch_spec_jacobi(P<double>(h->sp_H), b, P<float>(h->sp_Q), P<double>(h->sp_ev), st));
@@ -338,7 +363,7 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
         float* y2 = Z;
         CK(launch_spec_axpby(y1, W, y0, nullptr, nb, (float)(1.0 / e), (float)(-cen / e), 0.f, st));
         for (int k = 2; k <= kSpecDegree; ++k) {
-            CK(launch_spec_symm(M, rinv, n, y1, b, W, P<float>(h->sp_P), st));   // W as scratch: M y1
+            CK(product(y1, W));   // W as scratch: M y1
             ++matvecs;
             CK(launch_spec_axpby(y2, W, y1, y0, nb, (float)(2.0 / e), (float)(-2.0 * cen / e), -1.f, st));
             float* t = y0;
@@ -364,6 +389,8 @@ respca_status spectral_labels_impl(respca_ctx* h, const float* Y, int64_t ldy, i
     if (info) {
         info->outer_iters = outer;
         info->matvecs = matvecs;
+        info->ms_gram = ms_gram;
+        info->ms_products = ms_prod;
         info->residual = rmax;
         info->sigma2 = sig2;
         info->theta_c = ev[c - 1];

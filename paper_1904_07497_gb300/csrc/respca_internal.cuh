@@ -53,7 +53,6 @@ struct DevStatus {
     double ramp_r2;         // ||X - mu_p||_F^2 (ramp statistics)
     unsigned long long ramp_ratio;  // bits of max_j ||X_j - mu_p|| / sep(p)
     unsigned int ramp_abs;  // bits of max |X - mu_p|
-    int32_t recheck_done;   // CTAs of the near-tie re-decision that finished their distances
     int32_t flagged;        // columns queued for a nearest-centroid search
     int32_t changed;        // labels changed by the last assignment pass
     int32_t rechecked;      // near-tie columns re-decided in FP64
@@ -217,7 +216,8 @@ constexpr int kTcMaxClusters = 256;
 struct RcRec {
     int32_t col;
     uint32_t mask[kTcMaxClusters / 32];
-    int32_t pad[3];
+    int32_t done;     // candidate distances of this column computed so far (re-decision)
+    int32_t pad[2];
 };
 int tc_npad(int c);
 // Raises a kernel's dynamic shared memory cap to the device's opt-in limit,
@@ -412,7 +412,7 @@ cudaError_t launch_gram_tc(const float* Y, int64_t ldy, int64_t d, int64_t n, fl
                            cudaStream_t st);
 cudaError_t launch_spec_affinity(const float* Y, int64_t ldy, int64_t d, int64_t n, double scale, float* G,
                                  float* sqn, double* part, int parts, double* colsum, double* sig, double* deg,
-                                 float* rinv, DevStatus* status, cudaStream_t st);
+                                 float* rinv, DevStatus* status, cudaEvent_t g0, cudaEvent_t g1, cudaStream_t st);
 cudaError_t launch_spec_start(float* Y, int64_t n, int b, uint64_t seed, cudaStream_t st);
 cudaError_t launch_spec_axpby(float* out, const float* T, const float* Y, const float* Yp, int64_t count,
                               float alpha, float beta, float gamma, cudaStream_t st);

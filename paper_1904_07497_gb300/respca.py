@@ -42,7 +42,8 @@ class respca_spectral_info(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int32), ("matvecs", ctypes.c_int32),
                 ("residual", ctypes.c_double), ("sigma2", ctypes.c_double),
                 ("theta_c", ctypes.c_double), ("theta_next", ctypes.c_double),
-                ("lloyd_passes", ctypes.c_int32), ("converged", ctypes.c_int32)]
+                ("lloyd_passes", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("ms_gram", ctypes.c_double), ("ms_products", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
