@@ -95,7 +95,7 @@ __device__ void finalize_scores(int64_t col, float y2, Gather gather,
                                 const int32_t* __restrict__ counts, int c,
                                 int32_t* __restrict__ labels, float* __restrict__ ub,
                                 float* __restrict__ lb, DevStatus* __restrict__ status,
-                                RcRec* __restrict__ rc, float ylo = 0.f) {
+                                const RcQueue& rc, float ylo = 0.f) {
     float bs = INFINITY, ss = INFINITY, be = 0.f, se = 0.f;
     int bi = INT_MAX, si = INT_MAX;
     for (int i0 = 0; i0 < c; i0 += 8) {
@@ -137,7 +137,7 @@ __device__ void finalize_scores(int64_t col, float y2, Gather gather,
             }
         }
         const int slot = atomicAdd(&status->rechecked, 1);
-        RcRec* r = rc + slot;
+        RcRec* r = rc.rec + slot;
         for (int w = 0; w < kTcMaxClusters / 32; ++w) r->mask[w] = 0u;
         for (int i0 = 0; i0 < c; i0 += 8) {
             float g[8];
@@ -153,6 +153,13 @@ __device__ void finalize_scores(int64_t col, float y2, Gather gather,
         }
         r->col = (int32_t)col;
         r->done = 0;
+        if (slot < rc.cap) {
+            int cnt = 0;
+            for (int w = 0; w < kTcMaxClusters / 32; ++w) cnt += __popc(r->mask[w]);
+            int at = atomicAdd(&status->rc_pairs, cnt);
+            for (int i = 0; i < c; ++i)
+                if ((r->mask[i >> 5] >> (i & 31)) & 1u) rc.pairs[at++] = slot * c + i;
+        }
         return;
     }
     const float yerr = 1e-5f * y2;
@@ -192,7 +199,7 @@ __device__ __forceinline__ void warp_best(float& v, int& i, float& e) {
 template <typename G>
 __device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float (&mu2v)[4], const bool (&okv)[4],
                               int c, int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
-                              DevStatus* __restrict__ status, RcRec* __restrict__ rc) {
+                              DevStatus* __restrict__ status, const RcQueue& rc) {
     const int lane = threadIdx.x & 31;
     float sc[4], er[4];
     bool ok[4];
@@ -239,12 +246,25 @@ __device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float
         uint32_t m[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) m[q] = __ballot_sync(0xffffffffu, ok[q] && sc[q] - er[q] <= hi);
+        int slot = 0, at = 0;
         if (lane == 0) {
-            const int slot = atomicAdd(&status->rechecked, 1);
-            RcRec* r = rc + slot;
+            slot = atomicAdd(&status->rechecked, 1);
+            RcRec* r = rc.rec + slot;
             for (int w = 0; w < kTcMaxClusters / 32; ++w) r->mask[w] = w < 4 ? m[w] : 0u;
             r->col = (int32_t)col;
             r->done = 0;
+            if (slot < rc.cap) at = atomicAdd(&status->rc_pairs, __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]));
+        }
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (slot < rc.cap) {
+            // each lane its own candidates, in index order: lane + 32 q at its rank
+            const uint32_t below = (1u << lane) - 1u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if ((m[q] >> lane) & 1u) rc.pairs[at + __popc(m[q] & below)] = slot * c + lane + 32 * q;
+                at += __popc(m[q]);
+            }
         }
         return;
     }
@@ -268,7 +288,7 @@ __device__ __forceinline__ void finalize_column(int64_t col, float y2, const flo
                                                 const int32_t* __restrict__ counts, int c,
                                                 int32_t* __restrict__ labels, float* __restrict__ ub,
                                                 float* __restrict__ lb, DevStatus* __restrict__ status,
-                                                RcRec* __restrict__ rc) {
+                                                const RcQueue& rc) {
     finalize_scores(col, y2, [&](int i0, float* g) { gather8(gbase, nslots, Npad, m, i0, c, g); },
                     mu_normf, counts, c, labels, ub, lb, status, rc);
 }
@@ -307,7 +327,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                   const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
                   float* __restrict__ ub, float* __restrict__ lb, float* __restrict__ Gpart,
                   float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
-                  RcRec* __restrict__ rc_list) {
+                  RcQueue rc_list) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t mbar[kTcStages];
     __shared__ uint32_t tmem_base_sh;
@@ -564,7 +584,7 @@ __global__ void __launch_bounds__(kDnThreads, 1)
                    const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
                    float* __restrict__ ub, float* __restrict__ lb, float* __restrict__ Gpart,
                    float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
-                   RcRec* __restrict__ rc_list) {
+                   RcQueue rc_list) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t yfull[kDnMaxY], yempty[kDnMaxY];
     __shared__ uint64_t bfull[kDnMaxB], bempty[kDnMaxB], conv[kDnMaxB];
@@ -877,7 +897,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                      const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
                      float* __restrict__ ub, float* __restrict__ lb, float* __restrict__ Gpart,
                      float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
-                     RcRec* __restrict__ rc_list) {
+                     RcQueue rc_list) {
     extern __shared__ uint8_t smem_raw[];
     // conv: the split warps are done with a slab -- one per y_lo slot (a ring of 2), or, in
     // the two-term form (no y_lo ring to pace them), one per stage, so that a barrier can
@@ -1121,7 +1141,7 @@ __global__ void __launch_bounds__(kFinThreads)
     k_finalize_t(DenseTArgs a, int G, DevStatus* __restrict__ status, const float* __restrict__ mu_normf,
                  const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
                  float* __restrict__ ub, float* __restrict__ lb, const float* __restrict__ Gpart,
-                 const float* __restrict__ ynorm_part, RcRec* __restrict__ rc_list) {
+                 const float* __restrict__ ynorm_part, RcQueue rc_list) {
     constexpr int kGs = kFinCols + 1;       // row stride: the warps' lanes read down a column
     __shared__ float gs[128 * kGs];        // [centroid][column]
     __shared__ float ys[kFinCols], ylos[kFinCols];
@@ -1219,40 +1239,58 @@ struct DfSum {
     }
 };
 
+// 16-byte read-only global load that the compiler keeps in program order.
+__device__ __forceinline__ float4 ld_nc_v4(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // Returns the distance in thread 0 (0 in the other threads).
 template <typename TY>
 __device__ double block_dist2_exact(const TY* __restrict__ y, const float* __restrict__ mrow, int64_t d,
                                     bool vec, double* red) {
-    DfSum a0, a1;
+    DfSum a0, a1, a2, a3;
     if (vec && sizeof(TY) == 4) {
         const float4* y4 = reinterpret_cast<const float4*>(y);
         const float4* m4 = reinterpret_cast<const float4*>(mrow);
         const int64_t d4 = d / 4;
-        // eight 16-byte loads of each operand in flight per round: d = 10^4 is two rounds
-        for (int64_t b0 = threadIdx.x; b0 < d4; b0 += 8 * kThreads) {
-            float4 yv[8], mv[8];
+        // twelve 16-byte loads of each operand in flight per round: d up to 12288 is
+        // one memory round trip; four independent TwoSum chains
+        for (int64_t b0 = threadIdx.x; b0 < d4; b0 += 12 * kThreads) {
+            float4 yv[12], mv[12];
+            // volatile loads keep their order ahead of the arithmetic below, so all 24
+            // are in flight together; out-of-range slots load the last vector and are
+            // zeroed afterwards
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t j = b0 + u * kThreads;
-                yv[u] = j < d4 ? __ldg(y4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-                mv[u] = j < d4 ? __ldg(m4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int u = 0; u < 12; ++u) {
+                const int64_t j = min(b0 + u * kThreads, d4 - 1);
+                yv[u] = ld_nc_v4(y4 + j);
+                mv[u] = ld_nc_v4(m4 + j);
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 12; ++u)
+                if (b0 + u * kThreads >= d4) yv[u] = mv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 12; ++u) {
                 a0.add_sq_diff(yv[u].x, mv[u].x);
                 a1.add_sq_diff(yv[u].y, mv[u].y);
-                a0.add_sq_diff(yv[u].z, mv[u].z);
-                a1.add_sq_diff(yv[u].w, mv[u].w);
+                a2.add_sq_diff(yv[u].z, mv[u].z);
+                a3.add_sq_diff(yv[u].w, mv[u].w);
             }
         }
         for (int64_t r = d4 * 4 + threadIdx.x; r < d; r += kThreads) a0.add_sq_diff(XLoad<TY>::one(y + r), mrow[r]);
     } else {
         for (int64_t r = threadIdx.x; r < d; r += kThreads) a0.add_sq_diff(XLoad<TY>::one(y + r), mrow[r]);
     }
+    a0.merge(a1.h, a1.l);
+    a2.merge(a3.h, a3.l);
     // the threads' sums meet in double-float FP32 across the warp (FP64 per thread
     // would load this GPU's narrow FP64 pipe with a whole block's worth of work);
     // only the warps' totals are added in FP64, by thread 0
-    a0.merge(a1.h, a1.l);
+    a0.merge(a2.h, a2.l);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float oh = __shfl_xor_sync(0xffffffffu, a0.h, o);
@@ -1269,8 +1307,8 @@ __device__ double block_dist2_exact(const TY* __restrict__ y, const float* __res
 }
 
 // Exact re-decision of near ties, one launch.  The candidate distances of the
-// first rc_cap queued columns are spread over every SM, one CTA per
-// (column, candidate) pair; the CTA that computes a column's last candidate
+// first rc_cap queued columns are spread over every SM from the queue's pair
+// list, one CTA per (column, candidate) pair; the CTA that computes a column's last candidate
 // (a counter in the column's record) decides that column over its candidates
 // in increasing index (ties keep the lowest), so no single CTA decides them
 // all.  Columns queued beyond rc_cap are decided by one CTA each, candidate
@@ -1280,76 +1318,51 @@ __global__ void __launch_bounds__(kThreads)
     k_search_recheck(const TY* __restrict__ Y, int64_t ldy, int64_t d, bool vec,
                      DevStatus* __restrict__ status, const float* __restrict__ mu, int c,
                      int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
-                     RcRec* __restrict__ rc_list, double* __restrict__ rc_dist, int64_t rc_cap) {
+                     RcRec* __restrict__ rc_list, const int32_t* __restrict__ rc_pairs,
+                     double* __restrict__ rc_dist, int64_t rc_cap) {
     __shared__ double red[kThreads / 32];
-    __shared__ int64_t vlist[kThreads];
-    __shared__ int wcount[kThreads / 32];
     const int64_t nall = status->rechecked;
     if (nall == 0) return;
-    const int64_t nrc = min(nall, rc_cap);
-    const int64_t pairs = nrc * c;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t base = blockIdx.x; base < pairs; base += (int64_t)gridDim.x * kThreads) {
-        // the next kThreads pairs of this CTA (pr = base + t G) are tested at once and
-        // the candidates listed in order: a test per pair in turn would cost a
-        // memory round trip each
-        const int64_t pt = base + (int64_t)threadIdx.x * gridDim.x;
-        bool cand_t = false;
-        if (pt < pairs) {
-            const int64_t k = pt / c;
-            const int ci = (int)(pt - k * c);
-            cand_t = (__ldcg(&rc_list[k].mask[ci >> 5]) >> (ci & 31)) & 1u;
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, cand_t);
-        if (lane == 0) wcount[warp] = __popc(bal);
-        __syncthreads();
-        int off = 0, nv = 0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            off += w < warp ? wcount[w] : 0;
-            nv += wcount[w];
-        }
-        if (cand_t) vlist[off + __popc(bal & ((1u << lane) - 1u))] = pt;
-        __syncthreads();
-        for (int v = 0; v < nv; ++v) {
-            const int64_t pr = vlist[v];
-            const int64_t k = pr / c;
-            const int ci = (int)(pr - k * c);
-            RcRec* rec = rc_list + k;
-            const double dist = block_dist2_exact<TY>(Y + (int64_t)rec->col * ldy, mu + (int64_t)ci * d, d, vec, red);
-            if (threadIdx.x == 0) {
-                rc_dist[pr] = dist;
-                __threadfence();   // the distance is visible before this candidate counts as done
-                int cand = 0;
-                for (int w = 0; w < kTcMaxClusters / 32; ++w) cand += __popc(rec->mask[w]);
-                if (atomicAdd(&rec->done, 1) == cand - 1) {
-                    // this CTA computed the column's last candidate: it decides the column
-                    // (lowest distance, ties to the lowest index)
-                    __threadfence();
-                    const int64_t col = rec->col;
-                    double best = INFINITY;
-                    int besti = INT_MAX;
-                    for (int cj = 0; cj < c; ++cj) {
-                        if (!((rec->mask[cj >> 5] >> (cj & 31)) & 1u)) continue;
-                        const double dj = cj == ci ? dist : __ldcg(rc_dist + k * c + cj);
-                        if (dj < best) {
-                            best = dj;
-                            besti = cj;
-                        }
+    const int64_t npairs = status->rc_pairs;   // the candidates of the first rc_cap records
+    for (int64_t v = blockIdx.x; v < npairs; v += gridDim.x) {
+        const int64_t pr = __ldcg(rc_pairs + v);
+        const int64_t k = pr / c;
+        const int ci = (int)(pr - k * c);
+        RcRec* rec = rc_list + k;
+        const double dist = block_dist2_exact<TY>(Y + (int64_t)rec->col * ldy, mu + (int64_t)ci * d, d, vec, red);
+        if (threadIdx.x == 0) {
+            rc_dist[pr] = dist;
+            __threadfence();   // the distance is visible before this candidate counts as done
+            int cand = 0;
+            for (int w = 0; w < kTcMaxClusters / 32; ++w) cand += __popc(rec->mask[w]);
+            if (atomicAdd(&rec->done, 1) == cand - 1) {
+                // this CTA computed the column's last candidate: it decides the column
+                // (lowest distance, ties to the lowest index)
+                __threadfence();
+                const int64_t col = rec->col;
+                double best = INFINITY;
+                int besti = INT_MAX;
+                for (int cj = 0; cj < c; ++cj) {
+                    if (!((rec->mask[cj >> 5] >> (cj & 31)) & 1u)) continue;
+                    const double dj = cj == ci ? dist : __ldcg(rc_dist + k * c + cj);
+                    if (dj < best) {
+                        best = dj;
+                        besti = cj;
                     }
-                    if (besti < c) {
-                        if (labels[col] != besti) {
-                            labels[col] = besti;
-                            atomicAdd(&status->changed, 1);
-                        }
-                        if (ub) {
-                            ub[col] = (float)(sqrt(best) * (1.0 + 1e-6));
-                            lb[col] = 0.f;
-                        }
+                }
+                if (besti < c) {
+                    if (labels[col] != besti) {
+                        labels[col] = besti;
+                        atomicAdd(&status->changed, 1);
+                    }
+                    if (ub) {
+                        ub[col] = (float)(sqrt(best) * (1.0 + 1e-6));
+                        lb[col] = 0.f;
                     }
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
     // records beyond the distance buffer: one CTA per column, every candidate in turn
     for (int64_t k = rc_cap + blockIdx.x; k < nall; k += gridDim.x) {
@@ -1545,11 +1558,12 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              const float* mu_hi, const float* mu_lo, int64_t dpad,
                              const float* mu_normf, const int32_t* counts, int c, int32_t* labels,
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
-                             int32_t* tile_count, RcRec* rc_list, double* rc_dist, int64_t rc_cap,
+                             int32_t* tile_count, RcRec* rc_list, int32_t* rc_pairs, double* rc_dist, int64_t rc_cap,
                              bool vec, cudaStream_t st, cudaEvent_t ev_dense0, cudaEvent_t ev_dense1,
                              bool* dense_launched_out, const float* mu_a) {
     const int Npad = tc_npad(c);
     cudaError_t e = cudaSuccess;
+    const RcQueue rq{rc_list, rc_pairs, rc_cap};
     // dense TMA path: FP32 operand with 16-byte aligned columns
     const bool dense_ok = dtype == 0 && vec && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
                           ldy % 4 == 0 && (reinterpret_cast<uintptr_t>(mu_hi) % 16 == 0) &&
@@ -1587,12 +1601,12 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             count_launches(1);
             k_search_dense_t<<<dp.G, kTtThreads, dp.smem, st>>>(tmY, tmA, a, status, mu_normf, counts, c,
                                                                 labels, ub, lb, Gpart, ynorm_part,
-                                                                tile_count, rc_list);
+                                                                tile_count, rq);
             if (ev_dense1) cudaEventRecord(ev_dense1, st);
             count_launches(1);
             k_finalize_t<<<grid_for(n, kFinCols), kFinThreads, 0, st>>>(a, dp.G, status, mu_normf, counts, c,
                                                                         labels, ub, lb, Gpart, ynorm_part,
-                                                                        rc_list);
+                                                                        rq);
             dense_launched = true;
         }
     } else if (dense_ok) {
@@ -1623,7 +1637,7 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             count_launches(1);
             k_search_dense<<<dp.G, kDnThreads, dp.smem, st>>>(tmY, tmBh, tmBl, a, status, mu_normf,
                                                               counts, c, labels, ub, lb, Gpart,
-                                                              ynorm_part, tile_count, rc_list);
+                                                              ynorm_part, tile_count, rq);
             if (ev_dense1) cudaEventRecord(ev_dense1, st);
             dense_launched = true;
         }
@@ -1642,7 +1656,7 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                 kern<<<grid, kTcThreads, smem, st>>>((const TY*)Y, ldy, d, n, list, lmax, status, mu_hi,
                                                      mu_lo, dpad, Npad, kTcMaxSplit, mu_normf, counts,
                                                      c, labels, ub, lb, Gpart, ynorm_part, tile_count,
-                                                     rc_list);
+                                                     rq);
         });
         if (e != cudaSuccess) return e;
     }
@@ -1653,7 +1667,8 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
         const bool v4 = vec && sizeof(TY) == 4 && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
                         (reinterpret_cast<uintptr_t>(mu) % 16 == 0);
         k_search_recheck<TY><<<4 * num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu, c,
-                                                               labels, ub, lb, rc_list, rc_dist, rc_cap);
+                                                               labels, ub, lb, rc_list, rc_pairs, rc_dist,
+                                                               rc_cap);
     });
     return cudaGetLastError();
 }

@@ -781,6 +781,7 @@ __global__ void k_lloyd_init(DevStatus* __restrict__ status, int passes0) {
     status->flagged = 0;   // the per-pass counters start at zero (k_lloyd_pass_end re-zeroes them)
     status->changed = 0;
     status->rechecked = 0;
+    status->rc_pairs = 0;
     status->last_changed = 0;
 }
 
@@ -796,6 +797,7 @@ __global__ void k_lloyd_pass_end(DevStatus* __restrict__ status, cudaGraphCondit
     status->flagged = 0;
     status->changed = 0;
     status->rechecked = 0;
+    status->rc_pairs = 0;
 }
 
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }

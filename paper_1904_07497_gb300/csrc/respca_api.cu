@@ -67,7 +67,7 @@ struct respca_ctx {
         Dpart, own_part, norm_part, flag_list, seedD2, seed_part, centers, seed_u, fro_part, status,
         hX, hL, hS, hp, hp0,
         mu_next, mu_old, drift, ub, lb, dl_part, sums, moved, contrib, boff, labels_pass,
-        mu_hi, mu_lo, Gpart, ynorm_part, rc_list, tile_count, rc_dist,
+        mu_hi, mu_lo, Gpart, ynorm_part, rc_list, rc_plist, tile_count, rc_dist,
         L16, S16, T16, X16,   // BF16 state and X of the bf16 phase (precision = 1)
         mu_a,                 // centroid operand of the swapped dense search
         bn_part,              // per-chunk ||B_j||^2 of the l2,1 iteration
@@ -133,7 +133,7 @@ std::vector<DevBuf*> all_bufs(respca_ctx* h) {
                       &h->drift, &h->ub, &h->lb, &h->dl_part, &h->sums, &h->moved, &h->contrib, &h->boff,
                       &h->labels_pass,
                       &h->mu_hi, &h->mu_lo, &h->Gpart, &h->ynorm_part, &h->rc_list, &h->tile_count,
-                      &h->rc_dist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
+                      &h->rc_dist, &h->rc_plist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
                       &h->bn_part, &h->sumsD, &h->sp_M, &h->sp_sqn, &h->sp_part, &h->sp_gsum,
                       &h->sp_sig, &h->sp_deg, &h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z, &h->sp_H, &h->sp_Q,
                       &h->sp_ev, &h->sp_res, &h->sp_E, &h->sp_P, &h->sp_Ypad};
@@ -189,6 +189,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
         CK(ensure(h->ynorm_part, sizeof(float) * tp.ynorm));
         CK(ensure(h->tile_count, sizeof(int32_t) * tp.tiles));
         CK(ensure(h->rc_dist, sizeof(double) * (size_t)tp.rc_cap * c));
+        CK(ensure(h->rc_plist, sizeof(int32_t) * (size_t)tp.rc_cap * c));
         CK(ensure(h->mu_a, sizeof(float) * tp.mu_a));
         // per-tile arrival counters of the search kernels start every call at zero
         CK(cudaMemsetAsync(h->tile_count.p, 0, h->tile_count.bytes, h->stream));
@@ -214,7 +215,7 @@ respca_status read_status(respca_ctx* h) {
 // Zero the per-pass counters of the status block (not the running totals).
 cudaError_t zero_counters(respca_ctx* h) {
     DevStatus* s = P<DevStatus>(h->status);
-    return cudaMemsetAsync(&s->flagged, 0, 3 * sizeof(int32_t), h->stream);
+    return cudaMemsetAsync(&s->flagged, 0, 4 * sizeof(int32_t), h->stream);   // flagged .. rc_pairs
 }
 
 // Centroids (and their norms, drift from the centroids the last search used,
@@ -444,7 +445,7 @@ respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64
                             P<float>(h->mu_lo), dpad, P<float>(h->mu_normf), P<int32_t>(h->counts), c,
                             p, P<float>(h->ub), P<float>(h->lb), P<float>(h->Gpart),
                             P<float>(h->ynorm_part), P<int32_t>(h->tile_count), P<RcRec>(h->rc_list),
-                            P<double>(h->rc_dist), rc_cap, vec, h->stream, timing ? h->evd0 : nullptr,
+                            P<int32_t>(h->rc_plist), P<double>(h->rc_dist), rc_cap, vec, h->stream, timing ? h->evd0 : nullptr,
                             timing ? h->evd1 : nullptr, timing ? &h->dense_recorded : nullptr,
                             P<float>(h->mu_a)));
     } else {

@@ -56,6 +56,7 @@ struct DevStatus {
     int32_t flagged;        // columns queued for a nearest-centroid search
     int32_t changed;        // labels changed by the last assignment pass
     int32_t rechecked;      // near-tie columns re-decided in FP64
+    int32_t rc_pairs;       // (column, candidate) pairs queued for the re-decision
     int32_t nonfinite;      // X holds NaN/Inf
     int32_t ntiles;         // tiles of the current sort
     int32_t bad_labels;     // labels outside [0, c)
@@ -219,6 +220,14 @@ struct RcRec {
     int32_t done;     // candidate distances of this column computed so far (re-decision)
     int32_t pad[2];
 };
+// Near-tie queue: the records, and the (record, candidate) pairs of the first
+// cap records as record * c + candidate, appended in any order (the
+// re-decision spreads exactly these pairs over the CTAs).
+struct RcQueue {
+    RcRec* rec;
+    int32_t* pairs;
+    int64_t cap;
+};
 int tc_npad(int c);
 // Raises a kernel's dynamic shared memory cap to the device's opt-in limit,
 // once per (kernel, device).  The cap then no longer depends on the launch,
@@ -244,7 +253,7 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              const float* mu_hi, const float* mu_lo, int64_t dpad,
                              const float* mu_normf, const int32_t* counts, int c, int32_t* labels,
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
-                             int32_t* tile_count, RcRec* rc_list, double* rc_dist, int64_t rc_cap,
+                             int32_t* tile_count, RcRec* rc_list, int32_t* rc_pairs, double* rc_dist, int64_t rc_cap,
                              bool vec, cudaStream_t st, cudaEvent_t ev_dense0 = nullptr,
                              cudaEvent_t ev_dense1 = nullptr, bool* dense_launched = nullptr,
                              const float* mu_a = nullptr);
