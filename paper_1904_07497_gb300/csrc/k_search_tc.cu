@@ -1646,8 +1646,10 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
         const int64_t nslabs = (d + kTcK - 1) / kTcK;
         const int max_split = (int)std::min<int64_t>(kTcMaxSplit, nslabs);
         const size_t smem = (size_t)kTcStages * (2 * kTcM * 128 + 2 * (size_t)Npad * 128) + 1024;
-        const dim3 grid((unsigned)((n + kTcM - 1) / kTcM), (unsigned)max_split);
         const int64_t lmax = dense_launched ? list_max : n;
+        // tiles for at most lmax queued columns: beyond them the kernel would only
+        // start CTAs that return at once (in a pass the dense kernel takes, all do)
+        const dim3 grid((unsigned)((std::min(n, lmax) + kTcM - 1) / kTcM), (unsigned)max_split);
         count_launches(1);
         RESPCA_DISPATCH_X(dtype, TY, {
             auto kern = vec ? k_search_list<TY, true> : k_search_list<TY, false>;

@@ -297,24 +297,34 @@ __global__ void __launch_bounds__(kStatThreads)
 }
 
 // k_centroids_from_sums, the previous-centroid copy, k_mu_stats and the TF32
-// split in one CTA per centroid.  The stats use k_mu_stats' thread mapping and
-// summation order, so they are bit-identical to the separate kernels.
-__global__ void __launch_bounds__(kStatThreads)
+// split in one launch.  Centroid i's rows are split over gridDim.y CTAs of
+// kCsThreads (one CTA per centroid would leave most SMs idle at small c, each
+// doing two FP64 operations per element); each CTA reduces its rows' ||mu||^2
+// and drift terms (compensated FP32 per thread, FP32 tree across the CTA) to
+// part[i][s], and the CTA that finishes centroid i last (a counter, reset by
+// it) adds the parts in split order.
+constexpr int kCsThreads = 256;
+__global__ void __launch_bounds__(kCsThreads)
     k_centroids_stats(const double* __restrict__ sums, const int32_t* __restrict__ counts, int64_t d,
-                      float* __restrict__ mu, float* __restrict__ mu_old, double* __restrict__ mu_norm2,
-                      float* __restrict__ mu_normf, double* __restrict__ drift, MuSplitOut sp) {
-    __shared__ float red[kStatThreads / 32][2];
+                      int64_t per, float* __restrict__ mu, float* __restrict__ mu_old,
+                      double* __restrict__ mu_norm2, float* __restrict__ mu_normf, double* __restrict__ drift,
+                      MuSplitOut sp, float2* __restrict__ part, int32_t* __restrict__ done) {
+    __shared__ float red[kCsThreads / 32][2];
+    __shared__ int last_sh;
     const int i = blockIdx.x;
+    const int S = gridDim.y;
     const int cnt = counts[i];
+    const double inv = cnt != 0 ? 1.0 / (double)cnt : 0.0;
     float* m = mu + (int64_t)i * d;
     float* mo = mu_old + (int64_t)i * d;
+    const int64_t r0 = (int64_t)blockIdx.y * per, r1 = r0 + per < d ? r0 + per : d;
     float acc = 0.f, ca = 0.f, dr = 0.f, cd = 0.f;
-    for (int64_t r = threadIdx.x; r < d; r += kStatThreads) {
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += kCsThreads) {
         const float old = m[r];
         mo[r] = old;
         float v = old;
         if (cnt != 0) {
-            v = (float)(sums[(int64_t)i * d + r] * (1.0 / (double)cnt));
+            v = (float)(sums[(int64_t)i * d + r] * inv);
             m[r] = v;
         }
         {
@@ -350,16 +360,29 @@ __global__ void __launch_bounds__(kStatThreads)
         red[threadIdx.x >> 5][1] = dr;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        float a = red[threadIdx.x][0], b = red[threadIdx.x][1];
-        a = warp_sum(a);
-        b = warp_sum(b);
-        if (threadIdx.x == 0) {
-            mu_norm2[i] = (double)a;
-            mu_normf[i] = a;
-            drift[i] = sqrt((double)b) * (1.0 + 1e-5);
+    if (threadIdx.x == 0) {
+        float a = 0.f, bsum = 0.f;
+        for (int w = 0; w < kCsThreads / 32; ++w) {
+            a += red[w][0];
+            bsum += red[w][1];
         }
+        part[(int64_t)i * S + blockIdx.y] = make_float2(a, bsum);
+        __threadfence();
+        last_sh = atomicAdd(&done[i], 1) == S - 1;
     }
+    __syncthreads();
+    if (!last_sh || threadIdx.x != 0) return;
+    __threadfence();
+    float a = 0.f, bsum = 0.f;
+    for (int q = 0; q < S; ++q) {
+        const float2 v = __ldcg(part + (int64_t)i * S + q);
+        a += v.x;
+        bsum += v.y;
+    }
+    mu_norm2[i] = (double)a;
+    mu_normf[i] = a;
+    drift[i] = sqrt((double)bsum) * (1.0 + 1e-5);
+    done[i] = 0;
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -915,11 +938,21 @@ cudaError_t launch_sums_from_means(const float* mu, const int32_t* counts, int c
     return cudaGetLastError();
 }
 
+int centroids_stats_splits(int c, int64_t d) {
+    // about four CTAs per SM over the grid, at least 1024 rows per CTA
+    const int64_t want = (4 * 152 + c - 1) / c;
+    const int64_t most = (d + 1023) / 1024;
+    return (int)std::max<int64_t>(1, std::min(want, most));
+}
+
 cudaError_t launch_centroids_stats(const double* sums, const int32_t* counts, int c, int64_t d, float* mu,
                                    float* mu_old, double* mu_norm2, float* mu_normf, double* drift,
-                                   const MuSplitOut& sp, cudaStream_t st) {
+                                   const MuSplitOut& sp, float2* part, int32_t* done, cudaStream_t st) {
     count_launches(1);
-    k_centroids_stats<<<c, kStatThreads, 0, st>>>(sums, counts, d, mu, mu_old, mu_norm2, mu_normf, drift, sp);
+    const int S = centroids_stats_splits(c, d);
+    const int64_t per = (d + S - 1) / S;
+    k_centroids_stats<<<dim3(c, S), kCsThreads, 0, st>>>(sums, counts, d, per, mu, mu_old, mu_norm2, mu_normf,
+                                                          drift, sp, part, done);
     return cudaGetLastError();
 }
 

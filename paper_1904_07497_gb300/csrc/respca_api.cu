@@ -73,6 +73,7 @@ struct respca_ctx {
         bn_part,              // per-chunk ||B_j||^2 of the l2,1 iteration
         sumsD,                // FP64 sums of the next D under the iteration's starting labels
         sp_M, sp_sqn, sp_part, sp_gsum, sp_sig, sp_deg, sp_Y, sp_W, sp_T, sp_Z, sp_H, sp_Q, sp_ev,
+        cs_part, cs_done,     // per-split norms and counters of the centroid statistics
         sp_res, sp_E, sp_P, sp_Ypad;   // spectral p step: affinity, search blocks, Rayleigh-Ritz, embedding,
                               // M Y partials, a 16-byte-aligned copy of Y for the tensor maps
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
@@ -136,7 +137,7 @@ std::vector<DevBuf*> all_bufs(respca_ctx* h) {
                       &h->rc_dist, &h->rc_plist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
                       &h->bn_part, &h->sumsD, &h->sp_M, &h->sp_sqn, &h->sp_part, &h->sp_gsum,
                       &h->sp_sig, &h->sp_deg, &h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z, &h->sp_H, &h->sp_Q,
-                      &h->sp_ev, &h->sp_res, &h->sp_E, &h->sp_P, &h->sp_Ypad};
+                      &h->sp_ev, &h->sp_res, &h->sp_E, &h->sp_P, &h->sp_Ypad, &h->cs_part, &h->cs_done};
 }
 
 respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64_t lds,
@@ -164,6 +165,14 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
     CK(ensure(h->seed_u, sizeof(double) * c));
     CK(ensure(h->fro_part, sizeof(double) * kFroParts));
     CK(ensure(h->status, sizeof(DevStatus)));
+    {
+        // the statistics kernel's per-centroid counters start at zero and it leaves them so
+        const size_t need = sizeof(int32_t) * c;
+        const bool fresh = !h->cs_done.p || h->cs_done.bytes < need;
+        CK(ensure(h->cs_done, need));
+        if (fresh) CK(cudaMemsetAsync(h->cs_done.p, 0, need, h->stream));
+        CK(ensure(h->cs_part, sizeof(float2) * (size_t)c * centroids_stats_splits(c, d)));
+    }
     // centroid buffers start zeroed so entries of clusters that never had a
     // member hold finite values
     for (DevBuf* b : {&h->mu, &h->mu_next, &h->mu_old}) {
@@ -511,7 +520,7 @@ respca_status lloyd_pass_update(respca_ctx* h, int mode, int dtype, const void* 
     }
     CK(launch_centroids_stats(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
                               P<float>(h->mu_old), P<double>(h->mu_norm2), P<float>(h->mu_normf),
-                              P<double>(h->drift), sp, h->stream));
+                              P<double>(h->drift), sp, P<float2>(h->cs_part), P<int32_t>(h->cs_done), h->stream));
     return RESPCA_OK;
 }
 
@@ -657,7 +666,8 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
         MuSplitOut none;
         CK(launch_centroids_stats(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
                                   P<float>(h->mu_old), P<double>(h->mu_norm2), P<float>(h->mu_normf),
-                                  P<double>(h->drift), none, h->stream));
+                                  P<double>(h->drift), none, P<float2>(h->cs_part), P<int32_t>(h->cs_done),
+                                  h->stream));
     } else {
         CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts), P<int32_t>(h->tile_off),
                               P<TileDesc>(h->tiles), ds, h->stream));

@@ -130,11 +130,14 @@ cudaError_t launch_sums_from_means(const float* mu, const int32_t* counts, int c
                                    cudaStream_t st);
 
 // One Lloyd update in one launch: centroids from the FP64 sums (previous values
-// to mu_old), then exactly the statistics of launch_mu_stats, and the TF32
-// split when sp.hi is set.
+// to mu_old), their norms and drift (the statistics of launch_mu_stats, summed
+// in another fixed order), and the TF32 split when sp.hi is set.  part holds
+// c x centroids_stats_splits(c, d) float2, done c counters that start at zero
+// (the kernel leaves them at zero).
+int centroids_stats_splits(int c, int64_t d);
 cudaError_t launch_centroids_stats(const double* sums, const int32_t* counts, int c, int64_t d, float* mu,
                                    float* mu_old, double* mu_norm2, float* mu_normf, double* drift,
-                                   const MuSplitOut& sp, cudaStream_t st);
+                                   const MuSplitOut& sp, float2* part, int32_t* done, cudaStream_t st);
 
 cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_part, int nchunks,
                                int64_t n, int c, const int32_t* labels, const int32_t* counts,
