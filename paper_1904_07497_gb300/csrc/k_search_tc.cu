@@ -870,12 +870,14 @@ __global__ void __launch_bounds__(kDnThreads, 1)
 // the missing mu.y_lo is at most ||mu|| ||y - tf32(y)|| (Cauchy-Schwarz; the
 // split warps sum ||y - tf32(y)||^2 per column, at most 2^-10 ||y||) and widens
 // the score bound (score_err's ylo), so the near ties it can hide are
-// re-decided exactly.  Without
-// y_lo slabs the stacked form keeps four stages in flight.  Otherwise A1 =
-// raw centroids and A2 = lo parts, three MMAs (A1.Y_raw, A1.Y_lo, A2.Y_raw)
-// into D[i]; Y_lo is a B operand and lives in shared memory (a ring of 2 slabs).
+// re-decided exactly.  For 64 < Npad <= 128 the A operand is two 128-row slabs
+// per stage, A1 = raw centroids and A2 = their lo parts, and two MMAs per 8
+// rows (A1.Y_raw, A2.Y_raw) give D[i] = mu_hi.y_hi + mu_lo.y_hi with the same
+// bound.  No y_lo slab is formed, so the stages fill shared memory: four of
+// 48 KB (stacked) or three of 64 KB.
 //   warp 0: TMA producer (Y slab + A slab(s) per stage), warp 1: MMA issuer,
-//   warps 2-5: split (2 columns per thread) + epilogue (partials to Gpart).
+//   warps 2-5: ||y||^2 and ||y - tf32(y)||^2 sums (2 columns per thread) and
+//   the epilogue (partials to Gpart).
 // The scores, argmin and bounds follow in k_finalize_t, one thread per
 // column: done by the last CTA of a tile, the slot sums of 256 columns sat
 // on that CTA's critical path.
@@ -886,7 +888,6 @@ constexpr int kTtMaxS = 4;
 struct DenseTArgs {
     int64_t d, n, Q, T, W;   // rows, columns, slabs per tile, 256-column tiles, work units
     int Npad, stacked, S, cmax;
-    int two_term;            // products with y truncated to TF32 only (no y_lo slabs)
     int use_list;
     int64_t list_min;
 };
@@ -899,10 +900,9 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                      float* __restrict__ ynorm_part, int32_t* __restrict__ tile_count,
                      RcQueue rc_list) {
     extern __shared__ uint8_t smem_raw[];
-    // conv: the split warps are done with a slab -- one per y_lo slot (a ring of 2), or, in
-    // the two-term form (no y_lo ring to pace them), one per stage, so that a barrier can
-    // never complete twice before the MMA warp waits on it
-    __shared__ uint64_t full[kTtMaxS], empty[kTtMaxS], conv[kTtMaxS], loempty[2], acc_full[2], acc_empty[2];
+    // conv: the norm warps are done with a stage (one per stage, so that a barrier can never
+    // complete twice before the MMA warp waits on it)
+    __shared__ uint64_t full[kTtMaxS], empty[kTtMaxS], conv[kTtMaxS], acc_full[2], acc_empty[2];
     __shared__ float xch[64][17];   // lo rows handed to the hi rows in the epilogue (stacked)
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
@@ -921,7 +921,6 @@ __global__ void __launch_bounds__(kTtThreads, 1)
     const uint32_t stage_bytes = y_bytes + (uint32_t)na * a_bytes;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t lo_base = base + (uint32_t)S * stage_bytes;
     const int64_t w_tile0 = w0 / a.Q, w_blk0 = w0 % a.Q;
     constexpr uint32_t kTmemCols = 512;                // two 128 x 256 FP32 accumulators
 
@@ -930,13 +929,12 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         tc_fence_before();
     }
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) {   // S >= 2: covers conv[0..1] of the y_lo ring too
+        for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
             mbar_init(&conv[s], 4);
         }
         for (int s = 0; s < 2; ++s) {
-            mbar_init(&loempty[s], 1);
             mbar_init(&acc_full[s], 1);
             mbar_init(&acc_empty[s], 4);
         }
@@ -975,9 +973,9 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(128, kTtN);
-            const uint64_t dY0 = sw128_desc(base), dLo0 = sw128_desc(lo_base);
+            const uint64_t dY0 = sw128_desc(base);
             const uint32_t st16 = stage_bytes >> 4, y16 = y_bytes >> 4, a16 = a_bytes >> 4;
-            RingPos sr(S), lr(2), ar(2);
+            RingPos sr(S), ar(2);
             int64_t g = 0, blk = w_blk0;
             uint64_t* last_bar = nullptr;
             uint32_t last_par = 0;
@@ -990,29 +988,24 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                     break;
                 }
                 if (!mbar_wait_or_abort(&full[sr.idx], sr.phase, &abort_sh) ||
-                    !mbar_wait_or_abort(a.two_term ? &conv[sr.idx] : &conv[lr.idx],
-                                        a.two_term ? sr.phase : lr.phase, &abort_sh)) {
+                    !mbar_wait_or_abort(&conv[sr.idx], sr.phase, &abort_sh)) {
                     abort_sh = 1;
                     break;
                 }
                 tc_fence_after();
                 const uint64_t dY = dY0 + (uint64_t)(sr.idx * st16);
                 const uint64_t dA1 = dY + y16, dA2 = dA1 + a16;
-                const uint64_t dLo = dLo0 + (uint64_t)(lr.idx * y16);
                 const uint32_t acc = tmem + (uint32_t)(ar.idx * kTtN);
 #pragma unroll
                 for (int ks = 0; ks < kTcK / 8; ++ks) {
                     // 8 TF32 of K = 32 bytes = 2 descriptor address units
                     tc_mma(acc, dA1 + 2 * ks, dY + 2 * ks, idesc, (seg_start && ks == 0) ? 0u : 1u);
-                    if (!a.two_term) tc_mma(acc, dA1 + 2 * ks, dLo + 2 * ks, idesc, 1u);
                     if (na == 2) tc_mma(acc, dA2 + 2 * ks, dY + 2 * ks, idesc, 1u);
                 }
                 tc_commit(&empty[sr.idx]);
-                tc_commit(&loempty[lr.idx]);
-                last_bar = &loempty[lr.idx];
-                last_par = lr.phase;
+                last_bar = &empty[sr.idx];
+                last_par = sr.phase;
                 sr.next();
-                lr.next();
                 if (seg_end) {
                     tc_commit(&acc_full[ar.idx]);
                     ar.next();
@@ -1024,13 +1017,13 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             if (last_bar) mbar_wait(last_bar, last_par);
         }
     } else {
-        // ---------------- TF32 lo split + epilogue (warps 2-5)
+        // ---------------- column norms + epilogue (warps 2-5)
         const int m = 32 * (warp & 3) + lane;          // this thread's columns: m and m + 128
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        RingPos sr(S), lr(2), ar(2);
-        int64_t j = 0, tile = w_tile0, blk = w_blk0;
+        RingPos sr(S), ar(2);
+        int64_t tile = w_tile0, blk = w_blk0;
         float ysq[2] = {0.f, 0.f}, ycomp[2] = {0.f, 0.f}, ylo2[2] = {0.f, 0.f};
-        for (int64_t w = w0; w < w1; ++w, ++j) {
+        for (int64_t w = w0; w < w1; ++w) {
             const bool seg_start = (w == w0) || (blk == 0);
             const bool seg_end = (w == w1 - 1) || (blk == a.Q - 1);
             if (seg_start) ysq[0] = ysq[1] = ycomp[0] = ycomp[1] = ylo2[0] = ylo2[1] = 0.f;
@@ -1038,13 +1031,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                 abort_sh = 1;
                 break;
             }
-            // the lo slab is free once the MMAs of slab j - 2 are done
-            if (!a.two_term && j >= 2 && !mbar_wait_or_abort(&loempty[lr.idx], lr.phase ^ 1u, &abort_sh)) {
-                abort_sh = 1;
-                break;
-            }
             const uint32_t ysrc = base + (uint32_t)sr.idx * stage_bytes;
-            const uint32_t lodst = lo_base + (uint32_t)lr.idx * y_bytes;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int row = m + 128 * h;
@@ -1055,8 +1042,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                     const float4 x = ld_shared_v4(ysrc + off);
                     const float4 lo = make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y), x.z - tf32_hi(x.z),
                                                   x.w - tf32_hi(x.w));
-                    if (!a.two_term) st_shared_v4(lodst + off, lo);
-                    else ylo2[h] = fmaf(lo.x, lo.x, fmaf(lo.y, lo.y, fmaf(lo.z, lo.z, fmaf(lo.w, lo.w, ylo2[h]))));
+                    ylo2[h] = fmaf(lo.x, lo.x, fmaf(lo.y, lo.y, fmaf(lo.z, lo.z, fmaf(lo.w, lo.w, ylo2[h]))));
                     part = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, part))));
                 }
                 const float y = part - ycomp[h];   // Kahan accumulation of ||y_j||^2
@@ -1064,11 +1050,11 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                 ycomp[h] = (t - ysq[h]) - y;
                 ysq[h] = t;
             }
+            // this stage's reads are ordered before the TMA overwrite the MMA's commit releases
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(a.two_term ? &conv[sr.idx] : &conv[lr.idx]);
+            if (lane == 0) mbar_arrive(&conv[sr.idx]);
             sr.next();
-            lr.next();
             const int64_t cur_tile = tile;
             if (++blk == a.Q) {
                 blk = 0;
@@ -1111,11 +1097,9 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             float* yn = ynorm_part + ((int64_t)cur_tile * a.cmax + slot) * kTtN;
             yn[m] = ysq[0];
             yn[m + 128] = ysq[1];
-            if (a.two_term) {   // ||y - tf32(y)||^2 partials in the second half
-                float* yl = yn + a.T * a.cmax * kTtN;
-                yl[m] = ylo2[0];
-                yl[m + 128] = ylo2[1];
-            }
+            float* yl = yn + a.T * a.cmax * kTtN;   // ||y - tf32(y)||^2 partials in the second half
+            yl[m] = ylo2[0];
+            yl[m + 128] = ylo2[1];
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ar.idx]);
@@ -1177,16 +1161,12 @@ __global__ void __launch_bounds__(kFinThreads)
         float y2 = 0.f;
         for (int sl = 0; sl < ncontrib; ++sl) y2 += __ldcg(yt + (int64_t)sl * kTtN);
         ys[t] = y2;
-        float yl = 0.f;
-        if (a.two_term) {
-            // ||y - tf32(y)||: FP32 sums of at most d squares, so the norm is
-            // inflated by d 2^-24 to stay an upper bound
-            const float* ylt = yt + a.T * a.cmax * kTtN;
-            float l2 = 0.f;
-            for (int sl = 0; sl < ncontrib; ++sl) l2 += __ldcg(ylt + (int64_t)sl * kTtN);
-            yl = sqrtf(l2) * (1.f + (float)(a.d + 64) * 5.9604645e-8f);
-        }
-        ylos[t] = yl;
+        // ||y - tf32(y)||: FP32 sums of at most d squares, so the norm is
+        // inflated by d 2^-24 to stay an upper bound
+        const float* ylt = yt + a.T * a.cmax * kTtN;
+        float l2 = 0.f;
+        for (int sl = 0; sl < ncontrib; ++sl) l2 += __ldcg(ylt + (int64_t)sl * kTtN);
+        ylos[t] = sqrtf(l2) * (1.f + (float)(a.d + 64) * 5.9604645e-8f);
     }
     __syncthreads();
     // one warp per column (two columns per warp), lanes over the centroids
@@ -1479,8 +1459,9 @@ struct DenseTPlan {
 DenseTPlan dense_t_plan(int64_t n, int64_t d, int Npad) {
     DenseTPlan p;
     p.stacked = Npad <= 64 ? 1 : 0;
-    // the stacked form multiplies by y truncated to TF32 only: no y_lo ring, four stages
-    p.S = p.stacked ? 4 : 2;
+    // products with y truncated to TF32 only (no y_lo slabs): four stages of 48 KB
+    // (stacked) or three of 64 KB (two A slabs)
+    p.S = p.stacked ? 4 : 3;
     const size_t y_bytes = (size_t)kTtN * 128, a_bytes = 128 * 128;
     const size_t stage = y_bytes + (p.stacked ? 1 : 2) * a_bytes;
     p.Q = (d + kTcK - 1) / kTcK;
@@ -1492,7 +1473,7 @@ DenseTPlan dense_t_plan(int64_t n, int64_t d, int Npad) {
         const int64_t nc = sk_owner((t + 1) * p.Q - 1, p.W, p.G) - sk_owner(t * p.Q, p.W, p.G) + 1;
         if (nc > p.cmax) p.cmax = (int)nc;
     }
-    p.smem = (size_t)p.S * stage + (p.stacked ? 0 : 2 * y_bytes) + 1024;
+    p.smem = (size_t)p.S * stage + 1024;
     return p;
 }
 
@@ -1535,7 +1516,7 @@ TcPlan tc_plan(int64_t n, int64_t d, int c) {
         const DenseTPlan tp = dense_t_plan(n, d, t.Npad);
         t.gpart = std::max(t.gpart, (size_t)tp.T * tp.cmax * 128 * kTtN);
         // two halves when stacked: ||y||^2 and ||y - tf32(y)||^2 partials
-        t.ynorm = std::max(t.ynorm, (size_t)tp.T * tp.cmax * kTtN * (tp.stacked ? 2 : 1));
+        t.ynorm = std::max(t.ynorm, (size_t)tp.T * tp.cmax * kTtN * 2);   // ||y||^2 and ||y - tf32(y)||^2
     }
     t.mu_a = (size_t)256 * t.dpad;
     t.rc_cap = std::min<int64_t>(n, 2048);
@@ -1591,7 +1572,6 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             a.W = dp.W;
             a.Npad = Npad;
             a.stacked = dp.stacked;
-            a.two_term = dp.stacked;
             a.S = dp.S;
             a.cmax = dp.cmax;
             a.use_list = list ? 1 : 0;
