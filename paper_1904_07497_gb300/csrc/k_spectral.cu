@@ -174,6 +174,7 @@ __global__ void k_spec_axpby(float* __restrict__ out, const float* __restrict__ 
 // them in chunk order (deterministic).  BMAX >= b accumulators per row.
 constexpr int kSymWarps = 8;
 constexpr int kSymSmemFloats = 12288;   // the CTA's rows of Y (48 KB)
+constexpr int kSymBatch = 8;            // columns of A whose loads are issued together
 // CPL rows per lane: lane-strided (rows i0 + 32 u) when VEC = false, or
 // consecutive (one 16-byte load of rows 4 lane .. 4 lane + 3) when VEC = true
 // (n % 4 == 0), which doubles the bytes each load instruction moves.
@@ -194,11 +195,13 @@ __global__ void __launch_bounds__(kSymWarps * 32, 2)
     const int64_t wbase = ((int64_t)blockIdx.x * kSymWarps + warp) * 32 * CPL;
     // row of this lane's slot u
     auto row_of = [&](int u) -> int64_t { return VEC ? wbase + 4 * lane + u : wbase + lane + 32 * u; };
-    float acc[CPL][BMAX];
+    // accumulators in pairs: one packed two-lane FMA (__ffma2_rn, rounding as two
+    // fmaf) per pair halves the FMA instructions, which bound the issue rate here
+    float2 acc[CPL][BMAX / 2];
 #pragma unroll
     for (int u = 0; u < CPL; ++u)
 #pragma unroll
-        for (int q = 0; q < BMAX; ++q) acc[u][q] = 0.f;
+        for (int q = 0; q < BMAX / 2; ++q) acc[u][q] = make_float2(0.f, 0.f);
     const bool all_live = row_of(CPL - 1) < n;
     // acc[u][q] += m[u] * y[q] for one row kk of Y (broadcast from shared memory)
     auto fma_row = [&](const float* m, int64_t kk) {
@@ -206,26 +209,26 @@ __global__ void __launch_bounds__(kSymWarps * 32, 2)
 #pragma unroll
         for (int q4 = 0; q4 < BMAX / 4; ++q4) {
             const float4 y = yr[q4];
+            const float2 ya = make_float2(y.x, y.y), yb = make_float2(y.z, y.w);
 #pragma unroll
             for (int u = 0; u < CPL; ++u) {
-                acc[u][4 * q4 + 0] = fmaf(m[u], y.x, acc[u][4 * q4 + 0]);
-                acc[u][4 * q4 + 1] = fmaf(m[u], y.y, acc[u][4 * q4 + 1]);
-                acc[u][4 * q4 + 2] = fmaf(m[u], y.z, acc[u][4 * q4 + 2]);
-                acc[u][4 * q4 + 3] = fmaf(m[u], y.w, acc[u][4 * q4 + 3]);
+                const float2 mm = make_float2(m[u], m[u]);
+                acc[u][2 * q4] = __ffma2_rn(mm, ya, acc[u][2 * q4]);
+                acc[u][2 * q4 + 1] = __ffma2_rn(mm, yb, acc[u][2 * q4 + 1]);
             }
         }
     };
     int64_t kk = 0;
     if (VEC && all_live) {
-        // eight columns' loads issued together, then their products: the loads of
+        // kSymBatch columns' loads issued together, then their products: the loads of
         // one batch overlap each other (and other warps' products)
         const float* mc0 = M + k0 * n + row_of(0);
-        for (; kk + 8 <= kn; kk += 8) {
-            float4 mv[8];
+        for (; kk + kSymBatch <= kn; kk += kSymBatch) {
+            float4 mv[kSymBatch];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) mv[t] = __ldcs(reinterpret_cast<const float4*>(mc0 + (kk + t) * n));
+            for (int t = 0; t < kSymBatch; ++t) mv[t] = __ldcs(reinterpret_cast<const float4*>(mc0 + (kk + t) * n));
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
+            for (int t = 0; t < kSymBatch; ++t) {
                 const float m4[4] = {mv[t].x, mv[t].y, mv[t].z, mv[t].w};
                 fma_row(m4, kk + t);
             }
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(kSymWarps * 32, 2)
         if (i >= n) continue;
 #pragma unroll
         for (int q = 0; q < BMAX; ++q)
-            if (q < b) pc[(int64_t)q * n + i] = acc[u][q];
+            if (q < b) pc[(int64_t)q * n + i] = (q & 1) ? acc[u][q >> 1].y : acc[u][q >> 1].x;
     }
 }
 
