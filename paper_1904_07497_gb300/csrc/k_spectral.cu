@@ -410,6 +410,11 @@ __global__ void __launch_bounds__(NT)
         sched[e] = make_int2(p, q);
     }
     __syncthreads();
+    // each thread's 2 x 2 block and V entry, when one per thread covers them all
+    // (the divisions then leave the step loop)
+    const bool one_blk = half * half <= NT, one_v = bp * half <= NT;
+    const int bk2 = tid / half, bk1 = tid - bk2 * half;
+    const int vk = tid / bp, vi = tid - vk * bp;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         float o = 0.f, t2 = 0.f;
         for (int e = tid; e < bp * bp; e += NT) {
@@ -465,7 +470,7 @@ __global__ void __launch_bounds__(NT)
             __syncthreads();
             // A <- J^T A J by 2 x 2 blocks: rows of pair k1, columns of pair k2
             for (int e = tid; e < half * half; e += NT) {
-                const int k2 = e / half, k1 = e - k2 * half;
+                const int k2 = one_blk ? bk2 : e / half, k1 = one_blk ? bk1 : e - k2 * half;
                 const int p1 = pairs[k1].x, q1 = pairs[k1].y, p2 = pairs[k2].x, q2 = pairs[k2].y;
                 const float c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
                 const float xpp = a[p1 + p2 * bp], xpq = a[p1 + q2 * bp];
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(NT)
             }
             // V <- V J (pair k's two columns, row i)
             for (int e = tid; e < bp * half; e += NT) {
-                const int k = e / bp, i = e - k * bp;
+                const int k = one_v ? vk : e / bp, i = one_v ? vi : e - k * bp;
                 const int p = pairs[k].x, q = pairs[k].y;
                 const float c = cs[k], s = sn[k];
                 const float vp = v[i + p * bp], vq = v[i + q * bp];
