@@ -881,6 +881,38 @@ __global__ void __launch_bounds__(kDnThreads, 1)
 // The scores, argmin and bounds follow in k_finalize_t, one thread per
 // column: done by the last CTA of a tile, the slot sums of 256 columns sat
 // on that CTA's critical path.
+// A CTA's stream-K units [w0, w1), walked forward, or backward on alternate
+// passes: a pass then starts on the units the previous one read last, which the
+// L2 may still hold.  Tiles, 32-row blocks and the segment boundaries (the first
+// and last unit of a tile in walking order) advance without divisions.
+struct UnitWalk {
+    int64_t tile, blk, left, Q;
+    bool rev, first;
+    __device__ UnitWalk(int64_t w0, int64_t w1, int64_t Q_, bool rev_)
+        : left(w1 - w0), Q(Q_), rev(rev_), first(true) {
+        const int64_t w = rev ? w1 - 1 : w0;
+        tile = w / Q;
+        blk = w - tile * Q;
+    }
+    __device__ __forceinline__ bool seg_start() const { return first || blk == (rev ? Q - 1 : 0); }
+    __device__ __forceinline__ bool seg_end() const { return left == 1 || blk == (rev ? 0 : Q - 1); }
+    __device__ __forceinline__ void next() {
+        --left;
+        first = false;
+        if (rev) {
+            if (blk == 0) {
+                blk = Q - 1;
+                --tile;
+            } else {
+                --blk;
+            }
+        } else if (++blk == Q) {
+            blk = 0;
+            ++tile;
+        }
+    }
+};
+
 constexpr int kTtN = 256;          // data columns per tile (MMA N)
 constexpr int kTtThreads = 192;
 constexpr int kTtMaxS = 4;
@@ -921,7 +953,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
     const uint32_t stage_bytes = y_bytes + (uint32_t)na * a_bytes;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const int64_t w_tile0 = w0 / a.Q, w_blk0 = w0 % a.Q;
+    // walk backwards on every other all-column pass (the finalize counts them)
+    const bool rev = (status->dense_passes & 1) != 0;
     constexpr uint32_t kTmemCols = 512;                // two 128 x 256 FP32 accumulators
 
     if (warp == 1) {
@@ -949,23 +982,21 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         // ---------------- TMA producer
         if (lane == 0) {
             RingPos sr(S);
-            int64_t k = 0, tile = w_tile0, blk = w_blk0;
+            UnitWalk uw(w0, w1, a.Q, rev);
+            int64_t k = 0;
             for (int64_t w = w0; w < w1; ++w, ++k) {
                 if (k >= S && !mbar_wait_or_abort(&empty[sr.idx], sr.phase ^ 1u, &abort_sh)) {
                     abort_sh = 1;
                     break;
                 }
                 const uint32_t dst = base + (uint32_t)sr.idx * stage_bytes;
-                const int32_t row = (int32_t)(blk * kTcK);
+                const int32_t row = (int32_t)(uw.blk * kTcK);
                 mbar_expect_tx(&full[sr.idx], stage_bytes);
-                tma_load_2d(dst, &tmY, &full[sr.idx], row, (int32_t)(tile * kTtN));
+                tma_load_2d(dst, &tmY, &full[sr.idx], row, (int32_t)(uw.tile * kTtN));
                 tma_load_2d(dst + y_bytes, &tmA, &full[sr.idx], row, 0);
                 if (na == 2) tma_load_2d(dst + y_bytes + a_bytes, &tmA, &full[sr.idx], row, 128);
                 sr.next();
-                if (++blk == a.Q) {
-                    blk = 0;
-                    ++tile;
-                }
+                uw.next();
             }
             drain_ring(full, S, k);   // no copy may be in flight when the CTA leaves
         }
@@ -976,12 +1007,13 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             const uint64_t dY0 = sw128_desc(base);
             const uint32_t st16 = stage_bytes >> 4, y16 = y_bytes >> 4, a16 = a_bytes >> 4;
             RingPos sr(S), ar(2);
-            int64_t g = 0, blk = w_blk0;
+            UnitWalk uw(w0, w1, a.Q, rev);
+            int64_t g = 0;
             uint64_t* last_bar = nullptr;
             uint32_t last_par = 0;
             for (int64_t w = w0; w < w1; ++w) {
-                const bool seg_start = (w == w0) || (blk == 0);
-                const bool seg_end = (w == w1 - 1) || (blk == a.Q - 1);
+                const bool seg_start = uw.seg_start();
+                const bool seg_end = uw.seg_end();
                 if (seg_start && g >= 2 &&
                     !mbar_wait_or_abort(&acc_empty[ar.idx], ar.phase ^ 1u, &abort_sh)) {
                     abort_sh = 1;
@@ -1011,7 +1043,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                     ar.next();
                     ++g;
                 }
-                if (++blk == a.Q) blk = 0;
+                uw.next();
             }
             // drain: the last commit covers every MMA issued before it
             if (last_bar) mbar_wait(last_bar, last_par);
@@ -1021,11 +1053,11 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         const int m = 32 * (warp & 3) + lane;          // this thread's columns: m and m + 128
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         RingPos sr(S), ar(2);
-        int64_t tile = w_tile0, blk = w_blk0;
+        UnitWalk uw(w0, w1, a.Q, rev);
         float ysq[2] = {0.f, 0.f}, ycomp[2] = {0.f, 0.f}, ylo2[2] = {0.f, 0.f};
         for (int64_t w = w0; w < w1; ++w) {
-            const bool seg_start = (w == w0) || (blk == 0);
-            const bool seg_end = (w == w1 - 1) || (blk == a.Q - 1);
+            const bool seg_start = uw.seg_start();
+            const bool seg_end = uw.seg_end();
             if (seg_start) ysq[0] = ysq[1] = ycomp[0] = ycomp[1] = ylo2[0] = ylo2[1] = 0.f;
             if (!mbar_wait_or_abort(&full[sr.idx], sr.phase, &abort_sh)) {
                 abort_sh = 1;
@@ -1055,11 +1087,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&conv[sr.idx]);
             sr.next();
-            const int64_t cur_tile = tile;
-            if (++blk == a.Q) {
-                blk = 0;
-                ++tile;
-            }
+            const int64_t cur_tile = uw.tile;
+            uw.next();
             if (!seg_end) continue;
 
             // a tile segment is finished: drain its accumulator (lane = A row)
@@ -1130,6 +1159,7 @@ __global__ void __launch_bounds__(kFinThreads)
     __shared__ float gs[128 * kGs];        // [centroid][column]
     __shared__ float ys[kFinCols], ylos[kFinCols];
     if (a.use_list && (int64_t)status->flagged < a.list_min) return;   // the dense kernel did not run
+    if (blockIdx.x == 0 && threadIdx.x == 0) ++status->dense_passes;   // its walking direction alternates
     const int64_t col0 = (int64_t)blockIdx.x * kFinCols;
     const int64_t tile = col0 / kTtN;                 // kFinCols divides kTtN
     const int jc0 = (int)(col0 - tile * kTtN);

@@ -68,6 +68,7 @@ struct DevStatus {
     int32_t acc_passes;     //   passes run (including those before the loop)
     int32_t acc_rechecked;  //   near ties re-decided
     int32_t seed_done;      // CTAs of the current k-means++ step that finished (reset by the last)
+    int32_t dense_passes;   // all-column search passes so far (their parity sets the walking direction)
 };
 
 // Modes of the bound-based pruning kernel.
