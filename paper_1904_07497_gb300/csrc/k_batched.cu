@@ -194,6 +194,7 @@ struct BSmem {
     };
     double dscan[kBT + 1];
     double dred[kBW + 1];
+    double inv_n[kMaxC];                 // 1 / n_i of the item's problem (0: empty cluster)
     int32_t offs_s[kMaxC + 1];
     int32_t wlo[kBW], whi[kBW];          // first and last label of each warp's range (row items)
     int32_t pick;
@@ -401,17 +402,24 @@ __device__ void row_item(const BProb& pbr, double rho, int phase, int item, BSme
     ds2 += (double)ds2f;
     __syncthreads();
     if (sums) {
+        // 1 / n_i once per cluster and item (an FP64 division per element would
+        // load the narrow FP64 pipe with tens of operations each)
+        for (int i = threadIdx.x; i < c; i += kBT) {
+            const int cnt = ldi(offs + i + 1) - ldi(offs + i);
+            sm.inv_n[i] = cnt > 0 ? 1.0 / (double)cnt : 0.0;
+        }
+        __syncthreads();
         // mean of label i over rows: its slots (i + w) for the warps whose range held i
         for (int e = threadIdx.x; e < c * KR * 32; e += kBT) {
             const int i = e / (KR * 32), t = e - i * (KR * 32);
             const int64_t r = r0 + t;
-            const int cnt = ldi(offs + i + 1) - ldi(offs + i);
-            if (cnt == 0 || r >= d) continue;
+            const double inv = sm.inv_n[i];
+            if (inv == 0.0 || r >= d) continue;
             double sum = 0.0;
 #pragma unroll
             for (int w = 0; w < kBW; ++w)
                 if (sm.wlo[w] <= i && i <= sm.whi[w]) sum += (double)sm.slot[(i + w) * kChunk + t];
-            mu[(int64_t)i * d + r] = (float)(sum / (double)cnt);
+            mu[(int64_t)i * d + r] = (float)(sum * inv);
         }
     }
     __syncthreads();

@@ -151,36 +151,54 @@ __global__ void __launch_bounds__(kThreads)
     k_centroids(const float* __restrict__ Dpart, const int32_t* __restrict__ tile_off,
                 const int32_t* __restrict__ counts, int64_t d, float* __restrict__ mu,
                 double* __restrict__ sums_out) {
+    // 1 / n_i once per block: an FP64 division per thread would load this GPU's
+    // narrow FP64 pipe with tens of operations per element
+    __shared__ double inv_sh;
     const int i = blockIdx.y;
+    const int cnt = counts[i];
+    if (threadIdx.x == 0) inv_sh = cnt > 0 ? 1.0 / (double)cnt : 0.0;
+    __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (r >= d) return;
-    const int cnt = counts[i];
     const int t0 = tile_off[i], t1 = tile_off[i + 1];
-    // compensated FP32 sum of the tile partials (FP64 arithmetic is slow on this part)
+    // compensated FP32 sum of the tile partials (FP64 arithmetic is slow on this part),
+    // four tiles' loads issued together, added in tile order
     float s = 0.f, comp = 0.f;
-    for (int t = t0; t < t1; ++t) {
-        const float y = Dpart[(int64_t)t * d + r] - comp;
+    auto add = [&](float x) {
+        const float y = x - comp;
         const float u = s + y;
         comp = (u - s) - y;
         s = u;
+    };
+    int t = t0;
+    for (; t + 4 <= t1; t += 4) {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = Dpart[(int64_t)(t + q) * d + r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) add(v[q]);
     }
+    for (; t < t1; ++t) add(Dpart[(int64_t)t * d + r]);
     const double sd = (double)s - (double)comp;
     if (sums_out) sums_out[(int64_t)i * d + r] = sd;
-    if (cnt > 0) mu[(int64_t)i * d + r] = (float)(sd * (1.0 / (double)cnt));
+    if (cnt > 0) mu[(int64_t)i * d + r] = (float)(sd * inv_sh);
 }
 
 // Centroids from FP64 cluster sums (kept up to date incrementally).
 __global__ void __launch_bounds__(kThreads)
     k_centroids_from_sums(const double* __restrict__ sums, const int32_t* __restrict__ counts,
                           int64_t d, float* __restrict__ mu, float* __restrict__ mu_old) {
+    __shared__ double inv_sh;   // 1 / n_i once per block (see k_centroids)
     const int i = blockIdx.y;
+    const int cnt = counts[i];
+    if (threadIdx.x == 0) inv_sh = cnt > 0 ? 1.0 / (double)cnt : 0.0;
+    __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (r >= d) return;
     const int64_t e = (int64_t)i * d + r;
     if (mu_old) mu_old[e] = mu[e];   // the previous centroids, for the drift
-    const int cnt = counts[i];
     if (cnt == 0) return;
-    mu[e] = (float)(sums[e] * (1.0 / (double)cnt));
+    mu[e] = (float)(sums[e] * inv_sh);
 }
 
 // sums_i = n_i mu_i (FP64) for every row: the cluster sums that the centroids
@@ -311,10 +329,13 @@ __global__ void __launch_bounds__(kCsThreads)
                       MuSplitOut sp, float2* __restrict__ part, int32_t* __restrict__ done) {
     __shared__ float red[kCsThreads / 32][2];
     __shared__ int last_sh;
+    __shared__ double inv_sh;   // 1 / n_i once per block (see k_centroids)
     const int i = blockIdx.x;
     const int S = gridDim.y;
     const int cnt = counts[i];
-    const double inv = cnt != 0 ? 1.0 / (double)cnt : 0.0;
+    if (threadIdx.x == 0) inv_sh = cnt != 0 ? 1.0 / (double)cnt : 0.0;
+    __syncthreads();
+    const double inv = inv_sh;
     float* m = mu + (int64_t)i * d;
     float* mo = mu_old + (int64_t)i * d;
     const int64_t r0 = (int64_t)blockIdx.y * per, r1 = r0 + per < d ? r0 + per : d;
@@ -412,18 +433,20 @@ constexpr int kSepMaxC = 256;
 __global__ void __launch_bounds__(kThreads)
     k_pair_dist(const float* __restrict__ mu, const int32_t* __restrict__ counts, int c, int64_t d,
                 float* __restrict__ pair_ss) {
-    extern __shared__ __align__(16) float ms[];  // [c][kSepRows]
+    // [c][kSepRows + 1]: the padded stride puts the rows that a warp's threads
+    // read at once (different centroids j, same k) in different banks
+    extern __shared__ __align__(16) float ms[];
     const int64_t r0 = (int64_t)blockIdx.x * kSepRows;
     for (int idx = threadIdx.x; idx < c * kSepRows; idx += kThreads) {
         const int i = idx / kSepRows, rr = idx % kSepRows;
-        ms[idx] = (r0 + rr < d) ? mu[(int64_t)i * d + r0 + rr] : 0.f;
+        ms[i * (kSepRows + 1) + rr] = (r0 + rr < d) ? mu[(int64_t)i * d + r0 + rr] : 0.f;
     }
     __syncthreads();
     for (int p = threadIdx.x; p < c * c; p += kThreads) {
         const int i = p / c, j = p % c;
         if (j <= i || counts[i] == 0 || counts[j] == 0) continue;
-        const float* a = ms + i * kSepRows;
-        const float* b = ms + j * kSepRows;
+        const float* a = ms + i * (kSepRows + 1);
+        const float* b = ms + j * (kSepRows + 1);
         float s = 0.f;
 #pragma unroll 16
         for (int k = 0; k < kSepRows; ++k) {
@@ -458,15 +481,24 @@ __global__ void k_fill_double(double* __restrict__ p, int count, double v) {
 }
 
 // ---------------------------------------------------------------- finalisers
+// The three Sec. 5 norms from the fused pass's per-(chunk, tile) partials,
+// over kNormCtas CTAs (FP64 sums on one SM would be bound by its FP64 pipe):
+// CTA g adds units u = g kThreads + tid + k kNormCtas kThreads in that order,
+// its warps' and threads' sums in a fixed order, and the CTA that finishes
+// last adds the CTAs' parts in CTA order (a counter in the status block,
+// reset by that CTA).
+constexpr int kNormCtas = 64;
 __global__ void __launch_bounds__(kThreads)
     k_reduce_norms(const double* __restrict__ norm_part, int max_tiles, int nchunks,
-                   DevStatus* __restrict__ status) {
+                   DevStatus* __restrict__ status, double* __restrict__ part) {
     __shared__ double red[kThreads / 32][3];
+    __shared__ int last_sh;
     const int ntiles = status->ntiles;
     const int64_t units = (int64_t)ntiles * nchunks;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int64_t u = threadIdx.x; u < units; u += kThreads) {
-        const int64_t y = u / ntiles, t = u % ntiles;
+    const int64_t stride = (int64_t)kNormCtas * kThreads;
+    for (int64_t u = (int64_t)blockIdx.x * kThreads + threadIdx.x; u < units; u += stride) {
+        const int64_t y = u / ntiles, t = u - y * ntiles;
         const double* p = norm_part + (y * max_tiles + t) * 3;
         a0 += p[0];
         a1 += p[1];
@@ -481,11 +513,27 @@ __global__ void __launch_bounds__(kThreads)
         red[threadIdx.x >> 5][2] = a2;
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
-        double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
-        status->norm2[threadIdx.x] = t;
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            t0 += red[w][0];
+            t1 += red[w][1];
+            t2 += red[w][2];
+        }
+        part[blockIdx.x * 3 + 0] = t0;
+        part[blockIdx.x * 3 + 1] = t1;
+        part[blockIdx.x * 3 + 2] = t2;
+        __threadfence();
+        last_sh = atomicAdd(&status->norms_done, 1) == kNormCtas - 1;
     }
+    __syncthreads();
+    if (!last_sh || threadIdx.x >= 3) return;
+    __threadfence();
+    double t = 0.0;
+    for (int g = 0; g < kNormCtas; ++g) t += __ldcg(part + g * 3 + threadIdx.x);
+    status->norm2[threadIdx.x] = t;
+    __syncwarp(0x7u);
+    if (threadIdx.x == 0) status->norms_done = 0;
 }
 
 // Hamerly-style exact pruning of the nearest-centroid search.  Per column j
@@ -993,7 +1041,7 @@ cudaError_t launch_separation(const float* mu, const int32_t* counts, int c, int
     }
     cudaError_t e = cudaMemsetAsync(pair_ss, 0, sizeof(float) * (size_t)c * c, st);
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(float) * (size_t)c * kSepRows;
+    const size_t smem = sizeof(float) * (size_t)c * (kSepRows + 1);
     if (smem > 48 * 1024) {
         e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_pair_dist));
         if (e != cudaSuccess) return e;
@@ -1004,9 +1052,9 @@ cudaError_t launch_separation(const float* mu, const int32_t* counts, int c, int
 }
 
 cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchunks,
-                                DevStatus* status, cudaStream_t st) {
+                                DevStatus* status, double* part, cudaStream_t st) {
     count_launches(1);
-    k_reduce_norms<<<1, kThreads, 0, st>>>(norm_part, max_tiles, nchunks, status);
+    k_reduce_norms<<<kNormCtas, kThreads, 0, st>>>(norm_part, max_tiles, nchunks, status, part);
     return cudaGetLastError();
 }
 

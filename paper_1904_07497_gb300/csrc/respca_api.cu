@@ -74,6 +74,7 @@ struct respca_ctx {
         sumsD,                // FP64 sums of the next D under the iteration's starting labels
         sp_M, sp_sqn, sp_part, sp_gsum, sp_sig, sp_deg, sp_Y, sp_W, sp_T, sp_Z, sp_H, sp_Q, sp_ev,
         cs_part, cs_done,     // per-split norms and counters of the centroid statistics
+        norm_red,             // the norm reduction's per-CTA parts
         sp_res, sp_E, sp_P, sp_Ypad;   // spectral p step: affinity, search blocks, Rayleigh-Ritz, embedding,
                               // M Y partials, a 16-byte-aligned copy of Y for the tensor maps
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
@@ -137,7 +138,7 @@ std::vector<DevBuf*> all_bufs(respca_ctx* h) {
                       &h->rc_dist, &h->rc_plist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
                       &h->bn_part, &h->sumsD, &h->sp_M, &h->sp_sqn, &h->sp_part, &h->sp_gsum,
                       &h->sp_sig, &h->sp_deg, &h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z, &h->sp_H, &h->sp_Q,
-                      &h->sp_ev, &h->sp_res, &h->sp_E, &h->sp_P, &h->sp_Ypad, &h->cs_part, &h->cs_done};
+                      &h->sp_ev, &h->sp_res, &h->sp_E, &h->sp_P, &h->sp_Ypad, &h->cs_part, &h->cs_done, &h->norm_red};
 }
 
 respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64_t lds,
@@ -158,6 +159,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
     CK(ensure(h->own_part, sizeof(float) * (size_t)nch * n));
     CK(ensure(h->bn_part, sizeof(float) * (size_t)nch * n));
     CK(ensure(h->norm_part, sizeof(double) * 3 * (size_t)mt * nch));
+    CK(ensure(h->norm_red, sizeof(double) * 3 * 64));
     CK(ensure(h->flag_list, sizeof(int32_t) * n));
     CK(ensure(h->seedD2, sizeof(double) * n));
     CK(ensure(h->seed_part, sizeof(double) * ((n + 7) / 8 + 1)));
@@ -1018,7 +1020,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
                                 P<double>(h->norm_part), v.vec, h->stream));
         if (timing) CK(cudaEventRecord(h->evk1, h->stream));
         out.fused_launches += 1;
-        CK(launch_reduce_norms(P<double>(h->norm_part), mt, nch, ds, h->stream));
+        CK(launch_reduce_norms(P<double>(h->norm_part), mt, nch, ds, P<double>(h->norm_red), h->stream));
         double r2, dl2, ds2;
         if (spectral) {
             // p step by spectral clustering of the columns of L (Sec. 4.2), then the

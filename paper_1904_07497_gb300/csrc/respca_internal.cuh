@@ -69,6 +69,7 @@ struct DevStatus {
     int32_t acc_rechecked;  //   near ties re-decided
     int32_t seed_done;      // CTAs of the current k-means++ step that finished (reset by the last)
     int32_t dense_passes;   // all-column search passes so far (their parity sets the walking direction)
+    int32_t norms_done;     // CTAs of the norm reduction that finished (reset by the last)
 };
 
 // Modes of the bound-based pruning kernel.
@@ -162,8 +163,9 @@ cudaError_t launch_iteration(int dtype, int sdtype, const void* X, int64_t ldx, 
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
                              float* dl_part, double* norm_part, bool vec, cudaStream_t st);
 
+// part: 64 x 3 doubles of scratch
 cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchunks,
-                                DevStatus* status, cudaStream_t st);
+                                DevStatus* status, double* part, cudaStream_t st);
 
 cudaError_t launch_assign(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
                           const int32_t* list, const float* mu, const float* mu_normf,
