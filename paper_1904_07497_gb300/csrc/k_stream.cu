@@ -265,21 +265,27 @@ __global__ void __launch_bounds__(kDeltaThreads)
     }
 }
 
-// ||mu_i||^2 and, when mu_old is given, the drift ||mu_i - mu_old_i||, one
-// CTA per centroid: compensated FP32 sums per thread, FP32 tree across the CTA
-// (relative error ~1e-6, well inside the slack of the pruning bounds; the FP64
-// pipe of this part is too slow for a d-long FP64 reduction per centroid).
-constexpr int kStatThreads = 1024;
-__global__ void __launch_bounds__(kStatThreads)
-    k_mu_stats(const float* __restrict__ mu, const float* __restrict__ mu_old, int64_t d,
-               double* __restrict__ mu_norm2, float* __restrict__ mu_normf,
-               double* __restrict__ drift) {
-    __shared__ float red[kStatThreads / 32][2];
+constexpr int kCsThreads = 256;   // threads of the split centroid-statistics kernels
+
+// ||mu_i||^2 and, when mu_old is given, the drift ||mu_i - mu_old_i||: centroid
+// i's rows split over gridDim.y CTAs (one CTA per centroid would leave most SMs
+// idle at small c); compensated FP32 sums per thread, an FP32 tree across the
+// CTA (relative error ~1e-6, well inside the slack of the pruning bounds; the
+// FP64 pipe of this part is too slow for a d-long FP64 reduction per centroid),
+// and the CTA that finishes centroid i last adds the parts in split order.
+__global__ void __launch_bounds__(kCsThreads)
+    k_mu_stats(const float* __restrict__ mu, const float* __restrict__ mu_old, int64_t d, int64_t per,
+               double* __restrict__ mu_norm2, float* __restrict__ mu_normf, double* __restrict__ drift,
+               float2* __restrict__ part, int32_t* __restrict__ done) {
+    __shared__ float red[kCsThreads / 32][2];
+    __shared__ int last_sh;
     const int i = blockIdx.x;
+    const int S = gridDim.y;
     const float* m = mu + (int64_t)i * d;
     const float* mo = mu_old ? mu_old + (int64_t)i * d : nullptr;
+    const int64_t r0 = (int64_t)blockIdx.y * per, r1 = r0 + per < d ? r0 + per : d;
     float acc = 0.f, ca = 0.f, dr = 0.f, cd = 0.f;
-    for (int64_t r = threadIdx.x; r < d; r += kStatThreads) {
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += kCsThreads) {
         const float v = m[r];
         {
             const float y = v * v - ca;
@@ -302,16 +308,29 @@ __global__ void __launch_bounds__(kStatThreads)
         red[threadIdx.x >> 5][1] = dr;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        float a = red[threadIdx.x][0], b = red[threadIdx.x][1];
-        a = warp_sum(a);
-        b = warp_sum(b);
-        if (threadIdx.x == 0) {
-            mu_norm2[i] = (double)a;
-            mu_normf[i] = a;
-            if (drift) drift[i] = sqrt((double)b) * (1.0 + 1e-5);
+    if (threadIdx.x == 0) {
+        float a = 0.f, bsum = 0.f;
+        for (int w = 0; w < kCsThreads / 32; ++w) {
+            a += red[w][0];
+            bsum += red[w][1];
         }
+        part[(int64_t)i * S + blockIdx.y] = make_float2(a, bsum);
+        __threadfence();
+        last_sh = atomicAdd(&done[i], 1) == S - 1;
     }
+    __syncthreads();
+    if (!last_sh || threadIdx.x != 0) return;
+    __threadfence();
+    float a = 0.f, bsum = 0.f;
+    for (int q = 0; q < S; ++q) {
+        const float2 v = __ldcg(part + (int64_t)i * S + q);
+        a += v.x;
+        bsum += v.y;
+    }
+    mu_norm2[i] = (double)a;
+    mu_normf[i] = a;
+    if (drift) drift[i] = sqrt((double)bsum) * (1.0 + 1e-5);
+    done[i] = 0;
 }
 
 // k_centroids_from_sums, the previous-centroid copy, k_mu_stats and the TF32
@@ -321,7 +340,6 @@ __global__ void __launch_bounds__(kStatThreads)
 // and drift terms (compensated FP32 per thread, FP32 tree across the CTA) to
 // part[i][s], and the CTA that finishes centroid i last (a counter, reset by
 // it) adds the parts in split order.
-constexpr int kCsThreads = 256;
 __global__ void __launch_bounds__(kCsThreads)
     k_centroids_stats(const double* __restrict__ sums, const int32_t* __restrict__ counts, int64_t d,
                       int64_t per, float* __restrict__ mu, float* __restrict__ mu_old,
@@ -603,10 +621,34 @@ __global__ void __launch_bounds__(kThreads)
         const double other = (p == i1) ? d2 : d1;
         double u, l;
         if (mode == kBoundsIter) {
+            // the row chunks' partials in four compensated FP32 chains (an FP64 add per
+            // chunk would bound this pass by the FP64 pipe at large d), joined in FP64;
+            // their error, about 2^-23 relative, is far inside the 1e-5 slack below
+            float so[4] = {0.f, 0.f, 0.f, 0.f}, co[4] = {0.f, 0.f, 0.f, 0.f};
+            float sm[4] = {0.f, 0.f, 0.f, 0.f}, cm[4] = {0.f, 0.f, 0.f, 0.f};
+            auto kahan = [](float& sum, float& comp, float x) {
+                const float y = x - comp;
+                const float t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+            };
+            int ch = 0;
+            for (; ch + 4 <= nchunks; ch += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    kahan(so[q], co[q], own_part[(int64_t)(ch + q) * n + j]);
+                    kahan(sm[q], cm[q], dl_part[(int64_t)(ch + q) * n + j]);
+                }
+            }
+            for (; ch < nchunks; ++ch) {
+                kahan(so[0], co[0], own_part[(int64_t)ch * n + j]);
+                kahan(sm[0], cm[0], dl_part[(int64_t)ch * n + j]);
+            }
             double own = 0.0, mv = 0.0;
-            for (int ch = 0; ch < nchunks; ++ch) {
-                own += (double)own_part[(int64_t)ch * n + j];
-                mv += (double)dl_part[(int64_t)ch * n + j];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                own += (double)so[q] - (double)co[q];
+                mv += (double)sm[q] - (double)cm[q];
             }
             const double eo = sqrt(own);
             u = eo * (1.0 + kRelSlack) + 1e-30;
@@ -972,9 +1014,12 @@ cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, c
 }
 
 cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t d,
-                            double* mu_norm2, float* mu_normf, double* drift, cudaStream_t st) {
+                            double* mu_norm2, float* mu_normf, double* drift, float2* part, int32_t* done,
+                            cudaStream_t st) {
     count_launches(1);
-    k_mu_stats<<<c, kStatThreads, 0, st>>>(mu, mu_old, d, mu_norm2, mu_normf, drift);
+    const int S = centroids_stats_splits(c, d);
+    const int64_t per = (d + S - 1) / S;
+    k_mu_stats<<<dim3(c, S), kCsThreads, 0, st>>>(mu, mu_old, d, per, mu_norm2, mu_normf, drift, part, done);
     return cudaGetLastError();
 }
 

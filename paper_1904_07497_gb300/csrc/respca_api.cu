@@ -237,7 +237,7 @@ respca_status finish_centroids(respca_ctx* h, int c, int64_t d, float* dst, cons
     CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c, d,
                         dst, h->stream, sums_out));
     CK(launch_mu_stats(dst, prev, c, d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
-                       prev ? P<double>(h->drift) : nullptr, h->stream));
+                       prev ? P<double>(h->drift) : nullptr, P<float2>(h->cs_part), P<int32_t>(h->cs_done), h->stream));
     if (with_separation)
         CK(launch_separation(dst, P<int32_t>(h->counts), c, d, P<float>(h->pair_ss), P<double>(h->sep2),
                              h->stream));
@@ -680,7 +680,7 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
         CK(launch_centroids(P<float>(h->Dpart), P<int32_t>(h->tile_off), P<int32_t>(h->counts), c, d,
                             P<float>(h->mu), h->stream, P<double>(h->sums)));
         CK(launch_mu_stats(P<float>(h->mu), P<float>(h->mu_old), c, d, P<double>(h->mu_norm2),
-                           P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+                           P<float>(h->mu_normf), P<double>(h->drift), P<float2>(h->cs_part), P<int32_t>(h->cs_done), h->stream));
     }
     // the device loop pays off where a pass is long enough for the launches and
     // status reads it saves to matter; building the graph costs about as much
@@ -727,7 +727,7 @@ respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out
     CK(launch_gather_centers(pb.dtype, pb.X, pb.ldx, pb.d, P<int32_t>(h->centers), c, P<float>(h->mu),
                              P<int32_t>(h->counts), h->stream));
     CK(launch_mu_stats(P<float>(h->mu), nullptr, c, pb.d, P<double>(h->mu_norm2), P<float>(h->mu_normf),
-                       nullptr, h->stream));
+                       nullptr, P<float2>(h->cs_part), P<int32_t>(h->cs_done), h->stream));
     CK(cudaMemsetAsync(pb.p, 0xFF, sizeof(int32_t) * pb.n, h->stream));
     CK(cudaMemsetAsync(h->lb.p, 0, sizeof(float) * pb.n, h->stream));
     DevStatus* ds = P<DevStatus>(h->status);
@@ -1105,7 +1105,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
                 CK(launch_centroids_from_sums(P<double>(h->sumsD), P<int32_t>(h->counts), c, d,
                                               P<float>(h->mu_next), h->stream));
                 CK(launch_mu_stats(P<float>(h->mu_next), P<float>(h->mu), c, d, P<double>(h->mu_norm2),
-                                   P<float>(h->mu_normf), P<double>(h->drift), h->stream));
+                                   P<float>(h->mu_normf), P<double>(h->drift), P<float2>(h->cs_part), P<int32_t>(h->cs_done), h->stream));
                 CK(launch_separation(P<float>(h->mu_next), P<int32_t>(h->counts), c, d,
                                      P<float>(h->pair_ss), P<double>(h->sep2), h->stream));
             } else {

@@ -115,8 +115,10 @@ cudaError_t launch_delta_sums(int mode, int dtype, const void* X, int64_t ldx, c
                               double* sums, cudaStream_t st, const float* S = nullptr,
                               const float* Th = nullptr, float inv_rho = 0.f);
 
+// part / done: as for launch_centroids_stats (the two never run at once on a stream)
 cudaError_t launch_mu_stats(const float* mu, const float* mu_old, int c, int64_t d,
-                            double* mu_norm2, float* mu_normf, double* drift, cudaStream_t st);
+                            double* mu_norm2, float* mu_normf, double* drift, float2* part, int32_t* done,
+                            cudaStream_t st);
 
 // TF32 split of the centroids for the tensor-core search (layout of launch_mu_split).
 struct MuSplitOut {
