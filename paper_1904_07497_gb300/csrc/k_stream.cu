@@ -20,11 +20,13 @@ __global__ void __launch_bounds__(kThreads) k_fro2(const TX* __restrict__ X, int
     const int64_t rows_per_unit = kThreads * 4;
     const int64_t seg = (d + rows_per_unit - 1) / rows_per_unit;
     const int64_t units = seg * n;
-    double acc = 0.0;
+    // compensated FP32 per thread (an FP64 add per unit would bound this pass by the
+    // FP64 pipe), FP64 across threads
+    float acc = 0.f, comp = 0.f;
     bool bad = false;
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-        const int64_t j = u / seg;
-        const int64_t r = (u % seg) * rows_per_unit + threadIdx.x * 4;
+        const int64_t j = units < 0x7fffffff ? (int64_t)((uint32_t)u / (uint32_t)seg) : u / seg;
+        const int64_t r = (u - j * seg) * rows_per_unit + threadIdx.x * 4;
         const TX* col = X + j * ldx;
         float s = 0.f;
         if (VEC) {
@@ -42,10 +44,13 @@ __global__ void __launch_bounds__(kThreads) k_fro2(const TX* __restrict__ X, int
                     s = fmaf(v, v, s);
                 }
         }
-        acc += (double)s;
+        const float y = s - comp;
+        const float t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
     }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    double accd = warp_sum((double)acc - (double)comp);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&status->nonfinite, 1);
     if (threadIdx.x == 0) {
         double t = 0.0;
@@ -799,7 +804,7 @@ __global__ void __launch_bounds__(kThreads)
 // max |X - mu_p| over all elements and max_j ||X_j - mu_p(j)|| / sep(p(j)),
 // with sep^2 = sep2 * safety; both non-negative, combined with integer max on
 // their bit patterns (order-independent).  Also the FP64 sum of ||r_j||^2.
-template <typename TX>
+template <typename TX, bool VEC>
 __global__ void __launch_bounds__(kThreads)
     k_ramp_stats(const TX* __restrict__ X, int64_t ldx, int64_t d, int64_t n,
                  const int32_t* __restrict__ labels, const float* __restrict__ mu,
@@ -813,14 +818,29 @@ __global__ void __launch_bounds__(kThreads)
         const int p = labels[w];
         const TX* xc = X + w * ldx;
         const float* m = mu + (int64_t)p * d;
-        float mx = 0.f;
-        double s2 = 0.0;
-        for (int64_t r = lane; r < d; r += 32) {
-            const float e = XLoad<TX>::one(xc + r) - m[r];
+        float mx = 0.f, s2f = 0.f, c2 = 0.f;
+        // compensated FP32 per lane (an FP64 multiply-add per element would bound this
+        // pass by the FP64 pipe; the sums feed tests with 1e-3 margins), FP64 across lanes
+        auto add = [&](float e) {
             mx = fmaxf(mx, fabsf(e));
-            s2 += (double)e * (double)e;
+            const float y = fmaf(e, e, -c2);
+            const float t = s2f + y;
+            c2 = (t - s2f) - y;
+            s2f = t;
+        };
+        if (VEC) {   // four rows per lane and step (d % 4 == 0, 16-byte aligned rows)
+            for (int64_t r = 4 * lane; r < d; r += 128) {
+                const float4 x = XLoad<TX>::four(xc + r);
+                const float4 mm = __ldg(reinterpret_cast<const float4*>(m + r));
+                add(x.x - mm.x);
+                add(x.y - mm.y);
+                add(x.z - mm.z);
+                add(x.w - mm.w);
+            }
+        } else {
+            for (int64_t r = lane; r < d; r += 32) add(XLoad<TX>::one(xc + r) - m[r]);
         }
-        s2 = warp_sum(s2);
+        double s2 = warp_sum((double)s2f - (double)c2);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) {
@@ -835,19 +855,35 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // State after the skipped ramp: L = mu_p + alpha (X - mu_p), Theta = beta (X - mu_p).
-template <typename TX, typename TS>
+template <typename TX, typename TS, bool VEC>
 __global__ void __launch_bounds__(kThreads)
     k_ramp_state(const TX* __restrict__ X, int64_t ldx, int64_t d, int64_t n,
                  const int32_t* __restrict__ labels, const float* __restrict__ mu, float alpha,
                  float beta, TS* __restrict__ L, TS* __restrict__ Th, int64_t lds) {
-    const int64_t total = d * n;
-    for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * kThreads) {
-        const int64_t j = idx / d, r = idx % d;
-        const float m = mu[(int64_t)labels[j] * d + r];
-        const float e = XLoad<TX>::one(X + j * ldx + r) - m;
-        StateIO<TS>::store1(L + j * lds + r, fmaf(alpha, e, m));
-        StateIO<TS>::store1(Th + j * lds + r, beta * e);
+    // columns in turn per CTA, rows across its threads (four per thread and step when
+    // rows are 16-byte aligned): no division per element
+    for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+        const float* m = mu + (int64_t)labels[j] * d;
+        const TX* xc = X + j * ldx;
+        TS* lc = L + j * lds;
+        TS* tc = Th + j * lds;
+        if (VEC) {
+            for (int64_t r = 4 * (int64_t)threadIdx.x; r < d; r += 4 * kThreads) {
+                const float4 x = XLoad<TX>::four(xc + r);
+                const float4 mm = __ldg(reinterpret_cast<const float4*>(m + r));
+                const float4 e = make_float4(x.x - mm.x, x.y - mm.y, x.z - mm.z, x.w - mm.w);
+                StateIO<TS>::store4(lc + r, make_float4(fmaf(alpha, e.x, mm.x), fmaf(alpha, e.y, mm.y),
+                                                        fmaf(alpha, e.z, mm.z), fmaf(alpha, e.w, mm.w)));
+                StateIO<TS>::store4(tc + r, make_float4(beta * e.x, beta * e.y, beta * e.z, beta * e.w));
+            }
+        } else {
+            for (int64_t r = threadIdx.x; r < d; r += kThreads) {
+                const float mr = m[r];
+                const float e = XLoad<TX>::one(xc + r) - mr;
+                StateIO<TS>::store1(lc + r, fmaf(alpha, e, mr));
+                StateIO<TS>::store1(tc + r, beta * e);
+            }
+        }
     }
 }
 
@@ -1110,8 +1146,14 @@ cudaError_t launch_ramp_stats(int dtype, const void* X, int64_t ldx, int64_t d, 
     count_launches(1);
     const int grid = grid_for(n, kThreads / 32);
     RESPCA_DISPATCH_X(dtype, TX, {
-        k_ramp_stats<TX><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu, sep2, safety,
-                                                    max_abs_bits, max_ratio_bits, r2_part);
+        const bool vec = (ldx % 4 == 0) && (d % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(TX)) == 0) &&
+                         (reinterpret_cast<uintptr_t>(mu) % 16 == 0);
+        if (vec)
+            k_ramp_stats<TX, true><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu, sep2, safety,
+                                                              max_abs_bits, max_ratio_bits, r2_part);
+        else
+            k_ramp_stats<TX, false><<<grid, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu, sep2, safety,
+                                                               max_abs_bits, max_ratio_bits, r2_part);
     });
     return cudaGetLastError();
 }
@@ -1122,8 +1164,17 @@ cudaError_t launch_ramp_state(int dtype, const void* X, int64_t ldx, int64_t d, 
     count_launches(1);
     RESPCA_DISPATCH_X(dtype, TX, {
         RESPCA_DISPATCH_S(sdtype, TS, {
-            k_ramp_state<TX, TS><<<152 * 8, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu, alpha,
-                                                               beta, (TS*)L, (TS*)Th, lds);
+            const bool vec = (ldx % 4 == 0) && (lds % 4 == 0) && (d % 4 == 0) &&
+                             (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(TX)) == 0) &&
+                             (reinterpret_cast<uintptr_t>(L) % (4 * sizeof(TS)) == 0) &&
+                             (reinterpret_cast<uintptr_t>(Th) % (4 * sizeof(TS)) == 0) &&
+                             (reinterpret_cast<uintptr_t>(mu) % 16 == 0);
+            if (vec)
+                k_ramp_state<TX, TS, true><<<152 * 8, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu,
+                                                                        alpha, beta, (TS*)L, (TS*)Th, lds);
+            else
+                k_ramp_state<TX, TS, false><<<152 * 8, kThreads, 0, st>>>((const TX*)X, ldx, d, n, labels, mu,
+                                                                         alpha, beta, (TS*)L, (TS*)Th, lds);
         });
     });
     return cudaGetLastError();
