@@ -10,6 +10,12 @@
 // state; 14 with BF16 X and BF16 state (TS), where every stored value is the
 // FP32 result rounded to BF16 and the norms, own distances and next sums are
 // formed from the stored values (so the state is exactly what is stored).
+// With FP32 state the pass can also write a BF16 copy of L (2 more bytes per
+// element) and each column chunk's ||L_j - bf16(L_j)||^2: the nearest-centroid
+// search of this iteration then reads half the bytes and widens its decisions
+// by that norm.
+#include <type_traits>
+
 #include "respca_internal.cuh"
 
 namespace respca {
@@ -42,14 +48,16 @@ __device__ __forceinline__ void alm_element(float x, float s, float t, float l0,
     dnext = (x - sn) + tn * sc.inv_rho_next;          // D of the next iteration
 }
 
-template <typename TX, typename TS, bool VEC>
+// SH: also the BF16 copy Lsh (column stride ldsh) and ylo_part.
+template <typename TX, typename TS, bool VEC, bool SH>
 __global__ void __launch_bounds__(kThreads, 2)
     k_iteration(const TX* __restrict__ X, int64_t ldx, TS* __restrict__ L, TS* __restrict__ S,
                 TS* __restrict__ Th, int64_t lds, const float* __restrict__ mu,
                 const int32_t* __restrict__ perm, const TileDesc* __restrict__ tiles,
                 const DevStatus* __restrict__ status, int64_t d, int64_t n, IterScalars sc,
                 float* __restrict__ Dpart, float* __restrict__ own_part,
-                float* __restrict__ dl_part, double* __restrict__ norm_part) {
+                float* __restrict__ dl_part, double* __restrict__ norm_part,
+                __nv_bfloat16* __restrict__ Lsh, int64_t ldsh, float* __restrict__ ylo_part) {
     __shared__ float red[kThreads / 32][kChunkRows];
     __shared__ double nred[kThreads / 32][3];
     const int tile_idx = blockIdx.x;
@@ -82,7 +90,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         TS* lc = L + col * lds;
         TS* scol = S + col * lds;
         TS* tc = Th + col * lds;
-        float own = 0.f, dlc = 0.f;
+        float own = 0.f, dlc = 0.f, yl = 0.f;
         if (VEC) {
             float4 xv[4], sv[4], tv[4], lv[4];
 #pragma unroll
@@ -114,6 +122,18 @@ __global__ void __launch_bounds__(kThreads, 2)
                     StateIO<TS>::store4(lc + rr, lo);
                     StateIO<TS>::store4(scol + rr, so);
                     StateIO<TS>::store4(tc + rr, to);
+                    if constexpr (SH) {
+                        const __nv_bfloat162 b0 = __floats2bfloat162_rn(lo.x, lo.y);
+                        const __nv_bfloat162 b1 = __floats2bfloat162_rn(lo.z, lo.w);
+                        uint2 u;
+                        u.x = *reinterpret_cast<const uint32_t*>(&b0);
+                        u.y = *reinterpret_cast<const uint32_t*>(&b1);
+                        *reinterpret_cast<uint2*>(Lsh + col * ldsh + rr) = u;
+                        // l - bf16(l) is exact in FP32
+                        const float2 f0 = __bfloat1622float2(b0), f1 = __bfloat1622float2(b1);
+                        const float e0 = lo.x - f0.x, e1 = lo.y - f0.y, e2 = lo.z - f1.x, e3 = lo.w - f1.y;
+                        yl = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, yl))));
+                    }
                 }
             }
         } else {
@@ -138,9 +158,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         ndl += dlc;
         own = warp_sum(own);
         dlc = warp_sum(dlc);
+        if constexpr (SH) yl = warp_sum(yl);
         if (lane == 0) {
             own_part[(int64_t)blockIdx.y * n + col] = own;
             dl_part[(int64_t)blockIdx.y * n + col] = dlc;
+            if constexpr (SH) ylo_part[(int64_t)blockIdx.y * n + col] = yl;
         }
     }
 
@@ -179,19 +201,32 @@ cudaError_t launch_iteration(int dtype, int sdtype, const void* X, int64_t ldx, 
                              void* Th, int64_t lds, const float* mu, const int32_t* perm,
                              const TileDesc* tiles, int max_tiles, const DevStatus* status,
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
-                             float* dl_part, double* norm_part, bool vec, cudaStream_t st) {
+                             float* dl_part, double* norm_part, bool vec, cudaStream_t st, void* Lsh,
+                             int64_t ldsh, float* ylo_part) {
     count_launches(1);
     const dim3 grid(max_tiles, grid_for(d, kChunkRows));
+    auto* sh = static_cast<__nv_bfloat16*>(Lsh);
     RESPCA_DISPATCH_X(dtype, TX, {
         RESPCA_DISPATCH_S(sdtype, TS, {
-            if (vec)
-                k_iteration<TX, TS, true><<<grid, kThreads, 0, st>>>(
-                    (const TX*)X, ldx, (TS*)L, (TS*)S, (TS*)Th, lds, mu, perm, tiles, status, d, n, sc,
-                    Dpart, own_part, dl_part, norm_part);
-            else
-                k_iteration<TX, TS, false><<<grid, kThreads, 0, st>>>(
-                    (const TX*)X, ldx, (TS*)L, (TS*)S, (TS*)Th, lds, mu, perm, tiles, status, d, n, sc,
-                    Dpart, own_part, dl_part, norm_part);
+            bool done = false;
+            if constexpr (std::is_same<TS, float>::value) {
+                if (vec && sh) {
+                    k_iteration<TX, TS, true, true><<<grid, kThreads, 0, st>>>(
+                        (const TX*)X, ldx, (TS*)L, (TS*)S, (TS*)Th, lds, mu, perm, tiles, status, d, n, sc,
+                        Dpart, own_part, dl_part, norm_part, sh, ldsh, ylo_part);
+                    done = true;
+                }
+            }
+            if (!done) {
+                if (vec)
+                    k_iteration<TX, TS, true, false><<<grid, kThreads, 0, st>>>(
+                        (const TX*)X, ldx, (TS*)L, (TS*)S, (TS*)Th, lds, mu, perm, tiles, status, d, n, sc,
+                        Dpart, own_part, dl_part, norm_part, nullptr, 0, nullptr);
+                else
+                    k_iteration<TX, TS, false, false><<<grid, kThreads, 0, st>>>(
+                        (const TX*)X, ldx, (TS*)L, (TS*)S, (TS*)Th, lds, mu, perm, tiles, status, d, n, sc,
+                        Dpart, own_part, dl_part, norm_part, nullptr, 0, nullptr);
+            }
         });
     });
     return cudaGetLastError();

@@ -39,6 +39,7 @@
 #include <cfloat>
 #include <climits>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -195,9 +196,18 @@ __device__ __forceinline__ void warp_best(float& v, int& i, float& e) {
 }
 
 // mu2v[q], okv[q]: ||mu_i||^2 and "cluster i is not empty" for i = lane + 32 q,
-// loaded by the caller.
+// loaded by the caller.  y2 is ||y~||^2 of the operand y~ the products use;
+// yspl bounds ||y - y~|| when y2 is exact ||y||^2 (TF32 truncation) or the
+// centroid split term; ysh > 0 (a 16-bit copy y~ of FP32 data) bounds
+// ||y - y~||: the scores then widen by 2 ||mu_i|| ysh and the bounds are
+// distances to y~ moved by ysh (triangle inequality).
+__device__ __forceinline__ float pick4(const float (&v)[4], int q) {
+    return q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3];
+}
+
 template <typename G>
-__device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float (&mu2v)[4], const bool (&okv)[4],
+__device__ void finalize_warp(int64_t col, float y2, float yspl, float ysh, G g, const float (&mu2v)[4],
+                              const bool (&okv)[4],
                               int c, int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
                               DevStatus* __restrict__ status, const RcQueue& rc) {
     const int lane = threadIdx.x & 31;
@@ -212,7 +222,7 @@ __device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float
         if (ok[q]) {
             const float mu2 = mu2v[q];
             sc[q] = fmaf(-2.f, g(i), mu2);
-            er[q] = score_err(mu2, y2, ylo);
+            er[q] = score_err(mu2, y2, yspl + ysh);
         }
     }
     float bs = INFINITY, be = 0.f;
@@ -268,6 +278,13 @@ __device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float
         }
         return;
     }
+    float bb = be, sb = se;
+    if (ysh > 0.f) {   // uniform over the warp
+        const float mu2b = __shfl_sync(0xffffffffu, pick4(mu2v, bi >> 5), bi & 31);
+        const float mu2s = __shfl_sync(0xffffffffu, pick4(mu2v, si >> 5), si & 31);
+        bb = score_err(mu2b, y2, yspl);
+        sb = score_err(mu2s, y2, yspl);
+    }
     if (lane != 0) return;
     const float yerr = 1e-5f * y2;
     const int32_t old = labels[col];
@@ -276,8 +293,8 @@ __device__ void finalize_warp(int64_t col, float y2, float ylo, G g, const float
         atomicAdd(&status->changed, 1);
     }
     if (ub) {
-        ub[col] = sqrtf(fmaxf(bs + y2 + be + yerr, 0.f)) * (1.f + 1e-6f);
-        lb[col] = si < c ? sqrtf(fmaxf(ss + y2 - se - yerr, 0.f)) * (1.f - 1e-6f) : INFINITY;
+        ub[col] = (sqrtf(fmaxf(bs + y2 + bb + yerr, 0.f)) + ysh) * (1.f + 1e-6f);
+        lb[col] = si < c ? fmaxf(sqrtf(fmaxf(ss + y2 - sb - yerr, 0.f)) - ysh, 0.f) * (1.f - 1e-6f) : INFINITY;
     }
 }
 
@@ -917,13 +934,44 @@ constexpr int kTtN = 256;          // data columns per tile (MMA N)
 constexpr int kTtThreads = 192;
 constexpr int kTtMaxS = 4;
 
+// ymode: what bounds ||y - y~|| for the operand y~ the products use.
+//   0: FP32 operand truncated to TF32 by the MMA; the kernel sums ||y - tf32(y)||^2.
+//   1: 16-bit operand that is the data itself (y~ = y).
+//   2: 16-bit copy y~ of FP32 data y; ycol[j] bounds ||y_j - y~_j|| (formed where
+//      the copy is written) and the distances are bounded through y~.
+// With 16-bit operands the centroids are split into two 16-bit parts whose sum
+// is within 2^-16 ||mu|| + (subnormal terms) of mu; kSplit16 covers it.
 struct DenseTArgs {
     int64_t d, n, Q, T, W;   // rows, columns, slabs per tile, 256-column tiles, work units
     int Npad, stacked, S, cmax;
     int use_list;
     int64_t list_min;
+    int ymode;
+    const float* ycol;
 };
+constexpr float kSplit16 = 3.0517578e-5f;   // 2^-15: twice the BF16 two-part split bound
 
+// Adds the squares of the eight 16-bit values of a 16-byte chunk to acc.
+template <typename TY>
+__device__ __forceinline__ float sq8(const uint4 u, float acc) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float a, b;
+        if constexpr (std::is_same<TY, __nv_bfloat16>::value) {
+            a = __uint_as_float(w[k] << 16);
+            b = __uint_as_float(w[k] & 0xFFFF0000u);
+        } else {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+            a = f.x;
+            b = f.y;
+        }
+        acc = fmaf(a, a, fmaf(b, b, acc));
+    }
+    return acc;
+}
+
+template <typename TY>
 __global__ void __launch_bounds__(kTtThreads, 1)
     k_search_dense_t(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmA,
                      DenseTArgs a, DevStatus* __restrict__ status, const float* __restrict__ mu_normf,
@@ -946,9 +994,11 @@ __global__ void __launch_bounds__(kTtThreads, 1)
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
+    constexpr bool k16 = sizeof(TY) == 2;
+    constexpr int kRows = 128 / (int)sizeof(TY);      // d rows per slab: one 128-byte swizzle row
     const int S = a.S;
     const int na = a.stacked ? 1 : 2;                 // A slabs per stage
-    const uint32_t y_bytes = kTtN * 128;              // 256 columns x 32 rows of FP32
+    const uint32_t y_bytes = kTtN * 128;              // 256 columns x 128 bytes
     const uint32_t a_bytes = 128 * 128;               // 128 centroid rows x 32 rows
     const uint32_t stage_bytes = y_bytes + (uint32_t)na * a_bytes;
     const uint32_t raw = smem_u32(smem_raw);
@@ -990,7 +1040,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                     break;
                 }
                 const uint32_t dst = base + (uint32_t)sr.idx * stage_bytes;
-                const int32_t row = (int32_t)(uw.blk * kTcK);
+                const int32_t row = (int32_t)(uw.blk * kRows);
                 mbar_expect_tx(&full[sr.idx], stage_bytes);
                 tma_load_2d(dst, &tmY, &full[sr.idx], row, (int32_t)(uw.tile * kTtN));
                 tma_load_2d(dst + y_bytes, &tmA, &full[sr.idx], row, 0);
@@ -1003,7 +1053,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(128, kTtN);
+            const uint32_t idesc = k16 ? idesc_f16(128, kTtN, std::is_same<TY, __nv_bfloat16>::value)
+                                       : idesc_tf32(128, kTtN);
             const uint64_t dY0 = sw128_desc(base);
             const uint32_t st16 = stage_bytes >> 4, y16 = y_bytes >> 4, a16 = a_bytes >> 4;
             RingPos sr(S), ar(2);
@@ -1029,10 +1080,15 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                 const uint64_t dA1 = dY + y16, dA2 = dA1 + a16;
                 const uint32_t acc = tmem + (uint32_t)(ar.idx * kTtN);
 #pragma unroll
-                for (int ks = 0; ks < kTcK / 8; ++ks) {
-                    // 8 TF32 of K = 32 bytes = 2 descriptor address units
-                    tc_mma(acc, dA1 + 2 * ks, dY + 2 * ks, idesc, (seg_start && ks == 0) ? 0u : 1u);
-                    if (na == 2) tc_mma(acc, dA2 + 2 * ks, dY + 2 * ks, idesc, 1u);
+                for (int ks = 0; ks < 4; ++ks) {
+                    // 8 TF32 or 16 16-bit values of K = 32 bytes = 2 descriptor address units
+                    if constexpr (k16) {
+                        tc_mma_f16(acc, dA1 + 2 * ks, dY + 2 * ks, idesc, (seg_start && ks == 0) ? 0u : 1u);
+                        if (na == 2) tc_mma_f16(acc, dA2 + 2 * ks, dY + 2 * ks, idesc, 1u);
+                    } else {
+                        tc_mma(acc, dA1 + 2 * ks, dY + 2 * ks, idesc, (seg_start && ks == 0) ? 0u : 1u);
+                        if (na == 2) tc_mma(acc, dA2 + 2 * ks, dY + 2 * ks, idesc, 1u);
+                    }
                 }
                 tc_commit(&empty[sr.idx]);
                 last_bar = &empty[sr.idx];
@@ -1068,6 +1124,10 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             for (int h = 0; h < 2; ++h) {
                 const int row = m + 128 * h;
                 float part = 0.f;
+                if constexpr (k16) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) part = sq8<TY>(ld_shared_u4(ysrc + sw128_off(row, q)), part);
+                } else {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const uint32_t off = sw128_off(row, q);
@@ -1076,6 +1136,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                                                   x.w - tf32_hi(x.w));
                     ylo2[h] = fmaf(lo.x, lo.x, fmaf(lo.y, lo.y, fmaf(lo.z, lo.z, fmaf(lo.w, lo.w, ylo2[h]))));
                     part = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, part))));
+                }
                 }
                 const float y = part - ycomp[h];   // Kahan accumulation of ||y_j||^2
                 const float t = ysq[h] + y;
@@ -1126,9 +1187,11 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             float* yn = ynorm_part + ((int64_t)cur_tile * a.cmax + slot) * kTtN;
             yn[m] = ysq[0];
             yn[m + 128] = ysq[1];
-            float* yl = yn + a.T * a.cmax * kTtN;   // ||y - tf32(y)||^2 partials in the second half
-            yl[m] = ylo2[0];
-            yl[m + 128] = ylo2[1];
+            if (!k16) {
+                float* yl = yn + a.T * a.cmax * kTtN;   // ||y - tf32(y)||^2 partials in the second half
+                yl[m] = ylo2[0];
+                yl[m + 128] = ylo2[1];
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ar.idx]);
@@ -1157,7 +1220,7 @@ __global__ void __launch_bounds__(kFinThreads)
                  const float* __restrict__ ynorm_part, RcQueue rc_list) {
     constexpr int kGs = kFinCols + 1;       // row stride: the warps' lanes read down a column
     __shared__ float gs[128 * kGs];        // [centroid][column]
-    __shared__ float ys[kFinCols], ylos[kFinCols];
+    __shared__ float ys[kFinCols], ylos[kFinCols], yshs[kFinCols];
     if (a.use_list && (int64_t)status->flagged < a.list_min) return;   // the dense kernel did not run
     if (blockIdx.x == 0 && threadIdx.x == 0) ++status->dense_passes;   // its walking direction alternates
     const int64_t col0 = (int64_t)blockIdx.x * kFinCols;
@@ -1191,12 +1254,19 @@ __global__ void __launch_bounds__(kFinThreads)
         float y2 = 0.f;
         for (int sl = 0; sl < ncontrib; ++sl) y2 += __ldcg(yt + (int64_t)sl * kTtN);
         ys[t] = y2;
-        // ||y - tf32(y)||: FP32 sums of at most d squares, so the norm is
-        // inflated by d 2^-24 to stay an upper bound
-        const float* ylt = yt + a.T * a.cmax * kTtN;
-        float l2 = 0.f;
-        for (int sl = 0; sl < ncontrib; ++sl) l2 += __ldcg(ylt + (int64_t)sl * kTtN);
-        ylos[t] = sqrtf(l2) * (1.f + (float)(a.d + 64) * 5.9604645e-8f);
+        if (a.ymode == 0) {
+            // ||y - tf32(y)||: FP32 sums of at most d squares, so the norm is
+            // inflated by d 2^-24 to stay an upper bound
+            const float* ylt = yt + a.T * a.cmax * kTtN;
+            float l2 = 0.f;
+            for (int sl = 0; sl < ncontrib; ++sl) l2 += __ldcg(ylt + (int64_t)sl * kTtN);
+            ylos[t] = sqrtf(l2) * (1.f + (float)(a.d + 64) * 5.9604645e-8f);
+            yshs[t] = 0.f;
+        } else {
+            const int64_t col = col0 + t;
+            ylos[t] = kSplit16 * sqrtf(y2);
+            yshs[t] = (a.ymode == 2 && col < a.n) ? __ldg(a.ycol + col) : 0.f;
+        }
     }
     __syncthreads();
     // one warp per column (two columns per warp), lanes over the centroids
@@ -1207,7 +1277,7 @@ __global__ void __launch_bounds__(kFinThreads)
         const int jw = warp * kColsPerWarp + k2;
         const int64_t p = col0 + jw;
         if (p >= a.n) break;
-        finalize_warp(p, ys[jw], ylos[jw], [&](int i) { return gs[i * kGs + jw]; }, mu2v, okv, c, labels, ub, lb,
+        finalize_warp(p, ys[jw], ylos[jw], yshs[jw], [&](int i) { return gs[i * kGs + jw]; }, mu2v, okv, c, labels, ub, lb,
                       status, rc_list);
     }
 }
@@ -1407,25 +1477,38 @@ __global__ void __launch_bounds__(kThreads)
 // when mu_a is given, the A operand of the swapped dense kernel: for
 // stacked (Npad <= 64) rows i = raw mu_i and 64 + i = lo(mu_i) over 64 rows,
 // otherwise rows i = raw mu_i and 128 + i = lo(mu_i) over 128 rows (rows
-// beyond c zero).
+// beyond c zero).  mu_a16 (rows of dpad16): the same layout in two BF16 parts,
+// bf16(mu_i) and bf16(mu_i - bf16(mu_i)) (the difference is exact in FP32), so
+// that their sum is within 2^-16 |mu| of each element (plus 2^-134 below the
+// normal range).  One thread per (row, element) of the wider padding.
 __global__ void __launch_bounds__(kThreads)
     k_mu_split(const float* __restrict__ mu, int c, int64_t d, int Npad, int64_t dpad,
                float* __restrict__ mu_hi, float* __restrict__ mu_lo, float* __restrict__ mu_a,
-               int arows) {
+               int arows, __nv_bfloat16* __restrict__ mu_a16, int64_t dpad16) {
     const int rows = mu_a ? arows : Npad;
+    const int64_t dw = dpad16 > dpad ? dpad16 : dpad;
     const int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (idx >= (int64_t)rows * dpad) return;
-    const int i = (int)(idx / dpad);
-    const int64_t r = idx % dpad;
+    if (idx >= (int64_t)rows * dw) return;
+    const int i = (int)(idx / dw);
+    const int64_t r = idx % dw;
     const float v = (i < c && r < d) ? mu[(int64_t)i * d + r] : 0.f;
-    const float hi = tf32_hi(v);
-    if (i < Npad) {
-        mu_hi[idx] = hi;
-        mu_lo[idx] = v - hi;
+    if (r < dpad) {
+        const int64_t o = (int64_t)i * dpad + r;
+        const float hi = tf32_hi(v);
+        if (i < Npad) {
+            mu_hi[o] = hi;
+            mu_lo[o] = v - hi;
+        }
+        if (mu_a) {
+            mu_a[o] = v;
+            mu_a[(int64_t)arows * dpad + o] = v - hi;
+        }
     }
-    if (mu_a) {
-        mu_a[idx] = v;
-        mu_a[(int64_t)arows * dpad + idx] = v - hi;
+    if (mu_a16 && r < dpad16) {
+        const int64_t o = (int64_t)i * dpad16 + r;
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(v);
+        mu_a16[o] = h1;
+        mu_a16[(int64_t)arows * dpad16 + o] = __float2bfloat16_rn(v - __bfloat162float(h1));
     }
 }
 
@@ -1483,10 +1566,9 @@ struct DenseTPlan {
     size_t smem;
 };
 
-// Swapped dense kernel: 256-column tiles, 32-row slabs; stages of (Y slab,
-// A slab(s)): four when the centroids stack into one 128-row A (no y_lo
-// slabs), else two plus two y_lo slabs.
-DenseTPlan dense_t_plan(int64_t n, int64_t d, int Npad) {
+// Swapped dense kernel: 256-column tiles, slabs of one 128-byte row per column
+// (32 FP32 or 64 16-bit rows: slab_rows); stages of (Y slab, A slab(s)).
+DenseTPlan dense_t_plan(int64_t n, int64_t d, int Npad, int slab_rows = kTcK) {
     DenseTPlan p;
     p.stacked = Npad <= 64 ? 1 : 0;
     // products with y truncated to TF32 only (no y_lo slabs): four stages of 48 KB
@@ -1494,7 +1576,7 @@ DenseTPlan dense_t_plan(int64_t n, int64_t d, int Npad) {
     p.S = p.stacked ? 4 : 3;
     const size_t y_bytes = (size_t)kTtN * 128, a_bytes = 128 * 128;
     const size_t stage = y_bytes + (p.stacked ? 1 : 2) * a_bytes;
-    p.Q = (d + kTcK - 1) / kTcK;
+    p.Q = (d + slab_rows - 1) / slab_rows;
     p.T = (n + kTtN - 1) / kTtN;
     p.W = p.Q * p.T;
     p.G = (int)std::min<int64_t>(num_sms(), p.W);
@@ -1543,25 +1625,40 @@ TcPlan tc_plan(int64_t n, int64_t d, int c) {
     t.gpart = (size_t)slots * t.Npad * t.tiles * kTcM;
     t.ynorm = (size_t)slots * t.tiles * kTcM;
     if (t.Npad <= 128) {   // the swapped kernel's partials: [tile][slot][128 rows][256 columns]
-        const DenseTPlan tp = dense_t_plan(n, d, t.Npad);
-        t.gpart = std::max(t.gpart, (size_t)tp.T * tp.cmax * 128 * kTtN);
-        // two halves when stacked: ||y||^2 and ||y - tf32(y)||^2 partials
-        t.ynorm = std::max(t.ynorm, (size_t)tp.T * tp.cmax * kTtN * 2);   // ||y||^2 and ||y - tf32(y)||^2
+        for (int rows : {kTcK, 2 * kTcK}) {   // FP32 and 16-bit operands
+            const DenseTPlan tp = dense_t_plan(n, d, t.Npad, rows);
+            t.gpart = std::max(t.gpart, (size_t)tp.T * tp.cmax * 128 * kTtN);
+            // two halves: ||y||^2 and ||y - tf32(y)||^2 partials
+            t.ynorm = std::max(t.ynorm, (size_t)tp.T * tp.cmax * kTtN * 2);
+        }
     }
     t.mu_a = (size_t)256 * t.dpad;
+    t.dpad16 = (d + 63) / 64 * 64;
+    t.mu_a16 = (size_t)256 * t.dpad16;
     t.rc_cap = std::min<int64_t>(n, 2048);
     return t;
 }
 
 cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
-                            float* mu_lo, cudaStream_t st, float* mu_a) {
+                            float* mu_lo, cudaStream_t st, float* mu_a, __nv_bfloat16* mu_a16,
+                            int64_t dpad16) {
     count_launches(1);
     const int arows = Npad <= 64 ? 64 : 128;
     const bool with_a = mu_a != nullptr && Npad <= 128;
     const int rows = with_a ? arows : Npad;
-    k_mu_split<<<grid_for((int64_t)rows * dpad, kThreads), kThreads, 0, st>>>(
-        mu, c, d, Npad, dpad, mu_hi, mu_lo, with_a ? mu_a : nullptr, arows);
+    if (!with_a) mu_a16 = nullptr;
+    const int64_t dw = (mu_a16 && dpad16 > dpad) ? dpad16 : dpad;
+    k_mu_split<<<grid_for((int64_t)rows * dw, kThreads), kThreads, 0, st>>>(
+        mu, c, d, Npad, dpad, mu_hi, mu_lo, with_a ? mu_a : nullptr, arows, mu_a16, mu_a16 ? dpad16 : 0);
     return cudaGetLastError();
+}
+
+int64_t search_list_max(int64_t n, int c, bool op16) {
+    // for c <= 128 (256 columns per MMA) the all-column pass plus its finalize
+    // (~97 us at d = n = 10^4 with FP32 operands, ~55 us with 16-bit ones) beats
+    // the gathered list kernel (~0.8 TB/s) from about n / 6 (n / 10) queued columns on
+    if (tc_npad(c) > 128) return n / 4;
+    return op16 ? n / 10 : n / 6;
 }
 
 cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
@@ -1571,7 +1668,7 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              float* ub, float* lb, float* Gpart, float* ynorm_part,
                              int32_t* tile_count, RcRec* rc_list, int32_t* rc_pairs, double* rc_dist, int64_t rc_cap,
                              bool vec, cudaStream_t st, cudaEvent_t ev_dense0, cudaEvent_t ev_dense1,
-                             bool* dense_launched_out, const float* mu_a) {
+                             bool* dense_launched_out, const float* mu_a, const Search16* s16) {
     const int Npad = tc_npad(c);
     cudaError_t e = cudaSuccess;
     const RcQueue rq{rc_list, rc_pairs, rc_cap};
@@ -1579,21 +1676,29 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
     const bool dense_ok = dtype == 0 && vec && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
                           ldy % 4 == 0 && (reinterpret_cast<uintptr_t>(mu_hi) % 16 == 0) &&
                           (reinterpret_cast<uintptr_t>(mu_lo) % 16 == 0);
-    // larger queued lists use the dense kernel: for c <= 128 (256 columns per MMA)
-    // the all-column pass plus its finalize (~97 us at d = n = 10^4) beats the
-    // gathered list kernel from about n / 6 queued columns on
-    const int64_t list_max = (Npad <= 128) ? n / 6 : n / 4;
+    // 16-bit all-column path: BF16 columns (the data or a copy of it) and the
+    // centroids' BF16 split, 16-byte aligned columns
+    const bool dense16 = s16 && s16->y16 && s16->a16 && Npad <= 128 &&
+                         (reinterpret_cast<uintptr_t>(s16->y16) % 16 == 0) && s16->ld16 % 8 == 0 &&
+                         (reinterpret_cast<uintptr_t>(s16->a16) % 16 == 0) && s16->dpad16 % 64 == 0;
+    // larger queued lists use the dense kernel
+    const int64_t list_max = search_list_max(n, c, dense16);
     bool dense_launched = false;
     // The start event goes into the stream before the host-side preparation of
     // the launch (tensor-map encoding, attributes), so that it is reached while
     // the preceding kernel still runs and brackets this kernel, not the host.
-    const bool dense_t_path = dense_ok && Npad <= 128 && mu_a && (reinterpret_cast<uintptr_t>(mu_a) % 16 == 0);
-    if (ev_dense0 && dense_ok) cudaEventRecord(ev_dense0, st);
+    const bool dense_t_path =
+        dense16 || (dense_ok && Npad <= 128 && mu_a && (reinterpret_cast<uintptr_t>(mu_a) % 16 == 0));
+    if (ev_dense0 && (dense_ok || dense16)) cudaEventRecord(ev_dense0, st);
     if (dense_t_path) {
         CUtensorMap tmY, tmA;
-        const DenseTPlan dp = dense_t_plan(n, d, Npad);
-        if (encode_2d(&tmY, static_cast<const float*>(Y), d, n, ldy, kTcK, kTtN) &&
-            encode_2d(&tmA, mu_a, dpad, 256, dpad, kTcK, 128)) {
+        const DenseTPlan dp = dense_t_plan(n, d, Npad, dense16 ? 2 * kTcK : kTcK);
+        const bool enc_ok =
+            dense16 ? (encode_2d_16(&tmY, s16->y16, true, d, n, s16->ld16, 2 * kTcK, kTtN) &&
+                       encode_2d_16(&tmA, s16->a16, true, s16->dpad16, 256, s16->dpad16, 2 * kTcK, 128))
+                    : (encode_2d(&tmY, static_cast<const float*>(Y), d, n, ldy, kTcK, kTtN) &&
+                       encode_2d(&tmA, mu_a, dpad, 256, dpad, kTcK, 128));
+        if (enc_ok) {
             DenseTArgs a;
             a.d = d;
             a.n = n;
@@ -1606,12 +1711,14 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             a.cmax = dp.cmax;
             a.use_list = list ? 1 : 0;
             a.list_min = list_max + 1;
-            e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_search_dense_t));
+            a.ymode = dense16 ? (s16->ycol ? 2 : 1) : 0;
+            a.ycol = dense16 ? s16->ycol : nullptr;
+            auto kern = dense16 ? k_search_dense_t<__nv_bfloat16> : k_search_dense_t<float>;
+            e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
             if (e != cudaSuccess) return e;
             count_launches(1);
-            k_search_dense_t<<<dp.G, kTtThreads, dp.smem, st>>>(tmY, tmA, a, status, mu_normf, counts, c,
-                                                                labels, ub, lb, Gpart, ynorm_part,
-                                                                tile_count, rq);
+            kern<<<dp.G, kTtThreads, dp.smem, st>>>(tmY, tmA, a, status, mu_normf, counts, c, labels, ub, lb,
+                                                    Gpart, ynorm_part, tile_count, rq);
             if (ev_dense1) cudaEventRecord(ev_dense1, st);
             count_launches(1);
             k_finalize_t<<<grid_for(n, kFinCols), kFinThreads, 0, st>>>(a, dp.G, status, mu_normf, counts, c,

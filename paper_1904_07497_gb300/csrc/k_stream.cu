@@ -395,6 +395,12 @@ __global__ void __launch_bounds__(kCsThreads)
                 sp.a[idx] = v;
                 sp.a[(int64_t)sp.arows * sp.dpad + idx] = v - hi;
             }
+            if (sp.a16) {   // the BF16 split of k_mu_split
+                const int64_t o = (int64_t)i * sp.dpad16 + r;
+                const __nv_bfloat16 h1 = __float2bfloat16_rn(v);
+                sp.a16[o] = h1;
+                sp.a16[(int64_t)sp.arows * sp.dpad16 + o] = __float2bfloat16_rn(v - __bfloat162float(h1));
+            }
         }
     }
     acc = warp_sum(acc);
@@ -577,7 +583,8 @@ __global__ void __launch_bounds__(kThreads)
                   const int32_t* __restrict__ counts, const double* __restrict__ sep2,
                   double safety, const double* __restrict__ drift, float* __restrict__ ub,
                   float* __restrict__ lb, int32_t* __restrict__ flag_list,
-                  DevStatus* __restrict__ status, int32_t* __restrict__ labels_copy) {
+                  DevStatus* __restrict__ status, int32_t* __restrict__ labels_copy,
+                  const float* __restrict__ ylo_part, float* __restrict__ ycol, float ycol_floor) {
     // largest and second largest drift over active clusters (per block)
     __shared__ double s_d1[kThreads], s_d2[kThreads];
     __shared__ int s_i1[kThreads];
@@ -660,6 +667,22 @@ __global__ void __launch_bounds__(kThreads)
             l = (double)lb[j] - sqrt(mv) * (1.0 + kRelSlack) - other * (1.0 + kRelSlack);
             const double sp = sep2[p];
             if (sp > 0.0) l = fmax(l, sqrt(sp * safety) - u);
+            if (ycol) {
+                // ||L_j - bf16(L_j)|| from the fused pass's chunk partials (the search of
+                // this iteration's L runs on its 16-bit copy), same summation; the floor
+                // covers squares that underflowed
+                float sy[4] = {0.f, 0.f, 0.f, 0.f}, cy[4] = {0.f, 0.f, 0.f, 0.f};
+                int k = 0;
+                for (; k + 4 <= nchunks; k += 4) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) kahan(sy[q], cy[q], ylo_part[(int64_t)(k + q) * n + j]);
+                }
+                for (; k < nchunks; ++k) kahan(sy[0], cy[0], ylo_part[(int64_t)k * n + j]);
+                double yl = 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) yl += (double)sy[q] - (double)cy[q];
+                ycol[j] = (float)(sqrt(yl) * (1.0 + kRelSlack)) + ycol_floor;
+            }
         } else {
             const double own_drift = drift ? drift[p] : 0.0;
             u = (double)ub[j] + own_drift * (1.0 + kRelSlack);
@@ -1089,11 +1112,14 @@ cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_
                                int64_t n, int c, const int32_t* labels, const int32_t* counts,
                                const double* sep2, double safety, const double* drift, float* ub,
                                float* lb, int32_t* flag_list, DevStatus* status, cudaStream_t st,
-                               int32_t* labels_copy) {
+                               int32_t* labels_copy, const float* ylo_part, float* ycol, int64_t d) {
     count_launches(1);
+    // |l - bf16(l)| below 2^-75 squares to zero in FP32: sqrt(d) 2^-74 covers all of them
+    const float floor = ycol ? (float)(std::sqrt((double)d) * 5.29395592033938e-23) : 0.f;
     k_flag_bounds<<<grid_for(n, kThreads), kThreads, 0, st>>>(mode, own_part, dl_part, nchunks, n, c,
                                                               labels, counts, sep2, safety, drift,
-                                                              ub, lb, flag_list, status, labels_copy);
+                                                              ub, lb, flag_list, status, labels_copy,
+                                                              ylo_part, ycol, floor);
     return cudaGetLastError();
 }
 

@@ -75,8 +75,10 @@ struct respca_ctx {
         sp_M, sp_sqn, sp_part, sp_gsum, sp_sig, sp_deg, sp_Y, sp_W, sp_T, sp_Z, sp_H, sp_Q, sp_ev,
         cs_part, cs_done,     // per-split norms and counters of the centroid statistics
         norm_red,             // the norm reduction's per-CTA parts
-        sp_res, sp_E, sp_P, sp_Ypad;   // spectral p step: affinity, search blocks, Rayleigh-Ritz, embedding,
+        sp_res, sp_E, sp_P, sp_Ypad,   // spectral p step: affinity, search blocks, Rayleigh-Ritz, embedding,
                               // M Y partials, a 16-byte-aligned copy of Y for the tensor maps
+        mu_a16,               // the centroid operand's BF16 split (16-bit search operands)
+        Lsh, ylo_part, ycol;  // BF16 copy of the FP32 L, its per-chunk and per-column error norms
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -85,6 +87,11 @@ struct respca_ctx {
     bool dense_recorded = false;                  // evd0 / evd1 bracket the last search's dense launch
     float ms_dense = 0.f;                         // per-solve accumulators of that kernel's time
     int32_t dense_passes = 0;
+    float ms_dense16 = 0.f;                       // the part of them that read 16-bit operands
+    int32_t dense16_passes = 0;
+    bool dense16 = false;                         // the last search's all-column kernel read 16 bits
+    const void* sh_for = nullptr;                 // the FP32 L that Lsh / ycol currently mirror
+    int64_t sh_ld = 0;                            // column stride of Lsh
 };
 
 namespace {
@@ -138,7 +145,8 @@ std::vector<DevBuf*> all_bufs(respca_ctx* h) {
                       &h->rc_dist, &h->rc_plist, &h->L16, &h->S16, &h->T16, &h->X16, &h->mu_a,
                       &h->bn_part, &h->sumsD, &h->sp_M, &h->sp_sqn, &h->sp_part, &h->sp_gsum,
                       &h->sp_sig, &h->sp_deg, &h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z, &h->sp_H, &h->sp_Q,
-                      &h->sp_ev, &h->sp_res, &h->sp_E, &h->sp_P, &h->sp_Ypad, &h->cs_part, &h->cs_done, &h->norm_red};
+                      &h->sp_ev, &h->sp_res, &h->sp_E, &h->sp_P, &h->sp_Ypad, &h->cs_part, &h->cs_done, &h->norm_red,
+                      &h->mu_a16, &h->Lsh, &h->ylo_part, &h->ycol};
 }
 
 respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64_t lds,
@@ -202,6 +210,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
         CK(ensure(h->rc_dist, sizeof(double) * (size_t)tp.rc_cap * c));
         CK(ensure(h->rc_plist, sizeof(int32_t) * (size_t)tp.rc_cap * c));
         CK(ensure(h->mu_a, sizeof(float) * tp.mu_a));
+        CK(ensure(h->mu_a16, sizeof(uint16_t) * tp.mu_a16));
         // per-tile arrival counters of the search kernels start every call at zero
         CK(cudaMemsetAsync(h->tile_count.p, 0, h->tile_count.bytes, h->stream));
     }
@@ -429,14 +438,39 @@ struct Problem {
 // Nearest-centroid search (Sec. 4.2 assignment) for the listed columns of Y
 // (all columns when list is null) against the centroids in h->mu: tensor
 // cores for c <= 256 unless the handle asks for the CUDA-core kernel.
-bool tc_search(respca_ctx* h, int c) { return c <= kTcMaxClusters && h->cfg.search_impl == 0; }
+bool tc_search(respca_ctx* h, int c) {
+    return c <= kTcMaxClusters && (h->cfg.search_impl == 0 || h->cfg.search_impl == 2);
+}
 
 // The TF32 split of the centroids in h->mu (for the tensor-core search).
 respca_status split_centroids(respca_ctx* h, int c, int64_t d) {
     const int64_t dpad = (d + 31) / 32 * 32;
+    const bool a16 = h->cfg.search_impl == 0;
     CK(launch_mu_split(P<float>(h->mu), c, d, tc_npad(c), dpad, P<float>(h->mu_hi), P<float>(h->mu_lo),
-                       h->stream, P<float>(h->mu_a)));
+                       h->stream, P<float>(h->mu_a), a16 ? P<__nv_bfloat16>(h->mu_a16) : nullptr,
+                       (d + 63) / 64 * 64));
     return RESPCA_OK;
+}
+
+// The 16-bit operand of the all-column search of Y, if any: BF16 data itself,
+// or the BF16 copy of the FP32 L the fused iteration wrote (h->sh_for).
+bool search16_for(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64_t d, int c, Search16* s) {
+    if (h->cfg.search_impl != 0 || tc_npad(c) > 128) return false;
+    s->a16 = P<__nv_bfloat16>(h->mu_a16);
+    s->dpad16 = (d + 63) / 64 * 64;
+    if (dtype == RESPCA_BF16) {
+        s->y16 = static_cast<const __nv_bfloat16*>(Y);
+        s->ld16 = ldy;
+        s->ycol = nullptr;
+        return true;
+    }
+    if (dtype == RESPCA_F32 && Y && Y == h->sh_for) {
+        s->y16 = P<__nv_bfloat16>(h->Lsh);
+        s->ld16 = h->sh_ld;
+        s->ycol = P<float>(h->ycol);
+        return true;
+    }
+    return false;
 }
 
 // split_ready: the split of the current centroids is already in place (the
@@ -452,13 +486,16 @@ respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64
             if (rs != RESPCA_OK) return rs;
         }
         const bool timing = h->cfg.timing != 0;
+        Search16 s16;
+        const bool use16 = search16_for(h, dtype, Y, ldy, d, c, &s16);
+        h->dense16 = use16;
         CK(launch_search_tc(dtype, Y, ldy, d, n, list, ds, P<float>(h->mu), P<float>(h->mu_hi),
                             P<float>(h->mu_lo), dpad, P<float>(h->mu_normf), P<int32_t>(h->counts), c,
                             p, P<float>(h->ub), P<float>(h->lb), P<float>(h->Gpart),
                             P<float>(h->ynorm_part), P<int32_t>(h->tile_count), P<RcRec>(h->rc_list),
                             P<int32_t>(h->rc_plist), P<double>(h->rc_dist), rc_cap, vec, h->stream, timing ? h->evd0 : nullptr,
                             timing ? h->evd1 : nullptr, timing ? &h->dense_recorded : nullptr,
-                            P<float>(h->mu_a)));
+                            P<float>(h->mu_a), use16 ? &s16 : nullptr));
     } else {
         CK(launch_assign(dtype, Y, ldy, d, n, list, P<float>(h->mu), P<float>(h->mu_normf),
                          P<int32_t>(h->counts), c, p, ds, h->stream, P<float>(h->ub), P<float>(h->lb)));
@@ -468,15 +505,19 @@ respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64
 
 // Timing mode: after the status of a search pass is read, adds the dense
 // kernel's duration if it searched every column in this pass (no queue given,
-// or a queue longer than n / 4: otherwise that kernel returned at once).
-respca_status account_dense(respca_ctx* h, bool list_given, int64_t n) {
+// or a queue longer than search_list_max: otherwise that kernel returned at once).
+respca_status account_dense(respca_ctx* h, bool list_given, int64_t n, int c) {
     if (!h->dense_recorded) return RESPCA_OK;
     h->dense_recorded = false;
-    if (list_given && (int64_t)h->hstat->flagged <= n / 4) return RESPCA_OK;
+    if (list_given && (int64_t)h->hstat->flagged <= search_list_max(n, c, h->dense16)) return RESPCA_OK;
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->evd0, h->evd1));
     h->ms_dense += ms;
     h->dense_passes += 1;
+    if (h->dense16) {
+        h->ms_dense16 += ms;
+        h->dense16_passes += 1;
+    }
     return RESPCA_OK;
 }
 
@@ -519,6 +560,10 @@ respca_status lloyd_pass_update(respca_ctx* h, int mode, int dtype, const void* 
         sp.hi = P<float>(h->mu_hi);
         sp.lo = P<float>(h->mu_lo);
         sp.a = sp.Npad <= 128 ? P<float>(h->mu_a) : nullptr;
+        if (sp.a && h->cfg.search_impl == 0) {
+            sp.a16 = P<__nv_bfloat16>(h->mu_a16);
+            sp.dpad16 = (d + 63) / 64 * 64;
+        }
     }
     CK(launch_centroids_stats(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
                               P<float>(h->mu_old), P<double>(h->mu_norm2), P<float>(h->mu_normf),
@@ -543,6 +588,7 @@ uint64_t lloyd_key(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ld
     mix(vec ? 1u : 0u);
     mix((uint64_t)max_passes);
     mix((uint64_t)h->cfg.search_impl);
+    mix(Y == h->sh_for ? 1u : 0u);   // whether the searches read the BF16 copy
     mix(reinterpret_cast<uintptr_t>(h->stream));
     for (DevBuf* b : all_bufs(h)) mix(reinterpret_cast<uintptr_t>(b->p));
     return k;
@@ -696,7 +742,7 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
         if (rs != RESPCA_OK) return rs;
         rs = read_status(h);
         if (rs != RESPCA_OK) return rs;
-        rs = account_dense(h, true, n);
+        rs = account_dense(h, true, n, c);
         if (rs != RESPCA_OK) return rs;
         sc->passes += 1;
         sc->assigned += h->hstat->flagged;
@@ -738,7 +784,7 @@ respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out
     if (rs != RESPCA_OK) return rs;
     rs = read_status(h);
     if (rs != RESPCA_OK) return rs;
-    rs = account_dense(h, false, pb.n);
+    rs = account_dense(h, false, pb.n, pb.c);
     if (rs != RESPCA_OK) return rs;
     sc.passes = 1;
     if (h->hstat->changed > 0 && km > 1) {
@@ -808,7 +854,10 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     const bool timing = h->cfg.timing != 0;
     h->ms_dense = 0.f;
     h->dense_passes = 0;
+    h->ms_dense16 = 0.f;
+    h->dense16_passes = 0;
     h->dense_recorded = false;
+    h->sh_for = nullptr;
     CK(cudaEventRecord(h->ev0, h->stream));
     DevStatus* ds = P<DevStatus>(h->status);
     CK(cudaMemsetAsync(ds, 0, sizeof(DevStatus), h->stream));
@@ -995,6 +1044,12 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     const int iter_cap = (h->cfg.stop_after_ramp && !is_warm) ? t_start : max_iter;
 
     double err_hist[2] = {INFINITY, INFINITY};   // err of the last two bf16 iterations
+    // all-column search passes counted on the device up to the last status read: the
+    // copy of L (2 B per element more in the fused pass) is written for an iteration
+    // when the previous p step (or the initial labels) searched every column twice or
+    // more, each such pass then reading 2 B per element less (the status was last
+    // read after the initial labels, which are the only passes before this loop)
+    int32_t dense_seen = 0;
     for (int t = t_start; t < iter_cap; ++t) {
         const double rho_next = rho * kappa;
         IterScalars sc;
@@ -1006,6 +1061,17 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
 
         CK(zero_counters(h));
         CK(cudaMemcpyAsync(h->labels_prev.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
+        // the K-means p step on FP32 L searches a BF16 copy of it written by the same pass
+        const int32_t dense_now = h->hstat->dense_passes;
+        const bool use_sh = !l21 && !spectral && v.sd == 0 && v.vec && h->cfg.search_impl == 0 &&
+                            tc_npad(c) <= 128 && dense_now - dense_seen >= 2;
+        dense_seen = dense_now;
+        if (use_sh) {
+            h->sh_ld = (d + 7) / 8 * 8;
+            CK(ensure(h->Lsh, sizeof(uint16_t) * (size_t)h->sh_ld * n));
+            CK(ensure(h->ylo_part, sizeof(float) * (size_t)nch * n));
+            CK(ensure(h->ycol, sizeof(float) * n));
+        }
         // L, S, Theta, norms, own distances, column movement and next-D sums in one pass
         if (timing) CK(cudaEventRecord(h->evk0, h->stream));
         if (l21)
@@ -1017,7 +1083,9 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             CK(launch_iteration(v.xd, v.sd, v.X, v.ldx, v.L, v.S, v.Th, v.ld, P<float>(h->mu),
                                 P<int32_t>(h->perm), P<TileDesc>(h->tiles), mt, ds, d, n, sc,
                                 P<float>(h->Dpart), P<float>(h->own_part), P<float>(h->dl_part),
-                                P<double>(h->norm_part), v.vec, h->stream));
+                                P<double>(h->norm_part), v.vec, h->stream, use_sh ? h->Lsh.p : nullptr,
+                                h->sh_ld, P<float>(h->ylo_part)));
+        h->sh_for = use_sh ? v.L : nullptr;
         if (timing) CK(cudaEventRecord(h->evk1, h->stream));
         out.fused_launches += 1;
         CK(launch_reduce_norms(P<double>(h->norm_part), mt, nch, ds, P<double>(h->norm_red), h->stream));
@@ -1046,7 +1114,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         CK(launch_flag_bounds(kBoundsIter, P<float>(h->own_part), P<float>(h->dl_part), nch, n, c, p,
                               P<int32_t>(h->counts), P<double>(h->sep2), safety, P<double>(h->drift),
                               P<float>(h->ub), P<float>(h->lb), P<int32_t>(h->flag_list), ds,
-                              h->stream));
+                              h->stream, nullptr, h->sh_for ? P<float>(h->ylo_part) : nullptr,
+                              h->sh_for ? P<float>(h->ycol) : nullptr, d));
         rs = search(h, v.sd == 1 ? RESPCA_BF16 : RESPCA_F32, v.L, v.ld, d, n, P<int32_t>(h->flag_list),
                     c, p, v.vec);
         if (rs != RESPCA_OK) return rs;
@@ -1059,7 +1128,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         if (rs != RESPCA_OK) return rs;
         rs = read_status(h);
         if (rs != RESPCA_OK) return rs;
-        rs = account_dense(h, true, n);
+        rs = account_dense(h, true, n, c);
         if (rs != RESPCA_OK) return rs;
         if (timing) {
             float ms = 0.f;
@@ -1141,6 +1210,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             if (out.err <= h->cfg.switch_tol || stalled) {
                 rs = widen_state(h, v.L, v.S, v.Th, v.ld, L, S, pb.Th, lds, d, n);
                 if (rs != RESPCA_OK) return rs;
+                h->sh_for = nullptr;
                 v = View{dtype, X, ldx, 0, L, S, pb.Th, lds, pb.vec};
                 // centroids of the next iteration from the FP32 X and the widened state
                 CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts),
@@ -1166,6 +1236,9 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     out.kernel_launches = t_kernel_launches - launches0;
     out.ms_dense = h->ms_dense;
     out.dense_passes = h->dense_passes;
+    out.ms_dense16 = h->ms_dense16;
+    out.dense16_passes = h->dense16_passes;
+    h->sh_for = nullptr;
     cudaEventElapsedTime(&out.ms_total, h->ev0, h->ev1);
     cudaEventElapsedTime(&out.ms_init, h->ev0, h->ev2);
     if (warm) warm->rho = rho;

@@ -128,6 +128,10 @@ struct MuSplitOut {
     int64_t dpad = 0;
     int Npad = 0;
     int arows = 0;
+    // the same rows as two BF16 parts (bf16(mu), then bf16(mu - bf16(mu))) over
+    // dpad16 (d padded to 64), for the search of 16-bit operands; or null
+    __nv_bfloat16* a16 = nullptr;
+    int64_t dpad16 = 0;
 };
 
 cudaError_t launch_sums_from_means(const float* mu, const int32_t* counts, int c, int64_t d, double* sums,
@@ -147,7 +151,8 @@ cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_
                                int64_t n, int c, const int32_t* labels, const int32_t* counts,
                                const double* sep2, double safety, const double* drift, float* ub,
                                float* lb, int32_t* flag_list, DevStatus* status, cudaStream_t st,
-                               int32_t* labels_copy = nullptr);
+                               int32_t* labels_copy = nullptr, const float* ylo_part = nullptr,
+                               float* ycol = nullptr, int64_t d = 0);
 
 cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int c, int4* moved,
                          int2* contrib, int32_t* boff, int32_t* counts, DevStatus* status,
@@ -163,7 +168,8 @@ cudaError_t launch_iteration(int dtype, int sdtype, const void* X, int64_t ldx, 
                              void* Th, int64_t lds, const float* mu, const int32_t* perm,
                              const TileDesc* tiles, int max_tiles, const DevStatus* status,
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
-                             float* dl_part, double* norm_part, bool vec, cudaStream_t st);
+                             float* dl_part, double* norm_part, bool vec, cudaStream_t st,
+                             void* Lsh = nullptr, int64_t ldsh = 0, float* ylo_part = nullptr);
 
 // part: 64 x 3 doubles of scratch
 cudaError_t launch_reduce_norms(const double* norm_part, int max_tiles, int nchunks,
@@ -244,7 +250,19 @@ int tc_npad(int c);
 // launching.
 cudaError_t allow_max_dynamic_smem(const void* func);
 cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
-                            float* mu_lo, cudaStream_t st, float* mu_a = nullptr);
+                            float* mu_lo, cudaStream_t st, float* mu_a = nullptr,
+                            __nv_bfloat16* mu_a16 = nullptr, int64_t dpad16 = 0);
+// The 16-bit operand of the all-column tensor-core search (c <= 128): y16 holds
+// BF16 columns (column j at y16 + j * ld16, ld16 a multiple of 8); when ycol is
+// null they are the data themselves, otherwise a copy of the FP32 data with
+// ycol[j] >= ||Y_j - y16_j||.  a16 is the centroids' split (MuSplitOut::a16).
+struct Search16 {
+    const __nv_bfloat16* y16 = nullptr;
+    int64_t ld16 = 0;
+    const float* ycol = nullptr;
+    const __nv_bfloat16* a16 = nullptr;
+    int64_t dpad16 = 0;
+};
 // Workspace sizes of the tensor-core search for an n-column, d-row operand.
 struct TcPlan {
     int Npad;          // centroids padded to a multiple of 16
@@ -254,6 +272,8 @@ struct TcPlan {
     int64_t tiles;     // 128-column tiles
     int64_t rc_cap;    // queued near ties whose candidate distances run spread over all SMs
     size_t mu_a;       // floats of the swapped dense kernel's centroid operand (256 x dpad)
+    int64_t dpad16;    // d padded to a multiple of 64 (16-bit operands)
+    size_t mu_a16;     // BF16 elements of its 16-bit form (256 x dpad16)
 };
 TcPlan tc_plan(int64_t n, int64_t d, int c);
 cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, int64_t n,
@@ -264,7 +284,9 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
                              int32_t* tile_count, RcRec* rc_list, int32_t* rc_pairs, double* rc_dist, int64_t rc_cap,
                              bool vec, cudaStream_t st, cudaEvent_t ev_dense0 = nullptr,
                              cudaEvent_t ev_dense1 = nullptr, bool* dense_launched = nullptr,
-                             const float* mu_a = nullptr);
+                             const float* mu_a = nullptr, const Search16* s16 = nullptr);
+// Queued columns up to which a pass searches its list rather than every column.
+int64_t search_list_max(int64_t n, int c, bool op16);
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float warp_sum(float v) {

@@ -377,6 +377,84 @@ def test_search_paths_agree_bf16_x():
     np.testing.assert_array_equal(a[1], b[1])
 
 
+# ------------------------------------------------------------------ 16-bit search operand
+def _solve_cfg(X32, c, T, dtype=None, tol=0.0, timing=True, **cfg):
+    from paper_1904_07497_gb300 import respca
+    s = respca.Solver(seed=4, timing=timing, **cfg)
+    res = s.solve(_dev(X32, dtype), c, tol=tol, max_iter=T)
+    torch.cuda.synchronize()
+    out = (res.p.cpu().numpy(), _host(res.L), _host(res.S), res.stats)
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("d,n,c,T", [
+    (2048, 1300, 50, 40),    # stacked centroids (c <= 64), several 256-column tiles, ragged last tile
+    (780, 777, 33, 35),      # d not a multiple of 64 (the last slab reads zeros past d), ragged n
+    (1000, 900, 100, 30),    # two A slabs (64 < c <= 128)
+])
+def test_bf16_copy_search_matches_fp32_search(d, n, c, T):
+    """With FP32 state the p step's all-column search reads a BF16 copy of L,
+    widens each decision by ||L_j - bf16(L_j)|| and re-decides near ties from
+    the FP32 L: labels and state equal the FP32-operand tensor-core search and
+    the CUDA-core search bit for bit.  The timing mode counts the all-column
+    passes that read the copy."""
+    pr = synth.lowrank_sparse(d, n, min(c, 40), 0.1, seed=d + n)
+    a = _solve_cfg(pr.X, c, T, search_impl=0)
+    b = _solve_cfg(pr.X, c, T, search_impl=2)
+    r = _solve_cfg(pr.X, c, T, search_impl=1)
+    assert a[3]["dense16_passes"] > 0, "the all-column search never read the copy"
+    assert b[3]["dense_passes"] > 0 and b[3]["dense16_passes"] == 0
+    assert a[3]["rechecked_columns"] > 0, "no near tie was re-decided"
+    for x in (b, r):
+        np.testing.assert_array_equal(a[0], x[0])
+        np.testing.assert_array_equal(a[1], x[1])
+        np.testing.assert_array_equal(a[2], x[2])
+    assert a[3]["lloyd_passes"] == b[3]["lloyd_passes"] == r[3]["lloyd_passes"]
+
+
+def test_bf16_data_search_matches_cuda_core():
+    """16-bit data searched directly (no widening term): BF16 X for the initial
+    labels' all-column passes, and BF16 state in the bf16 phase (precision =
+    1).  Labels and state equal the CUDA-core search's."""
+    pr = synth.lowrank_sparse(1024, 900, 30, 0.1, seed=17)
+    kw = dict(precision=1, switch_tol=0.0, ramp_skip=False)
+    a = _solve_cfg(pr.X, 30, 20, dtype=torch.bfloat16, search_impl=0, **kw)
+    r = _solve_cfg(pr.X, 30, 20, dtype=torch.bfloat16, search_impl=1, **kw)
+    assert a[3]["bf16_iters"] > 0
+    assert a[3]["dense16_passes"] > 0, "the all-column search never read BF16 data"
+    np.testing.assert_array_equal(a[0], r[0])
+    np.testing.assert_array_equal(a[1], r[1])
+    np.testing.assert_array_equal(a[2], r[2])
+
+
+def test_bf16_copy_search_device_loop():
+    """Large enough for the device-run Lloyd loop (a captured graph, timing
+    off): the copy-operand solve equals the CUDA-core solve bit for bit."""
+    pr = synth.lowrank_sparse(2048, 2200, 40, 0.1, seed=23)
+    a = _solve_cfg(pr.X, 48, 30, timing=False, search_impl=0)
+    r = _solve_cfg(pr.X, 48, 30, timing=False, search_impl=1)
+    for k in range(3):
+        np.testing.assert_array_equal(a[k], r[k])
+    assert a[3]["lloyd_passes"] == r[3]["lloyd_passes"]
+
+
+def test_bf16_copy_search_full_size():
+    """At the d = n = 10^4, rank 50, c = 50 workload, in the launch
+    configuration bench.py times (device-run Lloyd loop, timing off), the solve
+    with the BF16 copy equals the FP32-operand solve bit for bit: labels, L, S
+    and the iteration count to 1e-6."""
+    pr = synth.lowrank_sparse(10000, 10000, 50, 0.10, 0, keep_parts=False)
+    a = _solve_cfg(pr.X, 50, 500, tol=1e-6, timing=False, search_impl=0)
+    b = _solve_cfg(pr.X, 50, 500, tol=1e-6, timing=False, search_impl=2)
+    assert a[3]["converged"] == b[3]["converged"] == 1
+    assert a[3]["iters"] == b[3]["iters"]
+    assert a[3]["lloyd_passes"] == b[3]["lloyd_passes"]
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[2], b[2])
+
+
 # ------------------------------------------------------------------ two-slab dense search
 @pytest.mark.parametrize("d,n,c,T", [
     (780, 700, 65, 30),       # smallest count past the stacked layout (Npad = 80); d, n ragged to the tiles
