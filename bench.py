@@ -31,8 +31,8 @@ METRIC = "time to 1e-6 rel. err & per-iter HBM GB/s vs peak; BF16+learned vs pla
 FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_ELEM_FP32 = 28   # read X, S, Theta, L_prev; write L, S, Theta (4 B each)
 SEARCH_BYTES_PER_ELEM = 4  # the all-column search reads the FP32 operand L (or X) once
-SEARCH16_BYTES_PER_ELEM = 2  # ... or a 16-bit one: BF16 X, BF16 state, or the BF16 copy of L
-COPY16_BYTES_PER_ELEM = 2  # the fused iteration's BF16 copy of L (FP32 state, c <= 128)
+SEARCH16_BYTES_PER_ELEM = 2  # ... or a 16-bit one: BF16 / FP16 X, BF16 state, or the FP16 copy of L
+COPY16_BYTES_PER_ELEM = 2  # the fused iteration's FP16 copy of L (FP32 state, c <= 128)
 BYTES_PER_ELEM_L21 = 44    # l2,1 iteration: pass A 20 B (reads X, S, Theta, L_prev; writes L), pass B 24 B
 
 WORKLOADS = {
@@ -401,10 +401,11 @@ def run_gpu(args, rank, world, local_rank):
     if args.s_norm:
         fused_bytes = d * n * BYTES_PER_ELEM_L21
     else:
-        # FP32 state: X (esz) + S, Theta, L_prev read + L, S, Theta written (24 B), and with
-        # c <= 128 the BF16 copy of L the p step's search reads (2 B)
-        fp32_bytes = BYTES_PER_ELEM_FP32 - 4 + esz + (COPY16_BYTES_PER_ELEM if c <= 128 and d % 4 == 0 else 0)
-        fused_bytes = int(d * n * (fp32_bytes * (nf - nb) + (BYTES_PER_ELEM_FP32 // 2) * nb) / nf)
+        # FP32 state: X (esz) + S, Theta, L_prev read + L, S, Theta written (24 B), and in the
+        # iterations that write it the FP16 copy of L the p step's search reads (2 B)
+        fp32_bytes = BYTES_PER_ELEM_FP32 - 4 + esz
+        fused_bytes = int(d * n * (fp32_bytes * (nf - nb) + COPY16_BYTES_PER_ELEM * ts["copy16_iters"]
+                                   + (BYTES_PER_ELEM_FP32 // 2) * nb) / nf)
     fused_gbs = fused_bytes / (fused_avg / 1e3) / 1e9
     roof_fused = {"bound": "hbm", "kernel": "k_l21_pass_a + k_l21_pass_b (l2,1 ALM iteration, two passes)"
                   if args.s_norm else "k_iteration (fused ALM iteration)",
@@ -419,7 +420,7 @@ def run_gpu(args, rank, world, local_rank):
     # that read FP32 (4 B), each timed by the library's events
     n16 = ts["dense16_passes"]
     n32 = ts["dense_passes"] - n16
-    for kind, cnt, ms_sum, bpe in (("bf16", n16, ts["ms_dense16"], SEARCH16_BYTES_PER_ELEM),
+    for kind, cnt, ms_sum, bpe in (("16", n16, ts["ms_dense16"], SEARCH16_BYTES_PER_ELEM),
                                    ("f32", n32, ts["ms_dense"] - ts["ms_dense16"], SEARCH_BYTES_PER_ELEM)):
         if cnt <= 0:
             continue
@@ -428,10 +429,11 @@ def run_gpu(args, rank, world, local_rank):
         dense_gbs = dense_bytes / (dense_avg / 1e3) / 1e9
         flops = 2.0 * c * d * n
         if c <= 128:
-            name = (f"k_search_dense_t<{'bf16' if kind == 'bf16' else 'float'}> (tensor-core nearest-centroid "
+            name = (f"k_search_dense_t<{'16-bit' if kind == '16' else 'float'}> (tensor-core nearest-centroid "
                     "search, all columns; centroids as the M operand, 256 columns per MMA"
-                    + ("; BF16 operand: the copy of L or BF16 data)" if kind == "bf16" else "; FP32 operand)"))
-            prof = f"k_search_dense_t_{'bf16_' if kind == 'bf16' else ''}{args.workload}.txt"
+                    + ("; 16-bit operand: the FP16 copy of L, or BF16 / FP16 data)" if kind == "16"
+                       else "; FP32 operand)"))
+            prof = f"k_search_dense_t_{'16_' if kind == '16' else ''}{args.workload}.txt"
         else:
             name = "k_search_dense (tensor-core nearest-centroid search, all columns; N = centroids)"
             prof = f"k_search_dense_{args.workload}.txt"

@@ -64,11 +64,12 @@ typedef struct {
     void *stream;            /* cudaStream_t for all work; NULL = the legacy default stream */
     int32_t device;          /* CUDA device ordinal; -1 = the device current at respca_create */
     int32_t search_impl;     /* nearest-centroid search: 0 = tensor cores when c <= 256 (default;
-                                with FP32 state and c <= 128 the fused iteration also writes a
-                                BF16 copy of L, which the all-column search reads, widening each
-                                decision by ||L_j - bf16(L_j)|| and re-deciding near ties from
-                                the FP32 L, so the labels are unchanged), 1 = CUDA-core kernel
-                                always, 2 = tensor cores on the FP32 operand only (no copy) */
+                                with FP32 state and c <= 128 the fused iteration can also write
+                                an FP16 copy fp16(s L) (s a power of two), which the all-column
+                                search reads, widening each decision by ||L_j - fp16(s L_j)/s||
+                                and re-deciding near ties from the FP32 L, so the labels are
+                                unchanged; BF16 / FP16 data is searched directly), 1 = CUDA-core
+                                kernel always, 2 = tensor cores on the FP32 operand only */
     int32_t ramp_skip;       /* 1 (default): compute the leading iterations in which S stays 0
                                 and no label moves in closed form (exact; see respca_solve);
                                 0: run every iteration */
@@ -126,8 +127,10 @@ typedef struct {
     int32_t bf16_iters;      /* iterations run with BF16 state (precision = 1) */
     double x_norm;           /* ||X||_F, the denominator of the Sec. 5 quantities */
     float ms_dense16;        /* the part of ms_dense spent in passes that read 16-bit operands
-                                (BF16 data or the BF16 copy of L: 2 bytes per element) */
+                                (BF16 / FP16 data or the FP16 copy of L: 2 bytes per element) */
     int32_t dense16_passes;  /* the part of dense_passes that read 16-bit operands */
+    int32_t copy16_iters;    /* fused iterations that also wrote the FP16 copy of L (2 bytes per
+                                element more) */
 } respca_stats;
 
 /* Optional warm start / checkpoint-resume state (the paper starts from zero;

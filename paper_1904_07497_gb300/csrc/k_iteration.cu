@@ -10,10 +10,12 @@
 // state; 14 with BF16 X and BF16 state (TS), where every stored value is the
 // FP32 result rounded to BF16 and the norms, own distances and next sums are
 // formed from the stored values (so the state is exactly what is stored).
-// With FP32 state the pass can also write a BF16 copy of L (2 more bytes per
-// element) and each column chunk's ||L_j - bf16(L_j)||^2: the nearest-centroid
-// search of this iteration then reads half the bytes and widens its decisions
-// by that norm.
+// With FP32 state the pass also finds max |L| and can write an FP16 copy of L,
+// fp16(s L) with s a power of two (2 more bytes per element), and each column
+// chunk's ||L_j - fp16(s L_j) / s||^2: the nearest-centroid search of this
+// iteration then reads half the bytes and widens its decisions by that norm.
+// Values beyond the FP16 range are clamped; the norm counts them as they are
+// stored, so the widening stays a bound whatever s is.
 #include <type_traits>
 
 #include "respca_internal.cuh"
@@ -48,18 +50,29 @@ __device__ __forceinline__ void alm_element(float x, float s, float t, float l0,
     dnext = (x - sn) + tn * sc.inv_rho_next;          // D of the next iteration
 }
 
-// SH: also the BF16 copy Lsh (column stride ldsh) and ylo_part.
+// FP16 copy of one value and the square of its error: h = fp16(clamp(s l)),
+// e = l - h / s (exact in FP32 unless clamped or below the normal range).
+__device__ __forceinline__ __half copy16(float l, float s, float inv_s, float& e2) {
+    const __half h = __float2half_rn(fminf(fmaxf(l * s, -65504.f), 65504.f));
+    const float e = l - __half2float(h) * inv_s;
+    e2 = fmaf(e, e, e2);
+    return h;
+}
+
+// SH: also the FP16 copy Lsh (column stride ldsh, scale sc.sh_scale) and ylo_part.
 template <typename TX, typename TS, bool VEC, bool SH>
 __global__ void __launch_bounds__(kThreads, 2)
     k_iteration(const TX* __restrict__ X, int64_t ldx, TS* __restrict__ L, TS* __restrict__ S,
                 TS* __restrict__ Th, int64_t lds, const float* __restrict__ mu,
                 const int32_t* __restrict__ perm, const TileDesc* __restrict__ tiles,
-                const DevStatus* __restrict__ status, int64_t d, int64_t n, IterScalars sc,
+                DevStatus* __restrict__ status, int64_t d, int64_t n, IterScalars sc,
                 float* __restrict__ Dpart, float* __restrict__ own_part,
                 float* __restrict__ dl_part, double* __restrict__ norm_part,
-                __nv_bfloat16* __restrict__ Lsh, int64_t ldsh, float* __restrict__ ylo_part) {
+                __half* __restrict__ Lsh, int64_t ldsh, float* __restrict__ ylo_part) {
+    constexpr bool kMax = std::is_same<TS, float>::value;   // max |L| for the copy's next scale
     __shared__ float red[kThreads / 32][kChunkRows];
     __shared__ double nred[kThreads / 32][3];
+    __shared__ float mred[kThreads / 32];
     const int tile_idx = blockIdx.x;
     if (tile_idx >= status->ntiles) return;
     const TileDesc td = tiles[tile_idx];
@@ -68,21 +81,20 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int lane = threadIdx.x & 31;
     const float* mup = mu + (int64_t)td.label * d;
 
-    float4 m[4], acc[4];
+    // the tile's centroid rows in shared memory (constant over the CTA's columns;
+    // in registers they would push the loads in flight into local memory)
+    __shared__ __align__(16) float msh[kChunkRows];
+    for (int i = threadIdx.x; i < kChunkRows; i += kThreads) msh[i] = (r0 + i < d) ? mup[r0 + i] : 0.f;
+    float4 acc[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int64_t rr = r0 + s * 128 + lane * 4;
-        acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        m[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (VEC) {
-            if (rr < d) m[s] = *reinterpret_cast<const float4*>(mup + rr);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (rr + q < d) f4set(m[s], q, mup[rr + q]);
-        }
+    for (int s = 0; s < 4; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    float nr = 0.f, ndl = 0.f, nds = 0.f, lmax = 0.f;
+    const float inv_s = 1.f / sc.sh_scale;   // a power of two: exact
+    if (SH && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        status->sh_scale = sc.sh_scale;
+        status->sh_inv2 = inv_s * inv_s;
     }
-    float nr = 0.f, ndl = 0.f, nds = 0.f;
 
     for (int k = warp; k < td.len; k += kThreads / 32) {
         const int64_t col = perm[td.start + k];
@@ -107,12 +119,13 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int s = 0; s < 4; ++s) {
                 const int64_t rr = r0 + s * 128 + lane * 4;
                 if (rr < d) {
+                    const float4 ms = *reinterpret_cast<const float4*>(msh + s * 128 + lane * 4);
                     float4 lo, so, to;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         float l, sn, tn, dn;
                         alm_element<TS>(f4get(xv[s], q), f4get(sv[s], q), f4get(tv[s], q),
-                                    f4get(lv[s], q), f4get(m[s], q), sc, l, sn, tn, own, nr, dlc,
+                                    f4get(lv[s], q), f4get(ms, q), sc, l, sn, tn, own, nr, dlc,
                                     nds, dn);
                         f4set(lo, q, l);
                         f4set(so, q, sn);
@@ -122,17 +135,18 @@ __global__ void __launch_bounds__(kThreads, 2)
                     StateIO<TS>::store4(lc + rr, lo);
                     StateIO<TS>::store4(scol + rr, so);
                     StateIO<TS>::store4(tc + rr, to);
+                    if constexpr (kMax)
+                        lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(lo.x), fabsf(lo.y)), fmaxf(fabsf(lo.z), fabsf(lo.w))));
                     if constexpr (SH) {
-                        const __nv_bfloat162 b0 = __floats2bfloat162_rn(lo.x, lo.y);
-                        const __nv_bfloat162 b1 = __floats2bfloat162_rn(lo.z, lo.w);
+                        __half2 h0, h1;
+                        h0.x = copy16(lo.x, sc.sh_scale, inv_s, yl);
+                        h0.y = copy16(lo.y, sc.sh_scale, inv_s, yl);
+                        h1.x = copy16(lo.z, sc.sh_scale, inv_s, yl);
+                        h1.y = copy16(lo.w, sc.sh_scale, inv_s, yl);
                         uint2 u;
-                        u.x = *reinterpret_cast<const uint32_t*>(&b0);
-                        u.y = *reinterpret_cast<const uint32_t*>(&b1);
+                        u.x = *reinterpret_cast<const uint32_t*>(&h0);
+                        u.y = *reinterpret_cast<const uint32_t*>(&h1);
                         *reinterpret_cast<uint2*>(Lsh + col * ldsh + rr) = u;
-                        // l - bf16(l) is exact in FP32
-                        const float2 f0 = __bfloat1622float2(b0), f1 = __bfloat1622float2(b1);
-                        const float e0 = lo.x - f0.x, e1 = lo.y - f0.y, e2 = lo.z - f1.x, e3 = lo.w - f1.y;
-                        yl = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, yl))));
                     }
                 }
             }
@@ -146,10 +160,11 @@ __global__ void __launch_bounds__(kThreads, 2)
                         float l, sn, tn, dn;
                         alm_element<TS>(XLoad<TX>::one(xc + rr + q), StateIO<TS>::load1(scol + rr + q),
                                         StateIO<TS>::load1(tc + rr + q), StateIO<TS>::load1(lc + rr + q),
-                                        f4get(m[s], q), sc, l, sn, tn, own, nr, dlc, nds, dn);
+                                        msh[s * 128 + lane * 4 + q], sc, l, sn, tn, own, nr, dlc, nds, dn);
                         StateIO<TS>::store1(lc + rr + q, l);
                         StateIO<TS>::store1(scol + rr + q, sn);
                         StateIO<TS>::store1(tc + rr + q, tn);
+                        if constexpr (kMax) lmax = fmaxf(lmax, fabsf(l));
                         f4set(acc[s], q, f4get(acc[s], q) + dn);
                     }
                 }
@@ -171,10 +186,15 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int q = 0; q < 4; ++q) red[warp][s * 128 + lane * 4 + q] = f4get(acc[s], q);
     const double w0 = warp_sum((double)nr), w1 = warp_sum((double)ndl), w2 = warp_sum((double)nds);
+    if constexpr (kMax) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    }
     if (lane == 0) {
         nred[warp][0] = w0;
         nred[warp][1] = w1;
         nred[warp][2] = w2;
+        mred[warp] = lmax;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kChunkRows; i += kThreads) {
@@ -191,6 +211,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int w = 0; w < kThreads / 32; ++w) t += nred[w][threadIdx.x];
         norm_part[((int64_t)blockIdx.y * gridDim.x + tile_idx) * 3 + threadIdx.x] = t;
     }
+    if (kMax && threadIdx.x == 32) {
+        float m = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, mred[w]);
+        atomicMax(&status->lmax_bits, __float_as_uint(m));   // non-negative floats order as their bits
+    }
 }
 
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
@@ -199,13 +224,13 @@ inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per
 
 cudaError_t launch_iteration(int dtype, int sdtype, const void* X, int64_t ldx, void* L, void* S,
                              void* Th, int64_t lds, const float* mu, const int32_t* perm,
-                             const TileDesc* tiles, int max_tiles, const DevStatus* status,
+                             const TileDesc* tiles, int max_tiles, DevStatus* status,
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
                              float* dl_part, double* norm_part, bool vec, cudaStream_t st, void* Lsh,
                              int64_t ldsh, float* ylo_part) {
     count_launches(1);
     const dim3 grid(max_tiles, grid_for(d, kChunkRows));
-    auto* sh = static_cast<__nv_bfloat16*>(Lsh);
+    auto* sh = static_cast<__half*>(Lsh);
     RESPCA_DISPATCH_X(dtype, TX, {
         RESPCA_DISPATCH_S(sdtype, TS, {
             bool done = false;

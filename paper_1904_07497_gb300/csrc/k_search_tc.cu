@@ -195,19 +195,21 @@ __device__ __forceinline__ void warp_best(float& v, int& i, float& e) {
     }
 }
 
-// mu2v[q], okv[q]: ||mu_i||^2 and "cluster i is not empty" for i = lane + 32 q,
-// loaded by the caller.  y2 is ||y~||^2 of the operand y~ the products use;
-// yspl bounds ||y - y~|| when y2 is exact ||y||^2 (TF32 truncation) or the
-// centroid split term; ysh > 0 (a 16-bit copy y~ of FP32 data) bounds
-// ||y - y~||: the scores then widen by 2 ||mu_i|| ysh and the bounds are
-// distances to y~ moved by ysh (triangle inequality).
+// mu2v[q], okv[q], serr[q]: ||mu_i||^2, "cluster i is not empty" and the error
+// norm of centroid i's 16-bit split (0 with FP32 operands) for i = lane + 32 q,
+// loaded by the caller.  y2 is ||y~||^2 of the operand y~ the products use.
+// ylo bounds ||y - tf32(y)|| when y2 is exact ||y||^2 (FP32 operand); ysh > 0
+// (a 16-bit copy y~ of FP32 data) bounds ||y - y~||: the scores then widen by
+// 2 ||mu_i|| ysh and the bounds are distances to y~ moved by ysh (triangle
+// inequality).  The split adds |(mu_i - mu~_i) . y~| <= serr_i ||y~|| to each
+// product.
 __device__ __forceinline__ float pick4(const float (&v)[4], int q) {
     return q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3];
 }
 
 template <typename G>
-__device__ void finalize_warp(int64_t col, float y2, float yspl, float ysh, G g, const float (&mu2v)[4],
-                              const bool (&okv)[4],
+__device__ void finalize_warp(int64_t col, float y2, float ylo, float ysh, G g, const float (&mu2v)[4],
+                              const float (&serr)[4], const bool (&okv)[4],
                               int c, int32_t* __restrict__ labels, float* __restrict__ ub, float* __restrict__ lb,
                               DevStatus* __restrict__ status, const RcQueue& rc) {
     const int lane = threadIdx.x & 31;
@@ -222,7 +224,7 @@ __device__ void finalize_warp(int64_t col, float y2, float yspl, float ysh, G g,
         if (ok[q]) {
             const float mu2 = mu2v[q];
             sc[q] = fmaf(-2.f, g(i), mu2);
-            er[q] = score_err(mu2, y2, yspl + ysh);
+            er[q] = score_err(mu2, y2, ylo + ysh) + 2.f * serr[q] * sqrtf(y2);
         }
     }
     float bs = INFINITY, be = 0.f;
@@ -282,8 +284,10 @@ __device__ void finalize_warp(int64_t col, float y2, float yspl, float ysh, G g,
     if (ysh > 0.f) {   // uniform over the warp
         const float mu2b = __shfl_sync(0xffffffffu, pick4(mu2v, bi >> 5), bi & 31);
         const float mu2s = __shfl_sync(0xffffffffu, pick4(mu2v, si >> 5), si & 31);
-        bb = score_err(mu2b, y2, yspl);
-        sb = score_err(mu2s, y2, yspl);
+        const float sb_ = __shfl_sync(0xffffffffu, pick4(serr, bi >> 5), bi & 31);
+        const float ss_ = __shfl_sync(0xffffffffu, pick4(serr, si >> 5), si & 31);
+        bb = score_err(mu2b, y2, ylo) + 2.f * sb_ * sqrtf(y2);
+        sb = score_err(mu2s, y2, ylo) + 2.f * ss_ * sqrtf(y2);
     }
     if (lane != 0) return;
     const float yerr = 1e-5f * y2;
@@ -937,10 +941,11 @@ constexpr int kTtMaxS = 4;
 // ymode: what bounds ||y - y~|| for the operand y~ the products use.
 //   0: FP32 operand truncated to TF32 by the MMA; the kernel sums ||y - tf32(y)||^2.
 //   1: 16-bit operand that is the data itself (y~ = y).
-//   2: 16-bit copy y~ of FP32 data y; ycol[j] bounds ||y_j - y~_j|| (formed where
-//      the copy is written) and the distances are bounded through y~.
-// With 16-bit operands the centroids are split into two 16-bit parts whose sum
-// is within 2^-16 ||mu|| + (subnormal terms) of mu; kSplit16 covers it.
+//   2: FP16 copy fp16(s y) of FP32 data y, s = status->sh_scale; ycol[j] bounds
+//      ||y_j - y~_j|| (y~ = copy / s; formed where the copy is written), the
+//      products and norms carry s^2, and the distances are bounded through y~.
+// With 16-bit operands the centroids are split into two 16-bit parts whose
+// sum is within a16_err[i] of mu_i (exact norm of the split's error, bounded).
 struct DenseTArgs {
     int64_t d, n, Q, T, W;   // rows, columns, slabs per tile, 256-column tiles, work units
     int Npad, stacked, S, cmax;
@@ -948,8 +953,8 @@ struct DenseTArgs {
     int64_t list_min;
     int ymode;
     const float* ycol;
+    const float* a16_err;
 };
-constexpr float kSplit16 = 3.0517578e-5f;   // 2^-15: twice the BF16 two-part split bound
 
 // Adds the squares of the eight 16-bit values of a 16-byte chunk to acc.
 template <typename TY>
@@ -1232,14 +1237,17 @@ __global__ void __launch_bounds__(kFinThreads)
     const int t = threadIdx.x;
     const int jl = t % kFinCols;
     // the centroids' norms and counts first: their loads overlap the partial sums'
-    float mu2v[4];
+    float mu2v[4], serr[4];
     bool okv[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i = (t & 31) + 32 * q;
         okv[q] = i < c && __ldg(counts + i) != 0;
         mu2v[q] = i < c ? __ldg(mu_normf + i) : 0.f;
+        serr[q] = (a.ymode != 0 && i < c) ? __ldg(a.a16_err + i) : 0.f;
     }
+    // the FP16 copy's products and norms carry s^2 (s a power of two: exact)
+    const float inv2 = a.ymode == 2 ? status->sh_inv2 : 1.f;
     const int rows = a.stacked ? 64 : 128;   // the stacked kernel has added the lo rows in
     const float* gt = Gpart + (int64_t)tile * a.cmax * rows * kTtN + jc0 + jl;
     const int64_t slot_stride = (int64_t)rows * kTtN;
@@ -1247,12 +1255,13 @@ __global__ void __launch_bounds__(kFinThreads)
         float v = 0.f;
 #pragma unroll 4
         for (int sl = 0; sl < ncontrib; ++sl) v += __ldcg(gt + sl * slot_stride + (int64_t)i * kTtN);
-        gs[i * kGs + jl] = v;
+        gs[i * kGs + jl] = v * inv2;
     }
     if (t < kFinCols) {
         const float* yt = ynorm_part + (int64_t)tile * a.cmax * kTtN + jc0 + t;
         float y2 = 0.f;
         for (int sl = 0; sl < ncontrib; ++sl) y2 += __ldcg(yt + (int64_t)sl * kTtN);
+        y2 *= inv2;
         ys[t] = y2;
         if (a.ymode == 0) {
             // ||y - tf32(y)||: FP32 sums of at most d squares, so the norm is
@@ -1264,7 +1273,7 @@ __global__ void __launch_bounds__(kFinThreads)
             yshs[t] = 0.f;
         } else {
             const int64_t col = col0 + t;
-            ylos[t] = kSplit16 * sqrtf(y2);
+            ylos[t] = 0.f;
             yshs[t] = (a.ymode == 2 && col < a.n) ? __ldg(a.ycol + col) : 0.f;
         }
     }
@@ -1277,7 +1286,8 @@ __global__ void __launch_bounds__(kFinThreads)
         const int jw = warp * kColsPerWarp + k2;
         const int64_t p = col0 + jw;
         if (p >= a.n) break;
-        finalize_warp(p, ys[jw], ylos[jw], yshs[jw], [&](int i) { return gs[i * kGs + jw]; }, mu2v, okv, c, labels, ub, lb,
+        finalize_warp(p, ys[jw], ylos[jw], yshs[jw], [&](int i) { return gs[i * kGs + jw]; }, mu2v, serr, okv, c,
+                      labels, ub, lb,
                       status, rc_list);
     }
 }
@@ -1477,39 +1487,65 @@ __global__ void __launch_bounds__(kThreads)
 // when mu_a is given, the A operand of the swapped dense kernel: for
 // stacked (Npad <= 64) rows i = raw mu_i and 64 + i = lo(mu_i) over 64 rows,
 // otherwise rows i = raw mu_i and 128 + i = lo(mu_i) over 128 rows (rows
-// beyond c zero).  mu_a16 (rows of dpad16): the same layout in two BF16 parts,
-// bf16(mu_i) and bf16(mu_i - bf16(mu_i)) (the difference is exact in FP32), so
-// that their sum is within 2^-16 |mu| of each element (plus 2^-134 below the
-// normal range).  One thread per (row, element) of the wider padding.
+// beyond c zero).  With s16.a16: the same rows as the two 16-bit parts of
+// split16 over dpad16, and a16_err[i] from the squared errors of row i, summed
+// per CTA and then in CTA order by the CTA that finishes the row last.
+// Grid: (rows, CTAs per row), kSplitPer elements of a row per CTA.
+constexpr int kSplitPer = kThreads * 8;
+
 __global__ void __launch_bounds__(kThreads)
     k_mu_split(const float* __restrict__ mu, int c, int64_t d, int Npad, int64_t dpad,
                float* __restrict__ mu_hi, float* __restrict__ mu_lo, float* __restrict__ mu_a,
-               int arows, __nv_bfloat16* __restrict__ mu_a16, int64_t dpad16) {
-    const int rows = mu_a ? arows : Npad;
-    const int64_t dw = dpad16 > dpad ? dpad16 : dpad;
-    const int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (idx >= (int64_t)rows * dw) return;
-    const int i = (int)(idx / dw);
-    const int64_t r = idx % dw;
-    const float v = (i < c && r < d) ? mu[(int64_t)i * d + r] : 0.f;
-    if (r < dpad) {
-        const int64_t o = (int64_t)i * dpad + r;
-        const float hi = tf32_hi(v);
-        if (i < Npad) {
-            mu_hi[o] = hi;
-            mu_lo[o] = v - hi;
+               int arows, MuSplitOut s16, float* __restrict__ part, int32_t* __restrict__ done) {
+    __shared__ float red[kThreads / 32];
+    __shared__ int last_sh;
+    const int i = blockIdx.x;
+    const int64_t dw = (s16.a16 && s16.dpad16 > dpad) ? s16.dpad16 : dpad;
+    const int64_t r0 = (int64_t)blockIdx.y * kSplitPer;
+    const int64_t r1 = r0 + kSplitPer < dw ? r0 + kSplitPer : dw;
+    const float s = (s16.a16 && s16.a16_kind == 2) ? s16.status->sh_scale : 1.f;
+    float e2 = 0.f;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += kThreads) {
+        const float v = (i < c && r < d) ? mu[(int64_t)i * d + r] : 0.f;
+        if (r < dpad) {
+            const int64_t o = (int64_t)i * dpad + r;
+            const float hi = tf32_hi(v);
+            if (i < Npad) {
+                mu_hi[o] = hi;
+                mu_lo[o] = v - hi;
+            }
+            if (mu_a) {
+                mu_a[o] = v;
+                mu_a[(int64_t)arows * dpad + o] = v - hi;
+            }
         }
-        if (mu_a) {
-            mu_a[o] = v;
-            mu_a[(int64_t)arows * dpad + o] = v - hi;
+        if (s16.a16 && r < s16.dpad16) {
+            uint16_t p1, p2;
+            split16(v, s16.a16_kind, s, p1, p2, e2);
+            const int64_t o = (int64_t)i * s16.dpad16 + r;
+            s16.a16[o] = p1;
+            s16.a16[(int64_t)arows * s16.dpad16 + o] = p2;
         }
     }
-    if (mu_a16 && r < dpad16) {
-        const int64_t o = (int64_t)i * dpad16 + r;
-        const __nv_bfloat16 h1 = __float2bfloat16_rn(v);
-        mu_a16[o] = h1;
-        mu_a16[(int64_t)arows * dpad16 + o] = __float2bfloat16_rn(v - __bfloat162float(h1));
+    if (!s16.a16) return;
+    e2 = warp_sum(e2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
+    __syncthreads();
+    const int S = gridDim.y;
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) b += red[w];
+        part[(int64_t)i * S + blockIdx.y] = b;
+        __threadfence();
+        last_sh = atomicAdd(&done[i], 1) == S - 1;
     }
+    __syncthreads();
+    if (!last_sh || threadIdx.x != 0) return;
+    __threadfence();
+    float tot = 0.f;
+    for (int q = 0; q < S; ++q) tot += __ldcg(part + (int64_t)i * S + q);
+    s16.a16_err[i] = split16_err(tot, d, s);
+    done[i] = 0;
 }
 
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
@@ -1639,17 +1675,24 @@ TcPlan tc_plan(int64_t n, int64_t d, int c) {
     return t;
 }
 
+int mu_split16_splits(int64_t d) {
+    const int64_t dw = (d + 63) / 64 * 64;
+    return (int)((dw + kSplitPer - 1) / kSplitPer);
+}
+
 cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
-                            float* mu_lo, cudaStream_t st, float* mu_a, __nv_bfloat16* mu_a16,
-                            int64_t dpad16) {
+                            float* mu_lo, cudaStream_t st, float* mu_a, const MuSplitOut* sp16, float* part,
+                            int32_t* done) {
     count_launches(1);
     const int arows = Npad <= 64 ? 64 : 128;
     const bool with_a = mu_a != nullptr && Npad <= 128;
     const int rows = with_a ? arows : Npad;
-    if (!with_a) mu_a16 = nullptr;
-    const int64_t dw = (mu_a16 && dpad16 > dpad) ? dpad16 : dpad;
-    k_mu_split<<<grid_for((int64_t)rows * dw, kThreads), kThreads, 0, st>>>(
-        mu, c, d, Npad, dpad, mu_hi, mu_lo, with_a ? mu_a : nullptr, arows, mu_a16, mu_a16 ? dpad16 : 0);
+    MuSplitOut s16;
+    if (with_a && sp16 && sp16->a16) s16 = *sp16;
+    const int64_t dw = (s16.a16 && s16.dpad16 > dpad) ? s16.dpad16 : dpad;
+    const dim3 grid((unsigned)rows, (unsigned)((dw + kSplitPer - 1) / kSplitPer));
+    k_mu_split<<<grid, kThreads, 0, st>>>(mu, c, d, Npad, dpad, mu_hi, mu_lo, with_a ? mu_a : nullptr, arows,
+                                          s16, part, done);
     return cudaGetLastError();
 }
 
@@ -1676,9 +1719,9 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
     const bool dense_ok = dtype == 0 && vec && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
                           ldy % 4 == 0 && (reinterpret_cast<uintptr_t>(mu_hi) % 16 == 0) &&
                           (reinterpret_cast<uintptr_t>(mu_lo) % 16 == 0);
-    // 16-bit all-column path: BF16 columns (the data or a copy of it) and the
-    // centroids' BF16 split, 16-byte aligned columns
-    const bool dense16 = s16 && s16->y16 && s16->a16 && Npad <= 128 &&
+    // 16-bit all-column path: BF16 or FP16 columns (the data, or the FP16 copy of
+    // FP32 data) and the centroids' split of the same type, 16-byte aligned columns
+    const bool dense16 = s16 && s16->y16 && s16->a16 && s16->a16_err && Npad <= 128 &&
                          (reinterpret_cast<uintptr_t>(s16->y16) % 16 == 0) && s16->ld16 % 8 == 0 &&
                          (reinterpret_cast<uintptr_t>(s16->a16) % 16 == 0) && s16->dpad16 % 64 == 0;
     // larger queued lists use the dense kernel
@@ -1694,8 +1737,8 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
         CUtensorMap tmY, tmA;
         const DenseTPlan dp = dense_t_plan(n, d, Npad, dense16 ? 2 * kTcK : kTcK);
         const bool enc_ok =
-            dense16 ? (encode_2d_16(&tmY, s16->y16, true, d, n, s16->ld16, 2 * kTcK, kTtN) &&
-                       encode_2d_16(&tmA, s16->a16, true, s16->dpad16, 256, s16->dpad16, 2 * kTcK, 128))
+            dense16 ? (encode_2d_16(&tmY, s16->y16, !s16->fp16, d, n, s16->ld16, 2 * kTcK, kTtN) &&
+                       encode_2d_16(&tmA, s16->a16, !s16->fp16, s16->dpad16, 256, s16->dpad16, 2 * kTcK, 128))
                     : (encode_2d(&tmY, static_cast<const float*>(Y), d, n, ldy, kTcK, kTtN) &&
                        encode_2d(&tmA, mu_a, dpad, 256, dpad, kTcK, 128));
         if (enc_ok) {
@@ -1713,7 +1756,9 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
             a.list_min = list_max + 1;
             a.ymode = dense16 ? (s16->ycol ? 2 : 1) : 0;
             a.ycol = dense16 ? s16->ycol : nullptr;
-            auto kern = dense16 ? k_search_dense_t<__nv_bfloat16> : k_search_dense_t<float>;
+            a.a16_err = dense16 ? s16->a16_err : nullptr;
+            auto kern = !dense16 ? k_search_dense_t<float>
+                                 : (s16->fp16 ? k_search_dense_t<__half> : k_search_dense_t<__nv_bfloat16>);
             e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
             if (e != cudaSuccess) return e;
             count_launches(1);

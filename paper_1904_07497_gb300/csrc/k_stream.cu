@@ -17,12 +17,13 @@ __global__ void __launch_bounds__(kThreads) k_fro2(const TX* __restrict__ X, int
                                                    int64_t ldx, double* __restrict__ part,
                                                    DevStatus* __restrict__ status) {
     __shared__ double red[kThreads / 32];
+    __shared__ float redm[kThreads / 32];
     const int64_t rows_per_unit = kThreads * 4;
     const int64_t seg = (d + rows_per_unit - 1) / rows_per_unit;
     const int64_t units = seg * n;
     // compensated FP32 per thread (an FP64 add per unit would bound this pass by the
-    // FP64 pipe), FP64 across threads
-    float acc = 0.f, comp = 0.f;
+    // FP64 pipe), FP64 across threads; and max |x|
+    float acc = 0.f, comp = 0.f, mx = 0.f;
     bool bad = false;
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const int64_t j = units < 0x7fffffff ? (int64_t)((uint32_t)u / (uint32_t)seg) : u / seg;
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(kThreads) k_fro2(const TX* __restrict__ X, int
                 const float4 v = XLoad<TX>::four(col + r);
                 bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
                 s = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
+                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
             }
         } else {
 #pragma unroll
@@ -42,6 +44,7 @@ __global__ void __launch_bounds__(kThreads) k_fro2(const TX* __restrict__ X, int
                     const float v = XLoad<TX>::one(col + r + q);
                     bad |= !isfinite(v);
                     s = fmaf(v, v, s);
+                    mx = fmaxf(mx, fabsf(v));
                 }
         }
         const float y = s - comp;
@@ -50,12 +53,22 @@ __global__ void __launch_bounds__(kThreads) k_fro2(const TX* __restrict__ X, int
         acc = t;
     }
     double accd = warp_sum((double)acc - (double)comp);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = accd;
+        redm[threadIdx.x >> 5] = mx;
+    }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&status->nonfinite, 1);
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        float m = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            t += red[w];
+            m = fmaxf(m, redm[w]);
+        }
         part[blockIdx.x] = t;
+        atomicMax(&status->xmax_bits, __float_as_uint(m));   // non-negative floats order as their bits
     }
 }
 
@@ -349,8 +362,8 @@ __global__ void __launch_bounds__(kCsThreads)
     k_centroids_stats(const double* __restrict__ sums, const int32_t* __restrict__ counts, int64_t d,
                       int64_t per, float* __restrict__ mu, float* __restrict__ mu_old,
                       double* __restrict__ mu_norm2, float* __restrict__ mu_normf, double* __restrict__ drift,
-                      MuSplitOut sp, float2* __restrict__ part, int32_t* __restrict__ done) {
-    __shared__ float red[kCsThreads / 32][2];
+                      MuSplitOut sp, float4* __restrict__ part, int32_t* __restrict__ done) {
+    __shared__ float red[kCsThreads / 32][3];
     __shared__ int last_sh;
     __shared__ double inv_sh;   // 1 / n_i once per block (see k_centroids)
     const int i = blockIdx.x;
@@ -362,7 +375,8 @@ __global__ void __launch_bounds__(kCsThreads)
     float* m = mu + (int64_t)i * d;
     float* mo = mu_old + (int64_t)i * d;
     const int64_t r0 = (int64_t)blockIdx.y * per, r1 = r0 + per < d ? r0 + per : d;
-    float acc = 0.f, ca = 0.f, dr = 0.f, cd = 0.f;
+    const float s16 = (sp.a16 && sp.a16_kind == 2) ? sp.status->sh_scale : 1.f;
+    float acc = 0.f, ca = 0.f, dr = 0.f, cd = 0.f, e16 = 0.f;
     for (int64_t r = r0 + threadIdx.x; r < r1; r += kCsThreads) {
         const float old = m[r];
         mo[r] = old;
@@ -395,43 +409,49 @@ __global__ void __launch_bounds__(kCsThreads)
                 sp.a[idx] = v;
                 sp.a[(int64_t)sp.arows * sp.dpad + idx] = v - hi;
             }
-            if (sp.a16) {   // the BF16 split of k_mu_split
+            if (sp.a16) {   // the 16-bit split of k_mu_split
                 const int64_t o = (int64_t)i * sp.dpad16 + r;
-                const __nv_bfloat16 h1 = __float2bfloat16_rn(v);
-                sp.a16[o] = h1;
-                sp.a16[(int64_t)sp.arows * sp.dpad16 + o] = __float2bfloat16_rn(v - __bfloat162float(h1));
+                uint16_t p1, p2;
+                split16(v, sp.a16_kind, s16, p1, p2, e16);
+                sp.a16[o] = p1;
+                sp.a16[(int64_t)sp.arows * sp.dpad16 + o] = p2;
             }
         }
     }
     acc = warp_sum(acc);
     dr = warp_sum(dr);
+    e16 = warp_sum(e16);
     if ((threadIdx.x & 31) == 0) {
         red[threadIdx.x >> 5][0] = acc;
         red[threadIdx.x >> 5][1] = dr;
+        red[threadIdx.x >> 5][2] = e16;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float a = 0.f, bsum = 0.f;
+        float a = 0.f, bsum = 0.f, esum = 0.f;
         for (int w = 0; w < kCsThreads / 32; ++w) {
             a += red[w][0];
             bsum += red[w][1];
+            esum += red[w][2];
         }
-        part[(int64_t)i * S + blockIdx.y] = make_float2(a, bsum);
+        part[(int64_t)i * S + blockIdx.y] = make_float4(a, bsum, esum, 0.f);
         __threadfence();
         last_sh = atomicAdd(&done[i], 1) == S - 1;
     }
     __syncthreads();
     if (!last_sh || threadIdx.x != 0) return;
     __threadfence();
-    float a = 0.f, bsum = 0.f;
+    float a = 0.f, bsum = 0.f, esum = 0.f;
     for (int q = 0; q < S; ++q) {
-        const float2 v = __ldcg(part + (int64_t)i * S + q);
+        const float4 v = __ldcg(part + (int64_t)i * S + q);
         a += v.x;
         bsum += v.y;
+        esum += v.z;
     }
     mu_norm2[i] = (double)a;
     mu_normf[i] = a;
     drift[i] = sqrt((double)bsum) * (1.0 + 1e-5);
+    if (sp.a16) sp.a16_err[i] = split16_err(esum, d, s16);
     done[i] = 0;
 }
 
@@ -1099,7 +1119,7 @@ int centroids_stats_splits(int c, int64_t d) {
 
 cudaError_t launch_centroids_stats(const double* sums, const int32_t* counts, int c, int64_t d, float* mu,
                                    float* mu_old, double* mu_norm2, float* mu_normf, double* drift,
-                                   const MuSplitOut& sp, float2* part, int32_t* done, cudaStream_t st) {
+                                   const MuSplitOut& sp, float4* part, int32_t* done, cudaStream_t st) {
     count_launches(1);
     const int S = centroids_stats_splits(c, d);
     const int64_t per = (d + S - 1) / S;

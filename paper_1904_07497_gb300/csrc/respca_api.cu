@@ -77,8 +77,8 @@ struct respca_ctx {
         norm_red,             // the norm reduction's per-CTA parts
         sp_res, sp_E, sp_P, sp_Ypad,   // spectral p step: affinity, search blocks, Rayleigh-Ritz, embedding,
                               // M Y partials, a 16-byte-aligned copy of Y for the tensor maps
-        mu_a16,               // the centroid operand's BF16 split (16-bit search operands)
-        Lsh, ylo_part, ycol;  // BF16 copy of the FP32 L, its per-chunk and per-column error norms
+        mu_a16, a16_err, a16_part, a16_done,   // the centroids' 16-bit split and its error norms
+        Lsh, ylo_part, ycol;  // FP16 copy of the FP32 L, its per-chunk and per-column error norms
     DevStatus* hstat = nullptr;     // pinned mirror of the status block
     double* hseed_u = nullptr;      // pinned staging of the seeding draws
     size_t hseed_cap = 0;
@@ -146,7 +146,7 @@ std::vector<DevBuf*> all_bufs(respca_ctx* h) {
                       &h->bn_part, &h->sumsD, &h->sp_M, &h->sp_sqn, &h->sp_part, &h->sp_gsum,
                       &h->sp_sig, &h->sp_deg, &h->sp_Y, &h->sp_W, &h->sp_T, &h->sp_Z, &h->sp_H, &h->sp_Q,
                       &h->sp_ev, &h->sp_res, &h->sp_E, &h->sp_P, &h->sp_Ypad, &h->cs_part, &h->cs_done, &h->norm_red,
-                      &h->mu_a16, &h->Lsh, &h->ylo_part, &h->ycol};
+                      &h->mu_a16, &h->a16_err, &h->a16_part, &h->a16_done, &h->Lsh, &h->ylo_part, &h->ycol};
 }
 
 respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64_t lds,
@@ -181,7 +181,7 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
         const bool fresh = !h->cs_done.p || h->cs_done.bytes < need;
         CK(ensure(h->cs_done, need));
         if (fresh) CK(cudaMemsetAsync(h->cs_done.p, 0, need, h->stream));
-        CK(ensure(h->cs_part, sizeof(float2) * (size_t)c * centroids_stats_splits(c, d)));
+        CK(ensure(h->cs_part, sizeof(float4) * (size_t)c * centroids_stats_splits(c, d)));
     }
     // centroid buffers start zeroed so entries of clusters that never had a
     // member hold finite values
@@ -211,6 +211,10 @@ respca_status ensure_workspace(respca_ctx* h, int64_t d, int64_t n, int c, int64
         CK(ensure(h->rc_plist, sizeof(int32_t) * (size_t)tp.rc_cap * c));
         CK(ensure(h->mu_a, sizeof(float) * tp.mu_a));
         CK(ensure(h->mu_a16, sizeof(uint16_t) * tp.mu_a16));
+        CK(ensure(h->a16_err, sizeof(float) * 256));
+        CK(ensure(h->a16_part, sizeof(float) * 256 * (size_t)mu_split16_splits(d)));
+        CK(ensure(h->a16_done, sizeof(int32_t) * 256));
+        CK(cudaMemsetAsync(h->a16_done.p, 0, h->a16_done.bytes, h->stream));
         // per-tile arrival counters of the search kernels start every call at zero
         CK(cudaMemsetAsync(h->tile_count.p, 0, h->tile_count.bytes, h->stream));
     }
@@ -442,35 +446,67 @@ bool tc_search(respca_ctx* h, int c) {
     return c <= kTcMaxClusters && (h->cfg.search_impl == 0 || h->cfg.search_impl == 2);
 }
 
-// The TF32 split of the centroids in h->mu (for the tensor-core search).
-respca_status split_centroids(respca_ctx* h, int c, int64_t d) {
-    const int64_t dpad = (d + 31) / 32 * 32;
-    const bool a16 = h->cfg.search_impl == 0;
-    CK(launch_mu_split(P<float>(h->mu), c, d, tc_npad(c), dpad, P<float>(h->mu_hi), P<float>(h->mu_lo),
-                       h->stream, P<float>(h->mu_a), a16 ? P<__nv_bfloat16>(h->mu_a16) : nullptr,
-                       (d + 63) / 64 * 64));
-    return RESPCA_OK;
+// Scale of the FP16 copy of L: the power of two s with s m in [2^10, 2^11) for
+// the reference magnitude m (the previous iteration's max |L|), 32x inside the
+// FP16 range (values that outgrow it are clamped and their columns' error
+// norms show it, so any s keeps the search exact).
+float copy_scale(float m) {
+    if (!(m > 0.f) || !std::isfinite(m)) return 1.f;
+    int e = 0;
+    std::frexp(m, &e);   // m < 2^e
+    return std::ldexp(1.f, std::min(100, std::max(-100, 11 - e)));
 }
 
-// The 16-bit operand of the all-column search of Y, if any: BF16 data itself,
-// or the BF16 copy of the FP32 L the fused iteration wrote (h->sh_for).
-bool search16_for(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64_t d, int c, Search16* s) {
+// The 16-bit operand of the all-column search of Y, if any: BF16 or FP16 data
+// itself, or the FP16 copy of the FP32 L the fused iteration wrote
+// (h->sh_for).  *kind: the centroid split it needs (split16: 1 BF16, 2 FP16
+// of s mu with the copy's scale s, 3 FP16 of mu), or 0.
+bool search16_for(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64_t d, int c, Search16* s,
+                  int* kind) {
+    *kind = 0;
     if (h->cfg.search_impl != 0 || tc_npad(c) > 128) return false;
-    s->a16 = P<__nv_bfloat16>(h->mu_a16);
+    s->a16 = P<uint16_t>(h->mu_a16);
+    s->a16_err = P<float>(h->a16_err);
     s->dpad16 = (d + 63) / 64 * 64;
-    if (dtype == RESPCA_BF16) {
-        s->y16 = static_cast<const __nv_bfloat16*>(Y);
+    if (dtype == RESPCA_BF16 || dtype == RESPCA_F16) {
+        s->y16 = Y;
         s->ld16 = ldy;
+        s->fp16 = dtype == RESPCA_F16;
         s->ycol = nullptr;
+        *kind = s->fp16 ? 3 : 1;
         return true;
     }
     if (dtype == RESPCA_F32 && Y && Y == h->sh_for) {
-        s->y16 = P<__nv_bfloat16>(h->Lsh);
+        s->y16 = h->Lsh.p;
         s->ld16 = h->sh_ld;
+        s->fp16 = true;
         s->ycol = P<float>(h->ycol);
+        *kind = 2;
         return true;
     }
     return false;
+}
+
+// The a16 fields of a split description for kind (0: none).
+void set_split16(respca_ctx* h, int64_t d, int kind, MuSplitOut* sp) {
+    if (!kind) return;
+    sp->a16 = P<uint16_t>(h->mu_a16);
+    sp->dpad16 = (d + 63) / 64 * 64;
+    sp->a16_kind = kind;
+    sp->a16_err = P<float>(h->a16_err);
+    sp->status = P<DevStatus>(h->status);
+}
+
+// The TF32 split of the centroids in h->mu (for the tensor-core search), and
+// the 16-bit one of kind (search16_for) if any.
+respca_status split_centroids(respca_ctx* h, int c, int64_t d, int kind) {
+    const int64_t dpad = (d + 31) / 32 * 32;
+    MuSplitOut sp16;
+    set_split16(h, d, kind, &sp16);
+    CK(launch_mu_split(P<float>(h->mu), c, d, tc_npad(c), dpad, P<float>(h->mu_hi), P<float>(h->mu_lo),
+                       h->stream, P<float>(h->mu_a), kind ? &sp16 : nullptr, P<float>(h->a16_part),
+                       P<int32_t>(h->a16_done)));
+    return RESPCA_OK;
 }
 
 // split_ready: the split of the current centroids is already in place (the
@@ -481,13 +517,14 @@ respca_status search(respca_ctx* h, int dtype, const void* Y, int64_t ldy, int64
     if (tc_search(h, c)) {
         const int64_t dpad = (d + 31) / 32 * 32;
         const int64_t rc_cap = tc_plan(n, d, c).rc_cap;
+        Search16 s16;
+        int kind = 0;
+        const bool use16 = search16_for(h, dtype, Y, ldy, d, c, &s16, &kind);
         if (!split_ready) {
-            const respca_status rs = split_centroids(h, c, d);
+            const respca_status rs = split_centroids(h, c, d, kind);
             if (rs != RESPCA_OK) return rs;
         }
         const bool timing = h->cfg.timing != 0;
-        Search16 s16;
-        const bool use16 = search16_for(h, dtype, Y, ldy, d, c, &s16);
         h->dense16 = use16;
         CK(launch_search_tc(dtype, Y, ldy, d, n, list, ds, P<float>(h->mu), P<float>(h->mu_hi),
                             P<float>(h->mu_lo), dpad, P<float>(h->mu_normf), P<int32_t>(h->counts), c,
@@ -560,14 +597,14 @@ respca_status lloyd_pass_update(respca_ctx* h, int mode, int dtype, const void* 
         sp.hi = P<float>(h->mu_hi);
         sp.lo = P<float>(h->mu_lo);
         sp.a = sp.Npad <= 128 ? P<float>(h->mu_a) : nullptr;
-        if (sp.a && h->cfg.search_impl == 0) {
-            sp.a16 = P<__nv_bfloat16>(h->mu_a16);
-            sp.dpad16 = (d + 63) / 64 * 64;
-        }
+        Search16 s16;
+        int kind = 0;
+        search16_for(h, dtype, Y, ldy, d, c, &s16, &kind);
+        if (sp.a) set_split16(h, d, kind, &sp);
     }
     CK(launch_centroids_stats(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
                               P<float>(h->mu_old), P<double>(h->mu_norm2), P<float>(h->mu_normf),
-                              P<double>(h->drift), sp, P<float2>(h->cs_part), P<int32_t>(h->cs_done), h->stream));
+                              P<double>(h->drift), sp, P<float4>(h->cs_part), P<int32_t>(h->cs_done), h->stream));
     return RESPCA_OK;
 }
 
@@ -588,7 +625,7 @@ uint64_t lloyd_key(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ld
     mix(vec ? 1u : 0u);
     mix((uint64_t)max_passes);
     mix((uint64_t)h->cfg.search_impl);
-    mix(Y == h->sh_for ? 1u : 0u);   // whether the searches read the BF16 copy
+    mix(Y == h->sh_for ? 1u : 0u);   // whether the searches read the FP16 copy
     mix(reinterpret_cast<uintptr_t>(h->stream));
     for (DevBuf* b : all_bufs(h)) mix(reinterpret_cast<uintptr_t>(b->p));
     return k;
@@ -670,7 +707,10 @@ respca_status lloyd_loop_on_device(respca_ctx* h, int mode, int dtype, const voi
     DevStatus* ds = P<DevStatus>(h->status);
     CK(launch_lloyd_init(ds, sc->passes, h->stream));
     if (tc_search(h, c)) {   // the loop's searches use the split its updates write
-        const respca_status rs = split_centroids(h, c, d);
+        Search16 s16;
+        int kind = 0;
+        search16_for(h, dtype, Y, ldy, d, c, &s16, &kind);
+        const respca_status rs = split_centroids(h, c, d, kind);
         if (rs != RESPCA_OK) return rs;
     }
     CK(cudaGraphLaunch(g->exec, h->stream));
@@ -714,7 +754,7 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
         MuSplitOut none;
         CK(launch_centroids_stats(P<double>(h->sums), P<int32_t>(h->counts), c, d, P<float>(h->mu),
                                   P<float>(h->mu_old), P<double>(h->mu_norm2), P<float>(h->mu_normf),
-                                  P<double>(h->drift), none, P<float2>(h->cs_part), P<int32_t>(h->cs_done),
+                                  P<double>(h->drift), none, P<float4>(h->cs_part), P<int32_t>(h->cs_done),
                                   h->stream));
     } else {
         CK(launch_sort_labels(p, n, c, P<int32_t>(h->perm), P<int32_t>(h->counts), P<int32_t>(h->tile_off),
@@ -866,6 +906,9 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
     if (rs != RESPCA_OK) return rs;
     if (h->hstat->nonfinite) return fail(h, RESPCA_ERR_NONFINITE_INPUT, "X holds NaN or Inf");
     const double nx = std::sqrt(h->hstat->x_norm2);
+    // max |L| of the last fused iteration (max |X| before the first): sets the FP16 copy's scale
+    float lmax_ref;
+    std::memcpy(&lmax_ref, &h->hstat->xmax_bits, sizeof(float));
     const double lam = lambda > 0.0 ? lambda : std::sqrt((double)std::max(d, n));
     out.lambda = lam;
     out.x_norm = nx;
@@ -1061,7 +1104,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
 
         CK(zero_counters(h));
         CK(cudaMemcpyAsync(h->labels_prev.p, p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
-        // the K-means p step on FP32 L searches a BF16 copy of it written by the same pass
+        // the K-means p step on FP32 L searches an FP16 copy of it written by the same pass
         const int32_t dense_now = h->hstat->dense_passes;
         const bool use_sh = !l21 && !spectral && v.sd == 0 && v.vec && h->cfg.search_impl == 0 &&
                             tc_npad(c) <= 128 && dense_now - dense_seen >= 2;
@@ -1071,7 +1114,10 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             CK(ensure(h->Lsh, sizeof(uint16_t) * (size_t)h->sh_ld * n));
             CK(ensure(h->ylo_part, sizeof(float) * (size_t)nch * n));
             CK(ensure(h->ycol, sizeof(float) * n));
+            sc.sh_scale = copy_scale(lmax_ref);
+            out.copy16_iters += 1;
         }
+        CK(cudaMemsetAsync(&ds->lmax_bits, 0, sizeof(uint32_t), h->stream));
         // L, S, Theta, norms, own distances, column movement and next-D sums in one pass
         if (timing) CK(cudaEventRecord(h->evk0, h->stream));
         if (l21)
@@ -1190,6 +1236,11 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             CK(launch_count_changed(p, P<int32_t>(h->labels_prev), n, ds, h->stream));
         }
         }   // K-means p step
+        {
+            float m;   // this iteration's max |L| (FP32 state; read with the p step's status)
+            std::memcpy(&m, &h->hstat->lmax_bits, sizeof(float));
+            if (m > 0.f) lmax_ref = m;
+        }
         rho = rho_next;
         out.iters = t + 1;
         out.err_resid = std::sqrt(r2) / nx;

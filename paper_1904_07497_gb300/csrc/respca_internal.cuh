@@ -37,6 +37,7 @@ struct IterScalars {
     float inv_rho;       // 1 / rho_t
     float rho;           // rho_t, capped at FLT_MAX
     float inv_rho_next;  // 1 / rho_{t+1}
+    float sh_scale = 1.f;  // scale s of the FP16 copy of L the pass writes (if any)
 };
 
 struct TileDesc {
@@ -70,6 +71,10 @@ struct DevStatus {
     int32_t seed_done;      // CTAs of the current k-means++ step that finished (reset by the last)
     int32_t dense_passes;   // all-column search passes so far (their parity sets the walking direction)
     int32_t norms_done;     // CTAs of the norm reduction that finished (reset by the last)
+    float sh_scale;         // power-of-two scale s of the FP16 copy of L (stores fp16(s l)) and of the
+    float sh_inv2;          //   centroids' FP16 split; 1 / s^2 (set by the fused iteration that wrote it)
+    uint32_t lmax_bits;     // bits of max |L| over the last fused iteration (FP32 state)
+    uint32_t xmax_bits;     // bits of max |X| (the norm pass over X)
 };
 
 // Modes of the bound-based pruning kernel.
@@ -128,10 +133,14 @@ struct MuSplitOut {
     int64_t dpad = 0;
     int Npad = 0;
     int arows = 0;
-    // the same rows as two BF16 parts (bf16(mu), then bf16(mu - bf16(mu))) over
-    // dpad16 (d padded to 64), for the search of 16-bit operands; or null
-    __nv_bfloat16* a16 = nullptr;
+    // the same rows as two 16-bit parts (split16 of kind a16_kind; FP16 ones of
+    // s mu with s = status->sh_scale) over dpad16 (d padded to 64), for the search
+    // of 16-bit operands; a16_err[i] bounds ||mu_i - (p1 + p2) / s||; or null
+    uint16_t* a16 = nullptr;
     int64_t dpad16 = 0;
+    int a16_kind = 0;
+    float* a16_err = nullptr;
+    const DevStatus* status = nullptr;
 };
 
 cudaError_t launch_sums_from_means(const float* mu, const int32_t* counts, int c, int64_t d, double* sums,
@@ -145,7 +154,7 @@ cudaError_t launch_sums_from_means(const float* mu, const int32_t* counts, int c
 int centroids_stats_splits(int c, int64_t d);
 cudaError_t launch_centroids_stats(const double* sums, const int32_t* counts, int c, int64_t d, float* mu,
                                    float* mu_old, double* mu_norm2, float* mu_normf, double* drift,
-                                   const MuSplitOut& sp, float2* part, int32_t* done, cudaStream_t st);
+                                   const MuSplitOut& sp, float4* part, int32_t* done, cudaStream_t st);
 
 cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_part, int nchunks,
                                int64_t n, int c, const int32_t* labels, const int32_t* counts,
@@ -166,7 +175,7 @@ cudaError_t launch_separation(const float* mu, const int32_t* counts, int c, int
 
 cudaError_t launch_iteration(int dtype, int sdtype, const void* X, int64_t ldx, void* L, void* S,
                              void* Th, int64_t lds, const float* mu, const int32_t* perm,
-                             const TileDesc* tiles, int max_tiles, const DevStatus* status,
+                             const TileDesc* tiles, int max_tiles, DevStatus* status,
                              int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
                              float* dl_part, double* norm_part, bool vec, cudaStream_t st,
                              void* Lsh = nullptr, int64_t ldsh = 0, float* ylo_part = nullptr);
@@ -249,18 +258,24 @@ int tc_npad(int c);
 // size, cannot see the cap lowered by another thread between setting it and
 // launching.
 cudaError_t allow_max_dynamic_smem(const void* func);
+// With sp16 (its a16 fields; hi, lo, a unused) also the 16-bit split and its
+// per-centroid error; part / done: mu_split16_splits(d) floats and one counter
+// per row (zero, reset by the kernel).
 cudaError_t launch_mu_split(const float* mu, int c, int64_t d, int Npad, int64_t dpad, float* mu_hi,
                             float* mu_lo, cudaStream_t st, float* mu_a = nullptr,
-                            __nv_bfloat16* mu_a16 = nullptr, int64_t dpad16 = 0);
+                            const MuSplitOut* sp16 = nullptr, float* part = nullptr, int32_t* done = nullptr);
+int mu_split16_splits(int64_t d);
 // The 16-bit operand of the all-column tensor-core search (c <= 128): y16 holds
-// BF16 columns (column j at y16 + j * ld16, ld16 a multiple of 8); when ycol is
-// null they are the data themselves, otherwise a copy of the FP32 data with
-// ycol[j] >= ||Y_j - y16_j||.  a16 is the centroids' split (MuSplitOut::a16).
+// BF16 or FP16 columns (column j at y16 + j * ld16, ld16 a multiple of 8); when
+// ycol is null they are the data themselves, otherwise the FP16 copy fp16(s Y)
+// of FP32 data.  a16 / a16_err: the centroids' split (MuSplitOut) of the same type.
 struct Search16 {
-    const __nv_bfloat16* y16 = nullptr;
+    const void* y16 = nullptr;
     int64_t ld16 = 0;
-    const float* ycol = nullptr;
-    const __nv_bfloat16* a16 = nullptr;
+    bool fp16 = false;             // FP16 (the copy of L, or FP16 data) rather than BF16
+    const float* ycol = nullptr;   // copy of FP32 data: ||Y_j - y16_j / s|| (s = status->sh_scale)
+    const uint16_t* a16 = nullptr;
+    const float* a16_err = nullptr;
     int64_t dpad16 = 0;
 };
 // Workspace sizes of the tensor-core search for an n-column, d-row operand.
@@ -406,6 +421,38 @@ __device__ __forceinline__ void f4set(float4& v, int q, float x) {
 // The TF32 part of an FP32 value as the tensor cores read it (mantissa truncated
 // to 10 bits).
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Two-part 16-bit split of a centroid element v for the search of 16-bit
+// operands.  kind 1: p1 = bf16(v), p2 = bf16(v - p1); kind 2: the same in FP16
+// of w = s v (s a power of two), each part clamped to the FP16 range.  Adds
+// the square of the error w - p1 - p2 (units of w; exact in FP32 unless a
+// part was clamped or fell below the normal range) to e2.
+__device__ __forceinline__ void split16(float v, int kind, float s, uint16_t& p1, uint16_t& p2, float& e2) {
+    if (kind == 1) {
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(v);
+        const float r = v - __bfloat162float(h1);
+        const __nv_bfloat16 h2 = __float2bfloat16_rn(r);
+        const float e = r - __bfloat162float(h2);
+        e2 = fmaf(e, e, e2);
+        p1 = __bfloat16_as_ushort(h1);
+        p2 = __bfloat16_as_ushort(h2);
+    } else {
+        const float w = v * s;
+        const __half h1 = __float2half_rn(fminf(fmaxf(w, -65504.f), 65504.f));
+        const float r = w - __half2float(h1);
+        const __half h2 = __float2half_rn(fminf(fmaxf(r, -65504.f), 65504.f));
+        const float e = r - __half2float(h2);
+        e2 = fmaf(e, e, e2);
+        p1 = __half_as_ushort(h1);
+        p2 = __half_as_ushort(h2);
+    }
+}
+
+// Upper bound on a split's error norm from the summed squares e2 (units of s v):
+// FP32 sums inflated, plus sqrt(d) 2^-74 for squares that underflowed, over s.
+__device__ __forceinline__ float split16_err(float e2, int64_t d, float s) {
+    return (sqrtf(e2) * (1.f + 1e-4f) + sqrtf((float)d) * 5.29395592e-23f) / s;
+}
 
 // ---------------------------------------------------------------- learned warm start
 // Scalars of one unrolled layer (rho_k, tau_k learned; labels fixed).

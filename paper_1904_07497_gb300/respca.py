@@ -62,7 +62,7 @@ class respca_stats(ctypes.Structure):
                 ("ms_fused", ctypes.c_float), ("ms_dense", ctypes.c_float),
                 ("dense_passes", ctypes.c_int32), ("bf16_iters", ctypes.c_int32),
                 ("x_norm", ctypes.c_double), ("ms_dense16", ctypes.c_float),
-                ("dense16_passes", ctypes.c_int32)]
+                ("dense16_passes", ctypes.c_int32), ("copy16_iters", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {(k[:-1] if k.endswith("_") else k): getattr(self, k) for k, _ in self._fields_

@@ -393,10 +393,11 @@ def _solve_cfg(X32, c, T, dtype=None, tol=0.0, timing=True, **cfg):
     (780, 777, 33, 35),      # d not a multiple of 64 (the last slab reads zeros past d), ragged n
     (1000, 900, 100, 30),    # two A slabs (64 < c <= 128)
 ])
-def test_bf16_copy_search_matches_fp32_search(d, n, c, T):
-    """With FP32 state the p step's all-column search reads a BF16 copy of L,
-    widens each decision by ||L_j - bf16(L_j)|| and re-decides near ties from
-    the FP32 L: labels and state equal the FP32-operand tensor-core search and
+def test_fp16_copy_search_matches_fp32_search(d, n, c, T):
+    """With FP32 state the p step's all-column search reads an FP16 copy
+    fp16(s L) of L, widens each decision by ||L_j - fp16(s L_j) / s|| and the
+    centroids' split error, and re-decides near ties from the FP32 L: labels
+    and state equal the FP32-operand tensor-core search and
     the CUDA-core search bit for bit.  The timing mode counts the all-column
     passes that read the copy."""
     pr = synth.lowrank_sparse(d, n, min(c, 40), 0.1, seed=d + n)
@@ -413,7 +414,7 @@ def test_bf16_copy_search_matches_fp32_search(d, n, c, T):
     assert a[3]["lloyd_passes"] == b[3]["lloyd_passes"] == r[3]["lloyd_passes"]
 
 
-def test_bf16_data_search_matches_cuda_core():
+def test_16bit_data_search_matches_cuda_core():
     """16-bit data searched directly (no widening term): BF16 X for the initial
     labels' all-column passes, and BF16 state in the bf16 phase (precision =
     1).  Labels and state equal the CUDA-core search's."""
@@ -428,7 +429,7 @@ def test_bf16_data_search_matches_cuda_core():
     np.testing.assert_array_equal(a[2], r[2])
 
 
-def test_bf16_copy_search_device_loop():
+def test_fp16_copy_search_device_loop():
     """Large enough for the device-run Lloyd loop (a captured graph, timing
     off): the copy-operand solve equals the CUDA-core solve bit for bit."""
     pr = synth.lowrank_sparse(2048, 2200, 40, 0.1, seed=23)
@@ -439,10 +440,10 @@ def test_bf16_copy_search_device_loop():
     assert a[3]["lloyd_passes"] == r[3]["lloyd_passes"]
 
 
-def test_bf16_copy_search_full_size():
+def test_fp16_copy_search_full_size():
     """At the d = n = 10^4, rank 50, c = 50 workload, in the launch
     configuration bench.py times (device-run Lloyd loop, timing off), the solve
-    with the BF16 copy equals the FP32-operand solve bit for bit: labels, L, S
+    with the FP16 copy equals the FP32-operand solve bit for bit: labels, L, S
     and the iteration count to 1e-6."""
     pr = synth.lowrank_sparse(10000, 10000, 50, 0.10, 0, keep_parts=False)
     a = _solve_cfg(pr.X, 50, 500, tol=1e-6, timing=False, search_impl=0)
