@@ -50,16 +50,20 @@ __device__ __forceinline__ void alm_element(float x, float s, float t, float l0,
     dnext = (x - sn) + tn * sc.inv_rho_next;          // D of the next iteration
 }
 
-// FP16 copy of one value and the square of its error: h = fp16(clamp(s l)),
-// e = l - h / s (exact in FP32 unless clamped or below the normal range).
-__device__ __forceinline__ __half copy16(float l, float s, float inv_s, float& e2) {
+// FP16 copy of one value, the square of its error e = l - y~ and of y~ = h / s,
+// h = fp16(clamp(s l)) (e exact in FP32 unless clamped or below the normal range).
+__device__ __forceinline__ __half copy16(float l, float s, float inv_s, float& e2, float& q2) {
     const __half h = __float2half_rn(fminf(fmaxf(l * s, -65504.f), 65504.f));
-    const float e = l - __half2float(h) * inv_s;
+    const float y = __half2float(h) * inv_s;
+    const float e = l - y;
     e2 = fmaf(e, e, e2);
+    q2 = fmaf(y, y, q2);
     return h;
 }
 
-// SH: also the FP16 copy Lsh (column stride ldsh, scale sc.sh_scale) and ylo_part.
+// SH: also the FP16 copy Lsh (column stride ldsh, scale sc.sh_scale) and, per
+// row chunk and column, ||L_j - y~_j||^2 in ylo_part[chunk][col] and ||y~_j||^2 in
+// ylo_part[nchunks + chunk][col] (y~ = copy / s).
 template <typename TX, typename TS, bool VEC, bool SH>
 __global__ void __launch_bounds__(kThreads, 2)
     k_iteration(const TX* __restrict__ X, int64_t ldx, TS* __restrict__ L, TS* __restrict__ S,
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         TS* lc = L + col * lds;
         TS* scol = S + col * lds;
         TS* tc = Th + col * lds;
-        float own = 0.f, dlc = 0.f, yl = 0.f;
+        float own = 0.f, dlc = 0.f, yl = 0.f, yq = 0.f;
         if (VEC) {
             float4 xv[4], sv[4], tv[4], lv[4];
 #pragma unroll
@@ -139,10 +143,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                         lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(lo.x), fabsf(lo.y)), fmaxf(fabsf(lo.z), fabsf(lo.w))));
                     if constexpr (SH) {
                         __half2 h0, h1;
-                        h0.x = copy16(lo.x, sc.sh_scale, inv_s, yl);
-                        h0.y = copy16(lo.y, sc.sh_scale, inv_s, yl);
-                        h1.x = copy16(lo.z, sc.sh_scale, inv_s, yl);
-                        h1.y = copy16(lo.w, sc.sh_scale, inv_s, yl);
+                        h0.x = copy16(lo.x, sc.sh_scale, inv_s, yl, yq);
+                        h0.y = copy16(lo.y, sc.sh_scale, inv_s, yl, yq);
+                        h1.x = copy16(lo.z, sc.sh_scale, inv_s, yl, yq);
+                        h1.y = copy16(lo.w, sc.sh_scale, inv_s, yl, yq);
                         uint2 u;
                         u.x = *reinterpret_cast<const uint32_t*>(&h0);
                         u.y = *reinterpret_cast<const uint32_t*>(&h1);
@@ -173,11 +177,17 @@ __global__ void __launch_bounds__(kThreads, 2)
         ndl += dlc;
         own = warp_sum(own);
         dlc = warp_sum(dlc);
-        if constexpr (SH) yl = warp_sum(yl);
+        if constexpr (SH) {
+            yl = warp_sum(yl);
+            yq = warp_sum(yq);
+        }
         if (lane == 0) {
             own_part[(int64_t)blockIdx.y * n + col] = own;
             dl_part[(int64_t)blockIdx.y * n + col] = dlc;
-            if constexpr (SH) ylo_part[(int64_t)blockIdx.y * n + col] = yl;
+            if constexpr (SH) {
+                ylo_part[(int64_t)blockIdx.y * n + col] = yl;
+                ylo_part[((int64_t)gridDim.y + blockIdx.y) * n + col] = yq;
+            }
         }
     }
 

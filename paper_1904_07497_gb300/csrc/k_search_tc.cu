@@ -942,8 +942,9 @@ constexpr int kTtMaxS = 4;
 //   0: FP32 operand truncated to TF32 by the MMA; the kernel sums ||y - tf32(y)||^2.
 //   1: 16-bit operand that is the data itself (y~ = y).
 //   2: FP16 copy fp16(s y) of FP32 data y, s = status->sh_scale; ycol[j] bounds
-//      ||y_j - y~_j|| (y~ = copy / s; formed where the copy is written), the
-//      products and norms carry s^2, and the distances are bounded through y~.
+//      ||y_j - y~_j|| and ycol[n + j] is ||y~_j||^2 (y~ = copy / s; both formed where
+//      the copy is written, so the kernel reads no norms from its stages), the
+//      products carry s^2, and the distances are bounded through y~.
 // With 16-bit operands the centroids are split into two 16-bit parts whose
 // sum is within a16_err[i] of mu_i (exact norm of the split's error, bounded).
 struct DenseTArgs {
@@ -1011,6 +1012,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
     // walk backwards on every other all-column pass (the finalize counts them)
     const bool rev = (status->dense_passes & 1) != 0;
     constexpr uint32_t kTmemCols = 512;                // two 128 x 256 FP32 accumulators
+    const bool norms = a.ymode != 2;                  // column norms from the stages (not given)
 
     if (warp == 1) {
         tmem_alloc(&tmem_base_sh, kTmemCols);
@@ -1076,7 +1078,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                     break;
                 }
                 if (!mbar_wait_or_abort(&full[sr.idx], sr.phase, &abort_sh) ||
-                    !mbar_wait_or_abort(&conv[sr.idx], sr.phase, &abort_sh)) {
+                    (norms && !mbar_wait_or_abort(&conv[sr.idx], sr.phase, &abort_sh))) {
                     abort_sh = 1;
                     break;
                 }
@@ -1116,10 +1118,65 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         RingPos sr(S), ar(2);
         UnitWalk uw(w0, w1, a.Q, rev);
         float ysq[2] = {0.f, 0.f}, ycomp[2] = {0.f, 0.f}, ylo2[2] = {0.f, 0.f};
+        // drains a finished tile segment's accumulator (lane = A row) into Gpart, with
+        // this thread's column-norm partials when the kernel forms them
+        auto epilogue = [&](int64_t cur_tile) {
+            const int slot = (int)(b - sk_owner(cur_tile * a.Q, a.W, G));
+            // stacked: row i + 64 (lo part) is added into row i before the store
+            const int rows_out = a.stacked ? 64 : 128;
+            const bool lo_row = a.stacked && m >= 64;
+            float* grow = Gpart + (((int64_t)cur_tile * a.cmax + slot) * rows_out + (m & (rows_out - 1))) * kTtN;
+            for (int cb = 0; cb < kTtN; cb += 16) {
+                float vv[16];
+                tc_ld16(tmem + lane_base + (uint32_t)(ar.idx * kTtN + cb), vv);
+                if (a.stacked) {
+                    if (lo_row) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) xch[m - 64][q] = vv[q];
+                    }
+                    named_sync(1, 128);
+                    if (!lo_row) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) vv[q] += xch[m][q];
+                    }
+                    named_sync(1, 128);
+                }
+                if (!lo_row) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4*>(grow + cb + q) = make_float4(vv[q], vv[q + 1], vv[q + 2], vv[q + 3]);
+                }
+            }
+            if (!norms) return;
+            float* yn = ynorm_part + ((int64_t)cur_tile * a.cmax + slot) * kTtN;
+            yn[m] = ysq[0];
+            yn[m + 128] = ysq[1];
+            if (!k16) {
+                float* yl = yn + a.T * a.cmax * kTtN;   // ||y - tf32(y)||^2 partials in the second half
+                yl[m] = ylo2[0];
+                yl[m + 128] = ylo2[1];
+            }
+        };
         for (int64_t w = w0; w < w1; ++w) {
             const bool seg_start = uw.seg_start();
             const bool seg_end = uw.seg_end();
             if (seg_start) ysq[0] = ysq[1] = ycomp[0] = ycomp[1] = ylo2[0] = ylo2[1] = 0.f;
+            if (!norms) {   // only the epilogue
+                const int64_t cur_tile = uw.tile;
+                uw.next();
+                if (!seg_end) continue;
+                if (!mbar_wait_or_abort(&acc_full[ar.idx], ar.phase, &abort_sh)) {
+                    abort_sh = 1;
+                    break;
+                }
+                tc_fence_after();
+                epilogue(cur_tile);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[ar.idx]);
+                ar.next();
+                continue;
+            }
             if (!mbar_wait_or_abort(&full[sr.idx], sr.phase, &abort_sh)) {
                 abort_sh = 1;
                 break;
@@ -1163,40 +1220,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                 break;
             }
             tc_fence_after();
-            const int slot = (int)(b - sk_owner(cur_tile * a.Q, a.W, G));
-            // stacked: row i + 64 (lo part) is added into row i before the store
-            const int rows_out = a.stacked ? 64 : 128;
-            const bool lo_row = a.stacked && m >= 64;
-            float* grow = Gpart + (((int64_t)cur_tile * a.cmax + slot) * rows_out + (m & (rows_out - 1))) * kTtN;
-            for (int cb = 0; cb < kTtN; cb += 16) {
-                float vv[16];
-                tc_ld16(tmem + lane_base + (uint32_t)(ar.idx * kTtN + cb), vv);
-                if (a.stacked) {
-                    if (lo_row) {
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) xch[m - 64][q] = vv[q];
-                    }
-                    named_sync(1, 128);
-                    if (!lo_row) {
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) vv[q] += xch[m][q];
-                    }
-                    named_sync(1, 128);
-                }
-                if (!lo_row) {
-#pragma unroll
-                    for (int q = 0; q < 16; q += 4)
-                        *reinterpret_cast<float4*>(grow + cb + q) = make_float4(vv[q], vv[q + 1], vv[q + 2], vv[q + 3]);
-                }
-            }
-            float* yn = ynorm_part + ((int64_t)cur_tile * a.cmax + slot) * kTtN;
-            yn[m] = ysq[0];
-            yn[m + 128] = ysq[1];
-            if (!k16) {
-                float* yl = yn + a.T * a.cmax * kTtN;   // ||y - tf32(y)||^2 partials in the second half
-                yl[m] = ylo2[0];
-                yl[m + 128] = ylo2[1];
-            }
+            epilogue(cur_tile);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ar.idx]);
@@ -1246,7 +1270,7 @@ __global__ void __launch_bounds__(kFinThreads)
         mu2v[q] = i < c ? __ldg(mu_normf + i) : 0.f;
         serr[q] = (a.ymode != 0 && i < c) ? __ldg(a.a16_err + i) : 0.f;
     }
-    // the FP16 copy's products and norms carry s^2 (s a power of two: exact)
+    // the FP16 copy's products carry s^2 (s a power of two: exact)
     const float inv2 = a.ymode == 2 ? status->sh_inv2 : 1.f;
     const int rows = a.stacked ? 64 : 128;   // the stacked kernel has added the lo rows in
     const float* gt = Gpart + (int64_t)tile * a.cmax * rows * kTtN + jc0 + jl;
@@ -1260,8 +1284,11 @@ __global__ void __launch_bounds__(kFinThreads)
     if (t < kFinCols) {
         const float* yt = ynorm_part + (int64_t)tile * a.cmax * kTtN + jc0 + t;
         float y2 = 0.f;
-        for (int sl = 0; sl < ncontrib; ++sl) y2 += __ldcg(yt + (int64_t)sl * kTtN);
-        y2 *= inv2;
+        if (a.ymode == 2) {   // ||y~||^2 formed with the copy
+            if (col0 + t < a.n) y2 = __ldg(a.ycol + a.n + col0 + t);
+        } else {
+            for (int sl = 0; sl < ncontrib; ++sl) y2 += __ldcg(yt + (int64_t)sl * kTtN);
+        }
         ys[t] = y2;
         if (a.ymode == 0) {
             // ||y - tf32(y)||: FP32 sums of at most d squares, so the norm is
@@ -1505,8 +1532,19 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t r1 = r0 + kSplitPer < dw ? r0 + kSplitPer : dw;
     const float s = (s16.a16 && s16.a16_kind == 2) ? s16.status->sh_scale : 1.f;
     float e2 = 0.f;
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += kThreads) {
-        const float v = (i < c && r < d) ? mu[(int64_t)i * d + r] : 0.f;
+    // the row chunk's loads first, all in flight together
+    constexpr int kPer = kSplitPer / kThreads;
+    float vv[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int64_t r = r0 + threadIdx.x + (int64_t)k * kThreads;
+        vv[k] = (i < c && r < d && r < r1) ? __ldg(mu + (int64_t)i * d + r) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int64_t r = r0 + threadIdx.x + (int64_t)k * kThreads;
+        if (r >= r1) break;
+        const float v = vv[k];
         if (r < dpad) {
             const int64_t o = (int64_t)i * dpad + r;
             const float hi = tf32_hi(v);

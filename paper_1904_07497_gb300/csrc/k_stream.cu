@@ -605,6 +605,7 @@ __global__ void __launch_bounds__(kThreads)
                   float* __restrict__ lb, int32_t* __restrict__ flag_list,
                   DevStatus* __restrict__ status, int32_t* __restrict__ labels_copy,
                   const float* __restrict__ ylo_part, float* __restrict__ ycol, float ycol_floor) {
+    // ycol: [0, n) ||L_j - y~_j|| (bounded), [n, 2n) ||y~_j||^2 of the FP16 copy
     // largest and second largest drift over active clusters (per block)
     __shared__ double s_d1[kThreads], s_d2[kThreads];
     __shared__ int s_i1[kThreads];
@@ -691,17 +692,29 @@ __global__ void __launch_bounds__(kThreads)
                 // ||L_j - bf16(L_j)|| from the fused pass's chunk partials (the search of
                 // this iteration's L runs on its 16-bit copy), same summation; the floor
                 // covers squares that underflowed
+                const float* yq_part = ylo_part + (int64_t)nchunks * n;
                 float sy[4] = {0.f, 0.f, 0.f, 0.f}, cy[4] = {0.f, 0.f, 0.f, 0.f};
+                float sq[4] = {0.f, 0.f, 0.f, 0.f}, cq[4] = {0.f, 0.f, 0.f, 0.f};
                 int k = 0;
                 for (; k + 4 <= nchunks; k += 4) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) kahan(sy[q], cy[q], ylo_part[(int64_t)(k + q) * n + j]);
+                    for (int q = 0; q < 4; ++q) {
+                        kahan(sy[q], cy[q], ylo_part[(int64_t)(k + q) * n + j]);
+                        kahan(sq[q], cq[q], yq_part[(int64_t)(k + q) * n + j]);
+                    }
                 }
-                for (; k < nchunks; ++k) kahan(sy[0], cy[0], ylo_part[(int64_t)k * n + j]);
-                double yl = 0.0;
+                for (; k < nchunks; ++k) {
+                    kahan(sy[0], cy[0], ylo_part[(int64_t)k * n + j]);
+                    kahan(sq[0], cq[0], yq_part[(int64_t)k * n + j]);
+                }
+                double yl = 0.0, yq = 0.0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) yl += (double)sy[q] - (double)cy[q];
+                for (int q = 0; q < 4; ++q) {
+                    yl += (double)sy[q] - (double)cy[q];
+                    yq += (double)sq[q] - (double)cq[q];
+                }
                 ycol[j] = (float)(sqrt(yl) * (1.0 + kRelSlack)) + ycol_floor;
+                ycol[n + j] = (float)yq;
             }
         } else {
             const double own_drift = drift ? drift[p] : 0.0;

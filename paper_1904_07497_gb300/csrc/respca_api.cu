@@ -1112,8 +1112,8 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
         if (use_sh) {
             h->sh_ld = (d + 7) / 8 * 8;
             CK(ensure(h->Lsh, sizeof(uint16_t) * (size_t)h->sh_ld * n));
-            CK(ensure(h->ylo_part, sizeof(float) * (size_t)nch * n));
-            CK(ensure(h->ycol, sizeof(float) * n));
+            CK(ensure(h->ylo_part, sizeof(float) * 2 * (size_t)nch * n));
+            CK(ensure(h->ycol, sizeof(float) * 2 * (size_t)n));
             sc.sh_scale = copy_scale(lmax_ref);
             out.copy16_iters += 1;
         }
