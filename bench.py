@@ -294,9 +294,10 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_traffic(kernel_file, profile_name):
-    """Per-launch DRAM bytes of the fused kernel from a committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+def kernel_traffic(kernel_file, profile_name, key="dram_bytes_per_launch_scaled"):
+    """Per-launch DRAM bytes of a kernel from a committed ncu summary (the
+    value under `key`), valid only while the kernel source is unchanged since
+    the capture."""
     prof = os.path.join(ROOT, "profiles", profile_name)
     src = os.path.join(ROOT, "paper_1904_07497_gb300", "csrc", kernel_file)
     try:
@@ -312,9 +313,23 @@ def kernel_traffic(kernel_file, profile_name):
     if vals.get("source_sha256_16") != sha:
         return None
     try:
-        return float(vals["dram_bytes_per_launch_scaled"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def iteration_traffic(workload, nf, nb, ncopy):
+    """Average DRAM bytes per fused-iteration launch: the summary's figure for
+    launches without the FP16 copy of L and, where any wrote it, the one for
+    launches with it, weighted by their counts (None with bf16-phase launches)."""
+    prof = f"k_iteration_{workload}.txt"
+    plain = kernel_traffic("k_iteration.cu", prof)
+    if plain is None or nb or nf <= 0:
+        return None
+    if ncopy == 0:
+        return plain
+    copy = kernel_traffic("k_iteration.cu", prof, "dram_bytes_per_launch_scaled_copy16")
+    return None if copy is None else round((plain * (nf - ncopy) + copy * ncopy) / nf)
 
 
 # ---------------------------------------------------------------- replicas
@@ -411,8 +426,7 @@ def run_gpu(args, rank, world, local_rank):
                   if args.s_norm else "k_iteration (fused ALM iteration)",
                   "achieved": round(fused_gbs, 1), "peak": peak, "unit": "GB/s",
                   "frac": round(fused_gbs / peak, 4), "peak_source": peak_kind,
-                  "traffic": None if args.s_norm else
-                  kernel_traffic("k_iteration.cu", f"k_iteration_{args.workload}.txt"),
+                  "traffic": None if args.s_norm else iteration_traffic(args.workload, nf, nb, ts["copy16_iters"]),
                   "algorithmic_bytes_per_launch": fused_bytes, "avg_launch_ms": round(fused_avg, 4),
                   "launches": ts["fused_launches"], "total_ms": round(ts["ms_fused"], 3)}
     rooflines = [roof_fused]
