@@ -1242,7 +1242,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
 // warp per column scores it from there.  Small blocks keep several per SM
 // resident, so one wave covers n = 10^4 and their latencies overlap.
 constexpr int kFinCols = 16, kFinThreads = 256;
-__global__ void __launch_bounds__(kFinThreads)
+// five blocks per SM (at most 48 registers): 625 blocks cover n = 10^4 in one wave
+__global__ void __launch_bounds__(kFinThreads, 5)
     k_finalize_t(DenseTArgs a, int G, DevStatus* __restrict__ status, const float* __restrict__ mu_normf,
                  const int32_t* __restrict__ counts, int c, int32_t* __restrict__ labels,
                  float* __restrict__ ub, float* __restrict__ lb, const float* __restrict__ Gpart,
@@ -1868,7 +1869,15 @@ cudaError_t launch_search_tc(int dtype, const void* Y, int64_t ldy, int64_t d, i
         // float4 rows need 16-byte aligned columns of Y and of the centroids (d % 4 == 0)
         const bool v4 = vec && sizeof(TY) == 4 && (reinterpret_cast<uintptr_t>(Y) % 16 == 0) &&
                         (reinterpret_cast<uintptr_t>(mu) % 16 == 0);
-        k_search_recheck<TY><<<4 * num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu, c,
+        // one resident wave (the pairs are taken grid-stride): further waves would be CTAs
+        // that find no pair (the FP32 form holds 171 registers, one CTA per SM)
+        static const int per_sm = [] {
+            int b = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search_recheck<TY>, kThreads, 0) != cudaSuccess)
+                b = 1;
+            return std::min(4, std::max(1, b));
+        }();
+        k_search_recheck<TY><<<per_sm * num_sms(), kThreads, 0, st>>>((const TY*)Y, ldy, d, v4, status, mu, c,
                                                                labels, ub, lb, rc_list, rc_pairs, rc_dist,
                                                                rc_cap);
     });
