@@ -733,6 +733,24 @@ __global__ void __launch_bounds__(kThreads)
     if (flag) flag_list[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)j;
 }
 
+// The end of a device-run Lloyd pass's search: adds the pass counters, sets the
+// loop's condition and clears the counters for the next pass (one thread).
+__device__ void lloyd_pass_end(DevStatus* __restrict__ status, cudaGraphConditionalHandle cond,
+                               int max_passes) {
+    status->acc_flagged += status->flagged;
+    status->acc_rechecked += status->rechecked;
+    status->acc_changed += status->changed;
+    const int passes = ++status->acc_passes;
+    const bool more = status->changed != 0 && passes < max_passes && status->timeout == 0;
+    cudaGraphSetConditional(cond, more ? 1u : 0u);
+    // hand the pass's result to the host and clear the counters for the next pass
+    status->last_changed = status->changed;
+    status->flagged = 0;
+    status->changed = 0;
+    status->rechecked = 0;
+    status->rc_pairs = 0;
+}
+
 // Columns whose label differs between `now` and `before`, in column order
 // (single CTA; deterministic), as (column, old, new) triples; the cluster
 // sizes follow the move.  Each thread takes kMovedK consecutive columns per
@@ -743,10 +761,13 @@ constexpr int kMovedThreads = 1024, kMovedK = 8;
 __global__ void __launch_bounds__(kMovedThreads)
     k_moved(const int32_t* __restrict__ now, const int32_t* __restrict__ before, int64_t n, int c,
             int4* __restrict__ moved, int2* __restrict__ contrib, int32_t* __restrict__ boff,
-            int32_t* __restrict__ counts, DevStatus* __restrict__ status) {
+            int32_t* __restrict__ counts, DevStatus* __restrict__ status, PassEnd pe) {
     __shared__ int wsum[32];
     __shared__ int base_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // in a device-run Lloyd pass this kernel follows the search: it also ends it (the
+    // fields it touches are read by none of the work below)
+    if (pe.on && threadIdx.x == 0) lloyd_pass_end(status, pe.cond, pe.max_passes);
     if (threadIdx.x == 0) base_sh = 0;
     __syncthreads();
     for (int64_t b0 = 0; b0 < n; b0 += (int64_t)kMovedThreads * kMovedK) {
@@ -983,27 +1004,14 @@ __global__ void k_lloyd_init(DevStatus* __restrict__ status, int passes0) {
     status->acc_flagged = 0;
     status->acc_passes = passes0;
     status->acc_rechecked = 0;
-    status->flagged = 0;   // the per-pass counters start at zero (k_lloyd_pass_end re-zeroes them)
+    status->acc_changed = 0;
+    status->flagged = 0;   // the per-pass counters start at zero (each pass's end re-zeroes them)
     status->changed = 0;
     status->rechecked = 0;
     status->rc_pairs = 0;
     status->last_changed = 0;
 }
 
-__global__ void k_lloyd_pass_end(DevStatus* __restrict__ status, cudaGraphConditionalHandle cond,
-                                 int max_passes) {
-    status->acc_flagged += status->flagged;
-    status->acc_rechecked += status->rechecked;
-    const int passes = ++status->acc_passes;
-    const bool more = status->changed != 0 && passes < max_passes && status->timeout == 0;
-    cudaGraphSetConditional(cond, more ? 1u : 0u);
-    // hand the pass's result to the host and clear the counters for the next pass
-    status->last_changed = status->changed;
-    status->flagged = 0;
-    status->changed = 0;
-    status->rechecked = 0;
-    status->rc_pairs = 0;
-}
 
 inline int grid_for(int64_t work, int per) { return (int)((work + per - 1) / per); }
 
@@ -1158,9 +1166,10 @@ cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_
 
 cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int c, int4* moved,
                          int2* contrib, int32_t* boff, int32_t* counts, DevStatus* status,
-                         cudaStream_t st) {
+                         cudaStream_t st, const PassEnd* pe) {
     count_launches(1);
-    k_moved<<<1, kMovedThreads, 0, st>>>(now, before, n, c, moved, contrib, boff, counts, status);
+    k_moved<<<1, kMovedThreads, 0, st>>>(now, before, n, c, moved, contrib, boff, counts, status,
+                                         pe ? *pe : PassEnd{});
     return cudaGetLastError();
 }
 
@@ -1262,13 +1271,6 @@ cudaError_t launch_column_norms(const float* S, int64_t lds, int64_t d, int64_t 
 cudaError_t launch_lloyd_init(DevStatus* status, int passes0, cudaStream_t st) {
     count_launches(1);
     k_lloyd_init<<<1, 1, 0, st>>>(status, passes0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lloyd_pass_end(DevStatus* status, cudaGraphConditionalHandle cond, int max_passes,
-                                  cudaStream_t st) {
-    count_launches(1);
-    k_lloyd_pass_end<<<1, 1, 0, st>>>(status, cond, max_passes);
     return cudaGetLastError();
 }
 

@@ -562,12 +562,13 @@ struct SearchCounts {
     int passes = 0;
     int64_t assigned = 0;
     int64_t rechecked = 0;
+    int64_t changed = 0;   // labels changed, summed over the passes counted here
 };
 
 // One Lloyd pass, first half: degrade the bounds by the centroid drift,
 // queue the columns they cannot settle, search them.
 // In the device-run loop the counters are cleared by the previous pass's
-// k_lloyd_pass_end (and by k_lloyd_init before the first), not here.
+// end (k_moved of its update) and by k_lloyd_init before the first, not here.
 respca_status lloyd_pass_search(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ldy,
                                 int64_t d, int64_t n, int c, int32_t* p, bool vec, bool in_graph = false) {
     (void)mode;
@@ -582,11 +583,11 @@ respca_status lloyd_pass_search(respca_ctx* h, int mode, int dtype, const void* 
 // Second half: move the changed columns between the cluster sums and form the
 // new centroids, their norms and drift.
 respca_status lloyd_pass_update(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ldy,
-                                int64_t d, int64_t n, int c, int32_t* p) {
+                                int64_t d, int64_t n, int c, int32_t* p, const PassEnd* pe = nullptr) {
     DevStatus* ds = P<DevStatus>(h->status);
     const float* Lp = (mode == kSumL) ? static_cast<const float*>(Y) : nullptr;
     CK(launch_moved(p, P<int32_t>(h->labels_pass), n, c, P<int4>(h->moved), P<int2>(h->contrib),
-                    P<int32_t>(h->boff), P<int32_t>(h->counts), ds, h->stream));
+                    P<int32_t>(h->boff), P<int32_t>(h->counts), ds, h->stream, pe));
     CK(launch_delta_sums(mode, dtype, Y, ldy, Lp, ldy, P<int2>(h->contrib), P<int32_t>(h->boff), c, d,
                          P<double>(h->sums), h->stream));
     MuSplitOut sp;
@@ -632,8 +633,8 @@ uint64_t lloyd_key(respca_ctx* h, int mode, int dtype, const void* Y, int64_t ld
 }
 
 // The Lloyd loop run on the device: one pass is captured once into the body
-// of a conditional while node; a one-thread kernel at the end of each pass's
-// search adds the pass counters and sets the condition.  The host reads the
+// of a conditional while node; the first kernel of each pass's update (k_moved)
+// also adds the pass counters and sets the condition.  The host reads the
 // status once, after the loop.  The centroid update runs after the last pass
 // too; when the loop stopped at max_passes with labels still moving, the
 // centroids of that pass's search are put back (the host loop stops before
@@ -681,10 +682,12 @@ respca_status lloyd_loop_on_device(respca_ctx* h, int mode, int dtype, const voi
             rs = RESPCA_ERR_UNSUPPORTED;
         } else {
             rs = lloyd_pass_search(h, mode, dtype, Y, ldy, d, n, c, p, vec, true);
-            if (rs == RESPCA_OK && launch_lloyd_pass_end(P<DevStatus>(h->status), cond, max_passes,
-                                                         h->stream) != cudaSuccess)
-                rs = RESPCA_ERR_CUDA;
-            if (rs == RESPCA_OK) rs = lloyd_pass_update(h, mode, dtype, Y, ldy, d, n, c, p);
+            // the update's first kernel ends the pass (counters, loop condition)
+            PassEnd pe;
+            pe.cond = cond;
+            pe.max_passes = max_passes;
+            pe.on = 1;
+            if (rs == RESPCA_OK) rs = lloyd_pass_update(h, mode, dtype, Y, ldy, d, n, c, p, &pe);
             cudaGraph_t captured = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(h->stream, &captured);
             if (rs == RESPCA_OK && ec != cudaSuccess) rs = RESPCA_ERR_UNSUPPORTED;
@@ -721,6 +724,7 @@ respca_status lloyd_loop_on_device(respca_ctx* h, int mode, int dtype, const voi
     sc->passes = h->hstat->acc_passes;
     sc->assigned += h->hstat->acc_flagged;
     sc->rechecked += h->hstat->acc_rechecked;
+    sc->changed += h->hstat->acc_changed;
     if (h->hstat->last_changed != 0)   // stopped at max_passes: back to the last search's centroids
         CK(cudaMemcpyAsync(h->mu.p, h->mu_old.p, sizeof(float) * (size_t)c * d, cudaMemcpyDeviceToDevice,
                            h->stream));
@@ -787,6 +791,7 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
         sc->passes += 1;
         sc->assigned += h->hstat->flagged;
         sc->rechecked += h->hstat->rechecked;
+        sc->changed += h->hstat->changed;
         if (h->hstat->changed == 0 || sc->passes >= max_passes) break;
         rs = lloyd_pass_update(h, mode, dtype, Y, ldy, d, n, c, p);
         if (rs != RESPCA_OK) return rs;
@@ -1196,6 +1201,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             // Lloyd on the columns of L until no label changes
             SearchCounts scount;
             scount.passes = 1;
+            scount.changed = h->hstat->changed;   // the first search's
             // (BF16 L is summed as the "X" operand: the sums only need its element type)
             rs = v.sd == 1 ? lloyd_continue(h, kSumX, RESPCA_BF16, v.L, v.ld, d, n, c, p, v.vec, km, &scount)
                            : lloyd_continue(h, kSumL, RESPCA_F32, v.L, v.ld, d, n, c, p, v.vec, km, &scount,
@@ -1204,8 +1210,11 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             out.lloyd_passes += scount.passes - 1;
             out.assigned_columns += scount.assigned;
             out.rechecked_columns += scount.rechecked;
-            // next centroids: D = X - S + Theta/rho_{t+1} under the final labels
-            if (v.sd == 0) {
+            // next centroids: D = X - S + Theta/rho_{t+1} under the final labels.  The
+            // correction below reads D at each moved column twice (24 B per element and
+            // moved column), the recount once for every column (12 B per element): it
+            // takes over from n / 8 moves on (the summed label changes bound the moves)
+            if (v.sd == 0 && scount.changed <= n / 8) {
                 // the fused pass's sums under the starting labels, corrected by
                 // the columns whose label the p step changed
                 CK(launch_moved(p, P<int32_t>(h->labels_prev), n, c, P<int4>(h->moved),

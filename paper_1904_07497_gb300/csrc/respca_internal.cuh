@@ -68,6 +68,7 @@ struct DevStatus {
     int64_t acc_flagged;    // device-run Lloyd loop: columns searched over its passes
     int32_t acc_passes;     //   passes run (including those before the loop)
     int32_t acc_rechecked;  //   near ties re-decided
+    int32_t acc_changed;    //   labels changed (summed over passes)
     int32_t seed_done;      // CTAs of the current k-means++ step that finished (reset by the last)
     int32_t dense_passes;   // all-column search passes so far (their parity sets the walking direction)
     int32_t norms_done;     // CTAs of the norm reduction that finished (reset by the last)
@@ -163,9 +164,16 @@ cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_
                                int32_t* labels_copy = nullptr, const float* ylo_part = nullptr,
                                float* ycol = nullptr, int64_t d = 0);
 
+// The end of a device-run Lloyd pass (its counters and the loop's condition),
+// done by the first kernel of the pass's update when on.
+struct PassEnd {
+    cudaGraphConditionalHandle cond = 0;
+    int max_passes = 0;
+    int on = 0;
+};
 cudaError_t launch_moved(const int32_t* now, const int32_t* before, int64_t n, int c, int4* moved,
                          int2* contrib, int32_t* boff, int32_t* counts, DevStatus* status,
-                         cudaStream_t st);
+                         cudaStream_t st, const PassEnd* pe = nullptr);
 
 cudaError_t launch_mu_norms(const float* mu, int c, int64_t d, double* mu_norm2, float* mu_normf,
                             cudaStream_t st);
@@ -211,12 +219,11 @@ cudaError_t launch_iteration_l21(int dtype, const void* X, int64_t ldx, float* L
                                  int64_t d, int64_t n, IterScalars sc, float* Dpart, float* own_part,
                                  float* dl_part, float* bn_part, double* norm_part, bool vec,
                                  cudaStream_t st);
-// Device-run Lloyd loop: start its counters at `passes0` passes; at the end
-// of each pass, add the pass's counters and set the loop's condition (labels
-// changed, fewer than max_passes passes, no wait gave up).
+// Device-run Lloyd loop: start its counters at `passes0` passes.  At the end of
+// each pass's search, the update's first kernel (launch_moved with a PassEnd)
+// adds the pass's counters and sets the loop's condition (labels changed, fewer
+// than max_passes passes, no wait gave up).
 cudaError_t launch_lloyd_init(DevStatus* status, int passes0, cudaStream_t st);
-cudaError_t launch_lloyd_pass_end(DevStatus* status, cudaGraphConditionalHandle cond, int max_passes,
-                                  cudaStream_t st);
 cudaError_t launch_column_norms(const float* S, int64_t lds, int64_t d, int64_t n, float* out,
                                 cudaStream_t st);
 cudaError_t launch_convert(int src_dtype, const void* src, int64_t lds, int dst_sdtype, void* dst,
