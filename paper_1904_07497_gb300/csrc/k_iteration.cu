@@ -50,17 +50,6 @@ __device__ __forceinline__ void alm_element(float x, float s, float t, float l0,
     dnext = (x - sn) + tn * sc.inv_rho_next;          // D of the next iteration
 }
 
-// FP16 copy of one value, the square of its error e = l - y~ and of y~ = h / s,
-// h = fp16(clamp(s l)) (e exact in FP32 unless clamped or below the normal range).
-__device__ __forceinline__ __half copy16(float l, float s, float inv_s, float& e2, float& q2) {
-    const __half h = __float2half_rn(fminf(fmaxf(l * s, -65504.f), 65504.f));
-    const float y = __half2float(h) * inv_s;
-    const float e = l - y;
-    e2 = fmaf(e, e, e2);
-    q2 = fmaf(y, y, q2);
-    return h;
-}
-
 // SH: also the FP16 copy Lsh (column stride ldsh, scale sc.sh_scale) and, per
 // row chunk and column, ||L_j - y~_j||^2 in ylo_part[chunk][col] and ||y~_j||^2 in
 // ylo_part[nchunks + chunk][col] (y~ = copy / s).

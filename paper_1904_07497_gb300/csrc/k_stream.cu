@@ -733,6 +733,54 @@ __global__ void __launch_bounds__(kThreads)
     if (flag) flag_list[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)j;
 }
 
+// FP16 copy fp16(s x) of FP32 columns for the all-column search over X (column
+// stride ld16), with each column's ||x - y~|| (bounded: compensated FP32 sums,
+// inflated, plus the underflow floor) in ycol[j] and ||y~||^2 in ycol[n + j],
+// y~ = copy / s; the scale goes to the status for the centroid split and the
+// finalize.  One warp per column, 16-byte rows (d % 4 == 0, aligned columns).
+__global__ void __launch_bounds__(kThreads)
+    k_copy16_cols(const float* __restrict__ X, int64_t ldx, int64_t d, int64_t n, float s,
+                  __half* __restrict__ Y16, int64_t ld16, float* __restrict__ ycol, float floor,
+                  DevStatus* __restrict__ status) {
+    const float inv_s = 1.f / s;   // a power of two: exact
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        status->sh_scale = s;
+        status->sh_inv2 = inv_s * inv_s;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const float* x = X + j * ldx;
+    __half* y = Y16 + j * ld16;
+    float se = 0.f, ce = 0.f, sq = 0.f, cq = 0.f;
+    auto kahan = [](float& sum, float& comp, float v) {
+        const float t = v - comp;
+        const float u = sum + t;
+        comp = (u - sum) - t;
+        sum = u;
+    };
+    for (int64_t r = (int64_t)lane * 4; r < d; r += 128) {
+        const float4 v = *reinterpret_cast<const float4*>(x + r);
+        float e2 = 0.f, q2 = 0.f;
+        __half2 h0, h1;
+        h0.x = copy16(v.x, s, inv_s, e2, q2);
+        h0.y = copy16(v.y, s, inv_s, e2, q2);
+        h1.x = copy16(v.z, s, inv_s, e2, q2);
+        h1.y = copy16(v.w, s, inv_s, e2, q2);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t*>(&h0);
+        u.y = *reinterpret_cast<const uint32_t*>(&h1);
+        *reinterpret_cast<uint2*>(y + r) = u;
+        kahan(se, ce, e2);
+        kahan(sq, cq, q2);
+    }
+    const double e = warp_sum((double)se - (double)ce), q = warp_sum((double)sq - (double)cq);
+    if (lane == 0) {
+        ycol[j] = (float)(sqrt(e) * (1.0 + 1e-5)) + floor;
+        ycol[n + j] = (float)q;
+    }
+}
+
 // The end of a device-run Lloyd pass's search: adds the pass counters, sets the
 // loop's condition and clears the counters for the next pass (one thread).
 __device__ void lloyd_pass_end(DevStatus* __restrict__ status, cudaGraphConditionalHandle cond,
@@ -1161,6 +1209,16 @@ cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_
                                                               labels, counts, sep2, safety, drift,
                                                               ub, lb, flag_list, status, labels_copy,
                                                               ylo_part, ycol, floor);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy16_cols(const float* X, int64_t ldx, int64_t d, int64_t n, float s, void* Y16,
+                              int64_t ld16, float* ycol, DevStatus* status, cudaStream_t st) {
+    count_launches(1);
+    // |x - y~| below 2^-75 squares to zero in FP32: sqrt(d) 2^-74 covers all of them
+    const float floor = (float)(std::sqrt((double)d) * 5.29395592033938e-23);
+    k_copy16_cols<<<grid_for(n, kThreads / 32), kThreads, 0, st>>>(X, ldx, d, n, s, static_cast<__half*>(Y16),
+                                                                  ld16, ycol, floor, status);
     return cudaGetLastError();
 }
 

@@ -801,7 +801,9 @@ respca_status lloyd_continue(respca_ctx* h, int mode, int dtype, const void* Y, 
 
 // Initial labels: k-means++ seeding (D^2 sampling with splitmix64 draws),
 // then Lloyd on the columns of X until no label changes.
-respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out) {
+// xmax > 0 (max |X|, known to the solve): the all-column passes over an FP32 X
+// read an FP16 copy of it, written once here (as the iterations' passes read L's).
+respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out, float xmax = 0.f) {
     const int c = pb.c;
     uint64_t st = h->cfg.seed;
     for (int k = 0; k < c; ++k) h->hseed_u[k] = unit_draw(st);
@@ -824,6 +826,18 @@ respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out
     DevStatus* ds = P<DevStatus>(h->status);
     const int km = std::max(1, h->cfg.kmeans_max_iter);
     SearchCounts sc;
+    // large enough that the passes' savings (2 B per element each) repay the copy's 6 B
+    constexpr int64_t kCopyXMinElems = int64_t(1) << 22;
+    const bool copy_x = xmax > 0.f && pb.dtype == RESPCA_F32 && pb.vec && h->cfg.search_impl == 0 &&
+                        tc_npad(c) <= 128 && pb.d * pb.n >= kCopyXMinElems;
+    if (copy_x) {
+        h->sh_ld = (pb.d + 7) / 8 * 8;
+        CK(ensure(h->Lsh, sizeof(uint16_t) * (size_t)h->sh_ld * pb.n));
+        CK(ensure(h->ycol, sizeof(float) * 2 * (size_t)pb.n));
+        CK(launch_copy16_cols(static_cast<const float*>(pb.X), pb.ldx, pb.d, pb.n, copy_scale(xmax), h->Lsh.p,
+                              h->sh_ld, P<float>(h->ycol), P<DevStatus>(h->status), h->stream));
+        h->sh_for = pb.X;
+    }
     CK(zero_counters(h));
     respca_status rs = search(h, pb.dtype, pb.X, pb.ldx, pb.d, pb.n, nullptr, c, pb.p, pb.vec);
     if (rs != RESPCA_OK) return rs;
@@ -836,6 +850,7 @@ respca_status init_labels_impl(respca_ctx* h, const Problem& pb, int* passes_out
         rs = lloyd_continue(h, kSumX, pb.dtype, pb.X, pb.ldx, pb.d, pb.n, c, pb.p, pb.vec, km, &sc);
         if (rs != RESPCA_OK) return rs;
     }
+    if (copy_x) h->sh_for = nullptr;   // the buffer serves L's copy next
     if (passes_out) *passes_out = sc.passes;
     return RESPCA_OK;
 }
@@ -980,7 +995,7 @@ respca_status solve_impl(respca_ctx* h, int dtype, const void* X, int64_t d, int
             out.init_lloyd_passes = si.lloyd_passes;
         } else if (nx > 0.0) {
             int passes = 0;
-            rs = init_labels_impl(h, pb, &passes);
+            rs = init_labels_impl(h, pb, &passes, lmax_ref);   // lmax_ref is max |X| here
             if (rs != RESPCA_OK) return rs;
             out.init_lloyd_passes = passes;
         } else {

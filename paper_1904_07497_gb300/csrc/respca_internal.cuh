@@ -164,6 +164,13 @@ cudaError_t launch_flag_bounds(int mode, const float* own_part, const float* dl_
                                int32_t* labels_copy = nullptr, const float* ylo_part = nullptr,
                                float* ycol = nullptr, int64_t d = 0);
 
+// FP16 copy fp16(s X) of FP32 columns (16-byte aligned, d % 4 == 0) into Y16
+// (column stride ld16), each column's ||x - y~|| and ||y~||^2 into ycol[j] and
+// ycol[n + j] (y~ = copy / s), and s into the status (launch_iteration's copy of L,
+// for X): the operand of the all-column search over X.
+cudaError_t launch_copy16_cols(const float* X, int64_t ldx, int64_t d, int64_t n, float s, void* Y16,
+                              int64_t ld16, float* ycol, DevStatus* status, cudaStream_t st);
+
 // The end of a device-run Lloyd pass (its counters and the loop's condition),
 // done by the first kernel of the pass's update when on.
 struct PassEnd {
@@ -428,6 +435,17 @@ __device__ __forceinline__ void f4set(float4& v, int q, float x) {
 // The TF32 part of an FP32 value as the tensor cores read it (mantissa truncated
 // to 10 bits).
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// FP16 copy of one value, the square of its error e = l - y~ and of y~ = h / s,
+// h = fp16(clamp(s l)) (e exact in FP32 unless clamped or below the normal range).
+__device__ __forceinline__ __half copy16(float l, float s, float inv_s, float& e2, float& q2) {
+    const __half h = __float2half_rn(fminf(fmaxf(l * s, -65504.f), 65504.f));
+    const float y = __half2float(h) * inv_s;
+    const float e = l - y;
+    e2 = fmaf(e, e, e2);
+    q2 = fmaf(y, y, q2);
+    return h;
+}
 
 // Two-part 16-bit split of a centroid element v for the search of 16-bit
 // operands.  kind 1: p1 = bf16(v), p2 = bf16(v - p1); kind 2: the same in FP16
