@@ -61,12 +61,14 @@ def test_binding_struct_sizes_match_header(lib):
     import tempfile
     from paper_1904_07497_gb300 import respca
     src = ('#include "respca.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-           'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(respca_config),'
+           'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+           ' sizeof(respca_config),'
            ' sizeof(respca_stats), sizeof(respca_warm), sizeof(respca_problem),'
            ' offsetof(respca_stats, ms_total), offsetof(respca_problem, p),'
            ' sizeof(respca_spectral_info), offsetof(respca_config, spectral_scale),'
            ' offsetof(respca_stats, x_norm), sizeof(respca_batch_options),'
-           ' offsetof(respca_batch_options, ms_kernel));return 0;}\n')
+           ' offsetof(respca_batch_options, ms_kernel), offsetof(respca_stats, ms_dense16),'
+           ' offsetof(respca_stats, dense16_passes), offsetof(respca_stats, copy16_iters));return 0;}\n')
     with tempfile.TemporaryDirectory() as td:
         c = os.path.join(td, "probe.c")
         exe = os.path.join(td, "probe")
@@ -78,7 +80,8 @@ def test_binding_struct_sizes_match_header(lib):
             respca.respca_stats.ms_total.offset, respca.respca_problem.p.offset,
             ctypes.sizeof(respca.respca_spectral_info), respca.respca_config.spectral_scale.offset,
             respca.respca_stats.x_norm.offset, ctypes.sizeof(respca.respca_batch_options),
-            respca.respca_batch_options.ms_kernel.offset]
+            respca.respca_batch_options.ms_kernel.offset, respca.respca_stats.ms_dense16.offset,
+            respca.respca_stats.dense16_passes.offset, respca.respca_stats.copy16_iters.offset]
     assert got == want
 
 
